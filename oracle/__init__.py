@@ -1,0 +1,204 @@
+"""CPU oracle for the UV-atlas layer-editing path -- TEST INFRASTRUCTURE ONLY.
+
+Plain, slow, obviously correct restatements of each step (see ``lcl_oracle.c``),
+wrapped for numpy.  Only the tests, the smoke check and the benchmark's CPU
+baseline / reference arm use this package; the product library never does, and it
+shares no code with it.
+
+Layouts (shared data formats, each side has its own code for them):
+* position planes: three int32 planes X, Y, Z of H rows x W texels, row 0 at v = 0;
+  an uncovered texel holds (INT32_MIN, 0, 0);
+* triangle plane: uint32, 0xFFFFFFFF = uncovered;
+* coverage bits: bit (y*W + x) of a linear uint32 array;
+* tile boxes: 8 int32 per tile (min xyz, count, max xyz, 0);
+* sphere stroke record: int32 cx, cy, cz, pad; int64 r2; uint32 label, flags (32 bytes).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import build_oracle, library_path
+
+_lib = None
+NONE = 0xFFFFFFFF
+SUPER = 16          # tiles per super-tile side
+AND, OR, XOR, MASK = 0, 1, 2, 3
+NOT_A, NOT_B, NOT_OUT = 1, 2, 4
+OPS = {"and": AND, "or": OR, "xor": XOR, "mask": MASK}
+
+SPHERE_DTYPE = np.dtype([("cx", "<i4"), ("cy", "<i4"), ("cz", "<i4"), ("pad", "<i4"),
+                         ("r2", "<i8"), ("label", "<u4"), ("flags", "<u4")])
+assert SPHERE_DTYPE.itemsize == 32
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            build_oracle()
+        _lib = C.CDLL(path)
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _chk(rc, what):
+    if rc != 0:
+        raise OracleError(f"{what} failed with status {rc}")
+
+
+def _f3(v):
+    return (C.c_float * 3)(*[float(x) for x in v])
+
+
+def quant_params(pos: np.ndarray):
+    """(bbox_min float32[3], scale float64) of the 21-bit grid."""
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    mn = (C.c_float * 3)()
+    s = C.c_double()
+    _chk(lib().orc_quant_params(_p(pos), C.c_int64(pos.shape[0]), mn, C.byref(s)), "quant_params")
+    return np.array(list(mn), dtype=np.float32), float(s.value)
+
+
+def quantize(pos, mn, S):
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    q = np.empty((pos.shape[0], 3), dtype=np.int32)
+    _chk(lib().orc_quantize(_p(pos), C.c_int64(pos.shape[0]), _f3(mn), C.c_double(S), _p(q)), "quantize")
+    return q
+
+
+class Atlas:
+    """Oracle atlas for rows [y0, y1) of a W x H texture (full texture by default)."""
+
+    def __init__(self, mesh, W, H, tile=32, y0=0, y1=None, quant=None):
+        y1 = H if y1 is None else y1
+        self.W, self.H, self.T, self.y0, self.y1 = W, H, tile, y0, y1
+        self.mn, self.S = quant_params(mesh.pos) if quant is None else quant
+        rows = y1 - y0
+        self.px = np.empty((rows, W), np.int32)
+        self.py = np.empty((rows, W), np.int32)
+        self.pz = np.empty((rows, W), np.int32)
+        self.tri = np.empty((rows, W), np.uint32)
+        _chk(lib().orc_atlas(_p(mesh.pos), C.c_int64(mesh.pos.shape[0]), _p(mesh.uv), C.c_int64(mesh.uv.shape[0]),
+                             _p(mesh.tri_pos), _p(mesh.tri_uv), C.c_int64(mesh.n_tri), _f3(self.mn),
+                             C.c_double(self.S), C.c_int32(W), C.c_int32(H), C.c_int32(y0), C.c_int32(y1),
+                             _p(self.px), _p(self.py), _p(self.pz), _p(self.tri)), "atlas")
+        self.area_w = np.empty(mesh.n_tri, np.uint64)
+        _chk(lib().orc_area_weights(_p(mesh.pos), _p(mesh.uv), _p(mesh.tri_pos), _p(mesh.tri_uv),
+                                    C.c_int64(mesh.n_tri), _f3(self.mn), C.c_double(self.S), C.c_int32(W),
+                                    C.c_int32(H), _p(self.area_w)), "area_weights")
+
+    @property
+    def n_texels(self):
+        return (self.y1 - self.y0) * self.W
+
+    def covered(self):
+        return self.tri != NONE
+
+    def cover_bits(self):
+        rows = self.y1 - self.y0
+        bits = np.empty((rows * self.W + 31) // 32, np.uint32)
+        _chk(lib().orc_cover_bits(C.c_int32(self.W), C.c_int32(rows), _p(self.tri), _p(bits)), "cover_bits")
+        return bits
+
+    def tile_aabb(self):
+        assert self.y0 == 0 and self.y1 == self.H, "tile boxes need the full texture"
+        ntx, nty = -(-self.W // self.T), -(-self.H // self.T)
+        box = np.empty((nty * ntx, 8), np.int32)
+        _chk(lib().orc_tile_aabb(C.c_int32(self.W), C.c_int32(self.H), C.c_int32(self.T), _p(self.px),
+                                 _p(self.py), _p(self.pz), _p(self.tri), _p(box)), "tile_aabb")
+        return box
+
+    def super_aabb(self, box=None):
+        box = self.tile_aabb() if box is None else box
+        ntx, nty = -(-self.W // self.T), -(-self.H // self.T)
+        nsx, nsy = -(-ntx // SUPER), -(-nty // SUPER)
+        sbox = np.empty((nsy * nsx, 8), np.int32)
+        _chk(lib().orc_super_aabb(C.c_int32(ntx), C.c_int32(nty), C.c_int32(SUPER), _p(box), _p(sbox)),
+             "super_aabb")
+        return sbox
+
+
+def sphere_stroke(mn, S, centre, radius, label):
+    out = np.zeros(1, SPHERE_DTYPE)
+    c = (C.c_double * 3)(*[float(x) for x in centre])
+    _chk(lib().orc_sphere_stroke(_f3(mn), C.c_double(S), c, C.c_double(float(radius)), C.c_uint32(int(label)),
+                                 _p(out)), "sphere_stroke")
+    return out[0]
+
+
+def sphere_records(mn, S, centres, radii, labels):
+    recs = np.zeros(len(radii), SPHERE_DTYPE)
+    for k in range(len(radii)):
+        recs[k] = sphere_stroke(mn, S, centres[k], radii[k], labels[k])
+    return recs
+
+
+def select_sphere(atlas: Atlas, layer: np.ndarray, strokes: np.ndarray):
+    """Applies strokes in order to ``layer`` (in place, rows of the atlas window); returns hits."""
+    assert layer.shape == atlas.tri.shape and layer.flags["C_CONTIGUOUS"]
+    strokes = np.ascontiguousarray(strokes, dtype=SPHERE_DTYPE)
+    hits = np.zeros(len(strokes), np.uint64)
+    _chk(lib().orc_select_sphere(C.c_int64(atlas.n_texels), _p(atlas.px), _p(atlas.py), _p(atlas.pz),
+                                 _p(atlas.tri), _p(layer), C.c_int(layer.itemsize), _p(strokes),
+                                 C.c_int32(len(strokes)), _p(hits)), "select_sphere")
+    return hits
+
+
+def camera_mq(vp, mn, S):
+    vp = np.ascontiguousarray(vp, dtype=np.float64).reshape(16)
+    m = np.empty(16, np.float32)
+    _chk(lib().orc_camera_mq(_p(vp), _f3(mn), C.c_double(S), _p(m)), "camera_mq")
+    return m
+
+
+def depth(mesh, mn, S, m, Ws, Hs):
+    m = np.ascontiguousarray(m, dtype=np.float32)
+    d = np.empty((Hs, Ws), np.float32)
+    _chk(lib().orc_depth(_p(mesh.pos), _p(mesh.tri_pos), C.c_int64(mesh.n_tri), _f3(mn), C.c_double(S), _p(m),
+                         C.c_int32(Ws), C.c_int32(Hs), _p(d)), "depth")
+    return d
+
+
+def select_lasso(atlas: Atlas, layer, m, dmap, poly, label, bias=2.0 ** -10, want_ambiguous=True):
+    """One lasso (screen-pixel polygon) on ``layer`` in place; returns (hits, ambiguous mask)."""
+    assert layer.shape == atlas.tri.shape
+    m = np.ascontiguousarray(m, dtype=np.float32)
+    poly = np.ascontiguousarray(poly, dtype=np.float32)
+    Hs, Ws = dmap.shape
+    hits = np.zeros(1, np.uint64)
+    amb = np.zeros(atlas.tri.shape, np.uint8) if want_ambiguous else None
+    _chk(lib().orc_select_lasso(C.c_int64(atlas.n_texels), _p(atlas.px), _p(atlas.py), _p(atlas.pz),
+                                _p(atlas.tri), _p(layer), C.c_int(layer.itemsize), _p(m), C.c_int32(Ws),
+                                C.c_int32(Hs), _p(np.ascontiguousarray(dmap, np.float32)), _p(poly),
+                                C.c_int32(poly.shape[0]), C.c_uint32(int(label)), C.c_float(bias), _p(hits),
+                                _p(amb)), "select_lasso")
+    return int(hits[0]), amb
+
+
+def overlay(atlas: Atlas, a, b, op, flags=0):
+    out = np.empty_like(a)
+    op = OPS[op] if isinstance(op, str) else int(op)
+    _chk(lib().orc_overlay(C.c_int64(atlas.n_texels), _p(atlas.tri), _p(np.ascontiguousarray(a)),
+                           _p(np.ascontiguousarray(b)), _p(out), C.c_int(a.itemsize), C.c_int(op),
+                           C.c_uint32(flags)), "overlay")
+    return out
+
+
+def label_area(atlas: Atlas, layer, n_labels):
+    count = np.empty(n_labels, np.uint64)
+    area = np.empty(n_labels, np.uint64)
+    _chk(lib().orc_label_area(C.c_int64(atlas.n_texels), _p(np.ascontiguousarray(layer)), C.c_int(layer.itemsize),
+                              _p(atlas.tri), _p(atlas.area_w), C.c_uint32(n_labels), _p(count), _p(area)),
+         "label_area")
+    return count, area

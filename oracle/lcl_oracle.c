@@ -1,0 +1,612 @@
+/*
+ * lcl_oracle.c -- plain, slow CPU oracle for the UV-atlas layer-editing path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline / reference arm may load this library.  It shares no code, header,
+ * table or helper with the CUDA library: it restates, step by step, what each
+ * operation computes, with plain loops over every texel (no tiles, no culling, no
+ * batching), so that a reader can check it against the paper by eye.
+ *
+ * The paper (arXiv 2501.14807) stores thematic information layers as 2D textures
+ * indexed by the mesh's texture coordinates (Section 4.1, 4.2) and edits them by
+ * rasterising the mesh in UV space and testing every produced texel against the
+ * editing tool and a depth texture (Section 4.3.1, Fig. 3).  Where the paper is
+ * silent (grid size, sub-pixel precision, fill rule, rounding, tie-breaks), this
+ * file takes one stated reading; each is marked READING below.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared (no FMA contraction, so
+ * every float/double operation is one IEEE rounding in the order written).
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+#define ORC_GRID_MAX ((1 << 21) - 1) /* 21-bit model-bbox grid */
+#define ORC_SUB 256                  /* READING: 8 sub-pixel bits for rasterisation */
+#define ORC_NONE 0xFFFFFFFFu         /* triangle id of an uncovered texel */
+#define ORC_R2_CAP ((int64_t)1 << 50)
+#define ORC_WEIGHT_CAP (((uint64_t)1 << 35) - 1)
+#define ORC_AREA_FRAC 8               /* fractional bits of the per-texel area weight */
+
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_EUNSUP = 4 };
+
+/* ------------------------------------------------------------------------- */
+/* Quantisation of vertex positions to the 21-bit model-bbox grid.            */
+/* The paper uploads the geometry once (Section 4, Geometry Manager); the      */
+/* quantised grid is the exact integer form in which positions enter the atlas.*/
+/* READING: one uniform scale for all axes, S = (2^21-1)/max extent, so that   */
+/* spheres stay spheres; round half up via floor(x + 0.5) in double.          */
+/* ------------------------------------------------------------------------- */
+int orc_quant_params(const float *pos, int64_t n_pos, float mn_out[3], double *scale_out)
+{
+    if (n_pos <= 0) return ORC_EINVAL;
+    float mn[3], mx[3];
+    for (int a = 0; a < 3; ++a) { mn[a] = pos[a]; mx[a] = pos[a]; }
+    for (int64_t i = 0; i < n_pos; ++i)
+        for (int a = 0; a < 3; ++a) {
+            float v = pos[3 * i + a];
+            if (!isfinite(v)) return ORC_EINVAL;
+            if (v < mn[a]) mn[a] = v;
+            if (v > mx[a]) mx[a] = v;
+        }
+    double ext = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double e = (double)mx[a] - (double)mn[a];
+        if (e > ext) ext = e;
+    }
+    if (!(ext > 0.0)) return ORC_EINVAL;
+    for (int a = 0; a < 3; ++a) mn_out[a] = mn[a];
+    *scale_out = (double)ORC_GRID_MAX / ext;
+    return ORC_OK;
+}
+
+static int32_t quantize_coord(float p, float mn, double S)
+{
+    double t = ((double)p - (double)mn) * S + 0.5;
+    double f = floor(t);
+    if (f < 0.0) f = 0.0;
+    if (f > (double)ORC_GRID_MAX) f = (double)ORC_GRID_MAX;
+    return (int32_t)f;
+}
+
+int orc_quantize(const float *pos, int64_t n_pos, const float mn[3], double S, int32_t *q)
+{
+    for (int64_t i = 0; i < n_pos; ++i)
+        for (int a = 0; a < 3; ++a) q[3 * i + a] = quantize_coord(pos[3 * i + a], mn[a], S);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* UV-space rasterisation (Section 4.3.1: the mesh is drawn with its texture   */
+/* coordinates as vertex positions, so every fragment is one texel of the      */
+/* layer).  READING: UVs are snapped to 1/256 texel, X = rint(u * 256 * W)      */
+/* (exact in double, ties to even); the texel centre of (i, j) is              */
+/* (256 i + 128, 256 j + 128); edge functions are exact int64; a texel on an   */
+/* edge belongs to the triangle that owns the edge (owner: direction d with    */
+/* d.y < 0, or d.y == 0 and d.x < 0, for counter-clockwise triangles); when    */
+/* several triangles cover a texel (UV overlap) the smallest triangle id wins. */
+/* ------------------------------------------------------------------------- */
+static int64_t edge_fn(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t px, int64_t py)
+{
+    return (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+}
+
+static int owner(int64_t dx, int64_t dy) { return dy < 0 || (dy == 0 && dx < 0); }
+
+static int inside_edge(int64_t w, int64_t dx, int64_t dy) { return w > 0 || (w == 0 && owner(dx, dy)); }
+
+static int64_t floordiv(int64_t a, int64_t b) /* b > 0 */
+{
+    int64_t q = a / b;
+    if ((a % b != 0) && (a < 0)) q -= 1;
+    return q;
+}
+
+static int snap_uv(float u, int32_t extent, int64_t *X)
+{
+    if (!isfinite(u) || u < -1.0f || u > 2.0f) return ORC_EINVAL; /* documented UV range */
+    *X = llrint((double)u * (double)(256 * (int64_t)extent));
+    return ORC_OK;
+}
+
+typedef struct {
+    int64_t X[3], Y[3];  /* snapped UV, counter-clockwise after normalisation */
+    int32_t q[3][3];     /* quantised positions of the same corners */
+    int64_t A;           /* twice the signed UV area, > 0 after normalisation */
+} orc_tri;
+
+/* Loads triangle t, returns 0 if its UV area is zero (it covers nothing). */
+static int load_tri(const float *pos, const float *uv, const uint32_t *tri_pos, const uint32_t *tri_uv,
+                    int64_t t, const float mn[3], double S, int32_t W, int32_t H, orc_tri *o, int *err)
+{
+    for (int k = 0; k < 3; ++k) {
+        uint32_t iu = tri_uv[3 * t + k], ip = tri_pos[3 * t + k];
+        if (snap_uv(uv[2 * (int64_t)iu], W, &o->X[k]) || snap_uv(uv[2 * (int64_t)iu + 1], H, &o->Y[k])) {
+            *err = ORC_EINVAL;
+            return 0;
+        }
+        for (int a = 0; a < 3; ++a) o->q[k][a] = quantize_coord(pos[3 * (int64_t)ip + a], mn[a], S);
+    }
+    o->A = edge_fn(o->X[0], o->Y[0], o->X[1], o->Y[1], o->X[2], o->Y[2]);
+    if (o->A == 0) return 0;
+    if (o->A < 0) { /* make the triangle counter-clockwise: swap corners 1 and 2 */
+        int64_t tx = o->X[1], ty = o->Y[1];
+        o->X[1] = o->X[2]; o->Y[1] = o->Y[2]; o->X[2] = tx; o->Y[2] = ty;
+        for (int a = 0; a < 3; ++a) { int32_t tq = o->q[1][a]; o->q[1][a] = o->q[2][a]; o->q[2][a] = tq; }
+        o->A = -o->A;
+    }
+    return 1;
+}
+
+/* Edge weights at point (px, py); w[k] belongs to the edge opposite corner k. */
+static int covers(const orc_tri *o, int64_t px, int64_t py, int64_t w[3])
+{
+    w[0] = edge_fn(o->X[1], o->Y[1], o->X[2], o->Y[2], px, py);
+    w[1] = edge_fn(o->X[2], o->Y[2], o->X[0], o->Y[0], px, py);
+    w[2] = edge_fn(o->X[0], o->Y[0], o->X[1], o->Y[1], px, py);
+    return inside_edge(w[0], o->X[2] - o->X[1], o->Y[2] - o->Y[1]) &&
+           inside_edge(w[1], o->X[0] - o->X[2], o->Y[0] - o->Y[2]) &&
+           inside_edge(w[2], o->X[1] - o->X[0], o->Y[1] - o->Y[0]);
+}
+
+/*
+ * Atlas: for every texel of rows [y0, y1) of a W x H texture, the id of the covering
+ * triangle (smallest id if several) and its 3D position interpolated at the texel centre
+ * with exact rational barycentrics w_k / A, rounded half up:
+ *     q = floor((2 * sum_k w_k q_k + A) / (2 A))          (READING: exact, half up)
+ * Uncovered texels get tri = 0xFFFFFFFF and position (INT32_MIN, 0, 0).
+ * Output planes hold (y1 - y0) rows of W texels each.
+ */
+int orc_atlas(const float *pos, int64_t n_pos, const float *uv, int64_t n_uv, const uint32_t *tri_pos,
+              const uint32_t *tri_uv, int64_t n_tri, const float mn[3], double S, int32_t W, int32_t H,
+              int32_t y0, int32_t y1, int32_t *px, int32_t *py, int32_t *pz, uint32_t *tri)
+{
+    (void)n_pos; (void)n_uv;
+    if (W <= 0 || H <= 0 || y0 < 0 || y1 > H || y0 > y1) return ORC_EINVAL;
+    int64_t n = (int64_t)(y1 - y0) * W;
+    for (int64_t i = 0; i < n; ++i) { tri[i] = ORC_NONE; px[i] = INT32_MIN; py[i] = 0; pz[i] = 0; }
+    for (int64_t t = 0; t < n_tri; ++t) {
+        orc_tri o;
+        int err = 0;
+        if (!load_tri(pos, uv, tri_pos, tri_uv, t, mn, S, W, H, &o, &err)) {
+            if (err) return err;
+            continue;
+        }
+        int64_t xmin = o.X[0], xmax = o.X[0], ymin = o.Y[0], ymax = o.Y[0];
+        for (int k = 1; k < 3; ++k) {
+            if (o.X[k] < xmin) xmin = o.X[k];
+            if (o.X[k] > xmax) xmax = o.X[k];
+            if (o.Y[k] < ymin) ymin = o.Y[k];
+            if (o.Y[k] > ymax) ymax = o.Y[k];
+        }
+        /* texel centres 256 i + 128 inside [xmin, xmax] */
+        int64_t i0 = -floordiv(-(xmin - 128), 256), i1 = floordiv(xmax - 128, 256);
+        int64_t j0 = -floordiv(-(ymin - 128), 256), j1 = floordiv(ymax - 128, 256);
+        if (i0 < 0) i0 = 0;
+        if (i1 > W - 1) i1 = W - 1;
+        if (j0 < y0) j0 = y0;
+        if (j1 > y1 - 1) j1 = y1 - 1;
+        for (int64_t j = j0; j <= j1; ++j)
+            for (int64_t i = i0; i <= i1; ++i) {
+                int64_t w[3];
+                if (!covers(&o, 256 * i + 128, 256 * j + 128, w)) continue;
+                int64_t idx = (j - y0) * W + i;
+                if (tri[idx] != ORC_NONE) continue; /* triangles run in id order: first = smallest */
+                tri[idx] = (uint32_t)t;
+                int32_t *dst[3] = {px, py, pz};
+                for (int a = 0; a < 3; ++a) {
+                    i128 N = (i128)w[0] * o.q[0][a] + (i128)w[1] * o.q[1][a] + (i128)w[2] * o.q[2][a];
+                    i128 num = 2 * N + o.A, den = 2 * (i128)o.A;
+                    dst[a][idx] = (int32_t)(num / den); /* num >= 0, so truncation is floor */
+                }
+            }
+    }
+    return ORC_OK;
+}
+
+/* Integer square root floor(sqrt(n)) by bisection on x with x*x <= n. */
+static uint64_t isqrt_u128(u128 n)
+{
+    uint64_t lo = 0, hi = (uint64_t)1 << 63; /* sqrt(2^128) = 2^64 > any answer here */
+    if (n < 2) return (uint64_t)n;
+    while (hi - lo > 1) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if ((u128)mid * mid <= n) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+/*
+ * Per-triangle area weight (Table 1 reports the area one texel stands for).
+ * READING: a texel owned by triangle t stands for (3D area of t) / (UV area of t in
+ * texels), in grid^2 units with 8 fractional bits:
+ *     n = (q1 - q0) x (q2 - q0),  A3 = floor(sqrt(|n|^2)),  A_uv2 = |A| (sub-pixel^2)
+ *     w = min(floor(A3 * 2^(16+8) / A_uv2), 2^35 - 1),  w = 0 if A_uv2 = 0.
+ */
+int orc_area_weights(const float *pos, const float *uv, const uint32_t *tri_pos, const uint32_t *tri_uv,
+                     int64_t n_tri, const float mn[3], double S, int32_t W, int32_t H, uint64_t *w_out)
+{
+    for (int64_t t = 0; t < n_tri; ++t) {
+        orc_tri o;
+        int err = 0;
+        int ok = load_tri(pos, uv, tri_pos, tri_uv, t, mn, S, W, H, &o, &err);
+        if (err) return err;
+        if (!ok) { w_out[t] = 0; continue; }
+        int64_t d1[3], d2[3];
+        for (int a = 0; a < 3; ++a) { d1[a] = (int64_t)o.q[1][a] - o.q[0][a]; d2[a] = (int64_t)o.q[2][a] - o.q[0][a]; }
+        int64_t nx = d1[1] * d2[2] - d1[2] * d2[1];
+        int64_t ny = d1[2] * d2[0] - d1[0] * d2[2];
+        int64_t nz = d1[0] * d2[1] - d1[1] * d2[0];
+        u128 nn = (u128)((i128)nx * nx) + (u128)((i128)ny * ny) + (u128)((i128)nz * nz);
+        uint64_t a3 = isqrt_u128(nn);
+        u128 w = ((u128)a3 << (16 + ORC_AREA_FRAC)) / (u128)o.A;
+        w_out[t] = w > ORC_WEIGHT_CAP ? ORC_WEIGHT_CAP : (uint64_t)w;
+    }
+    return ORC_OK;
+}
+
+/* Coverage bitmap: bit (y*W + x) of a linear array of 32-bit words is 1 iff covered. */
+int orc_cover_bits(int32_t W, int32_t H, const uint32_t *tri, uint32_t *bits)
+{
+    int64_t n = (int64_t)W * H;
+    memset(bits, 0, (size_t)((n + 31) / 32) * 4);
+    for (int64_t l = 0; l < n; ++l)
+        if (tri[l] != ORC_NONE) bits[l >> 5] |= 1u << (l & 31);
+    return ORC_OK;
+}
+
+/*
+ * Tile boxes: for each T x T tile (row-major over ceil(W/T) x ceil(H/T) tiles), 8 int32:
+ * min x, min y, min z, covered-texel count, max x, max y, max z, 0.  An empty tile holds
+ * INT32_MAX mins, INT32_MIN maxes and count 0.
+ */
+int orc_tile_aabb(int32_t W, int32_t H, int32_t T, const int32_t *px, const int32_t *py, const int32_t *pz,
+                  const uint32_t *tri, int32_t *box)
+{
+    int32_t ntx = (W + T - 1) / T, nty = (H + T - 1) / T;
+    for (int32_t ty = 0; ty < nty; ++ty)
+        for (int32_t tx = 0; tx < ntx; ++tx) {
+            int32_t *b = box + 8 * ((int64_t)ty * ntx + tx);
+            b[0] = b[1] = b[2] = INT32_MAX;
+            b[4] = b[5] = b[6] = INT32_MIN;
+            b[3] = 0; b[7] = 0;
+            for (int32_t y = ty * T; y < ty * T + T && y < H; ++y)
+                for (int32_t x = tx * T; x < tx * T + T && x < W; ++x) {
+                    int64_t l = (int64_t)y * W + x;
+                    if (tri[l] == ORC_NONE) continue;
+                    int32_t v[3] = {px[l], py[l], pz[l]};
+                    for (int a = 0; a < 3; ++a) {
+                        if (v[a] < b[a]) b[a] = v[a];
+                        if (v[a] > b[4 + a]) b[4 + a] = v[a];
+                    }
+                    b[3] += 1;
+                }
+        }
+    return ORC_OK;
+}
+
+/* Super-tile boxes: the union of the boxes of G x G tiles (same 8-int32 record). */
+int orc_super_aabb(int32_t ntx, int32_t nty, int32_t G, const int32_t *box, int32_t *sbox)
+{
+    int32_t nsx = (ntx + G - 1) / G, nsy = (nty + G - 1) / G;
+    for (int32_t sy = 0; sy < nsy; ++sy)
+        for (int32_t sx = 0; sx < nsx; ++sx) {
+            int32_t *s = sbox + 8 * ((int64_t)sy * nsx + sx);
+            s[0] = s[1] = s[2] = INT32_MAX;
+            s[4] = s[5] = s[6] = INT32_MIN;
+            s[3] = 0; s[7] = 0;
+            for (int32_t ty = sy * G; ty < sy * G + G && ty < nty; ++ty)
+                for (int32_t tx = sx * G; tx < sx * G + G && tx < ntx; ++tx) {
+                    const int32_t *b = box + 8 * ((int64_t)ty * ntx + tx);
+                    for (int a = 0; a < 3; ++a) {
+                        if (b[a] < s[a]) s[a] = b[a];
+                        if (b[4 + a] > s[4 + a]) s[4 + a] = b[4 + a];
+                    }
+                    s[3] += b[3];
+                }
+        }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sphere brush.  The paper's tool is a circle under the cursor (Section 4.3); */
+/* the 3D sphere is its object-space counterpart.  READING: a texel is        */
+/* selected iff it is covered and its squared grid distance to the centre is  */
+/* <= r2 (inclusive), computed in int64; strokes run in order and a later     */
+/* stroke overwrites an earlier one (the selected value is stored, Section    */
+/* 4.3.1).                                                                     */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t cx, cy, cz, pad;
+    int64_t r2;
+    uint32_t label, flags;
+} orc_sphere; /* 32 bytes */
+
+/* Stroke from a world-space centre and radius: centre quantised like a vertex but not
+ * clamped (rejected outside [-2^22, 2^22 + 2^21]); r2 = floor((r S)^2), capped at 2^50
+ * (every in-grid squared distance is below 3 * 2^46, so the cap changes no selection). */
+int orc_sphere_stroke(const float mn[3], double S, const double c[3], double r, uint32_t label, orc_sphere *out)
+{
+    if (!(r >= 0.0) || !isfinite(r)) return ORC_EINVAL;
+    int32_t q[3];
+    for (int a = 0; a < 3; ++a) {
+        if (!isfinite(c[a])) return ORC_EINVAL;
+        double f = floor((c[a] - (double)mn[a]) * S + 0.5);
+        if (f < -(double)(1 << 22) || f > (double)((1 << 22) + (1 << 21))) return ORC_EINVAL;
+        q[a] = (int32_t)f;
+    }
+    double t = r * S;
+    double t2 = floor(t * t);
+    int64_t r2 = t2 >= (double)ORC_R2_CAP ? ORC_R2_CAP : (int64_t)t2;
+    out->cx = q[0]; out->cy = q[1]; out->cz = q[2]; out->pad = 0;
+    out->r2 = r2; out->label = label; out->flags = 0;
+    return ORC_OK;
+}
+
+static void store_label(void *layer, int dtype_bytes, int64_t l, uint32_t v)
+{
+    if (dtype_bytes == 1) ((uint8_t *)layer)[l] = (uint8_t)v;
+    else ((uint16_t *)layer)[l] = (uint16_t)v;
+}
+
+static uint32_t load_label(const void *layer, int dtype_bytes, int64_t l)
+{
+    return dtype_bytes == 1 ? ((const uint8_t *)layer)[l] : ((const uint16_t *)layer)[l];
+}
+
+int orc_select_sphere(int64_t n_texels, const int32_t *px, const int32_t *py, const int32_t *pz,
+                      const uint32_t *tri, void *layer, int dtype_bytes, const orc_sphere *strokes, int32_t n,
+                      uint64_t *hits)
+{
+    if (dtype_bytes != 1 && dtype_bytes != 2) return ORC_EINVAL;
+    for (int32_t k = 0; k < n; ++k) {
+        const orc_sphere *s = &strokes[k];
+        if (s->r2 < 0 || s->label >= (1u << (8 * dtype_bytes))) return ORC_EINVAL;
+        uint64_t h = 0;
+        for (int64_t l = 0; l < n_texels; ++l) {
+            if (tri[l] == ORC_NONE) continue;
+            int64_t dx = (int64_t)px[l] - s->cx, dy = (int64_t)py[l] - s->cy, dz = (int64_t)pz[l] - s->cz;
+            int64_t d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 <= s->r2) {
+                store_label(layer, dtype_bytes, l, s->label);
+                ++h;
+            }
+        }
+        if (hits) hits[k] = h;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Camera and depth texture (Section 4.3.1, depth test of Fig. 3a).           */
+/* READING: the camera matrix M maps a grid position (q, 1) straight to clip  */
+/* space, M = VP * Dequant with Dequant(q) = bbox_min + q / S, composed in     */
+/* double and rounded to float.  Clip coordinates are evaluated in FP32 in the */
+/* fixed order ((m0 x + m1 y) + m2 z) + m3 with no fused multiply-add; NDC     */
+/* depth lies in [0, 1]; screen x = (x/w * 0.5 + 0.5) * W_s, row 0 at the      */
+/* bottom; pixels use the same sub-pixel snap, edge and owner rules as the     */
+/* atlas; a triangle is dropped if a corner has w <= 0, NDC z outside [0, 1]   */
+/* or lies more than 2^20 pixels off screen; the depth of a pixel is the       */
+/* minimum over triangles of the barycentric interpolation of corner NDC z,    */
+/* evaluated in double and rounded to float; +inf where nothing is drawn.      */
+/* ------------------------------------------------------------------------- */
+int orc_camera_mq(const double vp[16], const float mn[3], double S, float m_out[16])
+{
+    for (int i = 0; i < 4; ++i) {
+        for (int j = 0; j < 3; ++j) m_out[4 * i + j] = (float)(vp[4 * i + j] / S);
+        double t = ((vp[4 * i + 0] * (double)mn[0] + vp[4 * i + 1] * (double)mn[1]) + vp[4 * i + 2] * (double)mn[2]) +
+                   vp[4 * i + 3];
+        m_out[4 * i + 3] = (float)t;
+    }
+    for (int i = 0; i < 16; ++i)
+        if (!isfinite(m_out[i])) return ORC_EINVAL;
+    return ORC_OK;
+}
+
+static void clip_of(const float m[16], int32_t qx, int32_t qy, int32_t qz, float c[4])
+{
+    float x = (float)qx, y = (float)qy, z = (float)qz;
+    for (int r = 0; r < 4; ++r) c[r] = ((m[4 * r + 0] * x + m[4 * r + 1] * y) + m[4 * r + 2] * z) + m[4 * r + 3];
+}
+
+static float screen_of(float ndc, int32_t extent) { return (ndc * 0.5f + 0.5f) * (float)extent; }
+
+#define ORC_GUARD_SUB ((int64_t)1 << 28) /* 2^20 pixels in sub-pixel units */
+
+int orc_depth(const float *pos, const uint32_t *tri_pos, int64_t n_tri, const float mn[3], double S,
+              const float m[16], int32_t Ws, int32_t Hs, float *depth)
+{
+    if (Ws <= 0 || Hs <= 0) return ORC_EINVAL;
+    for (int64_t i = 0; i < (int64_t)Ws * Hs; ++i) depth[i] = INFINITY;
+    for (int64_t t = 0; t < n_tri; ++t) {
+        int64_t X[3], Y[3];
+        float Z[3];
+        int ok = 1;
+        for (int k = 0; k < 3 && ok; ++k) {
+            uint32_t ip = tri_pos[3 * t + k];
+            float c[4];
+            clip_of(m, quantize_coord(pos[3 * (int64_t)ip + 0], mn[0], S), quantize_coord(pos[3 * (int64_t)ip + 1], mn[1], S),
+                    quantize_coord(pos[3 * (int64_t)ip + 2], mn[2], S), c);
+            if (!(c[3] > 0.0f)) { ok = 0; break; }
+            float zn = c[2] / c[3];
+            if (!(zn >= 0.0f && zn <= 1.0f)) { ok = 0; break; }
+            float xs = screen_of(c[0] / c[3], Ws) * 256.0f, ys = screen_of(c[1] / c[3], Hs) * 256.0f;
+            if (!(fabsf(xs) <= (float)ORC_GUARD_SUB && fabsf(ys) <= (float)ORC_GUARD_SUB)) { ok = 0; break; }
+            X[k] = llrintf(xs); Y[k] = llrintf(ys); Z[k] = zn;
+        }
+        if (!ok) continue;
+        int64_t A = edge_fn(X[0], Y[0], X[1], Y[1], X[2], Y[2]);
+        if (A == 0) continue;
+        if (A < 0) {
+            int64_t tx = X[1], ty = Y[1]; float tz = Z[1];
+            X[1] = X[2]; Y[1] = Y[2]; Z[1] = Z[2]; X[2] = tx; Y[2] = ty; Z[2] = tz;
+            A = -A;
+        }
+        orc_tri o;
+        memset(&o, 0, sizeof o);
+        for (int k = 0; k < 3; ++k) { o.X[k] = X[k]; o.Y[k] = Y[k]; }
+        o.A = A;
+        int64_t xmin = X[0], xmax = X[0], ymin = Y[0], ymax = Y[0];
+        for (int k = 1; k < 3; ++k) {
+            if (X[k] < xmin) xmin = X[k];
+            if (X[k] > xmax) xmax = X[k];
+            if (Y[k] < ymin) ymin = Y[k];
+            if (Y[k] > ymax) ymax = Y[k];
+        }
+        int64_t i0 = -floordiv(-(xmin - 128), 256), i1 = floordiv(xmax - 128, 256);
+        int64_t j0 = -floordiv(-(ymin - 128), 256), j1 = floordiv(ymax - 128, 256);
+        if (i0 < 0) i0 = 0;
+        if (i1 > Ws - 1) i1 = Ws - 1;
+        if (j0 < 0) j0 = 0;
+        if (j1 > Hs - 1) j1 = Hs - 1;
+        for (int64_t j = j0; j <= j1; ++j)
+            for (int64_t i = i0; i <= i1; ++i) {
+                int64_t w[3];
+                if (!covers(&o, 256 * i + 128, 256 * j + 128, w)) continue;
+                double num = ((double)w[0] * (double)Z[0] + (double)w[1] * (double)Z[1]) + (double)w[2] * (double)Z[2];
+                float z = (float)(num / (double)A);
+                z = z + 0.0f; /* no negative zero in the map */
+                int64_t p = j * Ws + i;
+                if (z < depth[p]) depth[p] = z;
+            }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Lasso selection: the paper's TEA (Section 4.3.1, Fig. 3) -- depth test     */
+/* with a small bias, projection of the texel to the screen, and a test       */
+/* against the tool's shape -- with the shape given as a polygon in screen    */
+/* pixels.  READING: per covered texel, clip = M (q, 1) as for the depth map;  */
+/* drop if w <= 0, NDC z outside [0, 1] or the point is outside the viewport; */
+/* inside by the even-odd rule, an edge (a, b) toggling when                   */
+/*   (a.y > y) != (b.y > y)  and  x < (b.x - a.x) * (y - a.y) / (b.y - a.y) + a.x */
+/* in FP32 in that order; visible iff z <= D[floor(y)][floor(x)] + bias.       */
+/* A texel is ambiguous (its label may legitimately differ between two exact   */
+/* FP32 evaluations) if its screen point lies within 1e-4 px of an edge or    */
+/* its depth margin |z - (D + bias)| is below 1e-6; both measured in double.   */
+/* ------------------------------------------------------------------------- */
+static double seg_dist(double px, double py, double ax, double ay, double bx, double by)
+{
+    double vx = bx - ax, vy = by - ay, wx = px - ax, wy = py - ay;
+    double L = vx * vx + vy * vy, t = 0.0;
+    if (L > 0.0) {
+        t = (wx * vx + wy * vy) / L;
+        if (t < 0.0) t = 0.0;
+        if (t > 1.0) t = 1.0;
+    }
+    double dx = wx - t * vx, dy = wy - t * vy;
+    return sqrt(dx * dx + dy * dy);
+}
+
+int orc_select_lasso(int64_t n_texels, const int32_t *px, const int32_t *py, const int32_t *pz,
+                     const uint32_t *tri, void *layer, int dtype_bytes, const float m[16], int32_t Ws, int32_t Hs,
+                     const float *depth, const float *poly, int32_t nv, uint32_t label, float bias, uint64_t *hits,
+                     uint8_t *ambiguous)
+{
+    if (dtype_bytes != 1 && dtype_bytes != 2) return ORC_EINVAL;
+    if (nv < 3 || nv > 64) return ORC_EUNSUP;
+    if (label >= (1u << (8 * dtype_bytes))) return ORC_EINVAL;
+    uint64_t h = 0;
+    for (int64_t l = 0; l < n_texels; ++l) {
+        if (ambiguous) ambiguous[l] = 0;
+        if (tri[l] == ORC_NONE) continue;
+        float c[4];
+        clip_of(m, px[l], py[l], pz[l], c);
+        if (!(c[3] > 0.0f)) continue;
+        float zn = c[2] / c[3];
+        if (!(zn >= 0.0f && zn <= 1.0f)) continue;
+        float xs = screen_of(c[0] / c[3], Ws), ys = screen_of(c[1] / c[3], Hs);
+        if (!(xs >= 0.0f && xs < (float)Ws && ys >= 0.0f && ys < (float)Hs)) continue;
+        int inside = 0;
+        for (int32_t e = 0; e < nv; ++e) {
+            float ax = poly[2 * e], ay = poly[2 * e + 1];
+            float bx = poly[2 * ((e + 1) % nv)], by = poly[2 * ((e + 1) % nv) + 1];
+            if ((ay > ys) != (by > ys)) {
+                float xi = (bx - ax) * (ys - ay) / (by - ay) + ax;
+                if (xs < xi) inside = !inside;
+            }
+        }
+        int32_t ix = (int32_t)xs, iy = (int32_t)ys; /* xs, ys >= 0: truncation is floor */
+        float dref = depth[(int64_t)iy * Ws + ix];
+        float lim = dref + bias;
+        int visible = zn <= lim;
+        if (inside && visible) {
+            store_label(layer, dtype_bytes, l, label);
+            ++h;
+        }
+        if (ambiguous) {
+            double me = INFINITY;
+            for (int32_t e = 0; e < nv; ++e) {
+                double d = seg_dist(xs, ys, poly[2 * e], poly[2 * e + 1], poly[2 * ((e + 1) % nv)],
+                                    poly[2 * ((e + 1) % nv) + 1]);
+                if (d < me) me = d;
+            }
+            double md = fabs((double)zn - ((double)dref + (double)bias));
+            if (me < 1e-4 || md < 1e-6) ambiguous[l] = 1;
+        }
+    }
+    if (hits) *hits = h;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Overlay of two layers.  Layer systems combine layers with arithmetic,      */
+/* logic, geometric and topological operations (Section 3.4.2); the paper's   */
+/* architecture claims the same capability.  READING: bitwise operators on the */
+/* label values, with optional complement of either operand and of the result */
+/* (within the label width); MASK keeps a where b is non-zero; uncovered       */
+/* texels become 0.                                                           */
+/* ------------------------------------------------------------------------- */
+enum { ORC_AND = 0, ORC_OR = 1, ORC_XOR = 2, ORC_MASK = 3 };
+enum { ORC_NOT_A = 1, ORC_NOT_B = 2, ORC_NOT_OUT = 4 };
+
+int orc_overlay(int64_t n_texels, const uint32_t *tri, const void *a, const void *b, void *out, int dtype_bytes,
+                int op, uint32_t flags)
+{
+    if (dtype_bytes != 1 && dtype_bytes != 2) return ORC_EINVAL;
+    if (op < 0 || op > 3 || (flags & ~7u)) return ORC_EINVAL;
+    uint32_t full = dtype_bytes == 1 ? 0xFFu : 0xFFFFu;
+    for (int64_t l = 0; l < n_texels; ++l) {
+        uint32_t r = 0;
+        if (tri[l] != ORC_NONE) {
+            uint32_t x = load_label(a, dtype_bytes, l), y = load_label(b, dtype_bytes, l);
+            if (flags & ORC_NOT_A) x = ~x & full;
+            if (flags & ORC_NOT_B) y = ~y & full;
+            switch (op) {
+            case ORC_AND: r = x & y; break;
+            case ORC_OR: r = x | y; break;
+            case ORC_XOR: r = x ^ y; break;
+            default: r = y != 0 ? x : 0; break;
+            }
+            if (flags & ORC_NOT_OUT) r = ~r & full;
+        }
+        store_label(out, dtype_bytes, l, r);
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Per-label surface area (Table 1: area one texel stands for).  For every    */
+/* covered texel whose label l < n_labels: count[l] += 1 and                   */
+/* area[l] += weight of its triangle (fixed point, 8 fractional bits of grid^2). */
+/* ------------------------------------------------------------------------- */
+int orc_label_area(int64_t n_texels, const void *layer, int dtype_bytes, const uint32_t *tri, const uint64_t *w_tri,
+                   uint32_t n_labels, uint64_t *count, uint64_t *area)
+{
+    if (dtype_bytes != 1 && dtype_bytes != 2) return ORC_EINVAL;
+    for (uint32_t i = 0; i < n_labels; ++i) { count[i] = 0; area[i] = 0; }
+    for (int64_t l = 0; l < n_texels; ++l) {
+        if (tri[l] == ORC_NONE) continue;
+        uint32_t lab = load_label(layer, dtype_bytes, l);
+        if (lab >= n_labels) continue;
+        count[lab] += 1;
+        area[lab] += w_tri[tri[l]];
+    }
+    return ORC_OK;
+}
