@@ -1,0 +1,416 @@
+"""Benchmark: one step = one pass of the whole layer-editing path over one model.
+
+Workload (default): the roofline-size model -- a displaced vessel of 2828 x 1414 quads
+(~8M triangles) with a cylindrical unwrap into a 16384 x 16384 atlas (int32 x3 positions
++ uint32 triangle ids, 4.3 GB, far larger than L2) and 4 uint8 layers.  One step runs,
+through the C ABI:
+  atlas build (quantise, UV rasterise, interpolate, boxes, area weights)
+  1000 sphere strokes (radii log-uniform 1-30% of the bbox diagonal), one call per layer,
+      one cull + one apply launch per stroke
+  4 depth maps (2048^2) and 20 star lassos on them
+  XOR(L0, L1) and OR(L2, L3) overlays, per-label area (256 labels) of the 4 layers
+
+Metric: layer texels processed per second -- every texel an edit selected, plus every
+texel of each overlay and each area query -- over the whole step.  The roofline object is
+for the sphere edits (the dominant kernels): algorithmic bytes = hit texels x (12 B of
+position + 1 B of label), over their CUDA-event time, against the measured HBM copy peak.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "layer-edit Gtexels/s and % of HBM roofline; p50/p99 edit latency (serving)"
+UNIT = "Gtexels/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def make_workload(args):
+    import synth
+    if args.config == "roofline":
+        return synth.config_roofline(n_strokes=args.strokes, n_lassos=args.lassos)
+    if args.config == "large":
+        return synth.config_large(n_strokes=args.strokes, n_lassos=args.lassos)
+    if args.config == "mid":   # a 4096^2 version of the roofline model, for quick runs and profiles
+        return synth.config_roofline(n_strokes=args.strokes, n_lassos=args.lassos, n_theta=707, n_h=354,
+                                     side=4096)
+    return synth.config_small()
+
+
+def workload_desc(w, args):
+    return {
+        "workload": f"{w.name}: {w.mesh.n_tri} triangles, {w.width}x{w.height} atlas (tile {w.tile}), "
+                    f"{w.n_layers} x u{8 * w.dtype_bytes} layers, {len(w.strokes.radius)} sphere strokes, "
+                    f"{len(w.lassos)} lassos on {len(w.cams)} depth maps, overlays "
+                    f"{'/'.join(o[0] for o in w.overlays)}, per-label area x{w.n_layers}",
+        "atlas": f"{w.width}x{w.height}",
+        "n_tri": w.mesh.n_tri,
+        "layers": w.n_layers,
+        "strokes": int(len(w.strokes.radius)),
+        "lassos": len(w.lassos),
+        "n_labels": w.n_labels,
+        "l2": "inputs larger than L2" if w.width * w.height * 16 > 129e6 else "inputs smaller than L2",
+    }
+
+
+# ---------------------------------------------------------------------------------------
+# CPU baseline / reference arm: the oracle, as it stands, on a bounded row band
+# ---------------------------------------------------------------------------------------
+
+def oracle_sample(w, rows, n_cams_used=None):
+    """Runs the oracle over texture rows [0, rows) of the workload: the same strokes, lassos
+    (with their full depth maps), overlays and area queries.  Returns (texels, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    mn, S = oracle.quant_params(w.mesh.pos)
+    o = oracle.Atlas(w.mesh, w.width, w.height, tile=w.tile, y0=0, y1=rows, quant=(mn, S))
+    dt = np.uint8 if w.dtype_bytes == 1 else np.uint16
+    layers = [np.zeros((rows, w.width), dt) for _ in range(w.n_layers)]
+    recs = oracle.sphere_records(mn, S, w.strokes.centre, w.strokes.radius, w.strokes.label)
+    texels = 0
+    for li in range(w.n_layers):
+        sel = np.nonzero(w.strokes.layer == li)[0]
+        texels += int(oracle.select_sphere(o, layers[li], recs[sel]).sum())
+    cams = w.cams if n_cams_used is None else w.cams[:n_cams_used]
+    ms = [oracle.camera_mq(c.vp, mn, S) for c in cams]
+    dms = [oracle.depth(w.mesh, mn, S, m, c.width, c.height) for m, c in zip(ms, cams)]
+    for L in w.lassos:
+        if L.cam >= len(cams):
+            continue
+        h, _ = oracle.select_lasso(o, layers[L.layer], ms[L.cam], dms[L.cam], L.poly, L.label, want_ambiguous=False)
+        texels += h
+    for op, ia, ib in w.overlays:
+        oracle.overlay(o, layers[ia], layers[ib], op)
+        texels += rows * w.width
+    for li in range(w.n_layers):
+        oracle.label_area(o, layers[li], w.n_labels)
+        texels += rows * w.width
+    return texels, time.perf_counter() - t0
+
+
+def cpu_baseline(w, rows):
+    texels, secs = oracle_sample(w, rows)
+    return {"value": texels / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"texture rows [0, {rows}) of the same workload ({rows * w.width} texels): all strokes, "
+                      f"lassos (full depth maps), overlays and area queries; {texels} texels in {secs:.2f} s, "
+                      f"single-threaded C (-O2)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = make_workload(args)
+    rows = args.cpu_rows
+    for _ in range(args.warmup):
+        oracle_sample(w, rows)
+    tot_t, tot_x = 0.0, 0
+    times = []
+    for _ in range(args.steps):
+        x, s = oracle_sample(w, rows)
+        tot_t += s
+        tot_x += x
+        times.append(s)
+    val = tot_x / tot_t / 1e9
+    cb = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+          "sample": f"texture rows [0, {rows}) of the workload per step ({rows * w.width} texels), all strokes, "
+                    f"lassos, overlays and area queries; single-threaded C oracle"}
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": workload_desc(w, args), "cpu_baseline": cb,
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2501_14807_gb300 import lcl
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = make_workload(args)
+    W, H = w.width, w.height
+    cpu = cpu_baseline(w, args.cpu_rows) if (rank == 0 and world == 1 and args.cpu_rows > 0) else None
+
+    mesh = lcl.Mesh.from_host(w.mesh, dev)
+    atlas = lcl.Atlas(W, H, w.tile, w.mesh.n_tri, dev)
+    ws_atlas = torch.empty(lcl.lcl_atlas_workspace_bytes(mesh, W, H), dtype=torch.uint8, device=dev)
+    lcl.lcl_atlas_build(mesh, atlas, ws_atlas)
+    lt = torch.uint8 if w.dtype_bytes == 1 else torch.int16
+    layers = [torch.zeros((H, W), dtype=lt, device=dev) for _ in range(w.n_layers)]
+    outs = [torch.empty((H, W), dtype=lt, device=dev) for _ in w.overlays]
+    per_layer = []
+    for li in range(w.n_layers):
+        sel = np.nonzero(w.strokes.layer == li)[0]
+        recs = np.stack([lcl.lcl_quantize_sphere(atlas, w.strokes.centre[k], w.strokes.radius[k],
+                                                 w.strokes.label[k]) for k in sel]) if len(sel) else \
+            np.zeros(0, lcl.SPHERE_DTYPE)
+        per_layer.append(np.ascontiguousarray(recs, dtype=lcl.SPHERE_DTYPE))
+    n_strokes = sum(len(r) for r in per_layer)
+    ws_sel = torch.empty(lcl.lcl_select_workspace_bytes(atlas, max(len(r) for r in per_layer)), dtype=torch.uint8,
+                         device=dev)
+    sphere_hits = [torch.zeros(max(len(r), 1), dtype=torch.int64, device=dev) for r in per_layer]
+    cams = [lcl.lcl_camera_from_vp(atlas, c.vp, c.width, c.height) for c in w.cams]
+    depths = [torch.empty((c.height, c.width), dtype=torch.float32, device=dev) for c in w.cams]
+    ws_depth = torch.empty(max([lcl.lcl_depth_workspace_bytes(mesh, c.width, c.height) for c in w.cams] + [256]),
+                           dtype=torch.uint8, device=dev)
+    lasso_hits = torch.zeros(max(len(w.lassos), 1), dtype=torch.int64, device=dev)
+    counts = [torch.empty(w.n_labels, dtype=torch.int64, device=dev) for _ in range(w.n_layers)]
+    areas = [torch.empty(w.n_labels, dtype=torch.int64, device=dev) for _ in range(w.n_layers)]
+    stream = torch.cuda.current_stream(dev)
+
+    ev_sph = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in layers]
+
+    def step(mesh_dev, timed_sphere=None):
+        lcl.lcl_atlas_build(mesh_dev, atlas, ws_atlas, stream)
+        for li, layer in enumerate(layers):
+            if timed_sphere is not None:
+                ev_sph[li][0].record(stream)
+            lcl.lcl_select_sphere(atlas, layer, per_layer[li], sphere_hits[li], ws_sel, stream)
+            if timed_sphere is not None:
+                ev_sph[li][1].record(stream)
+        for ci, cam in enumerate(cams):
+            lcl.lcl_depth_render(mesh_dev, atlas, cam, depths[ci], ws_depth, stream)
+        for k, L in enumerate(w.lassos):
+            lcl.lcl_select_lasso(atlas, layers[L.layer], cams[L.cam], depths[L.cam], L.poly, L.label,
+                                 lcl.DEFAULT_BIAS, lasso_hits[k:k + 1], ws_sel, stream)
+        for oi, (op, ia, ib) in enumerate(w.overlays):
+            lcl.lcl_overlay(atlas, layers[ia], layers[ib], outs[oi], op, 0, stream)
+        for li, layer in enumerate(layers):
+            lcl.lcl_label_area(atlas, layer, w.n_labels, counts[li], areas[li], stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step(mesh)
+    barrier()
+
+    # texels per step (identical every step: the same strokes on the same atlas)
+    sph_hits = sum(int(h[:len(r)].sum().item()) for h, r in zip(sphere_hits, per_layer))
+    las_hits = int(lasso_hits[:len(w.lassos)].sum().item())
+    texels = sph_hits + las_hits + (len(w.overlays) + w.n_layers) * W * H
+
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = lcl.lcl_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sph_ms = 0.0
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(mesh, timed_sphere=True)
+        e1.record(stream)
+        e1.synchronize()
+        sph_ms += sum(a.elapsed_time(b) for a, b in ev_sph)
+    barrier()
+    e1.record(stream)
+    barrier()
+    total_ms = e0.elapsed_time(e1)
+    launches = lcl.lcl_kernel_launches() - launches0
+    clk = clocks.stop()
+
+    # end-to-end through the public API from host buffers: mesh upload from pinned memory each
+    # step, result tables (area + hit counts) read back each step
+    pinned = [torch.from_numpy(np.ascontiguousarray(a).view(dt)).pin_memory()
+              for a, dt in ((w.mesh.pos, np.float32), (w.mesh.uv, np.float32), (w.mesh.tri_pos, np.int32),
+                            (w.mesh.tri_uv, np.int32))]
+    h2d = sum(p.numel() * p.element_size() for p in pinned)
+    dev_bufs = [torch.empty_like(p, device=dev) for p in pinned]
+    mesh_e2e = lcl.Mesh(*dev_bufs)
+    host_counts = [torch.empty(w.n_labels, dtype=torch.int64).pin_memory() for _ in range(2 * w.n_layers)]
+    host_hits = [torch.empty(h.numel(), dtype=torch.int64).pin_memory() for h in sphere_hits + [lasso_hits]]
+    d2h = sum(t.numel() * 8 for t in host_counts + host_hits)
+
+    def e2e_step():
+        for p, d in zip(pinned, dev_bufs):
+            d.copy_(p, non_blocking=True)
+        step(mesh_e2e)
+        for i in range(w.n_layers):
+            host_counts[2 * i].copy_(counts[i], non_blocking=True)
+            host_counts[2 * i + 1].copy_(areas[i], non_blocking=True)
+        for hh, dd in zip(host_hits, sphere_hits + [lasso_hits]):
+            hh.copy_(dd, non_blocking=True)
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    f1.record(stream)
+    barrier()
+    e2e_ms = f0.elapsed_time(f1)
+
+    # max over ranks
+    tt = torch.tensor([total_ms, e2e_ms, sph_ms], dtype=torch.float64, device=dev)
+    tx = torch.tensor([texels], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tx, op=dist.ReduceOp.SUM)
+    total_ms, e2e_ms, sph_ms = tt.tolist()
+    all_texels = tx.item()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+    sph_bytes = sph_hits * (12 + w.dtype_bytes)
+    achieved = sph_bytes / (sph_ms / args.steps / 1e3) / 1e9
+    value = all_texels * args.steps / (total_ms / 1e3) / 1e9
+    traffic = profile_traffic(w)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded vessels; scans unavailable)",
+        "config": workload_desc(w, args),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": traffic,
+                     "kernel": "sphere edit (k_sphere_cull + k_sphere_apply per stroke)",
+                     "algorithmic_bytes_per_launch": sph_bytes / max(n_strokes, 1),
+                     "ms_per_launch": sph_ms / args.steps / max(n_strokes, 1)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": all_texels * args.steps / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "breakdown": {"sphere_ms_per_step": sph_ms / args.steps, "sphere_hit_texels": sph_hits,
+                      "lasso_hit_texels": las_hits, "texels_per_step": texels},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def profile_traffic(w):
+    """DRAM bytes per sphere-edit launch from the committed ncu summary, if it was taken on the
+    current kernel source (null otherwise)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "sphere_edit_traffic.json")
+    src = os.path.join(ROOT, "paper_2501_14807_gb300", "csrc", "select.cu")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    if d.get("select_cu_sha256_16") != h or d.get("workload") != w.name:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="roofline", choices=["roofline", "large", "mid", "small"])
+    ap.add_argument("--strokes", type=int, default=None)
+    ap.add_argument("--lassos", type=int, default=None)
+    ap.add_argument("--cpu-rows", type=int, default=64, help="rows of the texture the CPU oracle baseline covers")
+    args = ap.parse_args()
+    defaults = {"roofline": (1000, 20), "mid": (1000, 20), "large": (10000, 200), "small": (200, 0)}
+    if args.strokes is None:
+        args.strokes = defaults[args.config][0]
+    if args.lassos is None:
+        args.lassos = defaults[args.config][1]
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,244 @@
+/*
+ * lcl.h -- C ABI of the GPU layer-editing library (GB300, sm_103a).
+ *
+ * Thematic information layers are 2D textures indexed by a mesh's texture
+ * coordinates (arXiv 2501.14807, Section 4.1 and 4.2).  Editing a layer maps a
+ * selection made in 3D or on the screen onto the texels it covers (Section 4.3.1,
+ * Fig. 3).  This library precomputes, once per model, a UV atlas that tells for
+ * every texel which triangle covers it and where that texel lies on the surface,
+ * then edits, overlays and measures layers with per-texel kernels.
+ *
+ * Conventions shared by every entry point:
+ *  - All buffers are caller-owned.  "device" pointers are CUDA device memory of the
+ *    current device, "host" pointers are ordinary host memory.  The library keeps no
+ *    allocation between calls and allocates nothing itself.
+ *  - Calls enqueue work on `stream` (a cudaStream_t; NULL is the legacy default
+ *    stream) and return without waiting, except lcl_atlas_build, which waits for its
+ *    stream before returning (see there).  Calls that share an atlas workspace or
+ *    write the same layer must be ordered on one stream.
+ *  - Host-side argument checks happen before anything is enqueued and return
+ *    LCL_ERR_INVALID_ARG or LCL_ERR_UNSUPPORTED with nothing enqueued.  A failed
+ *    launch returns LCL_ERR_CUDA.  lcl_last_error() gives a one-line reason for the
+ *    last non-OK status on the calling thread.
+ *  - Layer textures are row-major planes of width x height labels (uint8 or uint16),
+ *    row 0 at v = 0.  Label 0 means "no data" (the paper's mask texture set to
+ *    false, Section 4.2).
+ *  - Limits: width a multiple of 4 in [4, 16384], height in [1, 16384],
+ *    tile in {8, 16, 32, 64, 128}; texture coordinates in [-1, 2]; at most 2^32-2
+ *    triangles.
+ */
+#ifndef LCL_H
+#define LCL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *lcl_stream; /* same type as cudaStream_t */
+
+typedef enum {
+    LCL_OK = 0,
+    LCL_ERR_INVALID_ARG = 1,
+    LCL_ERR_OUT_OF_MEMORY = 2, /* a caller buffer or workspace is too small */
+    LCL_ERR_CUDA = 3,
+    LCL_ERR_UNSUPPORTED = 4,
+    LCL_ERR_TIMEOUT = 5,
+    LCL_ERR_INTERNAL = 6
+} lcl_status;
+
+typedef enum { LCL_U8 = 1, LCL_U16 = 2 } lcl_dtype;
+typedef enum { LCL_AND = 0, LCL_OR = 1, LCL_XOR = 2, LCL_MASK = 3 } lcl_op;
+enum { LCL_NOT_A = 1, LCL_NOT_B = 2, LCL_NOT_OUT = 4 };
+
+#define LCL_GRID_BITS 21              /* quantised position grid: [0, 2^21 - 1] per axis */
+#define LCL_SUBPIXEL_BITS 8           /* rasteriser sub-pixel precision */
+#define LCL_AREA_FRAC_BITS 8          /* fractional bits of area weights */
+#define LCL_NO_TRIANGLE 0xFFFFFFFFu   /* triangle plane value of an uncovered texel */
+#define LCL_SUPER 16                  /* tiles per super-tile side (culling hierarchy) */
+#define LCL_MAX_LASSO_VERTICES 64
+
+/* Mesh in device memory (Section 4, Geometry Manager: geometry lives on the GPU).
+ * pos: n_pos x 3 float32; uv: n_uv x 2 float32; tri_pos / tri_uv: n_tri x 3 uint32
+ * indices into pos / uv (separate, so seams can duplicate texture coordinates). */
+typedef struct {
+    const float *pos;
+    int64_t n_pos;
+    const float *uv;
+    int64_t n_uv;
+    const uint32_t *tri_pos;
+    const uint32_t *tri_uv;
+    int64_t n_tri;
+} lcl_mesh;
+
+/* UV atlas of one model at one texture size.  Filled by lcl_atlas_bind (pointers into
+ * one caller buffer) and lcl_atlas_build (contents, bbox_min, scale).
+ *  pos_x/pos_y/pos_z: int32 planes (width x height): the 21-bit grid position of the
+ *      surface point at the texel centre; an uncovered texel holds (INT32_MIN, 0, 0).
+ *  tri: uint32 plane, the covering triangle (LCL_NO_TRIANGLE if none).
+ *  cover: coverage bits, bit (y*width + x) of a linear uint32 array.
+ *  tile_box: per tile (row-major over tiles_x x tiles_y) 8 int32: min x, min y, min z,
+ *      covered count, max x, max y, max z, 0 (empty: INT32_MAX mins, INT32_MIN maxes).
+ *  super_box: the same record per super-tile of LCL_SUPER x LCL_SUPER tiles.
+ *  area_w: uint64 per triangle, the surface area one of its texels stands for.
+ *  bbox_min, scale: the quantisation, grid = floor((p - bbox_min) * scale + 0.5).
+ *  row0: first texture row held by this atlas (0, or the start of a row view). */
+typedef struct {
+    int32_t width, height, tile;
+    int32_t tiles_x, tiles_y, supers_x, supers_y;
+    int32_t row0;
+    int64_t n_tri;
+    int32_t *pos_x, *pos_y, *pos_z;
+    uint32_t *tri;
+    uint32_t *cover;
+    int32_t *tile_box;  /* NULL in a row view */
+    int32_t *super_box; /* NULL in a row view */
+    uint64_t *area_w;
+    float bbox_min[3];
+    int32_t _pad;
+    double scale;
+} lcl_atlas;
+
+/* Sphere stroke in grid units (32 bytes): texels with (q - c)^2 <= r2 get `label`.
+ * flags is reserved and must be 0. */
+typedef struct {
+    int32_t cx, cy, cz, _pad;
+    int64_t r2;
+    uint32_t label, flags;
+} lcl_sphere;
+
+/* Camera: m maps a grid position (q, 1) to clip space (row-major 4x4, FP32),
+ * m = ViewProjection * Dequantise; width x height is the depth-map / screen size. */
+typedef struct {
+    float m[16];
+    int32_t width, height;
+} lcl_camera;
+
+/* ---- sizing and binding ------------------------------------------------- */
+
+/* Bytes of one atlas buffer for lcl_atlas_bind (0 if the sizes are invalid). */
+size_t lcl_atlas_bytes(int32_t width, int32_t height, int32_t tile, int64_t n_tri);
+
+/* Points the atlas planes into `base` (device, at least lcl_atlas_bytes bytes, 256-byte
+ * aligned).  Writes only *out; nothing is enqueued. */
+lcl_status lcl_atlas_bind(void *base, size_t bytes, int32_t width, int32_t height, int32_t tile,
+                          int64_t n_tri, lcl_atlas *out);
+
+/* A view of texture rows [y0, y1) of `atlas` for lcl_overlay and lcl_label_area on a
+ * band of the texture (layer pointers passed with it must point at row y0).  Requires
+ * y0 * width to be a multiple of 32.  Selections reject views. */
+lcl_status lcl_atlas_rows(const lcl_atlas *atlas, int32_t y0, int32_t y1, lcl_atlas *out);
+
+/* ---- atlas build -------------------------------------------------------- */
+
+/* Device workspace bytes lcl_atlas_build needs for this mesh and texture. */
+size_t lcl_atlas_workspace_bytes(const lcl_mesh *mesh, int32_t width, int32_t height);
+
+/* Builds the atlas of `mesh`: the UV-space rasterisation of Section 4.3.1 (the mesh drawn
+ * with its texture coordinates as positions, one fragment per texel), done once per model.
+ *  1. bbox of all positions; scale = (2^21 - 1) / largest extent; every vertex quantised to
+ *     the 21-bit grid, q = floor((p - bbox_min) * scale + 0.5) in double.
+ *  2. texture coordinates snapped to 1/256 texel (round half to even); texel (i, j) is
+ *     sampled at its centre; exact integer edge functions; a texel on an edge belongs to
+ *     the triangle owning that edge (counter-clockwise triangles own edges running down, or
+ *     left along a row); overlapping triangles: the smallest triangle id wins.
+ *  3. position at the texel centre from exact barycentrics w_k / A: floor((2 sum w_k q_k + A)
+ *     / (2 A)) per axis; coverage bits, tile and super-tile boxes.
+ *  4. area weights (Section 5, Table 1: area one texel stands for): 3D area over UV area,
+ *     floor(isqrt(|n|^2) * 2^24 / A) with n the grid-space normal, capped at 2^35 - 1.
+ * mesh, atlas planes and workspace are device memory; the call waits for `stream`
+ * before returning so that atlas->bbox_min and atlas->scale are valid on return.
+ * Errors: LCL_ERR_INVALID_ARG for sizes, a flat or non-finite bbox, an index out of range or
+ * texture coordinates outside [-1, 2] (the last three found on the device: the planes are
+ * then undefined); LCL_ERR_OUT_OF_MEMORY if ws_bytes is too small. */
+lcl_status lcl_atlas_build(const lcl_mesh *mesh, lcl_atlas *atlas, void *workspace, size_t ws_bytes,
+                           lcl_stream stream);
+
+/* ---- host helpers ------------------------------------------------------- */
+
+/* Sphere stroke from a world-space centre and radius (host only): the centre is quantised
+ * like a vertex but not clamped (LCL_ERR_INVALID_ARG outside [-2^22, 2^22 + 2^21]);
+ * r2 = floor((radius * scale)^2), capped at 2^50 (above every in-grid squared distance). */
+lcl_status lcl_quantize_sphere(const lcl_atlas *atlas, const double centre[3], double radius,
+                               uint32_t label, lcl_sphere *out);
+
+/* Camera from a world view-projection `vp` (row-major, host): m = vp * Dequantise, with
+ * Dequantise(q) = bbox_min + q / scale, composed in double and rounded to float. */
+lcl_status lcl_camera_from_vp(const lcl_atlas *atlas, const double vp[16], int32_t width, int32_t height,
+                              lcl_camera *out);
+
+/* ---- edits -------------------------------------------------------------- */
+
+/* Device workspace bytes for lcl_select_sphere / lcl_select_lasso with n strokes. */
+size_t lcl_select_workspace_bytes(const lcl_atlas *atlas, int32_t n_strokes);
+
+/* Sphere brush: the 3D counterpart of the paper's circular editing tool (Section 4.3).
+ * For each stroke k in order, every covered texel with squared grid distance
+ * (q - c)^2 <= r2 (int64) gets strokes[k].label; later strokes overwrite earlier ones; no
+ * other texel changes.  Tiles whose box lies farther than r from c are skipped.
+ *  layer: device, width x height labels of `dtype`, 4-byte aligned.
+ *  strokes: host array of n records (copied into the launch; the array may be reused on
+ *      return).  label must fit dtype; r2 >= 0 (values above 2^50 act as 2^50).
+ *  hits_out: device, n uint64 (nullable): the number of texels each stroke selected.
+ *  workspace: device, lcl_select_workspace_bytes(atlas, n) bytes. */
+lcl_status lcl_select_sphere(const lcl_atlas *atlas, void *layer, lcl_dtype dtype, const lcl_sphere *strokes,
+                             int32_t n, uint64_t *hits_out, void *workspace, size_t ws_bytes, lcl_stream stream);
+
+/* Device workspace bytes for lcl_depth_render. */
+size_t lcl_depth_workspace_bytes(const lcl_mesh *mesh, int32_t width, int32_t height);
+
+/* Depth texture (Section 4.3.1: scene depth from the current viewpoint, refreshed when the
+ * camera changes).  Vertices quantised as in the atlas, projected by camera->m in FP32 in
+ * the order ((m0 x + m1 y) + m2 z) + m3 without fused multiply-add; triangles with a corner
+ * at w <= 0, NDC depth outside [0, 1] or more than 2^20 px off screen are dropped; screen
+ * x = (x/w * 0.5 + 0.5) * width (row 0 at the bottom), snapped to 1/256 px; the same edge
+ * and ownership rules as the atlas at pixel centres; depth = minimum over triangles of the
+ * barycentric interpolation of corner NDC depth (double, rounded to float); +inf where
+ * nothing is drawn.  depth: device float32, camera->height rows x camera->width. */
+lcl_status lcl_depth_render(const lcl_mesh *mesh, const lcl_atlas *atlas, const lcl_camera *camera, float *depth,
+                            void *workspace, size_t ws_bytes, lcl_stream stream);
+
+/* Lasso selection: the paper's Texture Editing Algorithm (Section 4.3.1, Fig. 3) with the
+ * tool shape given as a polygon: for every covered texel, project its grid position as in
+ * lcl_depth_render; keep it if w > 0, NDC depth in [0, 1] and the point is on screen;
+ * inside by the even-odd rule (an edge (a, b) counts when (a.y > y) != (b.y > y) and
+ * x < (b.x - a.x) * (y - a.y) / (b.y - a.y) + a.x, FP32 in that order); visible iff
+ * z <= depth[floor(y)][floor(x)] + bias (Fig. 3a, "a small bias").  Selected texels get
+ * `label`.  poly_xy: host, n_vertices (3..64) x 2 float32 screen pixels.  depth: device,
+ * the map of the same camera.  hits_out: device, one uint64 (nullable). */
+lcl_status lcl_select_lasso(const lcl_atlas *atlas, void *layer, lcl_dtype dtype, const lcl_camera *camera,
+                            const float *depth, const float *poly_xy, int32_t n_vertices, uint32_t label,
+                            float bias, uint64_t *hits_out, void *workspace, size_t ws_bytes, lcl_stream stream);
+
+/* ---- layer operations --------------------------------------------------- */
+
+/* Boolean overlay of two layers (layer systems combine layers with logic operations,
+ * Section 3.4.2): per texel, a' = NOT_A ? ~a : a, b' = NOT_B ? ~b : b (within the label
+ * width), r = a' & b' | a' | b' | a' ^ b' | (b' != 0 ? a' : 0) for AND, OR, XOR, MASK,
+ * out = NOT_OUT ? ~r : r; uncovered texels get 0.  a, b, out: device layers of `dtype`;
+ * out may alias a or b. */
+lcl_status lcl_overlay(const lcl_atlas *atlas, const void *a, const void *b, void *out, lcl_dtype dtype, lcl_op op,
+                       uint32_t flags, lcl_stream stream);
+
+/* Per-label surface area (Section 5, Table 1: the area one texel stands for): over covered
+ * texels with label l < n_labels, count_out[l] = number of texels and area_out[l] = sum of
+ * their triangles' area weights (grid^2 units with 8 fractional bits; physical area =
+ * area * 2^-8 / scale^2).  Labels >= n_labels are ignored.  count_out, area_out: device,
+ * n_labels uint64 each (overwritten).  n_labels in [1, 65536]. */
+lcl_status lcl_label_area(const lcl_atlas *atlas, const void *layer, lcl_dtype dtype, uint32_t n_labels,
+                          uint64_t *count_out, uint64_t *area_out, lcl_stream stream);
+
+/* ---- diagnostics -------------------------------------------------------- */
+
+const char *lcl_status_str(lcl_status status);
+/* One-line reason for the last non-OK status returned on this thread ("" if none). */
+const char *lcl_last_error(void);
+/* Number of kernels this library has launched in this process (all devices). */
+uint64_t lcl_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LCL_H */

@@ -1,0 +1,203 @@
+// depth.cu -- the depth texture the lasso's visibility test reads (arXiv 2501.14807,
+// Section 4.3.1: scene depth from the current viewpoint, refreshed when the camera
+// changes; Fig. 3a).  The paper draws it with the graphics pipeline; here it is a CUDA
+// rasteriser with the same exact integer rules as the atlas build:
+//   k_clear       depth := +inf
+//   k_raster      one thread per triangle: quantise and project the corners (FP32, fixed
+//                 order, no FMA), snap to 1/256 px, and for small triangles test every pixel
+//                 centre of the bounding box; depth = barycentric interpolation of NDC z in
+//                 double, rounded to float; atomicMin on the float bits (all values >= 0)
+//   k_raster_big  big triangles split into 16 x 16-pixel blocks, one CTA per block
+#include <algorithm>
+
+#include "lcl_impl.cuh"
+
+namespace lcl {
+namespace {
+
+constexpr int64_t kGuardSub = int64_t(1) << 28;  // 2^20 px in sub-pixel units
+
+struct DepthHdr {
+    unsigned long long n_big;
+};
+
+struct DepthArgs {
+    const float *pos;
+    const uint32_t *tri_pos;
+    int64_t n_tri, n_pos;
+    float m[16];
+    float mn[3];
+    double scale;
+    int32_t w, h;
+    float fw, fh;
+    uint32_t *depth;  // float bits
+    DepthHdr *hdr;
+    uint2 *big;
+    int64_t big_cap;
+};
+
+struct DTri {
+    int64_t X[3], Y[3];
+    float Z[3];
+    int64_t A;
+};
+
+// Projects triangle t; false if it is dropped (bad index, w <= 0, z outside [0,1], off the
+// guard band, or zero screen area).  Corners are counter-clockwise on return.
+__device__ bool depth_setup(const DepthArgs &a, int64_t t, DTri &d) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const uint32_t ip = a.tri_pos[3 * t + k];
+        if (ip >= (uint64_t)a.n_pos) return false;
+        const float qx = (float)quantize_coord(a.pos[3 * (int64_t)ip + 0], a.mn[0], a.scale);
+        const float qy = (float)quantize_coord(a.pos[3 * (int64_t)ip + 1], a.mn[1], a.scale);
+        const float qz = (float)quantize_coord(a.pos[3 * (int64_t)ip + 2], a.mn[2], a.scale);
+        const float cw = clip_row(a.m + 12, qx, qy, qz);
+        if (!(cw > 0.0f)) return false;
+        const float zn = __fdiv_rn(clip_row(a.m + 8, qx, qy, qz), cw);
+        if (!(zn >= 0.0f && zn <= 1.0f)) return false;
+        const float xs = __fmul_rn(screen_of(__fdiv_rn(clip_row(a.m, qx, qy, qz), cw), a.fw), 256.0f);
+        const float ys = __fmul_rn(screen_of(__fdiv_rn(clip_row(a.m + 4, qx, qy, qz), cw), a.fh), 256.0f);
+        if (!(fabsf(xs) <= (float)kGuardSub && fabsf(ys) <= (float)kGuardSub)) return false;
+        d.X[k] = __float2ll_rn(xs);
+        d.Y[k] = __float2ll_rn(ys);
+        d.Z[k] = zn;
+    }
+    d.A = edge_fn(d.X[0], d.Y[0], d.X[1], d.Y[1], d.X[2], d.Y[2]);
+    if (d.A == 0) return false;
+    if (d.A < 0) {
+        int64_t tx = d.X[1], ty = d.Y[1];
+        float tz = d.Z[1];
+        d.X[1] = d.X[2]; d.Y[1] = d.Y[2]; d.Z[1] = d.Z[2];
+        d.X[2] = tx; d.Y[2] = ty; d.Z[2] = tz;
+        d.A = -d.A;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void pixel_range(const DTri &d, int32_t w, int32_t h, int64_t &i0, int64_t &i1, int64_t &j0,
+                                            int64_t &j1) {
+    int64_t xmin = min(d.X[0], min(d.X[1], d.X[2])), xmax = max(d.X[0], max(d.X[1], d.X[2]));
+    int64_t ymin = min(d.Y[0], min(d.Y[1], d.Y[2])), ymax = max(d.Y[0], max(d.Y[1], d.Y[2]));
+    i0 = -floordiv(-(xmin - 128), 256);
+    i1 = floordiv(xmax - 128, 256);
+    j0 = -floordiv(-(ymin - 128), 256);
+    j1 = floordiv(ymax - 128, 256);
+    i0 = max(i0, (int64_t)0);
+    j0 = max(j0, (int64_t)0);
+    i1 = min(i1, (int64_t)w - 1);
+    j1 = min(j1, (int64_t)h - 1);
+}
+
+// Depth of the pixel centre (px, py) if covered; writes it with atomicMin.
+__device__ __forceinline__ void depth_pixel(const DTri &d, int64_t i, int64_t j, int32_t w, uint32_t *depth) {
+    const int64_t px = 256 * i + 128, py = 256 * j + 128;
+    const int64_t w0 = edge_fn(d.X[1], d.Y[1], d.X[2], d.Y[2], px, py);
+    const int64_t w1 = edge_fn(d.X[2], d.Y[2], d.X[0], d.Y[0], px, py);
+    const int64_t w2 = edge_fn(d.X[0], d.Y[0], d.X[1], d.Y[1], px, py);
+    if (w0 + edge_bias(d.X[2] - d.X[1], d.Y[2] - d.Y[1]) <= 0) return;
+    if (w1 + edge_bias(d.X[0] - d.X[2], d.Y[0] - d.Y[2]) <= 0) return;
+    if (w2 + edge_bias(d.X[1] - d.X[0], d.Y[1] - d.Y[0]) <= 0) return;
+    const double num = __dadd_rn(__dadd_rn(__dmul_rn(__ll2double_rn(w0), (double)d.Z[0]),
+                                           __dmul_rn(__ll2double_rn(w1), (double)d.Z[1])),
+                                 __dmul_rn(__ll2double_rn(w2), (double)d.Z[2]));
+    float z = __double2float_rn(__ddiv_rn(num, __ll2double_rn(d.A)));
+    z = __fadd_rn(z, 0.0f);  // no negative zero
+    atomicMin(depth + j * (int64_t)w + i, __float_as_uint(z));
+}
+
+__global__ void k_clear(uint32_t *__restrict__ depth, int64_t n) {
+    const uint32_t inf = 0x7F800000u;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        depth[i] = inf;
+}
+
+__global__ void k_hdr_reset(DepthHdr *hdr) { hdr->n_big = 0; }
+
+__global__ void k_raster(const __grid_constant__ DepthArgs a) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= a.n_tri) return;
+    DTri d;
+    if (!depth_setup(a, t, d)) return;
+    int64_t i0, i1, j0, j1;
+    pixel_range(d, a.w, a.h, i0, i1, j0, j1);
+    if (i0 > i1 || j0 > j1) return;
+    const int64_t nx = i1 - i0 + 1, ny = j1 - j0 + 1;
+    if (nx * ny > kSmallRaster) {
+        const int64_t nb = ((nx + kBlockSide - 1) / kBlockSide) * ((ny + kBlockSide - 1) / kBlockSide);
+        const unsigned long long base = atomicAdd(&a.hdr->n_big, (unsigned long long)nb);
+        if ((int64_t)base + nb <= a.big_cap) {
+            for (int64_t b = 0; b < nb; ++b) a.big[base + b] = make_uint2((uint32_t)t, (uint32_t)b);
+            return;
+        }
+    }
+#pragma unroll 1
+    for (int64_t j = j0; j <= j1; ++j)
+#pragma unroll 1
+        for (int64_t i = i0; i <= i1; ++i) depth_pixel(d, i, j, a.w, a.depth);
+}
+
+__global__ void __launch_bounds__(kThreads) k_raster_big(const __grid_constant__ DepthArgs a) {
+    __shared__ DTri sd;
+    __shared__ int ok;
+    const int64_t n = min((int64_t)a.hdr->n_big, a.big_cap);
+    for (int64_t e = blockIdx.x; e < n; e += gridDim.x) {
+        const uint2 ent = a.big[e];
+        if (threadIdx.x == 0) ok = depth_setup(a, ent.x, sd) ? 1 : 0;
+        __syncthreads();
+        if (ok) {
+            const DTri d = sd;
+            int64_t i0, i1, j0, j1;
+            pixel_range(d, a.w, a.h, i0, i1, j0, j1);
+            const int64_t nbx = (i1 - i0 + 1 + kBlockSide - 1) / kBlockSide;
+            const int64_t bx = ent.y % nbx, by = ent.y / nbx;
+            const int64_t i = i0 + bx * kBlockSide + (threadIdx.x % kBlockSide);
+            const int64_t j = j0 + by * kBlockSide + (threadIdx.x / kBlockSide);
+            if (i <= i1 && j <= j1) depth_pixel(d, i, j, a.w, a.depth);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+size_t depth_ws_bytes(int64_t n_tri, int32_t w, int32_t h) {
+    return align256(sizeof(DepthHdr)) + align256(big_capacity(n_tri, w, h) * sizeof(uint2));
+}
+
+lcl_status depth_render_impl(const lcl_mesh *mesh, const lcl_atlas *atlas, const lcl_camera *cam, float *depth,
+                             void *ws, size_t ws_bytes, cudaStream_t st) {
+    if (ws_bytes < depth_ws_bytes(mesh->n_tri, cam->width, cam->height))
+        return fail(LCL_ERR_OUT_OF_MEMORY, "depth workspace smaller than lcl_depth_workspace_bytes");
+    DepthArgs a;
+    a.pos = mesh->pos;
+    a.tri_pos = mesh->tri_pos;
+    a.n_tri = mesh->n_tri;
+    a.n_pos = mesh->n_pos;
+    for (int i = 0; i < 16; ++i) a.m[i] = cam->m[i];
+    for (int i = 0; i < 3; ++i) a.mn[i] = atlas->bbox_min[i];
+    a.scale = atlas->scale;
+    a.w = cam->width;
+    a.h = cam->height;
+    a.fw = (float)cam->width;
+    a.fh = (float)cam->height;
+    a.depth = reinterpret_cast<uint32_t *>(depth);
+    a.hdr = reinterpret_cast<DepthHdr *>(ws);
+    a.big = reinterpret_cast<uint2 *>(static_cast<char *>(ws) + align256(sizeof(DepthHdr)));
+    a.big_cap = (int64_t)big_capacity(mesh->n_tri, cam->width, cam->height);
+    const int64_t n_px = (int64_t)cam->width * cam->height;
+    const int sms = sm_count();
+    k_clear<<<sms * 4, kThreads, 0, st>>>(a.depth, n_px);
+    k_hdr_reset<<<1, 1, 0, st>>>(a.hdr);
+    count_launches(2);
+    if (mesh->n_tri > 0) {
+        k_raster<<<(unsigned)((mesh->n_tri + 127) / 128), 128, 0, st>>>(a);
+        k_raster_big<<<sms * 8, kThreads, 0, st>>>(a);
+        count_launches(2);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "lcl_depth_render launch");
+    return LCL_OK;
+}
+
+}  // namespace lcl

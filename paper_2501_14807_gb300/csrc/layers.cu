@@ -1,0 +1,215 @@
+// layers.cu -- whole-layer operations: boolean overlays and per-label surface area.
+// Layer systems combine layers with logic operations (arXiv 2501.14807, Section 3.4.2) and
+// measure what they hold (Section 5, Table 1 gives the area one texel stands for).
+// Both are pure HBM streams over the texture:
+//   k_overlay  16 bytes of each operand and of the output per thread step, coverage bits
+//              expanded to byte / half-word masks in registers (SWAR), no shared memory
+//   k_area     16 texels per thread step: labels (16 or 32 bytes) and triangle ids (64 bytes);
+//              runs of equal labels are summed in registers, flushed into a shared-memory
+//              histogram (64-bit shared atomics), and the histogram into the outputs with
+//              one global atomic per non-zero bin per CTA; all sums are integers, so the
+//              result does not depend on the order.
+#include <algorithm>
+
+#include "lcl_impl.cuh"
+
+namespace lcl {
+namespace {
+
+constexpr uint32_t kSmemLabels = 2048;  // histograms up to this size live in shared memory
+
+// Byte (or half-word) lanes of x that are non-zero -> all-ones lanes.
+__device__ __forceinline__ uint32_t nonzero_lanes(uint32_t x, int bytes) {
+    if (bytes == 1) {
+        uint32_t t = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;
+        return ((t & 0x80808080u) >> 7) * 0xFFu;
+    }
+    uint32_t t = ((x & 0x7FFF7FFFu) + 0x7FFF7FFFu) | x;
+    return ((t & 0x80008000u) >> 15) * 0xFFFFu;
+}
+
+// Coverage bits of the lanes of one 32-bit word -> all-ones lanes.
+__device__ __forceinline__ uint32_t cover_lanes(uint32_t bits, int bytes) {
+    if (bytes == 1) return ((bits * 0x00204081u) & 0x01010101u) * 0xFFu;
+    return ((bits & 1u) ? 0x0000FFFFu : 0u) | ((bits & 2u) ? 0xFFFF0000u : 0u);
+}
+
+__device__ __forceinline__ uint32_t overlay_word(uint32_t a, uint32_t b, uint32_t cov, int op, uint32_t flags,
+                                                 int bytes) {
+    if (flags & LCL_NOT_A) a = ~a;
+    if (flags & LCL_NOT_B) b = ~b;
+    uint32_t r;
+    switch (op) {
+    case LCL_AND: r = a & b; break;
+    case LCL_OR: r = a | b; break;
+    case LCL_XOR: r = a ^ b; break;
+    default: r = a & nonzero_lanes(b, bytes); break;
+    }
+    if (flags & LCL_NOT_OUT) r = ~r;
+    return r & cover_lanes(cov, bytes);
+}
+
+template <int BYTES>
+__global__ void __launch_bounds__(kThreads) k_overlay(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b,
+                                                      uint32_t *__restrict__ out, const uint32_t *__restrict__ cover,
+                                                      int64_t n_words, int op, uint32_t flags) {
+    constexpr int kLanes = 4 / BYTES;  // texels per 32-bit word
+    const int64_t n_vec = n_words / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n_vec; v += stride) {
+        const uint4 A = __ldcs(reinterpret_cast<const uint4 *>(a) + v);
+        const uint4 B = __ldcs(reinterpret_cast<const uint4 *>(b) + v);
+        const int64_t t0 = v * 4 * kLanes;  // first texel of this 16-byte chunk
+        const uint32_t cw = __ldg(cover + (t0 >> 5)) >> (t0 & 31);
+        uint4 R;
+        R.x = overlay_word(A.x, B.x, cw & ((1u << kLanes) - 1), op, flags, BYTES);
+        R.y = overlay_word(A.y, B.y, (cw >> kLanes) & ((1u << kLanes) - 1), op, flags, BYTES);
+        R.z = overlay_word(A.z, B.z, (cw >> (2 * kLanes)) & ((1u << kLanes) - 1), op, flags, BYTES);
+        R.w = overlay_word(A.w, B.w, (cw >> (3 * kLanes)) & ((1u << kLanes) - 1), op, flags, BYTES);
+        __stcs(reinterpret_cast<uint4 *>(out) + v, R);
+    }
+    // tail: the last n_words % 4 words
+    const int64_t w = n_vec * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (w < n_words) {
+        const int64_t t0 = w * kLanes;
+        const uint32_t cw = (cover[t0 >> 5] >> (t0 & 31)) & ((1u << kLanes) - 1);
+        out[w] = overlay_word(a[w], b[w], cw, op, flags, BYTES);
+    }
+}
+
+__global__ void k_zero2(unsigned long long *x, unsigned long long *y, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        x[i] = 0;
+        y[i] = 0;
+    }
+}
+
+struct Run {
+    uint32_t label;
+    uint32_t cnt;
+    unsigned long long area;
+};
+
+template <bool SMEM>
+__device__ __forceinline__ void flush(const Run &r, unsigned long long *hc, unsigned long long *ha, uint32_t n_labels) {
+    if (r.cnt == 0) return;
+    atomicAdd(hc + r.label, (unsigned long long)r.cnt);
+    atomicAdd(ha + r.label, r.area);
+    (void)n_labels;
+}
+
+template <typename L, bool SMEM>
+__global__ void __launch_bounds__(kThreads) k_area(const L *__restrict__ layer, const uint32_t *__restrict__ tri,
+                                                   const uint64_t *__restrict__ area_w, int64_t n_texels,
+                                                   uint32_t n_labels, unsigned long long *__restrict__ count,
+                                                   unsigned long long *__restrict__ area) {
+    extern __shared__ unsigned long long sh[];
+    unsigned long long *hc = SMEM ? sh : count;
+    unsigned long long *ha = SMEM ? sh + n_labels : area;
+    if (SMEM) {
+        for (uint32_t i = threadIdx.x; i < 2 * n_labels; i += blockDim.x) sh[i] = 0;
+        __syncthreads();
+    }
+    Run run{0u, 0u, 0ull};
+    uint32_t last_t = kNone;
+    unsigned long long last_w = 0;
+    auto visit = [&](uint32_t lab, uint32_t t) {
+        if (t == kNone || lab >= n_labels) return;
+        if (t != last_t) {
+            last_t = t;
+            last_w = __ldg(reinterpret_cast<const unsigned long long *>(area_w) + t);
+        }
+        if (lab != run.label || run.cnt == 0) {
+            flush<SMEM>(run, hc, ha, n_labels);
+            run.label = lab;
+            run.cnt = 0;
+            run.area = 0;
+        }
+        run.cnt += 1;
+        run.area += last_w;
+    };
+    const int64_t n_chunks = n_texels / 16;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n_chunks; c += stride) {
+        const uint4 *tp = reinterpret_cast<const uint4 *>(tri + 16 * c);
+        uint4 T4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) T4[k] = __ldcs(tp + k);
+        uint32_t labs[16];
+        if (sizeof(L) == 1) {
+            const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(layer + 16 * c));
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 16; ++k) labs[k] = (w[k / 4] >> (8 * (k % 4))) & 0xFFu;
+        } else {
+            const uint4 v0 = __ldcs(reinterpret_cast<const uint4 *>(layer + 16 * c));
+            const uint4 v1 = __ldcs(reinterpret_cast<const uint4 *>(layer + 16 * c) + 1);
+            const uint32_t w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+            for (int k = 0; k < 16; ++k) labs[k] = (w[k / 2] >> (16 * (k % 2))) & 0xFFFFu;
+        }
+        const uint32_t ts[16] = {T4[0].x, T4[0].y, T4[0].z, T4[0].w, T4[1].x, T4[1].y, T4[1].z, T4[1].w,
+                                 T4[2].x, T4[2].y, T4[2].z, T4[2].w, T4[3].x, T4[3].y, T4[3].z, T4[3].w};
+#pragma unroll
+        for (int k = 0; k < 16; ++k) visit(labs[k], ts[k]);
+    }
+    // tail texels (n_texels % 16)
+    const int64_t tail = n_chunks * 16 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tail < n_texels) visit((uint32_t)layer[tail], tri[tail]);
+    flush<SMEM>(run, hc, ha, n_labels);
+    if (SMEM) {
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n_labels; i += blockDim.x) {
+            if (sh[i]) {
+                atomicAdd(count + i, sh[i]);
+                atomicAdd(area + i, sh[n_labels + i]);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+lcl_status overlay_impl(const lcl_atlas *atlas, const void *a, const void *b, void *out, int dtype_bytes, int op,
+                        uint32_t flags, cudaStream_t st) {
+    const int64_t n_tex = (int64_t)atlas->width * atlas->height;
+    const int64_t n_words = n_tex * dtype_bytes / 4;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count() * 8, (n_words / 4 + kThreads - 1) / kThreads));
+    if (dtype_bytes == 1)
+        k_overlay<1><<<grid, kThreads, 0, st>>>(static_cast<const uint32_t *>(a), static_cast<const uint32_t *>(b),
+                                                static_cast<uint32_t *>(out), atlas->cover, n_words, op, flags);
+    else
+        k_overlay<2><<<grid, kThreads, 0, st>>>(static_cast<const uint32_t *>(a), static_cast<const uint32_t *>(b),
+                                                static_cast<uint32_t *>(out), atlas->cover, n_words, op, flags);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "lcl_overlay launch");
+    return LCL_OK;
+}
+
+lcl_status label_area_impl(const lcl_atlas *atlas, const void *layer, int dtype_bytes, uint32_t n_labels,
+                           uint64_t *count, uint64_t *area, cudaStream_t st) {
+    const int64_t n_tex = (int64_t)atlas->width * atlas->height;
+    unsigned long long *c = reinterpret_cast<unsigned long long *>(count);
+    unsigned long long *ar = reinterpret_cast<unsigned long long *>(area);
+    k_zero2<<<std::max(1u, std::min(1024u, (n_labels + kThreads - 1) / kThreads)), kThreads, 0, st>>>(c, ar, n_labels);
+    const bool smem = n_labels <= kSmemLabels;
+    const size_t shb = smem ? 2 * (size_t)n_labels * sizeof(unsigned long long) : 0;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count() * 4, (n_tex / 16 + kThreads - 1) / kThreads));
+    const uint32_t *tri = atlas->tri;
+    if (dtype_bytes == 1) {
+        const uint8_t *l = static_cast<const uint8_t *>(layer);
+        if (smem) k_area<uint8_t, true><<<grid, kThreads, shb, st>>>(l, tri, atlas->area_w, n_tex, n_labels, c, ar);
+        else k_area<uint8_t, false><<<grid, kThreads, 0, st>>>(l, tri, atlas->area_w, n_tex, n_labels, c, ar);
+    } else {
+        const uint16_t *l = static_cast<const uint16_t *>(layer);
+        if (smem) k_area<uint16_t, true><<<grid, kThreads, shb, st>>>(l, tri, atlas->area_w, n_tex, n_labels, c, ar);
+        else k_area<uint16_t, false><<<grid, kThreads, 0, st>>>(l, tri, atlas->area_w, n_tex, n_labels, c, ar);
+    }
+    count_launches(2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "lcl_label_area launch");
+    return LCL_OK;
+}
+
+}  // namespace lcl

@@ -1,0 +1,334 @@
+"""Thin Python binding of the C ABI in include/lcl.h (ctypes).
+
+The functions keep the C names (``lcl_atlas_build`` ...) and only marshal arguments:
+every step of the path runs in the CUDA library ``liblcl.so``.  PyTorch provides device
+memory and streams.  If the library has not been built, loading fails loudly: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblcl.so")
+
+LCL_OK = 0
+STATUS = {0: "LCL_OK", 1: "LCL_ERR_INVALID_ARG", 2: "LCL_ERR_OUT_OF_MEMORY", 3: "LCL_ERR_CUDA",
+          4: "LCL_ERR_UNSUPPORTED", 5: "LCL_ERR_TIMEOUT", 6: "LCL_ERR_INTERNAL"}
+LCL_U8, LCL_U16 = 1, 2
+LCL_AND, LCL_OR, LCL_XOR, LCL_MASK = 0, 1, 2, 3
+LCL_NOT_A, LCL_NOT_B, LCL_NOT_OUT = 1, 2, 4
+OPS = {"and": LCL_AND, "or": LCL_OR, "xor": LCL_XOR, "mask": LCL_MASK}
+NO_TRIANGLE = 0xFFFFFFFF
+SUPER = 16
+DEFAULT_BIAS = 2.0 ** -10
+
+EXPORTS = ["lcl_atlas_bytes", "lcl_atlas_bind", "lcl_atlas_rows", "lcl_atlas_workspace_bytes", "lcl_atlas_build",
+           "lcl_quantize_sphere", "lcl_camera_from_vp", "lcl_select_workspace_bytes", "lcl_select_sphere",
+           "lcl_depth_workspace_bytes", "lcl_depth_render", "lcl_select_lasso", "lcl_overlay", "lcl_label_area",
+           "lcl_status_str", "lcl_last_error", "lcl_kernel_launches"]
+
+
+class lcl_mesh(C.Structure):
+    _fields_ = [("pos", C.c_void_p), ("n_pos", C.c_int64), ("uv", C.c_void_p), ("n_uv", C.c_int64),
+                ("tri_pos", C.c_void_p), ("tri_uv", C.c_void_p), ("n_tri", C.c_int64)]
+
+
+class lcl_atlas(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("tile", C.c_int32),
+                ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("supers_x", C.c_int32), ("supers_y", C.c_int32),
+                ("row0", C.c_int32), ("n_tri", C.c_int64),
+                ("pos_x", C.c_void_p), ("pos_y", C.c_void_p), ("pos_z", C.c_void_p), ("tri", C.c_void_p),
+                ("cover", C.c_void_p), ("tile_box", C.c_void_p), ("super_box", C.c_void_p), ("area_w", C.c_void_p),
+                ("bbox_min", C.c_float * 3), ("_pad", C.c_int32), ("scale", C.c_double)]
+
+
+class lcl_sphere(C.Structure):
+    _fields_ = [("cx", C.c_int32), ("cy", C.c_int32), ("cz", C.c_int32), ("_pad", C.c_int32),
+                ("r2", C.c_int64), ("label", C.c_uint32), ("flags", C.c_uint32)]
+
+
+class lcl_camera(C.Structure):
+    _fields_ = [("m", C.c_float * 16), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+assert C.sizeof(lcl_sphere) == 32 and C.sizeof(lcl_camera) == 72 and C.sizeof(lcl_atlas) == 128
+
+SPHERE_DTYPE = np.dtype([("cx", "<i4"), ("cy", "<i4"), ("cz", "<i4"), ("pad", "<i4"),
+                         ("r2", "<i8"), ("label", "<u4"), ("flags", "<u4")])
+
+
+class LclError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__(f"{fn}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library():
+    """Loads liblcl.so (built by __graft_entry__.build() or paper_2501_14807_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first (python -c 'import "
+                           "__graft_entry__ as g; g.build()'); there is no CPU fallback")
+    lib = C.CDLL(LIB_PATH)
+    P, I32, I64, U32, SZ, F, D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_size_t, C.c_float, C.c_double
+    st = C.c_int
+    sig = {
+        "lcl_atlas_bytes": (SZ, [I32, I32, I32, I64]),
+        "lcl_atlas_bind": (st, [P, SZ, I32, I32, I32, I64, C.POINTER(lcl_atlas)]),
+        "lcl_atlas_rows": (st, [C.POINTER(lcl_atlas), I32, I32, C.POINTER(lcl_atlas)]),
+        "lcl_atlas_workspace_bytes": (SZ, [C.POINTER(lcl_mesh), I32, I32]),
+        "lcl_atlas_build": (st, [C.POINTER(lcl_mesh), C.POINTER(lcl_atlas), P, SZ, P]),
+        "lcl_quantize_sphere": (st, [C.POINTER(lcl_atlas), C.POINTER(D), D, U32, C.POINTER(lcl_sphere)]),
+        "lcl_camera_from_vp": (st, [C.POINTER(lcl_atlas), C.POINTER(D), I32, I32, C.POINTER(lcl_camera)]),
+        "lcl_select_workspace_bytes": (SZ, [C.POINTER(lcl_atlas), I32]),
+        "lcl_select_sphere": (st, [C.POINTER(lcl_atlas), P, C.c_int, P, I32, P, P, SZ, P]),
+        "lcl_depth_workspace_bytes": (SZ, [C.POINTER(lcl_mesh), I32, I32]),
+        "lcl_depth_render": (st, [C.POINTER(lcl_mesh), C.POINTER(lcl_atlas), C.POINTER(lcl_camera), P, P, SZ, P]),
+        "lcl_select_lasso": (st, [C.POINTER(lcl_atlas), P, C.c_int, C.POINTER(lcl_camera), P, P, I32, U32, F, P, P,
+                                  SZ, P]),
+        "lcl_overlay": (st, [C.POINTER(lcl_atlas), P, P, P, C.c_int, C.c_int, U32, P]),
+        "lcl_label_area": (st, [C.POINTER(lcl_atlas), P, C.c_int, U32, P, P, P]),
+        "lcl_status_str": (C.c_char_p, [C.c_int]),
+        "lcl_last_error": (C.c_char_p, []),
+        "lcl_kernel_launches": (C.c_uint64, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(fn, status):
+    if status != LCL_OK:
+        raise LclError(fn, status, library().lcl_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _dtype_code(layer: torch.Tensor) -> int:
+    if layer.element_size() == 1:
+        return LCL_U8
+    if layer.element_size() == 2:
+        return LCL_U16
+    raise ValueError("layers hold uint8 or 16-bit labels")
+
+
+def _workspace(nbytes, device):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+class Mesh:
+    """Mesh arrays resident on the device plus their lcl_mesh descriptor."""
+
+    def __init__(self, pos: torch.Tensor, uv: torch.Tensor, tri_pos: torch.Tensor, tri_uv: torch.Tensor):
+        for t in (pos, uv, tri_pos, tri_uv):
+            assert t.is_cuda and t.is_contiguous()
+        self.pos, self.uv, self.tri_pos, self.tri_uv = pos, uv, tri_pos, tri_uv
+        self.c = lcl_mesh(pos.data_ptr(), pos.shape[0], uv.data_ptr(), uv.shape[0], tri_pos.data_ptr(),
+                          tri_uv.data_ptr(), tri_pos.shape[0])
+
+    @property
+    def n_tri(self):
+        return int(self.c.n_tri)
+
+    @staticmethod
+    def from_host(mesh, device="cuda", non_blocking=False):
+        """Copies a host mesh (numpy arrays: pos float32 [n,3], uv float32 [n,2], tri_pos/tri_uv uint32 [n,3])."""
+        def up(a, dt):
+            t = torch.from_numpy(np.ascontiguousarray(a).view(dt))
+            if non_blocking:
+                t = t.pin_memory()
+            return t.to(device, non_blocking=non_blocking)
+        return Mesh(up(mesh.pos, np.float32), up(mesh.uv, np.float32), up(mesh.tri_pos, np.int32),
+                    up(mesh.tri_uv, np.int32))
+
+
+class Atlas:
+    """One atlas buffer (device) bound with lcl_atlas_bind."""
+
+    def __init__(self, width, height, tile, n_tri, device="cuda", buffer=None):
+        lib = library()
+        nbytes = lib.lcl_atlas_bytes(width, height, tile, n_tri)
+        if nbytes == 0:
+            raise LclError("lcl_atlas_bytes", 1, "invalid atlas sizes")
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device) if buffer is None else buffer
+        self.c = lcl_atlas()
+        _check("lcl_atlas_bind", lib.lcl_atlas_bind(C.c_void_p(self.buf.data_ptr()), nbytes, width, height, tile,
+                                                   n_tri, C.byref(self.c)))
+
+    width = property(lambda s: int(s.c.width))
+    height = property(lambda s: int(s.c.height))
+    tile = property(lambda s: int(s.c.tile))
+
+    def _view(self, ptr, count, dtype, shape):
+        off = ptr - self.buf.data_ptr()
+        esz = torch.empty((), dtype=dtype).element_size()
+        return self.buf[off:off + count * esz].view(dtype).view(shape)
+
+    def plane(self, name):
+        """Device view of pos_x / pos_y / pos_z (int32) or tri (int32 bits of uint32) as [H, W]."""
+        return self._view(getattr(self.c, name), self.width * self.height, torch.int32, (self.height, self.width))
+
+    def cover(self):
+        n = (self.width * self.height + 31) // 32
+        return self._view(self.c.cover, n, torch.int32, (n,))
+
+    def tile_box(self):
+        n = self.c.tiles_x * self.c.tiles_y
+        return self._view(self.c.tile_box, n * 8, torch.int32, (n, 8))
+
+    def super_box(self):
+        n = self.c.supers_x * self.c.supers_y
+        return self._view(self.c.super_box, n * 8, torch.int32, (n, 8))
+
+    def area_w(self):
+        return self._view(self.c.area_w, int(self.c.n_tri), torch.int64, (int(self.c.n_tri),))
+
+    @property
+    def bbox_min(self):
+        return np.array(list(self.c.bbox_min), np.float32)
+
+    @property
+    def scale(self):
+        return float(self.c.scale)
+
+
+# ---- entry points (same names as the C ABI) ----------------------------------------
+
+def lcl_atlas_bytes(width, height, tile, n_tri):
+    return int(library().lcl_atlas_bytes(width, height, tile, n_tri))
+
+
+def lcl_atlas_workspace_bytes(mesh: Mesh, width, height):
+    return int(library().lcl_atlas_workspace_bytes(C.byref(mesh.c), width, height))
+
+
+def lcl_atlas_build(mesh: Mesh, atlas: Atlas, workspace=None, stream=None):
+    ws = workspace if workspace is not None else _workspace(lcl_atlas_workspace_bytes(mesh, atlas.width,
+                                                                                      atlas.height), mesh.pos.device)
+    _check("lcl_atlas_build", library().lcl_atlas_build(C.byref(mesh.c), C.byref(atlas.c), _ptr(ws), ws.numel(),
+                                                        _stream(stream)))
+    return atlas
+
+
+def lcl_atlas_rows(atlas: Atlas, y0, y1):
+    out = lcl_atlas()
+    _check("lcl_atlas_rows", library().lcl_atlas_rows(C.byref(atlas.c), y0, y1, C.byref(out)))
+    view = Atlas.__new__(Atlas)
+    view.buf, view.c = atlas.buf, out
+    return view
+
+
+def lcl_quantize_sphere(atlas: Atlas, centre, radius, label):
+    out = lcl_sphere()
+    c = (C.c_double * 3)(*[float(v) for v in centre])
+    _check("lcl_quantize_sphere", library().lcl_quantize_sphere(C.byref(atlas.c), c, float(radius), int(label),
+                                                                C.byref(out)))
+    rec = np.zeros(1, SPHERE_DTYPE)
+    rec[0] = (out.cx, out.cy, out.cz, 0, out.r2, out.label, out.flags)
+    return rec[0]
+
+
+def lcl_camera_from_vp(atlas: Atlas, vp, width, height):
+    out = lcl_camera()
+    v = (C.c_double * 16)(*[float(x) for x in np.asarray(vp, np.float64).reshape(16)])
+    _check("lcl_camera_from_vp", library().lcl_camera_from_vp(C.byref(atlas.c), v, width, height, C.byref(out)))
+    return out
+
+
+def camera(m, width, height):
+    """lcl_camera from a float32[16] matrix already in grid space."""
+    cam = lcl_camera()
+    for i, x in enumerate(np.asarray(m, np.float32).reshape(16)):
+        cam.m[i] = float(x)
+    cam.width, cam.height = int(width), int(height)
+    return cam
+
+
+def lcl_select_workspace_bytes(atlas: Atlas, n_strokes):
+    return int(library().lcl_select_workspace_bytes(C.byref(atlas.c), int(n_strokes)))
+
+
+def lcl_select_sphere(atlas: Atlas, layer: torch.Tensor, strokes, hits_out=None, workspace=None, stream=None):
+    """Applies sphere strokes (numpy records of SPHERE_DTYPE, in order) to ``layer`` on the device."""
+    recs = np.ascontiguousarray(strokes, dtype=SPHERE_DTYPE)
+    n = len(recs)
+    ws = workspace if workspace is not None else _workspace(lcl_select_workspace_bytes(atlas, n), layer.device)
+    _check("lcl_select_sphere", library().lcl_select_sphere(
+        C.byref(atlas.c), _ptr(layer), _dtype_code(layer), recs.ctypes.data_as(C.c_void_p), n, _ptr(hits_out),
+        _ptr(ws), ws.numel(), _stream(stream)))
+    return hits_out
+
+
+def lcl_depth_workspace_bytes(mesh: Mesh, width, height):
+    return int(library().lcl_depth_workspace_bytes(C.byref(mesh.c), width, height))
+
+
+def lcl_depth_render(mesh: Mesh, atlas: Atlas, cam: lcl_camera, depth: torch.Tensor, workspace=None, stream=None):
+    ws = workspace if workspace is not None else _workspace(lcl_depth_workspace_bytes(mesh, cam.width, cam.height),
+                                                            depth.device)
+    _check("lcl_depth_render", library().lcl_depth_render(C.byref(mesh.c), C.byref(atlas.c), C.byref(cam),
+                                                          _ptr(depth), _ptr(ws), ws.numel(), _stream(stream)))
+    return depth
+
+
+def lcl_select_lasso(atlas: Atlas, layer: torch.Tensor, cam: lcl_camera, depth: torch.Tensor, poly, label,
+                     bias=DEFAULT_BIAS, hits_out=None, workspace=None, stream=None):
+    poly = np.ascontiguousarray(poly, dtype=np.float32)
+    ws = workspace if workspace is not None else _workspace(lcl_select_workspace_bytes(atlas, 1), layer.device)
+    _check("lcl_select_lasso", library().lcl_select_lasso(
+        C.byref(atlas.c), _ptr(layer), _dtype_code(layer), C.byref(cam), _ptr(depth),
+        poly.ctypes.data_as(C.c_void_p), poly.shape[0], int(label), float(bias), _ptr(hits_out), _ptr(ws),
+        ws.numel(), _stream(stream)))
+    return hits_out
+
+
+def lcl_overlay(atlas: Atlas, a: torch.Tensor, b: torch.Tensor, out: torch.Tensor, op, flags=0, stream=None):
+    op = OPS[op] if isinstance(op, str) else int(op)
+    _check("lcl_overlay", library().lcl_overlay(C.byref(atlas.c), _ptr(a), _ptr(b), _ptr(out), _dtype_code(a), op,
+                                                int(flags), _stream(stream)))
+    return out
+
+
+def lcl_label_area(atlas: Atlas, layer: torch.Tensor, n_labels, count_out=None, area_out=None, stream=None):
+    dev = layer.device
+    count_out = torch.empty(n_labels, dtype=torch.int64, device=dev) if count_out is None else count_out
+    area_out = torch.empty(n_labels, dtype=torch.int64, device=dev) if area_out is None else area_out
+    _check("lcl_label_area", library().lcl_label_area(C.byref(atlas.c), _ptr(layer), _dtype_code(layer),
+                                                      int(n_labels), _ptr(count_out), _ptr(area_out),
+                                                      _stream(stream)))
+    return count_out, area_out
+
+
+def lcl_status_str(status):
+    return library().lcl_status_str(int(status)).decode()
+
+
+def lcl_last_error():
+    return library().lcl_last_error().decode()
+
+
+def lcl_kernel_launches():
+    return int(library().lcl_kernel_launches())

@@ -24,18 +24,30 @@ def bbox_diag(mesh: Mesh) -> float:
     return float(np.linalg.norm(p.max(0) - p.min(0)))
 
 
-def surface_points(mesh: Mesh, n: int, rng) -> np.ndarray:
-    """n points uniform on the surface: triangle by 3D area, then uniform barycentrics."""
+def _area_cdf(mesh: Mesh) -> np.ndarray:
+    cached = getattr(mesh, "_area_cdf", None)
+    if cached is not None:
+        return cached
     p = mesh.pos.astype(np.float64)
     a, b, c = p[mesh.tri_pos[:, 0]], p[mesh.tri_pos[:, 1]], p[mesh.tri_pos[:, 2]]
-    area = 0.5 * np.linalg.norm(np.cross(b - a, c - a), axis=1)
-    cdf = np.cumsum(area)
+    cdf = np.cumsum(0.5 * np.linalg.norm(np.cross(b - a, c - a), axis=1))
+    object.__setattr__(mesh, "_area_cdf", cdf)
+    return cdf
+
+
+def surface_points(mesh: Mesh, n: int, rng) -> np.ndarray:
+    """n points uniform on the surface: triangle by 3D area, then uniform barycentrics."""
+    p = mesh.pos
+    cdf = _area_cdf(mesh)
     t = np.searchsorted(cdf, rng.uniform(0.0, cdf[-1], size=n), side="right")
     t = np.minimum(t, mesh.n_tri - 1)
     r1 = np.sqrt(rng.uniform(size=n))
     r2 = rng.uniform(size=n)
     w0, w1, w2 = 1.0 - r1, r1 * (1.0 - r2), r1 * r2
-    return w0[:, None] * a[t] + w1[:, None] * b[t] + w2[:, None] * c[t]
+    a = p[mesh.tri_pos[t, 0]].astype(np.float64)
+    b = p[mesh.tri_pos[t, 1]].astype(np.float64)
+    c = p[mesh.tri_pos[t, 2]].astype(np.float64)
+    return w0[:, None] * a + w1[:, None] * b + w2[:, None] * c
 
 
 @dataclass
