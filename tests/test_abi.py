@@ -1,0 +1,201 @@
+"""The C ABI without a GPU: liblcl.so loads, exports every function include/lcl.h declares,
+lays out atlas buffers as documented, and rejects bad arguments on the host before anything
+is enqueued.  Every call here is built to fail a host-side check, so no device memory is
+ever touched (the pointers are placeholders)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lcl.h")
+
+
+@pytest.fixture(scope="module")
+def lcl():
+    from paper_2501_14807_gb300 import build, lcl as binding
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    binding.library()
+    return binding
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(lcl_[a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_path_entry_points():
+    names = declared_functions()
+    for n in ("lcl_atlas_build", "lcl_depth_render", "lcl_select_sphere", "lcl_select_lasso", "lcl_overlay",
+              "lcl_label_area"):
+        assert n in names
+
+
+def test_library_exports_every_declared_function(lcl):
+    lib = C.CDLL(lcl.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing
+    assert sorted(lcl.EXPORTS) == declared_functions()
+
+
+def test_status_strings(lcl):
+    assert lcl.lcl_status_str(0) == "LCL_OK" and lcl.lcl_status_str(4) == "LCL_ERR_UNSUPPORTED"
+    assert lcl.lcl_status_str(99) == "LCL_ERR_UNKNOWN"
+
+
+def test_atlas_layout(lcl):
+    lib = lcl.library()
+    assert lib.lcl_atlas_bytes(1000, 70, 32, 10) > 0
+    assert lib.lcl_atlas_bytes(1002, 70, 32, 10) == 0        # width not a multiple of 4
+    assert lib.lcl_atlas_bytes(64, 64, 24, 10) == 0          # tile not a power of two in [8, 128]
+    assert lib.lcl_atlas_bytes(20000, 64, 32, 10) == 0       # too wide
+    W, H, T, n = 100, 70, 32, 123
+    nb = lib.lcl_atlas_bytes(W, H, T, n)
+    a = lcl.lcl_atlas()
+    base = 1 << 40                                           # placeholder address, never dereferenced
+    assert lib.lcl_atlas_bind(C.c_void_p(base), nb, W, H, T, n, C.byref(a)) == 0
+    assert (a.tiles_x, a.tiles_y, a.supers_x, a.supers_y) == (4, 3, 1, 1)
+    planes = [a.pos_x, a.pos_y, a.pos_z, a.tri, a.cover, a.tile_box, a.super_box, a.area_w]
+    assert all(p % 256 == 0 for p in planes)
+    assert planes == sorted(planes)
+    assert a.pos_y - a.pos_x >= W * H * 4 and a.cover - a.tri >= W * H * 4
+    assert a.area_w + n * 8 <= base + nb
+    # too small, misaligned
+    assert lib.lcl_atlas_bind(C.c_void_p(base), nb - 1, W, H, T, n, C.byref(a)) == 2
+    assert lib.lcl_atlas_bind(C.c_void_p(base + 16), nb, W, H, T, n, C.byref(a)) == 1
+    # row views
+    v = lcl.lcl_atlas()
+    assert lib.lcl_atlas_rows(C.byref(a), 8, 40, C.byref(v)) == 0
+    assert v.height == 32 and v.row0 == 8 and v.tri == a.tri + 8 * W * 4 and v.cover == a.cover + 8 * W // 32 * 4
+    assert v.tile_box is None and v.super_box is None
+    assert lib.lcl_atlas_rows(C.byref(a), 3, 40, C.byref(v)) == 1   # 3 * 100 not a multiple of 32
+    assert lib.lcl_atlas_rows(C.byref(a), 0, 71, C.byref(v)) == 1
+
+
+def _bound(lcl, W=64, H=64, T=16, n=10):
+    lib = lcl.library()
+    a = lcl.lcl_atlas()
+    nb = lib.lcl_atlas_bytes(W, H, T, n)
+    assert lib.lcl_atlas_bind(C.c_void_p(1 << 40), nb, W, H, T, n, C.byref(a)) == 0
+    return lib, a
+
+
+def test_select_sphere_rejects_bad_arguments(lcl):
+    lib, a = _bound(lcl)
+    layer = C.c_void_p(1 << 41)
+    ws = C.c_void_p(1 << 42)
+    wsb = lib.lcl_select_workspace_bytes(C.byref(a), 4)
+    good = np.zeros(4, lcl.SPHERE_DTYPE)
+    P = lambda r: r.ctypes.data_as(C.c_void_p)  # noqa: E731
+
+    def call(recs, dtype=1, lay=layer, n=None, ws_bytes=wsb, wsp=ws, hits=None):
+        n = len(recs) if n is None else n
+        return lib.lcl_select_sphere(C.byref(a), lay, dtype, P(recs), n, hits, wsp, ws_bytes, None)
+
+    bad = good.copy(); bad[2]["label"] = 256
+    assert call(bad) == 1                                     # label does not fit uint8
+    bad = good.copy(); bad[1]["r2"] = -1
+    assert call(bad) == 1
+    bad = good.copy(); bad[0]["flags"] = 1
+    assert call(bad) == 1
+    bad = good.copy(); bad[3]["cx"] = 1 << 23
+    assert call(bad) == 1                                     # centre outside the accepted range
+    assert call(good, dtype=3) == 1                           # bad dtype
+    assert call(good, lay=C.c_void_p((1 << 41) + 4)) == 1     # layer not 16-byte aligned
+    assert call(good, ws_bytes=wsb - 1) == 2                  # workspace too small
+    assert call(good, wsp=C.c_void_p((1 << 42) + 8)) == 1     # workspace misaligned
+    assert call(good, n=-1) == 1
+    assert call(good, hits=C.c_void_p((1 << 43) + 4)) == 1    # hits not 8-byte aligned
+    assert "aligned" in lcl.lcl_last_error()
+
+
+def test_lasso_and_layer_ops_reject_bad_arguments(lcl):
+    lib, a = _bound(lcl)
+    cam = lcl.lcl_camera()
+    cam.width, cam.height = 64, 48
+    for i in range(16):
+        cam.m[i] = 1.0 if i % 5 == 0 else 0.0
+    poly = np.zeros((3, 2), np.float32)
+    P = lambda r: r.ctypes.data_as(C.c_void_p)  # noqa: E731
+    dptr, lay, ws = C.c_void_p(1 << 41), C.c_void_p(1 << 42), C.c_void_p(1 << 43)
+    wsb = lib.lcl_select_workspace_bytes(C.byref(a), 1)
+    args = lambda p, n, label=5, dt=1, bias=0.001, c=cam: (C.byref(a), lay, dt, C.byref(c), dptr, P(p), n, label,  # noqa
+                                                           C.c_float(bias), None, ws, wsb, None)
+    assert lib.lcl_select_lasso(*args(np.zeros((2, 2), np.float32), 2)) == 4       # too few vertices
+    assert lib.lcl_select_lasso(*args(np.zeros((65, 2), np.float32), 65)) == 4     # too many
+    nanp = poly.copy(); nanp[1, 0] = np.nan
+    assert lib.lcl_select_lasso(*args(nanp, 3)) == 1
+    assert lib.lcl_select_lasso(*args(poly, 3, label=300)) == 1
+    assert lib.lcl_select_lasso(*args(poly, 3, bias=float("inf"))) == 1
+    badcam = lcl.lcl_camera.from_buffer_copy(cam); badcam.m[3] = float("nan")
+    assert lib.lcl_select_lasso(*args(poly, 3, c=badcam)) == 1
+    badcam = lcl.lcl_camera.from_buffer_copy(cam); badcam.width = 0
+    assert lib.lcl_select_lasso(*args(poly, 3, c=badcam)) == 1
+    # overlay / area
+    assert lib.lcl_overlay(C.byref(a), lay, lay, lay, 1, 7, 0, None) == 1             # unknown op
+    assert lib.lcl_overlay(C.byref(a), lay, lay, lay, 1, 0, 8, None) == 1             # unknown flag
+    assert lib.lcl_overlay(C.byref(a), C.c_void_p((1 << 42) + 1), lay, lay, 1, 0, 0, None) == 1
+    assert lib.lcl_label_area(C.byref(a), lay, 1, 0, dptr, dptr, None) == 1          # n_labels = 0
+    assert lib.lcl_label_area(C.byref(a), lay, 1, 65537, dptr, dptr, None) == 1
+    assert lib.lcl_label_area(C.byref(a), lay, 2, 16, C.c_void_p((1 << 41) + 4), dptr, None) == 1
+
+
+def test_atlas_build_and_helpers_reject_bad_arguments(lcl):
+    lib, a = _bound(lcl, n=10)
+    m = lcl.lcl_mesh(1 << 40, 30, 1 << 41, 30, 1 << 42, 1 << 43, 11)   # triangle count differs from the atlas
+    ws = C.c_void_p(1 << 44)
+    assert lib.lcl_atlas_build(C.byref(m), C.byref(a), ws, 1 << 30, None) == 1
+    m.n_tri = 10
+    m.n_pos = 0
+    assert lib.lcl_atlas_build(C.byref(m), C.byref(a), ws, 1 << 30, None) == 1
+    m.n_pos = 30
+    assert lib.lcl_atlas_build(C.byref(m), C.byref(a), C.c_void_p((1 << 44) + 64), 1 << 30, None) == 1
+    v = lcl.lcl_atlas()
+    assert lib.lcl_atlas_rows(C.byref(a), 0, 32, C.byref(v)) == 0
+    assert lib.lcl_atlas_build(C.byref(m), C.byref(v), ws, 1 << 30, None) == 1       # a view
+    # helpers need a built atlas (scale > 0)
+    s = lcl.lcl_sphere()
+    c3 = (C.c_double * 3)(0, 0, 0)
+    assert lib.lcl_quantize_sphere(C.byref(a), c3, 1.0, 1, C.byref(s)) == 1
+    a.scale = 1000.0
+    assert lib.lcl_quantize_sphere(C.byref(a), c3, 0.5, 7, C.byref(s)) == 0
+    assert (s.cx, s.r2, s.label) == (0, 250000, 7)
+    assert lib.lcl_quantize_sphere(C.byref(a), c3, -1.0, 1, C.byref(s)) == 1
+    assert lib.lcl_quantize_sphere(C.byref(a), (C.c_double * 3)(1e5, 0, 0), 1.0, 1, C.byref(s)) == 1
+    vp = (C.c_double * 16)(*np.eye(4).ravel())
+    cam = lcl.lcl_camera()
+    assert lib.lcl_camera_from_vp(C.byref(a), vp, 0, 10, C.byref(cam)) == 1
+    assert lib.lcl_camera_from_vp(C.byref(a), vp, 10, 10, C.byref(cam)) == 0
+    assert cam.m[0] == np.float32(1e-3) and cam.m[15] == 1.0
+
+
+def test_host_helpers_match_oracle_without_gpu(lcl):
+    """The library's host-only helpers (stroke quantisation, camera composition) against the
+    oracle's independent ones, on a bbox/scale taken from the oracle."""
+    import oracle
+    import synth
+    mesh = synth.config_small().mesh
+    mn, S = oracle.quant_params(mesh.pos)
+    lib, a = _bound(lcl)
+    for i in range(3):
+        a.bbox_min[i] = float(mn[i])
+    a.scale = S
+    st = synth.sphere_strokes(mesh, 100, 9, 0.001, 0.5, 1, 255)
+    for k in range(100):
+        s = lcl.lcl_sphere()
+        c3 = (C.c_double * 3)(*st.centre[k])
+        assert lib.lcl_quantize_sphere(C.byref(a), c3, float(st.radius[k]), int(st.label[k]), C.byref(s)) == 0
+        e = oracle.sphere_stroke(mn, S, st.centre[k], st.radius[k], st.label[k])
+        assert (s.cx, s.cy, s.cz, s.r2, s.label) == (e["cx"], e["cy"], e["cz"], e["r2"], e["label"])
+    rng = np.random.default_rng(1)
+    for _ in range(10):
+        cam = synth.orbit_camera(mesh, 800, 600, rng)
+        out = lcl.lcl_camera()
+        vp = (C.c_double * 16)(*cam.vp.ravel())
+        assert lib.lcl_camera_from_vp(C.byref(a), vp, 800, 600, C.byref(out)) == 0
+        assert np.array_equal(np.array(list(out.m), np.float32), oracle.camera_mq(cam.vp, mn, S))
