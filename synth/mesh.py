@@ -1,6 +1,6 @@
 """Seeded synthetic meshes with texture coordinates.
 
-The paper edits layers of scanned cultural-heritage models (Fig. 4: a vessel of
+The paper edits layers of scanned cultural-heritage models (Fig. 5: a vessel of
 312k triangles up to a statue of 10M).  Those scans are not available, so the
 workloads use surfaces of revolution shaped like a vessel, with seeded gradient
 noise standing in for scan relief, and two kinds of texture parametrisation:

@@ -1,6 +1,6 @@
 """Seeded 3D gradient noise for the synthetic scanned-surface stand-ins.
 
-The paper's models are 3D scans (Fig. 4); their fine surface relief is stood in
+The paper's models are 3D scans (Fig. 5); their fine surface relief is stood in
 for by gradient noise in the style of Perlin's "improved noise" (quintic fade,
 gradients drawn from the 12 edge directions of a cube, a permutation table
 hashing lattice corners).  Unlike the classic fixed table, the permutation here
