@@ -186,6 +186,28 @@ size_t lcl_select_workspace_bytes(const lcl_atlas *atlas, int32_t n_strokes);
 lcl_status lcl_select_sphere(const lcl_atlas *atlas, void *layer, lcl_dtype dtype, const lcl_sphere *strokes,
                              int32_t n, uint64_t *hits_out, void *workspace, size_t ws_bytes, lcl_stream stream);
 
+#define LCL_STATIC_MAX_STROKES 4096   /* strokes per lcl_select_sphere_static call */
+#define LCL_STATIC_MAX_TILES 262144   /* atlas tiles lcl_select_sphere_static supports (16384^2 at tile 32) */
+
+/* The sphere brush without a workspace argument, for callers that cannot allocate device memory
+ * when they edit: for example a plugin running inside a host application that owns the device
+ * memory and its allocator, or an interactive editing loop that must not take allocator locks or
+ * risk an allocation failure in the middle of a stroke.  (The paper has no counterpart: it edits
+ * through the graphics pipeline, which keeps its own buffers.)
+ * Same arguments, results and errors as lcl_select_sphere, whose work it does, except that the
+ * scratch space (candidate counters and tile list, about 1 MiB) is a fixed array compiled into the
+ * library: every GPU that loads the library holds it until the process exits, and nothing is
+ * allocated or freed by this call.
+ * Limits: at most LCL_STATIC_MAX_STROKES strokes per call and atlases of at most
+ * LCL_STATIC_MAX_TILES tiles; larger requests return LCL_ERR_UNSUPPORTED.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture.
+ * All calls share the one array and it keeps the previous call's contents (each call clears the
+ * counters it needs first): calls that could overlap on the GPU -- on different streams, or from
+ * several host threads -- race and must be ordered on one stream. */
+lcl_status lcl_select_sphere_static(const lcl_atlas *atlas, void *layer, lcl_dtype dtype, const lcl_sphere *strokes,
+                                    int32_t n, uint64_t *hits_out, lcl_stream stream);
+
 /* Device workspace bytes for lcl_depth_render. */
 size_t lcl_depth_workspace_bytes(const lcl_mesh *mesh, int32_t width, int32_t height);
 

@@ -29,7 +29,7 @@ DEFAULT_BIAS = 2.0 ** -10
 
 EXPORTS = ["lcl_atlas_bytes", "lcl_atlas_bind", "lcl_atlas_rows", "lcl_atlas_workspace_bytes", "lcl_atlas_build",
            "lcl_quantize_sphere", "lcl_camera_from_vp", "lcl_select_workspace_bytes", "lcl_select_sphere",
-           "lcl_depth_workspace_bytes", "lcl_depth_render", "lcl_select_lasso", "lcl_overlay", "lcl_label_area",
+           "lcl_select_sphere_static", "lcl_depth_workspace_bytes", "lcl_depth_render", "lcl_select_lasso", "lcl_overlay", "lcl_label_area",
            "lcl_status_str", "lcl_last_error", "lcl_kernel_launches"]
 
 
@@ -92,6 +92,7 @@ def library():
         "lcl_camera_from_vp": (st, [C.POINTER(lcl_atlas), C.POINTER(D), I32, I32, C.POINTER(lcl_camera)]),
         "lcl_select_workspace_bytes": (SZ, [C.POINTER(lcl_atlas), I32]),
         "lcl_select_sphere": (st, [C.POINTER(lcl_atlas), P, C.c_int, P, I32, P, P, SZ, P]),
+        "lcl_select_sphere_static": (st, [C.POINTER(lcl_atlas), P, C.c_int, P, I32, P, P]),
         "lcl_depth_workspace_bytes": (SZ, [C.POINTER(lcl_mesh), I32, I32]),
         "lcl_depth_render": (st, [C.POINTER(lcl_mesh), C.POINTER(lcl_atlas), C.POINTER(lcl_camera), P, P, SZ, P]),
         "lcl_select_lasso": (st, [C.POINTER(lcl_atlas), P, C.c_int, C.POINTER(lcl_camera), P, P, I32, U32, F, P, P,
@@ -279,6 +280,16 @@ def lcl_select_sphere(atlas: Atlas, layer: torch.Tensor, strokes, hits_out=None,
     _check("lcl_select_sphere", library().lcl_select_sphere(
         C.byref(atlas.c), _ptr(layer), _dtype_code(layer), recs.ctypes.data_as(C.c_void_p), n, _ptr(hits_out),
         _ptr(ws), ws.numel(), _stream(stream)))
+    return hits_out
+
+
+def lcl_select_sphere_static(atlas: Atlas, layer: torch.Tensor, strokes, hits_out=None, stream=None):
+    """lcl_select_sphere with the library's built-in scratch array instead of a workspace (allocates
+    nothing; see include/lcl.h for its limits and its one-stream rule)."""
+    recs = np.ascontiguousarray(strokes, dtype=SPHERE_DTYPE)
+    _check("lcl_select_sphere_static", library().lcl_select_sphere_static(
+        C.byref(atlas.c), _ptr(layer), _dtype_code(layer), recs.ctypes.data_as(C.c_void_p), len(recs),
+        _ptr(hits_out), _stream(stream)))
     return hits_out
 
 
