@@ -331,14 +331,7 @@ def run_ours(args):
     barrier()
     e2e_ms = f0.elapsed_time(f1)
 
-    # max over ranks
-    tt = torch.tensor([total_ms, e2e_ms, sph_ms], dtype=torch.float64, device=dev)
-    tx = torch.tensor([texels], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tx, op=dist.ReduceOp.SUM)
-    total_ms, e2e_ms, sph_ms = tt.tolist()
-    all_texels = tx.item()
+    (total_ms, e2e_ms, sph_ms), all_texels = combine_ranks([total_ms, e2e_ms, sph_ms], texels, world, dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -369,6 +362,19 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def combine_ranks(times_ms, texels, world, device):
+    """Whole-job figures over ranks: the maximum of each time and the sum of the texels (each rank
+    edits its own model, so the texels add up; the slowest rank sets the time)."""
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor(list(times_ms), dtype=torch.float64, device=device)
+    tx = torch.tensor([float(texels)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tx, op=dist.ReduceOp.SUM)
+    return tt.tolist(), tx.item()
 
 
 def profile_traffic(w):

@@ -1,7 +1,7 @@
 // noalloc.cu -- lcl_select_sphere_static: the sphere brush for callers that cannot allocate
 // device memory, with its scratch space in a fixed array compiled into this library.
 //
-// The scratch (per-stroke candidate counters and the candidate-tile list) lives in the
+// The scratch (per-stroke candidate counters and the candidate-tile lists) lives in the
 // file-scope device array below: every GPU that loads the library holds it until the process
 // exits.  Host code cannot hand the array's name to a kernel (on the host it is only a
 // stand-in for the device symbol), so the device address is looked up once per device with
@@ -17,8 +17,10 @@ namespace {
 
 constexpr int32_t kStaticMaxStrokes = LCL_STATIC_MAX_STROKES;
 constexpr int64_t kStaticMaxTiles = LCL_STATIC_MAX_TILES;
+// Candidate counters (one per stroke) and two candidate-tile lists, laid out as the workspace of
+// lcl_select_sphere for kStaticMaxStrokes strokes on an atlas of kStaticMaxTiles tiles.
 constexpr size_t kStaticScratchBytes =
-    ((size_t(kStaticMaxStrokes + 1) * 4 + 255) & ~size_t(255)) + size_t(kStaticMaxTiles) * 4;
+    ((size_t(kStaticMaxStrokes + 1) * 4 + 255) & ~size_t(255)) + 2 * size_t(kStaticMaxTiles) * 4;
 
 static __device__ __align__(256) unsigned char g_sphere_scratch[kStaticScratchBytes];
 
