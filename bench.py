@@ -336,6 +336,7 @@ def run_ours(args):
         if world > 1:
             dist.destroy_process_group()
         return
+    serving = serving_summary(args.serving_models, 20000.0, 1.0) if (world == 1 and args.serving_models > 0) else None
     peak, peak_kind = peaks()
     sph_bytes = sph_hits * (12 + w.dtype_bytes)
     achieved = sph_bytes / (sph_ms / args.steps / 1e3) / 1e9
@@ -356,6 +357,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clk,
+        "serving": serving,
         "breakdown": {"sphere_ms_per_step": sph_ms / args.steps, "sphere_hit_texels": sph_hits,
                       "lasso_hit_texels": las_hits, "texels_per_step": texels},
     }
@@ -375,6 +377,177 @@ def combine_ranks(times_ms, texels, world, device):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         dist.all_reduce(tx, op=dist.ReduceOp.SUM)
     return tt.tolist(), tx.item()
+
+
+def run_batch(args):
+    """Batching workload: many models of uneven size, 64 queued sphere/lasso strokes each, edited by
+    one batched launch (descriptor upload + cull + persistent apply), against the same strokes as
+    per-model, per-stroke calls.  Both arms do identical work (bit-identical results, checked)."""
+    import torch
+
+    import synth
+    from paper_2501_14807_gb300 import lcl
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    bms = synth.config_batch(args.models, depth_side=1024)
+    models, queues, layers, inits = [], [], [], []
+    for bm in bms:
+        mesh = lcl.Mesh.from_host(bm.mesh, dev)
+        a = lcl.Atlas(bm.side, bm.side, 32, bm.mesh.n_tri, dev)
+        lcl.lcl_atlas_build(mesh, a)
+        cams = [lcl.lcl_camera_from_vp(a, c.vp, c.width, c.height) for c in bm.cams]
+        depths = []
+        for c in cams:
+            d = torch.empty((c.height, c.width), dtype=torch.float32, device=dev)
+            lcl.lcl_depth_render(mesh, a, c, d)
+            depths.append(d)
+        q = []
+        for e in bm.order:
+            if e >= 0:
+                q.append(("sphere", lcl.lcl_quantize_sphere(a, bm.strokes.centre[e], bm.strokes.radius[e],
+                                                            bm.strokes.label[e])))
+            else:
+                L = bm.lassos[-1 - e]
+                q.append(("lasso", (cams[L.cam], depths[L.cam], L.poly, L.label, lcl.DEFAULT_BIAS)))
+        layer = torch.zeros((bm.side, bm.side), dtype=torch.uint8, device=dev)
+        models.append(a)
+        queues.append(q)
+        layers.append(layer)
+    hit_bufs = [torch.zeros(len(q), dtype=torch.int64, device=dev) for q in queues]
+    ws_sel = torch.empty(max(lcl.lcl_select_workspace_bytes(a, 1) for a in models), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def sequential():
+        for a, q, layer, hb in zip(models, queues, layers, hit_bufs):
+            for k, (kind, payload) in enumerate(q):
+                if kind == "sphere":
+                    lcl.lcl_select_sphere(a, layer, np.array([payload], lcl.SPHERE_DTYPE), hb[k:k + 1], ws_sel, stream)
+                else:
+                    cam, depth, poly, label, bias = payload
+                    lcl.lcl_select_lasso(a, layer, cam, depth, poly, label, bias, hb[k:k + 1], ws_sel, stream)
+
+    batch = lcl.Batch(list(zip(models, layers)), queues)
+
+    def batched():
+        lcl.lcl_batch_edit(batch, stream)
+
+    def timed(fn, steps):
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+            torch.cuda.synchronize(dev)   # the staging of a batch is reused by the next one
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps
+
+    for _ in range(args.warmup):
+        sequential()
+    torch.cuda.synchronize(dev)
+    ref = [l.clone() for l in layers]
+    hits = int(sum(int(h.sum().item()) for h in hit_bufs))
+    seq_ms = timed(sequential, args.steps)
+    for l in layers:
+        l.zero_()
+    for _ in range(args.warmup):
+        batched()
+        torch.cuda.synchronize(dev)
+    clocks = Clocks(0)
+    clocks.start()
+    bat_ms = timed(batched, args.steps)
+    clk = clocks.stop()
+    same = all(torch.equal(r, l) for r, l in zip(ref, layers))
+    n_strokes = sum(len(q) for q in queues)
+    line = {"metric": METRIC, "value": hits / (bat_ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": bat_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"batching: {len(models)} models ({sum(b.mesh.n_tri for b in bms)} triangles, "
+                                   f"atlases 512^2-4096^2 u8), {n_strokes} queued strokes (48 sphere + 16 lasso "
+                                   f"per model)", "mode": "batched launch vs per-model per-stroke calls"},
+            "batched": {"ms": bat_ms, "gtexels_s": hits / (bat_ms / 1e3) / 1e9},
+            "per_stroke_calls": {"ms": seq_ms, "gtexels_s": hits / (seq_ms / 1e3) / 1e9,
+                                 "launches": lcl.lcl_kernel_launches()},
+            "speedup": seq_ms / bat_ms, "identical_results": bool(same), "hit_texels": hits, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def serving_setup(n_models, seed=5):
+    """Models of the serving workload (drawn like the batching workload) and payload samplers."""
+    import synth
+    from paper_2501_14807_gb300 import serve
+    bms = synth.config_batch(n_models, seed=seed, depth_side=1024)
+    models = [serve.ServedModel(b.mesh, b.side, b.cams, n_layers=2) for b in bms]
+    probe_bytes = [b.side * b.side * 18 + 8 * 1024 * 1024 for b in bms]
+    budget = int(sum(sorted(probe_bytes)[: len(bms) // 2]))
+
+    def sphere_of(m, rng):
+        st = bms[m].strokes
+        k = int(rng.integers(0, len(st.radius)))
+        return (st.centre[k], float(st.radius[k]), int(rng.integers(1, 256)))
+
+    def lasso_of(m, rng):
+        L = bms[m].lassos[int(rng.integers(0, len(bms[m].lassos)))]
+        return (L.cam, L.poly, int(rng.integers(1, 256)))
+
+    return models, budget, sphere_of, lasso_of
+
+
+def serving_summary(n_models, rate, duration):
+    """A short live serving run (continuous batching only) for the headline line's latency figures."""
+    import torch
+
+    from paper_2501_14807_gb300 import serve
+    models, budget, sphere_of, lasso_of = serving_setup(n_models)
+    srv = serve.Server(models, hbm_budget_bytes=budget)
+    srv.run(serve.poisson_requests(len(models), rate, 0.2, 6, sphere_of=sphere_of, lasso_of=lasso_of))
+    reqs = serve.poisson_requests(len(models), rate, duration, 5, sphere_of=sphere_of, lasso_of=lasso_of)
+    srv.run(reqs)
+    st = serve.latency_stats(reqs)
+    st.update({"models": len(models), "offered_rps": rate, "seconds": duration, "spills": srv.spills,
+               "mix": "70% sphere / 20% lasso / 10% overlay+area, Zipf(1.1) models, half of them resident"})
+    del srv
+    torch.cuda.empty_cache()
+    return st
+
+
+def run_serve(args):
+    """Serving workload: resident + spillover models (as in the batching workload), 2 layers each,
+    an HBM budget that holds about half of them, open-loop Poisson arrivals (70% sphere strokes, 20%
+    lassos, 10% overlay + area queries, models by a Zipf(1.1) law), served with continuous batching;
+    the same trace served one request per call is the baseline."""
+    import torch
+
+    from paper_2501_14807_gb300 import serve
+
+    torch.cuda.set_device(0)
+    models, budget, sphere_of, lasso_of = serving_setup(args.models)
+    out = {}
+    for mode in ("batched", "per_request"):
+        srv = serve.Server(models, hbm_budget_bytes=budget)
+        reqs = serve.poisson_requests(len(models), args.rate, args.duration, 5, sphere_of=sphere_of,
+                                      lasso_of=lasso_of)
+        warm = serve.poisson_requests(len(models), args.rate, 0.2, 6, sphere_of=sphere_of, lasso_of=lasso_of)
+        (srv.run if mode == "batched" else srv.run_per_request)(warm)
+        clocks = Clocks(0)
+        clocks.start()
+        (srv.run if mode == "batched" else srv.run_per_request)(reqs)
+        clk = clocks.stop()
+        st = serve.latency_stats(reqs)
+        st.update({"epochs": srv.epochs, "spills": srv.spills, "admissions": srv.admissions, "clocks": clk})
+        out[mode] = st
+        del srv
+        torch.cuda.empty_cache()
+    b = out["batched"]
+    line = {"metric": METRIC, "value": b["throughput_rps"], "unit": "requests/s", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": 1e3 * args.duration, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"serving: {len(models)} models (half resident under a {budget / 2**30:.2f} GiB "
+                                   f"budget), Poisson {args.rate:.0f} req/s for {args.duration:.1f} s, mix 70% sphere / "
+                                   f"20% lasso / 10% overlay+area, Zipf(1.1) model choice"},
+            "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"], "served": out}
+    print(json.dumps(line), flush=True)
 
 
 def profile_traffic(w):
@@ -400,19 +573,28 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="roofline", choices=["roofline", "large", "mid", "small"])
+    ap.add_argument("--config", default="roofline", choices=["roofline", "large", "mid", "small", "batch", "serve"])
+    ap.add_argument("--rate", type=float, default=20000.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--duration", type=float, default=5.0, help="serving: trace length (s)")
+    ap.add_argument("--models", type=int, default=256, help="models in the batching / serving workload")
+    ap.add_argument("--serving-models", type=int, default=32,
+                    help="models of the short serving run reported in the headline line (0: skip)")
     ap.add_argument("--strokes", type=int, default=None)
     ap.add_argument("--lassos", type=int, default=None)
     ap.add_argument("--cpu-rows", type=int, default=64, help="rows of the texture the CPU oracle baseline covers")
     args = ap.parse_args()
-    defaults = {"roofline": (1000, 20), "mid": (1000, 20), "large": (10000, 200), "small": (200, 0)}
+    defaults = {"roofline": (1000, 20), "mid": (1000, 20), "large": (10000, 200), "small": (200, 0), "batch": (0, 0), "serve": (0, 0)}
     if args.strokes is None:
         args.strokes = defaults[args.config][0]
     if args.lassos is None:
         args.lassos = defaults[args.config][1]
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
+    if args.config == "batch":
+        run_batch(args)
+    elif args.config == "serve":
+        run_serve(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

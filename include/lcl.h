@@ -164,6 +164,11 @@ lcl_status lcl_atlas_build(const lcl_mesh *mesh, lcl_atlas *atlas, void *workspa
 lcl_status lcl_quantize_sphere(const lcl_atlas *atlas, const double centre[3], double radius,
                                uint32_t label, lcl_sphere *out);
 
+/* lcl_quantize_sphere for n strokes at once (host arrays: centres n x 3, radii n, labels n; out n).
+ * Stops at the first invalid stroke and returns its error. */
+lcl_status lcl_quantize_spheres(const lcl_atlas *atlas, int32_t n, const double *centres, const double *radii,
+                                const uint32_t *labels, lcl_sphere *out);
+
 /* Camera from a world view-projection `vp` (row-major, host): m = vp * Dequantise, with
  * Dequantise(q) = bbox_min + q / scale, composed in double and rounded to float. */
 lcl_status lcl_camera_from_vp(const lcl_atlas *atlas, const double vp[16], int32_t width, int32_t height,
@@ -233,6 +238,66 @@ lcl_status lcl_depth_render(const lcl_mesh *mesh, const lcl_atlas *atlas, const 
 lcl_status lcl_select_lasso(const lcl_atlas *atlas, void *layer, lcl_dtype dtype, const lcl_camera *camera,
                             const float *depth, const float *poly_xy, int32_t n_vertices, uint32_t label,
                             float bias, uint64_t *hits_out, void *workspace, size_t ws_bytes, lcl_stream stream);
+
+/* ---- batched edits -------------------------------------------------------- */
+
+#define LCL_BATCH_MAX_STROKES 64  /* queued strokes per model per batch */
+enum { LCL_STROKE_SPHERE = 0, LCL_STROKE_LASSO = 1 };
+
+/* One model of a batch: its built atlas (host struct), the layer its strokes edit, and its queue:
+ * strokes [first_stroke, first_stroke + n_strokes) of the batch's stroke array, in queue order. */
+typedef struct {
+    const lcl_atlas *atlas;
+    void *layer; /* device, 16-byte aligned */
+    lcl_dtype dtype;
+    int32_t first_stroke, n_strokes;
+    int32_t _pad;
+} lcl_batch_model;
+
+/* One queued stroke: a sphere (kind LCL_STROKE_SPHERE, `sphere`) or a lasso (kind LCL_STROKE_LASSO,
+ * `lasso` indexes the batch's lasso array). */
+typedef struct {
+    int32_t kind, lasso;
+    lcl_sphere sphere;
+} lcl_batch_stroke;
+
+/* One lasso of a batch: camera, its depth map (device), polygon (host, n_vertices x 2 floats),
+ * label and bias, with the meaning of lcl_select_lasso. */
+typedef struct {
+    lcl_camera camera;
+    const float *depth;
+    const float *poly_xy;
+    int32_t n_vertices;
+    uint32_t label;
+    float bias;
+    int32_t _pad;
+} lcl_batch_lasso;
+
+/* Device workspace and host staging bytes for a batch of these models and counts. */
+size_t lcl_batch_workspace_bytes(const lcl_batch_model *models, int32_t n_models, int32_t n_strokes,
+                                 int32_t n_lassos);
+size_t lcl_batch_staging_bytes(const lcl_batch_model *models, int32_t n_models, int32_t n_strokes,
+                               int32_t n_lassos);
+
+/* Edits many models at once: every model's queued strokes are applied to its layer in queue order,
+ * with results identical to calling lcl_select_sphere / lcl_select_lasso once per stroke in that
+ * order (Section 4.3.1 applied per stroke; batching is a serving-side schedule the paper does not
+ * discuss).  One cull launch gives every touched tile of every model a mask of the strokes that can
+ * reach it; one persistent apply launch loads each such tile's positions once and runs its masked
+ * strokes in order.  Models must be distinct layers (two models writing one layer race).
+ * host_staging (lcl_batch_staging_bytes, host memory) receives an image of the descriptors that is
+ * copied to the workspace on `stream`; with pinned memory the copy is asynchronous and the staging
+ * must stay untouched until the stream has passed it.  Depth maps must be rendered before the call.
+ * Errors: as lcl_select_sphere / lcl_select_lasso; LCL_ERR_UNSUPPORTED for more than
+ * LCL_BATCH_MAX_STROKES strokes per model. */
+lcl_status lcl_batch_edit(const lcl_batch_model *models, int32_t n_models, const lcl_batch_stroke *strokes,
+                          int32_t n_strokes, const lcl_batch_lasso *lassos, int32_t n_lassos, void *workspace,
+                          size_t ws_bytes, void *host_staging, size_t staging_bytes, lcl_stream stream);
+
+/* Launches the kernels of the last lcl_batch_edit on this workspace and staging again, reading the
+ * descriptors already on the device (no host-to-device copy, so it can be captured in a CUDA graph
+ * and replayed; re-running a batch repeats its strokes). */
+lcl_status lcl_batch_launch(void *workspace, const void *host_staging, lcl_stream stream);
 
 /* ---- layer operations --------------------------------------------------- */
 

@@ -155,6 +155,23 @@ def select_sphere(atlas: Atlas, layer: np.ndarray, strokes: np.ndarray):
     return hits
 
 
+def select_sphere_2d(atlas: Atlas, layer: np.ndarray, strokes: np.ndarray):
+    """Like select_sphere, on the whole texture, with texture padding for strokes whose flags ask
+    for it (radius = flags & 15, thickness = (flags >> 4) & 15).  Returns (hits, padded)."""
+    assert atlas.y0 == 0 and atlas.y1 == atlas.H and layer.shape == atlas.tri.shape
+    strokes = np.ascontiguousarray(strokes, dtype=SPHERE_DTYPE)
+    hits = np.zeros(len(strokes), np.uint64)
+    padded = np.zeros(len(strokes), np.uint64)
+    _chk(lib().orc_select_sphere_2d(C.c_int32(atlas.W), C.c_int32(atlas.H), _p(atlas.px), _p(atlas.py), _p(atlas.pz),
+                                    _p(atlas.tri), _p(layer), C.c_int(layer.itemsize), _p(strokes),
+                                    C.c_int32(len(strokes)), _p(hits), _p(padded)), "select_sphere_2d")
+    return hits, padded
+
+
+def pad_flags(radius, thickness):
+    return int(radius) | (int(thickness) << 4)
+
+
 def camera_mq(vp, mn, S):
     vp = np.ascontiguousarray(vp, dtype=np.float64).reshape(16)
     m = np.empty(16, np.float32)

@@ -366,7 +366,7 @@ int orc_select_sphere(int64_t n_texels, const int32_t *px, const int32_t *py, co
     if (dtype_bytes != 1 && dtype_bytes != 2) return ORC_EINVAL;
     for (int32_t k = 0; k < n; ++k) {
         const orc_sphere *s = &strokes[k];
-        if (s->r2 < 0 || s->label >= (1u << (8 * dtype_bytes))) return ORC_EINVAL;
+        if (s->r2 < 0 || s->label >= (1u << (8 * dtype_bytes)) || s->flags != 0) return ORC_EINVAL;
         uint64_t h = 0;
         for (int64_t l = 0; l < n_texels; ++l) {
             if (tri[l] == ORC_NONE) continue;
@@ -378,6 +378,66 @@ int orc_select_sphere(int64_t n_texels, const int32_t *px, const int32_t *py, co
             }
         }
         if (hits) hits[k] = h;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Texture Padding Algorithm (Section 4.3.2, Fig. 4): after an edit, texels of  */
+/* the outline mask that lie within the kernel radius of the edited area get   */
+/* the edited value, so that sampling across island borders finds it.         */
+/* READING: the outline mask holds the uncovered texels within `thickness` of  */
+/* a covered texel; distances are measured with the square kernel (|dx| <= k   */
+/* and |dy| <= k); the edited area is the set of texels the stroke selected.   */
+/* Sphere strokes ask for padding in their flags: radius = flags & 15,         */
+/* thickness = (flags >> 4) & 15, both at most 8, other bits zero.            */
+/* ------------------------------------------------------------------------- */
+static int sphere_hits_texel(const int32_t *px, const int32_t *py, const int32_t *pz, const uint32_t *tri,
+                             int64_t l, const orc_sphere *s)
+{
+    if (tri[l] == ORC_NONE) return 0;
+    int64_t dx = (int64_t)px[l] - s->cx, dy = (int64_t)py[l] - s->cy, dz = (int64_t)pz[l] - s->cz;
+    return dx * dx + dy * dy + dz * dz <= s->r2;
+}
+
+int orc_select_sphere_2d(int32_t W, int32_t H, const int32_t *px, const int32_t *py, const int32_t *pz,
+                         const uint32_t *tri, void *layer, int dtype_bytes, const orc_sphere *strokes, int32_t n,
+                         uint64_t *hits, uint64_t *padded)
+{
+    if (dtype_bytes != 1 && dtype_bytes != 2) return ORC_EINVAL;
+    for (int32_t k = 0; k < n; ++k) {
+        const orc_sphere *s = &strokes[k];
+        uint32_t rad = s->flags & 15u, thick = (s->flags >> 4) & 15u;
+        if ((s->flags & ~0xFFu) || rad > 8 || thick > 8) return ORC_EINVAL;
+        orc_sphere plain = *s;
+        plain.flags = 0;
+        int rc = orc_select_sphere((int64_t)W * H, px, py, pz, tri, layer, dtype_bytes, &plain, 1, hits ? hits + k : NULL);
+        if (rc) return rc;
+        uint64_t np = 0;
+        if (rad > 0) {
+            int32_t reach = (int32_t)(rad > thick ? rad : thick);
+            for (int32_t y = 0; y < H; ++y)
+                for (int32_t x = 0; x < W; ++x) {
+                    int64_t l = (int64_t)y * W + x;
+                    if (tri[l] != ORC_NONE) continue;
+                    int outline = 0, near = 0;
+                    for (int32_t dy = -reach; dy <= reach; ++dy)
+                        for (int32_t dx = -reach; dx <= reach; ++dx) {
+                            int32_t yy = y + dy, xx = x + dx;
+                            if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                            int64_t m = (int64_t)yy * W + xx;
+                            if (tri[m] == ORC_NONE) continue;
+                            int32_t ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy;
+                            if (ax <= (int32_t)thick && ay <= (int32_t)thick) outline = 1;
+                            if (ax <= (int32_t)rad && ay <= (int32_t)rad && sphere_hits_texel(px, py, pz, tri, m, s)) near = 1;
+                        }
+                    if (outline && near) {
+                        store_label(layer, dtype_bytes, l, s->label);
+                        ++np;
+                    }
+                }
+        }
+        if (padded) padded[k] = np;
     }
     return ORC_OK;
 }

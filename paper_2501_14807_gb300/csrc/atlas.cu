@@ -299,12 +299,22 @@ __global__ void k_raster_big(const uint2 *__restrict__ big, const AtlasHdr *__re
 
 // Exact rounded barycentric interpolation of one axis, relative to corner 0:
 // q = q0 + floor((2 (w1 (q1-q0) + w2 (q2-q0)) + A) / (2A)), which equals
-// floor((2 sum_k w_k q_k + A) / (2A)) because q0 is an integer.
-__device__ __forceinline__ int32_t interp_axis(int64_t w1, int64_t w2, int64_t A, int32_t q0, int32_t q1, int32_t q2) {
-    int64_t d1 = (int64_t)q1 - q0, d2 = (int64_t)q2 - q0;
+// floor((2 sum_k w_k q_k + A) / (2A)) because q0 is an integer.  The quotient is estimated in
+// FP32 with `rden` ~ 1/(2A) (error well under 2 units) and then made exact with integer
+// remainder corrections.
+__device__ __forceinline__ int32_t interp_axis(int64_t w1, int64_t w2, int64_t A, float rden, int32_t q0, int32_t q1,
+                                               int32_t q2) {
+    const int64_t d1 = (int64_t)q1 - q0, d2 = (int64_t)q2 - q0;
     if (A < (int64_t(1) << 40)) {
-        int64_t num = 2 * (w1 * d1 + w2 * d2) + A;  // |num| < 2^63 since w <= A < 2^40, |d| < 2^21
-        return q0 + (int32_t)floor_div_est(num, 2 * A);
+        const int64_t num = 2 * (w1 * d1 + w2 * d2) + A;  // |num| < 2^63 since w <= A < 2^40, |d| < 2^21
+        const int64_t den = 2 * A;
+        int64_t est = (int64_t)floorf(__fmul_rn((float)num, rden));
+        int64_t r = num - est * den;
+#pragma unroll 1
+        for (int k = 0; k < 4 && r < 0; ++k) { est -= 1; r += den; }
+#pragma unroll 1
+        for (int k = 0; k < 4 && r >= den; ++k) { est += 1; r -= den; }
+        return q0 + (int32_t)est;
     }
     __int128 num = 2 * ((__int128)w1 * d1 + (__int128)w2 * d2) + A, den = 2 * (__int128)A;
     double dn = (double)(int64_t)(num >> 64) * 18446744073709551616.0 + (double)(uint64_t)num;
@@ -349,9 +359,10 @@ __global__ void __launch_bounds__(kThreads) k_resolve(const TriSetup *__restrict
                 int64_t A = edge_fn(s.x[0], s.y[0], s.x[1], s.y[1], s.x[2], s.y[2]);
                 int64_t w1 = edge_fn(s.x[2], s.y[2], s.x[0], s.y[0], cx, cy);
                 int64_t w2 = edge_fn(s.x[0], s.y[0], s.x[1], s.y[1], cx, cy);
-                ox[k] = interp_axis(w1, w2, A, s.qx[0], s.qx[1], s.qx[2]);
-                oy[k] = interp_axis(w1, w2, A, s.qy[0], s.qy[1], s.qy[2]);
-                oz[k] = interp_axis(w1, w2, A, s.qz[0], s.qz[1], s.qz[2]);
+                const float rden = __frcp_rn((float)(2 * A));
+                ox[k] = interp_axis(w1, w2, A, rden, s.qx[0], s.qx[1], s.qx[2]);
+                oy[k] = interp_axis(w1, w2, A, rden, s.qy[0], s.qy[1], s.qy[2]);
+                oz[k] = interp_axis(w1, w2, A, rden, s.qz[0], s.qz[1], s.qz[2]);
                 nib |= 1u << k;
                 mn[0] = min(mn[0], ox[k]); mx[0] = max(mx[0], ox[k]);
                 mn[1] = min(mn[1], oy[k]); mx[1] = max(mx[1], oy[k]);

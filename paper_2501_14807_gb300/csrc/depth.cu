@@ -3,10 +3,13 @@
 // changes; Fig. 3a).  The paper draws it with the graphics pipeline; here it is a CUDA
 // rasteriser with the same exact integer rules as the atlas build:
 //   k_clear       depth := +inf
-//   k_raster      one thread per triangle: quantise and project the corners (FP32, fixed
-//                 order, no FMA), snap to 1/256 px, and for small triangles test every pixel
-//                 centre of the bounding box; depth = barycentric interpolation of NDC z in
-//                 double, rounded to float; atomicMin on the float bits (all values >= 0)
+//   k_vertex      one thread per vertex: quantise and project it (FP32, fixed order, no FMA),
+//                 snap to 1/256 px, flag it if it drops its triangles (w <= 0, NDC depth
+//                 outside [0, 1], off the guard band); 16 bytes per vertex
+//   k_raster      one thread per triangle: gather its three vertex records, and for small
+//                 triangles test every pixel centre of the bounding box; depth = barycentric
+//                 interpolation of NDC z in double, rounded to float; atomicMin on the float
+//                 bits (all values >= 0)
 //   k_raster_big  big triangles split into 16 x 16-pixel blocks, one CTA per block
 #include <algorithm>
 
@@ -21,6 +24,14 @@ struct DepthHdr {
     unsigned long long n_big;
 };
 
+// Projected vertex: snapped screen position (1/256 px), NDC depth; X == INT32_MIN marks a vertex
+// whose triangles are dropped.
+struct __align__(16) PVert {
+    int32_t X, Y;
+    float z;
+    int32_t pad;
+};
+
 struct DepthArgs {
     const float *pos;
     const uint32_t *tri_pos;
@@ -31,6 +42,7 @@ struct DepthArgs {
     int32_t w, h;
     float fw, fh;
     uint32_t *depth;  // float bits
+    const PVert *pv;
     DepthHdr *hdr;
     uint2 *big;
     int64_t big_cap;
@@ -42,26 +54,49 @@ struct DTri {
     int64_t A;
 };
 
-// Projects triangle t; false if it is dropped (bad index, w <= 0, z outside [0,1], off the
-// guard band, or zero screen area).  Corners are counter-clockwise on return.
+struct Mat16 {
+    float v[16];
+};
+
+__global__ void k_vertex(const float *__restrict__ pos, int64_t n_pos, const Mat16 mat, float mn0, float mn1,
+                         float mn2, double scale, float fw, float fh, PVert *__restrict__ out) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n_pos) return;
+    const float *m = mat.v;
+    PVert r;
+    r.X = INT32_MIN;
+    r.Y = 0;
+    r.z = 0.0f;
+    r.pad = 0;
+    const float qx = (float)quantize_coord(pos[3 * v + 0], mn0, scale);
+    const float qy = (float)quantize_coord(pos[3 * v + 1], mn1, scale);
+    const float qz = (float)quantize_coord(pos[3 * v + 2], mn2, scale);
+    const float cw = clip_row(m + 12, qx, qy, qz);
+    if (cw > 0.0f) {
+        const float zn = __fdiv_rn(clip_row(m + 8, qx, qy, qz), cw);
+        const float xs = __fmul_rn(screen_of(__fdiv_rn(clip_row(m, qx, qy, qz), cw), fw), 256.0f);
+        const float ys = __fmul_rn(screen_of(__fdiv_rn(clip_row(m + 4, qx, qy, qz), cw), fh), 256.0f);
+        if (zn >= 0.0f && zn <= 1.0f && fabsf(xs) <= (float)kGuardSub && fabsf(ys) <= (float)kGuardSub) {
+            r.X = (int32_t)__float2ll_rn(xs);
+            r.Y = (int32_t)__float2ll_rn(ys);
+            r.z = zn;
+        }
+    }
+    out[v] = r;
+}
+
+// Triangle t from its projected corners; false if it is dropped (bad index, a dropped corner, or
+// zero screen area).  Corners are counter-clockwise on return.
 __device__ bool depth_setup(const DepthArgs &a, int64_t t, DTri &d) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const uint32_t ip = a.tri_pos[3 * t + k];
         if (ip >= (uint64_t)a.n_pos) return false;
-        const float qx = (float)quantize_coord(a.pos[3 * (int64_t)ip + 0], a.mn[0], a.scale);
-        const float qy = (float)quantize_coord(a.pos[3 * (int64_t)ip + 1], a.mn[1], a.scale);
-        const float qz = (float)quantize_coord(a.pos[3 * (int64_t)ip + 2], a.mn[2], a.scale);
-        const float cw = clip_row(a.m + 12, qx, qy, qz);
-        if (!(cw > 0.0f)) return false;
-        const float zn = __fdiv_rn(clip_row(a.m + 8, qx, qy, qz), cw);
-        if (!(zn >= 0.0f && zn <= 1.0f)) return false;
-        const float xs = __fmul_rn(screen_of(__fdiv_rn(clip_row(a.m, qx, qy, qz), cw), a.fw), 256.0f);
-        const float ys = __fmul_rn(screen_of(__fdiv_rn(clip_row(a.m + 4, qx, qy, qz), cw), a.fh), 256.0f);
-        if (!(fabsf(xs) <= (float)kGuardSub && fabsf(ys) <= (float)kGuardSub)) return false;
-        d.X[k] = __float2ll_rn(xs);
-        d.Y[k] = __float2ll_rn(ys);
-        d.Z[k] = zn;
+        const PVert p = a.pv[ip];
+        if (p.X == INT32_MIN) return false;
+        d.X[k] = p.X;
+        d.Y[k] = p.Y;
+        d.Z[k] = p.z;
     }
     d.A = edge_fn(d.X[0], d.Y[0], d.X[1], d.Y[1], d.X[2], d.Y[2]);
     if (d.A == 0) return false;
@@ -161,13 +196,14 @@ __global__ void __launch_bounds__(kThreads) k_raster_big(const __grid_constant__
 
 }  // namespace
 
-size_t depth_ws_bytes(int64_t n_tri, int32_t w, int32_t h) {
-    return align256(sizeof(DepthHdr)) + align256(big_capacity(n_tri, w, h) * sizeof(uint2));
+size_t depth_ws_bytes(int64_t n_pos, int64_t n_tri, int32_t w, int32_t h) {
+    return align256(sizeof(DepthHdr)) + align256(big_capacity(n_tri, w, h) * sizeof(uint2)) +
+           align256((size_t)n_pos * sizeof(PVert));
 }
 
 lcl_status depth_render_impl(const lcl_mesh *mesh, const lcl_atlas *atlas, const lcl_camera *cam, float *depth,
                              void *ws, size_t ws_bytes, cudaStream_t st) {
-    if (ws_bytes < depth_ws_bytes(mesh->n_tri, cam->width, cam->height))
+    if (ws_bytes < depth_ws_bytes(mesh->n_pos, mesh->n_tri, cam->width, cam->height))
         return fail(LCL_ERR_OUT_OF_MEMORY, "depth workspace smaller than lcl_depth_workspace_bytes");
     DepthArgs a;
     a.pos = mesh->pos;
@@ -185,15 +221,22 @@ lcl_status depth_render_impl(const lcl_mesh *mesh, const lcl_atlas *atlas, const
     a.hdr = reinterpret_cast<DepthHdr *>(ws);
     a.big = reinterpret_cast<uint2 *>(static_cast<char *>(ws) + align256(sizeof(DepthHdr)));
     a.big_cap = (int64_t)big_capacity(mesh->n_tri, cam->width, cam->height);
+    PVert *pv = reinterpret_cast<PVert *>(static_cast<char *>(ws) + align256(sizeof(DepthHdr)) +
+                                          align256((size_t)a.big_cap * sizeof(uint2)));
+    a.pv = pv;
     const int64_t n_px = (int64_t)cam->width * cam->height;
     const int sms = sm_count();
     k_clear<<<sms * 4, kThreads, 0, st>>>(a.depth, n_px);
     k_hdr_reset<<<1, 1, 0, st>>>(a.hdr);
     count_launches(2);
     if (mesh->n_tri > 0) {
+        Mat16 mat;
+        for (int i = 0; i < 16; ++i) mat.v[i] = cam->m[i];
+        k_vertex<<<(unsigned)((mesh->n_pos + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+            mesh->pos, mesh->n_pos, mat, a.mn[0], a.mn[1], a.mn[2], a.scale, a.fw, a.fh, pv);
         k_raster<<<(unsigned)((mesh->n_tri + 127) / 128), 128, 0, st>>>(a);
         k_raster_big<<<sms * 8, kThreads, 0, st>>>(a);
-        count_launches(2);
+        count_launches(3);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "lcl_depth_render launch");

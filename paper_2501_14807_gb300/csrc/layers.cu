@@ -130,28 +130,36 @@ __global__ void __launch_bounds__(kThreads) k_area(const L *__restrict__ layer, 
     };
     const int64_t n_chunks = n_texels / 16;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n_chunks; c += stride) {
+    // one chunk = 16 texels: four 16-byte loads of triangle ids and one or two of labels; the
+    // next chunk's loads are issued before the current chunk is visited
+    constexpr int LW = sizeof(L) == 1 ? 1 : 2;
+    uint4 T4[4], V[LW];
+    auto load = [&](int64_t c) {
         const uint4 *tp = reinterpret_cast<const uint4 *>(tri + 16 * c);
-        uint4 T4[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) T4[k] = __ldcs(tp + k);
-        uint32_t labs[16];
-        if (sizeof(L) == 1) {
-            const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(layer + 16 * c));
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int k = 0; k < 16; ++k) labs[k] = (w[k / 4] >> (8 * (k % 4))) & 0xFFu;
-        } else {
-            const uint4 v0 = __ldcs(reinterpret_cast<const uint4 *>(layer + 16 * c));
-            const uint4 v1 = __ldcs(reinterpret_cast<const uint4 *>(layer + 16 * c) + 1);
-            const uint32_t w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-#pragma unroll
-            for (int k = 0; k < 16; ++k) labs[k] = (w[k / 2] >> (16 * (k % 2))) & 0xFFFFu;
-        }
+        for (int k = 0; k < LW; ++k) V[k] = __ldcs(reinterpret_cast<const uint4 *>(layer + 16 * c) + k);
+    };
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c < n_chunks) load(c);
+    for (; c < n_chunks; c += stride) {
         const uint32_t ts[16] = {T4[0].x, T4[0].y, T4[0].z, T4[0].w, T4[1].x, T4[1].y, T4[1].z, T4[1].w,
                                  T4[2].x, T4[2].y, T4[2].z, T4[2].w, T4[3].x, T4[3].y, T4[3].z, T4[3].w};
+        uint32_t w[4 * LW];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) visit(labs[k], ts[k]);
+        for (int k = 0; k < LW; ++k) {
+            w[4 * k] = V[k].x;
+            w[4 * k + 1] = V[k].y;
+            w[4 * k + 2] = V[k].z;
+            w[4 * k + 3] = V[k].w;
+        }
+        if (c + stride < n_chunks) load(c + stride);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const uint32_t lab = sizeof(L) == 1 ? (w[k / 4] >> (8 * (k % 4))) & 0xFFu : (w[k / 2] >> (16 * (k % 2))) & 0xFFFFu;
+            visit(lab, ts[k]);
+        }
     }
     // tail texels (n_texels % 16)
     const int64_t tail = n_chunks * 16 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -195,16 +203,27 @@ lcl_status label_area_impl(const lcl_atlas *atlas, const void *layer, int dtype_
     k_zero2<<<std::max(1u, std::min(1024u, (n_labels + kThreads - 1) / kThreads)), kThreads, 0, st>>>(c, ar, n_labels);
     const bool smem = n_labels <= kSmemLabels;
     const size_t shb = smem ? 2 * (size_t)n_labels * sizeof(unsigned long long) : 0;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count() * 4, (n_tex / 16 + kThreads - 1) / kThreads));
+    // as many CTAs as fit at once (one wave), fewer for small textures
+    auto fit = [&](auto kernel) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, shb) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * per_sm,
+                                                           (n_tex / 16 + kThreads - 1) / kThreads));
+    };
     const uint32_t *tri = atlas->tri;
     if (dtype_bytes == 1) {
         const uint8_t *l = static_cast<const uint8_t *>(layer);
-        if (smem) k_area<uint8_t, true><<<grid, kThreads, shb, st>>>(l, tri, atlas->area_w, n_tex, n_labels, c, ar);
-        else k_area<uint8_t, false><<<grid, kThreads, 0, st>>>(l, tri, atlas->area_w, n_tex, n_labels, c, ar);
+        if (smem) k_area<uint8_t, true><<<fit(k_area<uint8_t, true>), kThreads, shb, st>>>(l, tri, atlas->area_w, n_tex,
+                                                                                          n_labels, c, ar);
+        else k_area<uint8_t, false><<<fit(k_area<uint8_t, false>), kThreads, 0, st>>>(l, tri, atlas->area_w, n_tex,
+                                                                                      n_labels, c, ar);
     } else {
         const uint16_t *l = static_cast<const uint16_t *>(layer);
-        if (smem) k_area<uint16_t, true><<<grid, kThreads, shb, st>>>(l, tri, atlas->area_w, n_tex, n_labels, c, ar);
-        else k_area<uint16_t, false><<<grid, kThreads, 0, st>>>(l, tri, atlas->area_w, n_tex, n_labels, c, ar);
+        if (smem) k_area<uint16_t, true><<<fit(k_area<uint16_t, true>), kThreads, shb, st>>>(l, tri, atlas->area_w,
+                                                                                            n_tex, n_labels, c, ar);
+        else k_area<uint16_t, false><<<fit(k_area<uint16_t, false>), kThreads, 0, st>>>(l, tri, atlas->area_w, n_tex,
+                                                                                        n_labels, c, ar);
     }
     count_launches(2);
     cudaError_t e = cudaGetLastError();

@@ -222,6 +222,16 @@ lcl_status lcl_quantize_sphere(const lcl_atlas *atlas, const double centre[3], d
     return LCL_OK;
 }
 
+lcl_status lcl_quantize_spheres(const lcl_atlas *atlas, int32_t n, const double *centres, const double *radii,
+                                const uint32_t *labels, lcl_sphere *out) {
+    if (n < 0 || (n > 0 && (!centres || !radii || !labels || !out))) return fail(LCL_ERR_INVALID_ARG, "NULL argument");
+    for (int32_t k = 0; k < n; ++k) {
+        const lcl_status s = lcl_quantize_sphere(atlas, centres + 3 * (int64_t)k, radii[k], labels[k], out + k);
+        if (s != LCL_OK) return s;
+    }
+    return LCL_OK;
+}
+
 lcl_status lcl_camera_from_vp(const lcl_atlas *atlas, const double vp[16], int32_t width, int32_t height,
                               lcl_camera *out) {
     if (!atlas || !vp || !out) return fail(LCL_ERR_INVALID_ARG, "NULL argument");
@@ -271,7 +281,8 @@ lcl_status lcl_select_sphere(const lcl_atlas *atlas, void *layer, lcl_dtype dtyp
         const lcl_sphere &st = strokes[k];
         if (st.r2 < 0) return fail(LCL_ERR_INVALID_ARG, "stroke r2 < 0");
         if (st.label > lab_max) return fail(LCL_ERR_INVALID_ARG, "stroke label does not fit the layer dtype");
-        if (st.flags != 0) return fail(LCL_ERR_INVALID_ARG, "stroke flags are reserved and must be 0");
+        if ((st.flags & ~0xFFu) || (st.flags & 15u) > 8 || ((st.flags >> 4) & 15u) > 8)
+            return fail(LCL_ERR_INVALID_ARG, "stroke flags: padding radius and thickness at most 8, other bits 0");
         const int32_t lo = -(1 << 22), hi = (1 << 22) + (1 << 21);
         if (st.cx < lo || st.cx > hi || st.cy < lo || st.cy > hi || st.cz < lo || st.cz > hi)
             return fail(LCL_ERR_INVALID_ARG, "stroke centre outside [-2^22, 2^22 + 2^21]");
@@ -280,8 +291,8 @@ lcl_status lcl_select_sphere(const lcl_atlas *atlas, void *layer, lcl_dtype dtyp
 }
 
 size_t lcl_depth_workspace_bytes(const lcl_mesh *mesh, int32_t width, int32_t height) {
-    if (!mesh || mesh->n_tri < 0) return 0;
-    return depth_ws_bytes(mesh->n_tri, width, height);
+    if (!mesh || mesh->n_tri < 0 || mesh->n_pos < 0) return 0;
+    return depth_ws_bytes(mesh->n_pos, mesh->n_tri, width, height);
 }
 
 lcl_status lcl_depth_render(const lcl_mesh *mesh, const lcl_atlas *atlas, const lcl_camera *camera, float *depth,
@@ -319,6 +330,36 @@ lcl_status lcl_select_lasso(const lcl_atlas *atlas, void *layer, lcl_dtype dtype
     if (ws_bytes < select_ws_bytes(atlas, 1)) return fail(LCL_ERR_OUT_OF_MEMORY, "workspace smaller than lcl_select_workspace_bytes");
     return select_lasso_impl(atlas, layer, db, camera, depth, poly_xy, n_vertices, label, bias, hits_out, workspace,
                              reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t lcl_batch_workspace_bytes(const lcl_batch_model *models, int32_t n_models, int32_t n_strokes,
+                                 int32_t n_lassos) {
+    int64_t ns = 0, nt = 0;
+    if (n_models < 0 || n_strokes < 0 || n_lassos < 0 || (n_models && !models)) return 0;
+    if (batch_sizes(models, n_models, &ns, &nt) != LCL_OK) return 0;
+    return batch_ws_bytes(n_models, n_strokes, n_lassos, ns, nt);
+}
+
+size_t lcl_batch_staging_bytes(const lcl_batch_model *models, int32_t n_models, int32_t n_strokes,
+                               int32_t n_lassos) {
+    int64_t ns = 0, nt = 0;
+    if (n_models < 0 || n_strokes < 0 || n_lassos < 0 || (n_models && !models)) return 0;
+    if (batch_sizes(models, n_models, &ns, &nt) != LCL_OK) return 0;
+    return batch_host_bytes(n_models, n_strokes, n_lassos, ns, nt);
+}
+
+lcl_status lcl_batch_edit(const lcl_batch_model *models, int32_t n_models, const lcl_batch_stroke *strokes,
+                          int32_t n_strokes, const lcl_batch_lasso *lassos, int32_t n_lassos, void *workspace,
+                          size_t ws_bytes, void *host_staging, size_t staging_bytes, lcl_stream stream) {
+    if (!workspace || !aligned(workspace, 256)) return fail(LCL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (!host_staging || !aligned(host_staging, 16)) return fail(LCL_ERR_INVALID_ARG, "host staging must be 16-byte aligned");
+    return batch_edit_impl(models, n_models, strokes, n_strokes, lassos, n_lassos, workspace, ws_bytes, host_staging,
+                           staging_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+lcl_status lcl_batch_launch(void *workspace, const void *host_staging, lcl_stream stream) {
+    if (!workspace || !host_staging) return fail(LCL_ERR_INVALID_ARG, "NULL argument");
+    return batch_launch_impl(workspace, host_staging, reinterpret_cast<cudaStream_t>(stream));
 }
 
 lcl_status lcl_overlay(const lcl_atlas *atlas, const void *a, const void *b, void *out, lcl_dtype dtype, lcl_op op,

@@ -1,0 +1,315 @@
+// select_common.cuh -- device pieces shared by the single-stroke edits (select.cu) and the
+// batched multi-model edits (batch.cu): stroke arguments, conservative box tests, the exact
+// per-texel lasso test, label stores, candidate lists and launch helpers.  Not part of the ABI.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+
+#include "lcl_impl.cuh"
+
+namespace lcl {
+
+struct AtlasDev {
+    const int32_t *px, *py, *pz;
+    const int32_t *tile_box, *super_box;
+    int32_t w, h, T, tiles_x, tiles_y, supers_x, supers_y;
+};
+
+inline AtlasDev dev_view(const lcl_atlas *a) {
+    AtlasDev d;
+    d.px = a->pos_x;
+    d.py = a->pos_y;
+    d.pz = a->pos_z;
+    d.tile_box = a->tile_box;
+    d.super_box = a->super_box;
+    d.w = a->width;
+    d.h = a->height;
+    d.T = a->tile;
+    d.tiles_x = a->tiles_x;
+    d.tiles_y = a->tiles_y;
+    d.supers_x = a->supers_x;
+    d.supers_y = a->supers_y;
+    return d;
+}
+
+struct SphereArg {
+    int64_t cx, cy, cz, r2;
+    uint32_t label;
+    int32_t pad_r, pad_t;  // texture padding: kernel radius and outline thickness (0: no padding)
+};
+
+
+
+__device__ __forceinline__ int64_t box_dist2(int4 lo, int4 hi, const SphereArg &s) {
+    int64_t ex = max(max((int64_t)lo.x - s.cx, s.cx - (int64_t)hi.x), (int64_t)0);
+    int64_t ey = max(max((int64_t)lo.y - s.cy, s.cy - (int64_t)hi.y), (int64_t)0);
+    int64_t ez = max(max((int64_t)lo.z - s.cz, s.cz - (int64_t)hi.z), (int64_t)0);
+    return ex * ex + ey * ey + ez * ez;
+}
+
+// Any box of the 3 x 3 neighbourhood of (bx, by) in a grid of nx x ny boxes within the sphere's
+// reach (used when padding may write texels next to the selected ones).
+__device__ __forceinline__ bool near_box_3x3(const int32_t *boxes, int32_t nx, int32_t ny, int32_t bx, int32_t by,
+                                             const SphereArg &s) {
+    bool any = false;
+    for (int32_t y = max(by - 1, 0); y <= min(by + 1, ny - 1); ++y)
+        for (int32_t x = max(bx - 1, 0); x <= min(bx + 1, nx - 1); ++x) {
+            const int4 *b = reinterpret_cast<const int4 *>(boxes + 8 * ((int64_t)y * nx + x));
+            const int4 lo = b[0], hi = b[1];
+            any |= lo.w > 0 && box_dist2(lo, hi, s) <= s.r2;
+        }
+    return any;
+}
+
+// Appends this lane's tile to the candidate list if `cand`; one atomic per warp.
+__device__ __forceinline__ void append_candidate(bool cand, uint32_t tile, uint32_t *counter, uint32_t *list) {
+    uint32_t m = __ballot_sync(0xffffffffu, cand);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(counter, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    if (cand) list[base + __popc(m & ((1u << lane) - 1))] = tile;
+}
+
+
+// Programmatic dependent launch: wait for the previous grid on the stream to complete (its
+// memory is then visible); let the next grid be scheduled.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_allow_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+
+// Writes `label` into the texels of one 4-texel word whose bit is set in `m` (m != 0).
+template <typename L>
+__device__ __forceinline__ void store_hits(L *layer, int64_t l, uint32_t m, uint32_t label);
+
+template <>
+__device__ __forceinline__ void store_hits<uint8_t>(uint8_t *layer, int64_t l, uint32_t m, uint32_t label) {
+    uint32_t *p = reinterpret_cast<uint32_t *>(layer + l);
+    uint32_t rep = label * 0x01010101u;
+    if (m == 0xFu) {
+        *p = rep;
+        return;
+    }
+    uint32_t bm = (m * 0x00204081u) & 0x01010101u;  // bit k of m -> byte k
+    bm *= 0xFFu;
+    *p = (*p & ~bm) | (rep & bm);
+}
+
+template <>
+__device__ __forceinline__ void store_hits<uint16_t>(uint16_t *layer, int64_t l, uint32_t m, uint32_t label) {
+    uint2 *p = reinterpret_cast<uint2 *>(layer + l);
+    uint32_t rep = label * 0x00010001u;
+    if (m == 0xFu) {
+        *p = make_uint2(rep, rep);
+        return;
+    }
+    uint2 o = *p;
+    uint32_t lo = ((m & 1u) ? 0x0000FFFFu : 0u) | ((m & 2u) ? 0xFFFF0000u : 0u);
+    uint32_t hi = ((m & 4u) ? 0x0000FFFFu : 0u) | ((m & 8u) ? 0xFFFF0000u : 0u);
+    *p = make_uint2((o.x & ~lo) | (rep & lo), (o.y & ~hi) | (rep & hi));
+}
+
+__device__ __forceinline__ void add_hits(unsigned long long *hits, uint32_t cnt) {
+    if (!hits) return;
+    __shared__ uint32_t s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&s_cnt, cnt);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_cnt) atomicAdd(hits, (unsigned long long)s_cnt);
+}
+
+
+template <typename... K, typename... A>
+cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, cudaStream_t st, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+
+constexpr int kBands = 32;                                    // y-bands of lasso edges
+constexpr int kBandEdgesMax = kBands * LCL_MAX_LASSO_VERTICES;
+
+struct LassoArg {
+    float m[16];
+    float ws, hs;           // screen size as float
+    int32_t w_s, h_s;
+    float bias;
+    uint32_t label;
+    int32_t nv;
+    float bx0, by0, bx1, by1;  // polygon bbox (clipped to the screen) widened by a margin, pixels
+    float nx0, nx1, ny0, ny1;  // the same widened bbox in NDC, for the division-free reject
+    float ymin, ymax;          // exact vertical extent of the polygon
+    float band_y0, band_inv_h; // band of a point: floor((y - band_y0) * band_inv_h), clamped
+    float vx[LCL_MAX_LASSO_VERTICES + 1], vy[LCL_MAX_LASSO_VERTICES + 1];  // vertex nv = vertex 0
+    uint16_t band_off[kBands + 1];
+    uint8_t band_edge[kBandEdgesMax];  // edge e runs from vertex e to vertex e + 1
+};
+
+struct LassoShared {
+    float vx[LCL_MAX_LASSO_VERTICES + 1], vy[LCL_MAX_LASSO_VERTICES + 1];
+    uint16_t band_off[kBands + 1];
+    uint8_t band_edge[kBandEdgesMax];
+};
+
+// Conservative: false only if no texel of the box can be selected by the lasso.  Two exact tests:
+//  - the box's projected corners (all with w > 0) bound the projection of every point of the box
+//    (a projective map keeps a convex box convex); if their bounding box, widened by the margin,
+//    misses the polygon's widened bounding box, no texel can be inside the polygon;
+//  - with a depth map: NDC depth z/w is linear-fractional along every segment of the box, so its
+//    minimum over the box is at a corner; if that minimum (less 1e-4 for FP32 rounding) exceeds
+//    the largest depth-map value over the box's widened pixel footprint plus the bias, every texel
+//    of the box fails the depth test.  Footprints above 1024 pixels are not scanned (kept).
+__device__ inline bool box_may_touch(const LassoArg &p, int4 lo, int4 hi, const float *__restrict__ depth = nullptr) {
+    float xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY, zmin = INFINITY;
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+        float x = (float)((c & 1) ? hi.x : lo.x), y = (float)((c & 2) ? hi.y : lo.y), z = (float)((c & 4) ? hi.z : lo.z);
+        float cw = clip_row(p.m + 12, x, y, z);
+        if (!(cw > 0.0f)) return true;
+        float xs = screen_of(__fdiv_rn(clip_row(p.m, x, y, z), cw), p.ws);
+        float ys = screen_of(__fdiv_rn(clip_row(p.m + 4, x, y, z), cw), p.hs);
+        float zn = __fdiv_rn(clip_row(p.m + 8, x, y, z), cw);
+        xmin = fminf(xmin, xs); xmax = fmaxf(xmax, xs);
+        ymin = fminf(ymin, ys); ymax = fmaxf(ymax, ys);
+        zmin = fminf(zmin, zn);
+    }
+    if (xmax < p.bx0 || xmin > p.bx1 || ymax < p.by0 || ymin > p.by1) return false;
+    if (!depth) return true;
+    const float margin = 2.0f;
+    const int ix0 = max(0, __float2int_rd(xmin - margin)), ix1 = min(p.w_s - 1, __float2int_rd(xmax + margin));
+    const int iy0 = max(0, __float2int_rd(ymin - margin)), iy1 = min(p.h_s - 1, __float2int_rd(ymax + margin));
+    if (ix0 > ix1 || iy0 > iy1) return false;  // the whole footprint is off screen
+    if ((ix1 - ix0 + 1) * (iy1 - iy0 + 1) > 1024) return true;
+    float dmax = -INFINITY;
+    for (int iy = iy0; iy <= iy1; ++iy)
+        for (int ix = ix0; ix <= ix1; ++ix) dmax = fmaxf(dmax, __ldg(depth + (int64_t)iy * p.w_s + ix));
+    return !(zmin - 1e-4f > dmax + p.bias);
+}
+
+
+// The lasso test of one texel.  The conditions of the definition are all required, so they are
+// evaluated cheapest first; every value that decides the result is computed in the exact FP32
+// order of the definition.  Two shortcuts are exact as well:
+//  - a point more than the margin outside the polygon's bounding box (clipped to the screen) is
+//    off screen or outside the polygon: left of every vertex each straddling edge counts, and a
+//    closed polygon has an even number of those; right of every vertex none counts.  The test
+//    compares clip-space x with the widened box times w (w > 0), so it needs no division; its
+//    rounding is far below the 2-pixel margin;
+//  - only edges listed for the point's y-band are tested: an edge can count only if its y-range
+//    contains y, and each band lists every edge whose y-range comes within a margin of the band.
+template <typename Edges>
+__device__ __forceinline__ bool lasso_hit(const LassoArg &p, const Edges &sh, const float *__restrict__ depth,
+                                          int32_t X, int32_t Y, int32_t Z) {
+    if (X == INT32_MIN) return false;  // uncovered
+    const float fx = (float)X, fy = (float)Y, fz = (float)Z;
+    const float cw = clip_row(p.m + 12, fx, fy, fz);
+    if (!(cw > 0.0f)) return false;
+    const float cx = clip_row(p.m, fx, fy, fz);
+    if (cx < __fmul_rn(p.nx0, cw) || cx > __fmul_rn(p.nx1, cw)) return false;
+    const float cy = clip_row(p.m + 4, fx, fy, fz);
+    if (cy < __fmul_rn(p.ny0, cw) || cy > __fmul_rn(p.ny1, cw)) return false;
+    const float xs = screen_of(__fdiv_rn(cx, cw), p.ws);
+    const float ys = screen_of(__fdiv_rn(cy, cw), p.hs);
+    if (!(xs >= 0.0f && xs < p.ws && ys >= 0.0f && ys < p.hs)) return false;
+    if (!(ys >= p.ymin && ys < p.ymax)) return false;  // no edge straddles y
+    int band = __float2int_rz(__fmul_rn(__fsub_rn(ys, p.band_y0), p.band_inv_h));
+    band = band < 0 ? 0 : (band >= kBands ? kBands - 1 : band);
+    bool inside = false;
+    for (int k = sh.band_off[band]; k < sh.band_off[band + 1]; ++k) {
+        const int e = sh.band_edge[k];
+        const float ax = sh.vx[e], ay = sh.vy[e], bx = sh.vx[e + 1], by = sh.vy[e + 1];
+        if ((ay > ys) != (by > ys)) {
+            const float xi = __fadd_rn(__fdiv_rn(__fmul_rn(__fsub_rn(bx, ax), __fsub_rn(ys, ay)), __fsub_rn(by, ay)), ax);
+            if (xs < xi) inside = !inside;
+        }
+    }
+    if (!inside) return false;
+    const float zn = __fdiv_rn(clip_row(p.m + 8, fx, fy, fz), cw);
+    if (!(zn >= 0.0f && zn <= 1.0f)) return false;
+    const int32_t ix = __float2int_rz(xs), iy = __float2int_rz(ys);
+    const float d = __ldg(depth + (int64_t)iy * p.w_s + ix);
+    return zn <= __fadd_rn(d, p.bias);
+}
+
+
+
+// A grid of as many CTAs as fit on the GPU at once (persistent loops need no second wave).
+template <typename K>
+inline int resident_grid(K kernel) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return per_sm * sm_count();
+}
+
+
+// Fills the lasso argument: matrix, screen, polygon (vertex nv repeated as vertex 0), the widened
+// bounding box in pixels and NDC, and the y-band edge lists.
+inline void fill_lasso_arg(LassoArg &p, const lcl_camera *cam, const float *poly, int32_t nv, uint32_t label,
+                           float bias) {
+    for (int i = 0; i < 16; ++i) p.m[i] = cam->m[i];
+    p.ws = (float)cam->width;
+    p.hs = (float)cam->height;
+    p.w_s = cam->width;
+    p.h_s = cam->height;
+    p.bias = bias;
+    p.label = label;
+    p.nv = nv;
+    float x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+    for (int i = 0; i < nv; ++i) {
+        p.vx[i] = poly[2 * i];
+        p.vy[i] = poly[2 * i + 1];
+        x0 = std::fmin(x0, p.vx[i]);
+        x1 = std::fmax(x1, p.vx[i]);
+        y0 = std::fmin(y0, p.vy[i]);
+        y1 = std::fmax(y1, p.vy[i]);
+    }
+    for (int i = nv; i <= LCL_MAX_LASSO_VERTICES; ++i) {
+        p.vx[i] = p.vx[0];
+        p.vy[i] = p.vy[0];
+    }
+    // Culling and the division-free reject use the bbox widened by a margin far above the FP32
+    // rounding of projected points (well under a thousandth of a pixel at these sizes).
+    const float margin = 2.0f + 1e-3f * (float)std::max(cam->width, cam->height);
+    p.bx0 = std::fmax(x0, 0.0f) - margin;
+    p.bx1 = std::fmin(x1, (float)cam->width) + margin;
+    p.by0 = std::fmax(y0, 0.0f) - margin;
+    p.by1 = std::fmin(y1, (float)cam->height) + margin;
+    p.nx0 = (float)(2.0 * p.bx0 / cam->width - 1.0);
+    p.nx1 = (float)(2.0 * p.bx1 / cam->width - 1.0);
+    p.ny0 = (float)(2.0 * p.by0 / cam->height - 1.0);
+    p.ny1 = (float)(2.0 * p.by1 / cam->height - 1.0);
+    p.ymin = y0;
+    p.ymax = y1;
+    // y-bands of edges; each band lists the edges whose y-range comes within `slack` of it
+    const double bh = std::max((double)y1 - (double)y0, 1e-3) / kBands;
+    const double slack = 1e-3 * bh + 1e-3;
+    p.band_y0 = y0;
+    p.band_inv_h = (float)(1.0 / bh);
+    int cnt = 0;
+    for (int b = 0; b < kBands; ++b) {
+        p.band_off[b] = (uint16_t)cnt;
+        const double lo = (double)y0 + b * bh - slack, hi = (double)y0 + (b + 1) * bh + slack;
+        for (int e = 0; e < nv; ++e) {
+            const double ea = p.vy[e], eb = p.vy[e + 1];
+            if (ea == eb) continue;  // horizontal edges never straddle
+            if (std::min(ea, eb) <= hi && std::max(ea, eb) >= lo) p.band_edge[cnt++] = (uint8_t)e;
+        }
+    }
+    p.band_off[kBands] = (uint16_t)cnt;
+}
+
+}  // namespace lcl

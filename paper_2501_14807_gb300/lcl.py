@@ -28,9 +28,10 @@ SUPER = 16
 DEFAULT_BIAS = 2.0 ** -10
 
 EXPORTS = ["lcl_atlas_bytes", "lcl_atlas_bind", "lcl_atlas_rows", "lcl_atlas_workspace_bytes", "lcl_atlas_build",
-           "lcl_quantize_sphere", "lcl_camera_from_vp", "lcl_select_workspace_bytes", "lcl_select_sphere",
-           "lcl_select_sphere_static", "lcl_depth_workspace_bytes", "lcl_depth_render", "lcl_select_lasso", "lcl_overlay", "lcl_label_area",
-           "lcl_status_str", "lcl_last_error", "lcl_kernel_launches"]
+           "lcl_quantize_sphere", "lcl_quantize_spheres", "lcl_camera_from_vp", "lcl_select_workspace_bytes", "lcl_select_sphere",
+           "lcl_select_sphere_static", "lcl_depth_workspace_bytes", "lcl_depth_render", "lcl_select_lasso",
+           "lcl_batch_workspace_bytes", "lcl_batch_staging_bytes", "lcl_batch_edit", "lcl_batch_launch",
+           "lcl_overlay", "lcl_label_area", "lcl_status_str", "lcl_last_error", "lcl_kernel_launches"]
 
 
 class lcl_mesh(C.Structure):
@@ -56,7 +57,25 @@ class lcl_camera(C.Structure):
     _fields_ = [("m", C.c_float * 16), ("width", C.c_int32), ("height", C.c_int32)]
 
 
+class lcl_batch_model(C.Structure):
+    _fields_ = [("atlas", C.POINTER(lcl_atlas)), ("layer", C.c_void_p), ("dtype", C.c_int),
+                ("first_stroke", C.c_int32), ("n_strokes", C.c_int32), ("_pad", C.c_int32)]
+
+
+class lcl_batch_stroke(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("lasso", C.c_int32), ("sphere", lcl_sphere)]
+
+
+class lcl_batch_lasso(C.Structure):
+    _fields_ = [("camera", lcl_camera), ("depth", C.c_void_p), ("poly_xy", C.c_void_p), ("n_vertices", C.c_int32),
+                ("label", C.c_uint32), ("bias", C.c_float), ("_pad", C.c_int32)]
+
+
+LCL_STROKE_SPHERE, LCL_STROKE_LASSO = 0, 1
+BATCH_MAX_STROKES = 64
+
 assert C.sizeof(lcl_sphere) == 32 and C.sizeof(lcl_camera) == 72 and C.sizeof(lcl_atlas) == 128
+assert C.sizeof(lcl_batch_model) == 32 and C.sizeof(lcl_batch_stroke) == 40 and C.sizeof(lcl_batch_lasso) == 104
 
 SPHERE_DTYPE = np.dtype([("cx", "<i4"), ("cy", "<i4"), ("cz", "<i4"), ("pad", "<i4"),
                          ("r2", "<i8"), ("label", "<u4"), ("flags", "<u4")])
@@ -89,6 +108,7 @@ def library():
         "lcl_atlas_workspace_bytes": (SZ, [C.POINTER(lcl_mesh), I32, I32]),
         "lcl_atlas_build": (st, [C.POINTER(lcl_mesh), C.POINTER(lcl_atlas), P, SZ, P]),
         "lcl_quantize_sphere": (st, [C.POINTER(lcl_atlas), C.POINTER(D), D, U32, C.POINTER(lcl_sphere)]),
+        "lcl_quantize_spheres": (st, [C.POINTER(lcl_atlas), I32, P, P, P, P]),
         "lcl_camera_from_vp": (st, [C.POINTER(lcl_atlas), C.POINTER(D), I32, I32, C.POINTER(lcl_camera)]),
         "lcl_select_workspace_bytes": (SZ, [C.POINTER(lcl_atlas), I32]),
         "lcl_select_sphere": (st, [C.POINTER(lcl_atlas), P, C.c_int, P, I32, P, P, SZ, P]),
@@ -97,6 +117,11 @@ def library():
         "lcl_depth_render": (st, [C.POINTER(lcl_mesh), C.POINTER(lcl_atlas), C.POINTER(lcl_camera), P, P, SZ, P]),
         "lcl_select_lasso": (st, [C.POINTER(lcl_atlas), P, C.c_int, C.POINTER(lcl_camera), P, P, I32, U32, F, P, P,
                                   SZ, P]),
+        "lcl_batch_workspace_bytes": (SZ, [C.POINTER(lcl_batch_model), I32, I32, I32]),
+        "lcl_batch_staging_bytes": (SZ, [C.POINTER(lcl_batch_model), I32, I32, I32]),
+        "lcl_batch_edit": (st, [C.POINTER(lcl_batch_model), I32, C.POINTER(lcl_batch_stroke), I32,
+                                C.POINTER(lcl_batch_lasso), I32, P, SZ, P, SZ, P]),
+        "lcl_batch_launch": (st, [P, P, P]),
         "lcl_overlay": (st, [C.POINTER(lcl_atlas), P, P, P, C.c_int, C.c_int, U32, P]),
         "lcl_label_area": (st, [C.POINTER(lcl_atlas), P, C.c_int, U32, P, P, P]),
         "lcl_status_str": (C.c_char_p, [C.c_int]),
@@ -252,6 +277,18 @@ def lcl_quantize_sphere(atlas: Atlas, centre, radius, label):
     return rec[0]
 
 
+def lcl_quantize_spheres(atlas: Atlas, centres, radii, labels):
+    """Stroke records (SPHERE_DTYPE) for n world-space spheres."""
+    c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
+    r = np.ascontiguousarray(radii, dtype=np.float64).reshape(-1)
+    lab = np.ascontiguousarray(labels, dtype=np.uint32).reshape(-1)
+    out = np.zeros(len(r), SPHERE_DTYPE)
+    _check("lcl_quantize_spheres", library().lcl_quantize_spheres(
+        C.byref(atlas.c), len(r), c.ctypes.data_as(C.c_void_p), r.ctypes.data_as(C.c_void_p),
+        lab.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
 def lcl_camera_from_vp(atlas: Atlas, vp, width, height):
     out = lcl_camera()
     v = (C.c_double * 16)(*[float(x) for x in np.asarray(vp, np.float64).reshape(16)])
@@ -314,6 +351,103 @@ def lcl_select_lasso(atlas: Atlas, layer: torch.Tensor, cam: lcl_camera, depth: 
         poly.ctypes.data_as(C.c_void_p), poly.shape[0], int(label), float(bias), _ptr(hits_out), _ptr(ws),
         ws.numel(), _stream(stream)))
     return hits_out
+
+
+BATCH_STROKE_DTYPE = np.dtype([("kind", "<i4"), ("lasso", "<i4"), ("cx", "<i4"), ("cy", "<i4"), ("cz", "<i4"),
+                               ("pad", "<i4"), ("r2", "<i8"), ("label", "<u4"), ("flags", "<u4")])
+assert BATCH_STROKE_DTYPE.itemsize == C.sizeof(lcl_batch_stroke)
+
+
+class Batch:
+    """Arguments of one batched edit, kept alive for lcl_batch_edit / lcl_batch_launch.
+
+    models: list of (Atlas, layer tensor); queues: per model, a list of ("sphere", record) or
+    ("lasso", (camera, depth tensor, polygon float32 [n, 2], label, bias)) in queue order.
+    workspace / staging: optional reusable buffers (device uint8 / pinned host uint8); new ones are
+    allocated if they are missing or too small.  A pinned staging is read by the copy that
+    lcl_batch_edit enqueues, so it must not be reused before that copy has run."""
+
+    def __init__(self, models, queues, workspace=None, staging=None):
+        assert len(models) == len(queues)
+        self._keep = []
+        n_total = sum(len(q) for q in queues)
+        strokes = np.zeros(max(n_total, 1), BATCH_STROKE_DTYPE)
+        lassos = []
+        self.models = (lcl_batch_model * max(len(models), 1))()
+        k = 0
+        for i, ((atlas, layer), queue) in enumerate(zip(models, queues)):
+            if len(queue) > BATCH_MAX_STROKES:
+                raise ValueError("at most 64 queued strokes per model per batch")
+            self.models[i].atlas = C.pointer(atlas.c)
+            self.models[i].layer = layer.data_ptr()
+            self.models[i].dtype = _dtype_code(layer)
+            self.models[i].first_stroke = k
+            self.models[i].n_strokes = len(queue)
+            self._keep.append((atlas, layer))
+            for kind, payload in queue:
+                if kind == "sphere":
+                    r = payload
+                    strokes[k] = (LCL_STROKE_SPHERE, 0, r["cx"], r["cy"], r["cz"], 0, r["r2"], r["label"], 0)
+                else:
+                    cam, depth, poly, label, bias = payload
+                    poly = np.ascontiguousarray(poly, dtype=np.float32)
+                    bl = lcl_batch_lasso()
+                    bl.camera = cam
+                    bl.depth = depth.data_ptr()
+                    bl.poly_xy = poly.ctypes.data
+                    bl.n_vertices = poly.shape[0]
+                    bl.label = int(label)
+                    bl.bias = float(bias)
+                    self._keep.append((depth, poly))
+                    strokes[k] = (LCL_STROKE_LASSO, len(lassos), 0, 0, 0, 0, 0, 0, 0)
+                    lassos.append(bl)
+                k += 1
+        self.n_models, self.n_strokes, self.n_lassos = len(models), n_total, len(lassos)
+        self._strokes_np = strokes
+        self.strokes = strokes.ctypes.data_as(C.POINTER(lcl_batch_stroke))
+        self.lassos = (lcl_batch_lasso * max(len(lassos), 1))(*lassos)
+        lib = library()
+        self.ws_bytes = int(lib.lcl_batch_workspace_bytes(self.models, self.n_models, self.n_strokes, self.n_lassos))
+        self.staging_bytes = int(lib.lcl_batch_staging_bytes(self.models, self.n_models, self.n_strokes,
+                                                             self.n_lassos))
+        dev = models[0][1].device if models else torch.device("cuda")
+        if workspace is None or workspace.numel() < self.ws_bytes:
+            workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        if staging is None or staging.numel() < self.staging_bytes:
+            staging = torch.empty(max(self.staging_bytes, 256), dtype=torch.uint8).pin_memory()
+        self.workspace, self.staging = workspace, staging
+
+
+def _torch_stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return stream
+    return torch.cuda.ExternalStream(int(stream))
+
+
+def lcl_batch_edit(batch: Batch, stream=None):
+    """Uploads the batch's descriptors from its pinned staging and launches the batch.  The staging
+    is rewritten on the host by every call, and the upload of the previous call that used it may
+    still be queued on the device, so this waits (on the host) until that call's work has finished
+    before reusing the staging."""
+    busy = getattr(batch.staging, "_lcl_busy", None)
+    if busy is not None:
+        busy.synchronize()
+    _check("lcl_batch_edit", library().lcl_batch_edit(
+        batch.models, batch.n_models, batch.strokes, batch.n_strokes, batch.lassos, batch.n_lassos,
+        _ptr(batch.workspace), batch.workspace.numel(), C.c_void_p(batch.staging.data_ptr()), batch.staging.numel(),
+        _stream(stream)))
+    done = torch.cuda.Event()
+    done.record(_torch_stream(stream))
+    batch.staging._lcl_busy = done
+    return batch
+
+
+def lcl_batch_launch(batch: Batch, stream=None):
+    _check("lcl_batch_launch", library().lcl_batch_launch(_ptr(batch.workspace), C.c_void_p(batch.staging.data_ptr()),
+                                                          _stream(stream)))
+    return batch
 
 
 def lcl_overlay(atlas: Atlas, a: torch.Tensor, b: torch.Tensor, out: torch.Tensor, op, flags=0, stream=None):

@@ -1,0 +1,419 @@
+"""Serving loop: many models resident on the device, edit and query requests arriving
+continuously, batched into launches, with per-request latency.
+
+The paper's architecture keeps every layer on the GPU and lets the CPU only manage (Section 4),
+and its texture manager reserves texture memory and commits it on demand (Section 4.2, sparse
+textures).  This module is the server-side counterpart for many models at once:
+
+* a resident pool: each model's atlas, layers and depth maps live in device memory while the pool's
+  HBM budget allows; a model that is needed when the budget is full evicts the least recently used
+  idle model, whose buffers are copied to pinned host memory on a copy stream and copied back when
+  it is admitted again;
+* per-model FIFO queues: a model's requests are applied in arrival order;
+* continuous batching: every epoch takes, for each model with queued work, the leading run of edit
+  requests (up to 64 per layer) and at most one query, launches all edits as one batched edit
+  (``lcl_batch_edit``) followed by the queries (``lcl_overlay`` + ``lcl_label_area``) on one compute
+  stream, and records an event; requests that arrive meanwhile join the next epoch, which is
+  prepared on the host while the previous one runs (two epochs in flight);
+* latency: host arrival time to the host observing the epoch's completion event.
+
+Everything that computes runs in liblcl.so; this module only schedules.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import lcl
+
+SPHERE, LASSO, QUERY = 0, 1, 2
+
+
+@dataclass
+class Request:
+    t_arrive: float          # seconds, on the server's clock (relative to run start)
+    model: int
+    kind: int                # SPHERE, LASSO or QUERY
+    layer: int = 0
+    sphere: object = None    # (centre[3], radius, label) in world units
+    lasso: object = None     # (camera index, polygon float32 [n, 2], label)
+    query: object = None     # (op name, layer a, layer b, n_labels)
+    t_done: float = -1.0
+    result: object = None    # QUERY: (counts, areas) as numpy uint64 arrays
+
+
+@dataclass
+class ServedModel:
+    """Host description of one servable model (mesh, atlas side, cameras)."""
+    mesh: object
+    side: int
+    cams: list               # synth.Camera list (view-projection matrices)
+    n_layers: int = 2
+    tile: int = 32
+
+
+@dataclass
+class _Slot:
+    spec: ServedModel
+    atlas: object = None
+    mesh_dev: object = None
+    layers: list = field(default_factory=list)
+    cams: list = field(default_factory=list)     # lcl_camera
+    depths: list = field(default_factory=list)   # device float32 maps
+    host: dict = None                            # pinned copies while spilled
+    resident: bool = False
+    last_used: float = 0.0
+    busy_until: object = None                    # event of the last epoch that used it
+    spilled: object = None                       # event after the last spill's device-to-host copy
+    bytes: int = 0
+
+
+class Server:
+    """Resident pool + FIFO queues + continuous batching over one compute stream."""
+
+    def __init__(self, models, hbm_budget_bytes, device="cuda", max_edits_per_layer=lcl.BATCH_MAX_STROKES,
+                 max_in_flight=2, result_ring=4096, max_labels=256):
+        self.dev = torch.device(device)
+        self.max_in_flight = max_in_flight
+        self._ws = [None] * max_in_flight       # batch workspace / staging per in-flight slot
+        self._stg = [None] * max_in_flight
+        self._ring = torch.empty((result_ring, 2, max_labels), dtype=torch.int64).pin_memory()
+        self._ring_next = 0
+        self.max_labels = max_labels
+        self.budget = int(hbm_budget_bytes)
+        self.max_edits = int(max_edits_per_layer)
+        self.compute = torch.cuda.Stream(self.dev)
+        self.copy = torch.cuda.Stream(self.dev)
+        self.slots = [_Slot(spec=m) for m in models]
+        self.resident_bytes = 0
+        self.spills = 0
+        self.admissions = 0
+        self.epochs = 0
+        for i, s in enumerate(self.slots):
+            self._build(s)
+            if self.resident_bytes > self.budget:
+                self._spill(s)
+        torch.cuda.synchronize(self.dev)
+        self.ws_sel = None
+
+    # ---- pool ---------------------------------------------------------------------------
+
+    def _build(self, s: _Slot):
+        spec = s.spec
+        s.mesh_dev = lcl.Mesh.from_host(spec.mesh, self.dev)
+        s.atlas = lcl.Atlas(spec.side, spec.side, spec.tile, spec.mesh.n_tri, self.dev)
+        lcl.lcl_atlas_build(s.mesh_dev, s.atlas)
+        s.layers = [torch.zeros((spec.side, spec.side), dtype=torch.uint8, device=self.dev)
+                    for _ in range(spec.n_layers)]
+        s.cams = [lcl.lcl_camera_from_vp(s.atlas, c.vp, c.width, c.height) for c in spec.cams]
+        s.depths = []
+        for c in s.cams:
+            d = torch.empty((c.height, c.width), dtype=torch.float32, device=self.dev)
+            lcl.lcl_depth_render(s.mesh_dev, s.atlas, c, d)
+            s.depths.append(d)
+        s.bytes = s.atlas.buf.numel() + sum(l.numel() for l in s.layers) + sum(4 * d.numel() for d in s.depths)
+        s.resident = True
+        self.resident_bytes += s.bytes
+
+    def _spill(self, s: _Slot):
+        """Copies a resident model's device buffers to its pinned host copy (allocated on the first
+        spill and reused) on the copy stream and releases them without waiting: the copy stream's
+        order puts any later re-admission after this copy, and record_stream keeps the device memory
+        from being reused before the copy has read it."""
+        if s.busy_until is not None:
+            self.copy.wait_event(s.busy_until)
+        if s.host is None:
+            s.host = {"atlas": torch.empty(s.atlas.buf.numel(), dtype=torch.uint8).pin_memory(),
+                      "layers": [torch.empty(l.shape, dtype=l.dtype).pin_memory() for l in s.layers],
+                      "depths": [torch.empty(d.shape, dtype=d.dtype).pin_memory() for d in s.depths]}
+        host = s.host
+        with torch.cuda.stream(self.copy):
+            host["atlas"].copy_(s.atlas.buf, non_blocking=True)
+            for h, l in zip(host["layers"], s.layers):
+                h.copy_(l, non_blocking=True)
+            for h, d in zip(host["depths"], s.depths):
+                h.copy_(d, non_blocking=True)
+        for t in [s.atlas.buf] + s.layers + s.depths:
+            t.record_stream(self.copy)
+        s.spilled = torch.cuda.Event()
+        s.spilled.record(self.copy)
+        s.atlas = _Rebind(s.atlas)
+        s.layers, s.depths = [], []
+        s.mesh_dev = None
+        s.resident = False
+        self.resident_bytes -= s.bytes
+        self.spills += 1
+
+    def _admit(self, s: _Slot, now: float, keep=()):
+        """Makes a spilled model resident again, evicting least recently used idle models (never
+        one in `keep`: the models already taken into the epoch being built)."""
+        while self.resident_bytes + s.bytes > self.budget:
+            victims = [v for v in self.slots if v.resident and v is not s and id(v) not in keep and
+                       (v.busy_until is None or v.busy_until.query())]
+            if not victims:
+                break
+            self._spill(min(victims, key=lambda v: v.last_used))
+        h = s.host
+        buf = torch.empty(h["atlas"].numel(), dtype=torch.uint8, device=self.dev)
+        buf.record_stream(self.copy)
+        with torch.cuda.stream(self.copy):
+            buf.copy_(h["atlas"], non_blocking=True)
+            s.layers = [l.to(self.dev, non_blocking=True) for l in h["layers"]]
+            s.depths = [d.to(self.dev, non_blocking=True) for d in h["depths"]]
+        s.atlas = s.atlas.restore(buf)
+        ready = torch.cuda.Event()
+        ready.record(self.copy)
+        self.compute.wait_event(ready)
+        for t in [buf] + s.layers + s.depths:
+            t.record_stream(self.compute)
+        s.resident = True
+        self.resident_bytes += s.bytes
+        self.admissions += 1
+
+    # ---- requests -----------------------------------------------------------------------
+
+    def _epoch(self, queues, now):
+        """Takes the next epoch's work from the FIFO queues and launches it; returns
+        (event, requests, query results, batch)."""
+        models, work, queries, taken = [], [], [], []
+        in_epoch = set()
+        for mi, q in queues.items():
+            if not q:
+                continue
+            s = self.slots[mi]
+            if not s.resident:
+                self._admit(s, now, keep=in_epoch)
+            in_epoch.add(id(s))
+            s.last_used = now
+            reqs, per_layer_n = [], collections.Counter()
+            while q and q[0].kind != QUERY and per_layer_n[q[0].layer] < self.max_edits:
+                per_layer_n[q[0].layer] += 1
+                reqs.append(q.popleft())
+            if reqs:
+                sph = [r for r in reqs if r.kind == SPHERE]
+                recs = iter(lcl.lcl_quantize_spheres(s.atlas, [r.sphere[0] for r in sph], [r.sphere[1] for r in sph],
+                                                     [r.sphere[2] for r in sph])) if sph else iter(())
+                per_layer = collections.defaultdict(list)
+                for r in reqs:
+                    if r.kind == SPHERE:
+                        per_layer[r.layer].append(("sphere", next(recs)))
+                    else:
+                        ci, poly, label = r.lasso
+                        per_layer[r.layer].append(("lasso", (s.cams[ci], s.depths[ci], poly, label, lcl.DEFAULT_BIAS)))
+                for li, ops in per_layer.items():
+                    models.append((s.atlas, s.layers[li]))
+                    work.append(ops)
+                taken.extend(reqs)
+            elif q and q[0].kind == QUERY:
+                req = q.popleft()
+                queries.append((s, req))
+                taken.append(req)
+        slot = self.epochs % self.max_in_flight
+        batch = None
+        with torch.cuda.stream(self.compute):
+            if models:
+                batch = lcl.Batch(models, work, self._ws[slot], self._stg[slot])
+                self._ws[slot], self._stg[slot] = batch.workspace, batch.staging
+                lcl.lcl_batch_edit(batch, self.compute)
+            results = []
+            for s, req in queries:
+                op, la, lb, n_labels = req.query
+                out = torch.empty_like(s.layers[la])
+                lcl.lcl_overlay(s.atlas, s.layers[la], s.layers[lb], out, op, 0, self.compute)
+                cnt, area = lcl.lcl_label_area(s.atlas, out, n_labels, stream=self.compute)
+                ri = self._ring_next
+                self._ring_next = (ri + 1) % self._ring.shape[0]
+                self._ring[ri, 0, :n_labels].copy_(cnt, non_blocking=True)
+                self._ring[ri, 1, :n_labels].copy_(area, non_blocking=True)
+                results.append((req, ri, n_labels, out, cnt, area))
+        ev = torch.cuda.Event()
+        ev.record(self.compute)
+        for r in taken:
+            self.slots[r.model].busy_until = ev
+        self.epochs += 1
+        return ev, taken, results, batch
+
+    def run(self, requests, poll_s=20e-6):
+        """Serves `requests` (sorted by t_arrive, seconds from now) open-loop; fills t_done/result."""
+        pending = collections.deque(requests)
+        queues = collections.defaultdict(collections.deque)
+        in_flight = collections.deque()
+        t0 = time.perf_counter()
+        outstanding = len(requests)
+        while outstanding:
+            now = time.perf_counter() - t0
+            while pending and pending[0].t_arrive <= now:
+                r = pending.popleft()
+                queues[r.model].append(r)
+            while in_flight and in_flight[0][0].query():
+                ev, taken, results, _batch = in_flight.popleft()
+                done = time.perf_counter() - t0
+                for r in taken:
+                    r.t_done = done
+                for req, ri, nl, *_ in results:
+                    req.result = (self._ring[ri, 0, :nl].numpy().view(np.uint64).copy(),
+                                  self._ring[ri, 1, :nl].numpy().view(np.uint64).copy())
+                outstanding -= len(taken)
+            if len(in_flight) < self.max_in_flight and any(queues[m] for m in queues):
+                in_flight.append(self._epoch(queues, now))
+                continue
+            if not in_flight and not any(queues[m] for m in queues) and pending:
+                wait = pending[0].t_arrive - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 1e-3))
+            else:
+                time.sleep(poll_s)
+        torch.cuda.synchronize(self.dev)
+        return requests
+
+    def run_per_request(self, requests, poll_s=20e-6):
+        """The same trace served without batching: each request, in arrival order, is one
+        single-stroke (or overlay + area) call on the compute stream; its completion event is
+        polled.  The baseline the batched loop is compared with."""
+        pending = collections.deque(requests)
+        in_flight = collections.deque()
+        ws = None
+        t0 = time.perf_counter()
+        done_n = 0
+        while done_n < len(requests):
+            now = time.perf_counter() - t0
+            while in_flight and in_flight[0][0].query():
+                ev, req, res = in_flight.popleft()
+                req.t_done = time.perf_counter() - t0
+                if res is not None:
+                    req.result = (res[0].numpy().view(np.uint64).copy(), res[1].numpy().view(np.uint64).copy())
+                done_n += 1
+            if pending and pending[0].t_arrive <= now and len(in_flight) < 4096:
+                req = pending.popleft()
+                s = self.slots[req.model]
+                if not s.resident:
+                    self._admit(s, now)
+                s.last_used = now
+                res = None
+                with torch.cuda.stream(self.compute):
+                    if ws is None:
+                        ws = torch.empty(max(lcl.lcl_select_workspace_bytes(sl.atlas, 1) for sl in self.slots
+                                             if sl.resident), dtype=torch.uint8, device=self.dev)
+                    if req.kind == SPHERE:
+                        c, r, label = req.sphere
+                        lcl.lcl_select_sphere(s.atlas, s.layers[req.layer], lcl.lcl_quantize_spheres(s.atlas, [c], [r], [label]),
+                                              None, ws, self.compute)
+                    elif req.kind == LASSO:
+                        ci, poly, label = req.lasso
+                        lcl.lcl_select_lasso(s.atlas, s.layers[req.layer], s.cams[ci], s.depths[ci], poly, label,
+                                             lcl.DEFAULT_BIAS, None, ws, self.compute)
+                    else:
+                        op, la, lb, n_labels = req.query
+                        out = torch.empty_like(s.layers[la])
+                        lcl.lcl_overlay(s.atlas, s.layers[la], s.layers[lb], out, op, 0, self.compute)
+                        cnt, area = lcl.lcl_label_area(s.atlas, out, n_labels, stream=self.compute)
+                        ri = self._ring_next
+                        self._ring_next = (ri + 1) % self._ring.shape[0]
+                        self._ring[ri, 0, :n_labels].copy_(cnt, non_blocking=True)
+                        self._ring[ri, 1, :n_labels].copy_(area, non_blocking=True)
+                        res = (self._ring[ri, 0, :n_labels], self._ring[ri, 1, :n_labels], out, cnt, area)
+                ev = torch.cuda.Event()
+                ev.record(self.compute)
+                s.busy_until = ev
+                in_flight.append((ev, req, res))
+                continue
+            time.sleep(poll_s if in_flight else min(1e-3, max(0.0, (pending[0].t_arrive - now) if pending else 0.0)))
+        torch.cuda.synchronize(self.dev)
+        return requests
+
+    def layers_of(self, mi):
+        s = self.slots[mi]
+        if s.resident:
+            return [l.clone() for l in s.layers]
+        s.spilled.synchronize()
+        return [h.to(self.dev) for h in s.host["layers"]]
+
+
+class _Rebind:
+    """The lcl_atlas of a spilled model: its struct, ready to be re-bound to a new device buffer."""
+
+    def __init__(self, atlas):
+        self.width, self.height, self.tile, self.n_tri = atlas.width, atlas.height, atlas.tile, int(atlas.c.n_tri)
+        self.bbox_min, self.scale = list(atlas.c.bbox_min), atlas.c.scale
+
+    def restore(self, buf):
+        a = lcl.Atlas(self.width, self.height, self.tile, self.n_tri, buf.device, buffer=buf)
+        for i in range(3):
+            a.c.bbox_min[i] = self.bbox_min[i]
+        a.c.scale = self.scale
+        return a
+
+
+def poisson_requests(n_models, rate_hz, duration_s, seed, mix=(0.7, 0.2, 0.1), zipf_s=1.1, n_layers=2,
+                     sphere_of=None, lasso_of=None, n_labels=256):
+    """Open-loop arrivals: exponential gaps at `rate_hz`, kinds by `mix` (sphere, lasso, query),
+    model by a Zipf(zipf_s) law over the models, layers uniform.  sphere_of(model, rng) and
+    lasso_of(model, rng) draw the payloads."""
+    rng = np.random.default_rng(seed)
+    n = int(rate_hz * duration_s)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, size=n))
+    w = 1.0 / np.arange(1, n_models + 1) ** zipf_s
+    models = rng.choice(n_models, size=n, p=w / w.sum())
+    kinds = rng.choice(3, size=n, p=np.array(mix) / sum(mix))
+    out = []
+    for i in range(n):
+        m, k = int(models[i]), int(kinds[i])
+        r = Request(float(t[i]), m, k, layer=int(rng.integers(0, n_layers)))
+        if k == SPHERE:
+            r.sphere = sphere_of(m, rng)
+        elif k == LASSO:
+            r.lasso = lasso_of(m, rng)
+        else:
+            r.query = (["and", "or", "xor"][int(rng.integers(0, 3))], 0, 1, n_labels)
+        out.append(r)
+    return out
+
+
+def replay_alone(server_models, requests, device="cuda"):
+    """Applies each model's requests alone, in arrival order, with single-stroke calls on fresh
+    layers; returns ({model: layers}, {request index: (counts, areas)}) for comparison."""
+    dev = torch.device(device)
+    by_model = collections.defaultdict(list)
+    for i, r in enumerate(requests):
+        by_model[r.model].append((i, r))
+    layers, results = {}, {}
+    for mi, reqs in by_model.items():
+        spec = server_models[mi]
+        mesh = lcl.Mesh.from_host(spec.mesh, dev)
+        a = lcl.Atlas(spec.side, spec.side, spec.tile, spec.mesh.n_tri, dev)
+        lcl.lcl_atlas_build(mesh, a)
+        ls = [torch.zeros((spec.side, spec.side), dtype=torch.uint8, device=dev) for _ in range(spec.n_layers)]
+        cams = [lcl.lcl_camera_from_vp(a, c.vp, c.width, c.height) for c in spec.cams]
+        depths = []
+        for c in cams:
+            d = torch.empty((c.height, c.width), dtype=torch.float32, device=dev)
+            lcl.lcl_depth_render(mesh, a, c, d)
+            depths.append(d)
+        for i, r in reqs:
+            if r.kind == SPHERE:
+                c, rad, label = r.sphere
+                lcl.lcl_select_sphere(a, ls[r.layer], np.array([lcl.lcl_quantize_sphere(a, c, rad, label)],
+                                                               lcl.SPHERE_DTYPE))
+            elif r.kind == LASSO:
+                ci, poly, label = r.lasso
+                lcl.lcl_select_lasso(a, ls[r.layer], cams[ci], depths[ci], poly, label)
+            else:
+                op, la, lb, n_labels = r.query
+                out = torch.empty_like(ls[la])
+                lcl.lcl_overlay(a, ls[la], ls[lb], out, op)
+                cnt, area = lcl.lcl_label_area(a, out, n_labels)
+                results[i] = (cnt.cpu().numpy().view(np.uint64), area.cpu().numpy().view(np.uint64))
+        layers[mi] = ls
+    torch.cuda.synchronize(dev)
+    return layers, results
+
+
+def latency_stats(requests):
+    lat = np.array([r.t_done - r.t_arrive for r in requests])
+    span = max(r.t_done for r in requests) - min(r.t_arrive for r in requests)
+    return {"requests": len(requests), "throughput_rps": len(requests) / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)), "max_ms": 1e3 * float(lat.max())}

@@ -224,3 +224,51 @@ def grid_patch(nx: int, ny: int, W: int, H: int, seed: int, jitter: float = 0.0)
     a, b, c, d = j * s + i, j * s + i + 1, (j + 1) * s + i + 1, (j + 1) * s + i
     tri = np.stack([np.stack([a, b, c], 1), np.stack([a, c, d], 1)], 1).reshape(-1, 3).astype(np.uint32)
     return Mesh(pos, uv, tri.copy(), tri.copy()).check()
+
+
+def _grid_mesh(pos_grid: np.ndarray, wrap_u: bool, wrap_v: bool) -> tuple:
+    """Triangles of an (nv+1) x (nu+1) parameter grid; positions wrap where the surface closes
+    (duplicated in UV only), texture coordinates (u, v) = (i/nu, j/nv) never wrap."""
+    nvp, nup = pos_grid.shape[:2]
+    nu, nv = nup - 1, nvp - 1
+    pu = nu if wrap_u else nup          # distinct position columns
+    pv = nv if wrap_v else nvp          # distinct position rows
+    pos = pos_grid[:pv, :pu].reshape(-1, 3).astype(np.float32)
+    iu = np.arange(nup) / nu
+    jv = np.arange(nvp) / nv
+    uu, vv = np.meshgrid(iu, jv)
+    uv = np.stack([uu, vv], -1).reshape(-1, 2).astype(np.float32)
+    i, j = np.meshgrid(np.arange(nu), np.arange(nv))
+    i, j = i.ravel(), j.ravel()
+    ip, jp = (i + 1) % pu if wrap_u else i + 1, (j + 1) % pv if wrap_v else j + 1
+    pa, pb, pc, pd = j * pu + i, j * pu + ip, jp * pu + ip, jp * pu + i
+    ua, ub, uc, ud = j * nup + i, j * nup + i + 1, (j + 1) * nup + i + 1, (j + 1) * nup + i
+    tri_pos = np.stack([np.stack([pa, pb, pc], 1), np.stack([pa, pc, pd], 1)], 1).reshape(-1, 3)
+    tri_uv = np.stack([np.stack([ua, ub, uc], 1), np.stack([ua, uc, ud], 1)], 1).reshape(-1, 3)
+    return Mesh(pos, uv, tri_pos.astype(np.uint32), tri_uv.astype(np.uint32)).check()
+
+
+def displaced_sphere(n_lon: int, n_lat: int, noise_amp: float = 0.03, noise_freq: float = 3.0,
+                     seed: int = 7) -> Mesh:
+    """Unit sphere with seeded radial noise, equirectangular UV (u = longitude, v = latitude);
+    2 * n_lon * n_lat triangles (those touching the poles have zero 3D area on one side)."""
+    lon = 2.0 * np.pi * np.arange(n_lon + 1) / n_lon
+    lat = np.pi * np.arange(n_lat + 1) / n_lat - np.pi / 2
+    LO, LA = np.meshgrid(lon, lat)
+    d = np.stack([np.cos(LA) * np.cos(LO), np.cos(LA) * np.sin(LO), np.sin(LA)], -1)
+    r = 1.0 + noise_amp * GradientNoise3(seed)(noise_freq * d[..., 0], noise_freq * d[..., 1], noise_freq * d[..., 2])
+    return _grid_mesh(d * r[..., None], wrap_u=True, wrap_v=False)
+
+
+def torus(n_u: int, n_v: int, major: float = 1.0, minor: float = 0.35, noise_amp: float = 0.01,
+          noise_freq: float = 4.0, seed: int = 9) -> Mesh:
+    """Torus with seeded noise on the tube radius, UV = (angle around the axis, angle around the
+    tube) / 2 pi; 2 * n_u * n_v triangles."""
+    a = 2.0 * np.pi * np.arange(n_u + 1) / n_u
+    b = 2.0 * np.pi * np.arange(n_v + 1) / n_v
+    A, B = np.meshgrid(a, b)
+    base = np.stack([np.cos(A), np.sin(A), np.zeros_like(A)], -1) * major
+    rr = minor * (1.0 + noise_amp / minor * GradientNoise3(seed)(noise_freq * np.cos(A), noise_freq * np.sin(A),
+                                                                 noise_freq * np.cos(B)))
+    p = base + rr[..., None] * np.stack([np.cos(B) * np.cos(A), np.cos(B) * np.sin(A), np.sin(B)], -1)
+    return _grid_mesh(p, wrap_u=True, wrap_v=True)

@@ -12,7 +12,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .mesh import Mesh, vessel_charts, vessel_cylindrical
+from .mesh import Mesh, displaced_sphere, torus, vessel_charts, vessel_cylindrical
 
 
 def _rng(*seed):
@@ -235,3 +235,45 @@ def config_roofline(n_strokes: int = 1000, n_lassos: int = 20, n_cams: int = 4,
     las = lassos(m, cams, n_lassos, 32, 1, 255, 4)
     return Workload("vessel-8M-16384sq-u8", m, side, side, 32, 1, 4, s, cams, las,
                     overlays=[("xor", 0, 1), ("or", 2, 3)])
+
+
+@dataclass
+class BatchModel:
+    mesh: Mesh
+    side: int            # square atlas side
+    strokes: Strokes     # sphere strokes, queue order interleaved with lassos by `order`
+    cams: list
+    lassos: list         # Lasso records (layer unused: one layer per model)
+    order: np.ndarray    # queue: entries >= 0 are sphere stroke indices, entries < 0 are lasso -1-index
+
+
+def batch_model(kind: str, n_tri: int, seed: int, n_sphere: int = 48, n_lasso: int = 16, depth_side: int = 1024,
+                r_lo: float = 0.005, r_hi: float = 0.10) -> BatchModel:
+    """One model of the batching workload: kind in {vessel, sphere, torus}, about n_tri triangles, an
+    atlas side of the power of two nearest sqrt(8 n_tri) clamped to [512, 4096], 48 sphere strokes
+    (radii log-uniform 0.5-10% of the diagonal) and 16 lassos on 2 orbit cameras, shuffled into one
+    queue."""
+    rng = _rng(0x4241, seed)
+    n = max(int(np.sqrt(n_tri / 4.0)), 4)
+    if kind == "vessel":
+        m = vessel_cylindrical(2 * n, n, noise_amp=0.01, noise_freq=8.0, seed=seed)
+    elif kind == "sphere":
+        m = displaced_sphere(2 * n, n, seed=seed)
+    else:
+        m = torus(2 * n, n, seed=seed)
+    side = int(2 ** np.clip(np.round(np.log2(np.sqrt(8.0 * m.n_tri))), 9, 12))
+    st = sphere_strokes(m, n_sphere, seed * 7 + 1, r_lo, r_hi, 1, 255)
+    cams = [orbit_camera(m, depth_side, depth_side, rng) for _ in range(2)]
+    las = lassos(m, cams, n_lasso, seed * 7 + 2, 1, 255, 1)
+    order = np.concatenate([np.arange(n_sphere), -1 - np.arange(n_lasso)])
+    rng.shuffle(order)
+    return BatchModel(m, side, st, cams, las, order)
+
+
+def config_batch(n_models: int = 256, seed: int = 4, tri_lo: float = 5e3, tri_hi: float = 5e5, **kw) -> list:
+    """The batching workload: n_models models of uneven size (triangles log-uniform in
+    [tri_lo, tri_hi]), kinds drawn uniformly from vessel / displaced sphere / torus."""
+    rng = _rng(0x42415443, seed)
+    kinds = rng.choice(["vessel", "sphere", "torus"], size=n_models)
+    tris = np.exp(rng.uniform(np.log(tri_lo), np.log(tri_hi), size=n_models))
+    return [batch_model(str(k), int(t), 1000 * seed + i, **kw) for i, (k, t) in enumerate(zip(kinds, tris))]

@@ -101,7 +101,9 @@ def test_select_sphere_rejects_bad_arguments(lcl):
     assert call(bad) == 1                                     # label does not fit uint8
     bad = good.copy(); bad[1]["r2"] = -1
     assert call(bad) == 1
-    bad = good.copy(); bad[0]["flags"] = 1
+    bad = good.copy(); bad[0]["flags"] = 9                     # padding radius above 8
+    assert call(bad) == 1
+    bad = good.copy(); bad[0]["flags"] = 1 << 8                # undefined flag bit
     assert call(bad) == 1
     bad = good.copy(); bad[3]["cx"] = 1 << 23
     assert call(bad) == 1                                     # centre outside the accepted range
@@ -199,3 +201,35 @@ def test_host_helpers_match_oracle_without_gpu(lcl):
         vp = (C.c_double * 16)(*cam.vp.ravel())
         assert lib.lcl_camera_from_vp(C.byref(a), vp, 800, 600, C.byref(out)) == 0
         assert np.array_equal(np.array(list(out.m), np.float32), oracle.camera_mq(cam.vp, mn, S))
+
+
+def test_batch_rejects_bad_arguments_on_host(lcl):
+    lib, a = _bound(lcl, W=128, H=128, T=32)
+    ws, stg = C.c_void_p(1 << 42), (C.c_uint8 * 4096)()
+    models = (lcl.lcl_batch_model * 1)()
+    models[0].atlas = C.pointer(a)
+    models[0].layer = 1 << 41
+    models[0].dtype = 1
+    models[0].first_stroke = 0
+    models[0].n_strokes = 65
+    strokes = (lcl.lcl_batch_stroke * 65)()
+    lassos = (lcl.lcl_batch_lasso * 1)()
+    call = lambda n_strokes=65, n_lassos=0: lib.lcl_batch_edit(models, 1, strokes, n_strokes, lassos, n_lassos,  # noqa
+                                                               ws, 1 << 30, stg, 4096, None)
+    assert call() == 4                                   # more than 64 strokes for one model
+    models[0].n_strokes = 10
+    assert call(n_strokes=5) == 1                        # stroke range outside the array
+    strokes[3].kind = 7
+    assert call() == 1                                   # unknown stroke kind
+    strokes[3].kind = 1
+    strokes[3].lasso = 0
+    assert call() == 1                                   # lasso index with no lassos
+    strokes[3].kind = 0
+    strokes[4].sphere.label = 300
+    assert call() == 1                                   # label too wide for uint8
+    strokes[4].sphere.label = 3
+    models[0].layer = (1 << 41) + 8
+    assert call() == 1                                   # layer misaligned
+    models[0].layer = 1 << 41
+    assert call() in (2,)                                # staging too small for the descriptors
+    assert lib.lcl_batch_workspace_bytes(models, 1, 65, 0) > 0

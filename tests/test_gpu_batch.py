@@ -1,0 +1,155 @@
+"""Batched edits (many models, queued sphere and lasso strokes, one cull and one persistent apply
+launch) against the same strokes applied one call at a time, in queue order, through the
+single-stroke entry points -- and, for some models, against the oracle.  Results must be
+identical bit for bit: the batch only changes the schedule."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import DEV, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+from paper_2501_14807_gb300 import lcl  # noqa: E402
+
+BIAS = lcl.DEFAULT_BIAS
+
+
+def build(models, tiles, dtypes, seed=0):
+    """GPU atlases, initial layers, depth maps and per-model queues for a list of BatchModel."""
+    out = []
+    rng = np.random.default_rng(seed)
+    for bm, T, dt in zip(models, tiles, dtypes):
+        mesh = lcl.Mesh.from_host(bm.mesh, DEV)
+        a = lcl.Atlas(bm.side, bm.side, T, bm.mesh.n_tri, DEV)
+        lcl.lcl_atlas_build(mesh, a)
+        init = rng.integers(0, 5, size=(bm.side, bm.side)).astype(dt)
+        cams = [lcl.lcl_camera_from_vp(a, c.vp, c.width, c.height) for c in bm.cams]
+        depths = []
+        for c in cams:
+            d = torch.empty((c.height, c.width), dtype=torch.float32, device=DEV)
+            lcl.lcl_depth_render(mesh, a, c, d)
+            depths.append(d)
+        top = int(np.iinfo(dt).max)
+        queue = []
+        for e in bm.order:
+            if e >= 0:
+                rec = lcl.lcl_quantize_sphere(a, bm.strokes.centre[e], bm.strokes.radius[e],
+                                              min(int(bm.strokes.label[e]) * 131 % top + 1, top))
+                queue.append(("sphere", rec))
+            else:
+                L = bm.lassos[-1 - e]
+                queue.append(("lasso", (cams[L.cam], depths[L.cam], L.poly, min(L.label * 7 % top + 1, top), BIAS)))
+        out.append(dict(bm=bm, mesh=mesh, atlas=a, init=init, queue=queue, dtype=dt))
+    return out
+
+
+def run_sequential(models):
+    layers = []
+    for m in models:
+        layer = to_dev(m["init"])
+        for kind, payload in m["queue"]:
+            if kind == "sphere":
+                lcl.lcl_select_sphere(m["atlas"], layer, np.array([payload], lcl.SPHERE_DTYPE))
+            else:
+                cam, depth, poly, label, bias = payload
+                lcl.lcl_select_lasso(m["atlas"], layer, cam, depth, poly, label, bias)
+        layers.append(layer)
+    return layers
+
+
+def make_batch(models):
+    layers = [to_dev(m["init"]) for m in models]
+    b = lcl.Batch([(m["atlas"], l) for m, l in zip(models, layers)], [m["queue"] for m in models])
+    return b, layers
+
+
+@pytest.fixture(scope="module")
+def models():
+    kinds = ["vessel", "sphere", "torus", "vessel", "torus", "sphere"]
+    tris = [3000, 9000, 20000, 40000, 6000, 15000]
+    bms = [synth.batch_model(k, t, 50 + i, n_sphere=40, n_lasso=12, depth_side=320) for i, (k, t) in
+           enumerate(zip(kinds, tris))]
+    for bm in bms:
+        bm.side = 256 if bm.mesh.n_tri < 10000 else 512
+    return build(bms, [16, 32, 64, 32, 128, 32], [np.uint8, np.uint16, np.uint8, np.uint8, np.uint16, np.uint8])
+
+
+def test_batch_equals_sequential_single_stroke_calls(models):
+    seq = run_sequential(models)
+    b, layers = make_batch(models)
+    lcl.lcl_batch_edit(b)
+    torch.cuda.synchronize()
+    for m, s, l in zip(models, seq, layers):
+        assert torch.equal(s, l), "batched layer differs from sequential calls"
+        assert not torch.equal(l, to_dev(m["init"]))
+
+
+def test_batch_matches_oracle_on_two_models(models):
+    b, layers = make_batch(models)
+    lcl.lcl_batch_edit(b)
+    torch.cuda.synchronize()
+    for mi in (0, 1):
+        m = models[mi]
+        bm = m["bm"]
+        o = oracle.Atlas(bm.mesh, bm.side, bm.side, tile=m["atlas"].tile)
+        exp = m["init"].copy()
+        amb = np.zeros(exp.shape, bool)
+        for kind, payload in m["queue"]:
+            if kind == "sphere":
+                oracle.select_sphere(o, exp, np.array([payload], oracle.SPHERE_DTYPE))
+            else:
+                cam, depth, poly, label, bias = payload
+                M = np.array(list(cam.m), np.float32)
+                dm = oracle.depth(bm.mesh, o.mn, o.S, M, cam.width, cam.height)
+                _, a = oracle.select_lasso(o, exp, M, dm, poly, label, bias)
+                amb |= a.astype(bool)
+        d = to_np(layers[mi], m["dtype"]) != exp
+        assert not (d & ~amb).any()
+
+
+def test_batch_relaunch_and_cuda_graph_replay(models):
+    seq = run_sequential(models)
+    b, layers = make_batch(models)
+    lcl.lcl_batch_edit(b)
+    torch.cuda.synchronize()
+    # the same queue again on its own result changes nothing
+    lcl.lcl_batch_launch(b)
+    torch.cuda.synchronize()
+    for s, l in zip(seq, layers):
+        assert torch.equal(s, l)
+    # capture the launch in a CUDA graph, reset the layers, replay
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            lcl.lcl_batch_launch(b)
+    torch.cuda.current_stream().wait_stream(side)
+    for m, l in zip(models, layers):
+        l.copy_(to_dev(m["init"]))
+    g.replay()
+    torch.cuda.synchronize()
+    for s, l in zip(seq, layers):
+        assert torch.equal(s, l)
+
+
+def test_batch_rejects_long_queues(models):
+    m = models[0]
+    rec = m["queue"][0]
+    with pytest.raises(ValueError):
+        lcl.Batch([(m["atlas"], to_dev(m["init"]))], [[rec] * 65])
+
+
+def test_batch_back_to_back_edits_reuse_staging_safely(models):
+    """Three edits in a row on one Batch without synchronising: each call must wait until the
+    previous upload from the shared pinned staging has run before rewriting it."""
+    seq = run_sequential(models)
+    b, layers = make_batch(models)
+    for _ in range(3):
+        lcl.lcl_batch_edit(b)
+    torch.cuda.synchronize()
+    for s, l in zip(seq, layers):
+        assert torch.equal(s, l)

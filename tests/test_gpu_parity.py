@@ -292,3 +292,28 @@ def test_empty_inputs():
     rec = np.array([(1 << 20, 1 << 20, 1 << 20, 0, 1 << 50, 9, 0)], lcl.SPHERE_DTYPE)
     lcl.lcl_select_sphere(a2, layer, rec, hits_out=hits)
     assert int(hits.item()) == 0 and int(layer.sum()) == 0
+
+
+@pytest.mark.parametrize("T,dt", [(16, np.uint8), (32, np.uint16), (64, np.uint8)])
+def test_sphere_with_texture_padding_bit_exact(T, dt):
+    """Texture padding (Section 4.3.2) requested per stroke: radius and thickness from 1 to 8, mixed
+    with unpadded strokes in one call, on a chart atlas whose gutters leave uncovered texels."""
+    mesh = synth.vessel_charts(200, 100, 25, 10, 512, seed=5)
+    W = H = 512
+    o = oracle.Atlas(mesh, W, H, tile=T)
+    _, a = gpu_atlas(mesh, W, H, T)
+    st = synth.sphere_strokes(mesh, 24, 41, 0.01, 0.3, 1, int(np.iinfo(dt).max))
+    recs = sphere_recs(o, st)
+    pads = [(1, 1), (0, 0), (2, 1), (1, 3), (8, 8), (3, 0), (0, 5), (1, 2)]
+    for k in range(len(recs)):
+        r, t = pads[k % len(pads)]
+        recs[k]["flags"] = oracle.pad_flags(r, t)
+    init = np.random.default_rng(4).integers(0, 7, size=(H, W)).astype(dt)
+    exp = init.copy()
+    exp_hits, padded = oracle.select_sphere_2d(o, exp, recs)
+    assert padded.sum() > 0
+    layer = to_dev(init)
+    hits = torch.zeros(len(recs), dtype=torch.int64, device=DEV)
+    lcl.lcl_select_sphere(a, layer, recs, hits_out=hits)
+    assert np.array_equal(to_np(layer, dt), exp)
+    assert np.array_equal(to_np(hits, np.uint64), exp_hits)

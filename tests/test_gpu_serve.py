@@ -1,0 +1,62 @@
+"""Serving: requests of many models arriving open-loop, batched continuously, with models spilled
+and re-admitted under an HBM budget.  Each model's final layers and each query's result must be
+the same as applying that model's requests alone, in arrival order, with single-stroke calls."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+from paper_2501_14807_gb300 import lcl, serve  # noqa: E402
+
+
+def served_models(n, seed=300):
+    out, pools = [], []
+    for i in range(n):
+        kind = ["vessel", "sphere", "torus"][i % 3]
+        bm = synth.batch_model(kind, [4000, 12000, 30000][i % 3], seed + i, n_sphere=32, n_lasso=8, depth_side=256)
+        side = 256 if bm.mesh.n_tri < 10000 else 512
+        out.append(serve.ServedModel(bm.mesh, side, bm.cams, n_layers=2))
+        pools.append(bm)
+    return out, pools
+
+
+def trace(pools, rate, duration, seed):
+    def sphere_of(m, rng):
+        st = pools[m].strokes
+        k = int(rng.integers(0, len(st.radius)))
+        return (st.centre[k], float(st.radius[k]), int(rng.integers(1, 256)))
+
+    def lasso_of(m, rng):
+        L = pools[m].lassos[int(rng.integers(0, len(pools[m].lassos)))]
+        return (L.cam, L.poly, int(rng.integers(1, 256)))
+
+    return serve.poisson_requests(len(pools), rate, duration, seed, sphere_of=sphere_of, lasso_of=lasso_of)
+
+
+def test_served_results_equal_requests_applied_alone():
+    models, pools = served_models(8)
+    footprint = []
+    probe = serve.Server(models[:1], hbm_budget_bytes=1 << 40)
+    one = probe.slots[0].bytes
+    del probe
+    torch.cuda.empty_cache()
+    srv = serve.Server(models, hbm_budget_bytes=int(3.5 * one))     # only a few models fit at once
+    reqs = trace(pools, rate=4000.0, duration=0.3, seed=11)
+    srv.run(reqs)
+    assert all(r.t_done >= r.t_arrive for r in reqs)
+    assert srv.spills > 0 and srv.admissions > 0 and srv.epochs > 1
+    alone_layers, alone_results = serve.replay_alone(models, reqs)
+    for mi, ls in alone_layers.items():
+        got = srv.layers_of(mi)
+        for a, b in zip(ls, got):
+            assert torch.equal(a, b), f"model {mi}: served layers differ from the requests applied alone"
+    n_q = 0
+    for i, r in enumerate(reqs):
+        if r.kind == serve.QUERY:
+            n_q += 1
+            ec, ea = alone_results[i]
+            assert np.array_equal(r.result[0], ec) and np.array_equal(r.result[1], ea)
+    assert n_q > 0

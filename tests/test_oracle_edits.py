@@ -296,3 +296,53 @@ def test_lasso_vertical_edges_are_half_open():
         lay = np.zeros(a.tri.shape, np.uint8)
         oracle.select_lasso(a, lay, M, dmap, rect, 1)
         assert lay[j, i] == want
+
+
+@pytest.mark.parametrize("rad,thick", [(1, 1), (2, 1), (1, 3), (3, 2), (8, 8)])
+def test_texture_padding_matches_square_kernel_dilation(rad, thick):
+    """Padding (Section 4.3.2) restated with morphology: after each stroke, the uncovered texels
+    within `thick` of an island (square kernel) and within `rad` of a texel the stroke selected get
+    its label -- computed here with scipy's maximum filter."""
+    from scipy.ndimage import maximum_filter
+    m = synth.vessel_charts(200, 100, 25, 10, 256, seed=5)
+    a = oracle.Atlas(m, 256, 256)
+    cov = a.covered()
+    st = synth.sphere_strokes(m, 6, 8, 0.03, 0.25, 1, 200)
+    recs = oracle.sphere_records(a.mn, a.S, st.centre, st.radius, st.label)
+    recs["flags"] = oracle.pad_flags(rad, thick)
+    init = np.random.default_rng(2).integers(0, 3, size=cov.shape).astype(np.uint8)
+    exp = init.copy()
+    q = np.stack([a.px, a.py, a.pz], -1).astype(np.int64)
+    ring = ~cov & maximum_filter(cov, size=2 * thick + 1, mode="constant", cval=False)
+    exp_pad = []
+    for s in recs:
+        hit = cov & (((q - np.array([s["cx"], s["cy"], s["cz"]])) ** 2).sum(-1) <= s["r2"])
+        pad = ring & maximum_filter(hit, size=2 * rad + 1, mode="constant", cval=False)
+        exp[hit] = s["label"]
+        exp[pad] = s["label"]
+        exp_pad.append(int(pad.sum()))
+    got = init.copy()
+    hits, padded = oracle.select_sphere_2d(a, got, recs)
+    assert np.array_equal(got, exp)
+    assert padded.tolist() == exp_pad and sum(exp_pad) > 0
+
+
+def test_texture_padding_off_and_flag_checks():
+    m = synth.vessel_charts(200, 100, 25, 10, 256, seed=5)
+    a = oracle.Atlas(m, 256, 256)
+    st = synth.sphere_strokes(m, 4, 9, 0.05, 0.2, 1, 200)
+    recs = oracle.sphere_records(a.mn, a.S, st.centre, st.radius, st.label)
+    l1 = np.zeros(a.tri.shape, np.uint8)
+    l2 = np.zeros(a.tri.shape, np.uint8)
+    oracle.select_sphere(a, l1, recs)
+    _, padded = oracle.select_sphere_2d(a, l2, recs)
+    assert np.array_equal(l1, l2) and padded.sum() == 0
+    for bad in (9, 9 << 4, 1 << 8):
+        r = recs.copy()
+        r["flags"] = bad
+        with pytest.raises(oracle.OracleError):
+            oracle.select_sphere_2d(a, np.zeros(a.tri.shape, np.uint8), r)
+    r = recs.copy()
+    r["flags"] = oracle.pad_flags(1, 1)
+    with pytest.raises(oracle.OracleError):       # the flat form has no texture layout for padding
+        oracle.select_sphere(a, np.zeros(a.tri.shape, np.uint8), r)
