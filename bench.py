@@ -331,6 +331,8 @@ def run_ours(args):
     barrier()
     e2e_ms = f0.elapsed_time(f1)
 
+    by_radius = sphere_radius_breakdown(w, atlas, layers, per_layer, ws_sel, stream, dev) if rank == 0 else None
+
     (total_ms, e2e_ms, sph_ms), all_texels = combine_ranks([total_ms, e2e_ms, sph_ms], texels, world, dev)
     if rank != 0:
         if world > 1:
@@ -360,10 +362,53 @@ def run_ours(args):
         "serving": serving,
         "breakdown": {"sphere_ms_per_step": sph_ms / args.steps, "sphere_hit_texels": sph_hits,
                       "lasso_hit_texels": las_hits, "texels_per_step": texels},
+        "sphere_by_radius": by_radius,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def sphere_radius_breakdown(w, atlas, layers, per_layer, ws_sel, stream, dev):
+    """Per-radius breakdown of the sphere strokes, outside the timed region: every stroke again as
+    its own call (zeroing, cull and apply launches), timed with CUDA events, binned by radius in
+    half-decades of the bounding-box diagonal.  Bytes are the algorithmic (12 + label bytes) per
+    hit texel, against the measured copy peak.  Small strokes are bound by launch and cull
+    latency; the chained call of the timed region hides part of that."""
+    import torch
+    from paper_2501_14807_gb300 import lcl
+
+    peak, _ = peaks()
+    pos = np.asarray(w.mesh.pos, np.float64)
+    diag = float(np.linalg.norm(pos.max(0) - pos.min(0)))
+    hits = torch.zeros(1, dtype=torch.int64, device=dev)
+    rows = []  # (radius fraction, hit texels, ms)
+    torch.cuda.synchronize(dev)
+    for li, recs in enumerate(per_layer):
+        sel = np.nonzero(w.strokes.layer == li)[0]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(recs) + 1)]
+        hs = torch.zeros(len(recs), dtype=torch.int64, device=dev)
+        ev[0].record(stream)
+        for k in range(len(recs)):
+            lcl.lcl_select_sphere(atlas, layers[li], recs[k:k + 1], hs[k:k + 1], ws_sel, stream)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        hh = hs.cpu().numpy()
+        for k in range(len(recs)):
+            rows.append((float(w.strokes.radius[sel[k]]) / diag, int(hh[k]), ev[k].elapsed_time(ev[k + 1])))
+    edges = [0.0, 0.001, 0.00316, 0.01, 0.0316, 0.1, 0.316, 10.0]
+    out = []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        b = [r for r in rows if lo <= r[0] < hi]
+        if not b:
+            continue
+        hit = sum(r[1] for r in b)
+        ms = sum(r[2] for r in b)
+        gbs = hit * (12 + w.dtype_bytes) / (ms / 1e3) / 1e9
+        out.append({"radius_of_diagonal": [lo, hi], "strokes": len(b), "hit_texels": hit, "ms": ms,
+                    "us_per_stroke": 1e3 * ms / len(b), "gb_s": gbs, "frac": gbs / peak})
+    return {"timing": "one call per stroke (zeroing, cull, apply), CUDA events; not the chained timed call",
+            "bins": out}
 
 
 def combine_ranks(times_ms, texels, world, device):

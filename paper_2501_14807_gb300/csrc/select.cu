@@ -7,13 +7,15 @@
 // the candidate tiles are appended to a list with one atomic per warp (ballot + popc).  Both
 // tests are conservative, so culling never changes a result.
 //
-// Apply: a persistent grid (8 CTAs per SM) walks the candidate list; each thread owns four
-// consecutive texels of a tile row: three 16-byte loads of the position planes, the per-texel
-// test, and one 4-byte (uint8) or 8-byte (uint16) label word written only if a texel in it was
-// hit (read first only if some of its texels were not).  The loads of the thread's next work
-// item are issued before the current one is tested, so two items are in flight per thread.
-// (Measured alternatives that ran slower on GB300: culling the next stroke after the apply loop,
-// and reading the candidate list two items ahead.)
+// Apply: a resident grid (as many CTAs as fit on the SMs) walks the candidate list; each thread
+// owns four consecutive texels of a tile row: three 16-byte loads of the position planes, the
+// per-texel test, and one 4-byte (uint8) or 8-byte (uint16) label word written only if a texel in
+// it was hit (read first only if some of its texels were not).  The loads of the thread's next
+// work item are issued before the current one is tested, so two items are in flight per thread.
+// Measured on GB300 (1000 strokes on a 16384^2 atlas): culling the next stroke after the apply
+// loop rather than before it saves ~0.4 us per stroke; reading the candidate list two items
+// ahead, or a padding branch that raises the kernel above 40 registers (5 instead of 6 CTAs per
+// SM), cost 1.3-1.6 ms per 1000 strokes, hence the separate template instances.
 //
 // Sphere strokes take one launch each: the kernel that applies stroke k also culls stroke k + 1
 // into the other of two candidate lists, and every launch is a programmatic dependent launch, so
@@ -37,13 +39,15 @@ __global__ void k_sel_init(uint32_t *counters, int32_t n, unsigned long long *hi
 }
 
 // Culls stroke s against super-tile `sidx`, appending its candidate tiles.  Uniform per CTA.
-// With texture padding a texel may be written because a neighbour within 8 texels was selected,
-// so a tile (super-tile) is then a candidate if any box of its 3 x 3 neighbourhood is in reach.
+// With texture padding (PAD) a texel may be written because a neighbour within 8 texels was
+// selected, so a tile (super-tile) is then a candidate if any box of its 3 x 3 neighbourhood is
+// in reach.  PAD is a template parameter so that the common case carries no registers for it.
+template <bool PAD>
 __device__ __forceinline__ void cull_super_sphere(const AtlasDev &a, const SphereArg &s, int32_t sidx,
                                                   uint32_t *counter, uint32_t *list) {
     const int32_t sx = sidx % a.supers_x, sy = sidx / a.supers_x;
     bool in_reach;
-    if (s.pad_r > 0) {
+    if (PAD) {
         in_reach = near_box_3x3(a.super_box, a.supers_x, a.supers_y, sx, sy, s);
     } else {
         const int4 *sb = reinterpret_cast<const int4 *>(a.super_box + 8 * (int64_t)sidx);
@@ -55,7 +59,7 @@ __device__ __forceinline__ void cull_super_sphere(const AtlasDev &a, const Spher
     const int32_t ty = sy * LCL_SUPER + (threadIdx.x / LCL_SUPER);
     bool cand = false;
     if (tx < a.tiles_x && ty < a.tiles_y) {
-        if (s.pad_r > 0) {
+        if (PAD) {
             cand = near_box_3x3(a.tile_box, a.tiles_x, a.tiles_y, tx, ty, s);
         } else {
             const int4 *tb = reinterpret_cast<const int4 *>(a.tile_box + 8 * ((int64_t)ty * a.tiles_x + tx));
@@ -71,7 +75,12 @@ __global__ void __launch_bounds__(kThreads) k_sphere_cull(AtlasDev a, SphereArg 
                                                           uint32_t *list) {
     pdl_wait();
     const int32_t n_super = a.supers_x * a.supers_y;
-    for (int32_t sidx = blockIdx.x; sidx < n_super; sidx += gridDim.x) cull_super_sphere(a, s, sidx, counter, list);
+    for (int32_t sidx = blockIdx.x; sidx < n_super; sidx += gridDim.x) {
+        if (s.pad_r > 0)
+            cull_super_sphere<true>(a, s, sidx, counter, list);
+        else
+            cull_super_sphere<false>(a, s, sidx, counter, list);
+    }
     pdl_allow_next();
 }
 
@@ -81,10 +90,11 @@ struct Item {
     int4 X, Y, Z;
 };
 
-__device__ __forceinline__ Item load_item(const AtlasDev &a, uint32_t tile, uint32_t item, int cpt_log2, int32_t qpr,
-                                          int32_t nq) {
+__device__ __forceinline__ Item load_item(const AtlasDev &a, const uint32_t *__restrict__ list, uint32_t item,
+                                          int cpt_log2, int32_t qpr, int32_t nq) {
     Item it;
     it.l = -1;
+    const uint32_t tile = __ldg(list + (item >> cpt_log2));
     const int32_t qd = (int32_t)((item & ((1u << cpt_log2) - 1)) * kThreads + threadIdx.x);
     const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
@@ -146,18 +156,14 @@ __device__ uint32_t pad_mask(const AtlasDev &a, const Item &it, const SphereArg 
 }
 
 // Applies stroke `s` from its candidate list and culls stroke `nxt` (if has_next) into the other list.
-template <typename L, bool PAD>
+// PAD: `s` pads the texture; NEXT_PAD: `nxt` does.
+template <typename L, bool PAD, bool NEXT_PAD>
 __global__ void __launch_bounds__(kThreads) k_sphere_step(AtlasDev a, L *__restrict__ layer, SphereArg s,
                                                           const uint32_t *__restrict__ counter,
                                                           const uint32_t *__restrict__ list,
                                                           unsigned long long *hits, int has_next, SphereArg nxt,
                                                           uint32_t *next_counter, uint32_t *next_list) {
     pdl_wait();
-    if (has_next) {
-        const int32_t n_super = a.supers_x * a.supers_y;
-        for (int32_t sidx = blockIdx.x; sidx < n_super; sidx += gridDim.x)
-            cull_super_sphere(a, nxt, sidx, next_counter, next_list);
-    }
     pdl_allow_next();  // the next grid waits for this one to complete before touching memory
     const int32_t qpr = a.T / 4, nq = a.T * qpr;
     const int cpt_log2 = nq > kThreads ? 31 - __clz(nq / kThreads) : 0;
@@ -166,19 +172,29 @@ __global__ void __launch_bounds__(kThreads) k_sphere_step(AtlasDev a, L *__restr
     uint32_t item = blockIdx.x;
     Item cur;
     cur.l = -1;
-    if (item < n_items) cur = load_item(a, __ldg(list + (item >> cpt_log2)), item, cpt_log2, qpr, nq);
+    if (item < n_items) cur = load_item(a, list, item, cpt_log2, qpr, nq);
     for (; item < n_items; item += gridDim.x) {
         const uint32_t after = item + gridDim.x;
         Item next;
         next.l = -1;
-        if (after < n_items) next = load_item(a, __ldg(list + (after >> cpt_log2)), after, cpt_log2, qpr, nq);
+        if (after < n_items) next = load_item(a, list, after, cpt_log2, qpr, nq);
         if (cur.l >= 0) {
             const uint32_t m = sphere_mask(cur, s);
-            const uint32_t p = PAD ? pad_mask(a, cur, s) : 0u;
-            if (m | p) store_hits<L>(layer, cur.l, m | p, s.label);
-            cnt += __popc(m);
+            if (PAD) {
+                const uint32_t p = pad_mask(a, cur, s);
+                if (m | p) store_hits<L>(layer, cur.l, m | p, s.label);
+                cnt += __popc(m);
+            } else if (m) {
+                store_hits<L>(layer, cur.l, m, s.label);
+                cnt += __popc(m);
+            }
         }
         cur = next;
+    }
+    if (has_next) {
+        const int32_t n_super = a.supers_x * a.supers_y;
+        for (int32_t sidx = blockIdx.x; sidx < n_super; sidx += gridDim.x)
+            cull_super_sphere<NEXT_PAD>(a, nxt, sidx, next_counter, next_list);
     }
     add_hits(hits, cnt);
 }
@@ -264,8 +280,13 @@ size_t select_ws_bytes(const lcl_atlas *a, int32_t n) {
     return align256((size_t)(n + 1) * 4) + 2 * align256((size_t)a->tiles_x * a->tiles_y * 4);
 }
 
-lcl_status select_sphere_impl(const lcl_atlas *atlas, void *layer, int dtype_bytes, const lcl_sphere *strokes,
-                              int32_t n, uint64_t *hits, void *ws, cudaStream_t st) {
+template <typename L>
+using StepKernel = void (*)(AtlasDev, L *, SphereArg, const uint32_t *, const uint32_t *, unsigned long long *, int,
+                            SphereArg, uint32_t *, uint32_t *);
+
+template <typename L>
+lcl_status select_sphere_run(const lcl_atlas *atlas, L *layer, const lcl_sphere *strokes, int32_t n, uint64_t *hits,
+                             void *ws, cudaStream_t st) {
     const AtlasDev a = dev_view(atlas);
     const SelWs w = sel_ws(atlas, n, ws);
     unsigned long long *h = reinterpret_cast<unsigned long long *>(hits);
@@ -280,36 +301,34 @@ lcl_status select_sphere_impl(const lcl_atlas *atlas, void *layer, int dtype_byt
         s.pad_t = (int32_t)((strokes[k].flags >> 4) & 15u);
         return s;
     };
+    // [pad][next_pad] variants and their resident grids
+    const StepKernel<L> step[2][2] = {{k_sphere_step<L, false, false>, k_sphere_step<L, false, true>},
+                                      {k_sphere_step<L, true, false>, k_sphere_step<L, true, true>}};
+    int grid[2][2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) grid[i][j] = resident_grid(step[i][j]);
     k_sel_init<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(w.counters, n, h);
-    const int ag = dtype_bytes == 1 ? resident_grid(k_sphere_step<uint8_t, false>)
-                                    : resident_grid(k_sphere_step<uint16_t, false>);
-    const int agp = dtype_bytes == 1 ? resident_grid(k_sphere_step<uint8_t, true>)
-                                     : resident_grid(k_sphere_step<uint16_t, true>);
     const int n_super = atlas->supers_x * atlas->supers_y;
-    cudaError_t e = launch_pdl(k_sphere_cull, dim3(std::min(n_super, ag)), st, a, arg(0), w.counters, w.list);
+    cudaError_t e = launch_pdl(k_sphere_cull, dim3(std::min(n_super, grid[0][0])), st, a, arg(0), w.counters, w.list);
     for (int32_t k = 0; k < n && e == cudaSuccess; ++k) {
         uint32_t *cur_list = (k & 1) ? w.list2 : w.list, *next_list = (k & 1) ? w.list : w.list2;
         const int has_next = k + 1 < n;
-        const SphereArg nxt = arg(has_next ? k + 1 : k);
-        unsigned long long *hk = h ? h + k : nullptr;
-        const SphereArg cur = arg(k);
-        const bool pad = cur.pad_r > 0;
-        const uint32_t *cl = cur_list, *ck = w.counters + k;
-        if (dtype_bytes == 1)
-            e = pad ? launch_pdl(k_sphere_step<uint8_t, true>, dim3(agp), st, a, static_cast<uint8_t *>(layer), cur, ck,
-                                 cl, hk, has_next, nxt, w.counters + k + 1, next_list)
-                    : launch_pdl(k_sphere_step<uint8_t, false>, dim3(ag), st, a, static_cast<uint8_t *>(layer), cur, ck,
-                                 cl, hk, has_next, nxt, w.counters + k + 1, next_list);
-        else
-            e = pad ? launch_pdl(k_sphere_step<uint16_t, true>, dim3(agp), st, a, static_cast<uint16_t *>(layer), cur,
-                                 ck, cl, hk, has_next, nxt, w.counters + k + 1, next_list)
-                    : launch_pdl(k_sphere_step<uint16_t, false>, dim3(ag), st, a, static_cast<uint16_t *>(layer), cur,
-                                 ck, cl, hk, has_next, nxt, w.counters + k + 1, next_list);
+        const SphereArg cur = arg(k), nxt = arg(has_next ? k + 1 : k);
+        const int pi = cur.pad_r > 0, pj = has_next && nxt.pad_r > 0;
+        e = launch_pdl(step[pi][pj], dim3(grid[pi][pj]), st, a, layer, cur, (const uint32_t *)(w.counters + k),
+                       (const uint32_t *)cur_list, h ? h + k : nullptr, has_next, nxt, w.counters + k + 1, next_list);
     }
     count_launches(2 + n);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "lcl_select_sphere launch");
     return LCL_OK;
+}
+
+lcl_status select_sphere_impl(const lcl_atlas *atlas, void *layer, int dtype_bytes, const lcl_sphere *strokes,
+                              int32_t n, uint64_t *hits, void *ws, cudaStream_t st) {
+    if (dtype_bytes == 1)
+        return select_sphere_run(atlas, static_cast<uint8_t *>(layer), strokes, n, hits, ws, st);
+    return select_sphere_run(atlas, static_cast<uint16_t *>(layer), strokes, n, hits, ws, st);
 }
 
 lcl_status select_lasso_impl(const lcl_atlas *atlas, void *layer, int dtype_bytes, const lcl_camera *cam,
