@@ -474,7 +474,8 @@ def run_batch(args):
 
     batch = lcl.Batch(list(zip(models, layers)), queues)
 
-    def batched():
+    def batched_default():
+        batch.config = None
         lcl.lcl_batch_edit(batch, stream)
 
     def timed(fn, steps):
@@ -493,14 +494,34 @@ def run_batch(args):
     torch.cuda.synchronize(dev)
     ref = [l.clone() for l in layers]
     hits = int(sum(int(h.sum().item()) for h in hit_bufs))
+    l0 = lcl.lcl_kernel_launches()
     seq_ms = timed(sequential, args.steps)
+    seq_launches = (lcl.lcl_kernel_launches() - l0) // args.steps
     for l in layers:
         l.zero_()
+    # default launch shape, then the autotuner on the uploaded batch, then one CUDA graph of the
+    # tuned launch; every timed step uploads the descriptors and replays the graph
+    for _ in range(args.warmup):
+        batched_default()
+        torch.cuda.synchronize(dev)
+    def_ms = timed(batched_default, args.steps)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    lcl.lcl_batch_upload(batch, stream)
+    upload_host_ms = 1e3 * (time.perf_counter() - t0)
+    tuned, tune_ms = lcl.lcl_batch_tune(batch, stream, reps=2)
+    graph = lcl.BatchGraph(batch.limits, tuned, batch.workspace)
+
+    def batched():
+        lcl.lcl_batch_upload(batch, stream)
+        graph.replay()
+
     for _ in range(args.warmup):
         batched()
         torch.cuda.synchronize(dev)
     clocks = Clocks(0)
     clocks.start()
+    time.sleep(0.3)
     bat_ms = timed(batched, args.steps)
     clk = clocks.stop()
     same = all(torch.equal(r, l) for r, l in zip(ref, layers))
@@ -510,11 +531,16 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": f"batching: {len(models)} models ({sum(b.mesh.n_tri for b in bms)} triangles, "
                                    f"atlases 512^2-4096^2 u8), {n_strokes} queued strokes (48 sphere + 16 lasso "
-                                   f"per model)", "mode": "batched launch vs per-model per-stroke calls"},
-            "batched": {"ms": bat_ms, "gtexels_s": hits / (bat_ms / 1e3) / 1e9},
-            "per_stroke_calls": {"ms": seq_ms, "gtexels_s": hits / (seq_ms / 1e3) / 1e9,
-                                 "launches": lcl.lcl_kernel_launches()},
-            "speedup": seq_ms / bat_ms, "identical_results": bool(same), "hit_texels": hits, "clocks": clk}
+                                   f"per model)", "mode": "batched launch (descriptor upload + CUDA graph replay "
+                                                          "of the tuned shape) vs per-model per-stroke calls"},
+            "batched": {"ms": bat_ms, "gtexels_s": hits / (bat_ms / 1e3) / 1e9, "config": tuned.as_dict(),
+                        "graph": True, "launches": 3},
+            "batched_default_shape": {"ms": def_ms, "config": lcl.batch_config().as_dict(), "graph": False},
+            "upload_host_ms": upload_host_ms,
+            "autotune": {"best_ms": tune_ms, "candidates": "threads 64/128/256 x split 1/2/4/8 x CTAs/SM all/half"},
+            "per_stroke_calls": {"ms": seq_ms, "gtexels_s": hits / (seq_ms / 1e3) / 1e9, "launches": int(seq_launches)},
+            "speedup": seq_ms / bat_ms, "identical_results": bool(same), "hit_texels": hits, "gpu_launches": 3,
+            "clocks": clk}
     print(json.dumps(line), flush=True)
 
 

@@ -273,31 +273,74 @@ typedef struct {
     int32_t _pad;
 } lcl_batch_lasso;
 
-/* Device workspace and host staging bytes for a batch of these models and counts. */
-size_t lcl_batch_workspace_bytes(const lcl_batch_model *models, int32_t n_models, int32_t n_strokes,
-                                 int32_t n_lassos);
-size_t lcl_batch_staging_bytes(const lcl_batch_model *models, int32_t n_models, int32_t n_strokes,
-                               int32_t n_lassos);
+/* Capacity of a batch workspace: every batch run on it has at most `models` models, `strokes`
+ * strokes, `lassos` lassos, and its models' atlases have at most `supers` super-tiles and `tiles`
+ * tiles in total.  The workspace layout and the launch shape depend only on the limits and the
+ * config, and the kernels read the actual counts from the workspace, so one launch (or one
+ * captured CUDA graph) serves every batch uploaded within the same limits. */
+typedef struct {
+    int32_t models, strokes, lassos, _pad;
+    int64_t supers, tiles;
+} lcl_batch_limits;
 
-/* Edits many models at once: every model's queued strokes are applied to its layer in queue order,
- * with results identical to calling lcl_select_sphere / lcl_select_lasso once per stroke in that
- * order (Section 4.3.1 applied per stroke; batching is a serving-side schedule the paper does not
- * discuss).  One cull launch gives every touched tile of every model a mask of the strokes that can
- * reach it; one persistent apply launch loads each such tile's positions once and runs its masked
- * strokes in order.  Models must be distinct layers (two models writing one layer race).
- * host_staging (lcl_batch_staging_bytes, host memory) receives an image of the descriptors that is
- * copied to the workspace on `stream`; with pinned memory the copy is asynchronous and the staging
- * must stay untouched until the stream has passed it.  Depth maps must be rendered before the call.
- * Errors: as lcl_select_sphere / lcl_select_lasso; LCL_ERR_UNSUPPORTED for more than
- * LCL_BATCH_MAX_STROKES strokes per model. */
-lcl_status lcl_batch_edit(const lcl_batch_model *models, int32_t n_models, const lcl_batch_stroke *strokes,
+/* Launch shape of the batched apply (all zero = the default {256, 0, 1}):
+ *   threads      threads per CTA: 64, 128 or 256;
+ *   ctas_per_sm  CTAs per SM, 0 = as many as fit, else 1..32 (capped at what fits);
+ *   split        parts each (model, tile) work item is cut into (contiguous rows of the tile),
+ *                1, 2, 4 or 8; a part is the unit a CTA takes from the work queue.
+ * Results do not depend on it. */
+typedef struct {
+    int32_t threads, ctas_per_sm, split, _pad;
+} lcl_batch_config;
+
+/* The limits of exactly this batch (sums over its models).  Errors: LCL_ERR_INVALID_ARG. */
+lcl_status lcl_batch_limits_of(const lcl_batch_model *models, int32_t n_models, int32_t n_strokes, int32_t n_lassos,
+                               lcl_batch_limits *out);
+/* Device workspace and host staging bytes for a batch workspace of these limits (0 if invalid). */
+size_t lcl_batch_workspace_bytes(const lcl_batch_limits *limits);
+size_t lcl_batch_staging_bytes(const lcl_batch_limits *limits);
+
+/* Checks a batch against the limits, packs its model, stroke and lasso descriptors into
+ * host_staging (lcl_batch_staging_bytes, host memory) and copies them to the workspace on
+ * `stream`; with pinned memory the copy is asynchronous and the staging must stay untouched until
+ * the stream has passed it.  No kernel runs.  Models must be distinct layers (two models writing
+ * one layer race); depth maps must be rendered before the batch is launched.
+ * Errors: LCL_ERR_INVALID_ARG (bad descriptors, counts above the limits), LCL_ERR_UNSUPPORTED (more
+ * than LCL_BATCH_MAX_STROKES strokes for a model, padded sphere strokes, lassos outside 3..64
+ * vertices), LCL_ERR_OUT_OF_MEMORY (workspace or staging smaller than required), LCL_ERR_CUDA. */
+lcl_status lcl_batch_upload(const lcl_batch_limits *limits, const lcl_batch_model *models, int32_t n_models,
+                            const lcl_batch_stroke *strokes, int32_t n_strokes, const lcl_batch_lasso *lassos,
+                            int32_t n_lassos, void *workspace, size_t ws_bytes, void *host_staging,
+                            size_t staging_bytes, lcl_stream stream);
+
+/* Edits the models of the batch last uploaded to `workspace`: every model's queued strokes are
+ * applied to its layer in queue order, with results identical to calling lcl_select_sphere /
+ * lcl_select_lasso once per stroke in that order (Section 4.3.1 applied per stroke; batching is a
+ * serving-side schedule the paper does not discuss).  One cull launch gives every touched tile of
+ * every model a mask of the strokes that can reach it; one persistent apply launch takes
+ * (model, tile part) units from a work queue, loads each texel's position once and evaluates its
+ * masked strokes from the newest down, stopping at the first that selects it (the label the
+ * sequence leaves).  No host-to-device copy and a launch shape fixed by (limits, config): the call
+ * can be captured in a CUDA graph and replayed after later uploads.  Launching a batch again
+ * repeats its strokes, which leaves every label as it is.  config may be NULL (default).
+ * Errors: LCL_ERR_INVALID_ARG (limits, config, workspace), LCL_ERR_CUDA. */
+lcl_status lcl_batch_launch(const lcl_batch_limits *limits, const lcl_batch_config *config, void *workspace,
+                            size_t ws_bytes, lcl_stream stream);
+
+/* lcl_batch_upload followed by lcl_batch_launch. */
+lcl_status lcl_batch_edit(const lcl_batch_limits *limits, const lcl_batch_config *config,
+                          const lcl_batch_model *models, int32_t n_models, const lcl_batch_stroke *strokes,
                           int32_t n_strokes, const lcl_batch_lasso *lassos, int32_t n_lassos, void *workspace,
                           size_t ws_bytes, void *host_staging, size_t staging_bytes, lcl_stream stream);
 
-/* Launches the kernels of the last lcl_batch_edit on this workspace and staging again, reading the
- * descriptors already on the device (no host-to-device copy, so it can be captured in a CUDA graph
- * and replayed; re-running a batch repeats its strokes). */
-lcl_status lcl_batch_launch(void *workspace, const void *host_staging, lcl_stream stream);
+/* Autotuner: launches the batch last uploaded to `workspace` under each candidate launch shape
+ * (threads 64/128/256 x split 1/2/4/8 x CTAs per SM as many as fit / half of that), `reps` timed
+ * launches each after one warm-up, timed with CUDA events on `stream`, and writes the fastest
+ * shape and its mean time per launch.  Synchronises the stream.  The batch's strokes are applied
+ * (1 + reps) x candidates times, which leaves the same labels as one application.
+ * Errors: LCL_ERR_INVALID_ARG, LCL_ERR_CUDA. */
+lcl_status lcl_batch_tune(const lcl_batch_limits *limits, void *workspace, size_t ws_bytes, int32_t reps,
+                          lcl_stream stream, lcl_batch_config *best, float *best_ms);
 
 /* ---- layer operations --------------------------------------------------- */
 

@@ -8,11 +8,21 @@
 //                  (queue order = bit order) whose conservative box test can reach the tile; the
 //                  super-tile's mask is computed first and only its strokes are tested per tile;
 //                  tiles with a non-empty mask become work items (model, tile, mask);
-//   k_batch_apply  walks the items; a thread loads its four texels' positions once, runs the
-//                  masked strokes in ascending order (a later hit overwrites an earlier label in
-//                  registers), and writes each label word once.
-// Each texel belongs to one item and one thread, so no two threads write a texel and the order
-// per texel is the queue order: the result is bit-identical to sequential single-stroke calls.
+//   k_batch_apply  takes (item, part) units from a work queue (one atomic per unit and CTA); a
+//                  thread loads its four texels' positions once and evaluates the masked strokes
+//                  from the newest down: the first stroke that selects a texel is the last one
+//                  sequential application would have written there, so the texel is final and
+//                  the thread stops once its four texels are final (or no stroke is left); each
+//                  label word is written once.
+// Each texel belongs to one unit and one thread, so no two threads write a texel, and the label a
+// texel receives is that of the newest stroke selecting it: the result is bit-identical to
+// sequential single-stroke calls.
+//
+// The host uploads compact descriptors (models, strokes, each lasso's camera and polygon);
+// k_batch_prep builds the lassos' culling boxes and y-band edge lists on the device, one warp per
+// lasso.  Workspace layout and launch shape depend only on the limits (capacities) and the config,
+// and the kernels read the batch's counts from the workspace header, so the launch is independent
+// of the batch's contents: it can be captured once in a CUDA graph and replayed after each upload.
 #include <cstring>
 
 #include "select_common.cuh"
@@ -34,9 +44,20 @@ struct BStroke {
     SphereArg sphere;
 };
 
-struct BLasso {
+struct BLasso {  // built on the device by k_batch_prep
     LassoArg arg;
     const float *depth;
+};
+
+struct BLassoIn {  // what the host uploads per lasso
+    float m[16];
+    int32_t w_s, h_s;
+    const float *depth;
+    float poly[2 * LCL_MAX_LASSO_VERTICES];
+    int32_t nv;
+    uint32_t label;
+    float bias;
+    int32_t pad;
 };
 
 struct BItem {
@@ -44,27 +65,32 @@ struct BItem {
     unsigned long long mask;
 };
 
-// Workspace header (first 256 bytes), uploaded with the descriptors.
+// Workspace header (first 256 bytes), uploaded with the descriptors; the counters are reset by
+// k_batch_prep at every launch.
 struct BHdr {
     int32_t n_models, n_strokes, n_lassos, n_supers;
-    int64_t n_tiles;          // capacity of the item list
-    unsigned int n_items;     // written by k_batch_cull
-    int32_t pad;
+    unsigned int n_items;          // written by k_batch_cull
+    unsigned int pad;
+    unsigned long long next_unit;  // work queue of k_batch_apply
 };
 
+// Workspace: [hdr | models | strokes | lasso inputs | super-tile -> model] is uploaded (the
+// staging holds its image); [lassos | items] is written by the kernels.
 struct BLayout {
-    size_t hdr, models, strokes, lassos, super_model, items, total;
+    size_t hdr, models, strokes, lasso_in, super_model, upload, lassos, items, total;
 };
 
-BLayout b_layout(int32_t n_models, int32_t n_strokes, int32_t n_lassos, int64_t n_supers, int64_t n_tiles) {
+BLayout b_layout(const lcl_batch_limits &lim) {
     BLayout L;
     L.hdr = 0;
     L.models = align256(sizeof(BHdr));
-    L.strokes = L.models + align256((size_t)n_models * sizeof(BModel));
-    L.lassos = L.strokes + align256((size_t)std::max(n_strokes, 1) * sizeof(BStroke));
-    L.super_model = L.lassos + align256((size_t)std::max(n_lassos, 1) * sizeof(BLasso));
-    L.items = L.super_model + align256((size_t)std::max<int64_t>(n_supers, 1) * 4);
-    L.total = L.items + align256((size_t)std::max<int64_t>(n_tiles, 1) * sizeof(BItem));
+    L.strokes = L.models + align256((size_t)std::max(lim.models, 1) * sizeof(BModel));
+    L.lasso_in = L.strokes + align256((size_t)std::max(lim.strokes, 1) * sizeof(BStroke));
+    L.super_model = L.lasso_in + align256((size_t)std::max(lim.lassos, 1) * sizeof(BLassoIn));
+    L.upload = L.super_model + align256((size_t)std::max<int64_t>(lim.supers, 1) * 4);
+    L.lassos = L.upload;
+    L.items = L.lassos + align256((size_t)std::max(lim.lassos, 1) * sizeof(BLasso));
+    L.total = L.items + align256((size_t)std::max<int64_t>(lim.tiles, 1) * sizeof(BItem));
     return L;
 }
 
@@ -74,7 +100,44 @@ __device__ __forceinline__ bool stroke_may_touch(const BStroke &st, const BLasso
     return box_may_touch(lassos[st.lasso].arg, lo, hi, lassos[st.lasso].depth);
 }
 
-__global__ void k_batch_init(BHdr *hdr) { hdr->n_items = 0; }
+constexpr int kPrepWarps = kThreads / 32;  // lassos per CTA of k_batch_prep
+static_assert(kBands == 32, "k_batch_prep gives each y-band one lane");
+
+// Resets the work counters and builds every lasso's argument, one warp per lasso: lane 0 the
+// head (bounding boxes, band mapping), then lane b counts and lists the edges of band b (the
+// same predicate, in the same edge order, as the host builder).
+__global__ void __launch_bounds__(kThreads) k_batch_prep(BHdr *hdr, const BLassoIn *__restrict__ in,
+                                                         BLasso *__restrict__ out) {
+    pdl_allow_next();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        hdr->n_items = 0;
+        hdr->next_unit = 0;
+    }
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * kPrepWarps + (int)(threadIdx.x / 32);
+    if (j >= hdr->n_lassos) return;  // uniform over the warp
+    const BLassoIn &L = in[j];
+    LassoArg &p = out[j].arg;
+    if (lane == 0) {
+        lasso_arg_head(p, L.m, L.w_s, L.h_s, L.poly, L.nv, L.label, L.bias);
+        out[j].depth = L.depth;
+    }
+    __syncwarp();
+    const double bh = lasso_band_height(p);
+    const int nv = p.nv;
+    int c = 0;
+    for (int e = 0; e < nv; ++e) c += lasso_band_has(p, lane, e, bh) ? 1 : 0;
+    int incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    int k = incl - c;
+    p.band_off[lane] = (uint16_t)k;
+    if (lane == 31) p.band_off[kBands] = (uint16_t)incl;
+    for (int e = 0; e < nv; ++e)
+        if (lasso_band_has(p, lane, e, bh)) p.band_edge[k++] = (uint8_t)e;
+}
 
 __global__ void __launch_bounds__(kThreads) k_batch_cull(const BHdr *__restrict__ hdr, const BModel *__restrict__ models,
                                                          const BStroke *__restrict__ strokes,
@@ -160,14 +223,16 @@ __device__ __forceinline__ void store_labels<uint16_t>(uint16_t *layer, int64_t 
     *p = make_uint2((o.x & ~lo) | (v0 & lo), (o.y & ~hi) | (v1 & hi));
 }
 
+// Quads [q0, q1) of a work item's tile (quad = 4 consecutive texels of a tile row, row-major in
+// the tile), one per thread per pass.
 template <typename L>
-__device__ __forceinline__ void apply_item(const BModel &M, const BItem &it, const BStroke *__restrict__ strokes,
-                                           const BLasso *__restrict__ lassos) {
+__device__ __forceinline__ void apply_part(const BModel &M, const BItem &it, int32_t q0, int32_t q1,
+                                           const BStroke *__restrict__ strokes, const BLasso *__restrict__ lassos) {
     const AtlasDev &a = M.a;
     L *layer = static_cast<L *>(M.layer);
     const int32_t tx = it.tile % a.tiles_x, ty = it.tile / a.tiles_x;
-    const int32_t qpr = a.T / 4, nq = a.T * qpr;
-    for (int32_t qd = threadIdx.x; qd < nq; qd += kThreads) {
+    const int32_t qpr = a.T / 4;
+    for (int32_t qd = q0 + (int32_t)threadIdx.x; qd < q1; qd += (int32_t)blockDim.x) {
         const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
         if (x >= a.w || y >= a.h) continue;
         const int64_t l = (int64_t)y * a.w + x;
@@ -175,44 +240,74 @@ __device__ __forceinline__ void apply_item(const BModel &M, const BItem &it, con
         const int4 Y = __ldg(reinterpret_cast<const int4 *>(a.py + l));
         const int4 Z = __ldg(reinterpret_cast<const int4 *>(a.pz + l));
         const int32_t xs[4] = {X.x, X.y, X.z, X.w}, ys[4] = {Y.x, Y.y, Y.z, Y.w}, zs[4] = {Z.x, Z.y, Z.z, Z.w};
-        uint32_t lab[4] = {0u, 0u, 0u, 0u}, hit = 0u;
-        for (unsigned long long m = it.mask; m; m &= m - 1) {
-            const BStroke &st = strokes[M.s0 + __ffsll((long long)m) - 1];
+        // uncovered texels (x = INT32_MIN) are never selected: they start final
+        uint32_t open = 0u;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                bool h;
-                if (st.kind == LCL_STROKE_SPHERE) {
-                    // uncovered texels hold x = INT32_MIN and never test as hit (see select.cu)
+        for (int k = 0; k < 4; ++k) open |= (xs[k] != INT32_MIN ? 1u : 0u) << k;
+        uint32_t lab[4] = {0u, 0u, 0u, 0u}, hit = 0u;
+        for (unsigned long long m = it.mask; m && open; ) {
+            const int si = 63 - __clzll((long long)m);  // newest stroke left
+            m &= ~(1ull << si);
+            const BStroke &st = strokes[M.s0 + si];
+            uint32_t sel = 0u;
+            if (st.kind == LCL_STROKE_SPHERE) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
                     const int64_t dx = (int64_t)xs[k] - st.sphere.cx, dy = (int64_t)ys[k] - st.sphere.cy;
                     const int64_t dz = (int64_t)zs[k] - st.sphere.cz;
-                    h = dx * dx + dy * dy + dz * dz <= st.sphere.r2;
-                } else {
-                    const BLasso &ls = lassos[st.lasso];
-                    h = lasso_hit(ls.arg, ls.arg, ls.depth, xs[k], ys[k], zs[k]);
+                    sel |= (dx * dx + dy * dy + dz * dz <= st.sphere.r2 ? 1u : 0u) << k;
                 }
-                if (h) {
-                    lab[k] = st.kind == LCL_STROKE_SPHERE ? st.sphere.label : lassos[st.lasso].arg.label;
-                    hit |= 1u << k;
+                sel &= open;
+                if (sel) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (sel & (1u << k)) lab[k] = st.sphere.label;
                 }
+            } else {
+                const BLasso &ls = lassos[st.lasso];
+#pragma unroll 1
+                for (int k = 0; k < 4; ++k) {  // selects, not a runtime index into the arrays
+                    if (!(open & (1u << k))) continue;
+                    const int32_t qx = k == 0 ? X.x : k == 1 ? X.y : k == 2 ? X.z : X.w;
+                    const int32_t qy = k == 0 ? Y.x : k == 1 ? Y.y : k == 2 ? Y.z : Y.w;
+                    const int32_t qz = k == 0 ? Z.x : k == 1 ? Z.y : k == 2 ? Z.z : Z.w;
+                    if (lasso_hit(ls.arg, ls.arg, ls.depth, qx, qy, qz)) sel |= 1u << k;
+                }
+                const uint32_t label = ls.arg.label;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (sel & (1u << k)) lab[k] = label;
             }
+            hit |= sel;
+            open &= ~sel;
         }
         if (hit) store_labels<L>(layer, l, hit, lab);
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_batch_apply(const BModel *__restrict__ models,
-                                                          const BStroke *__restrict__ strokes,
-                                                          const BLasso *__restrict__ lassos,
-                                                          const BItem *__restrict__ items,
-                                                          const unsigned int *__restrict__ n_items) {
+__global__ void __launch_bounds__(256, 3) k_batch_apply(const BHdr *__restrict__ hdr, const BModel *__restrict__ models,
+                                                     const BStroke *__restrict__ strokes,
+                                                     const BLasso *__restrict__ lassos,
+                                                     const BItem *__restrict__ items, unsigned long long *next_unit,
+                                                     int32_t split) {
     pdl_wait();
     pdl_allow_next();
-    const unsigned int n = *n_items;
-    for (unsigned int i = blockIdx.x; i < n; i += gridDim.x) {
-        const BItem it = items[i];
+    __shared__ unsigned long long s_unit;
+    const unsigned long long n_units = (unsigned long long)hdr->n_items * (unsigned)split;
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(next_unit, 1ull);
+        __syncthreads();
+        const unsigned long long u = s_unit;
+        __syncthreads();
+        if (u >= n_units) break;  // uniform over the CTA
+        const BItem it = items[u / (unsigned)split];
+        const int32_t part = (int32_t)(u % (unsigned)split);
         const BModel &M = models[it.model];
-        if (M.dtype_bytes == 1) apply_item<uint8_t>(M, it, strokes, lassos);
-        else apply_item<uint16_t>(M, it, strokes, lassos);
+        const int32_t nq = M.a.T * (M.a.T / 4), per = nq / split;  // nq is a power of 2 >= 16
+        if (M.dtype_bytes == 1)
+            apply_part<uint8_t>(M, it, part * per, (part + 1) * per, strokes, lassos);
+        else
+            apply_part<uint16_t>(M, it, part * per, (part + 1) * per, strokes, lassos);
     }
 }
 
@@ -281,88 +376,120 @@ lcl_status check_batch(const lcl_batch_model *models, int32_t n_models, const lc
     return LCL_OK;
 }
 
-struct LaunchInfo {  // what lcl_batch_launch needs on the host, kept at the start of the staging
-    int32_t n_models, n_strokes, n_lassos, n_supers;
-    int64_t n_tiles;
-    int64_t ws_bytes;
+bool limits_ok(const lcl_batch_limits *lim) {
+    return lim && lim->models >= 0 && lim->strokes >= 0 && lim->lassos >= 0 && lim->supers >= 0 &&
+           lim->supers <= INT32_MAX && lim->tiles >= 0 && lim->tiles <= (int64_t)UINT32_MAX;
+}
+
+bool config_ok(const lcl_batch_config &c) {
+    return (c.threads == 64 || c.threads == 128 || c.threads == 256) && c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32 &&
+           (c.split == 1 || c.split == 2 || c.split == 4 || c.split == 8);
+}
+
+lcl_batch_config default_config() {
+    lcl_batch_config c;
+    std::memset(&c, 0, sizeof(c));
+    c.threads = 256;
+    c.ctas_per_sm = 0;
+    c.split = 1;
+    return c;
+}
+
+struct BPtrs {
+    BHdr *hdr;
+    const BModel *models;
+    const BStroke *strokes;
+    const BLassoIn *lasso_in;
+    BLasso *lassos;
+    const uint32_t *super_model;
+    BItem *items;
 };
+
+BPtrs b_ptrs(const BLayout &L, void *ws) {
+    char *base = static_cast<char *>(ws);
+    BPtrs p;
+    p.hdr = reinterpret_cast<BHdr *>(base + L.hdr);
+    p.models = reinterpret_cast<const BModel *>(base + L.models);
+    p.strokes = reinterpret_cast<const BStroke *>(base + L.strokes);
+    p.lasso_in = reinterpret_cast<const BLassoIn *>(base + L.lasso_in);
+    p.lassos = reinterpret_cast<BLasso *>(base + L.lassos);
+    p.super_model = reinterpret_cast<const uint32_t *>(base + L.super_model);
+    p.items = reinterpret_cast<BItem *>(base + L.items);
+    return p;
+}
+
+cudaError_t launch_kernels(const BPtrs &p, const lcl_batch_limits &lim, const lcl_batch_config &c, cudaStream_t st) {
+    const int pg = (std::max(lim.lassos, 1) + kPrepWarps - 1) / kPrepWarps;
+    k_batch_prep<<<pg, kThreads, 0, st>>>(p.hdr, p.lasso_in, p.lassos);
+    cudaError_t e = cudaSuccess;
+    if (lim.supers > 0) {
+        const int cg = (int)std::min<int64_t>(lim.supers, resident_grid(k_batch_cull));
+        e = launch_pdl(k_batch_cull, dim3(cg), st, (const BHdr *)p.hdr, p.models, p.strokes, p.lassos, p.super_model,
+                       p.items, &p.hdr->n_items);
+        if (e == cudaSuccess) {
+            const int fit = resident_per_sm(k_batch_apply, c.threads);
+            const int per_sm = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, fit) : fit;
+            e = launch_pdl_shape(k_batch_apply, dim3(per_sm * sm_count()), dim3(c.threads), st, (const BHdr *)p.hdr,
+                                 p.models, p.strokes, p.lassos, (const BItem *)p.items, &p.hdr->next_unit,
+                                 (int32_t)c.split);
+        }
+    }
+    count_launches(lim.supers > 0 ? 3 : 1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e;
+}
 
 }  // namespace
 
-size_t batch_host_bytes(int32_t n_models, int32_t n_strokes, int32_t n_lassos, int64_t n_supers, int64_t n_tiles) {
-    return align256(sizeof(LaunchInfo)) + b_layout(n_models, n_strokes, n_lassos, n_supers, n_tiles).items;
-}
-
-size_t batch_ws_bytes(int32_t n_models, int32_t n_strokes, int32_t n_lassos, int64_t n_supers, int64_t n_tiles) {
-    return b_layout(n_models, n_strokes, n_lassos, n_supers, n_tiles).total;
-}
-
-lcl_status batch_sizes(const lcl_batch_model *models, int32_t n_models, int64_t *n_supers, int64_t *n_tiles) {
+lcl_status batch_limits_of(const lcl_batch_model *models, int32_t n_models, int32_t n_strokes, int32_t n_lassos,
+                           lcl_batch_limits *out) {
+    if (!out || n_models < 0 || n_strokes < 0 || n_lassos < 0 || (n_models && !models))
+        return fail(LCL_ERR_INVALID_ARG, "batch limits: bad counts or NULL");
     int64_t ns = 0, nt = 0;
     for (int32_t i = 0; i < n_models; ++i) {
-        if (!models[i].atlas) return fail(LCL_ERR_INVALID_ARG, "batch model without atlas");
-        ns += (int64_t)models[i].atlas->supers_x * models[i].atlas->supers_y;
-        nt += (int64_t)models[i].atlas->tiles_x * models[i].atlas->tiles_y;
+        const lcl_atlas *a = models[i].atlas;
+        if (!a || a->tiles_x <= 0 || a->tiles_y <= 0) return fail(LCL_ERR_INVALID_ARG, "batch model without atlas");
+        ns += (int64_t)a->supers_x * a->supers_y;
+        nt += (int64_t)a->tiles_x * a->tiles_y;
     }
-    *n_supers = ns;
-    *n_tiles = nt;
+    std::memset(out, 0, sizeof(*out));
+    out->models = n_models;
+    out->strokes = n_strokes;
+    out->lassos = n_lassos;
+    out->supers = ns;
+    out->tiles = nt;
+    if (!limits_ok(out)) return fail(LCL_ERR_UNSUPPORTED, "batch too large");
     return LCL_OK;
 }
 
-lcl_status batch_launch_impl(void *ws, const void *host_staging, cudaStream_t st) {
-    const LaunchInfo &info = *static_cast<const LaunchInfo *>(host_staging);
-    const BLayout L = b_layout(info.n_models, info.n_strokes, info.n_lassos, info.n_supers, info.n_tiles);
-    char *base = static_cast<char *>(ws);
-    BHdr *hdr = reinterpret_cast<BHdr *>(base + L.hdr);
-    const BModel *models = reinterpret_cast<const BModel *>(base + L.models);
-    const BStroke *strokes = reinterpret_cast<const BStroke *>(base + L.strokes);
-    const BLasso *lassos = reinterpret_cast<const BLasso *>(base + L.lassos);
-    const uint32_t *super_model = reinterpret_cast<const uint32_t *>(base + L.super_model);
-    BItem *items = reinterpret_cast<BItem *>(base + L.items);
-    k_batch_init<<<1, 1, 0, st>>>(hdr);
-    cudaError_t e = cudaSuccess;
-    if (info.n_supers > 0) {
-        const int cg = std::min<int64_t>(info.n_supers, resident_grid(k_batch_cull));
-        e = launch_pdl(k_batch_cull, dim3(cg), st, (const BHdr *)hdr, models, strokes, lassos, super_model, items,
-                       &hdr->n_items);
-        if (e == cudaSuccess)
-            e = launch_pdl(k_batch_apply, dim3(resident_grid(k_batch_apply)), st, models, strokes, lassos,
-                           (const BItem *)items, (const unsigned int *)&hdr->n_items);
-    }
-    count_launches(info.n_supers > 0 ? 3 : 1);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "batch launch");
-    return LCL_OK;
-}
+size_t batch_ws_bytes(const lcl_batch_limits *lim) { return limits_ok(lim) ? b_layout(*lim).total : 0; }
 
-lcl_status batch_edit_impl(const lcl_batch_model *models, int32_t n_models, const lcl_batch_stroke *strokes,
-                           int32_t n_strokes, const lcl_batch_lasso *lassos, int32_t n_lassos, void *ws,
-                           size_t ws_bytes, void *host_staging, size_t host_bytes, cudaStream_t st) {
+size_t batch_host_bytes(const lcl_batch_limits *lim) { return limits_ok(lim) ? b_layout(*lim).upload : 0; }
+
+lcl_status batch_upload_impl(const lcl_batch_limits *lim, const lcl_batch_model *models, int32_t n_models,
+                             const lcl_batch_stroke *strokes, int32_t n_strokes, const lcl_batch_lasso *lassos,
+                             int32_t n_lassos, void *ws, size_t ws_bytes, void *host_staging, size_t host_bytes,
+                             cudaStream_t st) {
+    if (!limits_ok(lim)) return fail(LCL_ERR_INVALID_ARG, "batch limits out of range");
+    if (!ws || !host_staging) return fail(LCL_ERR_INVALID_ARG, "batch workspace or staging is NULL");
     int64_t n_supers = 0, n_tiles = 0;
     lcl_status s = check_batch(models, n_models, strokes, n_strokes, lassos, n_lassos, &n_supers, &n_tiles);
     if (s != LCL_OK) return s;
-    const BLayout L = b_layout(n_models, n_strokes, n_lassos, n_supers, n_tiles);
+    if (n_models > lim->models || n_strokes > lim->strokes || n_lassos > lim->lassos || n_supers > lim->supers ||
+        n_tiles > lim->tiles)
+        return fail(LCL_ERR_INVALID_ARG, "batch exceeds the workspace limits");
+    const BLayout L = b_layout(*lim);
     if (ws_bytes < L.total) return fail(LCL_ERR_OUT_OF_MEMORY, "batch workspace smaller than lcl_batch_workspace_bytes");
-    const size_t need_host = align256(sizeof(LaunchInfo)) + L.items;
-    if (host_bytes < need_host) return fail(LCL_ERR_OUT_OF_MEMORY, "batch staging smaller than lcl_batch_staging_bytes");
-    char *hs = static_cast<char *>(host_staging);
-    LaunchInfo info;
-    info.n_models = n_models;
-    info.n_strokes = n_strokes;
-    info.n_lassos = n_lassos;
-    info.n_supers = (int32_t)n_supers;
-    info.n_tiles = n_tiles;
-    info.ws_bytes = (int64_t)L.total;
-    std::memcpy(hs, &info, sizeof(info));
-    char *img = hs + align256(sizeof(LaunchInfo));  // image of the workspace up to the item list
-    std::memset(img, 0, L.items);
+    if (host_bytes < L.upload) return fail(LCL_ERR_OUT_OF_MEMORY, "batch staging smaller than lcl_batch_staging_bytes");
+    char *img = static_cast<char *>(host_staging);  // image of the uploaded part of the workspace
+    const size_t used = L.super_model + align256((size_t)std::max<int64_t>(n_supers, 1) * 4);
+    std::memset(img, 0, L.lasso_in);  // header, models, strokes (lasso inputs are written field by field)
     BHdr hdr;
     std::memset(&hdr, 0, sizeof(hdr));
     hdr.n_models = n_models;
     hdr.n_strokes = n_strokes;
     hdr.n_lassos = n_lassos;
     hdr.n_supers = (int32_t)n_supers;
-    hdr.n_tiles = n_tiles;
     std::memcpy(img + L.hdr, &hdr, sizeof(hdr));
     BModel *bm = reinterpret_cast<BModel *>(img + L.models);
     uint32_t *super_model = reinterpret_cast<uint32_t *>(img + L.super_model);
@@ -397,15 +524,79 @@ lcl_status batch_edit_impl(const lcl_batch_model *models, int32_t n_models, cons
         d.sphere.pad_t = 0;
         bs[k] = d;
     }
-    BLasso *bl = reinterpret_cast<BLasso *>(img + L.lassos);
+    BLassoIn *bl = reinterpret_cast<BLassoIn *>(img + L.lasso_in);
     for (int32_t j = 0; j < n_lassos; ++j) {
-        fill_lasso_arg(bl[j].arg, &lassos[j].camera, lassos[j].poly_xy, lassos[j].n_vertices, lassos[j].label,
-                       lassos[j].bias);
-        bl[j].depth = lassos[j].depth;
+        BLassoIn &d = bl[j];
+        std::memcpy(d.m, lassos[j].camera.m, sizeof(d.m));
+        d.w_s = lassos[j].camera.width;
+        d.h_s = lassos[j].camera.height;
+        d.depth = lassos[j].depth;
+        std::memcpy(d.poly, lassos[j].poly_xy, sizeof(float) * 2 * (size_t)lassos[j].n_vertices);
+        d.nv = lassos[j].n_vertices;
+        d.label = lassos[j].label;
+        d.bias = lassos[j].bias;
+        d.pad = 0;
     }
-    cudaError_t e = cudaMemcpyAsync(ws, img, L.items, cudaMemcpyHostToDevice, st);
+    // the header and every used descriptor, in one copy (the unused tails of the arrays are not read)
+    cudaError_t e = cudaMemcpyAsync(ws, img, used, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "batch descriptor upload");
-    return batch_launch_impl(ws, host_staging, st);
+    return LCL_OK;
+}
+
+lcl_status batch_launch_impl(const lcl_batch_limits *lim, const lcl_batch_config *cfg, void *ws, size_t ws_bytes,
+                             cudaStream_t st) {
+    if (!limits_ok(lim)) return fail(LCL_ERR_INVALID_ARG, "batch limits out of range");
+    const lcl_batch_config c = cfg ? *cfg : default_config();
+    if (!config_ok(c)) return fail(LCL_ERR_INVALID_ARG, "batch config: threads 64/128/256, split 1/2/4/8, ctas_per_sm 0..32");
+    const BLayout L = b_layout(*lim);
+    if (!ws || ws_bytes < L.total) return fail(LCL_ERR_INVALID_ARG, "batch workspace NULL or smaller than the limits need");
+    const cudaError_t e = launch_kernels(b_ptrs(L, ws), *lim, c, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    return LCL_OK;
+}
+
+lcl_status batch_tune_impl(const lcl_batch_limits *lim, void *ws, size_t ws_bytes, int32_t reps, cudaStream_t st,
+                           lcl_batch_config *best, float *best_ms) {
+    if (!best || reps < 1 || reps > 100) return fail(LCL_ERR_INVALID_ARG, "batch tune: best is NULL or reps not in 1..100");
+    if (!limits_ok(lim)) return fail(LCL_ERR_INVALID_ARG, "batch limits out of range");
+    const BLayout L = b_layout(*lim);
+    if (!ws || ws_bytes < L.total) return fail(LCL_ERR_INVALID_ARG, "batch workspace NULL or smaller than the limits need");
+    const BPtrs p = b_ptrs(L, ws);
+    const int fit256 = resident_per_sm(k_batch_apply, 256);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float t_best = INFINITY;
+    lcl_batch_config c_best = default_config();
+    const int threads[3] = {64, 128, 256}, splits[4] = {1, 2, 4, 8};
+    for (int ti = 0; ti < 3 && e == cudaSuccess; ++ti)
+        for (int si = 0; si < 4 && e == cudaSuccess; ++si)
+            for (int half = 0; half < 2 && e == cudaSuccess; ++half) {
+                lcl_batch_config c = default_config();
+                c.threads = threads[ti];
+                c.split = splits[si];
+                const int fit = resident_per_sm(k_batch_apply, c.threads);
+                c.ctas_per_sm = half ? std::max(1, fit / 2) : 0;
+                if (half && c.ctas_per_sm >= fit) continue;
+                (void)fit256;
+                e = launch_kernels(p, *lim, c, st);  // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+                for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_kernels(p, *lim, c, st);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e == cudaSuccess && ms / reps < t_best) {
+                    t_best = ms / reps;
+                    c_best = c;
+                }
+            }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "batch tune");
+    *best = c_best;
+    if (best_ms) *best_ms = t_best;
+    return LCL_OK;
 }
 
 }  // namespace lcl

@@ -332,34 +332,45 @@ lcl_status lcl_select_lasso(const lcl_atlas *atlas, void *layer, lcl_dtype dtype
                              reinterpret_cast<cudaStream_t>(stream));
 }
 
-size_t lcl_batch_workspace_bytes(const lcl_batch_model *models, int32_t n_models, int32_t n_strokes,
-                                 int32_t n_lassos) {
-    int64_t ns = 0, nt = 0;
-    if (n_models < 0 || n_strokes < 0 || n_lassos < 0 || (n_models && !models)) return 0;
-    if (batch_sizes(models, n_models, &ns, &nt) != LCL_OK) return 0;
-    return batch_ws_bytes(n_models, n_strokes, n_lassos, ns, nt);
+lcl_status lcl_batch_limits_of(const lcl_batch_model *models, int32_t n_models, int32_t n_strokes, int32_t n_lassos,
+                               lcl_batch_limits *out) {
+    return batch_limits_of(models, n_models, n_strokes, n_lassos, out);
 }
 
-size_t lcl_batch_staging_bytes(const lcl_batch_model *models, int32_t n_models, int32_t n_strokes,
-                               int32_t n_lassos) {
-    int64_t ns = 0, nt = 0;
-    if (n_models < 0 || n_strokes < 0 || n_lassos < 0 || (n_models && !models)) return 0;
-    if (batch_sizes(models, n_models, &ns, &nt) != LCL_OK) return 0;
-    return batch_host_bytes(n_models, n_strokes, n_lassos, ns, nt);
-}
+size_t lcl_batch_workspace_bytes(const lcl_batch_limits *limits) { return batch_ws_bytes(limits); }
 
-lcl_status lcl_batch_edit(const lcl_batch_model *models, int32_t n_models, const lcl_batch_stroke *strokes,
-                          int32_t n_strokes, const lcl_batch_lasso *lassos, int32_t n_lassos, void *workspace,
-                          size_t ws_bytes, void *host_staging, size_t staging_bytes, lcl_stream stream) {
+size_t lcl_batch_staging_bytes(const lcl_batch_limits *limits) { return batch_host_bytes(limits); }
+
+lcl_status lcl_batch_upload(const lcl_batch_limits *limits, const lcl_batch_model *models, int32_t n_models,
+                            const lcl_batch_stroke *strokes, int32_t n_strokes, const lcl_batch_lasso *lassos,
+                            int32_t n_lassos, void *workspace, size_t ws_bytes, void *host_staging,
+                            size_t staging_bytes, lcl_stream stream) {
     if (!workspace || !aligned(workspace, 256)) return fail(LCL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     if (!host_staging || !aligned(host_staging, 16)) return fail(LCL_ERR_INVALID_ARG, "host staging must be 16-byte aligned");
-    return batch_edit_impl(models, n_models, strokes, n_strokes, lassos, n_lassos, workspace, ws_bytes, host_staging,
-                           staging_bytes, reinterpret_cast<cudaStream_t>(stream));
+    return batch_upload_impl(limits, models, n_models, strokes, n_strokes, lassos, n_lassos, workspace, ws_bytes,
+                             host_staging, staging_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
-lcl_status lcl_batch_launch(void *workspace, const void *host_staging, lcl_stream stream) {
-    if (!workspace || !host_staging) return fail(LCL_ERR_INVALID_ARG, "NULL argument");
-    return batch_launch_impl(workspace, host_staging, reinterpret_cast<cudaStream_t>(stream));
+lcl_status lcl_batch_launch(const lcl_batch_limits *limits, const lcl_batch_config *config, void *workspace,
+                            size_t ws_bytes, lcl_stream stream) {
+    if (!workspace || !aligned(workspace, 256)) return fail(LCL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    return batch_launch_impl(limits, config, workspace, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+lcl_status lcl_batch_edit(const lcl_batch_limits *limits, const lcl_batch_config *config,
+                          const lcl_batch_model *models, int32_t n_models, const lcl_batch_stroke *strokes,
+                          int32_t n_strokes, const lcl_batch_lasso *lassos, int32_t n_lassos, void *workspace,
+                          size_t ws_bytes, void *host_staging, size_t staging_bytes, lcl_stream stream) {
+    lcl_status s = lcl_batch_upload(limits, models, n_models, strokes, n_strokes, lassos, n_lassos, workspace,
+                                    ws_bytes, host_staging, staging_bytes, stream);
+    if (s != LCL_OK) return s;
+    return lcl_batch_launch(limits, config, workspace, ws_bytes, stream);
+}
+
+lcl_status lcl_batch_tune(const lcl_batch_limits *limits, void *workspace, size_t ws_bytes, int32_t reps,
+                          lcl_stream stream, lcl_batch_config *best, float *best_ms) {
+    if (!workspace || !aligned(workspace, 256)) return fail(LCL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    return batch_tune_impl(limits, workspace, ws_bytes, reps, reinterpret_cast<cudaStream_t>(stream), best, best_ms);
 }
 
 lcl_status lcl_overlay(const lcl_atlas *atlas, const void *a, const void *b, void *out, lcl_dtype dtype, lcl_op op,

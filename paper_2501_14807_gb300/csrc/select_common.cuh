@@ -124,10 +124,10 @@ __device__ __forceinline__ void add_hits(unsigned long long *hits, uint32_t cnt)
 
 
 template <typename... K, typename... A>
-cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, cudaStream_t st, A... args) {
+cudaError_t launch_pdl_shape(void (*kernel)(K...), dim3 grid, dim3 block, cudaStream_t st, A... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = block;
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -136,6 +136,12 @@ cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, cudaStream_t st, A... ar
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Programmatic dependent launch of `kernel` with kThreads threads per CTA.
+template <typename... K, typename... A>
+cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, cudaStream_t st, A... args) {
+    return launch_pdl_shape(kernel, grid, dim3(kThreads), st, args...);
 }
 
 
@@ -246,25 +252,37 @@ __device__ __forceinline__ bool lasso_hit(const LassoArg &p, const Edges &sh, co
 
 
 
+// CTAs of `threads` threads that fit on one SM at once (at least 1).
+template <typename K>
+inline int resident_per_sm(K kernel, int threads) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return per_sm;
+}
+
 // A grid of as many CTAs as fit on the GPU at once (persistent loops need no second wave).
 template <typename K>
 inline int resident_grid(K kernel) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    return per_sm * sm_count();
+    return resident_per_sm(kernel, kThreads) * sm_count();
 }
 
 
-// Fills the lasso argument: matrix, screen, polygon (vertex nv repeated as vertex 0), the widened
-// bounding box in pixels and NDC, and the y-band edge lists.
-inline void fill_lasso_arg(LassoArg &p, const lcl_camera *cam, const float *poly, int32_t nv, uint32_t label,
-                           float bias) {
-    for (int i = 0; i < 16; ++i) p.m[i] = cam->m[i];
-    p.ws = (float)cam->width;
-    p.hs = (float)cam->height;
-    p.w_s = cam->width;
-    p.h_s = cam->height;
+// y-bands of edges: band b lists the edges whose y-range comes within `slack` of it, in edge order.
+__host__ __device__ inline double lasso_band_height(const LassoArg &p) {
+    return fmax((double)p.ymax - (double)p.ymin, 1e-3) / kBands;
+}
+
+// The lasso argument without its y-bands: matrix, screen, polygon (vertex nv repeated as vertex
+// 0), the widened bounding box in pixels and NDC, the band mapping.  Host and device run the same
+// code (batched edits build their lassos on the device), so both get identical fields.
+__host__ __device__ inline void lasso_arg_head(LassoArg &p, const float *m16, int32_t w_s, int32_t h_s,
+                                               const float *poly, int32_t nv, uint32_t label, float bias) {
+    for (int i = 0; i < 16; ++i) p.m[i] = m16[i];
+    p.ws = (float)w_s;
+    p.hs = (float)h_s;
+    p.w_s = w_s;
+    p.h_s = h_s;
     p.bias = bias;
     p.label = label;
     p.nv = nv;
@@ -272,10 +290,10 @@ inline void fill_lasso_arg(LassoArg &p, const lcl_camera *cam, const float *poly
     for (int i = 0; i < nv; ++i) {
         p.vx[i] = poly[2 * i];
         p.vy[i] = poly[2 * i + 1];
-        x0 = std::fmin(x0, p.vx[i]);
-        x1 = std::fmax(x1, p.vx[i]);
-        y0 = std::fmin(y0, p.vy[i]);
-        y1 = std::fmax(y1, p.vy[i]);
+        x0 = fminf(x0, p.vx[i]);
+        x1 = fmaxf(x1, p.vx[i]);
+        y0 = fminf(y0, p.vy[i]);
+        y1 = fmaxf(y1, p.vy[i]);
     }
     for (int i = nv; i <= LCL_MAX_LASSO_VERTICES; ++i) {
         p.vx[i] = p.vx[0];
@@ -283,31 +301,39 @@ inline void fill_lasso_arg(LassoArg &p, const lcl_camera *cam, const float *poly
     }
     // Culling and the division-free reject use the bbox widened by a margin far above the FP32
     // rounding of projected points (well under a thousandth of a pixel at these sizes).
-    const float margin = 2.0f + 1e-3f * (float)std::max(cam->width, cam->height);
-    p.bx0 = std::fmax(x0, 0.0f) - margin;
-    p.bx1 = std::fmin(x1, (float)cam->width) + margin;
-    p.by0 = std::fmax(y0, 0.0f) - margin;
-    p.by1 = std::fmin(y1, (float)cam->height) + margin;
-    p.nx0 = (float)(2.0 * p.bx0 / cam->width - 1.0);
-    p.nx1 = (float)(2.0 * p.bx1 / cam->width - 1.0);
-    p.ny0 = (float)(2.0 * p.by0 / cam->height - 1.0);
-    p.ny1 = (float)(2.0 * p.by1 / cam->height - 1.0);
+    const float margin = 2.0f + 1e-3f * (float)(w_s > h_s ? w_s : h_s);
+    p.bx0 = fmaxf(x0, 0.0f) - margin;
+    p.bx1 = fminf(x1, (float)w_s) + margin;
+    p.by0 = fmaxf(y0, 0.0f) - margin;
+    p.by1 = fminf(y1, (float)h_s) + margin;
+    p.nx0 = (float)(2.0 * p.bx0 / w_s - 1.0);
+    p.nx1 = (float)(2.0 * p.bx1 / w_s - 1.0);
+    p.ny0 = (float)(2.0 * p.by0 / h_s - 1.0);
+    p.ny1 = (float)(2.0 * p.by1 / h_s - 1.0);
     p.ymin = y0;
     p.ymax = y1;
-    // y-bands of edges; each band lists the edges whose y-range comes within `slack` of it
-    const double bh = std::max((double)y1 - (double)y0, 1e-3) / kBands;
-    const double slack = 1e-3 * bh + 1e-3;
     p.band_y0 = y0;
-    p.band_inv_h = (float)(1.0 / bh);
+    p.band_inv_h = (float)(1.0 / lasso_band_height(p));
+}
+
+__host__ __device__ inline bool lasso_band_has(const LassoArg &p, int b, int e, double bh) {
+    const double slack = 1e-3 * bh + 1e-3;
+    const double lo = (double)p.ymin + b * bh - slack, hi = (double)p.ymin + (b + 1) * bh + slack;
+    const double ea = p.vy[e], eb = p.vy[e + 1];
+    if (ea == eb) return false;  // horizontal edges never straddle
+    return fmin(ea, eb) <= hi && fmax(ea, eb) >= lo;
+}
+
+// The whole lasso argument, on the host.
+inline void fill_lasso_arg(LassoArg &p, const lcl_camera *cam, const float *poly, int32_t nv, uint32_t label,
+                           float bias) {
+    lasso_arg_head(p, cam->m, cam->width, cam->height, poly, nv, label, bias);
+    const double bh = lasso_band_height(p);
     int cnt = 0;
     for (int b = 0; b < kBands; ++b) {
         p.band_off[b] = (uint16_t)cnt;
-        const double lo = (double)y0 + b * bh - slack, hi = (double)y0 + (b + 1) * bh + slack;
-        for (int e = 0; e < nv; ++e) {
-            const double ea = p.vy[e], eb = p.vy[e + 1];
-            if (ea == eb) continue;  // horizontal edges never straddle
-            if (std::min(ea, eb) <= hi && std::max(ea, eb) >= lo) p.band_edge[cnt++] = (uint8_t)e;
-        }
+        for (int e = 0; e < nv; ++e)
+            if (lasso_band_has(p, b, e, bh)) p.band_edge[cnt++] = (uint8_t)e;
     }
     p.band_off[kBands] = (uint16_t)cnt;
 }

@@ -30,7 +30,8 @@ DEFAULT_BIAS = 2.0 ** -10
 EXPORTS = ["lcl_atlas_bytes", "lcl_atlas_bind", "lcl_atlas_rows", "lcl_atlas_workspace_bytes", "lcl_atlas_build",
            "lcl_quantize_sphere", "lcl_quantize_spheres", "lcl_camera_from_vp", "lcl_select_workspace_bytes", "lcl_select_sphere",
            "lcl_select_sphere_static", "lcl_depth_workspace_bytes", "lcl_depth_render", "lcl_select_lasso",
-           "lcl_batch_workspace_bytes", "lcl_batch_staging_bytes", "lcl_batch_edit", "lcl_batch_launch",
+           "lcl_batch_limits_of", "lcl_batch_workspace_bytes", "lcl_batch_staging_bytes", "lcl_batch_upload",
+           "lcl_batch_launch", "lcl_batch_edit", "lcl_batch_tune",
            "lcl_overlay", "lcl_label_area", "lcl_status_str", "lcl_last_error", "lcl_kernel_launches"]
 
 
@@ -71,11 +72,24 @@ class lcl_batch_lasso(C.Structure):
                 ("label", C.c_uint32), ("bias", C.c_float), ("_pad", C.c_int32)]
 
 
+class lcl_batch_limits(C.Structure):
+    _fields_ = [("models", C.c_int32), ("strokes", C.c_int32), ("lassos", C.c_int32), ("_pad", C.c_int32),
+                ("supers", C.c_int64), ("tiles", C.c_int64)]
+
+
+class lcl_batch_config(C.Structure):
+    _fields_ = [("threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("split", C.c_int32), ("_pad", C.c_int32)]
+
+    def as_dict(self):
+        return {"threads": self.threads, "ctas_per_sm": self.ctas_per_sm, "split": self.split}
+
+
 LCL_STROKE_SPHERE, LCL_STROKE_LASSO = 0, 1
 BATCH_MAX_STROKES = 64
 
 assert C.sizeof(lcl_sphere) == 32 and C.sizeof(lcl_camera) == 72 and C.sizeof(lcl_atlas) == 128
 assert C.sizeof(lcl_batch_model) == 32 and C.sizeof(lcl_batch_stroke) == 40 and C.sizeof(lcl_batch_lasso) == 104
+assert C.sizeof(lcl_batch_limits) == 32 and C.sizeof(lcl_batch_config) == 16
 
 SPHERE_DTYPE = np.dtype([("cx", "<i4"), ("cy", "<i4"), ("cz", "<i4"), ("pad", "<i4"),
                          ("r2", "<i8"), ("label", "<u4"), ("flags", "<u4")])
@@ -117,11 +131,17 @@ def library():
         "lcl_depth_render": (st, [C.POINTER(lcl_mesh), C.POINTER(lcl_atlas), C.POINTER(lcl_camera), P, P, SZ, P]),
         "lcl_select_lasso": (st, [C.POINTER(lcl_atlas), P, C.c_int, C.POINTER(lcl_camera), P, P, I32, U32, F, P, P,
                                   SZ, P]),
-        "lcl_batch_workspace_bytes": (SZ, [C.POINTER(lcl_batch_model), I32, I32, I32]),
-        "lcl_batch_staging_bytes": (SZ, [C.POINTER(lcl_batch_model), I32, I32, I32]),
-        "lcl_batch_edit": (st, [C.POINTER(lcl_batch_model), I32, C.POINTER(lcl_batch_stroke), I32,
-                                C.POINTER(lcl_batch_lasso), I32, P, SZ, P, SZ, P]),
-        "lcl_batch_launch": (st, [P, P, P]),
+        "lcl_batch_limits_of": (st, [C.POINTER(lcl_batch_model), I32, I32, I32, C.POINTER(lcl_batch_limits)]),
+        "lcl_batch_workspace_bytes": (SZ, [C.POINTER(lcl_batch_limits)]),
+        "lcl_batch_staging_bytes": (SZ, [C.POINTER(lcl_batch_limits)]),
+        "lcl_batch_upload": (st, [C.POINTER(lcl_batch_limits), C.POINTER(lcl_batch_model), I32,
+                                  C.POINTER(lcl_batch_stroke), I32, C.POINTER(lcl_batch_lasso), I32, P, SZ, P, SZ, P]),
+        "lcl_batch_launch": (st, [C.POINTER(lcl_batch_limits), C.POINTER(lcl_batch_config), P, SZ, P]),
+        "lcl_batch_edit": (st, [C.POINTER(lcl_batch_limits), C.POINTER(lcl_batch_config), C.POINTER(lcl_batch_model),
+                                I32, C.POINTER(lcl_batch_stroke), I32, C.POINTER(lcl_batch_lasso), I32, P, SZ, P, SZ,
+                                P]),
+        "lcl_batch_tune": (st, [C.POINTER(lcl_batch_limits), P, SZ, I32, P, C.POINTER(lcl_batch_config),
+                                C.POINTER(C.c_float)]),
         "lcl_overlay": (st, [C.POINTER(lcl_atlas), P, P, P, C.c_int, C.c_int, U32, P]),
         "lcl_label_area": (st, [C.POINTER(lcl_atlas), P, C.c_int, U32, P, P, P]),
         "lcl_status_str": (C.c_char_p, [C.c_int]),
@@ -358,16 +378,47 @@ BATCH_STROKE_DTYPE = np.dtype([("kind", "<i4"), ("lasso", "<i4"), ("cx", "<i4"),
 assert BATCH_STROKE_DTYPE.itemsize == C.sizeof(lcl_batch_stroke)
 
 
+def batch_limits(models=0, strokes=0, lassos=0, supers=0, tiles=0):
+    """Capacity of a batch workspace (see lcl_batch_limits)."""
+    return lcl_batch_limits(int(models), int(strokes), int(lassos), 0, int(supers), int(tiles))
+
+
+def limits_max(a: lcl_batch_limits, b: lcl_batch_limits):
+    """Field-wise maximum of two limits."""
+    return batch_limits(max(a.models, b.models), max(a.strokes, b.strokes), max(a.lassos, b.lassos),
+                        max(a.supers, b.supers), max(a.tiles, b.tiles))
+
+
+def limits_fit(inner: lcl_batch_limits, outer: lcl_batch_limits):
+    return (inner.models <= outer.models and inner.strokes <= outer.strokes and inner.lassos <= outer.lassos and
+            inner.supers <= outer.supers and inner.tiles <= outer.tiles)
+
+
+def batch_workspace(limits: lcl_batch_limits, device):
+    """A device workspace for batches within `limits`."""
+    n = int(library().lcl_batch_workspace_bytes(C.byref(limits)))
+    if n == 0:
+        raise ValueError("invalid batch limits")
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def batch_config(threads=256, ctas_per_sm=0, split=1):
+    return lcl_batch_config(int(threads), int(ctas_per_sm), int(split), 0)
+
+
 class Batch:
-    """Arguments of one batched edit, kept alive for lcl_batch_edit / lcl_batch_launch.
+    """Arguments of one batched edit, kept alive for lcl_batch_upload / lcl_batch_edit.
 
     models: list of (Atlas, layer tensor); queues: per model, a list of ("sphere", record) or
     ("lasso", (camera, depth tensor, polygon float32 [n, 2], label, bias)) in queue order.
-    workspace / staging: optional reusable buffers (device uint8 / pinned host uint8); new ones are
-    allocated if they are missing or too small.  A pinned staging is read by the copy that
-    lcl_batch_edit enqueues, so it must not be reused before that copy has run."""
+    limits: capacity of the workspace (lcl_batch_limits); by default exactly this batch's.  A
+    workspace with larger limits can take many different batches under one launch shape (and one
+    captured graph, see BatchGraph).  config: launch shape (lcl_batch_config) or None (default);
+    lcl_batch_tune sets it.  workspace / staging: optional reusable buffers (device uint8 / pinned
+    host uint8); new ones are allocated if they are missing or too small.  A pinned staging is read
+    by the copy that lcl_batch_upload enqueues, so it is not rewritten before that copy has run."""
 
-    def __init__(self, models, queues, workspace=None, staging=None):
+    def __init__(self, models, queues, workspace=None, staging=None, limits=None, config=None):
         assert len(models) == len(queues)
         self._keep = []
         n_total = sum(len(q) for q in queues)
@@ -407,9 +458,16 @@ class Batch:
         self.strokes = strokes.ctypes.data_as(C.POINTER(lcl_batch_stroke))
         self.lassos = (lcl_batch_lasso * max(len(lassos), 1))(*lassos)
         lib = library()
-        self.ws_bytes = int(lib.lcl_batch_workspace_bytes(self.models, self.n_models, self.n_strokes, self.n_lassos))
-        self.staging_bytes = int(lib.lcl_batch_staging_bytes(self.models, self.n_models, self.n_strokes,
-                                                             self.n_lassos))
+        own = lcl_batch_limits()
+        _check("lcl_batch_limits_of", lib.lcl_batch_limits_of(self.models, self.n_models, self.n_strokes,
+                                                               self.n_lassos, C.byref(own)))
+        self.own_limits = own
+        self.limits = own if limits is None else limits
+        if not limits_fit(own, self.limits):
+            raise ValueError("batch exceeds the given limits")
+        self.config = config
+        self.ws_bytes = int(lib.lcl_batch_workspace_bytes(C.byref(self.limits)))
+        self.staging_bytes = int(lib.lcl_batch_staging_bytes(C.byref(self.limits)))
         dev = models[0][1].device if models else torch.device("cuda")
         if workspace is None or workspace.numel() < self.ws_bytes:
             workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
@@ -426,28 +484,85 @@ def _torch_stream(stream):
     return torch.cuda.ExternalStream(int(stream))
 
 
-def lcl_batch_edit(batch: Batch, stream=None):
-    """Uploads the batch's descriptors from its pinned staging and launches the batch.  The staging
-    is rewritten on the host by every call, and the upload of the previous call that used it may
-    still be queued on the device, so this waits (on the host) until that call's work has finished
-    before reusing the staging."""
+def _cfg(config):
+    return None if config is None else C.byref(config)
+
+
+def _staging_wait(batch):
+    """The staging is rewritten on the host by every upload, and the upload of the previous call that
+    used it may still be queued on the device: wait (on the host) until that call has passed."""
     busy = getattr(batch.staging, "_lcl_busy", None)
     if busy is not None:
         busy.synchronize()
-    _check("lcl_batch_edit", library().lcl_batch_edit(
-        batch.models, batch.n_models, batch.strokes, batch.n_strokes, batch.lassos, batch.n_lassos,
-        _ptr(batch.workspace), batch.workspace.numel(), C.c_void_p(batch.staging.data_ptr()), batch.staging.numel(),
-        _stream(stream)))
+
+
+def _staging_mark(batch, stream):
     done = torch.cuda.Event()
     done.record(_torch_stream(stream))
     batch.staging._lcl_busy = done
+
+
+def lcl_batch_upload(batch: Batch, stream=None):
+    """Packs the batch's descriptors into its pinned staging and copies them to its workspace."""
+    _staging_wait(batch)
+    _check("lcl_batch_upload", library().lcl_batch_upload(
+        C.byref(batch.limits), batch.models, batch.n_models, batch.strokes, batch.n_strokes, batch.lassos,
+        batch.n_lassos, _ptr(batch.workspace), batch.workspace.numel(), C.c_void_p(batch.staging.data_ptr()),
+        batch.staging.numel(), _stream(stream)))
+    _staging_mark(batch, stream)
     return batch
 
 
-def lcl_batch_launch(batch: Batch, stream=None):
-    _check("lcl_batch_launch", library().lcl_batch_launch(_ptr(batch.workspace), C.c_void_p(batch.staging.data_ptr()),
-                                                          _stream(stream)))
+def lcl_batch_launch(batch: Batch, stream=None, config=None):
+    """Launches the batch last uploaded to the batch's workspace (config: this shape, else batch.config)."""
+    cfg = config if config is not None else batch.config
+    _check("lcl_batch_launch", library().lcl_batch_launch(C.byref(batch.limits), _cfg(cfg), _ptr(batch.workspace),
+                                                          batch.workspace.numel(), _stream(stream)))
     return batch
+
+
+def lcl_batch_edit(batch: Batch, stream=None):
+    """Upload + launch (batch.config)."""
+    _staging_wait(batch)
+    _check("lcl_batch_edit", library().lcl_batch_edit(
+        C.byref(batch.limits), _cfg(batch.config), batch.models, batch.n_models, batch.strokes, batch.n_strokes,
+        batch.lassos, batch.n_lassos, _ptr(batch.workspace), batch.workspace.numel(),
+        C.c_void_p(batch.staging.data_ptr()), batch.staging.numel(), _stream(stream)))
+    _staging_mark(batch, stream)
+    return batch
+
+
+def lcl_batch_tune(batch: Batch, stream=None, reps=2):
+    """Autotunes the launch shape on the batch last uploaded to the batch's workspace (its strokes are
+    re-applied, which leaves the labels as they are); sets batch.config.  Returns (config, ms)."""
+    best = lcl_batch_config()
+    ms = C.c_float()
+    _check("lcl_batch_tune", library().lcl_batch_tune(C.byref(batch.limits), _ptr(batch.workspace),
+                                                      batch.workspace.numel(), int(reps), _stream(stream),
+                                                      C.byref(best), C.byref(ms)))
+    batch.config = best
+    return best, float(ms.value)
+
+
+class BatchGraph:
+    """A CUDA graph holding one batched launch (lcl_batch_launch) on a workspace of given limits and
+    launch shape.  The launch reads everything from the workspace, so after any batch within the
+    limits has been uploaded there (lcl_batch_upload), replay() edits it."""
+
+    def __init__(self, limits: lcl_batch_limits, config, workspace: torch.Tensor):
+        self.limits, self.config, self.workspace = limits, config, workspace
+        self.graph = torch.cuda.CUDAGraph()
+        cur = torch.cuda.current_stream(workspace.device)
+        side = torch.cuda.Stream(workspace.device)
+        side.wait_stream(cur)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(self.graph, stream=side):
+                _check("lcl_batch_launch", library().lcl_batch_launch(
+                    C.byref(limits), _cfg(config), _ptr(workspace), workspace.numel(), _stream(side)))
+        cur.wait_stream(side)
+
+    def replay(self):
+        self.graph.replay()
 
 
 def lcl_overlay(atlas: Atlas, a: torch.Tensor, b: torch.Tensor, out: torch.Tensor, op, flags=0, stream=None):

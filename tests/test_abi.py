@@ -214,8 +214,9 @@ def test_batch_rejects_bad_arguments_on_host(lcl):
     models[0].n_strokes = 65
     strokes = (lcl.lcl_batch_stroke * 65)()
     lassos = (lcl.lcl_batch_lasso * 1)()
-    call = lambda n_strokes=65, n_lassos=0: lib.lcl_batch_edit(models, 1, strokes, n_strokes, lassos, n_lassos,  # noqa
-                                                               ws, 1 << 30, stg, 4096, None)
+    lim = lcl.batch_limits(models=1, strokes=65, lassos=1, supers=a.supers_x * a.supers_y, tiles=a.tiles_x * a.tiles_y)
+    call = lambda n_strokes=65, n_lassos=0, limits=lim: lib.lcl_batch_upload(  # noqa
+        C.byref(limits), models, 1, strokes, n_strokes, lassos, n_lassos, ws, 1 << 30, stg, 4096, None)
     assert call() == 4                                   # more than 64 strokes for one model
     models[0].n_strokes = 10
     assert call(n_strokes=5) == 1                        # stroke range outside the array
@@ -228,8 +229,27 @@ def test_batch_rejects_bad_arguments_on_host(lcl):
     strokes[4].sphere.label = 300
     assert call() == 1                                   # label too wide for uint8
     strokes[4].sphere.label = 3
+    strokes[5].sphere.flags = 1
+    assert call() == 4                                   # padded strokes are not batched
+    strokes[5].sphere.flags = 0
     models[0].layer = (1 << 41) + 8
     assert call() == 1                                   # layer misaligned
     models[0].layer = 1 << 41
-    assert call() in (2,)                                # staging too small for the descriptors
-    assert lib.lcl_batch_workspace_bytes(models, 1, 65, 0) > 0
+    small = lcl.batch_limits(models=1, strokes=8, lassos=1, supers=lim.supers, tiles=lim.tiles)
+    assert call(limits=small) == 1                       # more strokes than the workspace limits
+    tiny = lcl.batch_limits(models=1, strokes=65, lassos=1, supers=lim.supers, tiles=lim.tiles - 1)
+    assert call(limits=tiny) == 1                        # more tiles than the limits
+    assert call() == 2                                   # staging too small for the descriptors
+    assert lib.lcl_batch_workspace_bytes(C.byref(lim)) > lib.lcl_batch_staging_bytes(C.byref(lim)) > 4096
+    bad = lcl.batch_limits(models=-1)
+    assert lib.lcl_batch_workspace_bytes(C.byref(bad)) == 0
+    own = lcl.lcl_batch_limits()
+    assert lib.lcl_batch_limits_of(models, 1, 65, 0, C.byref(own)) == 0
+    assert (own.models, own.strokes, own.lassos, own.supers, own.tiles) == (1, 65, 0, lim.supers, lim.tiles)
+    # launch shapes are checked before anything is enqueued
+    for cfg in (lcl.batch_config(threads=96), lcl.batch_config(split=3), lcl.batch_config(ctas_per_sm=33),
+                lcl.batch_config(threads=0, split=0)):
+        assert lib.lcl_batch_launch(C.byref(lim), C.byref(cfg), ws, 1 << 30, None) == 1
+    assert lib.lcl_batch_launch(C.byref(lim), None, ws, 16, None) == 1      # workspace smaller than the limits
+    best, ms = lcl.lcl_batch_config(), C.c_float()
+    assert lib.lcl_batch_tune(C.byref(lim), ws, 1 << 30, 0, None, C.byref(best), C.byref(ms)) == 1  # reps < 1

@@ -153,3 +153,77 @@ def test_batch_back_to_back_edits_reuse_staging_safely(models):
     torch.cuda.synchronize()
     for s, l in zip(seq, layers):
         assert torch.equal(s, l)
+
+
+def run_sequential_queues(models, queues, inits):
+    layers = []
+    for m, q, init in zip(models, queues, inits):
+        layer = to_dev(init)
+        for kind, payload in q:
+            if kind == "sphere":
+                lcl.lcl_select_sphere(m["atlas"], layer, np.array([payload], lcl.SPHERE_DTYPE))
+            else:
+                cam, depth, poly, label, bias = payload
+                lcl.lcl_select_lasso(m["atlas"], layer, cam, depth, poly, label, bias)
+        layers.append(layer)
+    return layers
+
+
+@pytest.mark.parametrize("threads,ctas,split", [(64, 0, 1), (128, 0, 2), (256, 2, 4), (64, 1, 8), (256, 0, 8),
+                                                (128, 3, 1)])
+def test_batch_launch_shapes_give_identical_results(models, threads, ctas, split):
+    seq = run_sequential(models)
+    b, layers = make_batch(models)
+    b.config = lcl.batch_config(threads, ctas, split)
+    lcl.lcl_batch_edit(b)
+    torch.cuda.synchronize()
+    for s, l in zip(seq, layers):
+        assert torch.equal(s, l)
+
+
+def test_batch_autotuner_keeps_results(models):
+    seq = run_sequential(models)
+    b, layers = make_batch(models)
+    lcl.lcl_batch_upload(b)
+    cfg, ms = lcl.lcl_batch_tune(b, reps=1)
+    assert cfg.threads in (64, 128, 256) and cfg.split in (1, 2, 4, 8) and 0 <= cfg.ctas_per_sm <= 32
+    assert ms > 0
+    torch.cuda.synchronize()
+    for s, l in zip(seq, layers):  # the tuner re-ran the strokes many times: same labels
+        assert torch.equal(s, l)
+    for l, m in zip(layers, models):
+        l.copy_(to_dev(m["init"]))
+    lcl.lcl_batch_edit(b)  # with the tuned shape
+    torch.cuda.synchronize()
+    for s, l in zip(seq, layers):
+        assert torch.equal(s, l)
+
+
+def test_one_graph_serves_different_batches_within_limits(models):
+    """Capture the launch once for limits covering every model; upload two different batches
+    (different models, queue orders and lengths) and replay the same graph for each."""
+    full, _ = make_batch(models)
+    limits = full.own_limits
+    ws = lcl.batch_workspace(limits, DEV)
+    graph = lcl.BatchGraph(limits, lcl.batch_config(128, 0, 2), ws)
+    picks = [(list(range(0, 3)), lambda q: q), (list(range(2, 6)), lambda q: q[::-1][:50])]
+    for idx, reorder in picks:
+        sub = [models[i] for i in idx]
+        queues = [reorder(m["queue"]) for m in sub]
+        inits = [m["init"] for m in sub]
+        seq = run_sequential_queues(sub, queues, inits)
+        layers = [to_dev(x) for x in inits]
+        b = lcl.Batch([(m["atlas"], l) for m, l in zip(sub, layers)], queues, workspace=ws, limits=limits)
+        assert b.workspace is ws
+        lcl.lcl_batch_upload(b)
+        graph.replay()
+        torch.cuda.synchronize()
+        for s, l in zip(seq, layers):
+            assert torch.equal(s, l)
+
+
+def test_batch_rejects_batches_above_the_limits(models):
+    small = lcl.batch_limits(1, 64, 16, 1 << 20, 1 << 24)
+    with pytest.raises(ValueError):
+        lcl.Batch([(m["atlas"], to_dev(m["init"])) for m in models[:2]], [m["queue"] for m in models[:2]],
+                  limits=small)
