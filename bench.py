@@ -53,9 +53,10 @@ def make_workload(args):
         return synth.config_roofline(n_strokes=args.strokes, n_lassos=args.lassos)
     if args.config == "large":
         return synth.config_large(n_strokes=args.strokes, n_lassos=args.lassos)
-    if args.config == "mid":   # a 4096^2 version of the roofline model, for quick runs and profiles
-        return synth.config_roofline(n_strokes=args.strokes, n_lassos=args.lassos, n_theta=707, n_h=354,
-                                     side=4096)
+    if args.config == "mid":   # a smaller version of the roofline model (default 4096^2), for quick runs and profiles
+        side = args.atlas_side or 4096
+        return synth.config_roofline(n_strokes=args.strokes, n_lassos=args.lassos, n_theta=round(2828 * side / 16384),
+                                     n_h=round(1414 * side / 16384), side=side)
     return synth.config_small()
 
 
@@ -435,7 +436,7 @@ def run_batch(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    bms = synth.config_batch(args.models, depth_side=1024)
+    bms = synth.config_batch(args.models or 256, depth_side=1024)
     models, queues, layers, inits = [], [], [], []
     for bm in bms:
         mesh = lcl.Mesh.from_host(bm.mesh, dev)
@@ -593,7 +594,7 @@ def run_serve(args):
     from paper_2501_14807_gb300 import serve
 
     torch.cuda.set_device(0)
-    models, budget, sphere_of, lasso_of = serving_setup(args.models)
+    models, budget, sphere_of, lasso_of = serving_setup(args.models or 128)
     out = {}
     for mode in ("batched", "per_request"):
         srv = serve.Server(models, hbm_budget_bytes=budget)
@@ -647,9 +648,12 @@ def main():
     ap.add_argument("--config", default="roofline", choices=["roofline", "large", "mid", "small", "batch", "serve"])
     ap.add_argument("--rate", type=float, default=20000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=5.0, help="serving: trace length (s)")
-    ap.add_argument("--models", type=int, default=256, help="models in the batching / serving workload")
+    ap.add_argument("--models", type=int, default=None,
+                    help="models in the batching (default 256) / serving (default 128: 64 resident + 64 spilled) workload")
     ap.add_argument("--serving-models", type=int, default=32,
                     help="models of the short serving run reported in the headline line (0: skip)")
+    ap.add_argument("--atlas-side", type=int, default=None,
+                    help="mid config: atlas side (default 4096; the mesh is scaled with it)")
     ap.add_argument("--strokes", type=int, default=None)
     ap.add_argument("--lassos", type=int, default=None)
     ap.add_argument("--cpu-rows", type=int, default=64, help="rows of the texture the CPU oracle baseline covers")

@@ -482,8 +482,8 @@ lcl_status batch_upload_impl(const lcl_batch_limits *lim, const lcl_batch_model 
     if (ws_bytes < L.total) return fail(LCL_ERR_OUT_OF_MEMORY, "batch workspace smaller than lcl_batch_workspace_bytes");
     if (host_bytes < L.upload) return fail(LCL_ERR_OUT_OF_MEMORY, "batch staging smaller than lcl_batch_staging_bytes");
     char *img = static_cast<char *>(host_staging);  // image of the uploaded part of the workspace
-    const size_t used = L.super_model + align256((size_t)std::max<int64_t>(n_supers, 1) * 4);
-    std::memset(img, 0, L.lasso_in);  // header, models, strokes (lasso inputs are written field by field)
+    const size_t head = L.models + (size_t)n_models * sizeof(BModel);  // header + models
+    std::memset(img, 0, head);
     BHdr hdr;
     std::memset(&hdr, 0, sizeof(hdr));
     hdr.n_models = n_models;
@@ -537,9 +537,17 @@ lcl_status batch_upload_impl(const lcl_batch_limits *lim, const lcl_batch_model 
         d.bias = lassos[j].bias;
         d.pad = 0;
     }
-    // the header and every used descriptor, in one copy (the unused tails of the arrays are not read)
-    cudaError_t e = cudaMemcpyAsync(ws, img, used, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "batch descriptor upload");
+    // the used front of each region (the kernels read no further; the limits may be far larger)
+    const size_t part[4][2] = {{0, head},
+                               {L.strokes, (size_t)n_strokes * sizeof(BStroke)},
+                               {L.lasso_in, (size_t)n_lassos * sizeof(BLassoIn)},
+                               {L.super_model, (size_t)n_supers * 4}};
+    char *dst = static_cast<char *>(ws);
+    for (const auto &pc : part) {
+        if (pc[1] == 0) continue;
+        const cudaError_t e = cudaMemcpyAsync(dst + pc[0], img + pc[0], pc[1], cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch descriptor upload");
+    }
     return LCL_OK;
 }
 

@@ -11,10 +11,14 @@ textures).  This module is the server-side counterpart for many models at once:
   it is admitted again;
 * per-model FIFO queues: a model's requests are applied in arrival order;
 * continuous batching: every epoch takes, for each model with queued work, the leading run of edit
-  requests (up to 64 per layer) and at most one query, launches all edits as one batched edit
-  (``lcl_batch_edit``) followed by the queries (``lcl_overlay`` + ``lcl_label_area``) on one compute
-  stream, and records an event; requests that arrive meanwhile join the next epoch, which is
-  prepared on the host while the previous one runs (two epochs in flight);
+  requests (up to 64 per layer) and at most one query, uploads all edits as one batch
+  (``lcl_batch_upload``) and replays a CUDA graph of the batched launch, followed by the queries
+  (``lcl_overlay`` + ``lcl_label_area``) on one compute stream, and records an event; requests that
+  arrive meanwhile join the next epoch, which is prepared on the host while the previous one runs
+  (two epochs in flight, each with its own workspace, staging and graph);
+* one launch shape for every epoch: the workspaces are sized for the largest possible epoch (every
+  layer of every model with a full queue), so the graph captured once per in-flight slot serves
+  every epoch;
 * latency: host arrival time to the host observing the epoch's completion event.
 
 Everything that computes runs in liblcl.so; this module only schedules.
@@ -76,11 +80,11 @@ class Server:
     """Resident pool + FIFO queues + continuous batching over one compute stream."""
 
     def __init__(self, models, hbm_budget_bytes, device="cuda", max_edits_per_layer=lcl.BATCH_MAX_STROKES,
-                 max_in_flight=2, result_ring=4096, max_labels=256):
+                 max_in_flight=2, result_ring=4096, max_labels=256, config=None, graphs=True):
         self.dev = torch.device(device)
         self.max_in_flight = max_in_flight
-        self._ws = [None] * max_in_flight       # batch workspace / staging per in-flight slot
-        self._stg = [None] * max_in_flight
+        self.config = config                    # batched launch shape (None: the library default)
+        self.use_graphs = graphs                # replay a captured launch (else launch directly)
         self._ring = torch.empty((result_ring, 2, max_labels), dtype=torch.int64).pin_memory()
         self._ring_next = 0
         self.max_labels = max_labels
@@ -99,6 +103,21 @@ class Server:
                 self._spill(s)
         torch.cuda.synchronize(self.dev)
         self.ws_sel = None
+        # the largest epoch: every layer of every model, each with a full queue of edits
+        def tiles_of(m):   # tiles per side, super-tiles per side
+            t = -(-m.side // m.tile)
+            return t, -(-t // lcl.SUPER)
+
+        pairs = sum(m.n_layers for m in models)
+        supers = sum(m.n_layers * tiles_of(m)[1] ** 2 for m in models)
+        tiles = sum(m.n_layers * tiles_of(m)[0] ** 2 for m in models)
+        self.limits = lcl.batch_limits(pairs, pairs * self.max_edits, pairs * self.max_edits, supers, tiles)
+        n_stg = int(lcl.library().lcl_batch_staging_bytes(lcl.C.byref(self.limits)))
+        self._ws = [lcl.batch_workspace(self.limits, self.dev) for _ in range(max_in_flight)]
+        self._stg = [torch.empty(n_stg, dtype=torch.uint8).pin_memory() for _ in range(max_in_flight)]
+        with torch.cuda.stream(self.compute):
+            self._graphs = [lcl.BatchGraph(self.limits, self.config, ws) if graphs else None for ws in self._ws]
+        torch.cuda.synchronize(self.dev)
 
     # ---- pool ---------------------------------------------------------------------------
 
@@ -216,9 +235,13 @@ class Server:
         batch = None
         with torch.cuda.stream(self.compute):
             if models:
-                batch = lcl.Batch(models, work, self._ws[slot], self._stg[slot])
-                self._ws[slot], self._stg[slot] = batch.workspace, batch.staging
-                lcl.lcl_batch_edit(batch, self.compute)
+                batch = lcl.Batch(models, work, self._ws[slot], self._stg[slot], limits=self.limits,
+                                  config=self.config)
+                if self.use_graphs:
+                    lcl.lcl_batch_upload(batch, self.compute)
+                    self._graphs[slot].replay()
+                else:
+                    lcl.lcl_batch_edit(batch, self.compute)
             results = []
             for s, req in queries:
                 op, la, lb, n_labels = req.query

@@ -233,7 +233,9 @@ def config_roofline(n_strokes: int = 1000, n_lassos: int = 20, n_cams: int = 4,
     rng = _rng(0x43414D, 32)
     cams = [orbit_camera(m, depth_side, depth_side, rng) for _ in range(n_cams)]
     las = lassos(m, cams, n_lassos, 32, 1, 255, 4)
-    return Workload("vessel-8M-16384sq-u8", m, side, side, 32, 1, 4, s, cams, las,
+    mt = m.n_tri / 1e6
+    tri = f"{mt:.0f}M" if mt >= 1 else f"{m.n_tri / 1e3:.0f}k"
+    return Workload(f"vessel-{tri}-{side}sq-u8", m, side, side, 32, 1, 4, s, cams, las,
                     overlays=[("xor", 0, 1), ("or", 2, 3)])
 
 
