@@ -6,7 +6,7 @@ Workload (default): the roofline-size model -- a displaced vessel of 2828 x 1414
 through the C ABI:
   atlas build (quantise, UV rasterise, interpolate, boxes, area weights)
   1000 sphere strokes (radii log-uniform 1-30% of the bbox diagonal), one call per layer,
-      one cull + one apply launch per stroke
+      one launch per stroke (it applies its stroke and culls the next)
   4 depth maps (2048^2) and 20 star lassos on them
   XOR(L0, L1) and OR(L2, L3) overlays, per-label area (256 labels) of the 4 layers
 
@@ -352,7 +352,7 @@ def run_ours(args):
         "config": workload_desc(w, args),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic,
-                     "kernel": "sphere edit (k_sphere_cull + k_sphere_apply per stroke)",
+                     "kernel": "sphere edit (k_sphere_step, one launch per stroke)",
                      "algorithmic_bytes_per_launch": sph_bytes / max(n_strokes, 1),
                      "ms_per_launch": sph_ms / args.steps / max(n_strokes, 1)},
         "cpu_baseline": cpu,
