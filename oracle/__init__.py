@@ -203,6 +203,26 @@ def select_lasso(atlas: Atlas, layer, m, dmap, poly, label, bias=2.0 ** -10, wan
     return int(hits[0]), amb
 
 
+def select_tool(atlas: Atlas, layer, m, dmap, centre, size, shape=None, label=1, bias=2.0 ** -10,
+                want_ambiguous=True):
+    """The paper's editing tool: a window of size = (tw, th) pixels centred at centre = (px, py) on the
+    screen, masked by `shape` (uint8 [H_m, W_m], row 0 at the bottom) or, if None, by the inscribed
+    circle.  Applies it to ``layer`` in place; returns (hits, ambiguous mask)."""
+    assert layer.shape == atlas.tri.shape
+    m = np.ascontiguousarray(m, dtype=np.float32)
+    Hs, Ws = dmap.shape
+    hits = np.zeros(1, np.uint64)
+    amb = np.zeros(atlas.tri.shape, np.uint8) if want_ambiguous else None
+    sh = None if shape is None else np.ascontiguousarray(shape, dtype=np.uint8)
+    sw, shh = (0, 0) if sh is None else (sh.shape[1], sh.shape[0])
+    _chk(lib().orc_select_tool(C.c_int64(atlas.n_texels), _p(atlas.px), _p(atlas.py), _p(atlas.pz), _p(atlas.tri),
+                               _p(layer), C.c_int(layer.itemsize), _p(m), C.c_int32(Ws), C.c_int32(Hs),
+                               _p(np.ascontiguousarray(dmap, np.float32)), C.c_float(centre[0]), C.c_float(centre[1]),
+                               C.c_float(size[0]), C.c_float(size[1]), _p(sh), C.c_int32(sw), C.c_int32(shh),
+                               C.c_uint32(int(label)), C.c_float(bias), _p(hits), _p(amb)), "select_tool")
+    return int(hits[0]), amb
+
+
 def overlay(atlas: Atlas, a, b, op, flags=0):
     out = np.empty_like(a)
     op = OPS[op] if isinstance(op, str) else int(op)

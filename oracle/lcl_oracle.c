@@ -616,6 +616,91 @@ int orc_select_lasso(int64_t n_texels, const int32_t *px, const int32_t *py, con
 }
 
 /* ------------------------------------------------------------------------- */
+/* The paper's editing tool (Section 4.3.1, Fig. 3).  The tool window is the   */
+/* tw x th pixel area centred on the tool position (px, py); projective        */
+/* texturing maps it onto the tool's shape texture (scale and translate        */
+/* factors S_f, T_f), coordinates outside it are discarded (Fig. 3 b), and the */
+/* shape texture masks the rest (Fig. 3 c); the depth test with a small bias   */
+/* comes first (Fig. 3 a).  READING:                                           */
+/*  - the screen point (xs, ys) of a covered texel is computed as for lassos;  */
+/*  - with a shape texture of W_m x H_m texels (row 0 at the bottom):          */
+/*      fu = (xs - x0) * su,  fv = (ys - y0) * sv   (FP32, in that order)       */
+/*    with x0 = float(px - tw/2), su = float(W_m / tw), y0, sv likewise        */
+/*    (computed in double, rounded once); the texel is in the tool iff         */
+/*    0 <= fu < W_m, 0 <= fv < H_m and shape[floor(fv)][floor(fu)] != 0;       */
+/*  - without a shape texture the shape is the circle (ellipse) inscribed in   */
+/*    the window: ex = (xs - px) * kx, ey = (ys - py) * ky with kx =           */
+/*    float(2 / tw), ky = float(2 / th), inside iff ex*ex + ey*ey <= 1 (FP32,  */
+/*    products then the sum);                                                  */
+/*  - visible iff z <= D[floor(ys)][floor(xs)] + bias, as for lassos.          */
+/* Ambiguous texels (double): within 1e-4 px of the circle or of a shape-cell  */
+/* boundary line, or depth margin below 1e-6.                                  */
+/* ------------------------------------------------------------------------- */
+int orc_select_tool(int64_t n_texels, const int32_t *px, const int32_t *py, const int32_t *pz, const uint32_t *tri,
+                    void *layer, int dtype_bytes, const float m[16], int32_t Ws, int32_t Hs, const float *depth,
+                    float tpx, float tpy, float tw, float th, const uint8_t *shape, int32_t shape_w,
+                    int32_t shape_h, uint32_t label, float bias, uint64_t *hits, uint8_t *ambiguous)
+{
+    if (dtype_bytes != 1 && dtype_bytes != 2) return ORC_EINVAL;
+    if (label >= (1u << (8 * dtype_bytes))) return ORC_EINVAL;
+    if (!(tw > 0.0f) || !(th > 0.0f)) return ORC_EINVAL;
+    if (shape && (shape_w < 1 || shape_h < 1)) return ORC_EINVAL;
+    const float x0 = (float)((double)tpx - 0.5 * (double)tw), y0 = (float)((double)tpy - 0.5 * (double)th);
+    const float su = shape ? (float)((double)shape_w / (double)tw) : 0.0f;
+    const float sv = shape ? (float)((double)shape_h / (double)th) : 0.0f;
+    const float kx = (float)(2.0 / (double)tw), ky = (float)(2.0 / (double)th);
+    uint64_t h = 0;
+    for (int64_t l = 0; l < n_texels; ++l) {
+        if (ambiguous) ambiguous[l] = 0;
+        if (tri[l] == ORC_NONE) continue;
+        float c[4];
+        clip_of(m, px[l], py[l], pz[l], c);
+        if (!(c[3] > 0.0f)) continue;
+        float zn = c[2] / c[3];
+        if (!(zn >= 0.0f && zn <= 1.0f)) continue;
+        float xs = screen_of(c[0] / c[3], Ws), ys = screen_of(c[1] / c[3], Hs);
+        if (!(xs >= 0.0f && xs < (float)Ws && ys >= 0.0f && ys < (float)Hs)) continue;
+        int32_t ix = (int32_t)xs, iy = (int32_t)ys; /* xs, ys >= 0: truncation is floor */
+        float dref = depth[(int64_t)iy * Ws + ix];
+        int visible = zn <= dref + bias;
+        int inside = 0;
+        double near_edge = INFINITY; /* px distance to the shape's boundary, for the ambiguity flag */
+        if (shape) {
+            float fu = (xs - x0) * su, fv = (ys - y0) * sv;
+            if (fu >= 0.0f && fu < (float)shape_w && fv >= 0.0f && fv < (float)shape_h)
+                inside = shape[(int64_t)(int32_t)fv * shape_w + (int32_t)fu] != 0;
+            if (ambiguous) {
+                double du = ((double)xs - x0) * ((double)shape_w / tw), dv = ((double)ys - y0) * ((double)shape_h / th);
+                if (du > -1.0 && du < shape_w + 1.0 && dv > -1.0 && dv < shape_h + 1.0) {
+                    double eu = fabs(du - floor(du + 0.5)) * (tw / (double)shape_w);
+                    double ev = fabs(dv - floor(dv + 0.5)) * (th / (double)shape_h);
+                    near_edge = eu < ev ? eu : ev;
+                }
+            }
+        } else {
+            float ex = (xs - tpx) * kx, ey = (ys - tpy) * ky;
+            float ex2 = ex * ex, ey2 = ey * ey;
+            inside = ex2 + ey2 <= 1.0f;
+            if (ambiguous) {
+                double dx = ((double)xs - tpx) * (2.0 / tw), dy = ((double)ys - tpy) * (2.0 / th);
+                double rmin = 0.5 * (tw < th ? tw : th);
+                near_edge = fabs(sqrt(dx * dx + dy * dy) - 1.0) * rmin;
+            }
+        }
+        if (inside && visible) {
+            store_label(layer, dtype_bytes, l, label);
+            ++h;
+        }
+        if (ambiguous) {
+            double md = fabs((double)zn - ((double)dref + (double)bias));
+            if (near_edge < 1e-4 || md < 1e-6) ambiguous[l] = 1;
+        }
+    }
+    if (hits) *hits = h;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Overlay of two layers.  Layer systems combine layers with arithmetic,      */
 /* logic, geometric and topological operations (Section 3.4.2); the paper's   */
 /* architecture claims the same capability.  READING: bitwise operators on the */
