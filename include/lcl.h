@@ -239,6 +239,32 @@ lcl_status lcl_select_lasso(const lcl_atlas *atlas, void *layer, lcl_dtype dtype
                             const float *depth, const float *poly_xy, int32_t n_vertices, uint32_t label,
                             float bias, uint64_t *hits_out, void *workspace, size_t ws_bytes, lcl_stream stream);
 
+/* The paper's editing tool (Section 4.3.1, Fig. 3): a tool window of tw x th pixels centred on the
+ * tool position (px, py) is mapped by projective texturing onto the tool's shape texture (the
+ * scale and translate factors S_f, T_f), points outside it are discarded (Fig. 3b) and the shape
+ * masks the rest (Fig. 3c), after the depth test with a small bias (Fig. 3a). */
+typedef struct {
+    float px, py;             /* tool position (window centre), screen pixels, row 0 at the bottom */
+    float tw, th;             /* tool window size in pixels, > 0 (a circle of radius R: 2R x 2R) */
+    const uint8_t *shape;     /* device, shape_h rows x shape_w bytes, row 0 at the bottom, non-zero =
+                                 inside; NULL = the circle (ellipse) inscribed in the window */
+    int32_t shape_w, shape_h; /* 1..4096 each when shape is given */
+} lcl_tool;
+
+/* Tool selection: for every covered texel, the screen point (xs, ys) and depth test as in
+ * lcl_select_lasso; then, in FP32 in this order,
+ *   with a shape: fu = (xs - x0) * su, fv = (ys - y0) * sv, x0 = float(px - tw/2),
+ *     su = float(shape_w / tw) (y0, sv likewise, each from double, rounded once); inside iff
+ *     0 <= fu < shape_w, 0 <= fv < shape_h and shape[floor(fv)][floor(fu)] != 0;
+ *   without: ex = (xs - px) * float(2/tw), ey = (ys - py) * float(2/th); inside iff
+ *     ex*ex + ey*ey <= 1.
+ * Selected texels get `label`.  Workspace: lcl_select_workspace_bytes(atlas, 1).  hits_out:
+ * device, one uint64 (nullable).  Errors: as lcl_select_lasso; LCL_ERR_INVALID_ARG for a
+ * non-finite or non-positive window, or shape sizes outside 1..4096. */
+lcl_status lcl_select_tool(const lcl_atlas *atlas, void *layer, lcl_dtype dtype, const lcl_camera *camera,
+                           const float *depth, const lcl_tool *tool, uint32_t label, float bias, uint64_t *hits_out,
+                           void *workspace, size_t ws_bytes, lcl_stream stream);
+
 /* ---- batched edits -------------------------------------------------------- */
 
 #define LCL_BATCH_MAX_STROKES 64  /* queued strokes per model per batch */

@@ -332,6 +332,33 @@ lcl_status lcl_select_lasso(const lcl_atlas *atlas, void *layer, lcl_dtype dtype
                              reinterpret_cast<cudaStream_t>(stream));
 }
 
+lcl_status lcl_select_tool(const lcl_atlas *atlas, void *layer, lcl_dtype dtype, const lcl_camera *camera,
+                           const float *depth, const lcl_tool *tool, uint32_t label, float bias, uint64_t *hits_out,
+                           void *workspace, size_t ws_bytes, lcl_stream stream) {
+    lcl_status s = check_atlas(atlas, true);
+    if (s != LCL_OK) return s;
+    const int db = dtype_bytes(dtype);
+    if (!db) return fail(LCL_ERR_INVALID_ARG, "dtype must be LCL_U8 or LCL_U16");
+    if (!layer || !aligned(layer, 16)) return fail(LCL_ERR_INVALID_ARG, "layer must be a 16-byte aligned device pointer");
+    s = check_camera(camera);
+    if (s != LCL_OK) return s;
+    if (!depth || !aligned(depth, 4)) return fail(LCL_ERR_INVALID_ARG, "depth must be a 4-byte aligned device pointer");
+    if (!tool) return fail(LCL_ERR_INVALID_ARG, "tool is NULL");
+    if (!std::isfinite(tool->px) || !std::isfinite(tool->py) || !std::isfinite(tool->tw) || !std::isfinite(tool->th) ||
+        !(tool->tw > 0.0f) || !(tool->th > 0.0f) || std::fabs(tool->px) > 1e7f || std::fabs(tool->py) > 1e7f ||
+        tool->tw > 1e7f || tool->th > 1e7f)
+        return fail(LCL_ERR_INVALID_ARG, "tool window must be finite, positive and below 1e7 px");
+    if (tool->shape && (tool->shape_w < 1 || tool->shape_w > 4096 || tool->shape_h < 1 || tool->shape_h > 4096))
+        return fail(LCL_ERR_INVALID_ARG, "tool shape sizes must be 1..4096");
+    if (label > (db == 1 ? 0xFFu : 0xFFFFu)) return fail(LCL_ERR_INVALID_ARG, "label does not fit the layer dtype");
+    if (!std::isfinite(bias)) return fail(LCL_ERR_INVALID_ARG, "bias is not finite");
+    if (hits_out && !aligned(hits_out, 8)) return fail(LCL_ERR_INVALID_ARG, "hits_out must be 8-byte aligned");
+    if (!workspace || !aligned(workspace, 256)) return fail(LCL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < select_ws_bytes(atlas, 1)) return fail(LCL_ERR_OUT_OF_MEMORY, "workspace smaller than lcl_select_workspace_bytes");
+    return select_tool_impl(atlas, layer, db, camera, depth, tool, label, bias, hits_out, workspace,
+                            reinterpret_cast<cudaStream_t>(stream));
+}
+
 lcl_status lcl_batch_limits_of(const lcl_batch_model *models, int32_t n_models, int32_t n_strokes, int32_t n_lassos,
                                lcl_batch_limits *out) {
     return batch_limits_of(models, n_models, n_strokes, n_lassos, out);

@@ -260,6 +260,42 @@ __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restr
     add_hits(hits, cnt);
 }
 
+// ---- the paper's editing tool -------------------------------------------------------------
+
+template <typename L, bool MASK>
+__global__ void __launch_bounds__(kThreads) k_tool_apply(AtlasDev a, L *__restrict__ layer,
+                                                         const __grid_constant__ LassoArg p, ToolArg t,
+                                                         const float *__restrict__ depth,
+                                                         const uint32_t *__restrict__ counter,
+                                                         const uint32_t *__restrict__ list,
+                                                         unsigned long long *hits) {
+    const uint32_t n = *counter;
+    const int32_t qpr = a.T / 4, nq = a.T * qpr;
+    uint32_t cnt = 0;
+    for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const uint32_t tile = list[i];
+        const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+        for (int32_t qd = threadIdx.x; qd < nq; qd += kThreads) {
+            const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
+            if (x >= a.w || y >= a.h) continue;
+            const int64_t l = (int64_t)y * a.w + x;
+            const int4 X = __ldg(reinterpret_cast<const int4 *>(a.px + l));
+            const int4 Y = __ldg(reinterpret_cast<const int4 *>(a.py + l));
+            const int4 Z = __ldg(reinterpret_cast<const int4 *>(a.pz + l));
+            uint32_t m = 0;
+            m |= tool_hit<MASK>(p, t, depth, X.x, Y.x, Z.x) ? 1u : 0u;
+            m |= tool_hit<MASK>(p, t, depth, X.y, Y.y, Z.y) ? 2u : 0u;
+            m |= tool_hit<MASK>(p, t, depth, X.z, Y.z, Z.z) ? 4u : 0u;
+            m |= tool_hit<MASK>(p, t, depth, X.w, Y.w, Z.w) ? 8u : 0u;
+            if (m) {
+                store_hits<L>(layer, l, m, p.label);
+                cnt += __popc(m);
+            }
+        }
+    }
+    add_hits(hits, cnt);
+}
+
 struct SelWs {
     uint32_t *counters, *list, *list2;  // two candidate lists: strokes alternate between them
 };
@@ -354,4 +390,41 @@ lcl_status select_lasso_impl(const lcl_atlas *atlas, void *layer, int dtype_byte
     return LCL_OK;
 }
 
+lcl_status select_tool_impl(const lcl_atlas *atlas, void *layer, int dtype_bytes, const lcl_camera *cam,
+                            const float *depth, const lcl_tool *tool, uint32_t label, float bias, uint64_t *hits,
+                            void *ws, cudaStream_t st) {
+    const AtlasDev a = dev_view(atlas);
+    const SelWs w = sel_ws(atlas, 1, ws);
+    unsigned long long *h = reinterpret_cast<unsigned long long *>(hits);
+    static thread_local LassoArg p;  // ~2.8 KB: kept off the stack
+    ToolArg t;
+    fill_tool_arg(t, p, cam, tool, label, bias);
+    k_sel_init<<<1, kThreads, 0, st>>>(w.counters, 1, h);
+    const dim3 cg(atlas->supers_x, atlas->supers_y);
+    k_lasso_cull<<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list);
+    const bool mask = tool->shape != nullptr;
+    if (dtype_bytes == 1) {
+        uint8_t *l = static_cast<uint8_t *>(layer);
+        if (mask)
+            k_tool_apply<uint8_t, true><<<resident_grid(k_tool_apply<uint8_t, true>), kThreads, 0, st>>>(
+                a, l, p, t, depth, w.counters, w.list, h);
+        else
+            k_tool_apply<uint8_t, false><<<resident_grid(k_tool_apply<uint8_t, false>), kThreads, 0, st>>>(
+                a, l, p, t, depth, w.counters, w.list, h);
+    } else {
+        uint16_t *l = static_cast<uint16_t *>(layer);
+        if (mask)
+            k_tool_apply<uint16_t, true><<<resident_grid(k_tool_apply<uint16_t, true>), kThreads, 0, st>>>(
+                a, l, p, t, depth, w.counters, w.list, h);
+        else
+            k_tool_apply<uint16_t, false><<<resident_grid(k_tool_apply<uint16_t, false>), kThreads, 0, st>>>(
+                a, l, p, t, depth, w.counters, w.list, h);
+    }
+    count_launches(3);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "lcl_select_tool launch");
+    return LCL_OK;
+}
+
 }  // namespace lcl
+

@@ -252,6 +252,49 @@ __device__ __forceinline__ bool lasso_hit(const LassoArg &p, const Edges &sh, co
 
 
 
+// The paper's editing tool (Section 4.3.1): window and shape, with the FP32 constants of the
+// tool-space map precomputed on the host (each from double, rounded once).
+struct ToolArg {
+    float px, py;    // tool position (window centre), pixels
+    float kx, ky;    // 2 / tw, 2 / th (inscribed circle)
+    float x0, y0;    // window corner px - tw/2, py - th/2
+    float su, sv;    // shape texels per pixel
+    float fw, fh;    // shape size as float
+    const uint8_t *shape;  // null: inscribed circle
+    int32_t sw, sh;
+};
+
+// Tool test of one texel: projection, viewport and depth test as for lassos (the window's
+// bounding box, widened, in p's division-free reject), then the shape (MASK) or the circle.
+template <bool MASK>
+__device__ __forceinline__ bool tool_hit(const LassoArg &p, const ToolArg &t, const float *__restrict__ depth,
+                                         int32_t X, int32_t Y, int32_t Z) {
+    if (X == INT32_MIN) return false;  // uncovered
+    const float fx = (float)X, fy = (float)Y, fz = (float)Z;
+    const float cw = clip_row(p.m + 12, fx, fy, fz);
+    if (!(cw > 0.0f)) return false;
+    const float cx = clip_row(p.m, fx, fy, fz);
+    if (cx < __fmul_rn(p.nx0, cw) || cx > __fmul_rn(p.nx1, cw)) return false;
+    const float cy = clip_row(p.m + 4, fx, fy, fz);
+    if (cy < __fmul_rn(p.ny0, cw) || cy > __fmul_rn(p.ny1, cw)) return false;
+    const float xs = screen_of(__fdiv_rn(cx, cw), p.ws);
+    const float ys = screen_of(__fdiv_rn(cy, cw), p.hs);
+    if (!(xs >= 0.0f && xs < p.ws && ys >= 0.0f && ys < p.hs)) return false;
+    if (MASK) {
+        const float fu = __fmul_rn(__fsub_rn(xs, t.x0), t.su), fv = __fmul_rn(__fsub_rn(ys, t.y0), t.sv);
+        if (!(fu >= 0.0f && fu < t.fw && fv >= 0.0f && fv < t.fh)) return false;
+        if (__ldg(t.shape + (int64_t)__float2int_rz(fv) * t.sw + __float2int_rz(fu)) == 0) return false;
+    } else {
+        const float ex = __fmul_rn(__fsub_rn(xs, t.px), t.kx), ey = __fmul_rn(__fsub_rn(ys, t.py), t.ky);
+        if (!(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)) <= 1.0f)) return false;
+    }
+    const float zn = __fdiv_rn(clip_row(p.m + 8, fx, fy, fz), cw);
+    if (!(zn >= 0.0f && zn <= 1.0f)) return false;
+    const int32_t ix = __float2int_rz(xs), iy = __float2int_rz(ys);
+    const float d = __ldg(depth + (int64_t)iy * p.w_s + ix);
+    return zn <= __fadd_rn(d, p.bias);
+}
+
 // CTAs of `threads` threads that fit on one SM at once (at least 1).
 template <typename K>
 inline int resident_per_sm(K kernel, int threads) {
@@ -336,6 +379,31 @@ inline void fill_lasso_arg(LassoArg &p, const lcl_camera *cam, const float *poly
             if (lasso_band_has(p, b, e, bh)) p.band_edge[cnt++] = (uint8_t)e;
     }
     p.band_off[kBands] = (uint16_t)cnt;
+}
+
+// Tool argument and the culling argument (the window as a 4-vertex polygon) from a tool.
+inline void fill_tool_arg(ToolArg &t, LassoArg &p, const lcl_camera *cam, const lcl_tool *tool, uint32_t label,
+                          float bias) {
+    const double px = tool->px, py = tool->py, tw = tool->tw, th = tool->th;
+    t.px = tool->px;
+    t.py = tool->py;
+    t.kx = (float)(2.0 / tw);
+    t.ky = (float)(2.0 / th);
+    t.x0 = (float)(px - 0.5 * tw);
+    t.y0 = (float)(py - 0.5 * th);
+    t.shape = tool->shape;
+    t.sw = tool->shape ? tool->shape_w : 0;
+    t.sh = tool->shape ? tool->shape_h : 0;
+    t.su = tool->shape ? (float)((double)tool->shape_w / tw) : 0.0f;
+    t.sv = tool->shape ? (float)((double)tool->shape_h / th) : 0.0f;
+    t.fw = (float)t.sw;
+    t.fh = (float)t.sh;
+    // the window's corners, widened by a pixel so rounding of x0 + tw cannot cut it
+    const float win[8] = {(float)(px - 0.5 * tw - 1.0), (float)(py - 0.5 * th - 1.0),
+                          (float)(px + 0.5 * tw + 1.0), (float)(py - 0.5 * th - 1.0),
+                          (float)(px + 0.5 * tw + 1.0), (float)(py + 0.5 * th + 1.0),
+                          (float)(px - 0.5 * tw - 1.0), (float)(py + 0.5 * th + 1.0)};
+    fill_lasso_arg(p, cam, win, 4, label, bias);
 }
 
 }  // namespace lcl

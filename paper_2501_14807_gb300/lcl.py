@@ -29,7 +29,7 @@ DEFAULT_BIAS = 2.0 ** -10
 
 EXPORTS = ["lcl_atlas_bytes", "lcl_atlas_bind", "lcl_atlas_rows", "lcl_atlas_workspace_bytes", "lcl_atlas_build",
            "lcl_quantize_sphere", "lcl_quantize_spheres", "lcl_camera_from_vp", "lcl_select_workspace_bytes", "lcl_select_sphere",
-           "lcl_select_sphere_static", "lcl_depth_workspace_bytes", "lcl_depth_render", "lcl_select_lasso",
+           "lcl_select_sphere_static", "lcl_depth_workspace_bytes", "lcl_depth_render", "lcl_select_lasso", "lcl_select_tool",
            "lcl_batch_limits_of", "lcl_batch_workspace_bytes", "lcl_batch_staging_bytes", "lcl_batch_upload",
            "lcl_batch_launch", "lcl_batch_edit", "lcl_batch_tune",
            "lcl_overlay", "lcl_label_area", "lcl_status_str", "lcl_last_error", "lcl_kernel_launches"]
@@ -56,6 +56,11 @@ class lcl_sphere(C.Structure):
 
 class lcl_camera(C.Structure):
     _fields_ = [("m", C.c_float * 16), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class lcl_tool(C.Structure):
+    _fields_ = [("px", C.c_float), ("py", C.c_float), ("tw", C.c_float), ("th", C.c_float),
+                ("shape", C.c_void_p), ("shape_w", C.c_int32), ("shape_h", C.c_int32)]
 
 
 class lcl_batch_model(C.Structure):
@@ -89,7 +94,7 @@ BATCH_MAX_STROKES = 64
 
 assert C.sizeof(lcl_sphere) == 32 and C.sizeof(lcl_camera) == 72 and C.sizeof(lcl_atlas) == 128
 assert C.sizeof(lcl_batch_model) == 32 and C.sizeof(lcl_batch_stroke) == 40 and C.sizeof(lcl_batch_lasso) == 104
-assert C.sizeof(lcl_batch_limits) == 32 and C.sizeof(lcl_batch_config) == 16
+assert C.sizeof(lcl_batch_limits) == 32 and C.sizeof(lcl_batch_config) == 16 and C.sizeof(lcl_tool) == 32
 
 SPHERE_DTYPE = np.dtype([("cx", "<i4"), ("cy", "<i4"), ("cz", "<i4"), ("pad", "<i4"),
                          ("r2", "<i8"), ("label", "<u4"), ("flags", "<u4")])
@@ -131,6 +136,8 @@ def library():
         "lcl_depth_render": (st, [C.POINTER(lcl_mesh), C.POINTER(lcl_atlas), C.POINTER(lcl_camera), P, P, SZ, P]),
         "lcl_select_lasso": (st, [C.POINTER(lcl_atlas), P, C.c_int, C.POINTER(lcl_camera), P, P, I32, U32, F, P, P,
                                   SZ, P]),
+        "lcl_select_tool": (st, [C.POINTER(lcl_atlas), P, C.c_int, C.POINTER(lcl_camera), P, C.POINTER(lcl_tool), U32, F,
+                                 P, P, SZ, P]),
         "lcl_batch_limits_of": (st, [C.POINTER(lcl_batch_model), I32, I32, I32, C.POINTER(lcl_batch_limits)]),
         "lcl_batch_workspace_bytes": (SZ, [C.POINTER(lcl_batch_limits)]),
         "lcl_batch_staging_bytes": (SZ, [C.POINTER(lcl_batch_limits)]),
@@ -370,6 +377,29 @@ def lcl_select_lasso(atlas: Atlas, layer: torch.Tensor, cam: lcl_camera, depth: 
         C.byref(atlas.c), _ptr(layer), _dtype_code(layer), C.byref(cam), _ptr(depth),
         poly.ctypes.data_as(C.c_void_p), poly.shape[0], int(label), float(bias), _ptr(hits_out), _ptr(ws),
         ws.numel(), _stream(stream)))
+    return hits_out
+
+
+def make_tool(centre, size, shape=None):
+    """lcl_tool for a window of size = (tw, th) pixels centred at centre = (px, py); shape: None (the
+    inscribed circle) or a device uint8 tensor [shape_h, shape_w], row 0 at the bottom."""
+    t = lcl_tool()
+    t.px, t.py = float(centre[0]), float(centre[1])
+    t.tw, t.th = float(size[0]), float(size[1])
+    if shape is not None:
+        assert shape.dtype == torch.uint8 and shape.is_cuda and shape.is_contiguous() and shape.dim() == 2
+        t.shape = shape.data_ptr()
+        t.shape_h, t.shape_w = int(shape.shape[0]), int(shape.shape[1])
+    return t
+
+
+def lcl_select_tool(atlas: Atlas, layer: torch.Tensor, cam: lcl_camera, depth: torch.Tensor, tool: lcl_tool, label,
+                    bias=DEFAULT_BIAS, hits_out=None, workspace=None, stream=None):
+    """The paper's editing tool (window + shape or inscribed circle, depth test) on ``layer``."""
+    ws = workspace if workspace is not None else _workspace(lcl_select_workspace_bytes(atlas, 1), layer.device)
+    _check("lcl_select_tool", library().lcl_select_tool(
+        C.byref(atlas.c), _ptr(layer), _dtype_code(layer), C.byref(cam), _ptr(depth), C.byref(tool), int(label),
+        float(bias), _ptr(hits_out), _ptr(ws), ws.numel(), _stream(stream)))
     return hits_out
 
 

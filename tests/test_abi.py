@@ -203,6 +203,34 @@ def test_host_helpers_match_oracle_without_gpu(lcl):
         assert np.array_equal(np.array(list(out.m), np.float32), oracle.camera_mq(cam.vp, mn, S))
 
 
+def test_tool_rejects_bad_arguments(lcl):
+    lib, a = _bound(lcl)
+    cam = lcl.lcl_camera()
+    cam.width, cam.height = 64, 48
+    for i in range(16):
+        cam.m[i] = 1.0 if i % 5 == 0 else 0.0
+    dptr, lay, ws = C.c_void_p(1 << 41), C.c_void_p(1 << 42), C.c_void_p(1 << 43)
+    wsb = lib.lcl_select_workspace_bytes(C.byref(a), 1)
+
+    def call(tool, label=5, bias=0.001, wsb=wsb):
+        return lib.lcl_select_tool(C.byref(a), lay, 1, C.byref(cam), dptr, C.byref(tool) if tool else None, label,
+                                   C.c_float(bias), None, ws, wsb, None)
+
+    def tool(px=10.0, py=10.0, tw=8.0, th=8.0, shape=None, sw=0, sh=0):
+        t = lcl.lcl_tool()
+        t.px, t.py, t.tw, t.th, t.shape, t.shape_w, t.shape_h = px, py, tw, th, shape, sw, sh
+        return t
+
+    assert call(None) == 1                                         # no tool
+    for bad in (tool(tw=0.0), tool(th=-2.0), tool(px=float("nan")), tool(tw=float("inf")), tool(py=2e7)):
+        assert call(bad) == 1                                      # window not finite / positive / bounded
+    assert call(tool(shape=1 << 40, sw=0, sh=4)) == 1              # shape sizes
+    assert call(tool(shape=1 << 40, sw=4, sh=5000)) == 1
+    assert call(tool(), label=256) == 1                            # label too wide for uint8
+    assert call(tool(), bias=float("nan")) == 1
+    assert call(tool(), wsb=16) == 2                               # workspace too small
+
+
 def test_batch_rejects_bad_arguments_on_host(lcl):
     lib, a = _bound(lcl, W=128, H=128, T=32)
     ws, stg = C.c_void_p(1 << 42), (C.c_uint8 * 4096)()

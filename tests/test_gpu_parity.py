@@ -213,6 +213,54 @@ def test_lasso_within_tolerance(name, make, W, H, T, dt, Ws, Hs):
     assert diff.sum() <= LASSO_TOL * touched
 
 
+@pytest.mark.parametrize("name,make,W,H,T,dt,Ws,Hs", LASSO_CASES, ids=[c[0] for c in LASSO_CASES])
+def test_tool_within_tolerance(name, make, W, H, T, dt, Ws, Hs):
+    """The paper's editing tool: circles of the paper's radii (10-200 px), ellipses, random shape
+    masks, windows half off screen; labels equal to the oracle's except on flagged texels."""
+    mesh = make()
+    o = oracle.Atlas(mesh, W, H, tile=T)
+    m, a = gpu_atlas(mesh, W, H, T)
+    rng = np.random.default_rng(77)
+    cams = [synth.orbit_camera(mesh, Ws, Hs, rng) for _ in range(2)]
+    centres = [(L.cam, L.poly.mean(0)) for L in synth.lassos(mesh, cams, 8, 78, 1, 2, 1)]
+    top = int(min(np.iinfo(dt).max, 900))
+    tools = []
+    for k, (ci, c) in enumerate(centres):
+        r = [10, 40, 70, 100, 200][k % 5]
+        tools.append((ci, (float(c[0]), float(c[1])), (2.0 * r, 2.0 * r), None))
+        mask = (rng.random((int(rng.integers(1, 24)), int(rng.integers(1, 24)))) < 0.5).astype(np.uint8)
+        tools.append((ci, (float(c[0]) + 0.37, float(c[1]) - 0.61), (float(rng.uniform(20, 140)),
+                                                                     float(rng.uniform(20, 140))), mask))
+    tools.append((0, (3.0, Hs - 2.0), (90.0, 60.0), None))                 # mostly off screen
+    tools.append((1, (Ws / 2, Hs / 2), (1.5 * Ws, 1.5 * Hs), np.ones((3, 5), np.uint8)))  # whole screen
+    exp = np.zeros((H, W), dt)
+    layer = to_dev(exp)
+    hits = torch.zeros(1, dtype=torch.int64, device=DEV)
+    touched, amb_all = 0, np.zeros((H, W), bool)
+    depths = {}
+    for ci, cam in enumerate(cams):
+        M = oracle.camera_mq(cam.vp, o.mn, o.S)
+        dm = oracle.depth(mesh, o.mn, o.S, M, Ws, Hs)
+        d = torch.empty((Hs, Ws), dtype=torch.float32, device=DEV)
+        lcl.lcl_depth_render(m, a, lcl.camera(M, Ws, Hs), d)
+        depths[ci] = (M, dm, d)
+    for i, (ci, centre, size, mask) in enumerate(tools):
+        M, dm, d = depths[ci]
+        label = 1 + (i * 37) % top
+        h, amb = oracle.select_tool(o, exp, M, dm, centre, size, mask, label)
+        touched += h
+        amb_all |= amb.astype(bool)
+        shape = None if mask is None else torch.from_numpy(mask).to(DEV)
+        tool = lcl.make_tool(centre, size, shape)
+        lcl.lcl_select_tool(a, layer, lcl.camera(M, Ws, Hs), d, tool, label, hits_out=hits)
+        assert abs(int(hits.item()) - h) <= amb.sum()
+    got = to_np(layer, dt)
+    diff = got != exp
+    assert touched > 1000
+    assert not (diff & ~amb_all).any(), "tool labels differ outside the ambiguous texels"
+    assert diff.sum() <= LASSO_TOL * touched
+
+
 @pytest.mark.parametrize("dt", [np.uint8, np.uint16])
 def test_overlay_bit_exact(dt):
     mesh = synth.vessel_cylindrical(60, 20, seed=4)
