@@ -223,6 +223,26 @@ def select_tool(atlas: Atlas, layer, m, dmap, centre, size, shape=None, label=1,
     return int(hits[0]), amb
 
 
+def select_tool_2d(atlas: Atlas, layer, m, dmap, centre, size, shape=None, label=1, bias=2.0 ** -10, flags=0):
+    """select_tool on the whole texture with texture padding (flags = radius | thickness << 4).
+    Returns (hits, padded, ambiguous mask)."""
+    assert atlas.y0 == 0 and atlas.y1 == atlas.H and layer.shape == atlas.tri.shape
+    m = np.ascontiguousarray(m, dtype=np.float32)
+    Hs, Ws = dmap.shape
+    hits = np.zeros(1, np.uint64)
+    padded = np.zeros(1, np.uint64)
+    amb = np.zeros(atlas.tri.shape, np.uint8)
+    sh = None if shape is None else np.ascontiguousarray(shape, dtype=np.uint8)
+    sw, shh = (0, 0) if sh is None else (sh.shape[1], sh.shape[0])
+    _chk(lib().orc_select_tool_2d(C.c_int32(atlas.W), C.c_int32(atlas.H), _p(atlas.px), _p(atlas.py), _p(atlas.pz),
+                                  _p(atlas.tri), _p(layer), C.c_int(layer.itemsize), _p(m), C.c_int32(Ws),
+                                  C.c_int32(Hs), _p(np.ascontiguousarray(dmap, np.float32)), C.c_float(centre[0]),
+                                  C.c_float(centre[1]), C.c_float(size[0]), C.c_float(size[1]), _p(sh), C.c_int32(sw),
+                                  C.c_int32(shh), C.c_uint32(int(label)), C.c_float(bias), C.c_uint32(int(flags)),
+                                  _p(hits), _p(padded), _p(amb)), "select_tool_2d")
+    return int(hits[0]), int(padded[0]), amb
+
+
 def overlay(atlas: Atlas, a, b, op, flags=0):
     out = np.empty_like(a)
     op = OPS[op] if isinstance(op, str) else int(op)

@@ -636,6 +636,83 @@ int orc_select_lasso(int64_t n_texels, const int32_t *px, const int32_t *py, con
 /* Ambiguous texels (double): within 1e-4 px of the circle or of a shape-cell  */
 /* boundary line, or depth margin below 1e-6.                                  */
 /* ------------------------------------------------------------------------- */
+typedef struct {
+    const int32_t *px, *py, *pz;
+    const uint32_t *tri;
+    const float *m;
+    int32_t Ws, Hs;
+    const float *depth;
+    float tpx, tpy, tw, th, x0, y0, su, sv, kx, ky, bias;
+    const uint8_t *shape;
+    int32_t shape_w, shape_h;
+} tool_ctx;
+
+/* The tool test of texel l: returns 1 if selected; *amb (if given) = ambiguous. */
+static int tool_eval(const tool_ctx *t, int64_t l, int *amb)
+{
+    if (amb) *amb = 0;
+    if (t->tri[l] == ORC_NONE) return 0;
+    float c[4];
+    clip_of(t->m, t->px[l], t->py[l], t->pz[l], c);
+    if (!(c[3] > 0.0f)) return 0;
+    float zn = c[2] / c[3];
+    if (!(zn >= 0.0f && zn <= 1.0f)) return 0;
+    float xs = screen_of(c[0] / c[3], t->Ws), ys = screen_of(c[1] / c[3], t->Hs);
+    if (!(xs >= 0.0f && xs < (float)t->Ws && ys >= 0.0f && ys < (float)t->Hs)) return 0;
+    int32_t ix = (int32_t)xs, iy = (int32_t)ys; /* xs, ys >= 0: truncation is floor */
+    float dref = t->depth[(int64_t)iy * t->Ws + ix];
+    int visible = zn <= dref + t->bias;
+    int inside = 0;
+    double near_edge = INFINITY; /* px distance to the shape's boundary, for the ambiguity flag */
+    if (t->shape) {
+        float fu = (xs - t->x0) * t->su, fv = (ys - t->y0) * t->sv;
+        if (fu >= 0.0f && fu < (float)t->shape_w && fv >= 0.0f && fv < (float)t->shape_h)
+            inside = t->shape[(int64_t)(int32_t)fv * t->shape_w + (int32_t)fu] != 0;
+        if (amb) {
+            double du = ((double)xs - t->x0) * ((double)t->shape_w / t->tw);
+            double dv = ((double)ys - t->y0) * ((double)t->shape_h / t->th);
+            if (du > -1.0 && du < t->shape_w + 1.0 && dv > -1.0 && dv < t->shape_h + 1.0) {
+                double eu = fabs(du - floor(du + 0.5)) * (t->tw / (double)t->shape_w);
+                double ev = fabs(dv - floor(dv + 0.5)) * (t->th / (double)t->shape_h);
+                near_edge = eu < ev ? eu : ev;
+            }
+        }
+    } else {
+        float ex = (xs - t->tpx) * t->kx, ey = (ys - t->tpy) * t->ky;
+        float ex2 = ex * ex, ey2 = ey * ey;
+        inside = ex2 + ey2 <= 1.0f;
+        if (amb) {
+            double dx = ((double)xs - t->tpx) * (2.0 / t->tw), dy = ((double)ys - t->tpy) * (2.0 / t->th);
+            double rmin = 0.5 * (t->tw < t->th ? t->tw : t->th);
+            near_edge = fabs(sqrt(dx * dx + dy * dy) - 1.0) * rmin;
+        }
+    }
+    if (amb) {
+        double md = fabs((double)zn - ((double)dref + (double)t->bias));
+        *amb = near_edge < 1e-4 || md < 1e-6;
+    }
+    return inside && visible;
+}
+
+static int tool_setup(tool_ctx *t, const int32_t *px, const int32_t *py, const int32_t *pz, const uint32_t *tri,
+                      const float m[16], int32_t Ws, int32_t Hs, const float *depth, float tpx, float tpy, float tw,
+                      float th, const uint8_t *shape, int32_t shape_w, int32_t shape_h, float bias)
+{
+    if (!(tw > 0.0f) || !(th > 0.0f)) return ORC_EINVAL;
+    if (shape && (shape_w < 1 || shape_h < 1)) return ORC_EINVAL;
+    t->px = px; t->py = py; t->pz = pz; t->tri = tri; t->m = m;
+    t->Ws = Ws; t->Hs = Hs; t->depth = depth;
+    t->tpx = tpx; t->tpy = tpy; t->tw = tw; t->th = th; t->bias = bias;
+    t->shape = shape; t->shape_w = shape_w; t->shape_h = shape_h;
+    t->x0 = (float)((double)tpx - 0.5 * (double)tw);
+    t->y0 = (float)((double)tpy - 0.5 * (double)th);
+    t->su = shape ? (float)((double)shape_w / (double)tw) : 0.0f;
+    t->sv = shape ? (float)((double)shape_h / (double)th) : 0.0f;
+    t->kx = (float)(2.0 / (double)tw);
+    t->ky = (float)(2.0 / (double)th);
+    return ORC_OK;
+}
+
 int orc_select_tool(int64_t n_texels, const int32_t *px, const int32_t *py, const int32_t *pz, const uint32_t *tri,
                     void *layer, int dtype_bytes, const float m[16], int32_t Ws, int32_t Hs, const float *depth,
                     float tpx, float tpy, float tw, float th, const uint8_t *shape, int32_t shape_w,
@@ -643,60 +720,87 @@ int orc_select_tool(int64_t n_texels, const int32_t *px, const int32_t *py, cons
 {
     if (dtype_bytes != 1 && dtype_bytes != 2) return ORC_EINVAL;
     if (label >= (1u << (8 * dtype_bytes))) return ORC_EINVAL;
-    if (!(tw > 0.0f) || !(th > 0.0f)) return ORC_EINVAL;
-    if (shape && (shape_w < 1 || shape_h < 1)) return ORC_EINVAL;
-    const float x0 = (float)((double)tpx - 0.5 * (double)tw), y0 = (float)((double)tpy - 0.5 * (double)th);
-    const float su = shape ? (float)((double)shape_w / (double)tw) : 0.0f;
-    const float sv = shape ? (float)((double)shape_h / (double)th) : 0.0f;
-    const float kx = (float)(2.0 / (double)tw), ky = (float)(2.0 / (double)th);
+    tool_ctx t;
+    int rc = tool_setup(&t, px, py, pz, tri, m, Ws, Hs, depth, tpx, tpy, tw, th, shape, shape_w, shape_h, bias);
+    if (rc) return rc;
     uint64_t h = 0;
     for (int64_t l = 0; l < n_texels; ++l) {
-        if (ambiguous) ambiguous[l] = 0;
-        if (tri[l] == ORC_NONE) continue;
-        float c[4];
-        clip_of(m, px[l], py[l], pz[l], c);
-        if (!(c[3] > 0.0f)) continue;
-        float zn = c[2] / c[3];
-        if (!(zn >= 0.0f && zn <= 1.0f)) continue;
-        float xs = screen_of(c[0] / c[3], Ws), ys = screen_of(c[1] / c[3], Hs);
-        if (!(xs >= 0.0f && xs < (float)Ws && ys >= 0.0f && ys < (float)Hs)) continue;
-        int32_t ix = (int32_t)xs, iy = (int32_t)ys; /* xs, ys >= 0: truncation is floor */
-        float dref = depth[(int64_t)iy * Ws + ix];
-        int visible = zn <= dref + bias;
-        int inside = 0;
-        double near_edge = INFINITY; /* px distance to the shape's boundary, for the ambiguity flag */
-        if (shape) {
-            float fu = (xs - x0) * su, fv = (ys - y0) * sv;
-            if (fu >= 0.0f && fu < (float)shape_w && fv >= 0.0f && fv < (float)shape_h)
-                inside = shape[(int64_t)(int32_t)fv * shape_w + (int32_t)fu] != 0;
-            if (ambiguous) {
-                double du = ((double)xs - x0) * ((double)shape_w / tw), dv = ((double)ys - y0) * ((double)shape_h / th);
-                if (du > -1.0 && du < shape_w + 1.0 && dv > -1.0 && dv < shape_h + 1.0) {
-                    double eu = fabs(du - floor(du + 0.5)) * (tw / (double)shape_w);
-                    double ev = fabs(dv - floor(dv + 0.5)) * (th / (double)shape_h);
-                    near_edge = eu < ev ? eu : ev;
-                }
-            }
-        } else {
-            float ex = (xs - tpx) * kx, ey = (ys - tpy) * ky;
-            float ex2 = ex * ex, ey2 = ey * ey;
-            inside = ex2 + ey2 <= 1.0f;
-            if (ambiguous) {
-                double dx = ((double)xs - tpx) * (2.0 / tw), dy = ((double)ys - tpy) * (2.0 / th);
-                double rmin = 0.5 * (tw < th ? tw : th);
-                near_edge = fabs(sqrt(dx * dx + dy * dy) - 1.0) * rmin;
-            }
-        }
-        if (inside && visible) {
+        int amb = 0;
+        if (tool_eval(&t, l, ambiguous ? &amb : NULL)) {
             store_label(layer, dtype_bytes, l, label);
             ++h;
         }
-        if (ambiguous) {
-            double md = fabs((double)zn - ((double)dref + (double)bias));
-            if (near_edge < 1e-4 || md < 1e-6) ambiguous[l] = 1;
-        }
+        if (ambiguous) ambiguous[l] = (uint8_t)amb;
     }
     if (hits) *hits = h;
+    return ORC_OK;
+}
+
+/* The tool with texture padding (Section 4.3.2, read as for sphere strokes): flags = radius |
+ * thickness << 4 (both at most 8).  A padded texel is ambiguous if a texel within the kernel
+ * radius is.  Whole texture (W x H) only. */
+int orc_select_tool_2d(int32_t W, int32_t H, const int32_t *px, const int32_t *py, const int32_t *pz,
+                       const uint32_t *tri, void *layer, int dtype_bytes, const float m[16], int32_t Ws, int32_t Hs,
+                       const float *depth, float tpx, float tpy, float tw, float th, const uint8_t *shape,
+                       int32_t shape_w, int32_t shape_h, uint32_t label, float bias, uint32_t flags, uint64_t *hits,
+                       uint64_t *padded, uint8_t *ambiguous)
+{
+    if (dtype_bytes != 1 && dtype_bytes != 2) return ORC_EINVAL;
+    if (label >= (1u << (8 * dtype_bytes))) return ORC_EINVAL;
+    uint32_t rad = flags & 15u, thick = (flags >> 4) & 15u;
+    if ((flags & ~0xFFu) || rad > 8 || thick > 8) return ORC_EINVAL;
+    tool_ctx t;
+    int rc = tool_setup(&t, px, py, pz, tri, m, Ws, Hs, depth, tpx, tpy, tw, th, shape, shape_w, shape_h, bias);
+    if (rc) return rc;
+    int64_t n = (int64_t)W * H;
+    uint8_t *sel = (uint8_t *)calloc((size_t)n, 1), *amb = (uint8_t *)calloc((size_t)n, 1);
+    if (!sel || !amb) {
+        free(sel);
+        free(amb);
+        return ORC_EINVAL;
+    }
+    uint64_t h = 0, np = 0;
+    for (int64_t l = 0; l < n; ++l) {
+        int a = 0;
+        sel[l] = (uint8_t)tool_eval(&t, l, &a);
+        amb[l] = (uint8_t)a;
+        if (sel[l]) {
+            store_label(layer, dtype_bytes, l, label);
+            ++h;
+        }
+    }
+    if (rad > 0) {
+        int32_t reach = (int32_t)(rad > thick ? rad : thick);
+        for (int32_t y = 0; y < H; ++y)
+            for (int32_t x = 0; x < W; ++x) {
+                int64_t l = (int64_t)y * W + x;
+                if (tri[l] != ORC_NONE) continue;
+                int outline = 0, near = 0, near_amb = 0;
+                for (int32_t dy = -reach; dy <= reach; ++dy)
+                    for (int32_t dx = -reach; dx <= reach; ++dx) {
+                        int32_t yy = y + dy, xx = x + dx;
+                        if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                        int64_t q = (int64_t)yy * W + xx;
+                        if (tri[q] == ORC_NONE) continue;
+                        int32_t ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy;
+                        if (ax <= (int32_t)thick && ay <= (int32_t)thick) outline = 1;
+                        if (ax <= (int32_t)rad && ay <= (int32_t)rad) {
+                            if (sel[q]) near = 1;
+                            if (amb[q]) near_amb = 1;
+                        }
+                    }
+                if (outline && near) {
+                    store_label(layer, dtype_bytes, l, label);
+                    ++np;
+                }
+                if (outline && near_amb) amb[l] = 1;
+            }
+    }
+    if (ambiguous) memcpy(ambiguous, amb, (size_t)n);
+    free(sel);
+    free(amb);
+    if (hits) *hits = h;
+    if (padded) *padded = np;
     return ORC_OK;
 }
 

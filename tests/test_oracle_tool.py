@@ -146,3 +146,40 @@ def test_tool_rejects_bad_arguments():
             oracle.select_tool(a, layer, M, dmap, (3.0, 3.0), size)
     with pytest.raises(oracle.OracleError):
         oracle.select_tool(a, layer, M, dmap, (3.0, 3.0), (5.0, 5.0), None, 256)
+
+
+@pytest.mark.parametrize("rad,thick", [(1, 1), (2, 1), (3, 4), (8, 8), (0, 5)])
+def test_tool_padding_matches_dilations(rad, thick):
+    """Texture padding of a tool edit: uncovered texels within `thickness` of a covered texel
+    (square kernel) and within `radius` of a selected texel get the label -- square-kernel
+    dilations with scipy; radius 0 pads nothing."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    m = synth.vessel_charts(60, 30, 12, 6, 96, seed=2)
+    a = oracle.Atlas(m, 96, 96, tile=16)
+    Ws, Hs = 64, 48
+    cam = synth.orbit_camera(m, Ws, Hs, np.random.default_rng(9))
+    M = oracle.camera_mq(cam.vp, a.mn, a.S)
+    dmap = oracle.depth(m, a.mn, a.S, M, Ws, Hs)
+    centre, size = (Ws * 0.5, Hs * 0.5), (Ws * 0.8, Hs * 0.9)
+    plain = np.zeros(a.tri.shape, np.uint8)
+    h0, amb0 = oracle.select_tool(a, plain, M, dmap, centre, size, None, 4, BIAS)
+    sel = plain == 4
+    lay = np.zeros(a.tri.shape, np.uint8)
+    h, npad, amb = oracle.select_tool_2d(a, lay, M, dmap, centre, size, None, 4, BIAS, oracle.pad_flags(rad, thick))
+    cov = a.covered()
+    if rad == 0:
+        exp_pad = np.zeros_like(cov)
+    else:
+        outline = ~cov & ndimage.maximum_filter(cov, size=2 * thick + 1, mode="constant")
+        exp_pad = outline & ndimage.maximum_filter(sel, size=2 * rad + 1, mode="constant")
+    assert h == h0 and np.array_equal(amb[cov], amb0[cov])
+    assert np.array_equal(lay == 4, sel | exp_pad) and npad == exp_pad.sum()
+    assert h0 > 50 and (rad == 0 or npad > 0)
+
+
+def test_tool_padding_rejects_bad_flags():
+    m, a, M, dmap = _lasso_setup(0)
+    layer = np.zeros(a.tri.shape, np.uint8)
+    for f in (9, 9 << 4, 1 << 8):
+        with pytest.raises(oracle.OracleError):
+            oracle.select_tool_2d(a, layer, M, dmap, (3.0, 3.0), (5.0, 5.0), None, 1, BIAS, f)
