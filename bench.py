@@ -584,6 +584,97 @@ def serving_summary(n_models, rate, duration):
     return st
 
 
+# The paper's per-edit times for its Vessel (312k triangles, GTX 970, OpenGL, texture editing +
+# padding), Fig. 6, by layer side and tool radius in pixels -- context only.
+PAPER_FIG6_VESSEL_MS = {2048: [0.86, 0.86, 0.86, 0.86, 0.86], 4096: [1.89, 1.9, 1.91, 1.91, 2.01],
+                        8192: [5.61, 5.64, 5.68, 5.74, 5.89]}
+TOOL_RADII_PX = [10, 40, 70, 100, 200]
+
+
+def run_tool(args):
+    """The paper's editing experiment (Fig. 6): one layer of a vessel of ~312k triangles at 2048^2,
+    4096^2 and 8192^2, edited with the circular tool of radius 10-200 px at points along the model
+    on a 1920 x 1080 view; per edit the tool selection with texture padding (radius 2, outline
+    thickness 2; the paper states neither), and without padding.  The depth map is rendered once per
+    view, as in the paper (it changes with the camera, not with the edit)."""
+    import torch
+
+    import synth
+    from paper_2501_14807_gb300 import lcl
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    mesh = synth.vessel_cylindrical(560, 280, noise_amp=0.005, noise_freq=16.0, seed=7)
+    Ws, Hs = 1920, 1080
+    p = mesh.pos.astype(np.float64)
+    lo, hi = p.min(0), p.max(0)
+    centre, radius = 0.5 * (lo + hi), 0.5 * float(np.linalg.norm(hi - lo))
+    el, az, dist = np.radians(15.0), 0.4, 2.2 * radius
+    eye = centre + dist * np.array([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)])
+    cam_host = synth.Camera(synth.perspective01(40.0, Ws / Hs, dist - 1.1 * radius, dist + 1.1 * radius) @
+                            synth.look_at(eye, centre), Ws, Hs)
+    rng = np.random.default_rng(61)
+    pts = synth.surface_points(mesh, 400, rng)
+    scr = synth.project_px(cam_host, pts)
+    facing = (pts - centre)[:, :2] @ (eye - centre)[:2] > 0
+    ok = facing & (scr[:, 0] > 250) & (scr[:, 0] < Ws - 250) & (scr[:, 1] > 250) & (scr[:, 1] < Hs - 250)
+    spots = scr[ok][:24]
+    n_edits = len(spots)
+    m = lcl.Mesh.from_host(mesh, dev)
+    stream = torch.cuda.current_stream(dev)
+    rows, tot_tex, tot_ms = [], 0, 0.0
+    for side in (2048, 4096, 8192):
+        a = lcl.Atlas(side, side, 32, mesh.n_tri, dev)
+        lcl.lcl_atlas_build(m, a)
+        cam = lcl.lcl_camera_from_vp(a, cam_host.vp, Ws, Hs)
+        depth = torch.empty((Hs, Ws), dtype=torch.float32, device=dev)
+        lcl.lcl_depth_render(m, a, cam, depth)
+        layer = torch.zeros((side, side), dtype=torch.uint8, device=dev)
+        ws = torch.empty(lcl.lcl_select_workspace_bytes(a, 1), dtype=torch.uint8, device=dev)
+        hits = torch.zeros(n_edits, dtype=torch.int64, device=dev)
+        for ri, r in enumerate(TOOL_RADII_PX):
+            res = {}
+            for mode, flags in (("tea", 0), ("tea_tpa", lcl.pad_flags(2, 2))):
+                tools = [lcl.make_tool((float(x), float(y)), (2.0 * r, 2.0 * r), None, flags) for x, y in spots]
+
+                def edits():
+                    for k, t in enumerate(tools):
+                        lcl.lcl_select_tool(a, layer, cam, depth, t, 1 + k % 250, lcl.DEFAULT_BIAS, hits[k:k + 1], ws,
+                                            stream)
+
+                for _ in range(max(args.warmup, 1)):
+                    edits()
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.steps):
+                    edits()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms = e0.elapsed_time(e1) / (args.steps * n_edits)
+                res[mode] = ms
+                if mode == "tea_tpa":
+                    h = int(hits.sum().item())
+                    tot_tex += h * args.steps
+                    tot_ms += ms * n_edits * args.steps
+                    res["hit_texels_per_edit"] = h / n_edits
+            rows.append({"layer_side": side, "radius_px": r, "ms_per_edit_tea": res["tea"],
+                         "ms_per_edit_tea_tpa": res["tea_tpa"], "hit_texels_per_edit": res["hit_texels_per_edit"],
+                         "paper_fig6_ms": PAPER_FIG6_VESSEL_MS[side][ri]})
+        del a, layer, depth
+        torch.cuda.empty_cache()
+    line = {"metric": METRIC, "value": tot_tex / (tot_ms / 1e3) / 1e9 if tot_ms else 0.0, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded vessel standing in for the paper's scanned Vessel)",
+            "config": {"workload": f"editing tool: vessel {mesh.n_tri} triangles, one u8 layer at 2048^2/4096^2/"
+                                   f"8192^2, circle radius 10-200 px on a {Ws}x{Hs} view, {n_edits} edits per "
+                                   f"radius, padding radius 2 / thickness 2", "view": f"{Ws}x{Hs}"},
+            "per_edit": rows,
+            "note": "paper_fig6_ms: the paper's GTX 970 OpenGL times for its scanned Vessel, context only"}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Serving workload: resident + spillover models (as in the batching workload), 2 layers each,
     an HBM budget that holds about half of them, open-loop Poisson arrivals (70% sphere strokes, 20%
@@ -645,7 +736,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="roofline", choices=["roofline", "large", "mid", "small", "batch", "serve"])
+    ap.add_argument("--config", default="roofline",
+                    choices=["roofline", "large", "mid", "small", "batch", "serve", "tool"])
     ap.add_argument("--rate", type=float, default=20000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=5.0, help="serving: trace length (s)")
     ap.add_argument("--models", type=int, default=None,
@@ -658,7 +750,8 @@ def main():
     ap.add_argument("--lassos", type=int, default=None)
     ap.add_argument("--cpu-rows", type=int, default=64, help="rows of the texture the CPU oracle baseline covers")
     args = ap.parse_args()
-    defaults = {"roofline": (1000, 20), "mid": (1000, 20), "large": (10000, 200), "small": (200, 0), "batch": (0, 0), "serve": (0, 0)}
+    defaults = {"roofline": (1000, 20), "mid": (1000, 20), "large": (10000, 200), "small": (200, 0), "batch": (0, 0),
+                "serve": (0, 0), "tool": (0, 0)}
     if args.strokes is None:
         args.strokes = defaults[args.config][0]
     if args.lassos is None:
@@ -669,6 +762,8 @@ def main():
         run_batch(args)
     elif args.config == "serve":
         run_serve(args)
+    elif args.config == "tool":
+        run_tool(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -249,6 +249,9 @@ typedef struct {
     const uint8_t *shape;     /* device, shape_h rows x shape_w bytes, row 0 at the bottom, non-zero =
                                  inside; NULL = the circle (ellipse) inscribed in the window */
     int32_t shape_w, shape_h; /* 1..4096 each when shape is given */
+    uint32_t flags;           /* texture padding (Section 4.3.2) as for sphere strokes: radius = bits 0-3,
+                                 outline thickness = bits 4-7, both <= 8, other bits 0; 0 = none */
+    int32_t _pad;
 } lcl_tool;
 
 /* Tool selection: for every covered texel, the screen point (xs, ys) and depth test as in
@@ -258,9 +261,12 @@ typedef struct {
  *     0 <= fu < shape_w, 0 <= fv < shape_h and shape[floor(fv)][floor(fu)] != 0;
  *   without: ex = (xs - px) * float(2/tw), ey = (ys - py) * float(2/th); inside iff
  *     ex*ex + ey*ey <= 1.
- * Selected texels get `label`.  Workspace: lcl_select_workspace_bytes(atlas, 1).  hits_out:
- * device, one uint64 (nullable).  Errors: as lcl_select_lasso; LCL_ERR_INVALID_ARG for a
- * non-finite or non-positive window, or shape sizes outside 1..4096. */
+ * Selected texels get `label`; with padding flags, uncovered texels within the outline thickness
+ * of a covered texel and within the radius of a selected texel (square kernels) get it too.
+ * Workspace: lcl_select_workspace_bytes(atlas, 1).  hits_out: device, one uint64 (nullable),
+ * selected texels (padded texels not counted).  Errors: as lcl_select_lasso;
+ * LCL_ERR_INVALID_ARG for a non-finite or non-positive window, shape sizes outside 1..4096 or
+ * padding flags out of range. */
 lcl_status lcl_select_tool(const lcl_atlas *atlas, void *layer, lcl_dtype dtype, const lcl_camera *camera,
                            const float *depth, const lcl_tool *tool, uint32_t label, float bias, uint64_t *hits_out,
                            void *workspace, size_t ws_bytes, lcl_stream stream);

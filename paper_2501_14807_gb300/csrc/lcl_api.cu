@@ -350,6 +350,8 @@ lcl_status lcl_select_tool(const lcl_atlas *atlas, void *layer, lcl_dtype dtype,
         return fail(LCL_ERR_INVALID_ARG, "tool window must be finite, positive and below 1e7 px");
     if (tool->shape && (tool->shape_w < 1 || tool->shape_w > 4096 || tool->shape_h < 1 || tool->shape_h > 4096))
         return fail(LCL_ERR_INVALID_ARG, "tool shape sizes must be 1..4096");
+    if ((tool->flags & ~0xFFu) || (tool->flags & 15u) > 8 || ((tool->flags >> 4) & 15u) > 8)
+        return fail(LCL_ERR_INVALID_ARG, "tool padding radius and thickness must be <= 8, other flag bits 0");
     if (label > (db == 1 ? 0xFFu : 0xFFFFu)) return fail(LCL_ERR_INVALID_ARG, "label does not fit the layer dtype");
     if (!std::isfinite(bias)) return fail(LCL_ERR_INVALID_ARG, "bias is not finite");
     if (hits_out && !aligned(hits_out, 8)) return fail(LCL_ERR_INVALID_ARG, "hits_out must be 8-byte aligned");

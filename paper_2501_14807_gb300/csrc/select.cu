@@ -201,19 +201,44 @@ __global__ void __launch_bounds__(kThreads) k_sphere_step(AtlasDev a, L *__restr
 
 // ---- lasso ---------------------------------------------------------------------------
 
+// Any box of the 3 x 3 neighbourhood of (bx, by) that may hold a texel the lasso (tool) selects.
+__device__ bool near_box_3x3_lasso(const int32_t *boxes, int32_t nx, int32_t ny, int32_t bx, int32_t by,
+                                   const LassoArg &p, const float *__restrict__ depth) {
+    for (int32_t y = max(by - 1, 0); y <= min(by + 1, ny - 1); ++y)
+        for (int32_t x = max(bx - 1, 0); x <= min(bx + 1, nx - 1); ++x) {
+            const int4 *b = reinterpret_cast<const int4 *>(boxes + 8 * ((int64_t)y * nx + x));
+            const int4 lo = b[0], hi = b[1];
+            if (lo.w > 0 && box_may_touch(p, lo, hi, depth)) return true;
+        }
+    return false;
+}
+
+// Candidate tiles of a lasso (or tool window).  With texture padding (PAD) a texel may be written
+// because a neighbour within 8 texels was selected, so a tile (super-tile) is then a candidate if
+// any box of its 3 x 3 neighbourhood is.
+template <bool PAD>
 __global__ void __launch_bounds__(kThreads) k_lasso_cull(AtlasDev a, const __grid_constant__ LassoArg p,
                                                          const float *__restrict__ depth, uint32_t *counter,
                                                          uint32_t *list) {
-    const int4 *sb = reinterpret_cast<const int4 *>(a.super_box + 8 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x));
-    int4 slo = sb[0], shi = sb[1];
-    if (slo.w == 0 || !box_may_touch(p, slo, shi)) return;
-    const int32_t tx = blockIdx.x * LCL_SUPER + (threadIdx.x % LCL_SUPER);
-    const int32_t ty = blockIdx.y * LCL_SUPER + (threadIdx.x / LCL_SUPER);
+    const int32_t sx = blockIdx.x, sy = blockIdx.y;
+    if (PAD) {
+        if (!near_box_3x3_lasso(a.super_box, a.supers_x, a.supers_y, sx, sy, p, nullptr)) return;
+    } else {
+        const int4 *sb = reinterpret_cast<const int4 *>(a.super_box + 8 * ((int64_t)sy * gridDim.x + sx));
+        int4 slo = sb[0], shi = sb[1];
+        if (slo.w == 0 || !box_may_touch(p, slo, shi)) return;
+    }
+    const int32_t tx = sx * LCL_SUPER + (threadIdx.x % LCL_SUPER);
+    const int32_t ty = sy * LCL_SUPER + (threadIdx.x / LCL_SUPER);
     bool cand = false;
     if (tx < a.tiles_x && ty < a.tiles_y) {
-        const int4 *tb = reinterpret_cast<const int4 *>(a.tile_box + 8 * ((int64_t)ty * a.tiles_x + tx));
-        int4 lo = tb[0], hi = tb[1];
-        cand = lo.w > 0 && box_may_touch(p, lo, hi, depth);
+        if (PAD) {
+            cand = near_box_3x3_lasso(a.tile_box, a.tiles_x, a.tiles_y, tx, ty, p, depth);
+        } else {
+            const int4 *tb = reinterpret_cast<const int4 *>(a.tile_box + 8 * ((int64_t)ty * a.tiles_x + tx));
+            int4 lo = tb[0], hi = tb[1];
+            cand = lo.w > 0 && box_may_touch(p, lo, hi, depth);
+        }
     }
     append_candidate(cand, (uint32_t)(ty * a.tiles_x + tx), counter, list);
 }
@@ -262,8 +287,42 @@ __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restr
 
 // ---- the paper's editing tool -------------------------------------------------------------
 
-template <typename L, bool MASK>
-__global__ void __launch_bounds__(kThreads) k_tool_apply(AtlasDev a, L *__restrict__ layer,
+// Texture padding of the uncovered texels of a quad for a tool edit (Section 4.3.2, as for
+// spheres): written if a covered texel lies within the outline thickness and a texel the tool
+// selects within the kernel radius (square kernels).
+template <bool MASK>
+__device__ __forceinline__ uint32_t tool_pad_mask(const AtlasDev &a, int64_t l, int4 X, const LassoArg &p, const ToolArg &t,
+                                  const float *__restrict__ depth) {
+    const int32_t x0 = (int32_t)(l % a.w), y0 = (int32_t)(l / a.w);
+    const int32_t reach = max(t.pad_r, t.pad_t);
+    uint32_t m = 0;
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+        const int32_t xk = k == 0 ? X.x : k == 1 ? X.y : k == 2 ? X.z : X.w;  // a select, not a local array
+        if (xk != INT32_MIN) continue;
+        bool outline = false, near = false;
+        for (int32_t dy = -reach; dy <= reach && !(outline && near); ++dy) {
+            const int32_t yy = y0 + dy;
+            if (yy < 0 || yy >= a.h) continue;
+            for (int32_t dx = -reach; dx <= reach; ++dx) {
+                const int32_t xx = x0 + k + dx;
+                if (xx < 0 || xx >= a.w) continue;
+                const int64_t n = (int64_t)yy * a.w + xx;
+                const int32_t qx = __ldg(a.px + n);
+                if (qx == INT32_MIN) continue;
+                const int32_t ax = abs(dx), ay = abs(dy);
+                if (ax <= t.pad_t && ay <= t.pad_t) outline = true;
+                if (ax <= t.pad_r && ay <= t.pad_r && !near)
+                    near = tool_hit<MASK>(p, t, depth, qx, __ldg(a.py + n), __ldg(a.pz + n));
+            }
+        }
+        if (outline && near) m |= 1u << k;
+    }
+    return m;
+}
+
+template <typename L, bool MASK, bool PAD>
+__global__ void __launch_bounds__(kThreads, 4) k_tool_apply(AtlasDev a, L *__restrict__ layer,
                                                          const __grid_constant__ LassoArg p, ToolArg t,
                                                          const float *__restrict__ depth,
                                                          const uint32_t *__restrict__ counter,
@@ -287,8 +346,9 @@ __global__ void __launch_bounds__(kThreads) k_tool_apply(AtlasDev a, L *__restri
             m |= tool_hit<MASK>(p, t, depth, X.y, Y.y, Z.y) ? 2u : 0u;
             m |= tool_hit<MASK>(p, t, depth, X.z, Y.z, Z.z) ? 4u : 0u;
             m |= tool_hit<MASK>(p, t, depth, X.w, Y.w, Z.w) ? 8u : 0u;
-            if (m) {
-                store_hits<L>(layer, l, m, p.label);
+            const uint32_t pm = PAD ? tool_pad_mask<MASK>(a, l, X, p, t, depth) : 0u;
+            if (m | pm) {
+                store_hits<L>(layer, l, m | pm, p.label);
                 cnt += __popc(m);
             }
         }
@@ -377,7 +437,7 @@ lcl_status select_lasso_impl(const lcl_atlas *atlas, void *layer, int dtype_byte
     fill_lasso_arg(p, cam, poly, nv, label, bias);
     k_sel_init<<<1, kThreads, 0, st>>>(w.counters, 1, h);
     const dim3 cg(atlas->supers_x, atlas->supers_y);
-    k_lasso_cull<<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list);
+    k_lasso_cull<false><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list);
     const int ag = dtype_bytes == 1 ? resident_grid(k_lasso_apply<uint8_t>) : resident_grid(k_lasso_apply<uint16_t>);
     if (dtype_bytes == 1)
         k_lasso_apply<uint8_t><<<ag, kThreads, 0, st>>>(a, static_cast<uint8_t *>(layer), p, depth, w.counters, w.list, h);
@@ -388,6 +448,29 @@ lcl_status select_lasso_impl(const lcl_atlas *atlas, void *layer, int dtype_byte
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "lcl_select_lasso launch");
     return LCL_OK;
+}
+
+template <typename L>
+void launch_tool(int sel, const AtlasDev &a, L *layer, const LassoArg &p, const ToolArg &t, const float *depth,
+                 const SelWs &w, unsigned long long *h, cudaStream_t st) {
+    switch (sel) {  // bit 0: shape mask, bit 1: padding
+    case 0:
+        k_tool_apply<L, false, false><<<resident_grid(k_tool_apply<L, false, false>), kThreads, 0, st>>>(
+            a, layer, p, t, depth, w.counters, w.list, h);
+        break;
+    case 1:
+        k_tool_apply<L, true, false><<<resident_grid(k_tool_apply<L, true, false>), kThreads, 0, st>>>(
+            a, layer, p, t, depth, w.counters, w.list, h);
+        break;
+    case 2:
+        k_tool_apply<L, false, true><<<resident_grid(k_tool_apply<L, false, true>), kThreads, 0, st>>>(
+            a, layer, p, t, depth, w.counters, w.list, h);
+        break;
+    default:
+        k_tool_apply<L, true, true><<<resident_grid(k_tool_apply<L, true, true>), kThreads, 0, st>>>(
+            a, layer, p, t, depth, w.counters, w.list, h);
+        break;
+    }
 }
 
 lcl_status select_tool_impl(const lcl_atlas *atlas, void *layer, int dtype_bytes, const lcl_camera *cam,
@@ -401,25 +484,16 @@ lcl_status select_tool_impl(const lcl_atlas *atlas, void *layer, int dtype_bytes
     fill_tool_arg(t, p, cam, tool, label, bias);
     k_sel_init<<<1, kThreads, 0, st>>>(w.counters, 1, h);
     const dim3 cg(atlas->supers_x, atlas->supers_y);
-    k_lasso_cull<<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list);
-    const bool mask = tool->shape != nullptr;
-    if (dtype_bytes == 1) {
-        uint8_t *l = static_cast<uint8_t *>(layer);
-        if (mask)
-            k_tool_apply<uint8_t, true><<<resident_grid(k_tool_apply<uint8_t, true>), kThreads, 0, st>>>(
-                a, l, p, t, depth, w.counters, w.list, h);
-        else
-            k_tool_apply<uint8_t, false><<<resident_grid(k_tool_apply<uint8_t, false>), kThreads, 0, st>>>(
-                a, l, p, t, depth, w.counters, w.list, h);
-    } else {
-        uint16_t *l = static_cast<uint16_t *>(layer);
-        if (mask)
-            k_tool_apply<uint16_t, true><<<resident_grid(k_tool_apply<uint16_t, true>), kThreads, 0, st>>>(
-                a, l, p, t, depth, w.counters, w.list, h);
-        else
-            k_tool_apply<uint16_t, false><<<resident_grid(k_tool_apply<uint16_t, false>), kThreads, 0, st>>>(
-                a, l, p, t, depth, w.counters, w.list, h);
-    }
+    const bool pad = t.pad_r > 0;
+    if (pad)
+        k_lasso_cull<true><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list);
+    else
+        k_lasso_cull<false><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list);
+    const int sel = (tool->shape != nullptr ? 1 : 0) + (pad ? 2 : 0);
+    if (dtype_bytes == 1)
+        launch_tool<uint8_t>(sel, a, static_cast<uint8_t *>(layer), p, t, depth, w, h, st);
+    else
+        launch_tool<uint16_t>(sel, a, static_cast<uint16_t *>(layer), p, t, depth, w, h, st);
     count_launches(3);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "lcl_select_tool launch");

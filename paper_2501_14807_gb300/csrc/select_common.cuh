@@ -262,6 +262,7 @@ struct ToolArg {
     float fw, fh;    // shape size as float
     const uint8_t *shape;  // null: inscribed circle
     int32_t sw, sh;
+    int32_t pad_r, pad_t;  // texture padding: kernel radius and outline thickness (0: no padding)
 };
 
 // Tool test of one texel: projection, viewport and depth test as for lassos (the window's
@@ -398,6 +399,8 @@ inline void fill_tool_arg(ToolArg &t, LassoArg &p, const lcl_camera *cam, const 
     t.sv = tool->shape ? (float)((double)tool->shape_h / th) : 0.0f;
     t.fw = (float)t.sw;
     t.fh = (float)t.sh;
+    t.pad_r = (int32_t)(tool->flags & 15u);
+    t.pad_t = (int32_t)((tool->flags >> 4) & 15u);
     // the window's corners, widened by a pixel so rounding of x0 + tw cannot cut it
     const float win[8] = {(float)(px - 0.5 * tw - 1.0), (float)(py - 0.5 * th - 1.0),
                           (float)(px + 0.5 * tw + 1.0), (float)(py - 0.5 * th - 1.0),

@@ -60,7 +60,8 @@ class lcl_camera(C.Structure):
 
 class lcl_tool(C.Structure):
     _fields_ = [("px", C.c_float), ("py", C.c_float), ("tw", C.c_float), ("th", C.c_float),
-                ("shape", C.c_void_p), ("shape_w", C.c_int32), ("shape_h", C.c_int32)]
+                ("shape", C.c_void_p), ("shape_w", C.c_int32), ("shape_h", C.c_int32), ("flags", C.c_uint32),
+                ("_pad", C.c_int32)]
 
 
 class lcl_batch_model(C.Structure):
@@ -94,7 +95,7 @@ BATCH_MAX_STROKES = 64
 
 assert C.sizeof(lcl_sphere) == 32 and C.sizeof(lcl_camera) == 72 and C.sizeof(lcl_atlas) == 128
 assert C.sizeof(lcl_batch_model) == 32 and C.sizeof(lcl_batch_stroke) == 40 and C.sizeof(lcl_batch_lasso) == 104
-assert C.sizeof(lcl_batch_limits) == 32 and C.sizeof(lcl_batch_config) == 16 and C.sizeof(lcl_tool) == 32
+assert C.sizeof(lcl_batch_limits) == 32 and C.sizeof(lcl_batch_config) == 16 and C.sizeof(lcl_tool) == 40
 
 SPHERE_DTYPE = np.dtype([("cx", "<i4"), ("cy", "<i4"), ("cz", "<i4"), ("pad", "<i4"),
                          ("r2", "<i8"), ("label", "<u4"), ("flags", "<u4")])
@@ -380,10 +381,17 @@ def lcl_select_lasso(atlas: Atlas, layer: torch.Tensor, cam: lcl_camera, depth: 
     return hits_out
 
 
-def make_tool(centre, size, shape=None):
+def pad_flags(radius, thickness):
+    """Texture padding flags of a sphere stroke or a tool: kernel radius and outline thickness (<= 8)."""
+    return int(radius) | (int(thickness) << 4)
+
+
+def make_tool(centre, size, shape=None, flags=0):
     """lcl_tool for a window of size = (tw, th) pixels centred at centre = (px, py); shape: None (the
-    inscribed circle) or a device uint8 tensor [shape_h, shape_w], row 0 at the bottom."""
+    inscribed circle) or a device uint8 tensor [shape_h, shape_w], row 0 at the bottom; flags:
+    texture padding (pad_flags)."""
     t = lcl_tool()
+    t.flags = int(flags)
     t.px, t.py = float(centre[0]), float(centre[1])
     t.tw, t.th = float(size[0]), float(size[1])
     if shape is not None:

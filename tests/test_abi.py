@@ -226,6 +226,10 @@ def test_tool_rejects_bad_arguments(lcl):
         assert call(bad) == 1                                      # window not finite / positive / bounded
     assert call(tool(shape=1 << 40, sw=0, sh=4)) == 1              # shape sizes
     assert call(tool(shape=1 << 40, sw=4, sh=5000)) == 1
+    for f in (9, 9 << 4, 1 << 8):
+        bad = tool()
+        bad.flags = f
+        assert call(bad) == 1                                      # padding flags out of range
     assert call(tool(), label=256) == 1                            # label too wide for uint8
     assert call(tool(), bias=float("nan")) == 1
     assert call(tool(), wsb=16) == 2                               # workspace too small

@@ -262,6 +262,46 @@ def test_tool_within_tolerance(name, make, W, H, T, dt, Ws, Hs):
 
 
 @pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+def test_tool_padding_within_tolerance(dt):
+    """Tool edits with texture padding on a chart atlas (islands with gutters): circle and mask
+    tools, radius / thickness 1..8, labels equal to the oracle's except on flagged texels."""
+    mesh = synth.vessel_charts(120, 60, 20, 10, 384, seed=8)
+    W = H = 384
+    o = oracle.Atlas(mesh, W, H, tile=16)
+    m, a = gpu_atlas(mesh, W, H, 16)
+    Ws, Hs = 320, 240
+    rng = np.random.default_rng(21)
+    cam = synth.orbit_camera(mesh, Ws, Hs, rng)
+    M = oracle.camera_mq(cam.vp, o.mn, o.S)
+    dm = oracle.depth(mesh, o.mn, o.S, M, Ws, Hs)
+    d = torch.empty((Hs, Ws), dtype=torch.float32, device=DEV)
+    lcl.lcl_depth_render(m, a, lcl.camera(M, Ws, Hs), d)
+    exp = np.zeros((H, W), dt)
+    layer = to_dev(exp)
+    hits = torch.zeros(1, dtype=torch.int64, device=DEV)
+    touched, padded, amb_all = 0, 0, np.zeros((H, W), bool)
+    centres = [L.poly.mean(0) for L in synth.lassos(mesh, [cam], 6, 31, 1, 2, 1)]
+    for i, c in enumerate(centres):
+        rad, thick = [(1, 1), (2, 1), (3, 4), (8, 8), (5, 2), (1, 6)][i]
+        mask = None if i % 2 == 0 else (rng.random((9, 7)) < 0.6).astype(np.uint8)
+        size = (float(rng.uniform(40, 160)), float(rng.uniform(40, 160)))
+        label = 3 + 11 * i
+        h, npad, amb = oracle.select_tool_2d(o, exp, M, dm, (float(c[0]), float(c[1])), size, mask, label,
+                                             flags=oracle.pad_flags(rad, thick))
+        touched += h + npad
+        padded += npad
+        amb_all |= amb.astype(bool)
+        shape = None if mask is None else torch.from_numpy(mask).to(DEV)
+        tool = lcl.make_tool((float(c[0]), float(c[1])), size, shape, lcl.pad_flags(rad, thick))
+        lcl.lcl_select_tool(a, layer, lcl.camera(M, Ws, Hs), d, tool, label, hits_out=hits)
+        assert abs(int(hits.item()) - h) <= amb.sum()
+    got = to_np(layer, dt)
+    diff = got != exp
+    assert touched > 1000 and padded > 50
+    assert not (diff & ~amb_all).any(), "padded tool labels differ outside the ambiguous texels"
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
 def test_overlay_bit_exact(dt):
     mesh = synth.vessel_cylindrical(60, 20, seed=4)
     W, H = 300, 170                      # W*H*s not a multiple of 16: exercises the tail
