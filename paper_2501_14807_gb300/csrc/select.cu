@@ -201,47 +201,54 @@ __global__ void __launch_bounds__(kThreads) k_sphere_step(AtlasDev a, L *__restr
 
 // ---- lasso ---------------------------------------------------------------------------
 
-// Any box of the 3 x 3 neighbourhood of (bx, by) that may hold a texel the lasso (tool) selects.
-__device__ bool near_box_3x3_lasso(const int32_t *boxes, int32_t nx, int32_t ny, int32_t bx, int32_t by,
-                                   const LassoArg &p, const float *__restrict__ depth) {
-    for (int32_t y = max(by - 1, 0); y <= min(by + 1, ny - 1); ++y)
-        for (int32_t x = max(bx - 1, 0); x <= min(bx + 1, nx - 1); ++x) {
-            const int4 *b = reinterpret_cast<const int4 *>(boxes + 8 * ((int64_t)y * nx + x));
-            const int4 lo = b[0], hi = b[1];
-            if (lo.w > 0 && box_may_touch(p, lo, hi, depth)) return true;
-        }
-    return false;
-}
-
-// Candidate tiles of a lasso (or tool window).  With texture padding (PAD) a texel may be written
-// because a neighbour within 8 texels was selected, so a tile (super-tile) is then a candidate if
-// any box of its 3 x 3 neighbourhood is.
-template <bool PAD>
+// Candidate tiles of a lasso (or tool window).  A CTA takes 32 tiles of one super-tile per pass
+// (blockIdx.z selects its share when a super-tile is split over several CTAs), 8 lanes per tile
+// (box_may_touch8); the super-tile's own box is tested first, uniformly over the CTA.  FLAGS:
+// write a 0/1 flag per tile instead of appending candidates (first pass of a padded edit).
+template <bool FLAGS>
 __global__ void __launch_bounds__(kThreads) k_lasso_cull(AtlasDev a, const __grid_constant__ LassoArg p,
                                                          const float *__restrict__ depth, uint32_t *counter,
                                                          uint32_t *list) {
     const int32_t sx = blockIdx.x, sy = blockIdx.y;
-    if (PAD) {
-        if (!near_box_3x3_lasso(a.super_box, a.supers_x, a.supers_y, sx, sy, p, nullptr)) return;
-    } else {
-        const int4 *sb = reinterpret_cast<const int4 *>(a.super_box + 8 * ((int64_t)sy * gridDim.x + sx));
-        int4 slo = sb[0], shi = sb[1];
-        if (slo.w == 0 || !box_may_touch(p, slo, shi)) return;
-    }
-    const int32_t tx = sx * LCL_SUPER + (threadIdx.x % LCL_SUPER);
-    const int32_t ty = sy * LCL_SUPER + (threadIdx.x / LCL_SUPER);
-    bool cand = false;
-    if (tx < a.tiles_x && ty < a.tiles_y) {
-        if (PAD) {
-            cand = near_box_3x3_lasso(a.tile_box, a.tiles_x, a.tiles_y, tx, ty, p, depth);
-        } else {
+    const int4 *sb = reinterpret_cast<const int4 *>(a.super_box + 8 * ((int64_t)sy * a.supers_x + sx));
+    const int4 slo = sb[0], shi = sb[1];
+    const bool super_in = slo.w > 0 && box_may_touch8(p, slo, shi, nullptr);  // uniform over the CTA
+    constexpr int kPerPass = kThreads / 8;
+    for (int32_t local = blockIdx.z * kPerPass + (int32_t)(threadIdx.x / 8); local < LCL_SUPER * LCL_SUPER;
+         local += gridDim.z * kPerPass) {
+        const int32_t tx = sx * LCL_SUPER + local % LCL_SUPER, ty = sy * LCL_SUPER + local / LCL_SUPER;
+        const bool in_grid = tx < a.tiles_x && ty < a.tiles_y;  // uniform over each group of 8 lanes
+        bool cand = false;
+        if (super_in && in_grid) {
             const int4 *tb = reinterpret_cast<const int4 *>(a.tile_box + 8 * ((int64_t)ty * a.tiles_x + tx));
-            int4 lo = tb[0], hi = tb[1];
-            cand = lo.w > 0 && box_may_touch(p, lo, hi, depth);
+            const int4 lo = tb[0], hi = tb[1];
+            cand = lo.w > 0 && box_may_touch8(p, lo, hi, depth);
+        }
+        const uint32_t tile = (uint32_t)(ty * a.tiles_x + tx);
+        if (FLAGS) {
+            if (in_grid && (threadIdx.x & 7u) == 0) list[tile] = cand ? 1u : 0u;
+        } else {
+            append_candidate(cand && (threadIdx.x & 7u) == 0, tile, counter, list);
         }
     }
-    append_candidate(cand, (uint32_t)(ty * a.tiles_x + tx), counter, list);
 }
+
+// Second pass of a padded edit: with texture padding a texel may be written because a neighbour
+// within 8 texels (at most one tile away) was selected, so a tile is a candidate if any tile of
+// its 3 x 3 neighbourhood is flagged.
+__global__ void __launch_bounds__(kThreads) k_dilate_candidates(AtlasDev a, const uint32_t *__restrict__ flags,
+                                                                uint32_t *counter, uint32_t *list) {
+    const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    bool cand = false;
+    if (t < (int64_t)a.tiles_x * a.tiles_y) {
+        const int32_t tx = (int32_t)(t % a.tiles_x), ty = (int32_t)(t / a.tiles_x);
+        for (int32_t y = max(ty - 1, 0); y <= min(ty + 1, a.tiles_y - 1) && !cand; ++y)
+            for (int32_t x = max(tx - 1, 0); x <= min(tx + 1, a.tiles_x - 1); ++x)
+                if (flags[(int64_t)y * a.tiles_x + x]) cand = true;
+    }
+    append_candidate(cand, (uint32_t)t, counter, list);
+}
+
 
 template <typename L>
 __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restrict__ layer,
@@ -370,6 +377,25 @@ SelWs sel_ws(const lcl_atlas *a, int32_t n, void *ws) {
     return w;
 }
 
+// Launches the cull of a lasso / tool into w.list (counter w.counters[0]); with padding, the flags
+// go to w.list2 first.  Small atlases split each super-tile over up to 8 CTAs so that the grid
+// still covers the GPU.  Returns the number of launches.
+int launch_lasso_cull(const AtlasDev &a, const lcl_atlas *atlas, const LassoArg &p, const float *depth,
+                      const SelWs &w, bool pad, cudaStream_t st) {
+    const int n_super = atlas->supers_x * atlas->supers_y;
+    const int split = std::max(1, std::min(8, (4 * sm_count() + n_super - 1) / n_super));
+    const dim3 cg(atlas->supers_x, atlas->supers_y, split);
+    if (!pad) {
+        k_lasso_cull<false><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list);
+        return 1;
+    }
+    k_lasso_cull<true><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list2);
+    const int64_t tiles = (int64_t)atlas->tiles_x * atlas->tiles_y;
+    k_dilate_candidates<<<(unsigned)((tiles + kThreads - 1) / kThreads), kThreads, 0, st>>>(a, w.list2, w.counters,
+                                                                                        w.list);
+    return 2;
+}
+
 }  // namespace
 
 size_t select_ws_bytes(const lcl_atlas *a, int32_t n) {
@@ -436,15 +462,14 @@ lcl_status select_lasso_impl(const lcl_atlas *atlas, void *layer, int dtype_byte
     static thread_local LassoArg p;  // ~2.8 KB: kept off the stack
     fill_lasso_arg(p, cam, poly, nv, label, bias);
     k_sel_init<<<1, kThreads, 0, st>>>(w.counters, 1, h);
-    const dim3 cg(atlas->supers_x, atlas->supers_y);
-    k_lasso_cull<false><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list);
+    const int n_cull = launch_lasso_cull(a, atlas, p, depth, w, false, st);
     const int ag = dtype_bytes == 1 ? resident_grid(k_lasso_apply<uint8_t>) : resident_grid(k_lasso_apply<uint16_t>);
     if (dtype_bytes == 1)
         k_lasso_apply<uint8_t><<<ag, kThreads, 0, st>>>(a, static_cast<uint8_t *>(layer), p, depth, w.counters, w.list, h);
     else
         k_lasso_apply<uint16_t><<<ag, kThreads, 0, st>>>(a, static_cast<uint16_t *>(layer), p, depth, w.counters,
                                                         w.list, h);
-    count_launches(3);
+    count_launches(2 + n_cull);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "lcl_select_lasso launch");
     return LCL_OK;
@@ -483,18 +508,14 @@ lcl_status select_tool_impl(const lcl_atlas *atlas, void *layer, int dtype_bytes
     ToolArg t;
     fill_tool_arg(t, p, cam, tool, label, bias);
     k_sel_init<<<1, kThreads, 0, st>>>(w.counters, 1, h);
-    const dim3 cg(atlas->supers_x, atlas->supers_y);
     const bool pad = t.pad_r > 0;
-    if (pad)
-        k_lasso_cull<true><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list);
-    else
-        k_lasso_cull<false><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list);
+    const int n_cull = launch_lasso_cull(a, atlas, p, depth, w, pad, st);
     const int sel = (tool->shape != nullptr ? 1 : 0) + (pad ? 2 : 0);
     if (dtype_bytes == 1)
         launch_tool<uint8_t>(sel, a, static_cast<uint8_t *>(layer), p, t, depth, w, h, st);
     else
         launch_tool<uint16_t>(sel, a, static_cast<uint16_t *>(layer), p, t, depth, w, h, st);
-    count_launches(3);
+    count_launches(2 + n_cull);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "lcl_select_tool launch");
     return LCL_OK;

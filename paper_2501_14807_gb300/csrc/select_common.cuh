@@ -206,6 +206,44 @@ __device__ inline bool box_may_touch(const LassoArg &p, int4 lo, int4 hi, const 
 }
 
 
+// box_may_touch evaluated by an aligned group of 8 lanes for one box (all 8 call it with the same
+// box): lane c projects corner c, the group reduces the screen box and the nearest depth, and the
+// depth-footprint scan is split by rows over the group.  The tests of box_may_touch, with
+// footprints of up to 2048 px scanned (1024 there) before the test gives up and keeps the box.
+__device__ __forceinline__ bool box_may_touch8(const LassoArg &p, int4 lo, int4 hi, const float *__restrict__ depth) {
+    const unsigned lane = threadIdx.x & 31u, sub = lane & 7u;
+    const unsigned gm = 0xFFu << (lane & 24u);
+    const float x = (float)((sub & 1u) ? hi.x : lo.x), y = (float)((sub & 2u) ? hi.y : lo.y);
+    const float z = (float)((sub & 4u) ? hi.z : lo.z);
+    const float cw = clip_row(p.m + 12, x, y, z);
+    if (__any_sync(gm, !(cw > 0.0f))) return true;
+    // each lane folds its corner into empty bounds exactly as the serial loop does (NaN ignored)
+    const float xs = screen_of(__fdiv_rn(clip_row(p.m, x, y, z), cw), p.ws);
+    const float ys = screen_of(__fdiv_rn(clip_row(p.m + 4, x, y, z), cw), p.hs);
+    float xmin = fminf(INFINITY, xs), xmax = fmaxf(-INFINITY, xs);
+    float ymin = fminf(INFINITY, ys), ymax = fmaxf(-INFINITY, ys);
+    float zmin = fminf(INFINITY, __fdiv_rn(clip_row(p.m + 8, x, y, z), cw));
+    for (int o = 1; o < 8; o <<= 1) {
+        xmin = fminf(xmin, __shfl_xor_sync(gm, xmin, o));
+        xmax = fmaxf(xmax, __shfl_xor_sync(gm, xmax, o));
+        ymin = fminf(ymin, __shfl_xor_sync(gm, ymin, o));
+        ymax = fmaxf(ymax, __shfl_xor_sync(gm, ymax, o));
+        zmin = fminf(zmin, __shfl_xor_sync(gm, zmin, o));
+    }
+    if (xmax < p.bx0 || xmin > p.bx1 || ymax < p.by0 || ymin > p.by1) return false;
+    if (!depth) return true;
+    const float margin = 2.0f;
+    const int ix0 = max(0, __float2int_rd(xmin - margin)), ix1 = min(p.w_s - 1, __float2int_rd(xmax + margin));
+    const int iy0 = max(0, __float2int_rd(ymin - margin)), iy1 = min(p.h_s - 1, __float2int_rd(ymax + margin));
+    if (ix0 > ix1 || iy0 > iy1) return false;  // the whole footprint is off screen
+    if ((ix1 - ix0 + 1) * (iy1 - iy0 + 1) > 2048) return true;
+    float dmax = -INFINITY;
+    for (int iy = iy0 + (int)sub; iy <= iy1; iy += 8)
+        for (int ix = ix0; ix <= ix1; ++ix) dmax = fmaxf(dmax, __ldg(depth + (int64_t)iy * p.w_s + ix));
+    for (int o = 1; o < 8; o <<= 1) dmax = fmaxf(dmax, __shfl_xor_sync(gm, dmax, o));
+    return !(zmin - 1e-4f > dmax + p.bias);
+}
+
 // The lasso test of one texel.  The conditions of the definition are all required, so they are
 // evaluated cheapest first; every value that decides the result is computed in the exact FP32
 // order of the definition.  Two shortcuts are exact as well:
