@@ -232,7 +232,7 @@ lcl_status lcl_depth_render(const lcl_mesh *mesh, const lcl_atlas *atlas, const 
  * lcl_depth_render; keep it if w > 0, NDC depth in [0, 1] and the point is on screen;
  * inside by the even-odd rule (an edge (a, b) counts when (a.y > y) != (b.y > y) and
  * x < (b.x - a.x) * (y - a.y) / (b.y - a.y) + a.x, FP32 in that order); visible iff
- * z <= depth[floor(y)][floor(x)] + bias (Fig. 3a, "a small bias").  Selected texels get
+ * z <= depth[floor(y)][floor(x)] + bias (Fig. 3a, the depth test's small bias).  Selected texels get
  * `label`.  poly_xy: host, n_vertices (3..64) x 2 float32 screen pixels.  depth: device,
  * the map of the same camera.  hits_out: device, one uint64 (nullable). */
 lcl_status lcl_select_lasso(const lcl_atlas *atlas, void *layer, lcl_dtype dtype, const lcl_camera *camera,
