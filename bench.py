@@ -245,25 +245,30 @@ def run_ours(args):
     areas = [torch.empty(w.n_labels, dtype=torch.int64, device=dev) for _ in range(w.n_layers)]
     stream = torch.cuda.current_stream(dev)
 
-    ev_sph = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in layers]
+    # one event at each boundary between the rows of a step (recorded on the launching stream)
+    ev_rows = [torch.cuda.Event(enable_timing=True) for _ in range(len(ROWS) + 1)]
 
-    def step(mesh_dev, timed_sphere=None):
+    def step(mesh_dev, timed=False):
+        mark = (lambda i: ev_rows[i].record(stream)) if timed else (lambda i: None)
+        mark(0)
         lcl.lcl_atlas_build(mesh_dev, atlas, ws_atlas, stream)
+        mark(1)
         for li, layer in enumerate(layers):
-            if timed_sphere is not None:
-                ev_sph[li][0].record(stream)
             lcl.lcl_select_sphere(atlas, layer, per_layer[li], sphere_hits[li], ws_sel, stream)
-            if timed_sphere is not None:
-                ev_sph[li][1].record(stream)
+        mark(2)
         for ci, cam in enumerate(cams):
             lcl.lcl_depth_render(mesh_dev, atlas, cam, depths[ci], ws_depth, stream)
+        mark(3)
         for k, L in enumerate(w.lassos):
             lcl.lcl_select_lasso(atlas, layers[L.layer], cams[L.cam], depths[L.cam], L.poly, L.label,
                                  lcl.DEFAULT_BIAS, lasso_hits[k:k + 1], ws_sel, stream)
+        mark(4)
         for oi, (op, ia, ib) in enumerate(w.overlays):
             lcl.lcl_overlay(atlas, layers[ia], layers[ib], outs[oi], op, 0, stream)
+        mark(5)
         for li, layer in enumerate(layers):
             lcl.lcl_label_area(atlas, layer, w.n_labels, counts[li], areas[li], stream)
+        mark(6)
 
     def barrier():
         if world > 1:
@@ -284,14 +289,16 @@ def run_ours(args):
     time.sleep(0.3)
     launches0 = lcl.lcl_kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sph_ms = 0.0
+    row_ms = [0.0] * len(ROWS)
     barrier()
     e0.record(stream)
     for _ in range(args.steps):
-        step(mesh, timed_sphere=True)
+        step(mesh, timed=True)
         e1.record(stream)
         e1.synchronize()
-        sph_ms += sum(a.elapsed_time(b) for a, b in ev_sph)
+        for i in range(len(ROWS)):
+            row_ms[i] += ev_rows[i].elapsed_time(ev_rows[i + 1])
+    sph_ms = row_ms[ROWS.index("sphere")]
     barrier()
     e1.record(stream)
     barrier()
@@ -363,11 +370,50 @@ def run_ours(args):
         "serving": serving,
         "breakdown": {"sphere_ms_per_step": sph_ms / args.steps, "sphere_hit_texels": sph_hits,
                       "lasso_hit_texels": las_hits, "texels_per_step": texels},
+        "rows": row_rooflines(w, row_ms, args.steps, sph_hits, las_hits, peak),
         "sphere_by_radius": by_radius,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+ROWS = ("atlas", "sphere", "depth", "lasso", "overlay", "area")
+
+
+def row_rooflines(w, row_ms, steps, sph_hits, las_hits, peak):
+    """Per-row CUDA-event time of one step and, for the streaming rows, algorithmic bytes over
+    that time against the HBM peak.  Bytes per unit (s = label bytes):
+      sphere / lasso   hit texels x (12 + s), plus the depth map read once per lasso
+      overlay          every texel x (3 s + 1/8)
+      area             every texel x (s + 4), plus 8 B per triangle
+      atlas            every texel x (16 + 1/8) written plus the mesh read (a rasteriser:
+                       reported, not bound by HBM)
+      depth            every screen pixel x 4 written plus the quantised vertices read"""
+    s = w.dtype_bytes
+    n = w.width * w.height
+    m = w.mesh
+    mesh_bytes = m.pos.nbytes + m.uv.nbytes + m.tri_pos.nbytes + m.tri_uv.nbytes
+    cam_px = sum(c.width * c.height for c in w.cams)
+    lasso_depth = sum(w.cams[L.cam].width * w.cams[L.cam].height * 4 for L in w.lassos)
+    spec = {
+        "atlas": (n * (16 + 1 / 8) + mesh_bytes, "raster", "atlas build (quantise, UV raster, resolve, boxes)"),
+        "sphere": (sph_hits * (12 + s), "hbm", f"{len(w.strokes.radius)} sphere strokes, {sph_hits} hit texels"),
+        "depth": (cam_px * 4 + m.pos.nbytes + m.tri_pos.nbytes, "raster", f"{len(w.cams)} depth maps"),
+        "lasso": (las_hits * (12 + s) + lasso_depth, "hbm", f"{len(w.lassos)} lassos, {las_hits} hit texels"),
+        "overlay": (len(w.overlays) * n * (3 * s + 1 / 8), "hbm", f"{len(w.overlays)} full-layer overlays"),
+        "area": (w.n_layers * (n * (s + 4) + 8 * m.n_tri), "hbm", f"{w.n_layers} per-label area queries"),
+    }
+    out = {}
+    for name, ms in zip(ROWS, row_ms):
+        b, bound, what = spec[name]
+        t = ms / steps
+        gbs = b / (t / 1e3) / 1e9 if t > 0 else 0.0
+        r = {"ms_per_step": t, "what": what, "algorithmic_bytes": int(b), "gb_s": gbs, "bound": bound}
+        if bound == "hbm":
+            r["frac"] = gbs / peak
+        out[name] = r
+    return out
 
 
 def sphere_radius_breakdown(w, atlas, layers, per_layer, ws_sel, stream, dev):

@@ -259,3 +259,122 @@ def label_area(atlas: Atlas, layer, n_labels):
                               _p(atlas.tri), _p(atlas.area_w), C.c_uint32(n_labels), _p(count), _p(area)),
          "label_area")
     return count, area
+
+
+# ---------------------------------------------------------------------------------------
+# Numeric layers (Section 4.2): data texture + mask texture.  Masks here are uint8 arrays
+# (one byte per texel, 0 or 1) of the layer's shape.
+# ---------------------------------------------------------------------------------------
+
+NUM_TYPES = {"u8": 0x11, "u16": 0x12, "u32": 0x14, "i8": 0x21, "i16": 0x22, "i32": 0x24, "f16": 0x32, "f32": 0x34}
+NUM_NP = {"u8": np.uint8, "u16": np.uint16, "u32": np.uint32, "i8": np.int8, "i16": np.int16, "i32": np.int32,
+          "f16": np.float16, "f32": np.float32}
+ARITH = {"add": 0, "sub": 1, "mul": 2, "div": 3, "min": 4, "max": 5}
+CMP = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5}
+ERASE = 0x100   # numeric stroke flag: clear the mask (and write 0) instead of storing the value
+
+
+def value_bits(value, ntype):
+    """Bits of `value` in numeric type `ntype` (numpy's own conversion: the caller-side encoding)."""
+    a = np.array([value], dtype=NUM_NP[ntype])
+    return int(a.view({1: np.uint8, 2: np.uint16, 4: np.uint32}[a.itemsize])[0])
+
+
+def half_to_float(bits):
+    """binary16 bits -> float32 values (the oracle's own decoder)."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint16)
+    out = np.empty(bits.shape, np.float32)
+    lib().orc_half_to_float_n(_p(bits), C.c_int64(bits.size), _p(out))
+    return out
+
+
+def float_to_half(x):
+    """float32 values -> binary16 bits, round to nearest even (the oracle's own encoder)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.empty(x.shape, np.uint16)
+    lib().orc_float_to_half_n(_p(x), C.c_int64(x.size), _p(out))
+    return out
+
+
+def _num_edit(data, mask, sel, value_bits_, flags):
+    """Stores one edit's selection into a numeric layer: the selected value into the data texture and
+    true into the mask texture (Section 4.3.1, last step); with ERASE, 0 and false."""
+    raw = data.view({1: np.uint8, 2: np.uint16, 4: np.uint32}[data.itemsize])
+    if flags & ERASE:
+        raw[sel] = 0
+        mask[sel] = 0
+    else:
+        raw[sel] = value_bits_
+        mask[sel] = 1
+
+
+def num_select_sphere(atlas: Atlas, data, mask, strokes):
+    """Sphere strokes on a numeric layer, in order: each stroke selects what select_sphere_2d
+    selects for it (padding included) and stores its value bits (the record's `label` field) and a
+    set mask there, or 0 and a clear mask with ERASE.  Returns (hits, padded) per stroke."""
+    strokes = np.ascontiguousarray(strokes, dtype=SPHERE_DTYPE)
+    hits = np.zeros(len(strokes), np.uint64)
+    padded = np.zeros(len(strokes), np.uint64)
+    for k, s in enumerate(strokes):
+        one = s.copy()
+        one["label"] = 1
+        one["flags"] = int(s["flags"]) & 0xFF
+        sel = np.zeros(atlas.tri.shape, np.uint8)
+        h, p = select_sphere_2d(atlas, sel, np.array([one], SPHERE_DTYPE))
+        hits[k], padded[k] = h[0], p[0]
+        _num_edit(data, mask, sel == 1, int(s["label"]), int(s["flags"]))
+    return hits, padded
+
+
+def num_select_lasso(atlas: Atlas, data, mask, m, dmap, poly, value_bits_, flags=0, bias=2.0 ** -10):
+    """A lasso on a numeric layer: the texels select_lasso selects get the value (or are erased).
+    Returns (hits, ambiguous mask)."""
+    sel = np.zeros(atlas.tri.shape, np.uint8)
+    h, amb = select_lasso(atlas, sel, m, dmap, poly, 1, bias)
+    _num_edit(data, mask, sel == 1, value_bits_, flags)
+    return h, amb
+
+
+def num_select_tool(atlas: Atlas, data, mask, m, dmap, centre, size, shape=None, value_bits_=0, flags=0,
+                    bias=2.0 ** -10):
+    """The paper's tool on a numeric layer (padding as in select_tool_2d from flags & 0xFF).
+    Returns (hits, padded, ambiguous mask)."""
+    sel = np.zeros(atlas.tri.shape, np.uint8)
+    h, p, amb = select_tool_2d(atlas, sel, m, dmap, centre, size, shape, 1, bias, flags & 0xFF)
+    _num_edit(data, mask, sel == 1, value_bits_, flags)
+    return h, p, amb
+
+
+def num_arith(atlas: Atlas, ntype, a, ma, b, mb, op, scalar_bits=0):
+    """Arithmetic overlay (b None: the scalar); returns (out data, out mask)."""
+    out = np.empty_like(a)
+    mout = np.empty(a.shape, np.uint8)
+    _chk(lib().orc_num_arith(C.c_int64(atlas.n_texels), _p(atlas.tri), C.c_int(NUM_TYPES[ntype]),
+                             _p(np.ascontiguousarray(a)), _p(np.ascontiguousarray(ma, np.uint8)),
+                             _p(None if b is None else np.ascontiguousarray(b)),
+                             _p(None if mb is None else np.ascontiguousarray(mb, np.uint8)),
+                             C.c_uint32(int(scalar_bits)), _p(out), _p(mout), C.c_int(ARITH[op])), "num_arith")
+    return out, mout
+
+
+def num_select(atlas: Atlas, ntype, data, mask, cmp, threshold_bits, layer, label):
+    """Selection by value into a label layer (in place); returns hits."""
+    hits = np.zeros(1, np.uint64)
+    _chk(lib().orc_num_select(C.c_int64(atlas.n_texels), _p(atlas.tri), C.c_int(NUM_TYPES[ntype]),
+                              _p(np.ascontiguousarray(data)), _p(np.ascontiguousarray(mask, np.uint8)),
+                              C.c_int(CMP[cmp]), C.c_uint32(int(threshold_bits)), _p(layer), C.c_int(layer.itemsize),
+                              C.c_uint32(int(label)), _p(hits)), "num_select")
+    return int(hits[0])
+
+
+def num_stats(atlas: Atlas, ntype, data, mask, zones, n_labels):
+    """Zonal statistics; returns a dict of arrays count, area (uint64), vmin, vmax, sum, wsum (float64)."""
+    r = {k: np.empty(n_labels, np.uint64) for k in ("count", "area")}
+    r.update({k: np.empty(n_labels, np.float64) for k in ("vmin", "vmax", "sum", "wsum")})
+    zb = 0 if zones is None else zones.itemsize
+    _chk(lib().orc_num_stats(C.c_int64(atlas.n_texels), _p(atlas.tri), _p(atlas.area_w), C.c_int(NUM_TYPES[ntype]),
+                             _p(np.ascontiguousarray(data)), _p(np.ascontiguousarray(mask, np.uint8)),
+                             _p(None if zones is None else np.ascontiguousarray(zones)), C.c_int(zb),
+                             C.c_uint32(n_labels), _p(r["count"]), _p(r["area"]), _p(r["vmin"]), _p(r["vmax"]),
+                             _p(r["sum"]), _p(r["wsum"])), "num_stats")
+    return r

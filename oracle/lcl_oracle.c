@@ -859,3 +859,265 @@ int orc_label_area(int64_t n_texels, const void *layer, int dtype_bytes, const u
     }
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Numeric layers (Section 4.2): a data texture holding one number per texel  */
+/* -- an integer of 8, 16 or 32 bits or a float of 16 or 32 bits -- and a     */
+/* mask texture holding one boolean per texel (the texel holds valid data).   */
+/* Here the mask is one byte per texel (0 or 1).  Type codes: low nibble =    */
+/* bytes, high nibble = kind (1 unsigned, 2 signed, 3 IEEE float).            */
+/* READING (the paper names the types, not their arithmetic):                 */
+/*  - integers add, subtract and multiply modulo 2^bits (two's complement),   */
+/*    compare by their signed or unsigned value; division is floats only;     */
+/*  - float32 operations are IEEE single, round to nearest even;              */
+/*  - float16 operands are widened to float32 (exact), the operation is done  */
+/*    once in float32 and the result rounded to float16 (nearest even); with  */
+/*    24 >= 2*11 + 2 significand bits this equals the correctly rounded        */
+/*    float16 operation for + - * /;                                          */
+/*  - a result is valid where both operands are valid and the texel is        */
+/*    covered; elsewhere data = 0 and mask = 0;                                 */
+/*  - MIN / MAX of floats: a < b ? a : b and a > b ? a : b.                    */
+/* ------------------------------------------------------------------------- */
+enum { ORC_NUM_U8 = 0x11, ORC_NUM_U16 = 0x12, ORC_NUM_U32 = 0x14, ORC_NUM_I8 = 0x21, ORC_NUM_I16 = 0x22,
+       ORC_NUM_I32 = 0x24, ORC_NUM_F16 = 0x32, ORC_NUM_F32 = 0x34 };
+enum { ORC_AR_ADD = 0, ORC_AR_SUB = 1, ORC_AR_MUL = 2, ORC_AR_DIV = 3, ORC_AR_MIN = 4, ORC_AR_MAX = 5 };
+enum { ORC_CMP_LT = 0, ORC_CMP_LE = 1, ORC_CMP_GT = 2, ORC_CMP_GE = 3, ORC_CMP_EQ = 4, ORC_CMP_NE = 5 };
+
+static int num_type_ok(int type)
+{
+    switch (type) {
+    case ORC_NUM_U8: case ORC_NUM_U16: case ORC_NUM_U32: case ORC_NUM_I8: case ORC_NUM_I16: case ORC_NUM_I32:
+    case ORC_NUM_F16: case ORC_NUM_F32: return 1;
+    default: return 0;
+    }
+}
+
+static int num_bytes(int type) { return type & 15; }
+static int num_kind(int type) { return type >> 4; }
+
+/* IEEE 754 binary16 -> binary32, exact: sign, 5 exponent bits (bias 15), 10 fraction bits. */
+float orc_half_to_float(uint16_t h)
+{
+    uint32_t sign = (uint32_t)(h >> 15) & 1u, e = (uint32_t)(h >> 10) & 31u, f = (uint32_t)h & 1023u;
+    float mag;
+    if (e == 0) mag = ldexpf((float)f, -24);                    /* zero or subnormal: f * 2^-24 */
+    else if (e == 31) mag = f ? NAN : INFINITY;
+    else mag = ldexpf((float)(1024u + f), (int)e - 25);         /* (1 + f/1024) * 2^(e-15) */
+    return sign ? -mag : mag;
+}
+
+/* binary32 -> binary16, round to nearest, ties to even, overflow to infinity, NaN kept quiet.
+ * Works on the exact value: |x| = M * 2^E with integer M; the half result is a multiple of
+ * 2^-24 (subnormal spacing) or of 2^(e-10) for a normal exponent e. */
+uint16_t orc_float_to_half(float x)
+{
+    uint32_t b;
+    memcpy(&b, &x, 4);
+    uint16_t sign = (uint16_t)((b >> 16) & 0x8000u);
+    if (isnan(x)) return (uint16_t)(sign | 0x7E00u);
+    double a = fabs((double)x);
+    if (isinf(x) || a >= 65520.0) return (uint16_t)(sign | 0x7C00u); /* 65520 = halfway above 65504 */
+    if (a == 0.0) return sign;
+    /* spacing of half values around a: 2^-24 below 2^-14, else 2^(floor(log2 a) - 10) */
+    int e2;
+    frexp(a, &e2); /* a = m * 2^e2, m in [0.5, 1): floor(log2 a) = e2 - 1 */
+    int ulp_exp = (e2 - 1) - 10;
+    if (ulp_exp < -24) ulp_exp = -24;
+    double q = ldexp(a, -ulp_exp); /* exact: a has 24 significant bits and q < 2^12 */
+    double r = floor(q), frac = q - r;
+    if (frac > 0.5 || (frac == 0.5 && fmod(r, 2.0) != 0.0)) r += 1.0;
+    double v = ldexp(r, ulp_exp); /* the rounded magnitude, exact in double */
+    if (v >= 65520.0) return (uint16_t)(sign | 0x7C00u);
+    /* encode v */
+    if (v < ldexp(1.0, -14)) return (uint16_t)(sign | (uint16_t)ldexp(v, 24));
+    int ev;
+    double mv = frexp(v, &ev); /* v = mv * 2^ev, mv in [0.5, 1) */
+    uint32_t frac10 = (uint32_t)(ldexp(mv, 11) - 1024.0);
+    uint32_t ebits = (uint32_t)(ev - 1 + 15);
+    return (uint16_t)(sign | (uint16_t)(ebits << 10) | (uint16_t)frac10);
+}
+
+void orc_half_to_float_n(const uint16_t *h, int64_t n, float *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_half_to_float(h[i]);
+}
+
+void orc_float_to_half_n(const float *x, int64_t n, uint16_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_float_to_half(x[i]);
+}
+
+static uint32_t num_load_bits(const void *data, int type, int64_t l)
+{
+    switch (num_bytes(type)) {
+    case 1: return ((const uint8_t *)data)[l];
+    case 2: return ((const uint16_t *)data)[l];
+    default: return ((const uint32_t *)data)[l];
+    }
+}
+
+static void num_store_bits(void *data, int type, int64_t l, uint32_t v)
+{
+    switch (num_bytes(type)) {
+    case 1: ((uint8_t *)data)[l] = (uint8_t)v; break;
+    case 2: ((uint16_t *)data)[l] = (uint16_t)v; break;
+    default: ((uint32_t *)data)[l] = v; break;
+    }
+}
+
+/* Integer value of the bits of an integer type (sign-extended for signed types). */
+static int64_t num_int(int type, uint32_t bits)
+{
+    switch (type) {
+    case ORC_NUM_I8: return (int8_t)(uint8_t)bits;
+    case ORC_NUM_I16: return (int16_t)(uint16_t)bits;
+    case ORC_NUM_I32: return (int32_t)bits;
+    default: return (int64_t)bits;
+    }
+}
+
+/* Float value of the bits of a float type. */
+static float num_float(int type, uint32_t bits)
+{
+    if (type == ORC_NUM_F16) return orc_half_to_float((uint16_t)bits);
+    float f;
+    memcpy(&f, &bits, 4);
+    return f;
+}
+
+static uint32_t num_from_float(int type, float f)
+{
+    if (type == ORC_NUM_F16) return orc_float_to_half(f);
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    return b;
+}
+
+static uint32_t width_mask(int type) { return num_bytes(type) == 4 ? 0xFFFFFFFFu : (1u << (8 * num_bytes(type))) - 1u; }
+
+/* One arithmetic operation on two values of `type` (bits in, bits out). */
+static uint32_t num_apply(int type, int op, uint32_t xa, uint32_t xb)
+{
+    if (num_kind(type) == 3) {
+        float a = num_float(type, xa), b = num_float(type, xb), r;
+        switch (op) {
+        case ORC_AR_ADD: r = a + b; break;
+        case ORC_AR_SUB: r = a - b; break;
+        case ORC_AR_MUL: r = a * b; break;
+        case ORC_AR_DIV: r = a / b; break;
+        case ORC_AR_MIN: r = a < b ? a : b; break;
+        default: r = a > b ? a : b; break;
+        }
+        return num_from_float(type, r);
+    }
+    int64_t a = num_int(type, xa), b = num_int(type, xb);
+    uint64_t r;
+    switch (op) {
+    case ORC_AR_ADD: r = (uint64_t)a + (uint64_t)b; break;
+    case ORC_AR_SUB: r = (uint64_t)a - (uint64_t)b; break;
+    case ORC_AR_MUL: r = (uint64_t)a * (uint64_t)b; break;
+    case ORC_AR_MIN: r = (uint64_t)(a < b ? a : b); break;
+    default: r = (uint64_t)(a > b ? a : b); break;
+    }
+    return (uint32_t)r & width_mask(type);
+}
+
+/* Arithmetic overlay of two numeric layers, or of a layer and a scalar (b == NULL: every texel
+ * of b holds b_scalar and is valid).  out / out_mask may alias a or b. */
+int orc_num_arith(int64_t n_texels, const uint32_t *tri, int type, const void *a, const uint8_t *ma, const void *b,
+                  const uint8_t *mb, uint32_t b_scalar, void *out, uint8_t *mout, int op)
+{
+    if (!num_type_ok(type) || op < ORC_AR_ADD || op > ORC_AR_MAX) return ORC_EINVAL;
+    if (op == ORC_AR_DIV && num_kind(type) != 3) return ORC_EUNSUP;
+    if (!b && (b_scalar & ~width_mask(type))) return ORC_EINVAL;
+    for (int64_t l = 0; l < n_texels; ++l) {
+        int valid = tri[l] != ORC_NONE && ma[l] && (b ? mb[l] != 0 : 1);
+        uint32_t r = 0;
+        if (valid) r = num_apply(type, op, num_load_bits(a, type, l), b ? num_load_bits(b, type, l) : b_scalar);
+        num_store_bits(out, type, l, r);
+        mout[l] = (uint8_t)valid;
+    }
+    return ORC_OK;
+}
+
+/* Selection by value: covered texels whose mask is set and whose value v satisfies
+ * v <cmp> threshold get `label` in a label layer; no other texel changes.  Integers compare
+ * by value, floats as IEEE floats (a NaN satisfies only NE). */
+int orc_num_select(int64_t n_texels, const uint32_t *tri, int type, const void *data, const uint8_t *mask, int cmp,
+                   uint32_t threshold, void *layer, int dtype_bytes, uint32_t label, uint64_t *hits)
+{
+    if (!num_type_ok(type) || cmp < ORC_CMP_LT || cmp > ORC_CMP_NE) return ORC_EINVAL;
+    if (dtype_bytes != 1 && dtype_bytes != 2) return ORC_EINVAL;
+    if (label >= (1u << (8 * dtype_bytes)) || (threshold & ~width_mask(type))) return ORC_EINVAL;
+    uint64_t h = 0;
+    for (int64_t l = 0; l < n_texels; ++l) {
+        if (tri[l] == ORC_NONE || !mask[l]) continue;
+        uint32_t bits = num_load_bits(data, type, l);
+        int sel;
+        if (num_kind(type) == 3) {
+            float v = num_float(type, bits), t = num_float(type, threshold);
+            switch (cmp) {
+            case ORC_CMP_LT: sel = v < t; break;
+            case ORC_CMP_LE: sel = v <= t; break;
+            case ORC_CMP_GT: sel = v > t; break;
+            case ORC_CMP_GE: sel = v >= t; break;
+            case ORC_CMP_EQ: sel = v == t; break;
+            default: sel = v != t; break;
+            }
+        } else {
+            int64_t v = num_int(type, bits), t = num_int(type, threshold);
+            switch (cmp) {
+            case ORC_CMP_LT: sel = v < t; break;
+            case ORC_CMP_LE: sel = v <= t; break;
+            case ORC_CMP_GT: sel = v > t; break;
+            case ORC_CMP_GE: sel = v >= t; break;
+            case ORC_CMP_EQ: sel = v == t; break;
+            default: sel = v != t; break;
+            }
+        }
+        if (sel) {
+            store_label(layer, dtype_bytes, l, label);
+            ++h;
+        }
+    }
+    if (hits) *hits = h;
+    return ORC_OK;
+}
+
+/* Zonal statistics of a numeric layer over the zones of a label layer (the quantitative side of
+ * Section 4.2 measured with the area weights of Table 1).  For every covered texel whose mask is
+ * set, whose value v is not NaN, and whose zone label z < n_labels (zones == NULL: z = 0):
+ *   count[z] += 1, area[z] += w (its triangle's area weight),
+ *   vmin[z] = min, vmax[z] = max of v (as double; -0 counts as +0),
+ *   sum[z] += v, wsum[z] += (double)w * v   (double, in texel order).
+ * Empty zones: count = area = 0, vmin = +inf, vmax = -inf, sums 0. */
+int orc_num_stats(int64_t n_texels, const uint32_t *tri, const uint64_t *w_tri, int type, const void *data,
+                  const uint8_t *mask, const void *zones, int zone_bytes, uint32_t n_labels, uint64_t *count,
+                  uint64_t *area, double *vmin, double *vmax, double *sum, double *wsum)
+{
+    if (!num_type_ok(type) || n_labels < 1) return ORC_EINVAL;
+    if (zones && zone_bytes != 1 && zone_bytes != 2) return ORC_EINVAL;
+    if (!zones && n_labels != 1) return ORC_EINVAL;
+    for (uint32_t i = 0; i < n_labels; ++i) {
+        count[i] = 0; area[i] = 0;
+        vmin[i] = INFINITY; vmax[i] = -INFINITY;
+        sum[i] = 0.0; wsum[i] = 0.0;
+    }
+    for (int64_t l = 0; l < n_texels; ++l) {
+        if (tri[l] == ORC_NONE || !mask[l]) continue;
+        uint32_t z = zones ? load_label(zones, zone_bytes, l) : 0u;
+        if (z >= n_labels) continue;
+        uint32_t bits = num_load_bits(data, type, l);
+        double v = num_kind(type) == 3 ? (double)num_float(type, bits) : (double)num_int(type, bits);
+        if (isnan(v)) continue;
+        if (v == 0.0) v = 0.0;
+        uint64_t w = w_tri[tri[l]];
+        count[z] += 1;
+        area[z] += w;
+        if (v < vmin[z]) vmin[z] = v;
+        if (v > vmax[z]) vmax[z] = v;
+        sum[z] += v;
+        wsum[z] += (double)w * v;
+    }
+    return ORC_OK;
+}
