@@ -721,6 +721,112 @@ def run_tool(args):
     print(json.dumps(line), flush=True)
 
 
+def run_numeric(args):
+    """Numeric layers (Section 4.2) on the roofline-size model: 16384^2 atlas of the ~8M-triangle
+    vessel, float32 data textures with their mask bits.  One step: the 1000 sphere strokes of the
+    roofline workload written as values (a seeded "age" in [0, 2000)) into two numeric layers
+    (500 each), their sum (arithmetic overlay), a selection by value (sum > 1000) into a u8 label
+    layer, and the zonal statistics of the sum over the selection's labels.  Reports every row's
+    CUDA-event time and algorithmic bytes against the HBM peak."""
+    import torch
+
+    from paper_2501_14807_gb300 import lcl
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = synth_roofline(args)
+    W, H = w.width, w.height
+    mesh = lcl.Mesh.from_host(w.mesh, dev)
+    atlas = lcl.Atlas(W, H, w.tile, w.mesh.n_tri, dev)
+    lcl.lcl_atlas_build(mesh, atlas)
+    A, B, S = (lcl.NumericLayer(W, H, "f32", dev) for _ in range(3))
+    zones = torch.zeros((H, W), dtype=torch.uint8, device=dev)
+    rng = np.random.default_rng(91)
+    ages = rng.uniform(0, 2000, size=len(w.strokes.radius)).astype(np.float32)
+    recs = np.stack([lcl.lcl_quantize_sphere(atlas, w.strokes.centre[k], w.strokes.radius[k], 0)
+                     for k in range(len(ages))])
+    recs["label"] = ages.view(np.uint32)
+    half = len(recs) // 2
+    per = [np.ascontiguousarray(recs[:half]), np.ascontiguousarray(recs[half:])]
+    ws = torch.empty(lcl.lcl_select_workspace_bytes(atlas, max(len(r) for r in per)), dtype=torch.uint8, device=dev)
+    hits = [torch.zeros(max(len(r), 1), dtype=torch.int64, device=dev) for r in per]
+    sel_hits = torch.zeros(1, dtype=torch.int64, device=dev)
+    stats = torch.empty(256 * 48, dtype=torch.uint8, device=dev)
+    thr = int(np.float32(1000.0).view(np.uint32))
+    stream = torch.cuda.current_stream(dev)
+    names = ("edit", "arith", "select", "stats")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+
+    def step(timed):
+        mark = (lambda i: ev[i].record(stream)) if timed else (lambda i: None)
+        mark(0)
+        lcl.lcl_numeric_sphere(atlas, A, per[0], hits[0], ws, stream)
+        lcl.lcl_numeric_sphere(atlas, B, per[1], hits[1], ws, stream)
+        mark(1)
+        lcl.lcl_numeric_arith(atlas, A, B, S, "add", stream=stream)
+        mark(2)
+        lcl.lcl_numeric_select(atlas, S, "gt", thr, zones, 1, sel_hits, stream)
+        mark(3)
+        lcl.lcl_numeric_stats(atlas, S, zones, 256, stats, stream)
+        mark(4)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize(dev)
+    n_hit = int(hits[0].sum().item() + hits[1].sum().item())
+    n_sel = int(sel_hits.item())
+    row_ms = [0.0] * len(names)
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+        ev[-1].synchronize()
+        for i in range(len(names)):
+            row_ms[i] += ev[i].elapsed_time(ev[i + 1])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    total_ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    peak, peak_kind = peaks()
+    n = W * H
+    spec = {  # algorithmic bytes per step (f32 values, 1 mask bit per texel, coverage bits)
+        "edit": (n_hit * (12 + 4 + 1 / 8), f"{len(recs)} value strokes, {n_hit} hit texels (12 B position + 4 B "
+                                            f"value + 1 mask bit each)"),
+        "arith": (n * (3 * 4 + 4 / 8), "float32 a + b over every texel (3 x 4 B + 3 mask bits + 1 cover bit)"),
+        "select": (n * (4 + 2 / 8) + n_sel, f"sum > 1000 into u8 labels, {n_sel} selected (4 B + 2 bits per texel, "
+                                             "1 B per label written)"),
+        "stats": (n * (4 + 1 + 4 + 2 / 8) + 8 * w.mesh.n_tri, "zonal statistics, 256 zones (4 B value + 1 B zone + "
+                                                              "4 B triangle + 2 bits per texel, 8 B per triangle)"),
+    }
+    rows = {}
+    for name, ms in zip(names, row_ms):
+        b, what = spec[name]
+        t = ms / args.steps
+        gbs = b / (t / 1e3) / 1e9
+        rows[name] = {"ms_per_step": t, "what": what, "algorithmic_bytes": int(b), "gb_s": gbs, "frac": gbs / peak}
+    texels = n_hit + 3 * n
+    line = {"metric": METRIC, "value": texels * args.steps / (total_ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded vessel)",
+            "config": {"workload": f"numeric layers: {w.name}, {w.mesh.n_tri} triangles, {W}x{H} atlas, float32 "
+                                   f"layers with mask bits: {len(recs)} value strokes into two layers, their sum, "
+                                   f"a selection by value, zonal statistics over 256 zones",
+                       "l2": "inputs larger than L2"},
+            "roofline": {"bound": "hbm", "peak": peak, "peak_kind": peak_kind, "unit": "GB/s"},
+            "rows": rows, "clocks": clk,
+            "note": "texels per step: every hit texel of the value strokes plus every texel of the sum, the "
+                    "selection and the statistics"}
+    print(json.dumps(line), flush=True)
+
+
+def synth_roofline(args):
+    import synth
+    return synth.config_roofline(n_strokes=args.strokes, n_lassos=0)
+
+
 def run_serve(args):
     """Serving workload: resident + spillover models (as in the batching workload), 2 layers each,
     an HBM budget that holds about half of them, open-loop Poisson arrivals (70% sphere strokes, 20%
@@ -783,7 +889,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="roofline",
-                    choices=["roofline", "large", "mid", "small", "batch", "serve", "tool"])
+                    choices=["roofline", "large", "mid", "small", "batch", "serve", "tool", "numeric"])
     ap.add_argument("--rate", type=float, default=20000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=5.0, help="serving: trace length (s)")
     ap.add_argument("--models", type=int, default=None,
@@ -797,7 +903,7 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=64, help="rows of the texture the CPU oracle baseline covers")
     args = ap.parse_args()
     defaults = {"roofline": (1000, 20), "mid": (1000, 20), "large": (10000, 200), "small": (200, 0), "batch": (0, 0),
-                "serve": (0, 0), "tool": (0, 0)}
+                "serve": (0, 0), "tool": (0, 0), "numeric": (1000, 0)}
     if args.strokes is None:
         args.strokes = defaults[args.config][0]
     if args.lassos is None:
@@ -810,6 +916,8 @@ def main():
         run_serve(args)
     elif args.config == "tool":
         run_tool(args)
+    elif args.config == "numeric":
+        run_numeric(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

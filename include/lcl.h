@@ -102,7 +102,8 @@ typedef struct {
 } lcl_atlas;
 
 /* Sphere stroke in grid units (32 bytes): texels with (q - c)^2 <= r2 get `label`.
- * flags is reserved and must be 0. */
+ * flags: texture padding (Section 4.3.2), radius = bits 0-3, outline thickness = bits 4-7, both
+ * <= 8 (0 = none); LCL_ERASE (bit 8) only in lcl_numeric_sphere; other bits 0. */
 typedef struct {
     int32_t cx, cy, cz, _pad;
     int64_t r2;
@@ -391,6 +392,99 @@ lcl_status lcl_overlay(const lcl_atlas *atlas, const void *a, const void *b, voi
  * n_labels uint64 each (overwritten).  n_labels in [1, 65536]. */
 lcl_status lcl_label_area(const lcl_atlas *atlas, const void *layer, lcl_dtype dtype, uint32_t n_labels,
                           uint64_t *count_out, uint64_t *area_out, lcl_stream stream);
+
+/* ---- numeric layers ------------------------------------------------------- */
+
+/* Numeric layers (Section 4.2): besides label layers, a layer can hold numeric properties
+ * (curvature, rugosity, age ...) as a data texture of integers (8, 16 or 32 bits) or floats
+ * (16 or 32 bits) with a mask texture that tells which texels hold valid data.  Type codes:
+ * low nibble = bytes per texel, high nibble = 1 unsigned, 2 signed, 3 IEEE float. */
+typedef enum {
+    LCL_NUM_U8 = 0x11, LCL_NUM_U16 = 0x12, LCL_NUM_U32 = 0x14,
+    LCL_NUM_I8 = 0x21, LCL_NUM_I16 = 0x22, LCL_NUM_I32 = 0x24,
+    LCL_NUM_F16 = 0x32, LCL_NUM_F32 = 0x34
+} lcl_num_type;
+
+/* A numeric layer: data, device, width x height values of `type`, row-major, 16-byte aligned;
+ * mask, device, one bit per texel, bit (y * width + x) of a linear uint32 array
+ * ((width * height + 31) / 32 words, 16-byte aligned), set = the texel holds data.  Values are
+ * passed to and from the library as their bit patterns in a uint32 (float16: the 16 bits of the
+ * binary16 value; narrower integers: the value's bits in the low bits, higher bits 0). */
+typedef struct {
+    void *data;
+    uint32_t *mask;
+    lcl_num_type type;
+    int32_t _pad;
+} lcl_numeric_layer;
+
+#define LCL_ERASE 0x100u  /* numeric edit flag: store 0 and clear the mask instead of the value */
+
+/* Sphere strokes on a numeric layer: the texels lcl_select_sphere would select (texture padding
+ * included, flags bits 0-7) get the stroke's value -- the bits in strokes[k].label -- in the data
+ * texture and a set mask bit, the last step of Section 4.3.1 (the selected value is stored in the
+ * data texture and true in the mask texture); with LCL_ERASE in flags they get 0 and a clear mask
+ * bit.  hits_out, workspace: as lcl_select_sphere.  Errors: as lcl_select_sphere;
+ * LCL_ERR_INVALID_ARG for a value wider than the type or flags outside bits 0-8. */
+lcl_status lcl_numeric_sphere(const lcl_atlas *atlas, const lcl_numeric_layer *layer, const lcl_sphere *strokes,
+                              int32_t n, uint64_t *hits_out, void *workspace, size_t ws_bytes, lcl_stream stream);
+
+/* A lasso on a numeric layer: the texels lcl_select_lasso would select get `value` and a set mask
+ * bit (flags = LCL_ERASE: 0 and a clear bit; otherwise flags = 0). */
+lcl_status lcl_numeric_lasso(const lcl_atlas *atlas, const lcl_numeric_layer *layer, const lcl_camera *camera,
+                             const float *depth, const float *poly_xy, int32_t n_vertices, uint32_t value,
+                             uint32_t flags, float bias, uint64_t *hits_out, void *workspace, size_t ws_bytes,
+                             lcl_stream stream);
+
+/* The paper's tool on a numeric layer (tool->flags: padding as for lcl_select_tool; flags:
+ * LCL_ERASE or 0). */
+lcl_status lcl_numeric_tool(const lcl_atlas *atlas, const lcl_numeric_layer *layer, const lcl_camera *camera,
+                            const float *depth, const lcl_tool *tool, uint32_t value, uint32_t flags, float bias,
+                            uint64_t *hits_out, void *workspace, size_t ws_bytes, lcl_stream stream);
+
+typedef enum { LCL_ADD = 0, LCL_SUB = 1, LCL_MUL = 2, LCL_DIV = 3, LCL_MIN = 4, LCL_MAX = 5 } lcl_arith;
+
+/* Arithmetic overlay of numeric layers (layer systems compute arithmetic operations between layers,
+ * Section 3.4.2): out = a <op> b per texel, all three of one type; b == NULL uses the scalar `b_value`
+ * (bits, always valid) for every texel.  Integers: add, subtract and multiply modulo 2^bits
+ * (two's complement), min / max by signed or unsigned value, no division.  float32: IEEE single,
+ * round to nearest even.  float16: both operands widened to float32 (exact), one float32 operation,
+ * the result rounded to float16 (nearest even) -- the correctly rounded float16 operation.  MIN /
+ * MAX: a < b ? a : b and a > b ? a : b.  A result is valid where a, b (if given) are valid and the
+ * texel is covered; other texels get data 0 and a clear mask bit.  out may alias a or b (data and
+ * mask).  NaN results are NaN, their bit pattern is not specified.
+ * Errors: LCL_ERR_INVALID_ARG (types differ, bad pointers, scalar wider than the type);
+ * LCL_ERR_UNSUPPORTED (LCL_DIV on integers). */
+lcl_status lcl_numeric_arith(const lcl_atlas *atlas, const lcl_numeric_layer *a, const lcl_numeric_layer *b,
+                             uint32_t b_value, const lcl_numeric_layer *out, lcl_arith op, lcl_stream stream);
+
+typedef enum { LCL_LT = 0, LCL_LE = 1, LCL_GT = 2, LCL_GE = 3, LCL_EQ = 4, LCL_NE = 5 } lcl_cmp;
+
+/* Selection by value, from a numeric layer into a label layer: covered texels whose mask bit is set
+ * and whose value v satisfies v <cmp> threshold (bits of the layer's type; integers compare by
+ * value, floats as IEEE floats, a NaN satisfies only LCL_NE) get `label`; no other texel changes.
+ * hits_out: device, one uint64 (nullable), the number of texels selected. */
+lcl_status lcl_numeric_select(const lcl_atlas *atlas, const lcl_numeric_layer *values, lcl_cmp cmp,
+                              uint32_t threshold, void *layer, lcl_dtype dtype, uint32_t label, uint64_t *hits_out,
+                              lcl_stream stream);
+
+/* Zonal statistics of one zone (48 bytes). */
+typedef struct {
+    uint64_t count;  /* texels */
+    uint64_t area;   /* sum of their area weights (as lcl_label_area) */
+    double vmin, vmax;  /* smallest and largest value (+inf / -inf for an empty zone) */
+    double sum;      /* sum of the values */
+    double wsum;     /* sum of area weight x value: the integral over the zone's surface */
+} lcl_zone_stats;
+
+/* Zonal statistics of a numeric layer over the zones of a label layer (quantitative layers measured
+ * with the area one texel stands for, Section 5, Table 1): over covered texels whose mask bit is
+ * set, whose value is not NaN and whose zone label z < n_labels (zones == NULL: every such texel is
+ * in zone 0 and n_labels must be 1), per zone: count, area, min, max (values as double; -0 counts
+ * as +0), sum of values and sum of weight x value in double.  count, area, vmin and vmax are
+ * exact; the sums are accumulated in an unspecified order (error at most (count - 1) * 2^-53 *
+ * sum of |terms|).  out: device, n_labels records (overwritten).  n_labels in [1, 65536]. */
+lcl_status lcl_numeric_stats(const lcl_atlas *atlas, const lcl_numeric_layer *values, const void *zones,
+                             lcl_dtype zone_dtype, uint32_t n_labels, lcl_zone_stats *out, lcl_stream stream);
 
 /* ---- diagnostics -------------------------------------------------------- */
 

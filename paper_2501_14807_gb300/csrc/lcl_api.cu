@@ -101,6 +101,37 @@ lcl_status check_mesh(const lcl_mesh *m) {
 
 int dtype_bytes(lcl_dtype d) { return d == LCL_U8 ? 1 : d == LCL_U16 ? 2 : 0; }
 
+bool num_type_ok(int t) {
+    switch (t) {
+    case LCL_NUM_U8: case LCL_NUM_U16: case LCL_NUM_U32: case LCL_NUM_I8: case LCL_NUM_I16: case LCL_NUM_I32:
+    case LCL_NUM_F16: case LCL_NUM_F32: return true;
+    default: return false;
+    }
+}
+
+uint32_t value_mask(int t) { return (t & 15) == 4 ? 0xFFFFFFFFu : ((1u << (8 * (t & 15))) - 1u); }
+
+lcl_status check_numeric(const lcl_numeric_layer *l, const char *what) {
+    if (!l) return fail(LCL_ERR_INVALID_ARG, std::string(what) + " is NULL");
+    if (!num_type_ok((int)l->type)) return fail(LCL_ERR_INVALID_ARG, std::string(what) + ": unknown numeric type");
+    if (!l->data || !aligned(l->data, 16) || !l->mask || !aligned(l->mask, 16))
+        return fail(LCL_ERR_INVALID_ARG, std::string(what) + ": data and mask must be 16-byte aligned device pointers");
+    return LCL_OK;
+}
+
+lcl_status check_tool(const lcl_tool *tool) {
+    if (!tool) return fail(LCL_ERR_INVALID_ARG, "tool is NULL");
+    if (!std::isfinite(tool->px) || !std::isfinite(tool->py) || !std::isfinite(tool->tw) || !std::isfinite(tool->th) ||
+        !(tool->tw > 0.0f) || !(tool->th > 0.0f) || std::fabs(tool->px) > 1e7f || std::fabs(tool->py) > 1e7f ||
+        tool->tw > 1e7f || tool->th > 1e7f)
+        return fail(LCL_ERR_INVALID_ARG, "tool window must be finite, positive and below 1e7 px");
+    if (tool->shape && (tool->shape_w < 1 || tool->shape_w > 4096 || tool->shape_h < 1 || tool->shape_h > 4096))
+        return fail(LCL_ERR_INVALID_ARG, "tool shape sizes must be 1..4096");
+    if ((tool->flags & ~0xFFu) || (tool->flags & 15u) > 8 || ((tool->flags >> 4) & 15u) > 8)
+        return fail(LCL_ERR_INVALID_ARG, "tool padding radius and thickness must be <= 8, other flag bits 0");
+    return LCL_OK;
+}
+
 lcl_status check_camera(const lcl_camera *c) {
     if (!c) return fail(LCL_ERR_INVALID_ARG, "camera is NULL");
     if (c->width < 1 || c->width > 16384 || c->height < 1 || c->height > 16384)
@@ -343,15 +374,8 @@ lcl_status lcl_select_tool(const lcl_atlas *atlas, void *layer, lcl_dtype dtype,
     s = check_camera(camera);
     if (s != LCL_OK) return s;
     if (!depth || !aligned(depth, 4)) return fail(LCL_ERR_INVALID_ARG, "depth must be a 4-byte aligned device pointer");
-    if (!tool) return fail(LCL_ERR_INVALID_ARG, "tool is NULL");
-    if (!std::isfinite(tool->px) || !std::isfinite(tool->py) || !std::isfinite(tool->tw) || !std::isfinite(tool->th) ||
-        !(tool->tw > 0.0f) || !(tool->th > 0.0f) || std::fabs(tool->px) > 1e7f || std::fabs(tool->py) > 1e7f ||
-        tool->tw > 1e7f || tool->th > 1e7f)
-        return fail(LCL_ERR_INVALID_ARG, "tool window must be finite, positive and below 1e7 px");
-    if (tool->shape && (tool->shape_w < 1 || tool->shape_w > 4096 || tool->shape_h < 1 || tool->shape_h > 4096))
-        return fail(LCL_ERR_INVALID_ARG, "tool shape sizes must be 1..4096");
-    if ((tool->flags & ~0xFFu) || (tool->flags & 15u) > 8 || ((tool->flags >> 4) & 15u) > 8)
-        return fail(LCL_ERR_INVALID_ARG, "tool padding radius and thickness must be <= 8, other flag bits 0");
+    s = check_tool(tool);
+    if (s != LCL_OK) return s;
     if (label > (db == 1 ? 0xFFu : 0xFFFFu)) return fail(LCL_ERR_INVALID_ARG, "label does not fit the layer dtype");
     if (!std::isfinite(bias)) return fail(LCL_ERR_INVALID_ARG, "bias is not finite");
     if (hits_out && !aligned(hits_out, 8)) return fail(LCL_ERR_INVALID_ARG, "hits_out must be 8-byte aligned");
@@ -426,6 +450,135 @@ lcl_status lcl_label_area(const lcl_atlas *atlas, const void *layer, lcl_dtype d
     if (!count_out || !area_out || !aligned(count_out, 8) || !aligned(area_out, 8))
         return fail(LCL_ERR_INVALID_ARG, "outputs must be 8-byte aligned device pointers");
     return label_area_impl(atlas, layer, db, n_labels, count_out, area_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ---- numeric layers ----------------------------------------------------------------
+
+lcl_status lcl_numeric_sphere(const lcl_atlas *atlas, const lcl_numeric_layer *layer, const lcl_sphere *strokes,
+                              int32_t n, uint64_t *hits_out, void *workspace, size_t ws_bytes, lcl_stream stream) {
+    lcl_status s = check_atlas(atlas, true);
+    if (s != LCL_OK) return s;
+    s = check_numeric(layer, "layer");
+    if (s != LCL_OK) return s;
+    if (n < 0 || n > (1 << 24)) return fail(LCL_ERR_INVALID_ARG, "stroke count out of range");
+    if (n == 0) return LCL_OK;
+    if (!strokes) return fail(LCL_ERR_INVALID_ARG, "strokes is NULL");
+    if (hits_out && !aligned(hits_out, 8)) return fail(LCL_ERR_INVALID_ARG, "hits_out must be 8-byte aligned");
+    if (!workspace || !aligned(workspace, 256)) return fail(LCL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < select_ws_bytes(atlas, n)) return fail(LCL_ERR_OUT_OF_MEMORY, "workspace smaller than lcl_select_workspace_bytes");
+    const uint32_t vmax = value_mask(layer->type);
+    for (int32_t k = 0; k < n; ++k) {
+        const lcl_sphere &st = strokes[k];
+        if (st.r2 < 0) return fail(LCL_ERR_INVALID_ARG, "stroke r2 < 0");
+        if (st.label & ~vmax) return fail(LCL_ERR_INVALID_ARG, "stroke value is wider than the layer type");
+        if ((st.flags & ~0x1FFu) || (st.flags & 15u) > 8 || ((st.flags >> 4) & 15u) > 8)
+            return fail(LCL_ERR_INVALID_ARG, "stroke flags: padding radius and thickness at most 8, LCL_ERASE, other bits 0");
+        const int32_t lo = -(1 << 22), hi = (1 << 22) + (1 << 21);
+        if (st.cx < lo || st.cx > hi || st.cy < lo || st.cy > hi || st.cz < lo || st.cz > hi)
+            return fail(LCL_ERR_INVALID_ARG, "stroke centre outside [-2^22, 2^22 + 2^21]");
+    }
+    return numeric_sphere_impl(atlas, layer->data, layer->type & 15, layer->mask, strokes, n, hits_out, workspace,
+                               reinterpret_cast<cudaStream_t>(stream));
+}
+
+lcl_status lcl_numeric_lasso(const lcl_atlas *atlas, const lcl_numeric_layer *layer, const lcl_camera *camera,
+                             const float *depth, const float *poly_xy, int32_t n_vertices, uint32_t value,
+                             uint32_t flags, float bias, uint64_t *hits_out, void *workspace, size_t ws_bytes,
+                             lcl_stream stream) {
+    lcl_status s = check_atlas(atlas, true);
+    if (s != LCL_OK) return s;
+    s = check_numeric(layer, "layer");
+    if (s != LCL_OK) return s;
+    s = check_camera(camera);
+    if (s != LCL_OK) return s;
+    if (!depth || !aligned(depth, 4)) return fail(LCL_ERR_INVALID_ARG, "depth must be a 4-byte aligned device pointer");
+    if (!poly_xy) return fail(LCL_ERR_INVALID_ARG, "polygon is NULL");
+    if (n_vertices < 3 || n_vertices > LCL_MAX_LASSO_VERTICES)
+        return fail(LCL_ERR_UNSUPPORTED, "lasso polygons need 3..64 vertices");
+    for (int i = 0; i < 2 * n_vertices; ++i)
+        if (!std::isfinite(poly_xy[i])) return fail(LCL_ERR_INVALID_ARG, "polygon vertex is not finite");
+    if (value & ~value_mask(layer->type)) return fail(LCL_ERR_INVALID_ARG, "value is wider than the layer type");
+    if (flags & ~LCL_ERASE) return fail(LCL_ERR_INVALID_ARG, "flags must be 0 or LCL_ERASE");
+    if (!std::isfinite(bias)) return fail(LCL_ERR_INVALID_ARG, "bias is not finite");
+    if (hits_out && !aligned(hits_out, 8)) return fail(LCL_ERR_INVALID_ARG, "hits_out must be 8-byte aligned");
+    if (!workspace || !aligned(workspace, 256)) return fail(LCL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < select_ws_bytes(atlas, 1)) return fail(LCL_ERR_OUT_OF_MEMORY, "workspace smaller than lcl_select_workspace_bytes");
+    return numeric_lasso_impl(atlas, layer->data, layer->type & 15, layer->mask, value, flags, camera, depth, poly_xy,
+                              n_vertices, bias, hits_out, workspace, reinterpret_cast<cudaStream_t>(stream));
+}
+
+lcl_status lcl_numeric_tool(const lcl_atlas *atlas, const lcl_numeric_layer *layer, const lcl_camera *camera,
+                            const float *depth, const lcl_tool *tool, uint32_t value, uint32_t flags, float bias,
+                            uint64_t *hits_out, void *workspace, size_t ws_bytes, lcl_stream stream) {
+    lcl_status s = check_atlas(atlas, true);
+    if (s != LCL_OK) return s;
+    s = check_numeric(layer, "layer");
+    if (s != LCL_OK) return s;
+    s = check_camera(camera);
+    if (s != LCL_OK) return s;
+    if (!depth || !aligned(depth, 4)) return fail(LCL_ERR_INVALID_ARG, "depth must be a 4-byte aligned device pointer");
+    s = check_tool(tool);
+    if (s != LCL_OK) return s;
+    if (value & ~value_mask(layer->type)) return fail(LCL_ERR_INVALID_ARG, "value is wider than the layer type");
+    if (flags & ~LCL_ERASE) return fail(LCL_ERR_INVALID_ARG, "flags must be 0 or LCL_ERASE");
+    if (!std::isfinite(bias)) return fail(LCL_ERR_INVALID_ARG, "bias is not finite");
+    if (hits_out && !aligned(hits_out, 8)) return fail(LCL_ERR_INVALID_ARG, "hits_out must be 8-byte aligned");
+    if (!workspace || !aligned(workspace, 256)) return fail(LCL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < select_ws_bytes(atlas, 1)) return fail(LCL_ERR_OUT_OF_MEMORY, "workspace smaller than lcl_select_workspace_bytes");
+    return numeric_tool_impl(atlas, layer->data, layer->type & 15, layer->mask, value, flags, camera, depth, tool, bias,
+                             hits_out, workspace, reinterpret_cast<cudaStream_t>(stream));
+}
+
+lcl_status lcl_numeric_arith(const lcl_atlas *atlas, const lcl_numeric_layer *a, const lcl_numeric_layer *b,
+                             uint32_t b_value, const lcl_numeric_layer *out, lcl_arith op, lcl_stream stream) {
+    lcl_status s = check_atlas(atlas, false);
+    if (s != LCL_OK) return s;
+    if ((s = check_numeric(a, "a")) != LCL_OK) return s;
+    if (b && (s = check_numeric(b, "b")) != LCL_OK) return s;
+    if ((s = check_numeric(out, "out")) != LCL_OK) return s;
+    if ((b && b->type != a->type) || out->type != a->type)
+        return fail(LCL_ERR_INVALID_ARG, "numeric layers of an arithmetic overlay must have one type");
+    if ((int)op < LCL_ADD || (int)op > LCL_MAX) return fail(LCL_ERR_INVALID_ARG, "unknown arithmetic op");
+    if (op == LCL_DIV && (a->type >> 4) != 3) return fail(LCL_ERR_UNSUPPORTED, "LCL_DIV is for float layers only");
+    if (!b && (b_value & ~value_mask(a->type))) return fail(LCL_ERR_INVALID_ARG, "scalar is wider than the layer type");
+    return numeric_arith_impl(atlas, a->type, a->data, a->mask, b ? b->data : nullptr, b ? b->mask : nullptr, b_value,
+                              out->data, out->mask, (int)op, reinterpret_cast<cudaStream_t>(stream));
+}
+
+lcl_status lcl_numeric_select(const lcl_atlas *atlas, const lcl_numeric_layer *values, lcl_cmp cmp,
+                              uint32_t threshold, void *layer, lcl_dtype dtype, uint32_t label, uint64_t *hits_out,
+                              lcl_stream stream) {
+    lcl_status s = check_atlas(atlas, false);
+    if (s != LCL_OK) return s;
+    if ((s = check_numeric(values, "values")) != LCL_OK) return s;
+    const int db = dtype_bytes(dtype);
+    if (!db) return fail(LCL_ERR_INVALID_ARG, "dtype must be LCL_U8 or LCL_U16");
+    if (!layer || !aligned(layer, 16)) return fail(LCL_ERR_INVALID_ARG, "layer must be a 16-byte aligned device pointer");
+    if ((int)cmp < LCL_LT || (int)cmp > LCL_NE) return fail(LCL_ERR_INVALID_ARG, "unknown comparison");
+    if (threshold & ~value_mask(values->type)) return fail(LCL_ERR_INVALID_ARG, "threshold is wider than the layer type");
+    if (label > (db == 1 ? 0xFFu : 0xFFFFu)) return fail(LCL_ERR_INVALID_ARG, "label does not fit the layer dtype");
+    if (hits_out && !aligned(hits_out, 8)) return fail(LCL_ERR_INVALID_ARG, "hits_out must be 8-byte aligned");
+    return numeric_select_impl(atlas, values->type, values->data, values->mask, (int)cmp, threshold, layer, db, label,
+                               hits_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+lcl_status lcl_numeric_stats(const lcl_atlas *atlas, const lcl_numeric_layer *values, const void *zones,
+                             lcl_dtype zone_dtype, uint32_t n_labels, lcl_zone_stats *out, lcl_stream stream) {
+    lcl_status s = check_atlas(atlas, false);
+    if (s != LCL_OK) return s;
+    if ((s = check_numeric(values, "values")) != LCL_OK) return s;
+    if (n_labels < 1 || n_labels > 65536) return fail(LCL_ERR_INVALID_ARG, "n_labels must be in [1, 65536]");
+    int zb = 0;
+    if (zones) {
+        zb = dtype_bytes(zone_dtype);
+        if (!zb) return fail(LCL_ERR_INVALID_ARG, "zone dtype must be LCL_U8 or LCL_U16");
+        if (!aligned(zones, 16)) return fail(LCL_ERR_INVALID_ARG, "zones must be a 16-byte aligned device pointer");
+    } else if (n_labels != 1) {
+        return fail(LCL_ERR_INVALID_ARG, "without zones n_labels must be 1");
+    }
+    if (!out || !aligned(out, 16)) return fail(LCL_ERR_INVALID_ARG, "out must be a 16-byte aligned device pointer");
+    return numeric_stats_impl(atlas, values->type, values->data, values->mask, zones, zb, n_labels, out,
+                              reinterpret_cast<cudaStream_t>(stream));
 }
 
 const char *lcl_status_str(lcl_status status) {

@@ -156,18 +156,20 @@ __device__ uint32_t pad_mask(const AtlasDev &a, const Item &it, const SphereArg 
 }
 
 // Applies stroke `s` from its candidate list and culls stroke `nxt` (if has_next) into the other list.
-// PAD: `s` pads the texture; NEXT_PAD: `nxt` does.
-template <typename L, bool PAD, bool NEXT_PAD>
+// PAD: `s` pads the texture; NEXT_PAD: `nxt` does.  NUM: a numeric layer, whose mask bits (vm) are
+// set (or cleared) for every texel written.
+template <typename L, bool PAD, bool NEXT_PAD, bool NUM>
 __global__ void __launch_bounds__(kThreads) k_sphere_step(AtlasDev a, L *__restrict__ layer, SphereArg s,
                                                           const uint32_t *__restrict__ counter,
                                                           const uint32_t *__restrict__ list,
                                                           unsigned long long *hits, int has_next, SphereArg nxt,
-                                                          uint32_t *next_counter, uint32_t *next_list) {
+                                                          uint32_t *next_counter, uint32_t *next_list, ValMask vm) {
     pdl_wait();
     pdl_allow_next();  // the next grid waits for this one to complete before touching memory
     const int32_t qpr = a.T / 4, nq = a.T * qpr;
     const int cpt_log2 = nq > kThreads ? 31 - __clz(nq / kThreads) : 0;
     const uint32_t n_items = *counter << cpt_log2;
+    const bool grouped = a.T >= 32 && (a.w & 31) == 0;  // uniform: see valid_update_warp
     uint32_t cnt = 0;
     uint32_t item = blockIdx.x;
     Item cur;
@@ -178,7 +180,17 @@ __global__ void __launch_bounds__(kThreads) k_sphere_step(AtlasDev a, L *__restr
         Item next;
         next.l = -1;
         if (after < n_items) next = load_item(a, list, after, cpt_log2, qpr, nq);
-        if (cur.l >= 0) {
+        if (NUM) {
+            uint32_t wm = 0;
+            if (cur.l >= 0) {
+                const uint32_t m = sphere_mask(cur, s);
+                wm = PAD ? (m | pad_mask(a, cur, s)) : m;
+                if (wm) store_hits<L>(layer, cur.l, wm, s.label);
+                cnt += __popc(m);
+            }
+            if (grouped) valid_update_warp<true>(vm, cur.l, wm);
+            else valid_update_warp<false>(vm, cur.l, wm);
+        } else if (cur.l >= 0) {
             const uint32_t m = sphere_mask(cur, s);
             if (PAD) {
                 const uint32_t p = pad_mask(a, cur, s);
@@ -250,13 +262,13 @@ __global__ void __launch_bounds__(kThreads) k_dilate_candidates(AtlasDev a, cons
 }
 
 
-template <typename L>
+template <typename L, bool NUM>
 __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restrict__ layer,
                                                           const __grid_constant__ LassoArg p,
                                                           const float *__restrict__ depth,
                                                           const uint32_t *__restrict__ counter,
                                                           const uint32_t *__restrict__ list,
-                                                          unsigned long long *hits) {
+                                                          unsigned long long *hits, ValMask vm) {
     __shared__ LassoShared sh;
     for (int e = threadIdx.x; e <= p.nv; e += kThreads) {
         sh.vx[e] = p.vx[e];
@@ -285,6 +297,7 @@ __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restr
             m |= lasso_hit(p, sh, depth, X.w, Y.w, Z.w) ? 8u : 0u;
             if (m) {
                 store_hits<L>(layer, l, m, p.label);
+                if (NUM) valid_update_atomic(vm, l, m);
                 cnt += __popc(m);
             }
         }
@@ -328,13 +341,13 @@ __device__ __forceinline__ uint32_t tool_pad_mask(const AtlasDev &a, int64_t l, 
     return m;
 }
 
-template <typename L, bool MASK, bool PAD>
+template <typename L, bool MASK, bool PAD, bool NUM>
 __global__ void __launch_bounds__(kThreads, 4) k_tool_apply(AtlasDev a, L *__restrict__ layer,
                                                          const __grid_constant__ LassoArg p, ToolArg t,
                                                          const float *__restrict__ depth,
                                                          const uint32_t *__restrict__ counter,
                                                          const uint32_t *__restrict__ list,
-                                                         unsigned long long *hits) {
+                                                         unsigned long long *hits, ValMask vm) {
     const uint32_t n = *counter;
     const int32_t qpr = a.T / 4, nq = a.T * qpr;
     uint32_t cnt = 0;
@@ -356,6 +369,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_tool_apply(AtlasDev a, L *__res
             const uint32_t pm = PAD ? tool_pad_mask<MASK>(a, l, X, p, t, depth) : 0u;
             if (m | pm) {
                 store_hits<L>(layer, l, m | pm, p.label);
+                if (NUM) valid_update_atomic(vm, l, m | pm);
                 cnt += __popc(m);
             }
         }
@@ -404,11 +418,13 @@ size_t select_ws_bytes(const lcl_atlas *a, int32_t n) {
 
 template <typename L>
 using StepKernel = void (*)(AtlasDev, L *, SphereArg, const uint32_t *, const uint32_t *, unsigned long long *, int,
-                            SphereArg, uint32_t *, uint32_t *);
+                            SphereArg, uint32_t *, uint32_t *, ValMask);
 
-template <typename L>
-lcl_status select_sphere_run(const lcl_atlas *atlas, L *layer, const lcl_sphere *strokes, int32_t n, uint64_t *hits,
-                             void *ws, cudaStream_t st) {
+// Sphere strokes on a label layer (NUM false) or on the data texture of a numeric layer whose mask
+// bits are `mask` (NUM true; an erase stroke writes 0 and clears the bits).
+template <typename L, bool NUM>
+lcl_status select_sphere_run(const lcl_atlas *atlas, L *layer, uint32_t *mask, const lcl_sphere *strokes, int32_t n,
+                             uint64_t *hits, void *ws, cudaStream_t st) {
     const AtlasDev a = dev_view(atlas);
     const SelWs w = sel_ws(atlas, n, ws);
     unsigned long long *h = reinterpret_cast<unsigned long long *>(hits);
@@ -418,14 +434,20 @@ lcl_status select_sphere_run(const lcl_atlas *atlas, L *layer, const lcl_sphere 
         s.cy = strokes[k].cy;
         s.cz = strokes[k].cz;
         s.r2 = strokes[k].r2 > kR2Cap ? kR2Cap : strokes[k].r2;
-        s.label = strokes[k].label;
+        s.label = (NUM && (strokes[k].flags & LCL_ERASE)) ? 0u : strokes[k].label;
         s.pad_r = (int32_t)(strokes[k].flags & 15u);
         s.pad_t = (int32_t)((strokes[k].flags >> 4) & 15u);
         return s;
     };
+    auto vmask = [&](int32_t k) {
+        ValMask vm;
+        vm.bits = mask;
+        vm.set = (strokes[k].flags & LCL_ERASE) ? 0u : 1u;
+        return vm;
+    };
     // [pad][next_pad] variants and their resident grids
-    const StepKernel<L> step[2][2] = {{k_sphere_step<L, false, false>, k_sphere_step<L, false, true>},
-                                      {k_sphere_step<L, true, false>, k_sphere_step<L, true, true>}};
+    const StepKernel<L> step[2][2] = {{k_sphere_step<L, false, false, NUM>, k_sphere_step<L, false, true, NUM>},
+                                      {k_sphere_step<L, true, false, NUM>, k_sphere_step<L, true, true, NUM>}};
     int grid[2][2];
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) grid[i][j] = resident_grid(step[i][j]);
@@ -438,24 +460,43 @@ lcl_status select_sphere_run(const lcl_atlas *atlas, L *layer, const lcl_sphere 
         const SphereArg cur = arg(k), nxt = arg(has_next ? k + 1 : k);
         const int pi = cur.pad_r > 0, pj = has_next && nxt.pad_r > 0;
         e = launch_pdl(step[pi][pj], dim3(grid[pi][pj]), st, a, layer, cur, (const uint32_t *)(w.counters + k),
-                       (const uint32_t *)cur_list, h ? h + k : nullptr, has_next, nxt, w.counters + k + 1, next_list);
+                       (const uint32_t *)cur_list, h ? h + k : nullptr, has_next, nxt, w.counters + k + 1, next_list,
+                       vmask(k));
     }
     count_launches(2 + n);
     if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "lcl_select_sphere launch");
+    if (e != cudaSuccess) return cuda_fail(e, NUM ? "lcl_numeric_sphere launch" : "lcl_select_sphere launch");
     return LCL_OK;
 }
 
 lcl_status select_sphere_impl(const lcl_atlas *atlas, void *layer, int dtype_bytes, const lcl_sphere *strokes,
                               int32_t n, uint64_t *hits, void *ws, cudaStream_t st) {
     if (dtype_bytes == 1)
-        return select_sphere_run(atlas, static_cast<uint8_t *>(layer), strokes, n, hits, ws, st);
-    return select_sphere_run(atlas, static_cast<uint16_t *>(layer), strokes, n, hits, ws, st);
+        return select_sphere_run<uint8_t, false>(atlas, static_cast<uint8_t *>(layer), nullptr, strokes, n, hits, ws,
+                                                 st);
+    return select_sphere_run<uint16_t, false>(atlas, static_cast<uint16_t *>(layer), nullptr, strokes, n, hits, ws, st);
 }
 
-lcl_status select_lasso_impl(const lcl_atlas *atlas, void *layer, int dtype_bytes, const lcl_camera *cam,
-                             const float *depth, const float *poly, int32_t nv, uint32_t label, float bias,
-                             uint64_t *hits, void *ws, cudaStream_t st) {
+lcl_status numeric_sphere_impl(const lcl_atlas *atlas, void *data, int data_bytes, uint32_t *mask,
+                               const lcl_sphere *strokes, int32_t n, uint64_t *hits, void *ws, cudaStream_t st) {
+    if (data_bytes == 1)
+        return select_sphere_run<uint8_t, true>(atlas, static_cast<uint8_t *>(data), mask, strokes, n, hits, ws, st);
+    if (data_bytes == 2)
+        return select_sphere_run<uint16_t, true>(atlas, static_cast<uint16_t *>(data), mask, strokes, n, hits, ws, st);
+    return select_sphere_run<uint32_t, true>(atlas, static_cast<uint32_t *>(data), mask, strokes, n, hits, ws, st);
+}
+
+template <typename L, bool NUM>
+void launch_lasso_apply(const AtlasDev &a, L *layer, const LassoArg &p, const float *depth, const SelWs &w,
+                        unsigned long long *h, ValMask vm, cudaStream_t st) {
+    k_lasso_apply<L, NUM><<<resident_grid(k_lasso_apply<L, NUM>), kThreads, 0, st>>>(a, layer, p, depth, w.counters,
+                                                                                    w.list, h, vm);
+}
+
+// Lasso on a label layer (mask NULL) or on a numeric layer (data bytes 1, 2 or 4 and its mask bits).
+lcl_status lasso_run(const lcl_atlas *atlas, void *layer, int bytes, uint32_t *mask, uint32_t set, const lcl_camera *cam,
+                     const float *depth, const float *poly, int32_t nv, uint32_t label, float bias, uint64_t *hits,
+                     void *ws, cudaStream_t st) {
     const AtlasDev a = dev_view(atlas);
     const SelWs w = sel_ws(atlas, 1, ws);
     unsigned long long *h = reinterpret_cast<unsigned long long *>(hits);
@@ -463,44 +504,66 @@ lcl_status select_lasso_impl(const lcl_atlas *atlas, void *layer, int dtype_byte
     fill_lasso_arg(p, cam, poly, nv, label, bias);
     k_sel_init<<<1, kThreads, 0, st>>>(w.counters, 1, h);
     const int n_cull = launch_lasso_cull(a, atlas, p, depth, w, false, st);
-    const int ag = dtype_bytes == 1 ? resident_grid(k_lasso_apply<uint8_t>) : resident_grid(k_lasso_apply<uint16_t>);
-    if (dtype_bytes == 1)
-        k_lasso_apply<uint8_t><<<ag, kThreads, 0, st>>>(a, static_cast<uint8_t *>(layer), p, depth, w.counters, w.list, h);
-    else
-        k_lasso_apply<uint16_t><<<ag, kThreads, 0, st>>>(a, static_cast<uint16_t *>(layer), p, depth, w.counters,
-                                                        w.list, h);
+    ValMask vm;
+    vm.bits = mask;
+    vm.set = set;
+    if (!mask) {
+        if (bytes == 1) launch_lasso_apply<uint8_t, false>(a, static_cast<uint8_t *>(layer), p, depth, w, h, vm, st);
+        else launch_lasso_apply<uint16_t, false>(a, static_cast<uint16_t *>(layer), p, depth, w, h, vm, st);
+    } else if (bytes == 1) {
+        launch_lasso_apply<uint8_t, true>(a, static_cast<uint8_t *>(layer), p, depth, w, h, vm, st);
+    } else if (bytes == 2) {
+        launch_lasso_apply<uint16_t, true>(a, static_cast<uint16_t *>(layer), p, depth, w, h, vm, st);
+    } else {
+        launch_lasso_apply<uint32_t, true>(a, static_cast<uint32_t *>(layer), p, depth, w, h, vm, st);
+    }
     count_launches(2 + n_cull);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "lcl_select_lasso launch");
+    if (e != cudaSuccess) return cuda_fail(e, mask ? "lcl_numeric_lasso launch" : "lcl_select_lasso launch");
     return LCL_OK;
 }
 
-template <typename L>
+lcl_status select_lasso_impl(const lcl_atlas *atlas, void *layer, int dtype_bytes, const lcl_camera *cam,
+                             const float *depth, const float *poly, int32_t nv, uint32_t label, float bias,
+                             uint64_t *hits, void *ws, cudaStream_t st) {
+    return lasso_run(atlas, layer, dtype_bytes, nullptr, 1u, cam, depth, poly, nv, label, bias, hits, ws, st);
+}
+
+lcl_status numeric_lasso_impl(const lcl_atlas *atlas, void *data, int data_bytes, uint32_t *mask, uint32_t value,
+                              uint32_t flags, const lcl_camera *cam, const float *depth, const float *poly, int32_t nv,
+                              float bias, uint64_t *hits, void *ws, cudaStream_t st) {
+    const bool erase = (flags & LCL_ERASE) != 0;
+    return lasso_run(atlas, data, data_bytes, mask, erase ? 0u : 1u, cam, depth, poly, nv, erase ? 0u : value, bias,
+                     hits, ws, st);
+}
+
+template <typename L, bool NUM>
 void launch_tool(int sel, const AtlasDev &a, L *layer, const LassoArg &p, const ToolArg &t, const float *depth,
-                 const SelWs &w, unsigned long long *h, cudaStream_t st) {
+                 const SelWs &w, unsigned long long *h, ValMask vm, cudaStream_t st) {
     switch (sel) {  // bit 0: shape mask, bit 1: padding
     case 0:
-        k_tool_apply<L, false, false><<<resident_grid(k_tool_apply<L, false, false>), kThreads, 0, st>>>(
-            a, layer, p, t, depth, w.counters, w.list, h);
+        k_tool_apply<L, false, false, NUM><<<resident_grid(k_tool_apply<L, false, false, NUM>), kThreads, 0, st>>>(
+            a, layer, p, t, depth, w.counters, w.list, h, vm);
         break;
     case 1:
-        k_tool_apply<L, true, false><<<resident_grid(k_tool_apply<L, true, false>), kThreads, 0, st>>>(
-            a, layer, p, t, depth, w.counters, w.list, h);
+        k_tool_apply<L, true, false, NUM><<<resident_grid(k_tool_apply<L, true, false, NUM>), kThreads, 0, st>>>(
+            a, layer, p, t, depth, w.counters, w.list, h, vm);
         break;
     case 2:
-        k_tool_apply<L, false, true><<<resident_grid(k_tool_apply<L, false, true>), kThreads, 0, st>>>(
-            a, layer, p, t, depth, w.counters, w.list, h);
+        k_tool_apply<L, false, true, NUM><<<resident_grid(k_tool_apply<L, false, true, NUM>), kThreads, 0, st>>>(
+            a, layer, p, t, depth, w.counters, w.list, h, vm);
         break;
     default:
-        k_tool_apply<L, true, true><<<resident_grid(k_tool_apply<L, true, true>), kThreads, 0, st>>>(
-            a, layer, p, t, depth, w.counters, w.list, h);
+        k_tool_apply<L, true, true, NUM><<<resident_grid(k_tool_apply<L, true, true, NUM>), kThreads, 0, st>>>(
+            a, layer, p, t, depth, w.counters, w.list, h, vm);
         break;
     }
 }
 
-lcl_status select_tool_impl(const lcl_atlas *atlas, void *layer, int dtype_bytes, const lcl_camera *cam,
-                            const float *depth, const lcl_tool *tool, uint32_t label, float bias, uint64_t *hits,
-                            void *ws, cudaStream_t st) {
+// The tool on a label layer (mask NULL) or on a numeric layer.
+lcl_status tool_run(const lcl_atlas *atlas, void *layer, int bytes, uint32_t *mask, uint32_t set, const lcl_camera *cam,
+                    const float *depth, const lcl_tool *tool, uint32_t label, float bias, uint64_t *hits, void *ws,
+                    cudaStream_t st) {
     const AtlasDev a = dev_view(atlas);
     const SelWs w = sel_ws(atlas, 1, ws);
     unsigned long long *h = reinterpret_cast<unsigned long long *>(hits);
@@ -511,14 +574,37 @@ lcl_status select_tool_impl(const lcl_atlas *atlas, void *layer, int dtype_bytes
     const bool pad = t.pad_r > 0;
     const int n_cull = launch_lasso_cull(a, atlas, p, depth, w, pad, st);
     const int sel = (tool->shape != nullptr ? 1 : 0) + (pad ? 2 : 0);
-    if (dtype_bytes == 1)
-        launch_tool<uint8_t>(sel, a, static_cast<uint8_t *>(layer), p, t, depth, w, h, st);
-    else
-        launch_tool<uint16_t>(sel, a, static_cast<uint16_t *>(layer), p, t, depth, w, h, st);
+    ValMask vm;
+    vm.bits = mask;
+    vm.set = set;
+    if (!mask) {
+        if (bytes == 1) launch_tool<uint8_t, false>(sel, a, static_cast<uint8_t *>(layer), p, t, depth, w, h, vm, st);
+        else launch_tool<uint16_t, false>(sel, a, static_cast<uint16_t *>(layer), p, t, depth, w, h, vm, st);
+    } else if (bytes == 1) {
+        launch_tool<uint8_t, true>(sel, a, static_cast<uint8_t *>(layer), p, t, depth, w, h, vm, st);
+    } else if (bytes == 2) {
+        launch_tool<uint16_t, true>(sel, a, static_cast<uint16_t *>(layer), p, t, depth, w, h, vm, st);
+    } else {
+        launch_tool<uint32_t, true>(sel, a, static_cast<uint32_t *>(layer), p, t, depth, w, h, vm, st);
+    }
     count_launches(2 + n_cull);
     const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "lcl_select_tool launch");
+    if (e != cudaSuccess) return cuda_fail(e, mask ? "lcl_numeric_tool launch" : "lcl_select_tool launch");
     return LCL_OK;
+}
+
+lcl_status select_tool_impl(const lcl_atlas *atlas, void *layer, int dtype_bytes, const lcl_camera *cam,
+                            const float *depth, const lcl_tool *tool, uint32_t label, float bias, uint64_t *hits,
+                            void *ws, cudaStream_t st) {
+    return tool_run(atlas, layer, dtype_bytes, nullptr, 1u, cam, depth, tool, label, bias, hits, ws, st);
+}
+
+lcl_status numeric_tool_impl(const lcl_atlas *atlas, void *data, int data_bytes, uint32_t *mask, uint32_t value,
+                             uint32_t flags, const lcl_camera *cam, const float *depth, const lcl_tool *tool,
+                             float bias, uint64_t *hits, void *ws, cudaStream_t st) {
+    const bool erase = (flags & LCL_ERASE) != 0;
+    return tool_run(atlas, data, data_bytes, mask, erase ? 0u : 1u, cam, depth, tool, erase ? 0u : value, bias, hits,
+                    ws, st);
 }
 
 }  // namespace lcl

@@ -111,6 +111,54 @@ __device__ __forceinline__ void store_hits<uint16_t>(uint16_t *layer, int64_t l,
     *p = make_uint2((o.x & ~lo) | (rep & lo), (o.y & ~hi) | (rep & hi));
 }
 
+template <>
+__device__ __forceinline__ void store_hits<uint32_t>(uint32_t *layer, int64_t l, uint32_t m, uint32_t value) {
+    if (m == 0xFu) {
+        *reinterpret_cast<uint4 *>(layer + l) = make_uint4(value, value, value, value);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (m & (1u << k)) layer[l + k] = value;
+}
+
+// Mask texture of a numeric layer (Section 4.2): one bit per texel, bit (y * width + x) of a linear
+// uint32 array like the coverage bits.  An edit sets the bits of the texels it writes (or clears
+// them when it erases).
+struct ValMask {
+    uint32_t *bits;
+    uint32_t set;  // 1: set the written texels' bits, 0: clear them
+};
+
+// Updates the mask bits of one quad (bits m at texel l, l a multiple of 4) with one atomic.
+__device__ __forceinline__ void valid_update_atomic(const ValMask &vm, int64_t l, uint32_t m) {
+    const uint32_t b = m << (l & 31);
+    if (vm.set) atomicOr(vm.bits + (l >> 5), b);
+    else atomicAnd(vm.bits + (l >> 5), ~b);
+}
+
+// Updates the mask bits of the quads of a whole warp; every lane calls it (l < 0: no quad).
+// GROUPED: the eight lanes 8g..8g+7 hold the 32 texels of one mask word, all of them or none (a
+// tile side of at least 32 and a width that is a multiple of 32); their bits are merged with three
+// shuffles and the word is written by its first lane, which owns it during the launch (one edit
+// per launch), so no atomic is needed.  Otherwise each quad updates its bits with one atomic.
+template <bool GROUPED>
+__device__ __forceinline__ void valid_update_warp(const ValMask &vm, int64_t l, uint32_t m) {
+    if (GROUPED) {
+        uint32_t b = (l >= 0) ? (m << (l & 31)) : 0u;
+        b |= __shfl_xor_sync(0xffffffffu, b, 1);
+        b |= __shfl_xor_sync(0xffffffffu, b, 2);
+        b |= __shfl_xor_sync(0xffffffffu, b, 4);
+        if ((threadIdx.x & 7u) == 0 && l >= 0 && b) {
+            uint32_t *p = vm.bits + (l >> 5);
+            if (vm.set) *p = (b == 0xFFFFFFFFu) ? b : (*p | b);
+            else *p = (b == 0xFFFFFFFFu) ? 0u : (*p & ~b);
+        }
+    } else if (l >= 0 && m) {
+        valid_update_atomic(vm, l, m);
+    }
+}
+
 __device__ __forceinline__ void add_hits(unsigned long long *hits, uint32_t cnt) {
     if (!hits) return;
     __shared__ uint32_t s_cnt;

@@ -32,7 +32,9 @@ EXPORTS = ["lcl_atlas_bytes", "lcl_atlas_bind", "lcl_atlas_rows", "lcl_atlas_wor
            "lcl_select_sphere_static", "lcl_depth_workspace_bytes", "lcl_depth_render", "lcl_select_lasso", "lcl_select_tool",
            "lcl_batch_limits_of", "lcl_batch_workspace_bytes", "lcl_batch_staging_bytes", "lcl_batch_upload",
            "lcl_batch_launch", "lcl_batch_edit", "lcl_batch_tune",
-           "lcl_overlay", "lcl_label_area", "lcl_status_str", "lcl_last_error", "lcl_kernel_launches"]
+           "lcl_overlay", "lcl_label_area", "lcl_numeric_sphere", "lcl_numeric_lasso", "lcl_numeric_tool",
+           "lcl_numeric_arith", "lcl_numeric_select", "lcl_numeric_stats",
+           "lcl_status_str", "lcl_last_error", "lcl_kernel_launches"]
 
 
 class lcl_mesh(C.Structure):
@@ -62,6 +64,15 @@ class lcl_tool(C.Structure):
     _fields_ = [("px", C.c_float), ("py", C.c_float), ("tw", C.c_float), ("th", C.c_float),
                 ("shape", C.c_void_p), ("shape_w", C.c_int32), ("shape_h", C.c_int32), ("flags", C.c_uint32),
                 ("_pad", C.c_int32)]
+
+
+class lcl_numeric_layer(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("mask", C.c_void_p), ("type", C.c_int), ("_pad", C.c_int32)]
+
+
+class lcl_zone_stats(C.Structure):
+    _fields_ = [("count", C.c_uint64), ("area", C.c_uint64), ("vmin", C.c_double), ("vmax", C.c_double),
+                ("sum", C.c_double), ("wsum", C.c_double)]
 
 
 class lcl_batch_model(C.Structure):
@@ -96,6 +107,7 @@ BATCH_MAX_STROKES = 64
 assert C.sizeof(lcl_sphere) == 32 and C.sizeof(lcl_camera) == 72 and C.sizeof(lcl_atlas) == 128
 assert C.sizeof(lcl_batch_model) == 32 and C.sizeof(lcl_batch_stroke) == 40 and C.sizeof(lcl_batch_lasso) == 104
 assert C.sizeof(lcl_batch_limits) == 32 and C.sizeof(lcl_batch_config) == 16 and C.sizeof(lcl_tool) == 40
+assert C.sizeof(lcl_numeric_layer) == 24 and C.sizeof(lcl_zone_stats) == 48
 
 SPHERE_DTYPE = np.dtype([("cx", "<i4"), ("cy", "<i4"), ("cz", "<i4"), ("pad", "<i4"),
                          ("r2", "<i8"), ("label", "<u4"), ("flags", "<u4")])
@@ -152,6 +164,16 @@ def library():
                                 C.POINTER(C.c_float)]),
         "lcl_overlay": (st, [C.POINTER(lcl_atlas), P, P, P, C.c_int, C.c_int, U32, P]),
         "lcl_label_area": (st, [C.POINTER(lcl_atlas), P, C.c_int, U32, P, P, P]),
+        "lcl_numeric_sphere": (st, [C.POINTER(lcl_atlas), C.POINTER(lcl_numeric_layer), P, I32, P, P, SZ, P]),
+        "lcl_numeric_lasso": (st, [C.POINTER(lcl_atlas), C.POINTER(lcl_numeric_layer), C.POINTER(lcl_camera), P, P,
+                                   I32, U32, U32, F, P, P, SZ, P]),
+        "lcl_numeric_tool": (st, [C.POINTER(lcl_atlas), C.POINTER(lcl_numeric_layer), C.POINTER(lcl_camera), P,
+                                  C.POINTER(lcl_tool), U32, U32, F, P, P, SZ, P]),
+        "lcl_numeric_arith": (st, [C.POINTER(lcl_atlas), C.POINTER(lcl_numeric_layer), C.POINTER(lcl_numeric_layer),
+                                   U32, C.POINTER(lcl_numeric_layer), C.c_int, P]),
+        "lcl_numeric_select": (st, [C.POINTER(lcl_atlas), C.POINTER(lcl_numeric_layer), C.c_int, U32, P, C.c_int, U32,
+                                    P, P]),
+        "lcl_numeric_stats": (st, [C.POINTER(lcl_atlas), C.POINTER(lcl_numeric_layer), P, C.c_int, U32, P, P]),
         "lcl_status_str": (C.c_char_p, [C.c_int]),
         "lcl_last_error": (C.c_char_p, []),
         "lcl_kernel_launches": (C.c_uint64, []),
@@ -618,6 +640,100 @@ def lcl_label_area(atlas: Atlas, layer: torch.Tensor, n_labels, count_out=None, 
                                                       int(n_labels), _ptr(count_out), _ptr(area_out),
                                                       _stream(stream)))
     return count_out, area_out
+
+
+# ---- numeric layers ------------------------------------------------------------------------
+
+NUM_TYPES = {"u8": 0x11, "u16": 0x12, "u32": 0x14, "i8": 0x21, "i16": 0x22, "i32": 0x24, "f16": 0x32, "f32": 0x34}
+NUM_TORCH = {"u8": torch.uint8, "u16": torch.int16, "u32": torch.int32, "i8": torch.int8, "i16": torch.int16,
+             "i32": torch.int32, "f16": torch.float16, "f32": torch.float32}
+ARITH = {"add": 0, "sub": 1, "mul": 2, "div": 3, "min": 4, "max": 5}
+CMP = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5}
+LCL_ERASE = 0x100
+ZONE_DTYPE = np.dtype([("count", "<u8"), ("area", "<u8"), ("vmin", "<f8"), ("vmax", "<f8"), ("sum", "<f8"),
+                       ("wsum", "<f8")])
+
+
+class NumericLayer:
+    """A numeric layer on the device (Section 4.2): ``data`` (height x width values; u16 / u32 held in
+    int16 / int32 tensors, bit for bit) and ``mask`` (one bit per texel, ceil(W*H/32) int32 words)."""
+
+    def __init__(self, width, height, ntype, device="cuda", data=None, mask=None):
+        self.width, self.height, self.ntype = int(width), int(height), ntype
+        self.data = torch.zeros((height, width), dtype=NUM_TORCH[ntype], device=device) if data is None else data
+        n_words = (width * height + 31) // 32
+        self.mask = torch.zeros(((n_words + 3) // 4) * 4, dtype=torch.int32, device=device) if mask is None else mask
+        self.c = lcl_numeric_layer(self.data.data_ptr(), self.mask.data_ptr(), NUM_TYPES[ntype], 0)
+
+    def mask_bits(self):
+        """The mask as a host bool array of the layer's shape."""
+        w = self.mask.cpu().numpy().view(np.uint32)
+        bits = np.unpackbits(w.view(np.uint8), bitorder="little")[: self.width * self.height]
+        return bits.reshape(self.height, self.width).astype(bool)
+
+
+def lcl_numeric_sphere(atlas: Atlas, layer: NumericLayer, strokes, hits_out=None, workspace=None, stream=None):
+    """Sphere strokes on a numeric layer (the record's ``label`` field holds the value's bits; flags
+    may add LCL_ERASE)."""
+    recs = np.ascontiguousarray(strokes, dtype=SPHERE_DTYPE)
+    n = len(recs)
+    ws = workspace if workspace is not None else _workspace(lcl_select_workspace_bytes(atlas, n), layer.data.device)
+    _check("lcl_numeric_sphere", library().lcl_numeric_sphere(
+        C.byref(atlas.c), C.byref(layer.c), recs.ctypes.data_as(C.c_void_p), n, _ptr(hits_out), _ptr(ws), ws.numel(),
+        _stream(stream)))
+    return hits_out
+
+
+def lcl_numeric_lasso(atlas: Atlas, layer: NumericLayer, cam: lcl_camera, depth: torch.Tensor, poly, value_bits,
+                      flags=0, bias=DEFAULT_BIAS, hits_out=None, workspace=None, stream=None):
+    poly = np.ascontiguousarray(poly, dtype=np.float32)
+    ws = workspace if workspace is not None else _workspace(lcl_select_workspace_bytes(atlas, 1), layer.data.device)
+    _check("lcl_numeric_lasso", library().lcl_numeric_lasso(
+        C.byref(atlas.c), C.byref(layer.c), C.byref(cam), _ptr(depth), poly.ctypes.data_as(C.c_void_p), poly.shape[0],
+        int(value_bits), int(flags), float(bias), _ptr(hits_out), _ptr(ws), ws.numel(), _stream(stream)))
+    return hits_out
+
+
+def lcl_numeric_tool(atlas: Atlas, layer: NumericLayer, cam: lcl_camera, depth: torch.Tensor, tool: lcl_tool,
+                     value_bits, flags=0, bias=DEFAULT_BIAS, hits_out=None, workspace=None, stream=None):
+    ws = workspace if workspace is not None else _workspace(lcl_select_workspace_bytes(atlas, 1), layer.data.device)
+    _check("lcl_numeric_tool", library().lcl_numeric_tool(
+        C.byref(atlas.c), C.byref(layer.c), C.byref(cam), _ptr(depth), C.byref(tool), int(value_bits), int(flags),
+        float(bias), _ptr(hits_out), _ptr(ws), ws.numel(), _stream(stream)))
+    return hits_out
+
+
+def lcl_numeric_arith(atlas: Atlas, a: NumericLayer, b, out: NumericLayer, op, b_value_bits=0, stream=None):
+    """out = a <op> b (b a NumericLayer, or None for the scalar b_value_bits)."""
+    op = ARITH[op] if isinstance(op, str) else int(op)
+    _check("lcl_numeric_arith", library().lcl_numeric_arith(
+        C.byref(atlas.c), C.byref(a.c), None if b is None else C.byref(b.c), int(b_value_bits), C.byref(out.c), op,
+        _stream(stream)))
+    return out
+
+
+def lcl_numeric_select(atlas: Atlas, values: NumericLayer, cmp, threshold_bits, layer: torch.Tensor, label,
+                       hits_out=None, stream=None):
+    cmp = CMP[cmp] if isinstance(cmp, str) else int(cmp)
+    _check("lcl_numeric_select", library().lcl_numeric_select(
+        C.byref(atlas.c), C.byref(values.c), cmp, int(threshold_bits), _ptr(layer), _dtype_code(layer), int(label),
+        _ptr(hits_out), _stream(stream)))
+    return hits_out
+
+
+def lcl_numeric_stats(atlas: Atlas, values: NumericLayer, zones, n_labels, out=None, stream=None):
+    """Zonal statistics; ``out``: device uint8 tensor of n_labels * 48 bytes (allocated if None)."""
+    dev = values.data.device
+    out = torch.empty(n_labels * 48, dtype=torch.uint8, device=dev) if out is None else out
+    zcode = 0 if zones is None else _dtype_code(zones)
+    _check("lcl_numeric_stats", library().lcl_numeric_stats(
+        C.byref(atlas.c), C.byref(values.c), _ptr(zones), zcode, int(n_labels), _ptr(out), _stream(stream)))
+    return out
+
+
+def zone_stats_host(out: torch.Tensor):
+    """Device zone records -> numpy structured array (count, area, vmin, vmax, sum, wsum)."""
+    return out.cpu().numpy().view(ZONE_DTYPE)
 
 
 def lcl_status_str(status):

@@ -285,3 +285,44 @@ def test_batch_rejects_bad_arguments_on_host(lcl):
     assert lib.lcl_batch_launch(C.byref(lim), None, ws, 16, None) == 1      # workspace smaller than the limits
     best, ms = lcl.lcl_batch_config(), C.c_float()
     assert lib.lcl_batch_tune(C.byref(lim), ws, 1 << 30, 0, None, C.byref(best), C.byref(ms)) == 1  # reps < 1
+
+
+def test_numeric_layers_reject_bad_arguments(lcl):
+    lib, a = _bound(lcl)
+    P = lambda r: r.ctypes.data_as(C.c_void_p)  # noqa: E731
+    data, mask = 1 << 41, 1 << 42
+    ws = C.c_void_p(1 << 43)
+    wsb = lib.lcl_select_workspace_bytes(C.byref(a), 4)
+
+    def layer(t, d=data, m=mask):
+        return lcl.lcl_numeric_layer(d, m, t, 0)
+
+    i16, f32 = layer(lcl.NUM_TYPES["i16"]), layer(lcl.NUM_TYPES["f32"])
+    good = np.zeros(4, lcl.SPHERE_DTYPE)
+
+    def sphere(recs, lay=i16):
+        return lib.lcl_numeric_sphere(C.byref(a), C.byref(lay), P(recs), len(recs), None, ws, wsb, None)
+
+    bad = good.copy(); bad[0]["label"] = 1 << 16
+    assert sphere(bad) == 1                                           # value wider than int16
+    bad = good.copy(); bad[1]["flags"] = 0x200
+    assert sphere(bad) == 1                                           # unknown flag bit
+    assert sphere(good, layer(0x13)) == 1                             # unknown type
+    assert sphere(good, layer(lcl.NUM_TYPES["i16"], d=data + 4)) == 1  # data misaligned
+    assert sphere(good, layer(lcl.NUM_TYPES["i16"], m=0)) == 1        # no mask
+    # arithmetic
+    ar = lambda x, y, o, op, s=0: lib.lcl_numeric_arith(C.byref(a), C.byref(x), None if y is None else C.byref(y),  # noqa
+                                                        s, C.byref(o), op, None)
+    assert ar(i16, f32, i16, 0) == 1                                  # types differ
+    assert ar(i16, i16, i16, 3) == 4                                  # integer division
+    assert ar(i16, i16, i16, 6) == 1                                  # unknown op
+    assert ar(i16, None, i16, 0, 1 << 16) == 1                        # scalar wider than the type
+    # selection by value and statistics
+    lay = C.c_void_p(1 << 44)
+    assert lib.lcl_numeric_select(C.byref(a), C.byref(f32), 6, 0, lay, 1, 1, None, None) == 1   # unknown cmp
+    assert lib.lcl_numeric_select(C.byref(a), C.byref(i16), 0, 1 << 16, lay, 1, 1, None, None) == 1
+    assert lib.lcl_numeric_select(C.byref(a), C.byref(f32), 0, 0, lay, 1, 256, None, None) == 1  # label > u8
+    out = C.c_void_p(1 << 45)
+    assert lib.lcl_numeric_stats(C.byref(a), C.byref(f32), None, 0, 2, out, None) == 1   # no zones, 2 labels
+    assert lib.lcl_numeric_stats(C.byref(a), C.byref(f32), lay, 1, 0, out, None) == 1    # n_labels 0
+    assert lib.lcl_numeric_stats(C.byref(a), C.byref(f32), lay, 3, 4, out, None) == 1    # zone dtype
