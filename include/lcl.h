@@ -481,8 +481,9 @@ typedef struct {
  * set, whose value is not NaN and whose zone label z < n_labels (zones == NULL: every such texel is
  * in zone 0 and n_labels must be 1), per zone: count, area, min, max (values as double; -0 counts
  * as +0), sum of values and sum of weight x value in double.  count, area, vmin and vmax are
- * exact; the sums are accumulated in an unspecified order (error at most (count - 1) * 2^-53 *
- * sum of |terms|).  out: device, n_labels records (overwritten).  n_labels in [1, 65536]. */
+ * exact; the sums are accumulated in an unspecified order, the weighted one per stretch of texels
+ * of one triangle as weight x (sum of their values): errors at most (count - 1) * 2^-53 * sum |v|
+ * for sum and 2 * count * 2^-53 * sum |w v| for wsum.  out: device, n_labels records (overwritten).  n_labels in [1, 65536]. */
 lcl_status lcl_numeric_stats(const lcl_atlas *atlas, const lcl_numeric_layer *values, const void *zones,
                              lcl_dtype zone_dtype, uint32_t n_labels, lcl_zone_stats *out, lcl_stream stream);
 

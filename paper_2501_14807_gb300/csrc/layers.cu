@@ -5,14 +5,13 @@
 //   k_overlay  16 bytes of each operand and of the output per thread step, coverage bits
 //              expanded to byte / half-word masks in registers (SWAR), no shared memory
 //   k_area     a contiguous range of 16-texel chunks per warp (one chunk per lane and step);
-//              runs of equal labels are summed in registers, a lane's runs into a warp run
-//              with warp reductions while the whole warp sees one label, otherwise grouped
-//              by label (match_any) and flushed into a shared-memory histogram (64-bit
-//              shared atomics); the histogram goes into the outputs with one global atomic
-//              per non-zero bin per CTA.  All sums are integers, so the result does not
-//              depend on the order.  Measured on GB300 (16384^2, 256 labels): 0.35-0.41 ms
-//              per query against 0.39-0.57 ms for one-lane-at-a-time flushes; without any
-//              flush the same loads and gathers take 0.25 ms.
+//              runs of equal labels stay in registers while the whole warp sees one label,
+//              then are reduced across the warp (shuffles, match_any groups) and flushed
+//              into a shared-memory histogram (64-bit shared atomics); the histogram goes
+//              into the outputs with one global atomic per non-zero bin per CTA.  All sums
+//              are integers, so the result does not depend on the order.  A flush per lane
+//              and chunk (one shared atomic pair each) cost 0.39-0.57 ms per 16384^2 query
+//              on GB300; the same loads and gathers without any flush take 0.25 ms.
 #include <algorithm>
 
 #include "lcl_impl.cuh"
@@ -153,12 +152,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ laye
 #pragma unroll
         for (int k = 0; k < LW; ++k) V[k] = __ldcs(reinterpret_cast<const uint4 *>(layer + 16 * c) + k);
     };
-    // warp run: while every lane's run of an iteration has the warp's label, the lanes' counts and
-    // areas are summed with warp reductions into registers (areas below 2^40 per lane: two 20-bit
-    // halves); otherwise the warp run is flushed and the lanes are grouped by label (match_any),
-    // one atomic pair per group
-    uint32_t wlabel = kNone, wcnt = 0;
-    unsigned long long warea = 0;
+    // warp run: while every lane's run of an iteration has the warp's label, each lane adds its run
+    // to its own share of the warp run (registers only); when an iteration brings another label, the
+    // shares are reduced across the warp and written by one lane, and this iteration's runs are
+    // reduced label by label (match_any groups)
+    uint32_t wlabel = kNone;
+    unsigned long long wcnt = 0, warea = 0;
     if (it0 < it1 && it0 * 32 + lane < n_chunks) load(it0 * 32 + lane);
     for (int64_t it = it0; it < it1; ++it) {
         const int64_t c = it * 32 + lane;
@@ -183,14 +182,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ laye
         }
         const uint32_t key = run.cnt ? run.label : kNone;
         if (__all_sync(0xffffffffu, key == wlabel || key == kNone)) {
-            wcnt += __reduce_add_sync(0xffffffffu, run.cnt);
-            const uint32_t lo = __reduce_add_sync(0xffffffffu, (uint32_t)(run.area & 0xFFFFFu));
-            const uint32_t hi = __reduce_add_sync(0xffffffffu, (uint32_t)(run.area >> 20));
-            warea += (unsigned long long)lo + ((unsigned long long)hi << 20);
+            wcnt += run.cnt;
+            warea += run.area;
         } else {
-            if (lane == 0 && wcnt) {
-                atomicAdd(hc + wlabel, (unsigned long long)wcnt);
-                atomicAdd(ha + wlabel, warea);
+            unsigned long long tc = wcnt, ta = warea;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                tc += __shfl_xor_sync(0xffffffffu, tc, o);
+                ta += __shfl_xor_sync(0xffffffffu, ta, o);
+            }
+            if (lane == 0 && tc) {
+                atomicAdd(hc + wlabel, tc);
+                atomicAdd(ha + wlabel, ta);
             }
             wcnt = 0;
             warea = 0;
@@ -207,9 +210,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ laye
         run.cnt = 0;
         run.area = 0;
     }
-    if (lane == 0 && wcnt) {
-        atomicAdd(hc + wlabel, (unsigned long long)wcnt);
-        atomicAdd(ha + wlabel, warea);
+    {
+        unsigned long long tc = wcnt, ta = warea;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            tc += __shfl_xor_sync(0xffffffffu, tc, o);
+            ta += __shfl_xor_sync(0xffffffffu, ta, o);
+        }
+        if (lane == 0 && tc) {
+            atomicAdd(hc + wlabel, tc);
+            atomicAdd(ha + wlabel, ta);
+        }
     }
     // tail texels (n_texels % 16), one per thread
     for (int64_t t = n_chunks * 16 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_texels;

@@ -6,8 +6,9 @@
 //                 the 2, 4 or 8 lanes of its group, and the group's output word is merged with
 //                 shuffles and written by its first lane
 //   k_num_select  selection by value into a label layer (the lane owns its texels' label bytes)
-//   k_num_stats   zonal statistics: a warp takes 512 texels per step (lane l: texels 4l + 128k),
-//                 runs of equal zone labels are accumulated in registers and flushed into a
+//   k_num_stats   zonal statistics: a contiguous range of 16-texel chunks per warp (one chunk per
+//                 lane and step); runs of equal zone labels stay in registers until the warp
+//                 meets another zone, then are reduced across the warp and flushed into a
 //                 shared-memory table (or the output, for many zones); min / max through
 //                 order-preserving 64-bit keys, sums in double
 #include <algorithm>
@@ -338,22 +339,129 @@ __global__ void k_stats_final(ZoneAcc *z, uint32_t n) {
     }
 }
 
+// ---- per-texel value handling for the statistics ------------------------------------------
+// Order-preserving 32-bit key of a value in its own type (integer min / max, no FP64):
+// unsigned: the value; signed: value ^ 2^31 (of the sign-extended value); floats: the float32
+// bits with the sign folded.  key_value turns a key back into the exact double.
+template <int S, int KIND>
+__device__ __forceinline__ uint32_t vkey(uint32_t f32_or_int_bits) {
+    if (KIND == kKindFloat) {
+        const uint32_t b = f32_or_int_bits;
+        return (b >> 31) ? ~b : (b | 0x80000000u);
+    }
+    if (KIND == kKindSigned) return (uint32_t)sext<S>(f32_or_int_bits) ^ 0x80000000u;
+    return f32_or_int_bits;
+}
+
+template <int S, int KIND>
+__device__ __forceinline__ double key_value(uint32_t k) {
+    if (KIND == kKindFloat) return (double)__uint_as_float((k >> 31) ? (k & 0x7FFFFFFFu) : ~k);
+    if (KIND == kKindSigned) return (double)(int32_t)(k ^ 0x80000000u);
+    return (double)k;
+}
+
+// float32 bits -> double, by integer operations for normal numbers and zeros (FP64 throughput
+// on this part is a small fraction of its integer throughput); subnormals and infinities through
+// the conversion instruction.
+__device__ __forceinline__ double f32_bits_to_double(uint32_t b) {
+    const uint32_t e = (b >> 23) & 0xFFu;
+    if (e == 0 || e == 0xFFu) {
+        if ((b & 0x7FFFFFFFu) == 0) return __hiloint2double((int)(b & 0x80000000u), 0);
+        return (double)__uint_as_float(b);
+    }
+    const uint32_t m = b & 0x7FFFFFu;
+    const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | (m >> 3);
+    return __hiloint2double((int)hi, (int)(m << 29));
+}
+
+// Running sums of one (zone, triangle) stretch: integers and finite float16 values (integer
+// multiples of 2^-24) exactly in int64, float32 values and float16 infinities in double; closed
+// into the zone run as sum += s and wsum += w * s.
+template <int S, int KIND>
+struct TriSum {
+    static constexpr bool kInt = !(KIND == kKindFloat && S == 4);
+    long long i;
+    double d;
+    __device__ __forceinline__ void reset() {
+        i = 0;
+        d = 0.0;
+    }
+    __device__ __forceinline__ double value() const {
+        if (!kInt) return d;
+        if (KIND == kKindFloat) return __dadd_rn(__dmul_rn((double)i, 0x1p-24), d);  // exact: |i| < 2^45; d: infinities
+        return (double)i;                                                             // exact: |i| < 2^37
+    }
+};
+
 struct StatsRun {
     uint32_t zone;
     uint32_t cnt;
     unsigned long long area;
-    double vmin, vmax, sum, wsum;
+    uint32_t kmin, kmax;  // value keys (vkey) of the smallest and largest value
+    double sum, wsum;
 };
 
+__device__ __forceinline__ void run_reset(StatsRun &r) {
+    r.cnt = 0;
+    r.area = 0;
+    r.kmin = 0xFFFFFFFFu;
+    r.kmax = 0u;
+    r.sum = 0.0;
+    r.wsum = 0.0;
+}
+
+__device__ __forceinline__ void run_merge(StatsRun &r, const StatsRun &o) {
+    r.cnt += o.cnt;
+    r.area += o.area;
+    r.kmin = min(r.kmin, o.kmin);
+    r.kmax = max(r.kmax, o.kmax);
+    r.sum = __dadd_rn(r.sum, o.sum);
+    r.wsum = __dadd_rn(r.wsum, o.wsum);
+}
+
+__device__ __forceinline__ void acc_add(ZoneAcc *z, unsigned long long cnt, unsigned long long area,
+                                        unsigned long long kmin, unsigned long long kmax, double sum, double wsum) {
+    atomicAdd(&z->count, cnt);
+    atomicAdd(&z->area, area);
+    atomicMin(&z->kmin, kmin);
+    atomicMax(&z->kmax, kmax);
+    atomicAdd(&z->sum, sum);
+    atomicAdd(&z->wsum, wsum);
+}
+
+template <int S, int KIND>
 __device__ __forceinline__ void flush_run(const StatsRun &r, ZoneAcc *tab) {
     if (r.cnt == 0) return;
-    ZoneAcc *z = tab + r.zone;
-    atomicAdd(&z->count, (unsigned long long)r.cnt);
-    atomicAdd(&z->area, r.area);
-    atomicMin(&z->kmin, dkey(r.vmin));
-    atomicMax(&z->kmax, dkey(r.vmax));
-    atomicAdd(&z->sum, r.sum);
-    atomicAdd(&z->wsum, r.wsum);
+    acc_add(tab + r.zone, r.cnt, r.area, dkey(key_value<S, KIND>(r.kmin)), dkey(key_value<S, KIND>(r.kmax)), r.sum,
+            r.wsum);
+}
+
+// Full-warp reductions (every lane gets the result).
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+__device__ __forceinline__ double warp_sum_f64(double x) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x = __dadd_rn(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// Adds the runs of the lanes with `take` set (all of one zone) into zone `zone` of `tab`: one warp
+// reduction per field, the atomics by lane `writer`.  Every lane of the warp calls it.
+template <int S, int KIND>
+__device__ __forceinline__ void warp_flush(const StatsRun &r, bool take, uint32_t zone, int writer, ZoneAcc *tab) {
+    const bool t = take && r.cnt;
+    const unsigned long long cnt = warp_sum_u64(t ? r.cnt : 0u);
+    if (cnt == 0) return;  // uniform
+    const unsigned long long area = warp_sum_u64(t ? r.area : 0ull);
+    const uint32_t kmin = __reduce_min_sync(0xffffffffu, t ? r.kmin : 0xFFFFFFFFu);
+    const uint32_t kmax = __reduce_max_sync(0xffffffffu, t ? r.kmax : 0u);
+    const double sum = warp_sum_f64(t ? r.sum : 0.0);
+    const double wsum = warp_sum_f64(t ? r.wsum : 0.0);
+    if ((int)(threadIdx.x & 31) == writer)
+        acc_add(tab + zone, cnt, area, dkey(key_value<S, KIND>(kmin)), dkey(key_value<S, KIND>(kmax)), sum, wsum);
 }
 
 struct StatsArgs {
@@ -366,34 +474,38 @@ struct StatsArgs {
     ZoneAcc *out;
 };
 
-template <int S, int KIND>
-__device__ __forceinline__ double value_of(uint32_t bits) {
-    if (KIND == kKindFloat) return (double)to_float<S>(bits);
-    if (KIND == kKindSigned) return (double)sext<S>(bits);
-    return (double)bits;
-}
-
-// Four consecutive S-byte values starting at texel t (t a multiple of 4).
+// Sixteen consecutive S-byte values starting at texel t (t a multiple of 16).
 template <int S>
-__device__ __forceinline__ void load4(const void *data, int64_t t, uint32_t (&v)[4]) {
-    if (S == 1) {
-        const uint32_t w = __ldcs(reinterpret_cast<const unsigned int *>(static_cast<const uint8_t *>(data) + t));
-        for (int k = 0; k < 4; ++k) v[k] = (w >> (8 * k)) & 0xFFu;
-    } else if (S == 2) {
-        const uint2 w = __ldcs(reinterpret_cast<const uint2 *>(static_cast<const uint16_t *>(data) + t));
-        v[0] = w.x & 0xFFFFu;
-        v[1] = w.x >> 16;
-        v[2] = w.y & 0xFFFFu;
-        v[3] = w.y >> 16;
-    } else {
-        const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(static_cast<const uint32_t *>(data) + t));
-        v[0] = w.x;
-        v[1] = w.y;
-        v[2] = w.z;
-        v[3] = w.w;
+__device__ __forceinline__ void load16(const void *data, int64_t t, uint32_t (&v)[16]) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const uint8_t *>(data) + t * S);
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        const uint4 w = __ldcs(p + q);
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (S == 4) {
+                v[4 * q + j] = ws[j];
+            } else if (S == 2) {
+                v[8 * q + 2 * j] = ws[j] & 0xFFFFu;
+                v[8 * q + 2 * j + 1] = ws[j] >> 16;
+            } else {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) v[16 * q + 4 * j + b] = (ws[j] >> (8 * b)) & 0xFFu;
+            }
+        }
     }
 }
 
+// Zonal statistics.  A warp takes a contiguous range of iterations; in one iteration lane l takes
+// the 16-texel chunk 32 it + l.  Each lane sums its chunk into a lane run (flushed by itself with
+// atomics only if the zone changes inside the chunk): count, area, min / max as integer keys of
+// the value's own type, and per stretch of texels of one triangle the value sum (exact in int64 for
+// integer and float16 layers, in double for float32) which is closed as sum += s, wsum += w * s.
+// While every lane's chunk run has the warp's current zone, the lane merges it into its share of
+// the warp run, in registers; when an iteration brings another zone, the warp run is reduced
+// across the warp and written by one lane, the iteration's chunk runs are reduced zone by zone,
+// and the zone of lane 31 becomes the warp's zone.
 template <int S, int KIND, int ZB, bool SMEM>
 __global__ void __launch_bounds__(kThreads) k_num_stats(StatsArgs p) {
     extern __shared__ ZoneAcc sh_zone[];
@@ -409,74 +521,123 @@ __global__ void __launch_bounds__(kThreads) k_num_stats(StatsArgs p) {
         }
         __syncthreads();
     }
-    StatsRun run;
-    run.zone = 0;
-    run.cnt = 0;
+    StatsRun run, wrun;
+    run.zone = kNone;
+    run_reset(run);
+    run_reset(wrun);
+    TriSum<S, KIND> ts_acc;
+    ts_acc.reset();
     uint32_t last_t = kNone;
     unsigned long long last_w = 0;
+    bool open = false;  // ts_acc holds texels of triangle last_t in zone run.zone
+    auto close_tri = [&]() {
+        if (!open) return;
+        const double sv = ts_acc.value();
+        run.sum = __dadd_rn(run.sum, sv);
+        run.wsum = __dadd_rn(run.wsum, __dmul_rn((double)last_w, sv));
+        ts_acc.reset();
+        open = false;
+    };
     auto visit = [&](uint32_t z, uint32_t t, uint32_t bits, bool valid) {
         if (!valid || t == kNone || z >= p.n_labels) return;
-        double v = value_of<S, KIND>(bits);
-        if (v != v) return;  // NaN
-        if (v == 0.0) v = 0.0;
+        uint32_t fb = bits;  // float layers: the float32 bits of the value
+        if (KIND == kKindFloat) {
+            if (S == 2) fb = __float_as_uint(__half2float(__ushort_as_half((unsigned short)bits)));
+            if ((fb & 0x7FFFFFFFu) > 0x7F800000u) return;  // NaN
+            if ((fb & 0x7FFFFFFFu) == 0) fb = 0;           // -0 counts as +0
+        }
+        if (z != run.zone && run.cnt) {
+            close_tri();
+            flush_run<S, KIND>(run, tab);
+            run_reset(run);
+        }
+        run.zone = z;
         if (t != last_t) {
+            close_tri();
             last_t = t;
             last_w = __ldg(p.area_w + t);
         }
-        const double wv = __dmul_rn((double)last_w, v);
-        if (z != run.zone || run.cnt == 0) {
-            flush_run(run, tab);
-            run.zone = z;
-            run.cnt = 0;
-            run.area = 0;
-            run.vmin = v;
-            run.vmax = v;
-            run.sum = 0.0;
-            run.wsum = 0.0;
-        }
+        open = true;
         run.cnt += 1;
         run.area += last_w;
-        run.vmin = v < run.vmin ? v : run.vmin;
-        run.vmax = v > run.vmax ? v : run.vmax;
-        run.sum = __dadd_rn(run.sum, v);
-        run.wsum = __dadd_rn(run.wsum, wv);
+        const uint32_t k = vkey<S, KIND>(fb);
+        run.kmin = min(run.kmin, k);
+        run.kmax = max(run.kmax, k);
+        if (KIND == kKindFloat && S == 4) ts_acc.d = __dadd_rn(ts_acc.d, f32_bits_to_double(fb));
+        else if (KIND == kKindFloat && (fb & 0x7FFFFFFFu) == 0x7F800000u) ts_acc.d = __dadd_rn(ts_acc.d, (double)__uint_as_float(fb));
+        else if (KIND == kKindFloat) ts_acc.i += __float2ll_rn(__fmul_rn(__uint_as_float(fb), 0x1p24f));  // exact
+        else if (KIND == kKindSigned) ts_acc.i += sext<S>(bits);
+        else ts_acc.i += bits;
     };
-    // a warp takes 512 texels per step: lane l holds texels 4l + 128k .. + 3, k = 0..3
-    constexpr int64_t kChunk = 512;
     const int lane = threadIdx.x & 31;
-    const int64_t gthread = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n_chunks = p.n_texels / 16;
     const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t n_chunks = p.n_texels / kChunk;
-    for (int64_t c = gthread >> 5; c < n_chunks; c += n_warps) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int64_t t = c * kChunk + 128 * k + 4 * lane;
-            const uint4 T = __ldcs(reinterpret_cast<const uint4 *>(p.tri + t));
-            uint32_t v[4];
-            load4<S>(p.data, t, v);
-            uint32_t z[4] = {0u, 0u, 0u, 0u};
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_iter = (n_chunks + 31) / 32;
+    const int64_t per = (n_iter + n_warps - 1) / n_warps;
+    const int64_t it0 = warp * per, it1 = min(n_iter, it0 + per);
+    uint32_t wzone = kNone;
+    for (int64_t it = it0; it < it1; ++it) {
+        const int64_t c = it * 32 + lane;
+        if (c < n_chunks) {
+            const int64_t t = 16 * c;
+            uint32_t v[16];
+            load16<S>(p.data, t, v);
+            const uint4 *tp = reinterpret_cast<const uint4 *>(p.tri + t);
+            const uint4 T0 = __ldcs(tp), T1 = __ldcs(tp + 1), T2 = __ldcs(tp + 2), T3 = __ldcs(tp + 3);
+            const uint32_t ts[16] = {T0.x, T0.y, T0.z, T0.w, T1.x, T1.y, T1.z, T1.w,
+                                     T2.x, T2.y, T2.z, T2.w, T3.x, T3.y, T3.z, T3.w};
+            uint32_t z[16];
             if (p.zones) {
-                if (ZB == 1) {
-                    const uint32_t w = __ldcs(reinterpret_cast<const unsigned int *>(static_cast<const uint8_t *>(p.zones) + t));
-                    for (int j = 0; j < 4; ++j) z[j] = (w >> (8 * j)) & 0xFFu;
-                } else {
-                    const uint2 w = __ldcs(reinterpret_cast<const uint2 *>(static_cast<const uint16_t *>(p.zones) + t));
-                    z[0] = w.x & 0xFFFFu;
-                    z[1] = w.x >> 16;
-                    z[2] = w.y & 0xFFFFu;
-                    z[3] = w.y >> 16;
+                const uint4 *zp = reinterpret_cast<const uint4 *>(static_cast<const uint8_t *>(p.zones) + t * ZB);
+#pragma unroll
+                for (int q = 0; q < ZB; ++q) {
+                    const uint4 w = __ldcs(zp + q);
+                    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (ZB == 1) {
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) z[4 * j + b] = (ws[j] >> (8 * b)) & 0xFFu;
+                        } else {
+                            z[8 * q + 2 * j] = ws[j] & 0xFFFFu;
+                            z[8 * q + 2 * j + 1] = ws[j] >> 16;
+                        }
+                    }
                 }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) z[k] = 0;
             }
             const uint32_t word = (uint32_t)(t >> 5);
-            const uint32_t valid = ((__ldg(p.mask + word) & __ldg(p.cover + word)) >> (t & 31)) & 0xFu;
-            visit(z[0], T.x, v[0], valid & 1u);
-            visit(z[1], T.y, v[1], valid & 2u);
-            visit(z[2], T.z, v[2], valid & 4u);
-            visit(z[3], T.w, v[3], valid & 8u);
+            const uint32_t valid = (__ldg(p.mask + word) & __ldg(p.cover + word)) >> (t & 31);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) visit(z[k], ts[k], v[k], (valid >> k) & 1u);
+            close_tri();
         }
+        const uint32_t key = run.cnt ? run.zone : kNone;
+        if (__all_sync(0xffffffffu, key == wzone || key == kNone)) {
+            if (run.cnt) run_merge(wrun, run);
+        } else {
+            warp_flush<S, KIND>(wrun, true, wzone, 0, tab);
+            run_reset(wrun);
+            // this iteration's chunk runs, zone by zone
+            unsigned left = __ballot_sync(0xffffffffu, key != kNone);
+            while (left) {
+                const int leader = __ffs(left) - 1;
+                const uint32_t zk = __shfl_sync(0xffffffffu, key, leader);
+                const bool mine = key == zk;
+                warp_flush<S, KIND>(run, mine, zk, leader, tab);
+                left &= ~__ballot_sync(0xffffffffu, mine);
+            }
+            wzone = __shfl_sync(0xffffffffu, key, 31);
+        }
+        run_reset(run);
     }
-    // tail texels (n_texels % 512), one per thread
-    for (int64_t t = n_chunks * kChunk + gthread; t < p.n_texels; t += (int64_t)gridDim.x * blockDim.x) {
+    warp_flush<S, KIND>(wrun, true, wzone, 0, tab);
+    // tail texels (n_texels % 16), one per thread
+    for (int64_t t = n_chunks * 16 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < p.n_texels;
+         t += (int64_t)gridDim.x * blockDim.x) {
         uint32_t bits, z = 0;
         if (S == 1) bits = static_cast<const uint8_t *>(p.data)[t];
         else if (S == 2) bits = static_cast<const uint16_t *>(p.data)[t];
@@ -486,19 +647,14 @@ __global__ void __launch_bounds__(kThreads) k_num_stats(StatsArgs p) {
         const bool valid = ((p.mask[word] & p.cover[word]) >> (t & 31)) & 1u;
         visit(z, p.tri[t], bits, valid);
     }
-    flush_run(run, tab);
+    close_tri();
+    flush_run<S, KIND>(run, tab);
     if (SMEM) {
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < p.n_labels; i += blockDim.x) {
             const ZoneAcc &a = sh_zone[i];
             if (a.count == 0) continue;
-            ZoneAcc *o = p.out + i;
-            atomicAdd(&o->count, a.count);
-            atomicAdd(&o->area, a.area);
-            atomicMin(&o->kmin, a.kmin);
-            atomicMax(&o->kmax, a.kmax);
-            atomicAdd(&o->sum, a.sum);
-            atomicAdd(&o->wsum, a.wsum);
+            acc_add(p.out + i, a.count, a.area, a.kmin, a.kmax, a.sum, a.wsum);
         }
     }
 }
@@ -525,9 +681,9 @@ void launch_stats_smem(const StatsArgs &p, size_t shb, cudaStream_t st) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, shb) != cudaSuccess || per_sm < 1)
         per_sm = 1;
-    const int64_t warps = p.n_texels / 512 + 1;
-    const int grid = (int)std::max<int64_t>(
-        1, std::min<int64_t>((int64_t)sm_count() * per_sm, (warps + kThreads / 32 - 1) / (kThreads / 32)));
+    const int64_t threads = p.n_texels / 16 + 1;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * per_sm,
+                                                                 (threads + kThreads - 1) / kThreads));
     kernel<<<grid, kThreads, shb, st>>>(p);
 }
 
