@@ -327,10 +327,10 @@ def num_select_sphere(atlas: Atlas, data, mask, strokes):
 
 
 def num_select_lasso(atlas: Atlas, data, mask, m, dmap, poly, value_bits_, flags=0, bias=2.0 ** -10):
-    """A lasso on a numeric layer: the texels select_lasso selects get the value (or are erased).
-    Returns (hits, ambiguous mask)."""
+    """A lasso on a numeric layer: the texels select_lasso_2d selects or pads (flags & 0xFF) get the
+    value (or are erased with ERASE).  Returns (hits, ambiguous mask)."""
     sel = np.zeros(atlas.tri.shape, np.uint8)
-    h, amb = select_lasso(atlas, sel, m, dmap, poly, 1, bias)
+    h, _, amb = select_lasso_2d(atlas, sel, m, dmap, poly, 1, bias, flags & 0xFF)
     _num_edit(data, mask, sel == 1, value_bits_, flags)
     return h, amb
 
@@ -378,3 +378,21 @@ def num_stats(atlas: Atlas, ntype, data, mask, zones, n_labels):
                              C.c_uint32(n_labels), _p(r["count"]), _p(r["area"]), _p(r["vmin"]), _p(r["vmax"]),
                              _p(r["sum"]), _p(r["wsum"])), "num_stats")
     return r
+
+
+def select_lasso_2d(atlas: Atlas, layer, m, dmap, poly, label, bias=2.0 ** -10, flags=0):
+    """select_lasso on the whole texture with texture padding (flags = radius | thickness << 4).
+    Returns (hits, padded, ambiguous mask)."""
+    assert atlas.y0 == 0 and atlas.y1 == atlas.H and layer.shape == atlas.tri.shape
+    m = np.ascontiguousarray(m, dtype=np.float32)
+    poly = np.ascontiguousarray(poly, dtype=np.float32)
+    Hs, Ws = dmap.shape
+    hits = np.zeros(1, np.uint64)
+    padded = np.zeros(1, np.uint64)
+    amb = np.zeros(atlas.tri.shape, np.uint8)
+    _chk(lib().orc_select_lasso_2d(C.c_int32(atlas.W), C.c_int32(atlas.H), _p(atlas.px), _p(atlas.py), _p(atlas.pz),
+                                   _p(atlas.tri), _p(layer), C.c_int(layer.itemsize), _p(m), C.c_int32(Ws),
+                                   C.c_int32(Hs), _p(np.ascontiguousarray(dmap, np.float32)), _p(poly),
+                                   C.c_int32(poly.shape[0]), C.c_uint32(int(label)), C.c_float(bias),
+                                   C.c_uint32(int(flags)), _p(hits), _p(padded), _p(amb)), "select_lasso_2d")
+    return int(hits[0]), int(padded[0]), amb

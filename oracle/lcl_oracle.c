@@ -564,6 +564,57 @@ static double seg_dist(double px, double py, double ax, double ay, double bx, do
     return sqrt(dx * dx + dy * dy);
 }
 
+typedef struct {
+    const int32_t *px, *py, *pz;
+    const uint32_t *tri;
+    const float *m;
+    int32_t Ws, Hs;
+    const float *depth;
+    const float *poly;
+    int32_t nv;
+    float bias;
+} lasso_ctx;
+
+/* The lasso test of texel l: returns 1 if selected; *amb (if given) = ambiguous. */
+static int lasso_eval(const lasso_ctx *t, int64_t l, int *amb)
+{
+    if (amb) *amb = 0;
+    if (t->tri[l] == ORC_NONE) return 0;
+    float c[4];
+    clip_of(t->m, t->px[l], t->py[l], t->pz[l], c);
+    if (!(c[3] > 0.0f)) return 0;
+    float zn = c[2] / c[3];
+    if (!(zn >= 0.0f && zn <= 1.0f)) return 0;
+    float xs = screen_of(c[0] / c[3], t->Ws), ys = screen_of(c[1] / c[3], t->Hs);
+    if (!(xs >= 0.0f && xs < (float)t->Ws && ys >= 0.0f && ys < (float)t->Hs)) return 0;
+    const float *poly = t->poly;
+    int32_t nv = t->nv;
+    int inside = 0;
+    for (int32_t e = 0; e < nv; ++e) {
+        float ax = poly[2 * e], ay = poly[2 * e + 1];
+        float bx = poly[2 * ((e + 1) % nv)], by = poly[2 * ((e + 1) % nv) + 1];
+        if ((ay > ys) != (by > ys)) {
+            float xi = (bx - ax) * (ys - ay) / (by - ay) + ax;
+            if (xs < xi) inside = !inside;
+        }
+    }
+    int32_t ix = (int32_t)xs, iy = (int32_t)ys; /* xs, ys >= 0: truncation is floor */
+    float dref = t->depth[(int64_t)iy * t->Ws + ix];
+    float lim = dref + t->bias;
+    int visible = zn <= lim;
+    if (amb) {
+        double me = INFINITY;
+        for (int32_t e = 0; e < nv; ++e) {
+            double d = seg_dist(xs, ys, poly[2 * e], poly[2 * e + 1], poly[2 * ((e + 1) % nv)],
+                                poly[2 * ((e + 1) % nv) + 1]);
+            if (d < me) me = d;
+        }
+        double md = fabs((double)zn - ((double)dref + (double)t->bias));
+        *amb = me < 1e-4 || md < 1e-6;
+    }
+    return inside && visible;
+}
+
 int orc_select_lasso(int64_t n_texels, const int32_t *px, const int32_t *py, const int32_t *pz,
                      const uint32_t *tri, void *layer, int dtype_bytes, const float m[16], int32_t Ws, int32_t Hs,
                      const float *depth, const float *poly, int32_t nv, uint32_t label, float bias, uint64_t *hits,
@@ -572,46 +623,93 @@ int orc_select_lasso(int64_t n_texels, const int32_t *px, const int32_t *py, con
     if (dtype_bytes != 1 && dtype_bytes != 2) return ORC_EINVAL;
     if (nv < 3 || nv > 64) return ORC_EUNSUP;
     if (label >= (1u << (8 * dtype_bytes))) return ORC_EINVAL;
+    lasso_ctx t = {px, py, pz, tri, m, Ws, Hs, depth, poly, nv, bias};
     uint64_t h = 0;
     for (int64_t l = 0; l < n_texels; ++l) {
-        if (ambiguous) ambiguous[l] = 0;
-        if (tri[l] == ORC_NONE) continue;
-        float c[4];
-        clip_of(m, px[l], py[l], pz[l], c);
-        if (!(c[3] > 0.0f)) continue;
-        float zn = c[2] / c[3];
-        if (!(zn >= 0.0f && zn <= 1.0f)) continue;
-        float xs = screen_of(c[0] / c[3], Ws), ys = screen_of(c[1] / c[3], Hs);
-        if (!(xs >= 0.0f && xs < (float)Ws && ys >= 0.0f && ys < (float)Hs)) continue;
-        int inside = 0;
-        for (int32_t e = 0; e < nv; ++e) {
-            float ax = poly[2 * e], ay = poly[2 * e + 1];
-            float bx = poly[2 * ((e + 1) % nv)], by = poly[2 * ((e + 1) % nv) + 1];
-            if ((ay > ys) != (by > ys)) {
-                float xi = (bx - ax) * (ys - ay) / (by - ay) + ax;
-                if (xs < xi) inside = !inside;
-            }
-        }
-        int32_t ix = (int32_t)xs, iy = (int32_t)ys; /* xs, ys >= 0: truncation is floor */
-        float dref = depth[(int64_t)iy * Ws + ix];
-        float lim = dref + bias;
-        int visible = zn <= lim;
-        if (inside && visible) {
+        int amb = 0;
+        if (lasso_eval(&t, l, ambiguous ? &amb : NULL)) {
             store_label(layer, dtype_bytes, l, label);
             ++h;
         }
-        if (ambiguous) {
-            double me = INFINITY;
-            for (int32_t e = 0; e < nv; ++e) {
-                double d = seg_dist(xs, ys, poly[2 * e], poly[2 * e + 1], poly[2 * ((e + 1) % nv)],
-                                    poly[2 * ((e + 1) % nv) + 1]);
-                if (d < me) me = d;
-            }
-            double md = fabs((double)zn - ((double)dref + (double)bias));
-            if (me < 1e-4 || md < 1e-6) ambiguous[l] = 1;
-        }
+        if (ambiguous) ambiguous[l] = (uint8_t)amb;
     }
     if (hits) *hits = h;
+    return ORC_OK;
+}
+
+/* Texture padding (Section 4.3.2) of one edit whose selection is `sel` (0/1 per texel, whole
+ * texture W x H), as for sphere strokes: uncovered texels within `thick` of a covered texel and
+ * within `rad` of a selected texel (square kernels) get `label`.  A padded texel is ambiguous
+ * (amb, in place) if a texel within the kernel radius is.  Returns the number of padded texels. */
+static uint64_t pad_selection(int32_t W, int32_t H, const uint32_t *tri, const uint8_t *sel, uint8_t *amb,
+                              uint32_t rad, uint32_t thick, void *layer, int dtype_bytes, uint32_t label)
+{
+    uint64_t np = 0;
+    if (rad == 0) return 0;
+    int32_t reach = (int32_t)(rad > thick ? rad : thick);
+    for (int32_t y = 0; y < H; ++y)
+        for (int32_t x = 0; x < W; ++x) {
+            int64_t l = (int64_t)y * W + x;
+            if (tri[l] != ORC_NONE) continue;
+            int outline = 0, near = 0, near_amb = 0;
+            for (int32_t dy = -reach; dy <= reach; ++dy)
+                for (int32_t dx = -reach; dx <= reach; ++dx) {
+                    int32_t yy = y + dy, xx = x + dx;
+                    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                    int64_t q = (int64_t)yy * W + xx;
+                    if (tri[q] == ORC_NONE) continue;
+                    int32_t ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy;
+                    if (ax <= (int32_t)thick && ay <= (int32_t)thick) outline = 1;
+                    if (ax <= (int32_t)rad && ay <= (int32_t)rad) {
+                        if (sel[q]) near = 1;
+                        if (amb[q]) near_amb = 1;
+                    }
+                }
+            if (outline && near) {
+                store_label(layer, dtype_bytes, l, label);
+                ++np;
+            }
+            if (outline && near_amb) amb[l] = 1;
+        }
+    return np;
+}
+
+/* A lasso with texture padding (flags = radius | thickness << 4, both at most 8): the selection of
+ * orc_select_lasso, then pad_selection.  Whole texture (W x H) only. */
+int orc_select_lasso_2d(int32_t W, int32_t H, const int32_t *px, const int32_t *py, const int32_t *pz,
+                        const uint32_t *tri, void *layer, int dtype_bytes, const float m[16], int32_t Ws, int32_t Hs,
+                        const float *depth, const float *poly, int32_t nv, uint32_t label, float bias, uint32_t flags,
+                        uint64_t *hits, uint64_t *padded, uint8_t *ambiguous)
+{
+    if (dtype_bytes != 1 && dtype_bytes != 2) return ORC_EINVAL;
+    if (nv < 3 || nv > 64) return ORC_EUNSUP;
+    if (label >= (1u << (8 * dtype_bytes))) return ORC_EINVAL;
+    uint32_t rad = flags & 15u, thick = (flags >> 4) & 15u;
+    if ((flags & ~0xFFu) || rad > 8 || thick > 8) return ORC_EINVAL;
+    lasso_ctx t = {px, py, pz, tri, m, Ws, Hs, depth, poly, nv, bias};
+    int64_t n = (int64_t)W * H;
+    uint8_t *sel = (uint8_t *)calloc((size_t)n, 1), *amb = (uint8_t *)calloc((size_t)n, 1);
+    if (!sel || !amb) {
+        free(sel);
+        free(amb);
+        return ORC_EINVAL;
+    }
+    uint64_t h = 0;
+    for (int64_t l = 0; l < n; ++l) {
+        int a = 0;
+        sel[l] = (uint8_t)lasso_eval(&t, l, &a);
+        amb[l] = (uint8_t)a;
+        if (sel[l]) {
+            store_label(layer, dtype_bytes, l, label);
+            ++h;
+        }
+    }
+    uint64_t np = pad_selection(W, H, tri, sel, amb, rad, thick, layer, dtype_bytes, label);
+    if (ambiguous) memcpy(ambiguous, amb, (size_t)n);
+    free(sel);
+    free(amb);
+    if (hits) *hits = h;
+    if (padded) *padded = np;
     return ORC_OK;
 }
 

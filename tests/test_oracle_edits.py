@@ -346,3 +346,44 @@ def test_texture_padding_off_and_flag_checks():
     r["flags"] = oracle.pad_flags(1, 1)
     with pytest.raises(oracle.OracleError):       # the flat form has no texture layout for padding
         oracle.select_sphere(a, np.zeros(a.tri.shape, np.uint8), r)
+
+
+@pytest.mark.parametrize("rad,thick", [(1, 1), (2, 1), (3, 4), (8, 8), (0, 5)])
+def test_lasso_padding_matches_dilations(rad, thick):
+    """Texture padding of a lasso edit (Section 4.3.2, read as for sphere strokes): uncovered texels
+    within `thickness` of a covered texel and within `radius` of a selected texel get the label --
+    square-kernel dilations with scipy; radius 0 pads nothing; the selection itself is the plain
+    lasso's, and padded texels next to an ambiguous one are flagged."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    m = synth.vessel_charts(60, 30, 12, 6, 96, seed=2)
+    a = oracle.Atlas(m, 96, 96, tile=16)
+    Ws, Hs = 64, 48
+    cam = synth.orbit_camera(m, Ws, Hs, np.random.default_rng(9))
+    M = oracle.camera_mq(cam.vp, a.mn, a.S)
+    dmap = oracle.depth(m, a.mn, a.S, M, Ws, Hs)
+    poly = synth.star_lasso((Ws / 2, Hs / 2), 14, 0.45 * Ws, np.random.default_rng(4))
+    plain = np.zeros(a.tri.shape, np.uint8)
+    h0, amb0 = oracle.select_lasso(a, plain, M, dmap, poly, 4, BIAS)
+    sel = plain == 4
+    lay = np.zeros(a.tri.shape, np.uint8)
+    h, npad, amb = oracle.select_lasso_2d(a, lay, M, dmap, poly, 4, BIAS, oracle.pad_flags(rad, thick))
+    cov = a.covered()
+    if rad == 0:
+        exp_pad = np.zeros_like(cov)
+    else:
+        outline = ~cov & ndimage.maximum_filter(cov, size=2 * thick + 1, mode="constant")
+        exp_pad = outline & ndimage.maximum_filter(sel, size=2 * rad + 1, mode="constant")
+        near_amb = outline & ndimage.maximum_filter(amb0.astype(bool), size=2 * rad + 1, mode="constant")
+        assert np.array_equal(amb.astype(bool)[~cov], near_amb[~cov])
+    assert h == h0 and np.array_equal(amb[cov], amb0[cov])
+    assert np.array_equal(lay == 4, sel | exp_pad) and npad == exp_pad.sum()
+    assert h0 > 50 and (rad == 0 or npad > 0)
+
+
+def test_lasso_padding_rejects_bad_flags():
+    m, a, M, dmap = _lasso_setup(0)
+    layer = np.zeros(a.tri.shape, np.uint8)
+    poly = np.float32([[1, 1], [20, 2], [10, 20]])
+    for f in (9, 9 << 4, 1 << 8):
+        with pytest.raises(oracle.OracleError):
+            oracle.select_lasso_2d(a, layer, M, dmap, poly, 1, BIAS, f)
