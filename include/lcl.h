@@ -235,10 +235,15 @@ lcl_status lcl_depth_render(const lcl_mesh *mesh, const lcl_atlas *atlas, const 
  * x < (b.x - a.x) * (y - a.y) / (b.y - a.y) + a.x, FP32 in that order); visible iff
  * z <= depth[floor(y)][floor(x)] + bias (Fig. 3a, the depth test's small bias).  Selected texels get
  * `label`.  poly_xy: host, n_vertices (3..64) x 2 float32 screen pixels.  depth: device,
- * the map of the same camera.  hits_out: device, one uint64 (nullable). */
+ * the map of the same camera.  flags: texture padding (Section 4.3.2) as for sphere strokes,
+ * radius = bits 0-3, outline thickness = bits 4-7, both <= 8, other bits 0 (0 = none): uncovered
+ * texels within the thickness of a covered texel and within the radius of a selected texel (square
+ * kernels) get `label` too.  hits_out: device, one uint64 (nullable), selected texels (padded
+ * texels not counted). */
 lcl_status lcl_select_lasso(const lcl_atlas *atlas, void *layer, lcl_dtype dtype, const lcl_camera *camera,
                             const float *depth, const float *poly_xy, int32_t n_vertices, uint32_t label,
-                            float bias, uint64_t *hits_out, void *workspace, size_t ws_bytes, lcl_stream stream);
+                            uint32_t flags, float bias, uint64_t *hits_out, void *workspace, size_t ws_bytes,
+                            lcl_stream stream);
 
 /* The paper's editing tool (Section 4.3.1, Fig. 3): a tool window of tw x th pixels centred on the
  * tool position (px, py) is mapped by projective texturing onto the tool's shape texture (the
@@ -303,7 +308,7 @@ typedef struct {
     int32_t n_vertices;
     uint32_t label;
     float bias;
-    int32_t _pad;
+    uint32_t flags; /* texture padding as for lcl_select_lasso (0 = none) */
 } lcl_batch_lasso;
 
 /* Capacity of a batch workspace: every batch run on it has at most `models` models, `strokes`
@@ -339,7 +344,7 @@ size_t lcl_batch_staging_bytes(const lcl_batch_limits *limits);
  * the stream has passed it.  No kernel runs.  Models must be distinct layers (two models writing
  * one layer race); depth maps must be rendered before the batch is launched.
  * Errors: LCL_ERR_INVALID_ARG (bad descriptors, counts above the limits), LCL_ERR_UNSUPPORTED (more
- * than LCL_BATCH_MAX_STROKES strokes for a model, padded sphere strokes, lassos outside 3..64
+ * than LCL_BATCH_MAX_STROKES strokes for a model, lassos outside 3..64
  * vertices), LCL_ERR_OUT_OF_MEMORY (workspace or staging smaller than required), LCL_ERR_CUDA. */
 lcl_status lcl_batch_upload(const lcl_batch_limits *limits, const lcl_batch_model *models, int32_t n_models,
                             const lcl_batch_stroke *strokes, int32_t n_strokes, const lcl_batch_lasso *lassos,
@@ -428,8 +433,8 @@ typedef struct {
 lcl_status lcl_numeric_sphere(const lcl_atlas *atlas, const lcl_numeric_layer *layer, const lcl_sphere *strokes,
                               int32_t n, uint64_t *hits_out, void *workspace, size_t ws_bytes, lcl_stream stream);
 
-/* A lasso on a numeric layer: the texels lcl_select_lasso would select get `value` and a set mask
- * bit (flags = LCL_ERASE: 0 and a clear bit; otherwise flags = 0). */
+/* A lasso on a numeric layer: the texels lcl_select_lasso would select or pad (flags bits 0-7) get
+ * `value` and a set mask bit (with LCL_ERASE in flags: 0 and a clear bit). */
 lcl_status lcl_numeric_lasso(const lcl_atlas *atlas, const lcl_numeric_layer *layer, const lcl_camera *camera,
                              const float *depth, const float *poly_xy, int32_t n_vertices, uint32_t value,
                              uint32_t flags, float bias, uint64_t *hits_out, void *workspace, size_t ws_bytes,

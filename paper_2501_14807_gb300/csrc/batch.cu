@@ -13,7 +13,10 @@
 //                  from the newest down: the first stroke that selects a texel is the last one
 //                  sequential application would have written there, so the texel is final and
 //                  the thread stops once its four texels are final (or no stroke is left); each
-//                  label word is written once.
+//                  label word is written once.  Texture padding (Section 4.3.2) writes only
+//                  uncovered texels, so for those the masked padded strokes are evaluated the
+//                  same way (newest first, on the neighbours' positions), and a padded stroke's
+//                  cull counts a tile whose 3 x 3 neighbourhood it may reach.
 // Each texel belongs to one unit and one thread, so no two threads write a texel, and the label a
 // texel receives is that of the newest stroke selecting it: the result is bit-identical to
 // sequential single-stroke calls.
@@ -47,6 +50,7 @@ struct BStroke {
 struct BLasso {  // built on the device by k_batch_prep
     LassoArg arg;
     const float *depth;
+    int32_t pad_r, pad_t;  // texture padding: kernel radius and outline thickness (0: none)
 };
 
 struct BLassoIn {  // what the host uploads per lasso
@@ -57,7 +61,7 @@ struct BLassoIn {  // what the host uploads per lasso
     int32_t nv;
     uint32_t label;
     float bias;
-    int32_t pad;
+    uint32_t flags;  // texture padding: radius = bits 0-3, thickness = bits 4-7
 };
 
 struct BItem {
@@ -100,6 +104,25 @@ __device__ __forceinline__ bool stroke_may_touch(const BStroke &st, const BLasso
     return box_may_touch(lassos[st.lasso].arg, lo, hi, lassos[st.lasso].depth);
 }
 
+__device__ __forceinline__ bool stroke_pads(const BStroke &st, const BLasso *lassos) {
+    return st.kind == LCL_STROKE_SPHERE ? st.sphere.pad_r > 0 : lassos[st.lasso].pad_r > 0;
+}
+
+// Box (bx, by) of a grid of nx x ny boxes (8 int32 each): can the stroke write a texel in it?  With
+// texture padding a texel may be written because a neighbour within 8 texels (at most one tile,
+// and so one super-tile, away) is selected, so then any box of the 3 x 3 neighbourhood counts.
+__device__ __forceinline__ bool stroke_may_reach(const BStroke &st, const BLasso *lassos, const int32_t *boxes,
+                                                 int32_t nx, int32_t ny, int32_t bx, int32_t by) {
+    const bool pad = stroke_pads(st, lassos);
+    const int32_t r = pad ? 1 : 0;
+    for (int32_t y = max(by - r, 0); y <= min(by + r, ny - 1); ++y)
+        for (int32_t x = max(bx - r, 0); x <= min(bx + r, nx - 1); ++x) {
+            const int4 *b = reinterpret_cast<const int4 *>(boxes + 8 * ((int64_t)y * nx + x));
+            if (stroke_may_touch(st, lassos, b[0], b[1])) return true;
+        }
+    return false;
+}
+
 constexpr int kPrepWarps = kThreads / 32;  // lassos per CTA of k_batch_prep
 static_assert(kBands == 32, "k_batch_prep gives each y-band one lane");
 
@@ -121,6 +144,8 @@ __global__ void __launch_bounds__(kThreads) k_batch_prep(BHdr *hdr, const BLasso
     if (lane == 0) {
         lasso_arg_head(p, L.m, L.w_s, L.h_s, L.poly, L.nv, L.label, L.bias);
         out[j].depth = L.depth;
+        out[j].pad_r = (int32_t)(L.flags & 15u);
+        out[j].pad_t = (int32_t)((L.flags >> 4) & 15u);
     }
     __syncwarp();
     const double bh = lasso_band_height(p);
@@ -155,24 +180,23 @@ __global__ void __launch_bounds__(kThreads) k_batch_cull(const BHdr *__restrict_
         const int32_t sidx = g - M.super0;
         if (threadIdx.x == 0) s_mask = 0ull;
         __syncthreads();
-        const int4 *sb = reinterpret_cast<const int4 *>(a.super_box + 8 * (int64_t)sidx);
-        const int4 slo = sb[0], shi = sb[1];
+        const int32_t sx = sidx % a.supers_x, sy = sidx / a.supers_x;
         // strokes that can reach the super-tile, one thread per stroke (ns <= 64)
-        if (threadIdx.x < (unsigned)M.ns && stroke_may_touch(strokes[M.s0 + threadIdx.x], lassos, slo, shi))
+        if (threadIdx.x < (unsigned)M.ns &&
+            stroke_may_reach(strokes[M.s0 + threadIdx.x], lassos, a.super_box, a.supers_x, a.supers_y, sx, sy))
             atomicOr(&s_mask, 1ull << threadIdx.x);
         __syncthreads();
         const unsigned long long smask = s_mask;
         __syncthreads();
         if (smask == 0ull) continue;  // uniform over the CTA
-        const int32_t tx = (sidx % a.supers_x) * LCL_SUPER + (threadIdx.x % LCL_SUPER);
-        const int32_t ty = (sidx / a.supers_x) * LCL_SUPER + (threadIdx.x / LCL_SUPER);
+        const int32_t tx = sx * LCL_SUPER + (threadIdx.x % LCL_SUPER);
+        const int32_t ty = sy * LCL_SUPER + (threadIdx.x / LCL_SUPER);
         unsigned long long mask = 0ull;
         if (tx < a.tiles_x && ty < a.tiles_y) {
-            const int4 *tb = reinterpret_cast<const int4 *>(a.tile_box + 8 * ((int64_t)ty * a.tiles_x + tx));
-            const int4 lo = tb[0], hi = tb[1];
             for (unsigned long long m = smask; m; m &= m - 1) {
                 const int k = __ffsll((long long)m) - 1;
-                if (stroke_may_touch(strokes[M.s0 + k], lassos, lo, hi)) mask |= 1ull << k;
+                if (stroke_may_reach(strokes[M.s0 + k], lassos, a.tile_box, a.tiles_x, a.tiles_y, tx, ty))
+                    mask |= 1ull << k;
             }
         }
         const bool cand = mask != 0ull;
@@ -221,6 +245,62 @@ __device__ __forceinline__ void store_labels<uint16_t>(uint16_t *layer, int64_t 
     const uint32_t lo = ((m & 1u) ? 0x0000FFFFu : 0u) | ((m & 2u) ? 0xFFFF0000u : 0u);
     const uint32_t hi = ((m & 4u) ? 0x0000FFFFu : 0u) | ((m & 8u) ? 0xFFFF0000u : 0u);
     *p = make_uint2((o.x & ~lo) | (v0 & lo), (o.y & ~hi) | (v1 & hi));
+}
+
+// Does stroke `st` select the covered texel n?
+__device__ __forceinline__ bool stroke_selects(const AtlasDev &a, const BStroke &st, const BLasso *__restrict__ lassos,
+                                               int64_t n, int32_t qx) {
+    if (st.kind == LCL_STROKE_SPHERE) {
+        const int64_t dx = (int64_t)qx - st.sphere.cx, dy = (int64_t)__ldg(a.py + n) - st.sphere.cy;
+        const int64_t dz = (int64_t)__ldg(a.pz + n) - st.sphere.cz;
+        return dx * dx + dy * dy + dz * dz <= st.sphere.r2;
+    }
+    const BLasso &ls = lassos[st.lasso];
+    return lasso_hit(ls.arg, ls.arg, ls.depth, qx, __ldg(a.py + n), __ldg(a.pz + n));
+}
+
+// Texture padding of the uncovered texels `unc` of the quad at l: for each, the masked padded strokes
+// from the newest down; the first whose outline (a covered texel within its thickness) and kernel
+// (a texel it selects within its radius) both hold gives the label.  Returns the texels written.
+__device__ __noinline__ uint32_t pad_texels(const AtlasDev &a, int64_t l, uint32_t unc, unsigned long long mask, int32_t s0,
+                               const BStroke *__restrict__ strokes, const BLasso *__restrict__ lassos,
+                               uint32_t lab[4]) {
+    const int32_t x0 = (int32_t)(l % a.w), y0 = (int32_t)(l / a.w);
+    uint32_t written = 0u;
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+        if (!(unc & (1u << k))) continue;
+        for (unsigned long long m = mask; m; ) {
+            const int si = 63 - __clzll((long long)m);  // newest stroke left
+            m &= ~(1ull << si);
+            const BStroke &st = strokes[s0 + si];
+            const int32_t pr = st.kind == LCL_STROKE_SPHERE ? st.sphere.pad_r : lassos[st.lasso].pad_r;
+            if (pr == 0) continue;
+            const int32_t pt = st.kind == LCL_STROKE_SPHERE ? st.sphere.pad_t : lassos[st.lasso].pad_t;
+            const int32_t reach = max(pr, pt);
+            bool outline = false, near = false;
+            for (int32_t dy = -reach; dy <= reach && !(outline && near); ++dy) {
+                const int32_t yy = y0 + dy;
+                if (yy < 0 || yy >= a.h) continue;
+                for (int32_t dx = -reach; dx <= reach; ++dx) {
+                    const int32_t xx = x0 + k + dx;
+                    if (xx < 0 || xx >= a.w) continue;
+                    const int64_t n = (int64_t)yy * a.w + xx;
+                    const int32_t qx = __ldg(a.px + n);
+                    if (qx == INT32_MIN) continue;
+                    const int32_t ax = abs(dx), ay = abs(dy);
+                    if (ax <= pt && ay <= pt) outline = true;
+                    if (ax <= pr && ay <= pr && !near) near = stroke_selects(a, st, lassos, n, qx);
+                }
+            }
+            if (outline && near) {
+                lab[k] = st.kind == LCL_STROKE_SPHERE ? st.sphere.label : lassos[st.lasso].arg.label;
+                written |= 1u << k;
+                break;
+            }
+        }
+    }
+    return written;
 }
 
 // Quads [q0, q1) of a work item's tile (quad = 4 consecutive texels of a tile row, row-major in
@@ -280,6 +360,16 @@ __device__ __forceinline__ void apply_part(const BModel &M, const BItem &it, int
             }
             hit |= sel;
             open &= ~sel;
+        }
+        // texture padding (Section 4.3.2) of the quad's uncovered texels: the newest padded stroke
+        // that selects a texel within its kernel radius, with a covered texel within its outline
+        // thickness, writes its label there
+        uint32_t unc = 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) unc |= (xs[k] == INT32_MIN ? 1u : 0u) << k;
+        if (unc) {
+            const uint32_t ph = pad_texels(a, l, unc, it.mask, M.s0, strokes, lassos, lab);
+            hit |= ph;
         }
         if (hit) store_labels<L>(layer, l, hit, lab);
     }
@@ -343,10 +433,9 @@ lcl_status check_batch(const lcl_batch_model *models, int32_t n_models, const lc
                 const lcl_sphere &sp = s.sphere;
                 const int32_t lo = -(1 << 22), hi = (1 << 22) + (1 << 21);
                 if (sp.r2 < 0 || sp.label > lab_max || sp.cx < lo || sp.cx > hi || sp.cy < lo || sp.cy > hi ||
-                    sp.cz < lo || sp.cz > hi || (sp.flags & ~0xFFu))
+                    sp.cz < lo || sp.cz > hi || (sp.flags & ~0xFFu) || (sp.flags & 15u) > 8 ||
+                    ((sp.flags >> 4) & 15u) > 8)
                     return fail(LCL_ERR_INVALID_ARG, "batch sphere stroke out of range");
-                if (sp.flags != 0)
-                    return fail(LCL_ERR_UNSUPPORTED, "texture padding is not supported in batched edits");
             } else if (s.kind == LCL_STROKE_LASSO) {
                 if (s.lasso < 0 || s.lasso >= n_lassos) return fail(LCL_ERR_INVALID_ARG, "batch lasso index");
                 if (lassos[s.lasso].label > lab_max) return fail(LCL_ERR_INVALID_ARG, "batch lasso label too wide");
@@ -369,6 +458,8 @@ lcl_status check_batch(const lcl_batch_model *models, int32_t n_models, const lc
         for (int i = 0; i < 2 * L.n_vertices; ++i)
             if (!std::isfinite(L.poly_xy[i])) return fail(LCL_ERR_INVALID_ARG, "batch lasso vertex is not finite");
         if (!std::isfinite(L.bias)) return fail(LCL_ERR_INVALID_ARG, "batch lasso bias is not finite");
+        if ((L.flags & ~0xFFu) || (L.flags & 15u) > 8 || ((L.flags >> 4) & 15u) > 8)
+            return fail(LCL_ERR_INVALID_ARG, "batch lasso flags: padding radius and thickness at most 8");
     }
     if (ns > INT32_MAX || nt > UINT32_MAX) return fail(LCL_ERR_UNSUPPORTED, "batch too large");
     *n_supers = ns;
@@ -520,8 +611,8 @@ lcl_status batch_upload_impl(const lcl_batch_limits *lim, const lcl_batch_model 
         d.sphere.cz = strokes[k].sphere.cz;
         d.sphere.r2 = strokes[k].sphere.r2 > kR2Cap ? kR2Cap : strokes[k].sphere.r2;
         d.sphere.label = strokes[k].sphere.label;
-        d.sphere.pad_r = 0;
-        d.sphere.pad_t = 0;
+        d.sphere.pad_r = (int32_t)(strokes[k].sphere.flags & 15u);
+        d.sphere.pad_t = (int32_t)((strokes[k].sphere.flags >> 4) & 15u);
         bs[k] = d;
     }
     BLassoIn *bl = reinterpret_cast<BLassoIn *>(img + L.lasso_in);
@@ -535,7 +626,7 @@ lcl_status batch_upload_impl(const lcl_batch_limits *lim, const lcl_batch_model 
         d.nv = lassos[j].n_vertices;
         d.label = lassos[j].label;
         d.bias = lassos[j].bias;
-        d.pad = 0;
+        d.flags = lassos[j].flags;
     }
     // the used front of each region (the kernels read no further; the limits may be far larger)
     const size_t part[4][2] = {{0, head},

@@ -339,8 +339,9 @@ lcl_status lcl_depth_render(const lcl_mesh *mesh, const lcl_atlas *atlas, const 
 }
 
 lcl_status lcl_select_lasso(const lcl_atlas *atlas, void *layer, lcl_dtype dtype, const lcl_camera *camera,
-                            const float *depth, const float *poly_xy, int32_t n_vertices, uint32_t label, float bias,
-                            uint64_t *hits_out, void *workspace, size_t ws_bytes, lcl_stream stream) {
+                            const float *depth, const float *poly_xy, int32_t n_vertices, uint32_t label,
+                            uint32_t flags, float bias, uint64_t *hits_out, void *workspace, size_t ws_bytes,
+                            lcl_stream stream) {
     lcl_status s = check_atlas(atlas, true);
     if (s != LCL_OK) return s;
     const int db = dtype_bytes(dtype);
@@ -355,12 +356,14 @@ lcl_status lcl_select_lasso(const lcl_atlas *atlas, void *layer, lcl_dtype dtype
     for (int i = 0; i < 2 * n_vertices; ++i)
         if (!std::isfinite(poly_xy[i])) return fail(LCL_ERR_INVALID_ARG, "polygon vertex is not finite");
     if (label > (db == 1 ? 0xFFu : 0xFFFFu)) return fail(LCL_ERR_INVALID_ARG, "label does not fit the layer dtype");
+    if ((flags & ~0xFFu) || (flags & 15u) > 8 || ((flags >> 4) & 15u) > 8)
+        return fail(LCL_ERR_INVALID_ARG, "lasso flags: padding radius and thickness at most 8, other bits 0");
     if (!std::isfinite(bias)) return fail(LCL_ERR_INVALID_ARG, "bias is not finite");
     if (hits_out && !aligned(hits_out, 8)) return fail(LCL_ERR_INVALID_ARG, "hits_out must be 8-byte aligned");
     if (!workspace || !aligned(workspace, 256)) return fail(LCL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     if (ws_bytes < select_ws_bytes(atlas, 1)) return fail(LCL_ERR_OUT_OF_MEMORY, "workspace smaller than lcl_select_workspace_bytes");
-    return select_lasso_impl(atlas, layer, db, camera, depth, poly_xy, n_vertices, label, bias, hits_out, workspace,
-                             reinterpret_cast<cudaStream_t>(stream));
+    return select_lasso_impl(atlas, layer, db, camera, depth, poly_xy, n_vertices, label, flags, bias, hits_out,
+                             workspace, reinterpret_cast<cudaStream_t>(stream));
 }
 
 lcl_status lcl_select_tool(const lcl_atlas *atlas, void *layer, lcl_dtype dtype, const lcl_camera *camera,
@@ -498,7 +501,8 @@ lcl_status lcl_numeric_lasso(const lcl_atlas *atlas, const lcl_numeric_layer *la
     for (int i = 0; i < 2 * n_vertices; ++i)
         if (!std::isfinite(poly_xy[i])) return fail(LCL_ERR_INVALID_ARG, "polygon vertex is not finite");
     if (value & ~value_mask(layer->type)) return fail(LCL_ERR_INVALID_ARG, "value is wider than the layer type");
-    if (flags & ~LCL_ERASE) return fail(LCL_ERR_INVALID_ARG, "flags must be 0 or LCL_ERASE");
+    if ((flags & ~(0xFFu | LCL_ERASE)) || (flags & 15u) > 8 || ((flags >> 4) & 15u) > 8)
+        return fail(LCL_ERR_INVALID_ARG, "flags: padding radius and thickness at most 8, LCL_ERASE, other bits 0");
     if (!std::isfinite(bias)) return fail(LCL_ERR_INVALID_ARG, "bias is not finite");
     if (hits_out && !aligned(hits_out, 8)) return fail(LCL_ERR_INVALID_ARG, "hits_out must be 8-byte aligned");
     if (!workspace || !aligned(workspace, 256)) return fail(LCL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");

@@ -21,7 +21,7 @@
 // into the other of two candidate lists, and every launch is a programmatic dependent launch, so
 // the next grid is scheduled while the current one drains and waits (griddepcontrol.wait) only
 // for its completion.  Strokes of one call run in stream order, so a later stroke overwrites an
-// earlier one.  Lassos take a cull and an apply launch.  Hit counts are per-warp popcounts
+// earlier one.  Lassos take a cull and an apply launch (two culls with texture padding).  Hit counts are per-warp popcounts
 // reduced per CTA into one 64-bit atomic.
 #include <algorithm>
 #include <cmath>
@@ -262,13 +262,46 @@ __global__ void __launch_bounds__(kThreads) k_dilate_candidates(AtlasDev a, cons
 }
 
 
-template <typename L, bool NUM>
+// Texture padding of the uncovered texels of a quad for a lasso edit (Section 4.3.2, as for
+// spheres): written if a covered texel lies within the outline thickness and a texel the lasso
+// selects within the kernel radius (square kernels).
+__device__ uint32_t lasso_pad_mask(const AtlasDev &a, int64_t l, int4 X, const LassoArg &p, const LassoShared &sh,
+                                   const float *__restrict__ depth, int32_t pad_r, int32_t pad_t) {
+    const int32_t x0 = (int32_t)(l % a.w), y0 = (int32_t)(l / a.w);
+    const int32_t reach = max(pad_r, pad_t);
+    uint32_t m = 0;
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+        const int32_t xk = k == 0 ? X.x : k == 1 ? X.y : k == 2 ? X.z : X.w;  // a select, not a local array
+        if (xk != INT32_MIN) continue;
+        bool outline = false, near = false;
+        for (int32_t dy = -reach; dy <= reach && !(outline && near); ++dy) {
+            const int32_t yy = y0 + dy;
+            if (yy < 0 || yy >= a.h) continue;
+            for (int32_t dx = -reach; dx <= reach; ++dx) {
+                const int32_t xx = x0 + k + dx;
+                if (xx < 0 || xx >= a.w) continue;
+                const int64_t n = (int64_t)yy * a.w + xx;
+                const int32_t qx = __ldg(a.px + n);
+                if (qx == INT32_MIN) continue;
+                const int32_t ax = abs(dx), ay = abs(dy);
+                if (ax <= pad_t && ay <= pad_t) outline = true;
+                if (ax <= pad_r && ay <= pad_r && !near) near = lasso_hit(p, sh, depth, qx, __ldg(a.py + n), __ldg(a.pz + n));
+            }
+        }
+        if (outline && near) m |= 1u << k;
+    }
+    return m;
+}
+
+template <typename L, bool NUM, bool PAD>
 __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restrict__ layer,
                                                           const __grid_constant__ LassoArg p,
                                                           const float *__restrict__ depth,
                                                           const uint32_t *__restrict__ counter,
                                                           const uint32_t *__restrict__ list,
-                                                          unsigned long long *hits, ValMask vm) {
+                                                          unsigned long long *hits, ValMask vm, int32_t pad_r,
+                                                          int32_t pad_t) {
     __shared__ LassoShared sh;
     for (int e = threadIdx.x; e <= p.nv; e += kThreads) {
         sh.vx[e] = p.vx[e];
@@ -295,9 +328,10 @@ __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restr
             m |= lasso_hit(p, sh, depth, X.y, Y.y, Z.y) ? 2u : 0u;
             m |= lasso_hit(p, sh, depth, X.z, Y.z, Z.z) ? 4u : 0u;
             m |= lasso_hit(p, sh, depth, X.w, Y.w, Z.w) ? 8u : 0u;
-            if (m) {
-                store_hits<L>(layer, l, m, p.label);
-                if (NUM) valid_update_atomic(vm, l, m);
+            const uint32_t pm = PAD ? lasso_pad_mask(a, l, X, p, sh, depth, pad_r, pad_t) : 0u;
+            if (m | pm) {
+                store_hits<L>(layer, l, m | pm, p.label);
+                if (NUM) valid_update_atomic(vm, l, m | pm);
                 cnt += __popc(m);
             }
         }
@@ -487,35 +521,46 @@ lcl_status numeric_sphere_impl(const lcl_atlas *atlas, void *data, int data_byte
 }
 
 template <typename L, bool NUM>
-void launch_lasso_apply(const AtlasDev &a, L *layer, const LassoArg &p, const float *depth, const SelWs &w,
-                        unsigned long long *h, ValMask vm, cudaStream_t st) {
-    k_lasso_apply<L, NUM><<<resident_grid(k_lasso_apply<L, NUM>), kThreads, 0, st>>>(a, layer, p, depth, w.counters,
-                                                                                    w.list, h, vm);
+void launch_lasso_apply(bool pad, const AtlasDev &a, L *layer, const LassoArg &p, const float *depth,
+                        const SelWs &w, unsigned long long *h, ValMask vm, int32_t pad_r, int32_t pad_t,
+                        cudaStream_t st) {
+    if (pad)
+        k_lasso_apply<L, NUM, true><<<resident_grid(k_lasso_apply<L, NUM, true>), kThreads, 0, st>>>(
+            a, layer, p, depth, w.counters, w.list, h, vm, pad_r, pad_t);
+    else
+        k_lasso_apply<L, NUM, false><<<resident_grid(k_lasso_apply<L, NUM, false>), kThreads, 0, st>>>(
+            a, layer, p, depth, w.counters, w.list, h, vm, 0, 0);
 }
 
-// Lasso on a label layer (mask NULL) or on a numeric layer (data bytes 1, 2 or 4 and its mask bits).
+// Lasso on a label layer (mask NULL) or on a numeric layer (data bytes 1, 2 or 4 and its mask bits),
+// with texture padding when pad_flags asks for it (radius = bits 0-3, thickness = bits 4-7).
 lcl_status lasso_run(const lcl_atlas *atlas, void *layer, int bytes, uint32_t *mask, uint32_t set, const lcl_camera *cam,
-                     const float *depth, const float *poly, int32_t nv, uint32_t label, float bias, uint64_t *hits,
-                     void *ws, cudaStream_t st) {
+                     const float *depth, const float *poly, int32_t nv, uint32_t label, float bias, uint32_t pad_flags,
+                     uint64_t *hits, void *ws, cudaStream_t st) {
     const AtlasDev a = dev_view(atlas);
     const SelWs w = sel_ws(atlas, 1, ws);
     unsigned long long *h = reinterpret_cast<unsigned long long *>(hits);
     static thread_local LassoArg p;  // ~2.8 KB: kept off the stack
     fill_lasso_arg(p, cam, poly, nv, label, bias);
+    const int32_t pad_r = (int32_t)(pad_flags & 15u), pad_t = (int32_t)((pad_flags >> 4) & 15u);
+    const bool pad = pad_r > 0;
     k_sel_init<<<1, kThreads, 0, st>>>(w.counters, 1, h);
-    const int n_cull = launch_lasso_cull(a, atlas, p, depth, w, false, st);
+    const int n_cull = launch_lasso_cull(a, atlas, p, depth, w, pad, st);
     ValMask vm;
     vm.bits = mask;
     vm.set = set;
     if (!mask) {
-        if (bytes == 1) launch_lasso_apply<uint8_t, false>(a, static_cast<uint8_t *>(layer), p, depth, w, h, vm, st);
-        else launch_lasso_apply<uint16_t, false>(a, static_cast<uint16_t *>(layer), p, depth, w, h, vm, st);
+        if (bytes == 1)
+            launch_lasso_apply<uint8_t, false>(pad, a, static_cast<uint8_t *>(layer), p, depth, w, h, vm, pad_r, pad_t, st);
+        else
+            launch_lasso_apply<uint16_t, false>(pad, a, static_cast<uint16_t *>(layer), p, depth, w, h, vm, pad_r, pad_t,
+                                                st);
     } else if (bytes == 1) {
-        launch_lasso_apply<uint8_t, true>(a, static_cast<uint8_t *>(layer), p, depth, w, h, vm, st);
+        launch_lasso_apply<uint8_t, true>(pad, a, static_cast<uint8_t *>(layer), p, depth, w, h, vm, pad_r, pad_t, st);
     } else if (bytes == 2) {
-        launch_lasso_apply<uint16_t, true>(a, static_cast<uint16_t *>(layer), p, depth, w, h, vm, st);
+        launch_lasso_apply<uint16_t, true>(pad, a, static_cast<uint16_t *>(layer), p, depth, w, h, vm, pad_r, pad_t, st);
     } else {
-        launch_lasso_apply<uint32_t, true>(a, static_cast<uint32_t *>(layer), p, depth, w, h, vm, st);
+        launch_lasso_apply<uint32_t, true>(pad, a, static_cast<uint32_t *>(layer), p, depth, w, h, vm, pad_r, pad_t, st);
     }
     count_launches(2 + n_cull);
     cudaError_t e = cudaGetLastError();
@@ -524,9 +569,10 @@ lcl_status lasso_run(const lcl_atlas *atlas, void *layer, int bytes, uint32_t *m
 }
 
 lcl_status select_lasso_impl(const lcl_atlas *atlas, void *layer, int dtype_bytes, const lcl_camera *cam,
-                             const float *depth, const float *poly, int32_t nv, uint32_t label, float bias,
-                             uint64_t *hits, void *ws, cudaStream_t st) {
-    return lasso_run(atlas, layer, dtype_bytes, nullptr, 1u, cam, depth, poly, nv, label, bias, hits, ws, st);
+                             const float *depth, const float *poly, int32_t nv, uint32_t label, uint32_t flags,
+                             float bias, uint64_t *hits, void *ws, cudaStream_t st) {
+    return lasso_run(atlas, layer, dtype_bytes, nullptr, 1u, cam, depth, poly, nv, label, bias, flags & 0xFFu, hits, ws,
+                     st);
 }
 
 lcl_status numeric_lasso_impl(const lcl_atlas *atlas, void *data, int data_bytes, uint32_t *mask, uint32_t value,
@@ -534,7 +580,7 @@ lcl_status numeric_lasso_impl(const lcl_atlas *atlas, void *data, int data_bytes
                               float bias, uint64_t *hits, void *ws, cudaStream_t st) {
     const bool erase = (flags & LCL_ERASE) != 0;
     return lasso_run(atlas, data, data_bytes, mask, erase ? 0u : 1u, cam, depth, poly, nv, erase ? 0u : value, bias,
-                     hits, ws, st);
+                     flags & 0xFFu, hits, ws, st);
 }
 
 template <typename L, bool NUM>

@@ -86,7 +86,7 @@ class lcl_batch_stroke(C.Structure):
 
 class lcl_batch_lasso(C.Structure):
     _fields_ = [("camera", lcl_camera), ("depth", C.c_void_p), ("poly_xy", C.c_void_p), ("n_vertices", C.c_int32),
-                ("label", C.c_uint32), ("bias", C.c_float), ("_pad", C.c_int32)]
+                ("label", C.c_uint32), ("bias", C.c_float), ("flags", C.c_uint32)]
 
 
 class lcl_batch_limits(C.Structure):
@@ -147,8 +147,8 @@ def library():
         "lcl_select_sphere_static": (st, [C.POINTER(lcl_atlas), P, C.c_int, P, I32, P, P]),
         "lcl_depth_workspace_bytes": (SZ, [C.POINTER(lcl_mesh), I32, I32]),
         "lcl_depth_render": (st, [C.POINTER(lcl_mesh), C.POINTER(lcl_atlas), C.POINTER(lcl_camera), P, P, SZ, P]),
-        "lcl_select_lasso": (st, [C.POINTER(lcl_atlas), P, C.c_int, C.POINTER(lcl_camera), P, P, I32, U32, F, P, P,
-                                  SZ, P]),
+        "lcl_select_lasso": (st, [C.POINTER(lcl_atlas), P, C.c_int, C.POINTER(lcl_camera), P, P, I32, U32, U32, F, P,
+                                  P, SZ, P]),
         "lcl_select_tool": (st, [C.POINTER(lcl_atlas), P, C.c_int, C.POINTER(lcl_camera), P, C.POINTER(lcl_tool), U32, F,
                                  P, P, SZ, P]),
         "lcl_batch_limits_of": (st, [C.POINTER(lcl_batch_model), I32, I32, I32, C.POINTER(lcl_batch_limits)]),
@@ -393,13 +393,14 @@ def lcl_depth_render(mesh: Mesh, atlas: Atlas, cam: lcl_camera, depth: torch.Ten
 
 
 def lcl_select_lasso(atlas: Atlas, layer: torch.Tensor, cam: lcl_camera, depth: torch.Tensor, poly, label,
-                     bias=DEFAULT_BIAS, hits_out=None, workspace=None, stream=None):
+                     bias=DEFAULT_BIAS, hits_out=None, workspace=None, stream=None, flags=0):
+    """A lasso (screen polygon) on ``layer``; flags: texture padding (pad_flags)."""
     poly = np.ascontiguousarray(poly, dtype=np.float32)
     ws = workspace if workspace is not None else _workspace(lcl_select_workspace_bytes(atlas, 1), layer.device)
     _check("lcl_select_lasso", library().lcl_select_lasso(
         C.byref(atlas.c), _ptr(layer), _dtype_code(layer), C.byref(cam), _ptr(depth),
-        poly.ctypes.data_as(C.c_void_p), poly.shape[0], int(label), float(bias), _ptr(hits_out), _ptr(ws),
-        ws.numel(), _stream(stream)))
+        poly.ctypes.data_as(C.c_void_p), poly.shape[0], int(label), int(flags), float(bias), _ptr(hits_out),
+        _ptr(ws), ws.numel(), _stream(stream)))
     return hits_out
 
 
@@ -470,7 +471,8 @@ class Batch:
     """Arguments of one batched edit, kept alive for lcl_batch_upload / lcl_batch_edit.
 
     models: list of (Atlas, layer tensor); queues: per model, a list of ("sphere", record) or
-    ("lasso", (camera, depth tensor, polygon float32 [n, 2], label, bias)) in queue order.
+    ("lasso", (camera, depth tensor, polygon float32 [n, 2], label, bias[, flags])) in queue order
+    (flags, and a sphere record's flags: texture padding, pad_flags).
     limits: capacity of the workspace (lcl_batch_limits); by default exactly this batch's.  A
     workspace with larger limits can take many different batches under one launch shape (and one
     captured graph, see BatchGraph).  config: launch shape (lcl_batch_config) or None (default);
@@ -498,9 +500,10 @@ class Batch:
             for kind, payload in queue:
                 if kind == "sphere":
                     r = payload
-                    strokes[k] = (LCL_STROKE_SPHERE, 0, r["cx"], r["cy"], r["cz"], 0, r["r2"], r["label"], 0)
+                    strokes[k] = (LCL_STROKE_SPHERE, 0, r["cx"], r["cy"], r["cz"], 0, r["r2"], r["label"], r["flags"])
                 else:
-                    cam, depth, poly, label, bias = payload
+                    cam, depth, poly, label, bias = payload[:5]
+                    flags = payload[5] if len(payload) > 5 else 0
                     poly = np.ascontiguousarray(poly, dtype=np.float32)
                     bl = lcl_batch_lasso()
                     bl.camera = cam
@@ -509,6 +512,7 @@ class Batch:
                     bl.n_vertices = poly.shape[0]
                     bl.label = int(label)
                     bl.bias = float(bias)
+                    bl.flags = int(flags)
                     self._keep.append((depth, poly))
                     strokes[k] = (LCL_STROKE_LASSO, len(lassos), 0, 0, 0, 0, 0, 0, 0)
                     lassos.append(bl)

@@ -126,14 +126,16 @@ def test_lasso_and_layer_ops_reject_bad_arguments(lcl):
     P = lambda r: r.ctypes.data_as(C.c_void_p)  # noqa: E731
     dptr, lay, ws = C.c_void_p(1 << 41), C.c_void_p(1 << 42), C.c_void_p(1 << 43)
     wsb = lib.lcl_select_workspace_bytes(C.byref(a), 1)
-    args = lambda p, n, label=5, dt=1, bias=0.001, c=cam: (C.byref(a), lay, dt, C.byref(c), dptr, P(p), n, label,  # noqa
-                                                           C.c_float(bias), None, ws, wsb, None)
+    args = lambda p, n, label=5, dt=1, bias=0.001, c=cam, fl=0: (C.byref(a), lay, dt, C.byref(c), dptr, P(p), n,  # noqa
+                                                                 label, fl, C.c_float(bias), None, ws, wsb, None)
     assert lib.lcl_select_lasso(*args(np.zeros((2, 2), np.float32), 2)) == 4       # too few vertices
     assert lib.lcl_select_lasso(*args(np.zeros((65, 2), np.float32), 65)) == 4     # too many
     nanp = poly.copy(); nanp[1, 0] = np.nan
     assert lib.lcl_select_lasso(*args(nanp, 3)) == 1
     assert lib.lcl_select_lasso(*args(poly, 3, label=300)) == 1
     assert lib.lcl_select_lasso(*args(poly, 3, bias=float("inf"))) == 1
+    assert lib.lcl_select_lasso(*args(poly, 3, fl=9)) == 1                          # padding radius above 8
+    assert lib.lcl_select_lasso(*args(poly, 3, fl=1 << 8)) == 1                     # undefined flag bit
     badcam = lcl.lcl_camera.from_buffer_copy(cam); badcam.m[3] = float("nan")
     assert lib.lcl_select_lasso(*args(poly, 3, c=badcam)) == 1
     badcam = lcl.lcl_camera.from_buffer_copy(cam); badcam.width = 0
@@ -261,8 +263,10 @@ def test_batch_rejects_bad_arguments_on_host(lcl):
     strokes[4].sphere.label = 300
     assert call() == 1                                   # label too wide for uint8
     strokes[4].sphere.label = 3
-    strokes[5].sphere.flags = 1
-    assert call() == 4                                   # padded strokes are not batched
+    strokes[5].sphere.flags = 9
+    assert call() == 1                                   # padding radius above 8
+    strokes[5].sphere.flags = 1 << 8
+    assert call() == 1                                   # undefined flag bit
     strokes[5].sphere.flags = 0
     models[0].layer = (1 << 41) + 8
     assert call() == 1                                   # layer misaligned

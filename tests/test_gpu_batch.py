@@ -54,10 +54,30 @@ def run_sequential(models):
             if kind == "sphere":
                 lcl.lcl_select_sphere(m["atlas"], layer, np.array([payload], lcl.SPHERE_DTYPE))
             else:
-                cam, depth, poly, label, bias = payload
-                lcl.lcl_select_lasso(m["atlas"], layer, cam, depth, poly, label, bias)
+                cam, depth, poly, label, bias = payload[:5]
+                flags = payload[5] if len(payload) > 5 else 0
+                lcl.lcl_select_lasso(m["atlas"], layer, cam, depth, poly, label, bias, flags=flags)
         layers.append(layer)
     return layers
+
+
+def with_padding(models, seed=7):
+    """The same models with texture padding on about a third of their strokes (radius and
+    thickness 1..8), spheres and lassos alike."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for m in models:
+        q = []
+        for kind, payload in m["queue"]:
+            pad = lcl.pad_flags(int(rng.integers(1, 9)), int(rng.integers(1, 9))) if rng.random() < 0.35 else 0
+            if kind == "sphere":
+                rec = payload.copy()
+                rec["flags"] = pad
+                q.append(("sphere", rec))
+            else:
+                q.append(("lasso", tuple(payload[:5]) + (pad,)))
+        out.append(dict(m, queue=q))
+    return out
 
 
 def make_batch(models):
@@ -227,3 +247,53 @@ def test_batch_rejects_batches_above_the_limits(models):
     with pytest.raises(ValueError):
         lcl.Batch([(m["atlas"], to_dev(m["init"])) for m in models[:2]], [m["queue"] for m in models[:2]],
                   limits=small)
+
+
+@pytest.fixture(scope="module")
+def chart_models():
+    """Models whose atlases have gutters (rectangular charts shelf-packed with 2-texel gaps), so that
+    texture padding has uncovered texels to write: three chart vessels with different tiles, label
+    widths and queues of 40 spheres and 12 lassos."""
+    bms = []
+    for i, (nt, nh, side) in enumerate([(60, 30, 256), (120, 60, 512), (80, 40, 384)]):
+        m = synth.vessel_charts(nt, nh, 10 if nt % 20 else 20, 10, side, seed=60 + i)
+        rng = np.random.default_rng(70 + i)
+        st = synth.sphere_strokes(m, 40, 80 + i, 0.01, 0.2, 1, 255)
+        cams = [synth.orbit_camera(m, 320, 320, rng) for _ in range(2)]
+        las = synth.lassos(m, cams, 12, 90 + i, 1, 255, 1)
+        order = np.concatenate([np.arange(40), -1 - np.arange(12)])
+        rng.shuffle(order)
+        bms.append(synth.BatchModel(m, side, st, cams, las, order))
+    return build(bms, [16, 32, 16], [np.uint8, np.uint16, np.uint8], seed=3)
+
+
+def test_batch_with_texture_padding_equals_sequential_calls(chart_models):
+    """Padded sphere and lasso strokes in a batch: identical to the single-stroke calls in queue order,
+    and to the oracle's padded edits except on flagged texels."""
+    pm = with_padding(chart_models)
+    seq = run_sequential(pm)
+    b, layers = make_batch(pm)
+    lcl.lcl_batch_edit(b)
+    torch.cuda.synchronize()
+    for s, l in zip(seq, layers):
+        assert torch.equal(s, l), "padded batched layer differs from sequential calls"
+    m = pm[0]
+    bm = m["bm"]
+    o = oracle.Atlas(bm.mesh, bm.side, bm.side, tile=m["atlas"].tile)
+    exp = m["init"].copy()
+    amb = np.zeros(exp.shape, bool)
+    n_pad = 0
+    for kind, payload in m["queue"]:
+        if kind == "sphere":
+            _, p = oracle.select_sphere_2d(o, exp, np.array([payload], oracle.SPHERE_DTYPE))
+            n_pad += int(p.sum())
+        else:
+            cam, depth, poly, label, bias, flags = payload
+            M = np.array(list(cam.m), np.float32)
+            dm = oracle.depth(bm.mesh, o.mn, o.S, M, cam.width, cam.height)
+            _, p, a = oracle.select_lasso_2d(o, exp, M, dm, poly, label, bias, flags)
+            n_pad += p
+            amb |= a.astype(bool)
+    d = to_np(layers[0], m["dtype"]) != exp
+    assert not (d & ~amb).any()
+    assert n_pad > 100

@@ -131,7 +131,7 @@ def test_numeric_lasso_and_tool_within_tolerance(setup, ntype):
     las = synth.lassos(mesh, [cam], 6, 114, 1, 2, 1)
     for i, L in enumerate(las):
         v = oracle.value_bits(rand_values(ntype, (1,), 200 + i)[0], ntype)
-        flags = oracle.ERASE if i == 2 else 0
+        flags = oracle.ERASE if i == 2 else (oracle.pad_flags(2, 3) if i == 4 else 0)
         if i % 2 == 0:
             h, amb = oracle.num_select_lasso(o, data, mask, M, dm, L.poly, v, flags)
             lcl.lcl_numeric_lasso(a, layer, lcl.camera(M, Ws, Hs), d, L.poly, v, flags, hits_out=hits)

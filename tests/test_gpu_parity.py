@@ -302,6 +302,41 @@ def test_tool_padding_within_tolerance(dt):
 
 
 @pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+def test_lasso_padding_within_tolerance(dt):
+    """Lasso edits with texture padding on a chart atlas (islands with gutters), radius / thickness
+    1..8: labels equal to the oracle's except on flagged texels (and padded texels next to them)."""
+    mesh = synth.vessel_charts(120, 60, 20, 10, 384, seed=8)
+    W = H = 384
+    o = oracle.Atlas(mesh, W, H, tile=16)
+    m, a = gpu_atlas(mesh, W, H, 16)
+    Ws, Hs = 320, 240
+    rng = np.random.default_rng(23)
+    cam = synth.orbit_camera(mesh, Ws, Hs, rng)
+    M = oracle.camera_mq(cam.vp, o.mn, o.S)
+    dm = oracle.depth(mesh, o.mn, o.S, M, Ws, Hs)
+    d = torch.empty((Hs, Ws), dtype=torch.float32, device=DEV)
+    lcl.lcl_depth_render(m, a, lcl.camera(M, Ws, Hs), d)
+    exp = np.zeros((H, W), dt)
+    layer = to_dev(exp)
+    hits = torch.zeros(1, dtype=torch.int64, device=DEV)
+    touched, padded, amb_all = 0, 0, np.zeros((H, W), bool)
+    for i, L in enumerate(synth.lassos(mesh, [cam], 6, 37, 1, 2, 1)):
+        rad, thick = [(1, 1), (2, 1), (3, 4), (8, 8), (5, 2), (1, 6)][i]
+        label = 5 + 13 * i
+        h, npad, amb = oracle.select_lasso_2d(o, exp, M, dm, L.poly, label, flags=oracle.pad_flags(rad, thick))
+        touched += h + npad
+        padded += npad
+        amb_all |= amb.astype(bool)
+        lcl.lcl_select_lasso(a, layer, lcl.camera(M, Ws, Hs), d, L.poly, label, hits_out=hits,
+                             flags=lcl.pad_flags(rad, thick))
+        assert abs(int(hits.item()) - h) <= amb.sum()
+    got = to_np(layer, dt)
+    diff = got != exp
+    assert touched > 1000 and padded > 50
+    assert not (diff & ~amb_all).any(), "padded lasso labels differ outside the ambiguous texels"
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
 def test_overlay_bit_exact(dt):
     mesh = synth.vessel_cylindrical(60, 20, seed=4)
     W, H = 300, 170                      # W*H*s not a multiple of 16: exercises the tail
