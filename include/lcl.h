@@ -492,6 +492,60 @@ typedef struct {
 lcl_status lcl_numeric_stats(const lcl_atlas *atlas, const lcl_numeric_layer *values, const void *zones,
                              lcl_dtype zone_dtype, uint32_t n_labels, lcl_zone_stats *out, lcl_stream stream);
 
+/* ---- sparse layer pool ------------------------------------------------------ */
+
+/* The texture manager of Section 4.2: layers of one (width, height, type) live in one texture array
+ * found by a hash of that key, and sparse textures separate reserving room for many layers from
+ * committing memory to the layers in use.  Here a key's array is a reserved range of device virtual
+ * addresses with max_layers_per_array equal slots (a slot holds a layer's data texture and, for
+ * numeric types, its mask bits, rounded up to the allocation granularity); acquiring a layer
+ * creates and maps physical memory for one slot, releasing it unmaps and frees that memory.  A
+ * layer's address never changes while it lives.  This is the one part of the library that
+ * allocates device memory, and only inside these calls.  A pool belongs to the device that was
+ * current at lcl_pool_create; its calls may come from several host threads. */
+typedef struct lcl_pool lcl_pool;
+
+typedef struct {
+    void *data;       /* device: width x height values of the type, row-major, 256-byte aligned */
+    uint32_t *mask;   /* device: mask bits of a numeric layer (lcl_numeric_layer.mask), NULL for label layers */
+    uint64_t handle;  /* names the layer to lcl_pool_release */
+    int32_t width, height;
+    int32_t type;     /* LCL_U8 / LCL_U16 (label layer) or an lcl_num_type (numeric layer) */
+    int32_t _pad;
+} lcl_pool_layer;
+
+typedef struct {
+    uint64_t reserved_bytes;   /* virtual address space reserved by all arrays */
+    uint64_t committed_bytes;  /* physical device memory mapped for live layers */
+    int64_t layers;            /* live layers */
+    int32_t arrays;            /* distinct (width, height, type) keys seen */
+    int32_t _pad;
+    uint64_t granularity;      /* allocation granularity (bytes) */
+} lcl_pool_stats;
+
+/* Creates an empty pool on the current device.  max_layers_per_array in [1, 2^20]: the slots each
+ * array reserves address space for.  Errors: LCL_ERR_INVALID_ARG; LCL_ERR_CUDA without a device or
+ * without the driver's virtual-memory entry points. */
+lcl_status lcl_pool_create(int32_t max_layers_per_array, lcl_pool **out);
+
+/* Commits one layer of (width, height, type) -- width a multiple of 4 in [4, 16384], height in
+ * [1, 16384] -- and enqueues on `stream` the clearing of its data and mask to 0 ("no data"); use
+ * the layer on other streams only after that.  Errors: LCL_ERR_INVALID_ARG;
+ * LCL_ERR_OUT_OF_MEMORY when the key's slots are all in use or the device has no memory left;
+ * LCL_ERR_CUDA. */
+lcl_status lcl_pool_acquire(lcl_pool *pool, int32_t width, int32_t height, int32_t type, lcl_stream stream,
+                            lcl_pool_layer *out);
+
+/* Releases a layer: synchronises `stream` (every other stream that used the layer must have been
+ * synchronised by the caller), then unmaps and frees its memory; the slot can be acquired again.
+ * Errors: LCL_ERR_INVALID_ARG for a handle that names no live layer of this pool; LCL_ERR_CUDA. */
+lcl_status lcl_pool_release(lcl_pool *pool, uint64_t handle, lcl_stream stream);
+
+lcl_status lcl_pool_stats_get(lcl_pool *pool, lcl_pool_stats *out);
+
+/* Synchronises the device, releases every live layer and the reserved ranges, frees the pool. */
+lcl_status lcl_pool_destroy(lcl_pool *pool);
+
 /* ---- diagnostics -------------------------------------------------------- */
 
 const char *lcl_status_str(lcl_status status);

@@ -34,6 +34,7 @@ EXPORTS = ["lcl_atlas_bytes", "lcl_atlas_bind", "lcl_atlas_rows", "lcl_atlas_wor
            "lcl_batch_launch", "lcl_batch_edit", "lcl_batch_tune",
            "lcl_overlay", "lcl_label_area", "lcl_numeric_sphere", "lcl_numeric_lasso", "lcl_numeric_tool",
            "lcl_numeric_arith", "lcl_numeric_select", "lcl_numeric_stats",
+           "lcl_pool_create", "lcl_pool_acquire", "lcl_pool_release", "lcl_pool_stats_get", "lcl_pool_destroy",
            "lcl_status_str", "lcl_last_error", "lcl_kernel_launches"]
 
 
@@ -75,6 +76,16 @@ class lcl_zone_stats(C.Structure):
                 ("sum", C.c_double), ("wsum", C.c_double)]
 
 
+class lcl_pool_layer(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("mask", C.c_void_p), ("handle", C.c_uint64), ("width", C.c_int32),
+                ("height", C.c_int32), ("type", C.c_int32), ("_pad", C.c_int32)]
+
+
+class lcl_pool_stats(C.Structure):
+    _fields_ = [("reserved_bytes", C.c_uint64), ("committed_bytes", C.c_uint64), ("layers", C.c_int64),
+                ("arrays", C.c_int32), ("_pad", C.c_int32), ("granularity", C.c_uint64)]
+
+
 class lcl_batch_model(C.Structure):
     _fields_ = [("atlas", C.POINTER(lcl_atlas)), ("layer", C.c_void_p), ("dtype", C.c_int),
                 ("first_stroke", C.c_int32), ("n_strokes", C.c_int32), ("_pad", C.c_int32)]
@@ -108,6 +119,7 @@ assert C.sizeof(lcl_sphere) == 32 and C.sizeof(lcl_camera) == 72 and C.sizeof(lc
 assert C.sizeof(lcl_batch_model) == 32 and C.sizeof(lcl_batch_stroke) == 40 and C.sizeof(lcl_batch_lasso) == 104
 assert C.sizeof(lcl_batch_limits) == 32 and C.sizeof(lcl_batch_config) == 16 and C.sizeof(lcl_tool) == 40
 assert C.sizeof(lcl_numeric_layer) == 24 and C.sizeof(lcl_zone_stats) == 48
+assert C.sizeof(lcl_pool_layer) == 40 and C.sizeof(lcl_pool_stats) == 40
 
 SPHERE_DTYPE = np.dtype([("cx", "<i4"), ("cy", "<i4"), ("cz", "<i4"), ("pad", "<i4"),
                          ("r2", "<i8"), ("label", "<u4"), ("flags", "<u4")])
@@ -174,6 +186,11 @@ def library():
         "lcl_numeric_select": (st, [C.POINTER(lcl_atlas), C.POINTER(lcl_numeric_layer), C.c_int, U32, P, C.c_int, U32,
                                     P, P]),
         "lcl_numeric_stats": (st, [C.POINTER(lcl_atlas), C.POINTER(lcl_numeric_layer), P, C.c_int, U32, P, P]),
+        "lcl_pool_create": (st, [I32, C.POINTER(P)]),
+        "lcl_pool_acquire": (st, [P, I32, I32, I32, P, C.POINTER(lcl_pool_layer)]),
+        "lcl_pool_release": (st, [P, C.c_uint64, P]),
+        "lcl_pool_stats_get": (st, [P, C.POINTER(lcl_pool_stats)]),
+        "lcl_pool_destroy": (st, [P]),
         "lcl_status_str": (C.c_char_p, [C.c_int]),
         "lcl_last_error": (C.c_char_p, []),
         "lcl_kernel_launches": (C.c_uint64, []),
@@ -738,6 +755,74 @@ def lcl_numeric_stats(atlas: Atlas, values: NumericLayer, zones, n_labels, out=N
 def zone_stats_host(out: torch.Tensor):
     """Device zone records -> numpy structured array (count, area, vmin, vmax, sum, wsum)."""
     return out.cpu().numpy().view(ZONE_DTYPE)
+
+
+# ---- sparse layer pool -------------------------------------------------------------------
+
+_POOL_TYPES = {"u8": (LCL_U8, torch.uint8), "u16": (LCL_U16, torch.int16)}
+
+
+class _DeviceArray:
+    """__cuda_array_interface__ of a pool layer's memory, so torch can view it without copying."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+_TYPESTR = {torch.uint8: "|u1", torch.int8: "|i1", torch.int16: "<i2", torch.int32: "<i4", torch.float16: "<f2",
+            torch.float32: "<f4"}
+
+
+class PoolLayer:
+    """A layer committed by a Pool: ``data`` (and, for numeric types, ``mask``) are torch views of the
+    pool's memory; ``numeric`` is the NumericLayer over them (numeric types only)."""
+
+    def __init__(self, pool, rec: lcl_pool_layer, kind, device):
+        self.pool, self.rec, self.kind = pool, rec, kind
+        self.handle = int(rec.handle)
+        W, H = rec.width, rec.height
+        dt = _POOL_TYPES[kind][1] if kind in _POOL_TYPES else NUM_TORCH[kind]
+        self.data = torch.as_tensor(_DeviceArray(rec.data, (H, W), _TYPESTR[dt]), device=device)
+        self.mask = None
+        self.numeric = None
+        if rec.mask:
+            n_words = (W * H + 31) // 32
+            self.mask = torch.as_tensor(_DeviceArray(rec.mask, (n_words,), "<i4"), device=device)
+            self.numeric = NumericLayer(W, H, kind, device, data=self.data, mask=self.mask)
+
+
+class Pool:
+    """The sparse layer pool (lcl_pool_*): layers of one (width, height, type) share one reserved
+    address range; memory is committed per acquired layer and returned on release."""
+
+    def __init__(self, max_layers_per_array=256, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.ptr = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check("lcl_pool_create", library().lcl_pool_create(int(max_layers_per_array), C.byref(self.ptr)))
+
+    def acquire(self, width, height, kind="u8", stream=None) -> PoolLayer:
+        code = _POOL_TYPES[kind][0] if kind in _POOL_TYPES else NUM_TYPES[kind]
+        rec = lcl_pool_layer()
+        _check("lcl_pool_acquire", library().lcl_pool_acquire(self.ptr, int(width), int(height), code,
+                                                              _stream(stream), C.byref(rec)))
+        return PoolLayer(self, rec, kind, self.device)
+
+    def release(self, layer: PoolLayer, stream=None):
+        _check("lcl_pool_release", library().lcl_pool_release(self.ptr, layer.handle, _stream(stream)))
+        layer.data = layer.mask = layer.numeric = None
+
+    def stats(self):
+        st = lcl_pool_stats()
+        _check("lcl_pool_stats_get", library().lcl_pool_stats_get(self.ptr, C.byref(st)))
+        return {"reserved_bytes": st.reserved_bytes, "committed_bytes": st.committed_bytes, "layers": st.layers,
+                "arrays": st.arrays, "granularity": st.granularity}
+
+    def destroy(self):
+        if self.ptr:
+            _check("lcl_pool_destroy", library().lcl_pool_destroy(self.ptr))
+            self.ptr = C.c_void_p()
 
 
 def lcl_status_str(status):

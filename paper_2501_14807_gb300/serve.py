@@ -19,7 +19,10 @@ textures).  This module is the server-side counterpart for many models at once:
 * one launch shape for every epoch: the workspaces are sized for the largest possible epoch (every
   layer of every model with a full queue), so the graph captured once per in-flight slot serves
   every epoch;
-* latency: host arrival time to the host observing the epoch's completion event.
+* latency: host arrival time to the host observing the epoch's completion event;
+* optionally (``layer_pool=True``) layers come from the sparse layer pool (``lcl_pool_*``): a model's
+  layers are committed when it is built or admitted and returned to the pool once its spill copy has
+  completed, so spilled models hold no device memory for their layers.
 
 Everything that computes runs in liblcl.so; this module only schedules.
 """
@@ -74,14 +77,21 @@ class _Slot:
     busy_until: object = None                    # event of the last epoch that used it
     spilled: object = None                       # event after the last spill's device-to-host copy
     bytes: int = 0
+    pool_layers: list = field(default_factory=list)  # lcl.PoolLayer of each layer (layer pool only)
 
 
 class Server:
     """Resident pool + FIFO queues + continuous batching over one compute stream."""
 
     def __init__(self, models, hbm_budget_bytes, device="cuda", max_edits_per_layer=lcl.BATCH_MAX_STROKES,
-                 max_in_flight=2, result_ring=4096, max_labels=256, config=None, graphs=True):
+                 max_in_flight=2, result_ring=4096, max_labels=256, config=None, graphs=True, layer_pool=False):
         self.dev = torch.device(device)
+        # layer pool (the sparse layer pool of lcl_pool_*): layers are committed when a model is built
+        # or admitted and returned when its spill copy has completed (polled, not waited for)
+        self.pool = lcl.Pool(max_layers_per_array=max(sum(m.n_layers for m in models), 1),
+                             device=self.dev) if layer_pool else None
+        self._idle = torch.cuda.Stream(self.dev) if layer_pool else None   # no work: releases need no wait
+        self._to_release = []
         self.max_in_flight = max_in_flight
         self.config = config                    # batched launch shape (None: the library default)
         self.use_graphs = graphs                # replay a captured launch (else launch directly)
@@ -126,15 +136,23 @@ class Server:
         s.mesh_dev = lcl.Mesh.from_host(spec.mesh, self.dev)
         s.atlas = lcl.Atlas(spec.side, spec.side, spec.tile, spec.mesh.n_tri, self.dev)
         lcl.lcl_atlas_build(s.mesh_dev, s.atlas)
-        s.layers = [torch.zeros((spec.side, spec.side), dtype=torch.uint8, device=self.dev)
-                    for _ in range(spec.n_layers)]
+        if self.pool is not None:
+            s.pool_layers = [self.pool.acquire(spec.side, spec.side, "u8") for _ in range(spec.n_layers)]
+            s.layers = [pl.data for pl in s.pool_layers]
+        else:
+            s.layers = [torch.zeros((spec.side, spec.side), dtype=torch.uint8, device=self.dev)
+                        for _ in range(spec.n_layers)]
         s.cams = [lcl.lcl_camera_from_vp(s.atlas, c.vp, c.width, c.height) for c in spec.cams]
         s.depths = []
         for c in s.cams:
             d = torch.empty((c.height, c.width), dtype=torch.float32, device=self.dev)
             lcl.lcl_depth_render(s.mesh_dev, s.atlas, c, d)
             s.depths.append(d)
-        s.bytes = s.atlas.buf.numel() + sum(l.numel() for l in s.layers) + sum(4 * d.numel() for d in s.depths)
+        layer_bytes = sum(l.numel() for l in s.layers)
+        if self.pool is not None:   # committed in whole allocation-granularity units
+            g = self.pool.stats()["granularity"]
+            layer_bytes = sum(-(-l.numel() // g) * g for l in s.layers)
+        s.bytes = s.atlas.buf.numel() + layer_bytes + sum(4 * d.numel() for d in s.depths)
         s.resident = True
         self.resident_bytes += s.bytes
 
@@ -156,16 +174,30 @@ class Server:
                 h.copy_(l, non_blocking=True)
             for h, d in zip(host["depths"], s.depths):
                 h.copy_(d, non_blocking=True)
-        for t in [s.atlas.buf] + s.layers + s.depths:
+        for t in [s.atlas.buf] + (s.depths if self.pool is not None else s.layers + s.depths):
             t.record_stream(self.copy)
         s.spilled = torch.cuda.Event()
         s.spilled.record(self.copy)
+        if self.pool is not None:
+            self._to_release.append((s.spilled, s.pool_layers))
+            s.pool_layers = []
         s.atlas = _Rebind(s.atlas)
         s.layers, s.depths = [], []
         s.mesh_dev = None
         s.resident = False
         self.resident_bytes -= s.bytes
         self.spills += 1
+
+    def _reap(self):
+        """Returns to the layer pool the layers of spilled models whose copy to the host is done."""
+        keep = []
+        for ev, layers in self._to_release:
+            if ev.query():
+                for pl in layers:
+                    self.pool.release(pl, stream=self._idle)
+            else:
+                keep.append((ev, layers))
+        self._to_release = keep
 
     def _admit(self, s: _Slot, now: float, keep=()):
         """Makes a spilled model resident again, evicting least recently used idle models (never
@@ -179,15 +211,23 @@ class Server:
         h = s.host
         buf = torch.empty(h["atlas"].numel(), dtype=torch.uint8, device=self.dev)
         buf.record_stream(self.copy)
+        if self.pool is not None:
+            self._reap()
+            s.pool_layers = [self.pool.acquire(l.shape[1], l.shape[0], "u8", stream=self.copy) for l in h["layers"]]
         with torch.cuda.stream(self.copy):
             buf.copy_(h["atlas"], non_blocking=True)
-            s.layers = [l.to(self.dev, non_blocking=True) for l in h["layers"]]
+            if self.pool is not None:
+                s.layers = [pl.data for pl in s.pool_layers]
+                for d, l in zip(s.layers, h["layers"]):
+                    d.copy_(l, non_blocking=True)
+            else:
+                s.layers = [l.to(self.dev, non_blocking=True) for l in h["layers"]]
             s.depths = [d.to(self.dev, non_blocking=True) for d in h["depths"]]
         s.atlas = s.atlas.restore(buf)
         ready = torch.cuda.Event()
         ready.record(self.copy)
         self.compute.wait_event(ready)
-        for t in [buf] + s.layers + s.depths:
+        for t in [buf] + (s.depths if self.pool is not None else s.layers + s.depths):
             t.record_stream(self.compute)
         s.resident = True
         self.resident_bytes += s.bytes
@@ -291,7 +331,16 @@ class Server:
             else:
                 time.sleep(poll_s)
         torch.cuda.synchronize(self.dev)
+        if self.pool is not None:
+            self._reap()
         return requests
+
+    def close(self):
+        """Synchronises the device and returns every pooled layer (layer pool only)."""
+        if self.pool is not None:
+            torch.cuda.synchronize(self.dev)
+            self.pool.destroy()
+            self.pool = None
 
     def run_per_request(self, requests, poll_s=20e-6):
         """The same trace served without batching: each request, in arrival order, is one

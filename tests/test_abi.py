@@ -330,3 +330,17 @@ def test_numeric_layers_reject_bad_arguments(lcl):
     assert lib.lcl_numeric_stats(C.byref(a), C.byref(f32), None, 0, 2, out, None) == 1   # no zones, 2 labels
     assert lib.lcl_numeric_stats(C.byref(a), C.byref(f32), lay, 1, 0, out, None) == 1    # n_labels 0
     assert lib.lcl_numeric_stats(C.byref(a), C.byref(f32), lay, 3, 4, out, None) == 1    # zone dtype
+
+
+def test_pool_rejects_bad_arguments_on_host(lcl):
+    lib = lcl.library()
+    p = C.c_void_p()
+    assert lib.lcl_pool_create(0, C.byref(p)) == 1                  # no slots
+    assert lib.lcl_pool_create(1 << 21, C.byref(p)) == 1            # too many slots
+    assert lib.lcl_pool_create(4, None) == 1
+    rec = lcl.lcl_pool_layer()
+    assert lib.lcl_pool_acquire(None, 64, 64, 1, None, C.byref(rec)) == 1
+    assert lib.lcl_pool_release(None, 0, None) == 1
+    st = lcl.lcl_pool_stats()
+    assert lib.lcl_pool_stats_get(None, C.byref(st)) == 1
+    assert lib.lcl_pool_destroy(None) == 0

@@ -36,14 +36,15 @@ def trace(pools, rate, duration, seed):
     return serve.poisson_requests(len(pools), rate, duration, seed, sphere_of=sphere_of, lasso_of=lasso_of)
 
 
-def test_served_results_equal_requests_applied_alone():
+@pytest.mark.parametrize("layer_pool", [False, True])
+def test_served_results_equal_requests_applied_alone(layer_pool):
     models, pools = served_models(8)
-    footprint = []
-    probe = serve.Server(models[:1], hbm_budget_bytes=1 << 40)
+    probe = serve.Server(models[:1], hbm_budget_bytes=1 << 40, layer_pool=layer_pool)
     one = probe.slots[0].bytes
+    probe.close()
     del probe
     torch.cuda.empty_cache()
-    srv = serve.Server(models, hbm_budget_bytes=int(3.5 * one))     # only a few models fit at once
+    srv = serve.Server(models, hbm_budget_bytes=int(3.5 * one), layer_pool=layer_pool)   # only a few models fit
     reqs = trace(pools, rate=4000.0, duration=0.3, seed=11)
     srv.run(reqs)
     assert all(r.t_done >= r.t_arrive for r in reqs)
@@ -60,3 +61,8 @@ def test_served_results_equal_requests_applied_alone():
             ec, ea = alone_results[i]
             assert np.array_equal(r.result[0], ec) and np.array_equal(r.result[1], ea)
     assert n_q > 0
+    if layer_pool:
+        st = srv.pool.stats()
+        resident_layers = sum(len(sl.layers) for sl in srv.slots if sl.resident)
+        assert st["layers"] == resident_layers < sum(m.n_layers for m in models)
+    srv.close()
