@@ -597,8 +597,10 @@ def serving_setup(n_models, seed=5):
     from paper_2501_14807_gb300 import serve
     bms = synth.config_batch(n_models, seed=seed, depth_side=1024)
     models = [serve.ServedModel(b.mesh, b.side, b.cams, n_layers=2) for b in bms]
+    # the HBM budget holds the first half of the models (the resident set: model i is the i-th most
+    # popular under the Zipf law of the trace); the other half are spillover models admitted on demand
     probe_bytes = [b.side * b.side * 18 + 8 * 1024 * 1024 for b in bms]
-    budget = int(sum(sorted(probe_bytes)[: len(bms) // 2]))
+    budget = int(sum(probe_bytes[: len(bms) // 2]))
 
     def sphere_of(m, rng):
         st = bms[m].strokes
@@ -827,6 +829,67 @@ def synth_roofline(args):
     return synth.config_roofline(n_strokes=args.strokes, n_lassos=0)
 
 
+def run_pool(args):
+    """The sparse layer pool (lcl_pool_*): time to commit (acquire, clear included) and return (release)
+    one layer of several sizes, median of 20 each with the device idle; then the serving workload
+    served with layers taken from the pool against the same trace served with ordinary device
+    tensors (continuous batching both times)."""
+    import torch
+
+    from paper_2501_14807_gb300 import lcl, serve
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    pool = lcl.Pool(max_layers_per_array=64, device=dev)
+    sizes = []
+    for side, kind in ((1024, "u8"), (4096, "u8"), (4096, "f32"), (16384, "u8")):
+        acq, rel = [], []
+        for _ in range(22):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            L = pool.acquire(side, side, kind)
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            pool.release(L)
+            t2 = time.perf_counter()
+            acq.append(t1 - t0)
+            rel.append(t2 - t1)
+        sizes.append({"side": side, "type": kind, "acquire_us": 1e6 * statistics.median(acq[2:]),
+                      "release_us": 1e6 * statistics.median(rel[2:])})
+    st = pool.stats()
+    pool.destroy()
+    models, budget, sphere_of, lasso_of = serving_setup(args.models or 64)
+    out = {}
+    for mode, use_pool in (("tensors", False), ("layer_pool", True)):
+        srv = serve.Server(models, hbm_budget_bytes=budget, layer_pool=use_pool)
+        warm = serve.poisson_requests(len(models), args.rate, 0.2, 6, sphere_of=sphere_of, lasso_of=lasso_of)
+        srv.run(warm)
+        reqs = serve.poisson_requests(len(models), args.rate, args.duration, 5, sphere_of=sphere_of,
+                                      lasso_of=lasso_of)
+        clocks = Clocks(0)
+        clocks.start()
+        srv.run(reqs)
+        clk = clocks.stop()
+        r = serve.latency_stats(reqs)
+        r.update({"spills": srv.spills, "admissions": srv.admissions, "clocks": clk})
+        if use_pool:
+            r["pool"] = srv.pool.stats()
+        out[mode] = r
+        srv.close()
+        del srv
+        torch.cuda.empty_cache()
+    p = out["layer_pool"]
+    line = {"metric": METRIC, "value": p["throughput_rps"], "unit": "requests/s", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": 1e3 * args.duration, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"sparse layer pool: commit / return times per layer; serving {len(models)} "
+                                   f"models under a {budget / 2**30:.2f} GiB budget, Poisson {args.rate:.0f} req/s for "
+                                   f"{args.duration:.1f} s, layers from the pool vs ordinary tensors"},
+            "p50_ms": p["p50_ms"], "p99_ms": p["p99_ms"], "pool_layer_times": sizes,
+            "pool_granularity": st["granularity"], "served": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Serving workload: resident + spillover models (as in the batching workload), 2 layers each,
     an HBM budget that holds about half of them, open-loop Poisson arrivals (70% sphere strokes, 20%
@@ -889,7 +952,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="roofline",
-                    choices=["roofline", "large", "mid", "small", "batch", "serve", "tool", "numeric"])
+                    choices=["roofline", "large", "mid", "small", "batch", "serve", "tool", "numeric", "pool"])
     ap.add_argument("--rate", type=float, default=20000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=5.0, help="serving: trace length (s)")
     ap.add_argument("--models", type=int, default=None,
@@ -903,7 +966,7 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=64, help="rows of the texture the CPU oracle baseline covers")
     args = ap.parse_args()
     defaults = {"roofline": (1000, 20), "mid": (1000, 20), "large": (10000, 200), "small": (200, 0), "batch": (0, 0),
-                "serve": (0, 0), "tool": (0, 0), "numeric": (1000, 0)}
+                "serve": (0, 0), "tool": (0, 0), "numeric": (1000, 0), "pool": (0, 0)}
     if args.strokes is None:
         args.strokes = defaults[args.config][0]
     if args.lassos is None:
@@ -918,6 +981,8 @@ def main():
         run_tool(args)
     elif args.config == "numeric":
         run_numeric(args)
+    elif args.config == "pool":
+        run_pool(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -6,12 +6,18 @@ and its texture manager reserves texture memory and commits it on demand (Sectio
 textures).  This module is the server-side counterpart for many models at once:
 
 * a resident pool: each model's atlas, layers and depth maps live in device memory while the pool's
-  HBM budget allows; a model that is needed when the budget is full evicts the least recently used
-  idle model, whose buffers are copied to pinned host memory on a copy stream and copied back when
-  it is admitted again;
+  HBM budget allows; a model that is needed when the budget is full evicts the idle model with the
+  lowest recent request rate (requests decayed with a 1 s time constant; least recently used among
+  equals), whose layers are copied to pinned host memory on a copy stream (its atlas and depth maps
+  only on the first spill: they never change) and copied back when it is admitted again;
 * per-model FIFO queues: a model's requests are applied in arrival order;
-* continuous batching: every epoch takes, for each model with queued work, the leading run of edit
-  requests (up to 64 per layer) and at most one query, uploads all edits as one batch
+* asynchronous admission: a spilled model with queued work is copied back on the copy stream and
+  its requests join the first epoch built after that copy has completed, so epochs of resident
+  models never wait for an admission; an admitted model cannot be evicted before an epoch has used
+  it (otherwise two models could keep evicting each other); an admission that would exceed the
+  budget while the resident models are busy waits for a later epoch;
+* continuous batching: every epoch takes, for each ready model with queued work, the leading run of
+  edit requests (up to 64 per layer) and at most one query, uploads all edits as one batch
   (``lcl_batch_upload``) and replays a CUDA graph of the batched launch, followed by the queries
   (``lcl_overlay`` + ``lcl_label_area``) on one compute stream, and records an event; requests that
   arrive meanwhile join the next epoch, which is prepared on the host while the previous one runs
@@ -38,6 +44,7 @@ import torch
 from . import lcl
 
 SPHERE, LASSO, QUERY = 0, 1, 2
+TAU_S = 1.0   # time constant of the request-rate score that picks eviction victims
 
 
 @dataclass
@@ -78,6 +85,9 @@ class _Slot:
     spilled: object = None                       # event after the last spill's device-to-host copy
     bytes: int = 0
     pool_layers: list = field(default_factory=list)  # lcl.PoolLayer of each layer (layer pool only)
+    ready: object = None                         # event after the last admission's host-to-device copy
+    score: float = 0.0                           # requests received, decayed with time constant TAU_S
+    t_score: float = 0.0
 
 
 class Server:
@@ -92,6 +102,7 @@ class Server:
                              device=self.dev) if layer_pool else None
         self._idle = torch.cuda.Stream(self.dev) if layer_pool else None   # no work: releases need no wait
         self._to_release = []
+        self.max_admitting = 16
         self.max_in_flight = max_in_flight
         self.config = config                    # batched launch shape (None: the library default)
         self.use_graphs = graphs                # replay a captured launch (else launch directly)
@@ -169,11 +180,13 @@ class Server:
                       "depths": [torch.empty(d.shape, dtype=d.dtype).pin_memory() for d in s.depths]}
         host = s.host
         with torch.cuda.stream(self.copy):
-            host["atlas"].copy_(s.atlas.buf, non_blocking=True)
+            if not host.get("static_copied"):   # atlas and depth maps never change after the build
+                host["atlas"].copy_(s.atlas.buf, non_blocking=True)
+                for h, d in zip(host["depths"], s.depths):
+                    h.copy_(d, non_blocking=True)
+                host["static_copied"] = True
             for h, l in zip(host["layers"], s.layers):
                 h.copy_(l, non_blocking=True)
-            for h, d in zip(host["depths"], s.depths):
-                h.copy_(d, non_blocking=True)
         for t in [s.atlas.buf] + (s.depths if self.pool is not None else s.layers + s.depths):
             t.record_stream(self.copy)
         s.spilled = torch.cuda.Event()
@@ -188,6 +201,15 @@ class Server:
         self.resident_bytes -= s.bytes
         self.spills += 1
 
+    @staticmethod
+    def _score(s: _Slot, now: float):
+        """The model's recent request rate: requests decayed with time constant TAU_S."""
+        return s.score * float(np.exp(-(now - s.t_score) / TAU_S))
+
+    def _touch(self, s: _Slot, now: float):
+        s.score = self._score(s, now) + 1.0
+        s.t_score = now
+
     def _reap(self):
         """Returns to the layer pool the layers of spilled models whose copy to the host is done."""
         keep = []
@@ -199,15 +221,19 @@ class Server:
                 keep.append((ev, layers))
         self._to_release = keep
 
-    def _admit(self, s: _Slot, now: float, keep=()):
-        """Makes a spilled model resident again, evicting least recently used idle models (never
-        one in `keep`: the models already taken into the epoch being built)."""
+    def _admit(self, s: _Slot, now: float, keep=(), force=False):
+        """Makes a spilled model resident again, evicting idle models with the lowest recent request
+        rate (never one in `keep`, the models already taken into the epoch being built).  If the
+        budget cannot be met now (the other resident models are busy), the admission is deferred
+        and False returned, unless `force` or nothing else is resident."""
         while self.resident_bytes + s.bytes > self.budget:
             victims = [v for v in self.slots if v.resident and v is not s and id(v) not in keep and
-                       (v.busy_until is None or v.busy_until.query())]
+                       (v.busy_until is None or v.busy_until.query()) and v.ready is None]
             if not victims:
-                break
-            self._spill(min(victims, key=lambda v: v.last_used))
+                if force or self.resident_bytes == 0:
+                    break
+                return False
+            self._spill(min(victims, key=lambda v: (self._score(v, now), v.last_used)))
         h = s.host
         buf = torch.empty(h["atlas"].numel(), dtype=torch.uint8, device=self.dev)
         buf.record_stream(self.copy)
@@ -224,14 +250,14 @@ class Server:
                 s.layers = [l.to(self.dev, non_blocking=True) for l in h["layers"]]
             s.depths = [d.to(self.dev, non_blocking=True) for d in h["depths"]]
         s.atlas = s.atlas.restore(buf)
-        ready = torch.cuda.Event()
-        ready.record(self.copy)
-        self.compute.wait_event(ready)
+        s.ready = torch.cuda.Event()
+        s.ready.record(self.copy)
         for t in [buf] + (s.depths if self.pool is not None else s.layers + s.depths):
             t.record_stream(self.compute)
         s.resident = True
         self.resident_bytes += s.bytes
         self.admissions += 1
+        return True
 
     # ---- requests -----------------------------------------------------------------------
 
@@ -240,12 +266,24 @@ class Server:
         (event, requests, query results, batch)."""
         models, work, queries, taken = [], [], [], []
         in_epoch = set()
+        waits = []
+        admitting = sum(1 for sl in self.slots if sl.ready is not None)
         for mi, q in queues.items():
             if not q:
                 continue
             s = self.slots[mi]
             if not s.resident:
-                self._admit(s, now, keep=in_epoch)
+                # admission runs on the copy stream; the model's requests join a later epoch, once
+                # its copy is done, so this epoch's resident models do not wait for it (at most
+                # max_admitting admissions in flight)
+                if admitting < self.max_admitting and self._admit(s, now, keep=in_epoch):
+                    admitting += 1
+                continue
+            if s.ready is not None:
+                if not s.ready.query():
+                    continue
+                waits.append(s.ready)
+                s.ready = None
             in_epoch.add(id(s))
             s.last_used = now
             reqs, per_layer_n = [], collections.Counter()
@@ -271,8 +309,12 @@ class Server:
                 req = q.popleft()
                 queries.append((s, req))
                 taken.append(req)
+        if not taken:
+            return None
         slot = self.epochs % self.max_in_flight
         batch = None
+        for w in waits:   # already complete: orders the compute stream after the admission copies
+            self.compute.wait_event(w)
         with torch.cuda.stream(self.compute):
             if models:
                 batch = lcl.Batch(models, work, self._ws[slot], self._stg[slot], limits=self.limits,
@@ -300,18 +342,26 @@ class Server:
         self.epochs += 1
         return ev, taken, results, batch
 
-    def run(self, requests, poll_s=20e-6):
-        """Serves `requests` (sorted by t_arrive, seconds from now) open-loop; fills t_done/result."""
+    def run(self, requests, poll_s=20e-6, stall_limit_s=60.0):
+        """Serves `requests` (sorted by t_arrive, seconds from now) open-loop; fills t_done/result.
+        Raises RuntimeError if no request completes for stall_limit_s seconds while work is queued."""
         pending = collections.deque(requests)
         queues = collections.defaultdict(collections.deque)
         in_flight = collections.deque()
         t0 = time.perf_counter()
         outstanding = len(requests)
+        last_progress, last_outstanding = t0, outstanding
         while outstanding:
             now = time.perf_counter() - t0
+            if outstanding != last_outstanding:
+                last_progress, last_outstanding = time.perf_counter(), outstanding
+            elif not pending and time.perf_counter() - last_progress > stall_limit_s:
+                raise RuntimeError(f"serving loop made no progress for {stall_limit_s} s "
+                                   f"({outstanding} requests outstanding)")
             while pending and pending[0].t_arrive <= now:
                 r = pending.popleft()
                 queues[r.model].append(r)
+                self._touch(self.slots[r.model], now)
             while in_flight and in_flight[0][0].query():
                 ev, taken, results, _batch = in_flight.popleft()
                 done = time.perf_counter() - t0
@@ -322,8 +372,10 @@ class Server:
                                   self._ring[ri, 1, :nl].numpy().view(np.uint64).copy())
                 outstanding -= len(taken)
             if len(in_flight) < self.max_in_flight and any(queues[m] for m in queues):
-                in_flight.append(self._epoch(queues, now))
-                continue
+                ep = self._epoch(queues, now)
+                if ep is not None:
+                    in_flight.append(ep)
+                    continue
             if not in_flight and not any(queues[m] for m in queues) and pending:
                 wait = pending[0].t_arrive - (time.perf_counter() - t0)
                 if wait > 0:
@@ -362,8 +414,12 @@ class Server:
             if pending and pending[0].t_arrive <= now and len(in_flight) < 4096:
                 req = pending.popleft()
                 s = self.slots[req.model]
+                self._touch(s, now)
                 if not s.resident:
-                    self._admit(s, now)
+                    self._admit(s, now, force=True)
+                if s.ready is not None:
+                    self.compute.wait_event(s.ready)
+                    s.ready = None
                 s.last_used = now
                 res = None
                 with torch.cuda.stream(self.compute):
@@ -400,6 +456,8 @@ class Server:
     def layers_of(self, mi):
         s = self.slots[mi]
         if s.resident:
+            if s.ready is not None:
+                s.ready.synchronize()
             return [l.clone() for l in s.layers]
         s.spilled.synchronize()
         return [h.to(self.dev) for h in s.host["layers"]]
