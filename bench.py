@@ -913,7 +913,8 @@ def run_serve(args):
         (srv.run if mode == "batched" else srv.run_per_request)(reqs)
         clk = clocks.stop()
         st = serve.latency_stats(reqs)
-        st.update({"epochs": srv.epochs, "spills": srv.spills, "admissions": srv.admissions, "clocks": clk})
+        st.update({"epochs": srv.epochs, "spills": srv.spills, "admissions": srv.admissions, "clocks": clk,
+                   "host_s": {k: round(v, 3) for k, v in srv.host_s.items()}})
         out[mode] = st
         del srv
         torch.cuda.empty_cache()

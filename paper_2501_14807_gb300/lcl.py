@@ -220,6 +220,11 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _addr(a: np.ndarray) -> int:
+    """Address of a contiguous numpy array's data."""
+    return a.__array_interface__["data"][0]
+
+
 def _dtype_code(layer: torch.Tensor) -> int:
     if layer.element_size() == 1:
         return LCL_U8
@@ -346,13 +351,15 @@ def lcl_quantize_sphere(atlas: Atlas, centre, radius, label):
 
 def lcl_quantize_spheres(atlas: Atlas, centres, radii, labels):
     """Stroke records (SPHERE_DTYPE) for n world-space spheres."""
-    c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
-    r = np.ascontiguousarray(radii, dtype=np.float64).reshape(-1)
-    lab = np.ascontiguousarray(labels, dtype=np.uint32).reshape(-1)
-    out = np.zeros(len(r), SPHERE_DTYPE)
+    c = np.ascontiguousarray(centres, dtype=np.float64)
+    r = np.ascontiguousarray(radii, dtype=np.float64)
+    lab = np.ascontiguousarray(labels, dtype=np.uint32)
+    n = r.size
+    if c.size != 3 * n or lab.size != n:
+        raise ValueError("centres must be n x 3, radii and labels n")
+    out = np.zeros(n, SPHERE_DTYPE)
     _check("lcl_quantize_spheres", library().lcl_quantize_spheres(
-        C.byref(atlas.c), len(r), c.ctypes.data_as(C.c_void_p), r.ctypes.data_as(C.c_void_p),
-        lab.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p)))
+        C.byref(atlas.c), n, _addr(c), _addr(r), _addr(lab), _addr(out)))
     return out
 
 
@@ -501,42 +508,38 @@ class Batch:
         assert len(models) == len(queues)
         self._keep = []
         n_total = sum(len(q) for q in queues)
-        strokes = np.zeros(max(n_total, 1), BATCH_STROKE_DTYPE)
+        rows = []
         lassos = []
         self.models = (lcl_batch_model * max(len(models), 1))()
         k = 0
         for i, ((atlas, layer), queue) in enumerate(zip(models, queues)):
             if len(queue) > BATCH_MAX_STROKES:
                 raise ValueError("at most 64 queued strokes per model per batch")
-            self.models[i].atlas = C.pointer(atlas.c)
-            self.models[i].layer = layer.data_ptr()
-            self.models[i].dtype = _dtype_code(layer)
-            self.models[i].first_stroke = k
-            self.models[i].n_strokes = len(queue)
+            bm = self.models[i]
+            bm.atlas = C.pointer(atlas.c)
+            bm.layer = layer.data_ptr()
+            bm.dtype = _dtype_code(layer)
+            bm.first_stroke = k
+            bm.n_strokes = len(queue)
             self._keep.append((atlas, layer))
             for kind, payload in queue:
                 if kind == "sphere":
                     r = payload
-                    strokes[k] = (LCL_STROKE_SPHERE, 0, r["cx"], r["cy"], r["cz"], 0, r["r2"], r["label"], r["flags"])
+                    rows.append((LCL_STROKE_SPHERE, 0, r["cx"], r["cy"], r["cz"], 0, r["r2"], r["label"], r["flags"]))
                 else:
                     cam, depth, poly, label, bias = payload[:5]
                     flags = payload[5] if len(payload) > 5 else 0
                     poly = np.ascontiguousarray(poly, dtype=np.float32)
-                    bl = lcl_batch_lasso()
-                    bl.camera = cam
-                    bl.depth = depth.data_ptr()
-                    bl.poly_xy = poly.ctypes.data
-                    bl.n_vertices = poly.shape[0]
-                    bl.label = int(label)
-                    bl.bias = float(bias)
-                    bl.flags = int(flags)
+                    bl = lcl_batch_lasso(cam, depth.data_ptr(), _addr(poly), poly.shape[0], int(label),
+                                         float(bias), int(flags))
                     self._keep.append((depth, poly))
-                    strokes[k] = (LCL_STROKE_LASSO, len(lassos), 0, 0, 0, 0, 0, 0, 0)
+                    rows.append((LCL_STROKE_LASSO, len(lassos), 0, 0, 0, 0, 0, 0, 0))
                     lassos.append(bl)
                 k += 1
+        strokes = np.array(rows, dtype=BATCH_STROKE_DTYPE) if rows else np.zeros(1, BATCH_STROKE_DTYPE)
         self.n_models, self.n_strokes, self.n_lassos = len(models), n_total, len(lassos)
         self._strokes_np = strokes
-        self.strokes = strokes.ctypes.data_as(C.POINTER(lcl_batch_stroke))
+        self.strokes = C.cast(_addr(strokes), C.POINTER(lcl_batch_stroke))
         self.lassos = (lcl_batch_lasso * max(len(lassos), 1))(*lassos)
         lib = library()
         own = lcl_batch_limits()

@@ -35,6 +35,7 @@ Everything that computes runs in liblcl.so; this module only schedules.
 from __future__ import annotations
 
 import collections
+import math
 import time
 from dataclasses import dataclass, field
 
@@ -103,6 +104,7 @@ class Server:
         self._idle = torch.cuda.Stream(self.dev) if layer_pool else None   # no work: releases need no wait
         self._to_release = []
         self.max_admitting = 16
+        self.host_s = collections.Counter()   # host seconds spent building epochs, admitting, spilling
         self.max_in_flight = max_in_flight
         self.config = config                    # batched launch shape (None: the library default)
         self.use_graphs = graphs                # replay a captured launch (else launch directly)
@@ -204,7 +206,7 @@ class Server:
     @staticmethod
     def _score(s: _Slot, now: float):
         """The model's recent request rate: requests decayed with time constant TAU_S."""
-        return s.score * float(np.exp(-(now - s.t_score) / TAU_S))
+        return s.score * math.exp(-(now - s.t_score) / TAU_S)
 
     def _touch(self, s: _Slot, now: float):
         s.score = self._score(s, now) + 1.0
@@ -226,14 +228,20 @@ class Server:
         rate (never one in `keep`, the models already taken into the epoch being built).  If the
         budget cannot be met now (the other resident models are busy), the admission is deferred
         and False returned, unless `force` or nothing else is resident."""
-        while self.resident_bytes + s.bytes > self.budget:
-            victims = [v for v in self.slots if v.resident and v is not s and id(v) not in keep and
-                       (v.busy_until is None or v.busy_until.query()) and v.ready is None]
-            if not victims:
-                if force or self.resident_bytes == 0:
+        th = time.perf_counter()
+        if self.resident_bytes + s.bytes > self.budget:
+            # candidates by rising request rate; the busy test (an event query) only as far as needed
+            cands = sorted((self._score(v, now), v.last_used, i) for i, v in enumerate(self.slots)
+                           if v.resident and v is not s and v.ready is None and id(v) not in keep)
+            for _, _, i in cands:
+                if self.resident_bytes + s.bytes <= self.budget:
                     break
+                v = self.slots[i]
+                if v.busy_until is None or v.busy_until.query():
+                    self._spill(v)
+            if self.resident_bytes + s.bytes > self.budget and not (force or self.resident_bytes == 0):
+                self.host_s["admit"] += time.perf_counter() - th
                 return False
-            self._spill(min(victims, key=lambda v: (self._score(v, now), v.last_used)))
         h = s.host
         buf = torch.empty(h["atlas"].numel(), dtype=torch.uint8, device=self.dev)
         buf.record_stream(self.copy)
@@ -257,6 +265,7 @@ class Server:
         s.resident = True
         self.resident_bytes += s.bytes
         self.admissions += 1
+        self.host_s["admit"] += time.perf_counter() - th
         return True
 
     # ---- requests -----------------------------------------------------------------------
@@ -372,7 +381,9 @@ class Server:
                                   self._ring[ri, 1, :nl].numpy().view(np.uint64).copy())
                 outstanding -= len(taken)
             if len(in_flight) < self.max_in_flight and any(queues[m] for m in queues):
+                th = time.perf_counter()
                 ep = self._epoch(queues, now)
+                self.host_s["epoch"] += time.perf_counter() - th
                 if ep is not None:
                     in_flight.append(ep)
                     continue
