@@ -620,16 +620,25 @@ def serving_summary(n_models, rate, duration):
 
     from paper_2501_14807_gb300 import serve
     models, budget, sphere_of, lasso_of = serving_setup(n_models)
-    srv = serve.Server(models, hbm_budget_bytes=budget)
-    srv.run(serve.poisson_requests(len(models), rate, 0.2, 6, sphere_of=sphere_of, lasso_of=lasso_of))
-    reqs = serve.poisson_requests(len(models), rate, duration, 5, sphere_of=sphere_of, lasso_of=lasso_of)
-    srv.run(reqs)
-    st = serve.latency_stats(reqs)
-    st.update({"models": len(models), "offered_rps": rate, "seconds": duration, "spills": srv.spills,
-               "mix": "70% sphere / 20% lasso / 10% overlay+area, Zipf(1.1) models, half of them resident"})
-    del srv
-    torch.cuda.empty_cache()
-    return st
+    out = None
+    for b in (budget, 1 << 50):   # the half-resident budget, then every model resident
+        srv = serve.Server(models, hbm_budget_bytes=b)
+        srv.run(serve.poisson_requests(len(models), rate, 0.2, 6, sphere_of=sphere_of, lasso_of=lasso_of))
+        reqs = serve.poisson_requests(len(models), rate, duration, 5, sphere_of=sphere_of, lasso_of=lasso_of)
+        spills0 = srv.spills
+        srv.run(reqs)
+        st = serve.latency_stats(reqs)
+        st.update({"spills": srv.spills - spills0, "host_s": {k: round(v, 3) for k, v in srv.host_s.items()}})
+        if out is None:
+            out = dict(st)
+            out.update({"models": len(models), "offered_rps": rate, "seconds": duration,
+                        "budget_gib": budget / 2**30,
+                        "mix": "70% sphere / 20% lasso / 10% overlay+area, Zipf(1.1) models, the hot half resident"})
+        else:
+            out["all_resident"] = st
+        del srv
+        torch.cuda.empty_cache()
+    return out
 
 
 # The paper's per-edit times for its Vessel (312k triangles, GTX 970, OpenGL, texture editing +

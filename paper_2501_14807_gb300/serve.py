@@ -35,6 +35,7 @@ Everything that computes runs in liblcl.so; this module only schedules.
 from __future__ import annotations
 
 import collections
+import heapq
 import math
 import time
 from dataclasses import dataclass, field
@@ -87,8 +88,12 @@ class _Slot:
     bytes: int = 0
     pool_layers: list = field(default_factory=list)  # lcl.PoolLayer of each layer (layer pool only)
     ready: object = None                         # event after the last admission's host-to-device copy
+    buf: object = None                           # the model's device buffer (atlas | layers | depth maps)
+    lay: tuple = None                            # its layout (_layout)
     score: float = 0.0                           # requests received, decayed with time constant TAU_S
     t_score: float = 0.0
+    key: float = -math.inf                       # victim-heap key (see Server._touch)
+    idx: int = 0
 
 
 class Server:
@@ -115,7 +120,8 @@ class Server:
         self.max_edits = int(max_edits_per_layer)
         self.compute = torch.cuda.Stream(self.dev)
         self.copy = torch.cuda.Stream(self.dev)
-        self.slots = [_Slot(spec=m) for m in models]
+        self.slots = [_Slot(spec=m, idx=i) for i, m in enumerate(models)]
+        self._heap = [(-math.inf, i) for i in range(len(models))]   # every model starts with rate 0
         self.resident_bytes = 0
         self.spills = 0
         self.admissions = 0
@@ -144,53 +150,83 @@ class Server:
 
     # ---- pool ---------------------------------------------------------------------------
 
+    def _layout(self, s: _Slot):
+        """Offsets of a model's one device buffer: atlas | layers (unless pooled) | depth maps, each
+        section 256-byte aligned.  Returns (atlas bytes, layer offset, layer stride, depth offsets, total)."""
+        spec = s.spec
+        a256 = lambda x: (x + 255) // 256 * 256  # noqa: E731
+        ab = int(lcl.library().lcl_atlas_bytes(spec.side, spec.side, spec.tile, spec.mesh.n_tri))
+        lb = a256(spec.side * spec.side)
+        off_l = a256(ab)
+        off = off_l + (0 if self.pool is not None else spec.n_layers * lb)
+        offs_d = []
+        for c in spec.cams:
+            offs_d.append(off)
+            off += a256(4 * c.width * c.height)
+        return ab, off_l, lb, offs_d, off
+
+    def _views(self, s: _Slot, buf):
+        """Layer and depth-map views of a model buffer laid out by _layout."""
+        spec = s.spec
+        _, off_l, lb, offs_d, _ = s.lay
+        n = spec.side * spec.side
+        if self.pool is None:
+            s.layers = [buf[off_l + i * lb: off_l + i * lb + n].view(spec.side, spec.side)
+                        for i in range(spec.n_layers)]
+        s.depths = [buf[o: o + 4 * c.width * c.height].view(torch.float32).view(c.height, c.width)
+                    for o, c in zip(offs_d, spec.cams)]
+
     def _build(self, s: _Slot):
         spec = s.spec
+        s.lay = self._layout(s)
+        buf = torch.empty(s.lay[4], dtype=torch.uint8, device=self.dev)
         s.mesh_dev = lcl.Mesh.from_host(spec.mesh, self.dev)
-        s.atlas = lcl.Atlas(spec.side, spec.side, spec.tile, spec.mesh.n_tri, self.dev)
+        s.atlas = lcl.Atlas(spec.side, spec.side, spec.tile, spec.mesh.n_tri, self.dev, buffer=buf)
         lcl.lcl_atlas_build(s.mesh_dev, s.atlas)
+        self._views(s, buf)
         if self.pool is not None:
             s.pool_layers = [self.pool.acquire(spec.side, spec.side, "u8") for _ in range(spec.n_layers)]
             s.layers = [pl.data for pl in s.pool_layers]
         else:
-            s.layers = [torch.zeros((spec.side, spec.side), dtype=torch.uint8, device=self.dev)
-                        for _ in range(spec.n_layers)]
+            for l in s.layers:
+                l.zero_()
         s.cams = [lcl.lcl_camera_from_vp(s.atlas, c.vp, c.width, c.height) for c in spec.cams]
-        s.depths = []
-        for c in s.cams:
-            d = torch.empty((c.height, c.width), dtype=torch.float32, device=self.dev)
+        for c, d in zip(s.cams, s.depths):
             lcl.lcl_depth_render(s.mesh_dev, s.atlas, c, d)
-            s.depths.append(d)
-        layer_bytes = sum(l.numel() for l in s.layers)
+        s.buf = buf
+        layer_bytes = 0
         if self.pool is not None:   # committed in whole allocation-granularity units
             g = self.pool.stats()["granularity"]
             layer_bytes = sum(-(-l.numel() // g) * g for l in s.layers)
-        s.bytes = s.atlas.buf.numel() + layer_bytes + sum(4 * d.numel() for d in s.depths)
+        s.bytes = s.lay[4] + layer_bytes
         s.resident = True
         self.resident_bytes += s.bytes
 
     def _spill(self, s: _Slot):
-        """Copies a resident model's device buffers to its pinned host copy (allocated on the first
-        spill and reused) on the copy stream and releases them without waiting: the copy stream's
-        order puts any later re-admission after this copy, and record_stream keeps the device memory
-        from being reused before the copy has read it."""
+        """Copies a resident model to its pinned host image (allocated on the first spill and reused)
+        on the copy stream and releases its device buffer without waiting: the copy stream's order
+        puts any later re-admission after this copy, and record_stream keeps the device memory from
+        being reused before the copy has read it.  The atlas and depth maps never change, so after
+        the first spill only the layers' section is copied (one copy)."""
         if s.busy_until is not None:
             self.copy.wait_event(s.busy_until)
+        _, off_l, lb, offs_d, total = s.lay
         if s.host is None:
-            s.host = {"atlas": torch.empty(s.atlas.buf.numel(), dtype=torch.uint8).pin_memory(),
-                      "layers": [torch.empty(l.shape, dtype=l.dtype).pin_memory() for l in s.layers],
-                      "depths": [torch.empty(d.shape, dtype=d.dtype).pin_memory() for d in s.depths]}
+            s.host = {"image": torch.empty(total, dtype=torch.uint8).pin_memory(), "full": False,
+                      "layers": [torch.empty(l.shape, dtype=l.dtype).pin_memory() for l in s.layers]
+                      if self.pool is not None else None}
         host = s.host
         with torch.cuda.stream(self.copy):
-            if not host.get("static_copied"):   # atlas and depth maps never change after the build
-                host["atlas"].copy_(s.atlas.buf, non_blocking=True)
-                for h, d in zip(host["depths"], s.depths):
-                    h.copy_(d, non_blocking=True)
-                host["static_copied"] = True
-            for h, l in zip(host["layers"], s.layers):
-                h.copy_(l, non_blocking=True)
-        for t in [s.atlas.buf] + (s.depths if self.pool is not None else s.layers + s.depths):
-            t.record_stream(self.copy)
+            if not host["full"]:
+                host["image"].copy_(s.buf, non_blocking=True)
+                host["full"] = True
+            elif self.pool is None:
+                end = off_l + s.spec.n_layers * lb
+                host["image"][off_l:end].copy_(s.buf[off_l:end], non_blocking=True)
+            if self.pool is not None:
+                for h, l in zip(host["layers"], s.layers):
+                    h.copy_(l, non_blocking=True)
+        s.buf.record_stream(self.copy)
         s.spilled = torch.cuda.Event()
         s.spilled.record(self.copy)
         if self.pool is not None:
@@ -198,6 +234,7 @@ class Server:
             s.pool_layers = []
         s.atlas = _Rebind(s.atlas)
         s.layers, s.depths = [], []
+        s.buf = None
         s.mesh_dev = None
         s.resident = False
         self.resident_bytes -= s.bytes
@@ -211,6 +248,13 @@ class Server:
     def _touch(self, s: _Slot, now: float):
         s.score = self._score(s, now) + 1.0
         s.t_score = now
+        # rank key of the victim heap: log(score at time 0) = log(score) + t / TAU_S orders models by
+        # their current rate at any time, so keys never need refreshing (stale entries are skipped)
+        s.key = math.log(s.score) + now / TAU_S
+        heapq.heappush(self._heap, (s.key, s.idx))
+        if len(self._heap) > 8 * len(self.slots) + 1024:   # drop the stale entries
+            self._heap = [(sl.key, sl.idx) for sl in self.slots]
+            heapq.heapify(self._heap)
 
     def _reap(self):
         """Returns to the layer pool the layers of spilled models whose copy to the host is done."""
@@ -230,38 +274,43 @@ class Server:
         and False returned, unless `force` or nothing else is resident."""
         th = time.perf_counter()
         if self.resident_bytes + s.bytes > self.budget:
-            # candidates by rising request rate; the busy test (an event query) only as far as needed
-            cands = sorted((self._score(v, now), v.last_used, i) for i, v in enumerate(self.slots)
-                           if v.resident and v is not s and v.ready is None and id(v) not in keep)
-            for _, _, i in cands:
-                if self.resident_bytes + s.bytes <= self.budget:
-                    break
+            # candidates by rising request rate from the heap (entries whose key changed since are
+            # stale and dropped); models that cannot go now are pushed back afterwards
+            held = []
+            while self._heap and self.resident_bytes + s.bytes > self.budget:
+                key, i = heapq.heappop(self._heap)
                 v = self.slots[i]
+                if key != v.key:
+                    continue
+                held.append((key, i))
+                if not v.resident or v is s or v.ready is not None or id(v) in keep:
+                    continue
                 if v.busy_until is None or v.busy_until.query():
                     self._spill(v)
+            for e in held:
+                heapq.heappush(self._heap, e)
             if self.resident_bytes + s.bytes > self.budget and not (force or self.resident_bytes == 0):
                 self.host_s["admit"] += time.perf_counter() - th
                 return False
         h = s.host
-        buf = torch.empty(h["atlas"].numel(), dtype=torch.uint8, device=self.dev)
+        buf = torch.empty(s.lay[4], dtype=torch.uint8, device=self.dev)
         buf.record_stream(self.copy)
         if self.pool is not None:
             self._reap()
             s.pool_layers = [self.pool.acquire(l.shape[1], l.shape[0], "u8", stream=self.copy) for l in h["layers"]]
         with torch.cuda.stream(self.copy):
-            buf.copy_(h["atlas"], non_blocking=True)
+            buf.copy_(h["image"], non_blocking=True)
             if self.pool is not None:
-                s.layers = [pl.data for pl in s.pool_layers]
-                for d, l in zip(s.layers, h["layers"]):
-                    d.copy_(l, non_blocking=True)
-            else:
-                s.layers = [l.to(self.dev, non_blocking=True) for l in h["layers"]]
-            s.depths = [d.to(self.dev, non_blocking=True) for d in h["depths"]]
+                for pl, l in zip(s.pool_layers, h["layers"]):
+                    pl.data.copy_(l, non_blocking=True)
         s.atlas = s.atlas.restore(buf)
+        self._views(s, buf)
+        if self.pool is not None:
+            s.layers = [pl.data for pl in s.pool_layers]
+        s.buf = buf
         s.ready = torch.cuda.Event()
         s.ready.record(self.copy)
-        for t in [buf] + (s.depths if self.pool is not None else s.layers + s.depths):
-            t.record_stream(self.compute)
+        buf.record_stream(self.compute)
         s.resident = True
         self.resident_bytes += s.bytes
         self.admissions += 1
@@ -471,7 +520,12 @@ class Server:
                 s.ready.synchronize()
             return [l.clone() for l in s.layers]
         s.spilled.synchronize()
-        return [h.to(self.dev) for h in s.host["layers"]]
+        if self.pool is not None:
+            return [h.to(self.dev) for h in s.host["layers"]]
+        _, off_l, lb, _, _ = s.lay
+        n, side = s.spec.side * s.spec.side, s.spec.side
+        return [s.host["image"][off_l + i * lb: off_l + i * lb + n].view(side, side).to(self.dev)
+                for i in range(s.spec.n_layers)]
 
 
 class _Rebind:
@@ -483,8 +537,7 @@ class _Rebind:
 
     def restore(self, buf):
         a = lcl.Atlas(self.width, self.height, self.tile, self.n_tri, buf.device, buffer=buf)
-        for i in range(3):
-            a.c.bbox_min[i] = self.bbox_min[i]
+        a.c.bbox_min[:] = self.bbox_min
         a.c.scale = self.scale
         return a
 
