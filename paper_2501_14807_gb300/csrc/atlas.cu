@@ -348,18 +348,35 @@ __global__ void __launch_bounds__(kThreads) k_resolve(const TriSetup *__restrict
             uint4 t4 = *reinterpret_cast<const uint4 *>(tri_plane + l);
             uint32_t tt[4] = {t4.x, t4.y, t4.z, t4.w};
             int32_t ox[4], oy[4], oz[4];
+            // texels of one triangle in a row share its set-up record, its area and reciprocal, and
+            // their edge functions differ by exact integer steps along x (d/dpx of edge_fn(a, b, p)
+            // is -(b.y - a.y), 256 sub-pixels per texel)
+            uint32_t cur = kNone;
+            int32_t last_k = 0;
+            TriSetup s;
+            int64_t A = 0, w1 = 0, w2 = 0, dw1 = 0, dw2 = 0;
+            float rden = 0.0f;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 ox[k] = INT32_MIN;
                 oy[k] = 0;
                 oz[k] = 0;
                 if (tt[k] == kNone) continue;
-                const TriSetup s = setup[tt[k]];
-                int64_t cx = 256 * (int64_t)(x + k) + 128, cy = 256 * (int64_t)y + 128;
-                int64_t A = edge_fn(s.x[0], s.y[0], s.x[1], s.y[1], s.x[2], s.y[2]);
-                int64_t w1 = edge_fn(s.x[2], s.y[2], s.x[0], s.y[0], cx, cy);
-                int64_t w2 = edge_fn(s.x[0], s.y[0], s.x[1], s.y[1], cx, cy);
-                const float rden = __frcp_rn((float)(2 * A));
+                if (tt[k] != cur) {
+                    cur = tt[k];
+                    s = setup[cur];
+                    const int64_t cx = 256 * (int64_t)(x + k) + 128, cy = 256 * (int64_t)y + 128;
+                    A = edge_fn(s.x[0], s.y[0], s.x[1], s.y[1], s.x[2], s.y[2]);
+                    w1 = edge_fn(s.x[2], s.y[2], s.x[0], s.y[0], cx, cy);
+                    w2 = edge_fn(s.x[0], s.y[0], s.x[1], s.y[1], cx, cy);
+                    dw1 = -256 * ((int64_t)s.y[0] - s.y[2]);
+                    dw2 = -256 * ((int64_t)s.y[1] - s.y[0]);
+                    rden = __frcp_rn((float)(2 * A));
+                } else {
+                    w1 += dw1 * (k - last_k);
+                    w2 += dw2 * (k - last_k);
+                }
+                last_k = k;
                 ox[k] = interp_axis(w1, w2, A, rden, s.qx[0], s.qx[1], s.qx[2]);
                 oy[k] = interp_axis(w1, w2, A, rden, s.qy[0], s.qy[1], s.qy[2]);
                 oz[k] = interp_axis(w1, w2, A, rden, s.qz[0], s.qz[1], s.qz[2]);
