@@ -324,8 +324,24 @@ __device__ __forceinline__ bool lasso_hit(const LassoArg &p, const Edges &sh, co
         const int e = sh.band_edge[k];
         const float ax = sh.vx[e], ay = sh.vy[e], bx = sh.vx[e + 1], by = sh.vy[e + 1];
         if ((ay > ys) != (by > ys)) {
-            const float xi = __fadd_rn(__fdiv_rn(__fmul_rn(__fsub_rn(bx, ax), __fsub_rn(ys, ay)), __fsub_rn(by, ay)), ax);
-            if (xs < xi) inside = !inside;
+            // The crossing x of the definition, xi = ((bx - ax)(ys - ay)) / (by - ay) + ax in FP32,
+            // lies within [min(ax, bx) - d, max(ax, bx) + d] with d = 4.01 u (|ax| + |bx|), u = 2^-24:
+            // (ys - ay) / (by - ay) is in [0, 1] because ys lies between ay and by, and each of the
+            // five roundings adds at most u.  So a point left or right of the edge's x-range by more
+            // than m = 1e-6 (|ax| + |bx| + 1) >= 16 u (...) (which also covers the roundings of the
+            // range bounds) takes the same decision as the division, which runs only for the rest.
+            const float m = __fmul_rn(1e-6f, __fadd_rn(__fadd_rn(fabsf(ax), fabsf(bx)), 1.0f));
+            bool left;
+            if (xs < __fsub_rn(fminf(ax, bx), m)) {
+                left = true;
+            } else if (xs > __fadd_rn(fmaxf(ax, bx), m)) {
+                left = false;
+            } else {
+                const float xi =
+                    __fadd_rn(__fdiv_rn(__fmul_rn(__fsub_rn(bx, ax), __fsub_rn(ys, ay)), __fsub_rn(by, ay)), ax);
+                left = xs < xi;
+            }
+            if (left) inside = !inside;
         }
     }
     if (!inside) return false;
