@@ -834,8 +834,11 @@ def run_numeric(args):
 
 
 def synth_roofline(args):
+    """The roofline model (16384^2), or the same model scaled to --atlas-side for profiles."""
     import synth
-    return synth.config_roofline(n_strokes=args.strokes, n_lassos=0)
+    side = args.atlas_side or 16384
+    return synth.config_roofline(n_strokes=args.strokes, n_lassos=0, n_theta=round(2828 * side / 16384),
+                                 n_h=round(1414 * side / 16384), side=side)
 
 
 def run_pool(args):
