@@ -17,11 +17,13 @@
 // ahead, or a padding branch that raises the kernel above 40 registers (5 instead of 6 CTAs per
 // SM), cost 1.3-1.6 ms per 1000 strokes, hence the separate template instances.
 //
-// Sphere strokes take one launch each: the kernel that applies stroke k also culls stroke k + 1
-// into the other of two candidate lists, and every launch is a programmatic dependent launch, so
-// the next grid is scheduled while the current one drains and waits (griddepcontrol.wait) only
-// for its completion.  Strokes of one call run in stream order, so a later stroke overwrites an
-// earlier one.  Lassos take a cull and an apply launch (two culls with texture padding).  Hit counts are per-warp popcounts
+// Sphere strokes take one launch each: the kernel that applies stroke k also culls stroke k + 1,
+// and every launch is a programmatic dependent launch, so the next grid is scheduled while the
+// current one drains and waits (griddepcontrol.wait) only for its completion.  Stroke k's
+// candidates go to list k mod 3, and the cull of stroke k + 1 runs before the wait, in the
+// shadow of stroke k - 1's tail: list (k + 1) mod 3 was last read by stroke k - 2, which has
+// completed, because grid k is only launched once every CTA of grid k - 1 has passed its own
+// wait.  Strokes of one call run in stream order, so a later stroke overwrites an earlier one.  Lassos take a cull and an apply launch (two culls with texture padding).  Hit counts are per-warp popcounts
 // reduced per CTA into one 64-bit atomic.
 #include <algorithm>
 #include <cmath>
@@ -164,8 +166,14 @@ __global__ void __launch_bounds__(kThreads) k_sphere_step(AtlasDev a, L *__restr
                                                           const uint32_t *__restrict__ list,
                                                           unsigned long long *hits, int has_next, SphereArg nxt,
                                                           uint32_t *next_counter, uint32_t *next_list, ValMask vm) {
+    // Cull of the next stroke: reads only the atlas boxes; its list is free (see the top of the file).
+    if (has_next) {
+        const int32_t n_super = a.supers_x * a.supers_y;
+        for (int32_t sidx = blockIdx.x; sidx < n_super; sidx += gridDim.x)
+            cull_super_sphere<NEXT_PAD>(a, nxt, sidx, next_counter, next_list);
+    }
     pdl_wait();
-    pdl_allow_next();  // the next grid waits for this one to complete before touching memory
+    pdl_allow_next();  // after the wait: grid k + 1 starts once every CTA of this grid got here
     const int32_t qpr = a.T / 4, nq = a.T * qpr;
     const int cpt_log2 = nq > kThreads ? 31 - __clz(nq / kThreads) : 0;
     const uint32_t n_items = *counter << cpt_log2;
@@ -202,11 +210,6 @@ __global__ void __launch_bounds__(kThreads) k_sphere_step(AtlasDev a, L *__restr
             }
         }
         cur = next;
-    }
-    if (has_next) {
-        const int32_t n_super = a.supers_x * a.supers_y;
-        for (int32_t sidx = blockIdx.x; sidx < n_super; sidx += gridDim.x)
-            cull_super_sphere<NEXT_PAD>(a, nxt, sidx, next_counter, next_list);
     }
     add_hits(hits, cnt);
 }
@@ -303,12 +306,7 @@ __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restr
                                                           unsigned long long *hits, ValMask vm, int32_t pad_r,
                                                           int32_t pad_t) {
     __shared__ LassoShared sh;
-    for (int e = threadIdx.x; e <= p.nv; e += kThreads) {
-        sh.vx[e] = p.vx[e];
-        sh.vy[e] = p.vy[e];
-    }
-    for (int k = threadIdx.x; k <= kBands; k += kThreads) sh.band_off[k] = p.band_off[k];
-    for (int k = threadIdx.x; k < p.band_off[kBands]; k += kThreads) sh.band_edge[k] = p.band_edge[k];
+    stage_lasso(sh, p);
     __syncthreads();
     const uint32_t n = *counter;
     const int32_t qpr = a.T / 4, nq = a.T * qpr;
@@ -323,11 +321,7 @@ __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restr
             const int4 X = __ldg(reinterpret_cast<const int4 *>(a.px + l));
             const int4 Y = __ldg(reinterpret_cast<const int4 *>(a.py + l));
             const int4 Z = __ldg(reinterpret_cast<const int4 *>(a.pz + l));
-            uint32_t m = 0;
-            m |= lasso_hit(p, sh, depth, X.x, Y.x, Z.x) ? 1u : 0u;
-            m |= lasso_hit(p, sh, depth, X.y, Y.y, Z.y) ? 2u : 0u;
-            m |= lasso_hit(p, sh, depth, X.z, Y.z, Z.z) ? 4u : 0u;
-            m |= lasso_hit(p, sh, depth, X.w, Y.w, Z.w) ? 8u : 0u;
+            const uint32_t m = lasso_quad(p, sh, depth, X, Y, Z);
             const uint32_t pm = PAD ? lasso_pad_mask(a, l, X, p, sh, depth, pad_r, pad_t) : 0u;
             if (m | pm) {
                 store_hits<L>(layer, l, m | pm, p.label);
@@ -412,16 +406,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_tool_apply(AtlasDev a, L *__res
 }
 
 struct SelWs {
-    uint32_t *counters, *list, *list2;  // two candidate lists: strokes alternate between them
+    uint32_t *counters, *list, *list2, *list3;  // three candidate lists: sphere stroke k uses list k mod 3
 };
 
 SelWs sel_ws(const lcl_atlas *a, int32_t n, void *ws) {
     SelWs w;
     char *base = static_cast<char *>(ws);
+    const size_t lb = align256((size_t)a->tiles_x * a->tiles_y * 4);
     w.counters = reinterpret_cast<uint32_t *>(base);
     w.list = reinterpret_cast<uint32_t *>(base + align256((size_t)(n + 1) * 4));
-    w.list2 = reinterpret_cast<uint32_t *>(base + align256((size_t)(n + 1) * 4) +
-                                           align256((size_t)a->tiles_x * a->tiles_y * 4));
+    w.list2 = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(w.list) + lb);
+    w.list3 = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(w.list2) + lb);
     return w;
 }
 
@@ -447,7 +442,7 @@ int launch_lasso_cull(const AtlasDev &a, const lcl_atlas *atlas, const LassoArg 
 }  // namespace
 
 size_t select_ws_bytes(const lcl_atlas *a, int32_t n) {
-    return align256((size_t)(n + 1) * 4) + 2 * align256((size_t)a->tiles_x * a->tiles_y * 4);
+    return align256((size_t)(n + 1) * 4) + 3 * align256((size_t)a->tiles_x * a->tiles_y * 4);
 }
 
 template <typename L>
@@ -489,7 +484,8 @@ lcl_status select_sphere_run(const lcl_atlas *atlas, L *layer, uint32_t *mask, c
     const int n_super = atlas->supers_x * atlas->supers_y;
     cudaError_t e = launch_pdl(k_sphere_cull, dim3(std::min(n_super, grid[0][0])), st, a, arg(0), w.counters, w.list);
     for (int32_t k = 0; k < n && e == cudaSuccess; ++k) {
-        uint32_t *cur_list = (k & 1) ? w.list2 : w.list, *next_list = (k & 1) ? w.list : w.list2;
+        uint32_t *const lists[3] = {w.list, w.list2, w.list3};
+        uint32_t *cur_list = lists[k % 3], *next_list = lists[(k + 1) % 3];
         const int has_next = k + 1 < n;
         const SphereArg cur = arg(k), nxt = arg(has_next ? k + 1 : k);
         const int pi = cur.pad_r > 0, pj = has_next && nxt.pad_r > 0;

@@ -212,11 +212,50 @@ struct LassoArg {
     uint8_t band_edge[kBandEdgesMax];  // edge e runs from vertex e to vertex e + 1
 };
 
+// A CTA's copy of the polygon and its bands, plus one record per edge e (vertex e to e + 1):
+// {ay, by, lo, hi}, lo and hi its x-range widened by the margin of edge_xrange.
 struct LassoShared {
+    float4 rec[LCL_MAX_LASSO_VERTICES];
     float vx[LCL_MAX_LASSO_VERTICES + 1], vy[LCL_MAX_LASSO_VERTICES + 1];
     uint16_t band_off[kBands + 1];
     uint8_t band_edge[kBandEdgesMax];
 };
+
+// The crossing x of the even-odd rule, xi = ((bx - ax)(ys - ay)) / (by - ay) + ax in FP32, lies
+// within [min(ax, bx) - d, max(ax, bx) + d] with d = 4.01 u (|ax| + |bx|), u = 2^-24, whenever ys
+// lies between ay and by: (ys - ay) / (by - ay) is then in [0, 1] and each of the five roundings
+// adds at most u.  A point left or right of that range by more than m = 1e-6 (|ax| + |bx| + 1)
+// >= 16 u (|ax| + |bx| + 1) (which also covers the roundings of the bounds) takes the same
+// decision as the division.  Returns the widened range {lo, hi}.
+__device__ __forceinline__ float2 edge_xrange(float ax, float bx) {
+    const float m = __fmul_rn(1e-6f, __fadd_rn(__fadd_rn(fabsf(ax), fabsf(bx)), 1.0f));
+    return make_float2(__fsub_rn(fminf(ax, bx), m), __fadd_rn(fmaxf(ax, bx), m));
+}
+
+// Whether (xs, ys), with ys between ay and by, lies left of edge e's crossing (the definition's
+// `xs < xi`); the division runs only inside the widened x-range [lo, hi].
+__device__ __forceinline__ bool edge_left(const float *__restrict__ vx, int e, float xs, float ys, float ay, float by,
+                                          float lo, float hi) {
+    if (xs < lo) return true;
+    if (xs > hi) return false;
+    const float ax = vx[e], bx = vx[e + 1];
+    const float xi = __fadd_rn(__fdiv_rn(__fmul_rn(__fsub_rn(bx, ax), __fsub_rn(ys, ay)), __fsub_rn(by, ay)), ax);
+    return xs < xi;
+}
+
+// Copies the polygon and its bands into shared memory and builds the edge records (one CTA).
+__device__ __forceinline__ void stage_lasso(LassoShared &sh, const LassoArg &p) {
+    for (int e = threadIdx.x; e <= p.nv; e += blockDim.x) {
+        sh.vx[e] = p.vx[e];
+        sh.vy[e] = p.vy[e];
+        if (e < p.nv) {
+            const float2 r = edge_xrange(p.vx[e], p.vx[e + 1]);
+            sh.rec[e] = make_float4(p.vy[e], p.vy[e + 1], r.x, r.y);
+        }
+    }
+    for (int k = threadIdx.x; k <= kBands; k += blockDim.x) sh.band_off[k] = p.band_off[k];
+    for (int k = threadIdx.x; k < p.band_off[kBands]; k += blockDim.x) sh.band_edge[k] = p.band_edge[k];
+}
 
 // Conservative: false only if no texel of the box can be selected by the lasso.  Two exact tests:
 //  - the box's projected corners (all with w > 0) bound the projection of every point of the box
@@ -324,24 +363,8 @@ __device__ __forceinline__ bool lasso_hit(const LassoArg &p, const Edges &sh, co
         const int e = sh.band_edge[k];
         const float ax = sh.vx[e], ay = sh.vy[e], bx = sh.vx[e + 1], by = sh.vy[e + 1];
         if ((ay > ys) != (by > ys)) {
-            // The crossing x of the definition, xi = ((bx - ax)(ys - ay)) / (by - ay) + ax in FP32,
-            // lies within [min(ax, bx) - d, max(ax, bx) + d] with d = 4.01 u (|ax| + |bx|), u = 2^-24:
-            // (ys - ay) / (by - ay) is in [0, 1] because ys lies between ay and by, and each of the
-            // five roundings adds at most u.  So a point left or right of the edge's x-range by more
-            // than m = 1e-6 (|ax| + |bx| + 1) >= 16 u (...) (which also covers the roundings of the
-            // range bounds) takes the same decision as the division, which runs only for the rest.
-            const float m = __fmul_rn(1e-6f, __fadd_rn(__fadd_rn(fabsf(ax), fabsf(bx)), 1.0f));
-            bool left;
-            if (xs < __fsub_rn(fminf(ax, bx), m)) {
-                left = true;
-            } else if (xs > __fadd_rn(fmaxf(ax, bx), m)) {
-                left = false;
-            } else {
-                const float xi =
-                    __fadd_rn(__fdiv_rn(__fmul_rn(__fsub_rn(bx, ax), __fsub_rn(ys, ay)), __fsub_rn(by, ay)), ax);
-                left = xs < xi;
-            }
-            if (left) inside = !inside;
+            const float2 r = edge_xrange(ax, bx);
+            if (edge_left(sh.vx, e, xs, ys, ay, by, r.x, r.y)) inside = !inside;
         }
     }
     if (!inside) return false;
@@ -352,6 +375,83 @@ __device__ __forceinline__ bool lasso_hit(const LassoArg &p, const Edges &sh, co
     return zn <= __fadd_rn(d, p.bias);
 }
 
+
+// lasso_hit for the four texels of a quad (bit k: texel k).  Each texel takes the steps of
+// lasso_hit up to its band; when the quad's live texels share a band (nearly always: they are
+// neighbours on the surface) one pass over that band's edge records tests all of them.  Texels
+// that failed a step carry ys = NaN, which straddles no edge.
+__device__ __forceinline__ uint32_t lasso_quad(const LassoArg &p, const LassoShared &sh,
+                                               const float *__restrict__ depth, int4 X, int4 Y, int4 Z) {
+    const int32_t xq[4] = {X.x, X.y, X.z, X.w}, yq[4] = {Y.x, Y.y, Y.z, Y.w}, zq[4] = {Z.x, Z.y, Z.z, Z.w};
+    float xs[4], ys[4], cw[4];
+    int band[4];
+    uint32_t live = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        xs[k] = 0.0f;
+        ys[k] = __int_as_float(0x7fc00000);
+        cw[k] = 1.0f;
+        band[k] = -1;
+        if (xq[k] == INT32_MIN) continue;  // uncovered
+        const float fx = (float)xq[k], fy = (float)yq[k], fz = (float)zq[k];
+        const float w = clip_row(p.m + 12, fx, fy, fz);
+        if (!(w > 0.0f)) continue;
+        const float cx = clip_row(p.m, fx, fy, fz);
+        if (cx < __fmul_rn(p.nx0, w) || cx > __fmul_rn(p.nx1, w)) continue;
+        const float cy = clip_row(p.m + 4, fx, fy, fz);
+        if (cy < __fmul_rn(p.ny0, w) || cy > __fmul_rn(p.ny1, w)) continue;
+        const float x = screen_of(__fdiv_rn(cx, w), p.ws);
+        const float y = screen_of(__fdiv_rn(cy, w), p.hs);
+        if (!(x >= 0.0f && x < p.ws && y >= 0.0f && y < p.hs)) continue;
+        if (!(y >= p.ymin && y < p.ymax)) continue;
+        int b = __float2int_rz(__fmul_rn(__fsub_rn(y, p.band_y0), p.band_inv_h));
+        b = b < 0 ? 0 : (b >= kBands ? kBands - 1 : b);
+        xs[k] = x;
+        ys[k] = y;
+        cw[k] = w;
+        band[k] = b;
+        live |= 1u << k;
+    }
+    if (!live) return 0;
+    const int b0 = (live & 1u) ? band[0] : (live & 2u) ? band[1] : (live & 4u) ? band[2] : band[3];
+    bool same = true;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) same = same && (band[k] < 0 || band[k] == b0);
+    uint32_t inside = 0;
+    if (same) {
+        for (int j = sh.band_off[b0]; j < sh.band_off[b0 + 1]; ++j) {
+            const int e = sh.band_edge[j];
+            const float4 r = sh.rec[e];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if ((r.x > ys[k]) != (r.y > ys[k]) && edge_left(sh.vx, e, xs[k], ys[k], r.x, r.y, r.z, r.w))
+                    inside ^= 1u << k;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (band[k] < 0) continue;
+            for (int j = sh.band_off[band[k]]; j < sh.band_off[band[k] + 1]; ++j) {
+                const int e = sh.band_edge[j];
+                const float4 r = sh.rec[e];
+                if ((r.x > ys[k]) != (r.y > ys[k]) && edge_left(sh.vx, e, xs[k], ys[k], r.x, r.y, r.z, r.w))
+                    inside ^= 1u << k;
+            }
+        }
+    }
+    live &= inside;
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (!(live & (1u << k))) continue;
+        const float zn = __fdiv_rn(clip_row(p.m + 8, (float)xq[k], (float)yq[k], (float)zq[k]), cw[k]);
+        if (!(zn >= 0.0f && zn <= 1.0f)) continue;
+        const int32_t ix = __float2int_rz(xs[k]), iy = __float2int_rz(ys[k]);
+        const float d = __ldg(depth + (int64_t)iy * p.w_s + ix);
+        if (zn <= __fadd_rn(d, p.bias)) m |= 1u << k;
+    }
+    return m;
+}
 
 
 // The paper's editing tool (Section 4.3.1): window and shape, with the FP32 constants of the
