@@ -12,10 +12,12 @@
 // per-texel test, and one 4-byte (uint8) or 8-byte (uint16) label word written only if a texel in
 // it was hit (read first only if some of its texels were not).  The loads of the thread's next
 // work item are issued before the current one is tested, so two items are in flight per thread.
-// Measured on GB300 (1000 strokes on a 16384^2 atlas): culling the next stroke after the apply
-// loop rather than before it saves ~0.4 us per stroke; reading the candidate list two items
-// ahead, or a padding branch that raises the kernel above 40 registers (5 instead of 6 CTAs per
-// SM), cost 1.3-1.6 ms per 1000 strokes, hence the separate template instances.
+// Measured on GB300 (1000 strokes on a 16384^2 atlas): culling the next stroke before the wait
+// (below) rather than after the apply loop saves ~0.65 us per stroke; culling two strokes ahead
+// over four lists so that a grid could also read its counter, list and first work item before
+// its wait cost ~2.2 us per stroke; reading the candidate list two items ahead, or a padding
+// branch that raises the kernel above 40 registers (5 instead of 6 CTAs per SM), cost 1.3-1.6 ms
+// per 1000 strokes, hence the separate template instances.
 //
 // Sphere strokes take one launch each: the kernel that applies stroke k also culls stroke k + 1,
 // and every launch is a programmatic dependent launch, so the next grid is scheduled while the
