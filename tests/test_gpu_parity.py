@@ -213,6 +213,60 @@ def test_lasso_within_tolerance(name, make, W, H, T, dt, Ws, Hs):
     assert diff.sum() <= LASSO_TOL * touched
 
 
+def _star(cx, cy, r, n, step):
+    k = (np.arange(n) * step) % n
+    a = 2.0 * np.pi * k / n + 0.1
+    return np.stack([cx + r * np.cos(a), cy + r * np.sin(a)], 1)
+
+
+ODD_POLYGONS = {
+    "off-screen": [(-200, -200), (-100, -200), (-150, -100)],
+    "collinear": [(10, 10), (200, 150), (390, 290)],
+    "single-point": [(200.5, 150.5)] * 3,
+    "pentagram": _star(200, 150, 130, 5, 2),            # even-odd: the centre pentagon is outside
+    "bow-tie": [(60, 40), (340, 260), (340, 40), (60, 260)],
+    "repeated-vertices": [(100, 100), (100, 100), (300, 100), (300, 220), (300, 220), (100, 220), (100, 100)],
+    "horizontal-edges": [(50, 60.5), (150, 60.5), (150, 120.5), (250, 120.5), (250, 60.5), (350, 60.5),
+                         (350, 240.5), (50, 240.5)],
+    "full-screen": [(-10, -10), (410, -10), (410, 310), (-10, 310)],
+    "past-the-edges": [(-80, 150), (200, -90), (480, 150), (200, 390)],
+    "triangle": [(50, 50), (350, 80), (200, 280)],
+    "64-gon": _star(210, 140, 110, 64, 1),
+    "64-star": _star(190, 160, 140, 64, 29),             # heavily self-intersecting
+}
+
+
+@pytest.mark.parametrize("kind", list(ODD_POLYGONS))
+def test_lasso_odd_polygons_within_tolerance(kind):
+    """Degenerate and self-intersecting lassos (no area, off screen, repeated vertices, horizontal
+    edges, a pentagram and a 64-vertex star under the even-odd rule, the 3- and 64-vertex limits,
+    polygons past the screen edges) against the oracle."""
+    mesh = synth.config_small().mesh
+    W = H = 512
+    o = oracle.Atlas(mesh, W, H, tile=32)
+    m, a = gpu_atlas(mesh, W, H, 32)
+    Ws, Hs = 400, 300
+    cam = synth.orbit_camera(mesh, Ws, Hs, np.random.default_rng(12))
+    M = oracle.camera_mq(cam.vp, o.mn, o.S)
+    dm = oracle.depth(mesh, o.mn, o.S, M, Ws, Hs)
+    d = torch.empty((Hs, Ws), dtype=torch.float32, device=DEV)
+    lcl.lcl_depth_render(m, a, lcl.camera(M, Ws, Hs), d)
+    poly = np.asarray(ODD_POLYGONS[kind], np.float32)
+    exp = np.zeros((H, W), np.uint8)
+    h, amb = oracle.select_lasso(o, exp, M, dm, poly, 7)
+    layer = to_dev(np.zeros((H, W), np.uint8))
+    hits = torch.zeros(1, dtype=torch.int64, device=DEV)
+    lcl.lcl_select_lasso(a, layer, lcl.camera(M, Ws, Hs), d, poly, 7, hits_out=hits)
+    got = to_np(layer, np.uint8)
+    diff = got != exp
+    assert not (diff & ~amb.astype(bool)).any(), "lasso labels differ outside the ambiguous texels"
+    assert abs(int(hits.item()) - h) <= amb.sum()
+    if kind in ("off-screen", "collinear", "single-point"):
+        assert h == 0 and int(hits.item()) == 0
+    else:
+        assert h > 100
+
+
 @pytest.mark.parametrize("name,make,W,H,T,dt,Ws,Hs", LASSO_CASES, ids=[c[0] for c in LASSO_CASES])
 def test_tool_within_tolerance(name, make, W, H, T, dt, Ws, Hs):
     """The paper's editing tool: circles of the paper's radii (10-200 px), ellipses, random shape
