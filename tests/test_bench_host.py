@@ -1,0 +1,81 @@
+"""Host logic of bench.py, on the CPU: where the roofline's peak and DRAM-traffic figures come from,
+and the per-row algorithmic bytes and fractions."""
+import hashlib
+import json
+import os
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+import bench
+
+
+def _root_with(tmp_path, select_src=b"// kernel source\n", traffic=None, peaks=None):
+    csrc = tmp_path / "paper_2501_14807_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "select.cu").write_bytes(select_src)
+    (tmp_path / "profiles").mkdir()
+    if traffic is not None:
+        (tmp_path / "profiles" / "sphere_edit_traffic.json").write_text(json.dumps(traffic))
+    if peaks is not None:
+        (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps(peaks))
+    return str(tmp_path)
+
+
+def test_traffic_is_reported_only_for_the_captured_source_and_workload(tmp_path, monkeypatch):
+    src = b"__global__ void k() {}\n"
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    rec = {"workload": "vessel-8M-16384sq-u8", "select_cu_sha256_16": sha, "dram_bytes_per_launch": 123}
+    monkeypatch.setattr(bench, "ROOT", _root_with(tmp_path, src, traffic=rec))
+    assert bench.profile_traffic(SimpleNamespace(name="vessel-8M-16384sq-u8")) == 123
+    assert bench.profile_traffic(SimpleNamespace(name="vessel-2M-8192sq-u8")) is None
+    (tmp_path / "paper_2501_14807_gb300" / "csrc" / "select.cu").write_bytes(src + b"// changed\n")
+    assert bench.profile_traffic(SimpleNamespace(name="vessel-8M-16384sq-u8")) is None
+
+
+def test_traffic_absent_is_null(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", _root_with(tmp_path))
+    assert bench.profile_traffic(SimpleNamespace(name="vessel-8M-16384sq-u8")) is None
+
+
+def test_peak_is_the_measured_copy_bandwidth_else_the_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", _root_with(tmp_path, peaks={"hbm_gbs": 6792.4, "bf16_tflops": 1900}))
+    assert bench.peaks() == (6792.4, "measured")
+    other = tmp_path / "other"
+    other.mkdir()
+    monkeypatch.setattr(bench, "ROOT", _root_with(other))
+    assert bench.peaks() == (bench.FALLBACK_HBM_GBS, "fallback")
+
+
+def _stub_workload(s=1):
+    mesh = SimpleNamespace(pos=np.zeros((10, 3), np.float32), uv=np.zeros((12, 2), np.float32),
+                           tri_pos=np.zeros((7, 3), np.uint32), tri_uv=np.zeros((7, 3), np.uint32), n_tri=7)
+    cams = [SimpleNamespace(width=64, height=32), SimpleNamespace(width=16, height=16)]
+    return SimpleNamespace(dtype_bytes=s, width=128, height=64, mesh=mesh, cams=cams,
+                           lassos=[SimpleNamespace(cam=0), SimpleNamespace(cam=1), SimpleNamespace(cam=0)],
+                           strokes=SimpleNamespace(radius=np.zeros(5)), overlays=[("xor", 0, 1)], n_layers=3)
+
+
+@pytest.mark.parametrize("s", [1, 2])
+def test_row_rooflines_units(s):
+    w = _stub_workload(s)
+    n = 128 * 64
+    row_ms = [2.0, 4.0, 1.0, 3.0, 0.5, 1.5]          # per row, summed over 2 steps
+    out = bench.row_rooflines(w, row_ms, 2, 1000, 300, 5000.0)
+    assert list(out) == list(bench.ROWS)
+    expect = {
+        "sphere": 1000 * (12 + s),
+        "lasso": 300 * (12 + s) + (64 * 32 + 16 * 16 + 64 * 32) * 4,
+        "overlay": n * (3 * s + 1 / 8),
+        "area": 3 * (n * (s + 4) + 8 * 7),
+    }
+    for name, ms in zip(bench.ROWS, row_ms):
+        r = out[name]
+        assert r["ms_per_step"] == ms / 2
+        assert r["gb_s"] == pytest.approx(r["algorithmic_bytes"] / (ms / 2 / 1e3) / 1e9)
+        if name in expect:
+            assert r["algorithmic_bytes"] == int(expect[name])
+            assert r["bound"] == "hbm" and r["frac"] == pytest.approx(r["gb_s"] / 5000.0)
+        else:
+            assert r["bound"] == "raster" and "frac" not in r
