@@ -201,7 +201,7 @@ lcl_status lcl_select_sphere(const lcl_atlas *atlas, void *layer, lcl_dtype dtyp
  * risk an allocation failure in the middle of a stroke.  (The paper has no counterpart: it edits
  * through the graphics pipeline, which keeps its own buffers.)
  * Same arguments, results and errors as lcl_select_sphere, whose work it does, except that the
- * scratch space (candidate counters and two tile lists, about 2 MiB) is a fixed array compiled into the
+ * scratch space (candidate counters and three tile lists, about 3 MiB) is a fixed array compiled into the
  * library: every GPU that loads the library holds it until the process exits, and nothing is
  * allocated or freed by this call.
  * Limits: at most LCL_STATIC_MAX_STROKES strokes per call and atlases of at most
