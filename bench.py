@@ -80,25 +80,20 @@ def workload_desc(w, args):
 # CPU baseline / reference arm: the oracle, as it stands, on a bounded row band
 # ---------------------------------------------------------------------------------------
 
-def oracle_sample(w, rows, n_cams_used=None):
-    """Runs the oracle over texture rows [0, rows) of the workload: the same strokes, lassos
-    (with their full depth maps), overlays and area queries.  Returns (texels, seconds)."""
+def _oracle_band(w, y0, y1, mn, S, recs, ms, dms):
+    """The oracle over texture rows [y0, y1) of the workload: the same strokes, the lassos of the
+    cameras in ms / dms (with their full depth maps), overlays and area queries.  Returns texels."""
     import oracle
-    t0 = time.perf_counter()
-    mn, S = oracle.quant_params(w.mesh.pos)
-    o = oracle.Atlas(w.mesh, w.width, w.height, tile=w.tile, y0=0, y1=rows, quant=(mn, S))
+    rows = y1 - y0
+    o = oracle.Atlas(w.mesh, w.width, w.height, tile=w.tile, y0=y0, y1=y1, quant=(mn, S))
     dt = np.uint8 if w.dtype_bytes == 1 else np.uint16
     layers = [np.zeros((rows, w.width), dt) for _ in range(w.n_layers)]
-    recs = oracle.sphere_records(mn, S, w.strokes.centre, w.strokes.radius, w.strokes.label)
     texels = 0
     for li in range(w.n_layers):
         sel = np.nonzero(w.strokes.layer == li)[0]
         texels += int(oracle.select_sphere(o, layers[li], recs[sel]).sum())
-    cams = w.cams if n_cams_used is None else w.cams[:n_cams_used]
-    ms = [oracle.camera_mq(c.vp, mn, S) for c in cams]
-    dms = [oracle.depth(w.mesh, mn, S, m, c.width, c.height) for m, c in zip(ms, cams)]
     for L in w.lassos:
-        if L.cam >= len(cams):
+        if L.cam >= len(ms):
             continue
         h, _ = oracle.select_lasso(o, layers[L.layer], ms[L.cam], dms[L.cam], L.poly, L.label, want_ambiguous=False)
         texels += h
@@ -108,7 +103,39 @@ def oracle_sample(w, rows, n_cams_used=None):
     for li in range(w.n_layers):
         oracle.label_area(o, layers[li], w.n_labels)
         texels += rows * w.width
+    return texels
+
+
+def oracle_sample(w, rows, n_cams_used=None, y0=0):
+    """Runs the oracle over texture rows [y0, y0 + rows) of the workload: the same strokes, lassos
+    (with their full depth maps), overlays and area queries.  Returns (texels, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    mn, S = oracle.quant_params(w.mesh.pos)
+    recs = oracle.sphere_records(mn, S, w.strokes.centre, w.strokes.radius, w.strokes.label)
+    cams = w.cams if n_cams_used is None else w.cams[:n_cams_used]
+    ms = [oracle.camera_mq(c.vp, mn, S) for c in cams]
+    dms = [oracle.depth(w.mesh, mn, S, m, c.width, c.height) for m, c in zip(ms, cams)]
+    texels = _oracle_band(w, y0, y0 + rows, mn, S, recs, ms, dms)
     return texels, time.perf_counter() - t0
+
+
+def oracle_sample_cores(w, rows, n_threads):
+    """The same plain oracle on all host cores: the depth maps once, one thread per camera, then
+    row bands [k rows, (k + 1) rows), one thread each (the C oracle runs without the GIL; each band
+    has its own atlas rows and layers).  Returns (texels, seconds, bands)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    t0 = time.perf_counter()
+    mn, S = oracle.quant_params(w.mesh.pos)
+    recs = oracle.sphere_records(mn, S, w.strokes.centre, w.strokes.radius, w.strokes.label)
+    ms = [oracle.camera_mq(c.vp, mn, S) for c in w.cams]
+    bands = [(k * rows, min((k + 1) * rows, w.height)) for k in range(max(n_threads, 1)) if k * rows < w.height]
+    with ThreadPoolExecutor(max(n_threads, 1)) as ex:
+        dms = list(ex.map(lambda mc: oracle.depth(w.mesh, mn, S, mc[0], mc[1].width, mc[1].height), zip(ms, w.cams)))
+        texels = sum(ex.map(lambda b: _oracle_band(w, b[0], b[1], mn, S, recs, ms, dms), bands))
+    return texels, time.perf_counter() - t0, len(bands)
 
 
 def cpu_baseline(w, rows):
@@ -117,6 +144,20 @@ def cpu_baseline(w, rows):
             "sample": f"texture rows [0, {rows}) of the same workload ({rows * w.width} texels): all strokes, "
                       f"lassos (full depth maps), overlays and area queries; {texels} texels in {secs:.2f} s, "
                       f"single-threaded C (-O2)"}
+
+
+def cpu_baseline_all_cores(w, rows):
+    """The oracle on every host core (row bands of `rows` rows, one thread each); a failure is
+    reported in the line instead of ending the run."""
+    try:
+        n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        texels, secs, bands = oracle_sample_cores(w, rows, n)
+    except Exception as e:  # the single-threaded baseline above stands either way
+        return {"kind": "oracle", "error": f"{type(e).__name__}: {e}"[:200]}
+    return {"value": texels / secs / 1e9, "unit": UNIT, "cores": bands, "kind": "oracle",
+            "sample": f"texture rows [0, {bands * rows}) of the same workload in {bands} bands of {rows} rows, one "
+                      f"thread each, after the depth maps (one thread per camera): {texels} texels in {secs:.2f} s, "
+                      f"the same C as the single-threaded baseline"}
 
 
 def run_reference(args):
@@ -217,6 +258,7 @@ def run_ours(args):
     w = make_workload(args)
     W, H = w.width, w.height
     cpu = cpu_baseline(w, args.cpu_rows) if (rank == 0 and world == 1 and args.cpu_rows > 0) else None
+    cpu_all = cpu_baseline_all_cores(w, args.cpu_rows) if cpu is not None else None
 
     mesh = lcl.Mesh.from_host(w.mesh, dev)
     atlas = lcl.Atlas(W, H, w.tile, w.mesh.n_tri, dev)
@@ -363,6 +405,7 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": sph_bytes / max(n_strokes, 1),
                      "ms_per_launch": sph_ms / args.steps / max(n_strokes, 1)},
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
         "e2e": {"value": all_texels * args.steps / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),

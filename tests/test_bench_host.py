@@ -79,3 +79,15 @@ def test_row_rooflines_units(s):
             assert r["bound"] == "hbm" and r["frac"] == pytest.approx(r["gb_s"] / 5000.0)
         else:
             assert r["bound"] == "raster" and "frac" not in r
+
+
+def test_all_cores_oracle_sample_equals_its_bands_run_one_by_one():
+    """The all-cores CPU baseline runs the same oracle on row bands in threads: its texel count must
+    equal the single-threaded sample of each band added up (a 512^2 version of the roofline model,
+    with lassos on its depth maps)."""
+    import synth
+    w = synth.config_roofline(n_strokes=12, n_lassos=3, depth_side=256, n_theta=88, n_h=44, side=512)
+    texels, secs, bands = bench.oracle_sample_cores(w, 24, 3)
+    assert bands == 3 and secs > 0
+    assert texels == sum(bench.oracle_sample(w, 24, y0=24 * k)[0] for k in range(3))
+    assert texels > 3 * 24 * 512 * (len(w.overlays) + w.n_layers)    # full-row passes plus some hits
