@@ -184,7 +184,7 @@ size_t lcl_select_workspace_bytes(const lcl_atlas *atlas, int32_t n_strokes);
  * For each stroke k in order, every covered texel with squared grid distance
  * (q - c)^2 <= r2 (int64) gets strokes[k].label; later strokes overwrite earlier ones; no
  * other texel changes.  Tiles whose box lies farther than r from c are skipped.
- *  layer: device, width x height labels of `dtype`, 4-byte aligned.
+ *  layer: device, width x height labels of `dtype`, 16-byte aligned.
  *  strokes: host array of n records (copied into the launch; the array may be reused on
  *      return).  label must fit dtype; r2 >= 0 (values above 2^50 act as 2^50).
  *  hits_out: device, n uint64 (nullable): the number of texels each stroke selected.
@@ -200,17 +200,21 @@ lcl_status lcl_select_sphere(const lcl_atlas *atlas, void *layer, lcl_dtype dtyp
  * memory and its allocator, or an interactive editing loop that must not take allocator locks or
  * risk an allocation failure in the middle of a stroke.  (The paper has no counterpart: it edits
  * through the graphics pipeline, which keeps its own buffers.)
- * Same arguments, results and errors as lcl_select_sphere, whose work it does, except that the
- * scratch space (candidate counters and three tile lists, about 3 MiB) is a fixed array compiled into the
- * library: every GPU that loads the library holds it until the process exits, and nothing is
- * allocated or freed by this call.
+ * Same arguments, results and errors as lcl_select_sphere, whose work it does (its argument checks
+ * run first), except that the scratch space (candidate counters and three tile lists, about 3 MiB)
+ * is a fixed array compiled into the library, and the limits below.
+ * Memory: the array belongs to the module of the library that holds it.  CUDA loads that module
+ * into a context on first use, so the first call in each context (each device, or each context a
+ * host application creates) loads it and allocates the ~3 MiB there; that first call can fail
+ * with LCL_ERR_CUDA (out of memory).  Make it once, before the stroke loop and before any stream
+ * capture; from then on the array stays until the context ends, and no call allocates or frees
+ * anything.  Every call looks up the array's address in the current context (cudaGetSymbolAddress,
+ * a host-side table lookup), so calls under different contexts of one device each use their own copy.
  * Limits: at most LCL_STATIC_MAX_STROKES strokes per call and atlases of at most
  * LCL_STATIC_MAX_TILES tiles; larger requests return LCL_ERR_UNSUPPORTED.
- * The first call on each device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current); make that first call before any stream capture.
- * All calls share the one array and it keeps the previous call's contents (each call clears the
- * counters it needs first): calls that could overlap on the GPU -- on different streams, or from
- * several host threads -- race and must be ordered on one stream. */
+ * All calls in one context share the one array and it keeps the previous call's contents (each
+ * call clears the counters it needs first): calls that could overlap on the GPU -- on different
+ * streams, or from several host threads -- race and must be ordered on one stream. */
 lcl_status lcl_select_sphere_static(const lcl_atlas *atlas, void *layer, lcl_dtype dtype, const lcl_sphere *strokes,
                                     int32_t n, uint64_t *hits_out, lcl_stream stream);
 

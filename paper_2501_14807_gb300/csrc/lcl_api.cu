@@ -42,7 +42,6 @@ int sm_count() {
 
 void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
-size_t select_ws_bytes(const lcl_atlas *a, int32_t n);
 
 namespace {
 
@@ -294,8 +293,15 @@ size_t lcl_select_workspace_bytes(const lcl_atlas *atlas, int32_t n_strokes) {
     return select_ws_bytes(atlas, std::max(n_strokes, 1));
 }
 
-lcl_status lcl_select_sphere(const lcl_atlas *atlas, void *layer, lcl_dtype dtype, const lcl_sphere *strokes,
-                             int32_t n, uint64_t *hits_out, void *workspace, size_t ws_bytes, lcl_stream stream) {
+}  // extern "C"
+
+namespace lcl {
+
+// Every check of lcl_select_sphere except those of the workspace (shared with the entry point
+// that brings its own scratch).  *proceed is false when there is nothing to do (n == 0).
+lcl_status check_sphere_call(const lcl_atlas *atlas, const void *layer, lcl_dtype dtype, const lcl_sphere *strokes,
+                             int32_t n, const uint64_t *hits_out, bool *proceed) {
+    *proceed = false;
     lcl_status s = check_atlas(atlas, true);
     if (s != LCL_OK) return s;
     const int db = dtype_bytes(dtype);
@@ -305,8 +311,6 @@ lcl_status lcl_select_sphere(const lcl_atlas *atlas, void *layer, lcl_dtype dtyp
     if (n == 0) return LCL_OK;
     if (!strokes) return fail(LCL_ERR_INVALID_ARG, "strokes is NULL");
     if (hits_out && !aligned(hits_out, 8)) return fail(LCL_ERR_INVALID_ARG, "hits_out must be 8-byte aligned");
-    if (!workspace || !aligned(workspace, 256)) return fail(LCL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-    if (ws_bytes < select_ws_bytes(atlas, n)) return fail(LCL_ERR_OUT_OF_MEMORY, "workspace smaller than lcl_select_workspace_bytes");
     const uint32_t lab_max = db == 1 ? 0xFFu : 0xFFFFu;
     for (int32_t k = 0; k < n; ++k) {
         const lcl_sphere &st = strokes[k];
@@ -318,7 +322,23 @@ lcl_status lcl_select_sphere(const lcl_atlas *atlas, void *layer, lcl_dtype dtyp
         if (st.cx < lo || st.cx > hi || st.cy < lo || st.cy > hi || st.cz < lo || st.cz > hi)
             return fail(LCL_ERR_INVALID_ARG, "stroke centre outside [-2^22, 2^22 + 2^21]");
     }
-    return select_sphere_impl(atlas, layer, db, strokes, n, hits_out, workspace, reinterpret_cast<cudaStream_t>(stream));
+    *proceed = true;
+    return LCL_OK;
+}
+
+}  // namespace lcl
+
+extern "C" {
+
+lcl_status lcl_select_sphere(const lcl_atlas *atlas, void *layer, lcl_dtype dtype, const lcl_sphere *strokes,
+                             int32_t n, uint64_t *hits_out, void *workspace, size_t ws_bytes, lcl_stream stream) {
+    bool proceed = false;
+    lcl_status s = check_sphere_call(atlas, layer, dtype, strokes, n, hits_out, &proceed);
+    if (s != LCL_OK || !proceed) return s;
+    if (!workspace || !aligned(workspace, 256)) return fail(LCL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < select_ws_bytes(atlas, n)) return fail(LCL_ERR_OUT_OF_MEMORY, "workspace smaller than lcl_select_workspace_bytes");
+    return select_sphere_impl(atlas, layer, dtype_bytes(dtype), strokes, n, hits_out, workspace,
+                              reinterpret_cast<cudaStream_t>(stream));
 }
 
 size_t lcl_depth_workspace_bytes(const lcl_mesh *mesh, int32_t width, int32_t height) {

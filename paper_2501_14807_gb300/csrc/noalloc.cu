@@ -2,14 +2,15 @@
 // device memory, with its scratch space in a fixed array compiled into this library.
 //
 // The scratch (per-stroke candidate counters and the candidate-tile lists) lives in the
-// file-scope device array below: every GPU that loads the library holds it until the process
-// exits.  Host code cannot hand the array's name to a kernel (on the host it is only a
-// stand-in for the device symbol), so the device address is looked up once per device with
-// cudaGetSymbolAddress, with that device current, and passed on as the workspace of the
-// ordinary lcl_select_sphere.  Nothing here calls cudaMalloc, cudaFree or any allocating
-// library routine.
-#include <mutex>
-
+// file-scope device array below, which exists once in every CUDA context that has loaded this
+// file's module and stays until that context ends.  Host code cannot hand the array's name to a
+// kernel (on the host it is only a stand-in for the device symbol), so every call looks up the
+// device address with cudaGetSymbolAddress in the context current at the call and passes it on
+// as the workspace of the ordinary lcl_select_sphere.  The lookup is not cached: a cached
+// address would be wrong for a call made under another context of the same device (a host
+// application's own driver context, or one re-created after cudaDeviceReset).  Nothing here
+// calls cudaMalloc, cudaFree or any allocating library routine; the one allocation is the
+// module load itself (see the header).
 #include "lcl_impl.cuh"
 
 namespace lcl {
@@ -24,26 +25,6 @@ constexpr size_t kStaticScratchBytes =
 
 static __device__ __align__(256) unsigned char g_sphere_scratch[kStaticScratchBytes];
 
-std::mutex g_setup_mu;
-void *g_scratch_addr[64] = {nullptr};
-
-// Device address of the scratch array on the current device (looked up on first use).
-lcl_status scratch_address(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "lcl_select_sphere_static: cudaGetDevice");
-    if (dev < 0 || dev >= 64) return fail(LCL_ERR_UNSUPPORTED, "lcl_select_sphere_static: device index above 63");
-    std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_sphere_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "lcl_select_sphere_static: cudaGetSymbolAddress");
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
-    return LCL_OK;
-}
-
 }  // namespace
 }  // namespace lcl
 
@@ -52,7 +33,9 @@ using namespace lcl;
 extern "C" lcl_status lcl_select_sphere_static(const lcl_atlas *atlas, void *layer, lcl_dtype dtype,
                                                const lcl_sphere *strokes, int32_t n, uint64_t *hits_out,
                                                lcl_stream stream) {
-    if (!atlas) return fail(LCL_ERR_INVALID_ARG, "atlas is NULL");
+    bool proceed = false;
+    lcl_status s = check_sphere_call(atlas, layer, dtype, strokes, n, hits_out, &proceed);
+    if (s != LCL_OK || !proceed) return s;
     if (n > kStaticMaxStrokes)
         return fail(LCL_ERR_UNSUPPORTED, "lcl_select_sphere_static takes at most LCL_STATIC_MAX_STROKES (4096) "
                                          "strokes per call");
@@ -60,7 +43,9 @@ extern "C" lcl_status lcl_select_sphere_static(const lcl_atlas *atlas, void *lay
         return fail(LCL_ERR_UNSUPPORTED, "lcl_select_sphere_static supports atlases of at most "
                                          "LCL_STATIC_MAX_TILES (262144) tiles");
     void *scratch = nullptr;
-    lcl_status s = scratch_address(&scratch);
-    if (s != LCL_OK) return s;
+    const cudaError_t e = cudaGetSymbolAddress(&scratch, g_sphere_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "lcl_select_sphere_static: cudaGetSymbolAddress of the scratch array");
+    if (select_ws_bytes(atlas, n) > kStaticScratchBytes)
+        return fail(LCL_ERR_INTERNAL, "lcl_select_sphere_static: scratch array smaller than the workspace layout");
     return lcl_select_sphere(atlas, layer, dtype, strokes, n, hits_out, scratch, kStaticScratchBytes, stream);
 }

@@ -116,6 +116,35 @@ def test_select_sphere_rejects_bad_arguments(lcl):
     assert "aligned" in lcl.lcl_last_error()
 
 
+def test_static_sphere_checks_arguments_like_the_workspace_entry_point(lcl):
+    """lcl_select_sphere_static runs lcl_select_sphere's argument checks before its own size limits:
+    a bad atlas, label or layer gives the same status from both, and only valid calls beyond the
+    scratch array's limits get LCL_ERR_UNSUPPORTED (host-side checks only, nothing is launched)."""
+    lib, a = _bound(lcl)
+    layer, ws = C.c_void_p(1 << 41), C.c_void_p(1 << 42)
+    wsb = lib.lcl_select_workspace_bytes(C.byref(a), 4)
+    good = np.zeros(4, lcl.SPHERE_DTYPE)
+    P = lambda r: r.ctypes.data_as(C.c_void_p)  # noqa: E731
+
+    def both(atlas, recs, dtype=1, lay=layer):
+        ws_st = lib.lcl_select_sphere(C.byref(atlas), lay, dtype, P(recs), len(recs), None, ws, wsb, None)
+        st_st = lib.lcl_select_sphere_static(C.byref(atlas), lay, dtype, P(recs), len(recs), None, None)
+        return ws_st, st_st
+
+    bad = good.copy(); bad[2]["label"] = 256
+    assert both(a, bad) == (1, 1)
+    assert both(a, good, dtype=3) == (1, 1)
+    assert both(a, good, lay=C.c_void_p((1 << 41) + 4)) == (1, 1)
+    # an unbound atlas whose tile counts exceed the array: the atlas check answers first
+    junk = lcl.lcl_atlas()
+    junk.tiles_x, junk.tiles_y = 4096, 4096
+    assert lib.lcl_select_sphere_static(C.byref(junk), layer, 1, P(good), 4, None, None) == 1
+    assert lib.lcl_select_sphere_static(C.byref(a), layer, 1, P(good), 0, None, None) == 0   # nothing to do
+    many = np.zeros(4097, lcl.SPHERE_DTYPE)
+    assert lib.lcl_select_sphere_static(C.byref(a), layer, 1, P(many), 4097, None, None) == 4
+    assert "4096" in lcl.lcl_last_error()
+
+
 def test_lasso_and_layer_ops_reject_bad_arguments(lcl):
     lib, a = _bound(lcl)
     cam = lcl.lcl_camera()
