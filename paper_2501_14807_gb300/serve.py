@@ -567,45 +567,6 @@ def poisson_requests(n_models, rate_hz, duration_s, seed, mix=(0.7, 0.2, 0.1), z
     return out
 
 
-def replay_alone(server_models, requests, device="cuda"):
-    """Applies each model's requests alone, in arrival order, with single-stroke calls on fresh
-    layers; returns ({model: layers}, {request index: (counts, areas)}) for comparison."""
-    dev = torch.device(device)
-    by_model = collections.defaultdict(list)
-    for i, r in enumerate(requests):
-        by_model[r.model].append((i, r))
-    layers, results = {}, {}
-    for mi, reqs in by_model.items():
-        spec = server_models[mi]
-        mesh = lcl.Mesh.from_host(spec.mesh, dev)
-        a = lcl.Atlas(spec.side, spec.side, spec.tile, spec.mesh.n_tri, dev)
-        lcl.lcl_atlas_build(mesh, a)
-        ls = [torch.zeros((spec.side, spec.side), dtype=torch.uint8, device=dev) for _ in range(spec.n_layers)]
-        cams = [lcl.lcl_camera_from_vp(a, c.vp, c.width, c.height) for c in spec.cams]
-        depths = []
-        for c in cams:
-            d = torch.empty((c.height, c.width), dtype=torch.float32, device=dev)
-            lcl.lcl_depth_render(mesh, a, c, d)
-            depths.append(d)
-        for i, r in reqs:
-            if r.kind == SPHERE:
-                c, rad, label = r.sphere
-                lcl.lcl_select_sphere(a, ls[r.layer], np.array([lcl.lcl_quantize_sphere(a, c, rad, label)],
-                                                               lcl.SPHERE_DTYPE))
-            elif r.kind == LASSO:
-                ci, poly, label = r.lasso
-                lcl.lcl_select_lasso(a, ls[r.layer], cams[ci], depths[ci], poly, label)
-            else:
-                op, la, lb, n_labels = r.query
-                out = torch.empty_like(ls[la])
-                lcl.lcl_overlay(a, ls[la], ls[lb], out, op)
-                cnt, area = lcl.lcl_label_area(a, out, n_labels)
-                results[i] = (cnt.cpu().numpy().view(np.uint64), area.cpu().numpy().view(np.uint64))
-        layers[mi] = ls
-    torch.cuda.synchronize(dev)
-    return layers, results
-
-
 def latency_stats(requests):
     lat = np.array([r.t_done - r.t_arrive for r in requests])
     span = max(r.t_done for r in requests) - min(r.t_arrive for r in requests)
