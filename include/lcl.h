@@ -558,6 +558,29 @@ const char *lcl_last_error(void);
 /* Number of kernels this library has launched in this process (all devices). */
 uint64_t lcl_kernel_launches(void);
 
+/* Device-side status of the work enqueued so far (the CPU manages, the GPU computes and keeps the
+ * data: Section 4, Fig. 2 -- so faults and checks made on the GPU have to be fetched by the CPU).
+ * Synchronises `stream`; returns LCL_ERR_CUDA (with the CUDA error text) if the stream reports an
+ * error.  In a library built with bounds checks (lcl_build_flags() & LCL_BUILD_BOUNDS_CHECKS, the
+ * LCL_DEBUG_BOUNDS build), every index a kernel computes into a plane, layer, candidate list,
+ * depth map or table is checked before its access; an index out of range skips that access (no
+ * trap: the context stays usable) and is counted, and this call returns LCL_ERR_INTERNAL with
+ * lcl_last_error() naming the first such site (file:line), its index and the buffer's extent, then
+ * clears the records.  Kernels on other streams must have finished (synchronise them first) for
+ * their checks to be seen.  In the normal build there are no checks and the call returns LCL_OK
+ * once the stream has finished without error.  No kernel of this library waits on another, so
+ * no call returns LCL_ERR_TIMEOUT (reserved). */
+lcl_status lcl_last_device_status(lcl_stream stream);
+
+#define LCL_BUILD_BOUNDS_CHECKS 1u  /* lcl_build_flags bit: kernels check their indices */
+/* How this library was built (LCL_BUILD_* bits). */
+uint32_t lcl_build_flags(void);
+
+/* Writes "file:line" of a bounds-check site as recorded on the device (site = 16-bit hash of the
+ * source file name << 16 | line) into buf (n bytes, NUL-terminated; buf may be NULL) and returns
+ * the full length.  Unknown files are written as "file#hhhh:line". */
+size_t lcl_describe_site(uint32_t site, char *buf, size_t n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,9 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblcl.so")
+# the bounds-checking build (-DLCL_DEBUG_BOUNDS): every kernel index checked before its access
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "liblcl_debug.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -46,17 +49,21 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, debug: bool = False) -> str:
+    """Builds liblcl.so, or with debug=True liblcl_debug.so (bounds checks in every kernel)."""
+    out_dir, lib_path = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     common = [ARCH, "-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-I", INCLUDE, "-I", CSRC,
               "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math", "-Wno-deprecated-gpu-targets"]
+    if debug:
+        common += ["-DLCL_DEBUG_BOUNDS"]
     if ptxas_info:
         common += ["-Xptxas", "-v"]
     hdrs = _deps()
     jobs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         if force or ptxas_info or _stale(obj, [src] + hdrs):
             jobs.append((src, obj))
 
@@ -76,17 +83,18 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                     failed.append(src)
     if failed:
         raise RuntimeError("nvcc failed on: " + ", ".join(os.path.basename(f) for f in failed))
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in sources()]
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    objs = [os.path.join(out_dir, os.path.basename(s)[:-3] + ".o") for s in sources()]
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         cmd = [cc, ARCH, "-shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             sys.stderr.write(r.stdout + r.stderr)
-            raise RuntimeError("linking liblcl.so failed")
-        os.replace(tmp, LIB)
-    return LIB
+            raise RuntimeError(f"linking {os.path.basename(lib_path)} failed")
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                debug="--debug" in sys.argv))

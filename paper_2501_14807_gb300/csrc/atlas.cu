@@ -31,8 +31,10 @@ __global__ void k_init(uint32_t *__restrict__ tri, int64_t n_texels, uint32_t *_
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     uint4 none = make_uint4(kNone, kNone, kNone, kNone);
-    for (int64_t k = i; k < n_texels / 4; k += stride) reinterpret_cast<uint4 *>(tri)[k] = none;
-    for (int64_t k = i; k < n_words; k += stride) cover[k] = 0u;
+    for (int64_t k = i; k < n_texels / 4; k += stride)
+        if (LCL_IN(4 * k + 3, n_texels)) reinterpret_cast<uint4 *>(tri)[k] = none;
+    for (int64_t k = i; k < n_words; k += stride)
+        if (LCL_IN(k, n_words)) cover[k] = 0u;
     if (i == 0) {
         for (int a = 0; a < 3; ++a) {
             hdr->key_min[a] = 0x7FFFFFFF;
@@ -49,6 +51,7 @@ __global__ void k_bbox(const float *__restrict__ pos, int64_t n_pos, AtlasHdr *h
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n_pos; v += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
+            if (!LCL_IN(3 * v + a, 3 * n_pos)) continue;
             float p = pos[3 * v + a];
             bad |= !isfinite(p);
             mn[a] = fminf(mn[a], p);
@@ -96,6 +99,7 @@ __global__ void k_quant(const float *__restrict__ pos, int64_t n_pos, const Atla
     int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (v >= n_pos) return;
     double S = hdr->scale;
+    if (!LCL_IN(3 * v + 2, 3 * n_pos)) return;
     int4 r;
     r.x = quantize_coord(pos[3 * v + 0], hdr->mn[0], S);
     r.y = quantize_coord(pos[3 * v + 1], hdr->mn[1], S);
@@ -108,6 +112,7 @@ __global__ void k_snap(const float *__restrict__ uv, int64_t n_uv, int32_t w, in
                        int2 *__restrict__ out) {
     int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (v >= n_uv) return;
+    if (!LCL_IN(2 * v + 1, 2 * n_uv)) return;
     float u = uv[2 * v], t = uv[2 * v + 1];
     bool ok = isfinite(u) && isfinite(t) && u >= -1.0f && u <= 2.0f && t >= -1.0f && t <= 2.0f;
     if (!ok) {
@@ -161,7 +166,7 @@ __device__ __forceinline__ void texel_range(int64_t lo, int64_t hi, int32_t n, i
 
 // Rasterises texels [i0, i1] x [j0, j1] of a set-up triangle: atomicMin of its id.
 __device__ void raster_rect(const TriSetup &s, uint32_t t, int64_t i0, int64_t i1, int64_t j0, int64_t j1, int32_t w,
-                            uint32_t *__restrict__ tri_plane) {
+                            int32_t h, uint32_t *__restrict__ tri_plane) {
     int64_t X0 = s.x[0], X1 = s.x[1], X2 = s.x[2], Y0 = s.y[0], Y1 = s.y[1], Y2 = s.y[2];
     int64_t px = 256 * i0 + 128, py = 256 * j0 + 128;
     // w_k + bias_k > 0 <=> covered (integer edge values, owned edges get bias 1)
@@ -178,7 +183,7 @@ __device__ void raster_rect(const TriSetup &s, uint32_t t, int64_t i0, int64_t i
         uint32_t *row = tri_plane + j * (int64_t)w;
 #pragma unroll 1
         for (int64_t i = i0; i <= i1; ++i) {
-            if (r0 > 0 && r1 > 0 && r2 > 0) atomicMin(row + i, t);
+            if (r0 > 0 && r1 > 0 && r2 > 0 && LCL_IN(j * (int64_t)w + i, (int64_t)w * h)) atomicMin(row + i, t);
             r0 += dx0;
             r1 += dx1;
             r2 += dx2;
@@ -259,24 +264,28 @@ __global__ void k_raster(RasterArgs a) {
     if (i0 > i1 || j0 > j1) return;
     int64_t nx = i1 - i0 + 1, ny = j1 - j0 + 1;
     if (nx * ny <= kSmallRaster) {
-        raster_rect(s, (uint32_t)t, i0, i1, j0, j1, a.w, a.tri_plane);
+        raster_rect(s, (uint32_t)t, i0, i1, j0, j1, a.w, a.h, a.tri_plane);
         return;
     }
     int64_t nbx = (nx + kBlockSide - 1) / kBlockSide, nby = (ny + kBlockSide - 1) / kBlockSide;
     int64_t nb = nbx * nby;
     unsigned long long base = atomicAdd(&a.hdr->n_big, (unsigned long long)nb);
     if ((int64_t)base + nb <= a.big_cap) {
-        for (int64_t b = 0; b < nb; ++b) a.big[base + b] = make_uint2((uint32_t)t, (uint32_t)b);
+        for (int64_t b = 0; b < nb; ++b)
+            if (LCL_IN((int64_t)base + b, a.big_cap)) a.big[base + b] = make_uint2((uint32_t)t, (uint32_t)b);
     } else {
-        raster_rect(s, (uint32_t)t, i0, i1, j0, j1, a.w, a.tri_plane);  // list full: do it here
+        raster_rect(s, (uint32_t)t, i0, i1, j0, j1, a.w, a.h, a.tri_plane);  // list full: do it here
     }
 }
 
 __global__ void k_raster_big(const uint2 *__restrict__ big, const AtlasHdr *__restrict__ hdr, int64_t cap,
-                             const TriSetup *__restrict__ setup, int32_t w, int32_t h, uint32_t *__restrict__ tri_plane) {
+                             const TriSetup *__restrict__ setup, int64_t n_tri, int32_t w, int32_t h,
+                             uint32_t *__restrict__ tri_plane) {
     int64_t n = min((int64_t)hdr->n_big, cap);
     for (int64_t e = blockIdx.x; e < n; e += gridDim.x) {
+        if (!LCL_IN(e, cap)) break;
         uint2 ent = big[e];
+        if (!LCL_IN(ent.x, n_tri)) continue;
         TriSetup s = setup[ent.x];
         int64_t xmin = min(s.x[0], min(s.x[1], s.x[2])), xmax = max(s.x[0], max(s.x[1], s.x[2]));
         int64_t ymin = min(s.y[0], min(s.y[1], s.y[2])), ymax = max(s.y[0], max(s.y[1], s.y[2]));
@@ -293,7 +302,8 @@ __global__ void k_raster_big(const uint2 *__restrict__ big, const AtlasHdr *__re
         int64_t e0 = edge_fn(X1, Y1, X2, Y2, px, py) + edge_bias(X2 - X1, Y2 - Y1);
         int64_t e1 = edge_fn(X2, Y2, X0, Y0, px, py) + edge_bias(X0 - X2, Y0 - Y2);
         int64_t e2 = edge_fn(X0, Y0, X1, Y1, px, py) + edge_bias(X1 - X0, Y1 - Y0);
-        if (e0 > 0 && e1 > 0 && e2 > 0) atomicMin(tri_plane + j * (int64_t)w + i, ent.x);
+        if (e0 > 0 && e1 > 0 && e2 > 0 && LCL_IN(j * (int64_t)w + i, (int64_t)w * h))
+            atomicMin(tri_plane + j * (int64_t)w + i, ent.x);
     }
 }
 
@@ -328,8 +338,8 @@ __device__ __forceinline__ int32_t interp_axis(int64_t w1, int64_t w2, int64_t A
     return q0 + (int32_t)est;
 }
 
-__global__ void __launch_bounds__(kThreads) k_resolve(const TriSetup *__restrict__ setup, int32_t w, int32_t h,
-                                                      int32_t T, const uint32_t *__restrict__ tri_plane,
+__global__ void __launch_bounds__(kThreads) k_resolve(const TriSetup *__restrict__ setup, int64_t n_tri, int32_t w,
+                                                      int32_t h, int32_t T, const uint32_t *__restrict__ tri_plane,
                                                       int32_t *__restrict__ px, int32_t *__restrict__ py,
                                                       int32_t *__restrict__ pz, uint32_t *__restrict__ cover,
                                                       int32_t *__restrict__ tile_box) {
@@ -341,7 +351,7 @@ __global__ void __launch_bounds__(kThreads) k_resolve(const TriSetup *__restrict
     for (int it = 0; it < iters; ++it) {
         int32_t qd = it * kThreads + threadIdx.x;
         int32_t x = tx * T + 4 * (qd % qpr), y = ty * T + qd / qpr;
-        bool valid = qd < nq && x < w && y < h;
+        bool valid = qd < nq && x < w && y < h && LCL_IN((int64_t)y * w + x + 3, (int64_t)w * h);
         uint32_t nib = 0;
         int64_t l = valid ? (int64_t)y * w + x : 0;
         if (valid) {
@@ -362,6 +372,7 @@ __global__ void __launch_bounds__(kThreads) k_resolve(const TriSetup *__restrict
                 oy[k] = 0;
                 oz[k] = 0;
                 if (tt[k] == kNone) continue;
+                if (!LCL_IN(tt[k], n_tri)) continue;
                 if (tt[k] != cur) {
                     cur = tt[k];
                     s = setup[cur];
@@ -395,7 +406,8 @@ __global__ void __launch_bounds__(kThreads) k_resolve(const TriSetup *__restrict
         uint32_t val = nib << (uint32_t)(l & 31);
         uint32_t peers = __match_any_sync(0xffffffffu, valid ? word : 0xFFFFFFFFu);
         uint32_t orv = __reduce_or_sync(peers, val);
-        if (valid && orv != 0 && (threadIdx.x & 31) == (__ffs(peers) - 1)) atomicOr(cover + word, orv);
+        if (valid && orv != 0 && (threadIdx.x & 31) == (__ffs(peers) - 1) && LCL_IN(word, ((int64_t)w * h + 31) / 32))
+            atomicOr(cover + word, orv);
     }
     // tile box: block reduction
     __shared__ int32_t red[7][kThreads / 32];
@@ -420,9 +432,11 @@ __global__ void __launch_bounds__(kThreads) k_resolve(const TriSetup *__restrict
             v[3] += red[3][j];
             v[4] = max(v[4], red[4][j]); v[5] = max(v[5], red[5][j]); v[6] = max(v[6], red[6][j]);
         }
-        int32_t *b = tile_box + 8 * ((int64_t)ty * gridDim.x + tx);
-        reinterpret_cast<int4 *>(b)[0] = make_int4(v[0], v[1], v[2], v[3]);
-        reinterpret_cast<int4 *>(b)[1] = make_int4(v[4], v[5], v[6], 0);
+        if (LCL_IN((int64_t)ty * gridDim.x + tx, (int64_t)((w + T - 1) / T) * ((h + T - 1) / T))) {
+            int32_t *b = tile_box + 8 * ((int64_t)ty * gridDim.x + tx);
+            reinterpret_cast<int4 *>(b)[0] = make_int4(v[0], v[1], v[2], v[3]);
+            reinterpret_cast<int4 *>(b)[1] = make_int4(v[4], v[5], v[6], 0);
+        }
     }
 }
 
@@ -431,7 +445,7 @@ __global__ void __launch_bounds__(kThreads) k_super(const int32_t *__restrict__ 
     const int32_t sx = blockIdx.x, sy = blockIdx.y;
     const int32_t tx = sx * LCL_SUPER + (threadIdx.x % LCL_SUPER), ty = sy * LCL_SUPER + (threadIdx.x / LCL_SUPER);
     int32_t v[7] = {INT32_MAX, INT32_MAX, INT32_MAX, 0, INT32_MIN, INT32_MIN, INT32_MIN};
-    if (tx < tiles_x && ty < tiles_y) {
+    if (tx < tiles_x && ty < tiles_y && LCL_IN((int64_t)ty * tiles_x + tx, (int64_t)tiles_x * tiles_y)) {
         const int4 *b = reinterpret_cast<const int4 *>(tile_box + 8 * ((int64_t)ty * tiles_x + tx));
         int4 lo = b[0], hi = b[1];
         v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w; v[4] = hi.x; v[5] = hi.y; v[6] = hi.z;
@@ -457,9 +471,13 @@ __global__ void __launch_bounds__(kThreads) k_super(const int32_t *__restrict__ 
             v[3] += red[3][j];
             v[4] = max(v[4], red[4][j]); v[5] = max(v[5], red[5][j]); v[6] = max(v[6], red[6][j]);
         }
-        int4 *b = reinterpret_cast<int4 *>(super_box + 8 * ((int64_t)sy * gridDim.x + sx));
-        b[0] = make_int4(v[0], v[1], v[2], v[3]);
-        b[1] = make_int4(v[4], v[5], v[6], 0);
+        const int64_t n_sup = (int64_t)((tiles_x + LCL_SUPER - 1) / LCL_SUPER) * ((tiles_y + LCL_SUPER - 1) / LCL_SUPER);
+        if (LCL_IN((int64_t)sy * gridDim.x + sx, n_sup)) {
+            int4 *b = reinterpret_cast<int4 *>(super_box + 8 * ((int64_t)sy * gridDim.x + sx));
+            b[0] = make_int4(v[0], v[1], v[2], v[3]);
+            b[1] = make_int4(v[4], v[5], v[6], 0);
+        }
+        (void)n_sup;
     }
 }
 
@@ -528,12 +546,13 @@ lcl_status atlas_build_impl(const lcl_mesh *mesh, lcl_atlas *at, void *ws, size_
         ra.big = big;
         ra.big_cap = (int64_t)big_capacity(mesh->n_tri, at->width, at->height);
         k_raster<<<(unsigned)((mesh->n_tri + 127) / 128), 128, 0, st>>>(ra);
-        k_raster_big<<<sms * 8, kThreads, 0, st>>>(big, hdr, ra.big_cap, setup, at->width, at->height, at->tri);
+        k_raster_big<<<sms * 8, kThreads, 0, st>>>(big, hdr, ra.big_cap, setup, mesh->n_tri, at->width, at->height,
+                                                   at->tri);
         count_launches(2);
     }
     dim3 tg(at->tiles_x, at->tiles_y);
-    k_resolve<<<tg, kThreads, 0, st>>>(setup, at->width, at->height, at->tile, at->tri, at->pos_x, at->pos_y,
-                                       at->pos_z, at->cover, at->tile_box);
+    k_resolve<<<tg, kThreads, 0, st>>>(setup, mesh->n_tri, at->width, at->height, at->tile, at->tri, at->pos_x,
+                                       at->pos_y, at->pos_z, at->cover, at->tile_box);
     dim3 sg(at->supers_x, at->supers_y);
     k_super<<<sg, kThreads, 0, st>>>(at->tile_box, at->tiles_x, at->tiles_y, at->super_box);
     count_launches(2);

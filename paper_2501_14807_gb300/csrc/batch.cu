@@ -69,6 +69,19 @@ struct BItem {
     unsigned long long mask;
 };
 
+// Capacities of a workspace's arrays (its limits), for the kernels' index checks.
+struct BCaps {
+    int32_t models, strokes, lassos, pad;
+    int64_t supers, tiles;
+};
+
+// Can the stroke's descriptors be read: its index within the strokes and, for a lasso, the lasso's
+// within the lassos (the debug build's checks; always true otherwise).
+__device__ __forceinline__ bool stroke_in_bounds(const BStroke *strokes, int64_t si, const BCaps &caps) {
+    if (!LCL_IN(si, caps.strokes)) return false;
+    return strokes[si].kind == LCL_STROKE_SPHERE || LCL_IN(strokes[si].lasso, caps.lassos);
+}
+
 // Workspace header (first 256 bytes), uploaded with the descriptors; the counters are reset by
 // k_batch_prep at every launch.
 struct BHdr {
@@ -117,6 +130,7 @@ __device__ __forceinline__ bool stroke_may_reach(const BStroke &st, const BLasso
     const int32_t r = pad ? 1 : 0;
     for (int32_t y = max(by - r, 0); y <= min(by + r, ny - 1); ++y)
         for (int32_t x = max(bx - r, 0); x <= min(bx + r, nx - 1); ++x) {
+            if (!LCL_IN((int64_t)y * nx + x, (int64_t)nx * ny)) continue;
             const int4 *b = reinterpret_cast<const int4 *>(boxes + 8 * ((int64_t)y * nx + x));
             if (stroke_may_touch(st, lassos, b[0], b[1])) return true;
         }
@@ -130,7 +144,7 @@ static_assert(kBands == 32, "k_batch_prep gives each y-band one lane");
 // head (bounding boxes, band mapping), then lane b counts and lists the edges of band b (the
 // same predicate, in the same edge order, as the host builder).
 __global__ void __launch_bounds__(kThreads) k_batch_prep(BHdr *hdr, const BLassoIn *__restrict__ in,
-                                                         BLasso *__restrict__ out) {
+                                                         BLasso *__restrict__ out, BCaps caps) {
     pdl_allow_next();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         hdr->n_items = 0;
@@ -139,6 +153,8 @@ __global__ void __launch_bounds__(kThreads) k_batch_prep(BHdr *hdr, const BLasso
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * kPrepWarps + (int)(threadIdx.x / 32);
     if (j >= hdr->n_lassos) return;  // uniform over the warp
+    if (!LCL_IN(j, caps.lassos)) return;
+    (void)caps;
     const BLassoIn &L = in[j];
     LassoArg &p = out[j].arg;
     if (lane == 0) {
@@ -168,21 +184,24 @@ __global__ void __launch_bounds__(kThreads) k_batch_cull(const BHdr *__restrict_
                                                          const BStroke *__restrict__ strokes,
                                                          const BLasso *__restrict__ lassos,
                                                          const uint32_t *__restrict__ super_model, BItem *items,
-                                                         unsigned int *n_items) {
+                                                         unsigned int *n_items, BCaps caps) {
     pdl_wait();
     pdl_allow_next();
     __shared__ unsigned long long s_mask;
     const int32_t n_supers = hdr->n_supers;
     for (int32_t g = blockIdx.x; g < n_supers; g += gridDim.x) {
+        if (!LCL_IN(g, caps.supers)) break;  // uniform over the CTA
         const uint32_t mi = super_model[g];
+        if (!LCL_IN(mi, caps.models)) continue;
         const BModel &M = models[mi];
         const AtlasDev &a = M.a;
         const int32_t sidx = g - M.super0;
+        if (!LCL_IN(sidx, (int64_t)a.supers_x * a.supers_y)) continue;
         if (threadIdx.x == 0) s_mask = 0ull;
         __syncthreads();
         const int32_t sx = sidx % a.supers_x, sy = sidx / a.supers_x;
         // strokes that can reach the super-tile, one thread per stroke (ns <= 64)
-        if (threadIdx.x < (unsigned)M.ns &&
+        if (threadIdx.x < (unsigned)M.ns && stroke_in_bounds(strokes, (int64_t)M.s0 + threadIdx.x, caps) &&
             stroke_may_reach(strokes[M.s0 + threadIdx.x], lassos, a.super_box, a.supers_x, a.supers_y, sx, sy))
             atomicOr(&s_mask, 1ull << threadIdx.x);
         __syncthreads();
@@ -195,7 +214,8 @@ __global__ void __launch_bounds__(kThreads) k_batch_cull(const BHdr *__restrict_
         if (tx < a.tiles_x && ty < a.tiles_y) {
             for (unsigned long long m = smask; m; m &= m - 1) {
                 const int k = __ffsll((long long)m) - 1;
-                if (stroke_may_reach(strokes[M.s0 + k], lassos, a.tile_box, a.tiles_x, a.tiles_y, tx, ty))
+                if (stroke_in_bounds(strokes, (int64_t)M.s0 + k, caps) &&
+                    stroke_may_reach(strokes[M.s0 + k], lassos, a.tile_box, a.tiles_x, a.tiles_y, tx, ty))
                     mask |= 1ull << k;
             }
         }
@@ -206,12 +226,13 @@ __global__ void __launch_bounds__(kThreads) k_batch_cull(const BHdr *__restrict_
             uint32_t base = 0;
             if (lane == __ffs(bal) - 1) base = atomicAdd(n_items, (unsigned)__popc(bal));
             base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
-            if (cand) {
+            const uint32_t slot = base + __popc(bal & ((1u << lane) - 1));
+            if (cand && LCL_IN(slot, caps.tiles)) {
                 BItem it;
                 it.model = mi;
                 it.tile = (uint32_t)(ty * a.tiles_x + tx);
                 it.mask = mask;
-                items[base + __popc(bal & ((1u << lane) - 1))] = it;
+                items[slot] = it;
             }
         }
     }
@@ -264,7 +285,7 @@ __device__ __forceinline__ bool stroke_selects(const AtlasDev &a, const BStroke 
 // (a texel it selects within its radius) both hold gives the label.  Returns the texels written.
 __device__ __noinline__ uint32_t pad_texels(const AtlasDev &a, int64_t l, uint32_t unc, unsigned long long mask, int32_t s0,
                                const BStroke *__restrict__ strokes, const BLasso *__restrict__ lassos,
-                               uint32_t lab[4]) {
+                               uint32_t lab[4], const BCaps &caps) {
     const int32_t x0 = (int32_t)(l % a.w), y0 = (int32_t)(l / a.w);
     uint32_t written = 0u;
 #pragma unroll 1
@@ -273,6 +294,7 @@ __device__ __noinline__ uint32_t pad_texels(const AtlasDev &a, int64_t l, uint32
         for (unsigned long long m = mask; m; ) {
             const int si = 63 - __clzll((long long)m);  // newest stroke left
             m &= ~(1ull << si);
+            if (!stroke_in_bounds(strokes, (int64_t)s0 + si, caps)) continue;
             const BStroke &st = strokes[s0 + si];
             const int32_t pr = st.kind == LCL_STROKE_SPHERE ? st.sphere.pad_r : lassos[st.lasso].pad_r;
             if (pr == 0) continue;
@@ -286,6 +308,7 @@ __device__ __noinline__ uint32_t pad_texels(const AtlasDev &a, int64_t l, uint32
                     const int32_t xx = x0 + k + dx;
                     if (xx < 0 || xx >= a.w) continue;
                     const int64_t n = (int64_t)yy * a.w + xx;
+                    if (!LCL_IN(n, (int64_t)a.w * a.h)) continue;
                     const int32_t qx = __ldg(a.px + n);
                     if (qx == INT32_MIN) continue;
                     const int32_t ax = abs(dx), ay = abs(dy);
@@ -307,15 +330,18 @@ __device__ __noinline__ uint32_t pad_texels(const AtlasDev &a, int64_t l, uint32
 // the tile), one per thread per pass.
 template <typename L>
 __device__ __forceinline__ void apply_part(const BModel &M, const BItem &it, int32_t q0, int32_t q1,
-                                           const BStroke *__restrict__ strokes, const BLasso *__restrict__ lassos) {
+                                           const BStroke *__restrict__ strokes, const BLasso *__restrict__ lassos,
+                                           const BCaps &caps) {
     const AtlasDev &a = M.a;
     L *layer = static_cast<L *>(M.layer);
+    if (!LCL_IN(it.tile, (int64_t)a.tiles_x * a.tiles_y)) return;
     const int32_t tx = it.tile % a.tiles_x, ty = it.tile / a.tiles_x;
     const int32_t qpr = a.T / 4;
     for (int32_t qd = q0 + (int32_t)threadIdx.x; qd < q1; qd += (int32_t)blockDim.x) {
         const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
         if (x >= a.w || y >= a.h) continue;
         const int64_t l = (int64_t)y * a.w + x;
+        if (!LCL_IN(l + 3, (int64_t)a.w * a.h)) continue;
         const int4 X = __ldg(reinterpret_cast<const int4 *>(a.px + l));
         const int4 Y = __ldg(reinterpret_cast<const int4 *>(a.py + l));
         const int4 Z = __ldg(reinterpret_cast<const int4 *>(a.pz + l));
@@ -328,6 +354,7 @@ __device__ __forceinline__ void apply_part(const BModel &M, const BItem &it, int
         for (unsigned long long m = it.mask; m && open; ) {
             const int si = 63 - __clzll((long long)m);  // newest stroke left
             m &= ~(1ull << si);
+            if (!stroke_in_bounds(strokes, (int64_t)M.s0 + si, caps)) continue;
             const BStroke &st = strokes[M.s0 + si];
             uint32_t sel = 0u;
             if (st.kind == LCL_STROKE_SPHERE) {
@@ -368,7 +395,7 @@ __device__ __forceinline__ void apply_part(const BModel &M, const BItem &it, int
 #pragma unroll
         for (int k = 0; k < 4; ++k) unc |= (xs[k] == INT32_MIN ? 1u : 0u) << k;
         if (unc) {
-            const uint32_t ph = pad_texels(a, l, unc, it.mask, M.s0, strokes, lassos, lab);
+            const uint32_t ph = pad_texels(a, l, unc, it.mask, M.s0, strokes, lassos, lab, caps);
             hit |= ph;
         }
         if (hit) store_labels<L>(layer, l, hit, lab);
@@ -379,7 +406,7 @@ __global__ void __launch_bounds__(256, 3) k_batch_apply(const BHdr *__restrict__
                                                      const BStroke *__restrict__ strokes,
                                                      const BLasso *__restrict__ lassos,
                                                      const BItem *__restrict__ items, unsigned long long *next_unit,
-                                                     int32_t split) {
+                                                     int32_t split, BCaps caps) {
     pdl_wait();
     pdl_allow_next();
     __shared__ unsigned long long s_unit;
@@ -390,14 +417,16 @@ __global__ void __launch_bounds__(256, 3) k_batch_apply(const BHdr *__restrict__
         const unsigned long long u = s_unit;
         __syncthreads();
         if (u >= n_units) break;  // uniform over the CTA
+        if (!LCL_IN(u / (unsigned)split, caps.tiles)) continue;
         const BItem it = items[u / (unsigned)split];
         const int32_t part = (int32_t)(u % (unsigned)split);
+        if (!LCL_IN(it.model, caps.models)) continue;
         const BModel &M = models[it.model];
         const int32_t nq = M.a.T * (M.a.T / 4), per = nq / split;  // nq is a power of 2 >= 16
         if (M.dtype_bytes == 1)
-            apply_part<uint8_t>(M, it, part * per, (part + 1) * per, strokes, lassos);
+            apply_part<uint8_t>(M, it, part * per, (part + 1) * per, strokes, lassos, caps);
         else
-            apply_part<uint16_t>(M, it, part * per, (part + 1) * per, strokes, lassos);
+            apply_part<uint16_t>(M, it, part * per, (part + 1) * per, strokes, lassos, caps);
     }
 }
 
@@ -510,19 +539,26 @@ BPtrs b_ptrs(const BLayout &L, void *ws) {
 }
 
 cudaError_t launch_kernels(const BPtrs &p, const lcl_batch_limits &lim, const lcl_batch_config &c, cudaStream_t st) {
+    BCaps caps;
+    caps.models = lim.models;
+    caps.strokes = lim.strokes;
+    caps.lassos = lim.lassos;
+    caps.pad = 0;
+    caps.supers = lim.supers;
+    caps.tiles = lim.tiles;
     const int pg = (std::max(lim.lassos, 1) + kPrepWarps - 1) / kPrepWarps;
-    k_batch_prep<<<pg, kThreads, 0, st>>>(p.hdr, p.lasso_in, p.lassos);
+    k_batch_prep<<<pg, kThreads, 0, st>>>(p.hdr, p.lasso_in, p.lassos, caps);
     cudaError_t e = cudaSuccess;
     if (lim.supers > 0) {
         const int cg = (int)std::min<int64_t>(lim.supers, resident_grid(k_batch_cull));
         e = launch_pdl(k_batch_cull, dim3(cg), st, (const BHdr *)p.hdr, p.models, p.strokes, p.lassos, p.super_model,
-                       p.items, &p.hdr->n_items);
+                       p.items, &p.hdr->n_items, caps);
         if (e == cudaSuccess) {
             const int fit = resident_per_sm(k_batch_apply, c.threads);
             const int per_sm = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, fit) : fit;
             e = launch_pdl_shape(k_batch_apply, dim3(per_sm * sm_count()), dim3(c.threads), st, (const BHdr *)p.hdr,
                                  p.models, p.strokes, p.lassos, (const BItem *)p.items, &p.hdr->next_unit,
-                                 (int32_t)c.split);
+                                 (int32_t)c.split, caps);
         }
     }
     count_launches(lim.supers > 0 ? 3 : 1);

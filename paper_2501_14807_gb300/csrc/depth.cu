@@ -62,6 +62,7 @@ __global__ void k_vertex(const float *__restrict__ pos, int64_t n_pos, const Mat
                          float mn2, double scale, float fw, float fh, PVert *__restrict__ out) {
     const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (v >= n_pos) return;
+    if (!LCL_IN(3 * v + 2, 3 * n_pos)) return;
     const float *m = mat.v;
     PVert r;
     r.X = INT32_MIN;
@@ -88,6 +89,7 @@ __global__ void k_vertex(const float *__restrict__ pos, int64_t n_pos, const Mat
 // Triangle t from its projected corners; false if it is dropped (bad index, a dropped corner, or
 // zero screen area).  Corners are counter-clockwise on return.
 __device__ bool depth_setup(const DepthArgs &a, int64_t t, DTri &d) {
+    if (!LCL_IN(3 * t + 2, 3 * a.n_tri)) return false;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const uint32_t ip = a.tri_pos[3 * t + k];
@@ -125,7 +127,7 @@ __device__ __forceinline__ void pixel_range(const DTri &d, int32_t w, int32_t h,
 }
 
 // Depth of the pixel centre (px, py) if covered; writes it with atomicMin.
-__device__ __forceinline__ void depth_pixel(const DTri &d, int64_t i, int64_t j, int32_t w, uint32_t *depth) {
+__device__ __forceinline__ void depth_pixel(const DTri &d, int64_t i, int64_t j, int32_t w, int32_t h, uint32_t *depth) {
     const int64_t px = 256 * i + 128, py = 256 * j + 128;
     const int64_t w0 = edge_fn(d.X[1], d.Y[1], d.X[2], d.Y[2], px, py);
     const int64_t w1 = edge_fn(d.X[2], d.Y[2], d.X[0], d.Y[0], px, py);
@@ -138,13 +140,15 @@ __device__ __forceinline__ void depth_pixel(const DTri &d, int64_t i, int64_t j,
                                  __dmul_rn(__ll2double_rn(w2), (double)d.Z[2]));
     float z = __double2float_rn(__ddiv_rn(num, __ll2double_rn(d.A)));
     z = __fadd_rn(z, 0.0f);  // no negative zero
+    if (!LCL_IN(j * (int64_t)w + i, (int64_t)w * h)) return;
     atomicMin(depth + j * (int64_t)w + i, __float_as_uint(z));
+    (void)h;
 }
 
 __global__ void k_clear(uint32_t *__restrict__ depth, int64_t n) {
     const uint32_t inf = 0x7F800000u;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        depth[i] = inf;
+        if (LCL_IN(i, n)) depth[i] = inf;
 }
 
 __global__ void k_hdr_reset(DepthHdr *hdr) { hdr->n_big = 0; }
@@ -162,14 +166,15 @@ __global__ void k_raster(const __grid_constant__ DepthArgs a) {
         const int64_t nb = ((nx + kBlockSide - 1) / kBlockSide) * ((ny + kBlockSide - 1) / kBlockSide);
         const unsigned long long base = atomicAdd(&a.hdr->n_big, (unsigned long long)nb);
         if ((int64_t)base + nb <= a.big_cap) {
-            for (int64_t b = 0; b < nb; ++b) a.big[base + b] = make_uint2((uint32_t)t, (uint32_t)b);
+            for (int64_t b = 0; b < nb; ++b)
+                if (LCL_IN((int64_t)base + b, a.big_cap)) a.big[base + b] = make_uint2((uint32_t)t, (uint32_t)b);
             return;
         }
     }
 #pragma unroll 1
     for (int64_t j = j0; j <= j1; ++j)
 #pragma unroll 1
-        for (int64_t i = i0; i <= i1; ++i) depth_pixel(d, i, j, a.w, a.depth);
+        for (int64_t i = i0; i <= i1; ++i) depth_pixel(d, i, j, a.w, a.h, a.depth);
 }
 
 __global__ void __launch_bounds__(kThreads) k_raster_big(const __grid_constant__ DepthArgs a) {
@@ -177,6 +182,7 @@ __global__ void __launch_bounds__(kThreads) k_raster_big(const __grid_constant__
     __shared__ int ok;
     const int64_t n = min((int64_t)a.hdr->n_big, a.big_cap);
     for (int64_t e = blockIdx.x; e < n; e += gridDim.x) {
+        if (!LCL_IN(e, a.big_cap)) break;  // uniform over the CTA
         const uint2 ent = a.big[e];
         if (threadIdx.x == 0) ok = depth_setup(a, ent.x, sd) ? 1 : 0;
         __syncthreads();
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) k_raster_big(const __grid_constant__
             const int64_t bx = ent.y % nbx, by = ent.y / nbx;
             const int64_t i = i0 + bx * kBlockSide + (threadIdx.x % kBlockSide);
             const int64_t j = j0 + by * kBlockSide + (threadIdx.x / kBlockSide);
-            if (i <= i1 && j <= j1) depth_pixel(d, i, j, a.w, a.depth);
+            if (i <= i1 && j <= j1) depth_pixel(d, i, j, a.w, a.h, a.depth);
         }
         __syncthreads();
     }

@@ -58,8 +58,11 @@ __global__ void __launch_bounds__(kThreads) k_overlay(const uint32_t *__restrict
                                                       int64_t n_words, int op, uint32_t flags) {
     constexpr int kLanes = 4 / BYTES;  // texels per 32-bit word
     const int64_t n_vec = n_words / 4;
+    const int64_t n_cover = (n_words * kLanes + 31) / 32;  // coverage words of the texture
+    (void)n_cover;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n_vec; v += stride) {
+        if (!LCL_IN(4 * v + 3, n_words) || !LCL_IN((v * 4 * kLanes) >> 5, n_cover)) continue;
         const uint4 A = __ldcs(reinterpret_cast<const uint4 *>(a) + v);
         const uint4 B = __ldcs(reinterpret_cast<const uint4 *>(b) + v);
         const int64_t t0 = v * 4 * kLanes;  // first texel of this 16-byte chunk
@@ -73,7 +76,7 @@ __global__ void __launch_bounds__(kThreads) k_overlay(const uint32_t *__restrict
     }
     // tail: the last n_words % 4 words
     const int64_t w = n_vec * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (w < n_words) {
+    if (w < n_words && LCL_IN(w, n_words) && LCL_IN((w * kLanes) >> 5, n_cover)) {
         const int64_t t0 = w * kLanes;
         const uint32_t cw = (cover[t0 >> 5] >> (t0 & 31)) & ((1u << kLanes) - 1);
         out[w] = overlay_word(a[w], b[w], cw, op, flags, BYTES);
@@ -96,6 +99,7 @@ struct Run {
 template <bool SMEM>
 __device__ __forceinline__ void flush(const Run &r, unsigned long long *hc, unsigned long long *ha, uint32_t n_labels) {
     if (r.cnt == 0) return;
+    if (!LCL_IN(r.label, n_labels)) return;
     atomicAdd(hc + r.label, (unsigned long long)r.cnt);
     atomicAdd(ha + r.label, r.area);
     (void)n_labels;
@@ -103,9 +107,11 @@ __device__ __forceinline__ void flush(const Run &r, unsigned long long *hc, unsi
 
 template <typename L, bool SMEM>
 __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ layer, const uint32_t *__restrict__ tri,
-                                                      const uint64_t *__restrict__ area_w, int64_t n_texels,
-                                                      uint32_t n_labels, unsigned long long *__restrict__ count,
+                                                      const uint64_t *__restrict__ area_w, int64_t n_tri,
+                                                      int64_t n_texels, uint32_t n_labels,
+                                                      unsigned long long *__restrict__ count,
                                                       unsigned long long *__restrict__ area) {
+    (void)n_tri;
     extern __shared__ unsigned long long sh[];
     unsigned long long *hc = SMEM ? sh : count;
     unsigned long long *ha = SMEM ? sh + n_labels : area;
@@ -120,6 +126,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ laye
     // a lane's run is flushed by itself only when the label changes inside its chunk
     auto visit = [&](uint32_t lab, uint32_t t) {
         if (t == kNone || lab >= n_labels) return;
+        if (!LCL_IN(t, n_tri)) return;
         if (t != last_t) {
             last_t = t;
             last_w = __ldg(aw + t);
@@ -146,6 +153,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ laye
     const int64_t it0 = warp * per, it1 = min(n_iter, it0 + per);
     uint4 T4[4], V[LW];
     auto load = [&](int64_t c) {
+        if (!LCL_IN(16 * c + 15, n_texels)) return;
         const uint4 *tp = reinterpret_cast<const uint4 *>(tri + 16 * c);
 #pragma unroll
         for (int k = 0; k < 4; ++k) T4[k] = __ldcs(tp + k);
@@ -191,7 +199,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ laye
                 tc += __shfl_xor_sync(0xffffffffu, tc, o);
                 ta += __shfl_xor_sync(0xffffffffu, ta, o);
             }
-            if (lane == 0 && tc) {
+            if (lane == 0 && tc && LCL_IN(wlabel, n_labels)) {
                 atomicAdd(hc + wlabel, tc);
                 atomicAdd(ha + wlabel, ta);
             }
@@ -201,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ laye
             const uint32_t cnt = __reduce_add_sync(peers, run.cnt);
             const uint32_t lo = __reduce_add_sync(peers, (uint32_t)(run.area & 0xFFFFFu));
             const uint32_t hi = __reduce_add_sync(peers, (uint32_t)(run.area >> 20));
-            if (key != kNone && lane == __ffs(peers) - 1) {
+            if (key != kNone && lane == __ffs(peers) - 1 && LCL_IN(key, n_labels)) {
                 atomicAdd(hc + key, (unsigned long long)cnt);
                 atomicAdd(ha + key, (unsigned long long)lo + ((unsigned long long)hi << 20));
             }
@@ -217,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ laye
             tc += __shfl_xor_sync(0xffffffffu, tc, o);
             ta += __shfl_xor_sync(0xffffffffu, ta, o);
         }
-        if (lane == 0 && tc) {
+        if (lane == 0 && tc && LCL_IN(wlabel, n_labels)) {
             atomicAdd(hc + wlabel, tc);
             atomicAdd(ha + wlabel, ta);
         }
@@ -225,7 +233,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ laye
     // tail texels (n_texels % 16), one per thread
     for (int64_t t = n_chunks * 16 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_texels;
          t += (int64_t)gridDim.x * blockDim.x)
-        visit((uint32_t)layer[t], tri[t]);
+        if (LCL_IN(t, n_texels)) visit((uint32_t)layer[t], tri[t]);
     flush<SMEM>(run, hc, ha, n_labels);
     if (SMEM) {
         __syncthreads();
@@ -276,16 +284,17 @@ lcl_status label_area_impl(const lcl_atlas *atlas, const void *layer, int dtype_
     const uint32_t *tri = atlas->tri;
     if (dtype_bytes == 1) {
         const uint8_t *l = static_cast<const uint8_t *>(layer);
-        if (smem) k_area<uint8_t, true><<<fit(k_area<uint8_t, true>), kThreads, shb, st>>>(l, tri, atlas->area_w, n_tex,
-                                                                                          n_labels, c, ar);
-        else k_area<uint8_t, false><<<fit(k_area<uint8_t, false>), kThreads, 0, st>>>(l, tri, atlas->area_w, n_tex,
-                                                                                      n_labels, c, ar);
+        if (smem) k_area<uint8_t, true><<<fit(k_area<uint8_t, true>), kThreads, shb, st>>>(l, tri, atlas->area_w, atlas->n_tri,
+                                                                                          n_tex, n_labels, c, ar);
+        else k_area<uint8_t, false><<<fit(k_area<uint8_t, false>), kThreads, 0, st>>>(l, tri, atlas->area_w, atlas->n_tri,
+                                                                                      n_tex, n_labels, c, ar);
     } else {
         const uint16_t *l = static_cast<const uint16_t *>(layer);
         if (smem) k_area<uint16_t, true><<<fit(k_area<uint16_t, true>), kThreads, shb, st>>>(l, tri, atlas->area_w,
-                                                                                            n_tex, n_labels, c, ar);
-        else k_area<uint16_t, false><<<fit(k_area<uint16_t, false>), kThreads, 0, st>>>(l, tri, atlas->area_w, n_tex,
-                                                                                        n_labels, c, ar);
+                                                                                            atlas->n_tri, n_tex,
+                                                                                            n_labels, c, ar);
+        else k_area<uint16_t, false><<<fit(k_area<uint16_t, false>), kThreads, 0, st>>>(l, tri, atlas->area_w, atlas->n_tri,
+                                                                                        n_tex, n_labels, c, ar);
     }
     count_launches(2);
     cudaError_t e = cudaGetLastError();

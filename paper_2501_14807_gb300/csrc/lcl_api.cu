@@ -5,8 +5,11 @@
 #include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "lcl_impl.cuh"
 
@@ -41,6 +44,27 @@ int sm_count() {
 }
 
 void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+// Readers of the bounds-check records, one per module of the debug build (empty otherwise).
+namespace {
+std::vector<BoundsReader> &bounds_readers() {
+    static std::vector<BoundsReader> r;
+    return r;
+}
+std::mutex &bounds_mu() {
+    static std::mutex m;
+    return m;
+}
+
+// Source files whose checks can report, for decoding a site's file hash.
+const char *const kSourceNames[] = {"atlas.cu", "batch.cu", "depth.cu", "layers.cu", "numeric.cu", "select.cu",
+                                    "noalloc.cu", "lcl_api.cu", "pool.cu", "select_common.cuh", "lcl_impl.cuh"};
+}  // namespace
+
+void register_bounds_reader(BoundsReader reader) {
+    std::lock_guard<std::mutex> lock(bounds_mu());
+    bounds_readers().push_back(reader);
+}
 
 
 namespace {
@@ -619,6 +643,57 @@ const char *lcl_status_str(lcl_status status) {
 }
 
 const char *lcl_last_error(void) { return g_last_error.c_str(); }
+
+uint32_t lcl_build_flags(void) {
+#ifdef LCL_DEBUG_BOUNDS
+    return LCL_BUILD_BOUNDS_CHECKS;
+#else
+    return 0u;
+#endif
+}
+
+size_t lcl_describe_site(uint32_t site, char *buf, size_t n) {
+    const uint32_t h = site >> 16, line = site & 0xFFFFu;
+    const char *name = nullptr;
+    for (const char *cand : kSourceNames)
+        if (file_hash16(cand) == h) name = cand;
+    char tmp[64];
+    if (name) std::snprintf(tmp, sizeof(tmp), "%s:%u", name, line);
+    else std::snprintf(tmp, sizeof(tmp), "file#%04x:%u", h, line);
+    const size_t len = std::strlen(tmp);
+    if (buf && n) {
+        std::strncpy(buf, tmp, n - 1);
+        buf[n - 1] = '\0';
+    }
+    return len;
+}
+
+lcl_status lcl_last_device_status(lcl_stream stream) {
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "lcl_last_device_status: the stream reported an error");
+    std::vector<BoundsReader> readers;
+    {
+        std::lock_guard<std::mutex> lock(bounds_mu());
+        readers = bounds_readers();
+    }
+    BoundsRecord first = {0, 0, 0, 0};
+    unsigned long long total = 0;
+    for (BoundsReader r : readers) {
+        BoundsRecord rec;
+        e = r(st, &rec);
+        if (e != cudaSuccess) return cuda_fail(e, "lcl_last_device_status: reading a bounds record");
+        if (rec.count && !total) first = rec;
+        total += rec.count;
+    }
+    if (!total) return LCL_OK;
+    char where[64];
+    lcl_describe_site((uint32_t)first.site, where, sizeof(where));
+    char msg[256];
+    std::snprintf(msg, sizeof(msg), "bounds check at %s: index %lld outside [0, %llu); %llu out-of-range accesses skipped",
+                  where, (long long)first.index, first.extent, total);
+    return fail(LCL_ERR_INTERNAL, msg);
+}
 
 uint64_t lcl_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 

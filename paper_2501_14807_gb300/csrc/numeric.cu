@@ -117,9 +117,9 @@ __global__ void __launch_bounds__(kThreads) k_num_arith(ArithArgs p) {
     // whole warps iterate together (the group merge uses shuffles over the full warp)
     const int64_t n_iter = (p.n_chunks + 31) & ~int64_t(31);
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c - (threadIdx.x & 31) < n_iter; c += stride) {
-        const bool live = c < p.n_chunks;
-        uint32_t bits = 0;
         int64_t t0 = c * kPer;
+        const bool live = c < p.n_chunks && LCL_IN(t0 + kPer - 1, p.n_texels);
+        uint32_t bits = 0;
         if (live) {
             const uint4 A = __ldcs(p.a + c);
             uint4 B;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kThreads) k_num_arith(ArithArgs p) {
     // the last n_texels % 32 texels (one partial mask word), by the grid's first thread
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const int64_t t_begin = (p.n_texels >> 5) << 5;
-        if (t_begin < p.n_texels) {
+        if (t_begin < p.n_texels && LCL_IN(t_begin >> 5, (p.n_texels + 31) >> 5)) {
             const uint32_t word = (uint32_t)(t_begin >> 5);
             uint32_t valid = p.ma[word] & p.cover[word];
             if (p.b) valid &= p.mb[word];
@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(kThreads) k_num_select(SelectArgs p) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     uint32_t cnt = 0;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < p.n_chunks; c += stride) {
+        if (!LCL_IN(c * kPer + kPer - 1, p.n_texels)) continue;
         const uint4 D = __ldcs(p.data + c);
         const int64_t t0 = c * kPer;
         const uint32_t word = (uint32_t)(t0 >> 5);
@@ -281,6 +282,7 @@ __global__ void __launch_bounds__(kThreads) k_num_select(SelectArgs p) {
     // tail texels after the whole chunks (fewer than 16 / S), by the grid's first thread
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int64_t t = p.n_chunks * kPer; t < p.n_texels; ++t) {
+            if (!LCL_IN(t, p.n_texels)) break;
             const uint32_t word = (uint32_t)(t >> 5);
             if (!(((p.mask[word] & p.cover[word]) >> (t & 31)) & 1u)) continue;
             uint32_t v;
@@ -430,8 +432,10 @@ __device__ __forceinline__ void acc_add(ZoneAcc *z, unsigned long long cnt, unsi
 }
 
 template <int S, int KIND>
-__device__ __forceinline__ void flush_run(const StatsRun &r, ZoneAcc *tab) {
+__device__ __forceinline__ void flush_run(const StatsRun &r, ZoneAcc *tab, uint32_t n_zones) {
     if (r.cnt == 0) return;
+    if (!LCL_IN(r.zone, n_zones)) return;
+    (void)n_zones;
     acc_add(tab + r.zone, r.cnt, r.area, dkey(key_value<S, KIND>(r.kmin)), dkey(key_value<S, KIND>(r.kmax)), r.sum,
             r.wsum);
 }
@@ -451,7 +455,8 @@ __device__ __forceinline__ double warp_sum_f64(double x) {
 // Adds the runs of the lanes with `take` set (all of one zone) into zone `zone` of `tab`: one warp
 // reduction per field, the atomics by lane `writer`.  Every lane of the warp calls it.
 template <int S, int KIND>
-__device__ __forceinline__ void warp_flush(const StatsRun &r, bool take, uint32_t zone, int writer, ZoneAcc *tab) {
+__device__ __forceinline__ void warp_flush(const StatsRun &r, bool take, uint32_t zone, int writer, ZoneAcc *tab,
+                                           uint32_t n_zones) {
     const bool t = take && r.cnt;
     const unsigned long long cnt = warp_sum_u64(t ? r.cnt : 0u);
     if (cnt == 0) return;  // uniform
@@ -460,8 +465,9 @@ __device__ __forceinline__ void warp_flush(const StatsRun &r, bool take, uint32_
     const uint32_t kmax = __reduce_max_sync(0xffffffffu, t ? r.kmax : 0u);
     const double sum = warp_sum_f64(t ? r.sum : 0.0);
     const double wsum = warp_sum_f64(t ? r.wsum : 0.0);
-    if ((int)(threadIdx.x & 31) == writer)
+    if ((int)(threadIdx.x & 31) == writer && LCL_IN(zone, n_zones))
         acc_add(tab + zone, cnt, area, dkey(key_value<S, KIND>(kmin)), dkey(key_value<S, KIND>(kmax)), sum, wsum);
+    (void)n_zones;
 }
 
 struct StatsArgs {
@@ -471,6 +477,7 @@ struct StatsArgs {
     const void *zones;  // NULL: one zone
     uint32_t n_labels;
     int64_t n_texels;
+    int64_t n_tri;
     ZoneAcc *out;
 };
 
@@ -548,9 +555,10 @@ __global__ void __launch_bounds__(kThreads) k_num_stats(StatsArgs p) {
         }
         if (z != run.zone && run.cnt) {
             close_tri();
-            flush_run<S, KIND>(run, tab);
+            flush_run<S, KIND>(run, tab, p.n_labels);
             run_reset(run);
         }
+        if (!LCL_IN(t, p.n_tri)) return;
         run.zone = z;
         if (t != last_t) {
             close_tri();
@@ -579,7 +587,7 @@ __global__ void __launch_bounds__(kThreads) k_num_stats(StatsArgs p) {
     uint32_t wzone = kNone;
     for (int64_t it = it0; it < it1; ++it) {
         const int64_t c = it * 32 + lane;
-        if (c < n_chunks) {
+        if (c < n_chunks && LCL_IN(16 * c + 15, p.n_texels)) {
             const int64_t t = 16 * c;
             uint32_t v[16];
             load16<S>(p.data, t, v);
@@ -619,7 +627,7 @@ __global__ void __launch_bounds__(kThreads) k_num_stats(StatsArgs p) {
         if (__all_sync(0xffffffffu, key == wzone || key == kNone)) {
             if (run.cnt) run_merge(wrun, run);
         } else {
-            warp_flush<S, KIND>(wrun, true, wzone, 0, tab);
+            warp_flush<S, KIND>(wrun, true, wzone, 0, tab, p.n_labels);
             run_reset(wrun);
             // this iteration's chunk runs, zone by zone
             unsigned left = __ballot_sync(0xffffffffu, key != kNone);
@@ -627,17 +635,18 @@ __global__ void __launch_bounds__(kThreads) k_num_stats(StatsArgs p) {
                 const int leader = __ffs(left) - 1;
                 const uint32_t zk = __shfl_sync(0xffffffffu, key, leader);
                 const bool mine = key == zk;
-                warp_flush<S, KIND>(run, mine, zk, leader, tab);
+                warp_flush<S, KIND>(run, mine, zk, leader, tab, p.n_labels);
                 left &= ~__ballot_sync(0xffffffffu, mine);
             }
             wzone = __shfl_sync(0xffffffffu, key, 31);
         }
         run_reset(run);
     }
-    warp_flush<S, KIND>(wrun, true, wzone, 0, tab);
+    warp_flush<S, KIND>(wrun, true, wzone, 0, tab, p.n_labels);
     // tail texels (n_texels % 16), one per thread
     for (int64_t t = n_chunks * 16 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < p.n_texels;
          t += (int64_t)gridDim.x * blockDim.x) {
+        if (!LCL_IN(t, p.n_texels)) break;
         uint32_t bits, z = 0;
         if (S == 1) bits = static_cast<const uint8_t *>(p.data)[t];
         else if (S == 2) bits = static_cast<const uint16_t *>(p.data)[t];
@@ -648,7 +657,7 @@ __global__ void __launch_bounds__(kThreads) k_num_stats(StatsArgs p) {
         visit(z, p.tri[t], bits, valid);
     }
     close_tri();
-    flush_run<S, KIND>(run, tab);
+    flush_run<S, KIND>(run, tab, p.n_labels);
     if (SMEM) {
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < p.n_labels; i += blockDim.x) {
@@ -784,6 +793,7 @@ lcl_status numeric_stats_impl(const lcl_atlas *atlas, int type, const void *data
     p.zones = zones;
     p.n_labels = n_labels;
     p.n_texels = (int64_t)atlas->width * atlas->height;
+    p.n_tri = atlas->n_tri;
     p.out = reinterpret_cast<ZoneAcc *>(out);
     const unsigned zg = std::max(1u, std::min(1024u, (n_labels + kThreads - 1) / kThreads));
     k_stats_init<<<zg, kThreads, 0, st>>>(p.out, n_labels);

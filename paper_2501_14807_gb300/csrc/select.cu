@@ -37,6 +37,7 @@ namespace {
 
 __global__ void k_sel_init(uint32_t *counters, int32_t n, unsigned long long *hits) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!LCL_IN(i, n)) break;
         counters[i] = 0;
         if (hits) hits[i] = 0;
     }
@@ -53,25 +54,28 @@ __device__ __forceinline__ void cull_super_sphere(const AtlasDev &a, const Spher
     bool in_reach;
     if (PAD) {
         in_reach = near_box_3x3(a.super_box, a.supers_x, a.supers_y, sx, sy, s);
-    } else {
+    } else if (LCL_IN(sidx, (int64_t)a.supers_x * a.supers_y)) {
         const int4 *sb = reinterpret_cast<const int4 *>(a.super_box + 8 * (int64_t)sidx);
         const int4 slo = sb[0], shi = sb[1];
         in_reach = slo.w > 0 && box_dist2(slo, shi, s) <= s.r2;
+    } else {
+        in_reach = false;
     }
     if (!in_reach) return;  // uniform over the CTA
     const int32_t tx = sx * LCL_SUPER + (threadIdx.x % LCL_SUPER);
     const int32_t ty = sy * LCL_SUPER + (threadIdx.x / LCL_SUPER);
     bool cand = false;
+    const int64_t n_tiles = (int64_t)a.tiles_x * a.tiles_y;
     if (tx < a.tiles_x && ty < a.tiles_y) {
         if (PAD) {
             cand = near_box_3x3(a.tile_box, a.tiles_x, a.tiles_y, tx, ty, s);
-        } else {
+        } else if (LCL_IN((int64_t)ty * a.tiles_x + tx, n_tiles)) {
             const int4 *tb = reinterpret_cast<const int4 *>(a.tile_box + 8 * ((int64_t)ty * a.tiles_x + tx));
             const int4 lo = tb[0], hi = tb[1];
             cand = lo.w > 0 && box_dist2(lo, hi, s) <= s.r2;
         }
     }
-    append_candidate(cand, (uint32_t)(ty * a.tiles_x + tx), counter, list);
+    append_candidate(cand, (uint32_t)(ty * a.tiles_x + tx), counter, list, n_tiles);
 }
 
 // Culls the first stroke of a call.
@@ -98,11 +102,12 @@ __device__ __forceinline__ Item load_item(const AtlasDev &a, const uint32_t *__r
                                           int cpt_log2, int32_t qpr, int32_t nq) {
     Item it;
     it.l = -1;
+    if (!LCL_IN(item >> cpt_log2, (int64_t)a.tiles_x * a.tiles_y)) return it;
     const uint32_t tile = __ldg(list + (item >> cpt_log2));
     const int32_t qd = (int32_t)((item & ((1u << cpt_log2) - 1)) * kThreads + threadIdx.x);
     const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
-    if (qd < nq && x < a.w && y < a.h) {
+    if (qd < nq && x < a.w && y < a.h && LCL_IN((int64_t)y * a.w + x + 3, (int64_t)a.w * a.h)) {
         it.l = (int64_t)y * a.w + x;
         it.X = __ldg(reinterpret_cast<const int4 *>(a.px + it.l));
         it.Y = __ldg(reinterpret_cast<const int4 *>(a.py + it.l));
@@ -143,6 +148,7 @@ __device__ uint32_t pad_mask(const AtlasDev &a, const Item &it, const SphereArg 
                 const int32_t xx = x0 + k + dx;
                 if (xx < 0 || xx >= a.w) continue;
                 const int64_t n = (int64_t)yy * a.w + xx;
+                if (!LCL_IN(n, (int64_t)a.w * a.h)) continue;
                 const int32_t qx = __ldg(a.px + n);
                 if (qx == INT32_MIN) continue;
                 const int32_t ax = abs(dx), ay = abs(dy);
@@ -180,6 +186,8 @@ __global__ void __launch_bounds__(kThreads) k_sphere_step(AtlasDev a, L *__restr
     const int cpt_log2 = nq > kThreads ? 31 - __clz(nq / kThreads) : 0;
     const uint32_t n_items = *counter << cpt_log2;
     const bool grouped = a.T >= 32 && (a.w & 31) == 0;  // uniform: see valid_update_warp
+    const int64_t n_tex = (int64_t)a.w * a.h;
+    (void)n_tex;
     uint32_t cnt = 0;
     uint32_t item = blockIdx.x;
     Item cur;
@@ -195,19 +203,19 @@ __global__ void __launch_bounds__(kThreads) k_sphere_step(AtlasDev a, L *__restr
             if (cur.l >= 0) {
                 const uint32_t m = sphere_mask(cur, s);
                 wm = PAD ? (m | pad_mask(a, cur, s)) : m;
-                if (wm) store_hits<L>(layer, cur.l, wm, s.label);
+                if (wm && LCL_IN(cur.l + 3, n_tex)) store_hits<L>(layer, cur.l, wm, s.label);
                 cnt += __popc(m);
             }
-            if (grouped) valid_update_warp<true>(vm, cur.l, wm);
-            else valid_update_warp<false>(vm, cur.l, wm);
+            if (grouped) valid_update_warp<true>(vm, cur.l, wm, n_tex);
+            else valid_update_warp<false>(vm, cur.l, wm, n_tex);
         } else if (cur.l >= 0) {
             const uint32_t m = sphere_mask(cur, s);
             if (PAD) {
                 const uint32_t p = pad_mask(a, cur, s);
-                if (m | p) store_hits<L>(layer, cur.l, m | p, s.label);
+                if ((m | p) && LCL_IN(cur.l + 3, n_tex)) store_hits<L>(layer, cur.l, m | p, s.label);
                 cnt += __popc(m);
             } else if (m) {
-                store_hits<L>(layer, cur.l, m, s.label);
+                if (LCL_IN(cur.l + 3, n_tex)) store_hits<L>(layer, cur.l, m, s.label);
                 cnt += __popc(m);
             }
         }
@@ -227,25 +235,28 @@ __global__ void __launch_bounds__(kThreads) k_lasso_cull(AtlasDev a, const __gri
                                                          const float *__restrict__ depth, uint32_t *counter,
                                                          uint32_t *list) {
     const int32_t sx = blockIdx.x, sy = blockIdx.y;
+    if (!LCL_IN((int64_t)sy * a.supers_x + sx, (int64_t)a.supers_x * a.supers_y)) return;  // uniform
     const int4 *sb = reinterpret_cast<const int4 *>(a.super_box + 8 * ((int64_t)sy * a.supers_x + sx));
     const int4 slo = sb[0], shi = sb[1];
     const bool super_in = slo.w > 0 && box_may_touch8(p, slo, shi, nullptr);  // uniform over the CTA
+    const int64_t n_tiles = (int64_t)a.tiles_x * a.tiles_y;
     constexpr int kPerPass = kThreads / 8;
     for (int32_t local = blockIdx.z * kPerPass + (int32_t)(threadIdx.x / 8); local < LCL_SUPER * LCL_SUPER;
          local += gridDim.z * kPerPass) {
         const int32_t tx = sx * LCL_SUPER + local % LCL_SUPER, ty = sy * LCL_SUPER + local / LCL_SUPER;
         const bool in_grid = tx < a.tiles_x && ty < a.tiles_y;  // uniform over each group of 8 lanes
         bool cand = false;
-        if (super_in && in_grid) {
+        // the group's 8 lanes take the same branch (in_grid and the index check are per tile)
+        if (super_in && in_grid && LCL_IN((int64_t)ty * a.tiles_x + tx, n_tiles)) {
             const int4 *tb = reinterpret_cast<const int4 *>(a.tile_box + 8 * ((int64_t)ty * a.tiles_x + tx));
             const int4 lo = tb[0], hi = tb[1];
             cand = lo.w > 0 && box_may_touch8(p, lo, hi, depth);
         }
         const uint32_t tile = (uint32_t)(ty * a.tiles_x + tx);
         if (FLAGS) {
-            if (in_grid && (threadIdx.x & 7u) == 0) list[tile] = cand ? 1u : 0u;
+            if (in_grid && (threadIdx.x & 7u) == 0 && LCL_IN(tile, n_tiles)) list[tile] = cand ? 1u : 0u;
         } else {
-            append_candidate(cand && (threadIdx.x & 7u) == 0, tile, counter, list);
+            append_candidate(cand && (threadIdx.x & 7u) == 0, tile, counter, list, n_tiles);
         }
     }
 }
@@ -256,14 +267,15 @@ __global__ void __launch_bounds__(kThreads) k_lasso_cull(AtlasDev a, const __gri
 __global__ void __launch_bounds__(kThreads) k_dilate_candidates(AtlasDev a, const uint32_t *__restrict__ flags,
                                                                 uint32_t *counter, uint32_t *list) {
     const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t n_tiles = (int64_t)a.tiles_x * a.tiles_y;
     bool cand = false;
-    if (t < (int64_t)a.tiles_x * a.tiles_y) {
+    if (t < n_tiles) {
         const int32_t tx = (int32_t)(t % a.tiles_x), ty = (int32_t)(t / a.tiles_x);
         for (int32_t y = max(ty - 1, 0); y <= min(ty + 1, a.tiles_y - 1) && !cand; ++y)
             for (int32_t x = max(tx - 1, 0); x <= min(tx + 1, a.tiles_x - 1); ++x)
-                if (flags[(int64_t)y * a.tiles_x + x]) cand = true;
+                if (LCL_IN((int64_t)y * a.tiles_x + x, n_tiles) && flags[(int64_t)y * a.tiles_x + x]) cand = true;
     }
-    append_candidate(cand, (uint32_t)t, counter, list);
+    append_candidate(cand, (uint32_t)t, counter, list, n_tiles);
 }
 
 
@@ -287,6 +299,7 @@ __device__ uint32_t lasso_pad_mask(const AtlasDev &a, int64_t l, int4 X, const L
                 const int32_t xx = x0 + k + dx;
                 if (xx < 0 || xx >= a.w) continue;
                 const int64_t n = (int64_t)yy * a.w + xx;
+                if (!LCL_IN(n, (int64_t)a.w * a.h)) continue;
                 const int32_t qx = __ldg(a.px + n);
                 if (qx == INT32_MIN) continue;
                 const int32_t ax = abs(dx), ay = abs(dy);
@@ -313,13 +326,16 @@ __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restr
     const uint32_t n = *counter;
     const int32_t qpr = a.T / 4, nq = a.T * qpr;
     uint32_t cnt = 0;
+    const int64_t n_tex = (int64_t)a.w * a.h;
     for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+        if (!LCL_IN(i, (int64_t)a.tiles_x * a.tiles_y)) break;
         const uint32_t tile = list[i];
         const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
         for (int32_t qd = threadIdx.x; qd < nq; qd += kThreads) {
             const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
             if (x >= a.w || y >= a.h) continue;
             const int64_t l = (int64_t)y * a.w + x;
+            if (!LCL_IN(l + 3, n_tex)) continue;
             const int4 X = __ldg(reinterpret_cast<const int4 *>(a.px + l));
             const int4 Y = __ldg(reinterpret_cast<const int4 *>(a.py + l));
             const int4 Z = __ldg(reinterpret_cast<const int4 *>(a.pz + l));
@@ -327,7 +343,7 @@ __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restr
             const uint32_t pm = PAD ? lasso_pad_mask(a, l, X, p, sh, depth, pad_r, pad_t) : 0u;
             if (m | pm) {
                 store_hits<L>(layer, l, m | pm, p.label);
-                if (NUM) valid_update_atomic(vm, l, m | pm);
+                if (NUM) valid_update_atomic(vm, l, m | pm, n_tex);
                 cnt += __popc(m);
             }
         }
@@ -358,6 +374,7 @@ __device__ __forceinline__ uint32_t tool_pad_mask(const AtlasDev &a, int64_t l, 
                 const int32_t xx = x0 + k + dx;
                 if (xx < 0 || xx >= a.w) continue;
                 const int64_t n = (int64_t)yy * a.w + xx;
+                if (!LCL_IN(n, (int64_t)a.w * a.h)) continue;
                 const int32_t qx = __ldg(a.px + n);
                 if (qx == INT32_MIN) continue;
                 const int32_t ax = abs(dx), ay = abs(dy);
@@ -381,13 +398,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_tool_apply(AtlasDev a, L *__res
     const uint32_t n = *counter;
     const int32_t qpr = a.T / 4, nq = a.T * qpr;
     uint32_t cnt = 0;
+    const int64_t n_tex = (int64_t)a.w * a.h;
     for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+        if (!LCL_IN(i, (int64_t)a.tiles_x * a.tiles_y)) break;
         const uint32_t tile = list[i];
         const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
         for (int32_t qd = threadIdx.x; qd < nq; qd += kThreads) {
             const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
             if (x >= a.w || y >= a.h) continue;
             const int64_t l = (int64_t)y * a.w + x;
+            if (!LCL_IN(l + 3, n_tex)) continue;
             const int4 X = __ldg(reinterpret_cast<const int4 *>(a.px + l));
             const int4 Y = __ldg(reinterpret_cast<const int4 *>(a.py + l));
             const int4 Z = __ldg(reinterpret_cast<const int4 *>(a.pz + l));
@@ -399,7 +419,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_tool_apply(AtlasDev a, L *__res
             const uint32_t pm = PAD ? tool_pad_mask<MASK>(a, l, X, p, t, depth) : 0u;
             if (m | pm) {
                 store_hits<L>(layer, l, m | pm, p.label);
-                if (NUM) valid_update_atomic(vm, l, m | pm);
+                if (NUM) valid_update_atomic(vm, l, m | pm, n_tex);
                 cnt += __popc(m);
             }
         }

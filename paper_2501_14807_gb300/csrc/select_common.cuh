@@ -55,6 +55,7 @@ __device__ __forceinline__ bool near_box_3x3(const int32_t *boxes, int32_t nx, i
     bool any = false;
     for (int32_t y = max(by - 1, 0); y <= min(by + 1, ny - 1); ++y)
         for (int32_t x = max(bx - 1, 0); x <= min(bx + 1, nx - 1); ++x) {
+            if (!LCL_IN((int64_t)y * nx + x, (int64_t)nx * ny)) continue;
             const int4 *b = reinterpret_cast<const int4 *>(boxes + 8 * ((int64_t)y * nx + x));
             const int4 lo = b[0], hi = b[1];
             any |= lo.w > 0 && box_dist2(lo, hi, s) <= s.r2;
@@ -62,15 +63,19 @@ __device__ __forceinline__ bool near_box_3x3(const int32_t *boxes, int32_t nx, i
     return any;
 }
 
-// Appends this lane's tile to the candidate list if `cand`; one atomic per warp.
-__device__ __forceinline__ void append_candidate(bool cand, uint32_t tile, uint32_t *counter, uint32_t *list) {
+// Appends this lane's tile to the candidate list (room for `cap` entries) if `cand`; one atomic
+// per warp.
+__device__ __forceinline__ void append_candidate(bool cand, uint32_t tile, uint32_t *counter, uint32_t *list,
+                                                 int64_t cap) {
     uint32_t m = __ballot_sync(0xffffffffu, cand);
     if (!m) return;
     const int lane = threadIdx.x & 31;
     uint32_t base = 0;
     if (lane == __ffs(m) - 1) base = atomicAdd(counter, (uint32_t)__popc(m));
     base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-    if (cand) list[base + __popc(m & ((1u << lane) - 1))] = tile;
+    const uint32_t slot = base + __popc(m & ((1u << lane) - 1));
+    if (cand && LCL_IN(slot, cap)) list[slot] = tile;
+    (void)cap;
 }
 
 
@@ -130,11 +135,14 @@ struct ValMask {
     uint32_t set;  // 1: set the written texels' bits, 0: clear them
 };
 
-// Updates the mask bits of one quad (bits m at texel l, l a multiple of 4) with one atomic.
-__device__ __forceinline__ void valid_update_atomic(const ValMask &vm, int64_t l, uint32_t m) {
+// Updates the mask bits of one quad (bits m at texel l, l a multiple of 4) with one atomic; the
+// mask has a bit for each of n_tex texels.
+__device__ __forceinline__ void valid_update_atomic(const ValMask &vm, int64_t l, uint32_t m, int64_t n_tex) {
     const uint32_t b = m << (l & 31);
+    if (!LCL_IN(l >> 5, (n_tex + 31) >> 5)) return;
     if (vm.set) atomicOr(vm.bits + (l >> 5), b);
     else atomicAnd(vm.bits + (l >> 5), ~b);
+    (void)n_tex;
 }
 
 // Updates the mask bits of the quads of a whole warp; every lane calls it (l < 0: no quad).
@@ -143,19 +151,19 @@ __device__ __forceinline__ void valid_update_atomic(const ValMask &vm, int64_t l
 // shuffles and the word is written by its first lane, which owns it during the launch (one edit
 // per launch), so no atomic is needed.  Otherwise each quad updates its bits with one atomic.
 template <bool GROUPED>
-__device__ __forceinline__ void valid_update_warp(const ValMask &vm, int64_t l, uint32_t m) {
+__device__ __forceinline__ void valid_update_warp(const ValMask &vm, int64_t l, uint32_t m, int64_t n_tex) {
     if (GROUPED) {
         uint32_t b = (l >= 0) ? (m << (l & 31)) : 0u;
         b |= __shfl_xor_sync(0xffffffffu, b, 1);
         b |= __shfl_xor_sync(0xffffffffu, b, 2);
         b |= __shfl_xor_sync(0xffffffffu, b, 4);
-        if ((threadIdx.x & 7u) == 0 && l >= 0 && b) {
+        if ((threadIdx.x & 7u) == 0 && l >= 0 && b && LCL_IN(l >> 5, (n_tex + 31) >> 5)) {
             uint32_t *p = vm.bits + (l >> 5);
             if (vm.set) *p = (b == 0xFFFFFFFFu) ? b : (*p | b);
             else *p = (b == 0xFFFFFFFFu) ? 0u : (*p & ~b);
         }
     } else if (l >= 0 && m) {
-        valid_update_atomic(vm, l, m);
+        valid_update_atomic(vm, l, m, n_tex);
     }
 }
 
@@ -288,7 +296,9 @@ __device__ inline bool box_may_touch(const LassoArg &p, int4 lo, int4 hi, const 
     if ((ix1 - ix0 + 1) * (iy1 - iy0 + 1) > 1024) return true;
     float dmax = -INFINITY;
     for (int iy = iy0; iy <= iy1; ++iy)
-        for (int ix = ix0; ix <= ix1; ++ix) dmax = fmaxf(dmax, __ldg(depth + (int64_t)iy * p.w_s + ix));
+        for (int ix = ix0; ix <= ix1; ++ix)
+            if (LCL_IN((int64_t)iy * p.w_s + ix, (int64_t)p.w_s * p.h_s))
+                dmax = fmaxf(dmax, __ldg(depth + (int64_t)iy * p.w_s + ix));
     return !(zmin - 1e-4f > dmax + p.bias);
 }
 
@@ -326,7 +336,9 @@ __device__ __forceinline__ bool box_may_touch8(const LassoArg &p, int4 lo, int4 
     if ((ix1 - ix0 + 1) * (iy1 - iy0 + 1) > 2048) return true;
     float dmax = -INFINITY;
     for (int iy = iy0 + (int)sub; iy <= iy1; iy += 8)
-        for (int ix = ix0; ix <= ix1; ++ix) dmax = fmaxf(dmax, __ldg(depth + (int64_t)iy * p.w_s + ix));
+        for (int ix = ix0; ix <= ix1; ++ix)
+            if (LCL_IN((int64_t)iy * p.w_s + ix, (int64_t)p.w_s * p.h_s))
+                dmax = fmaxf(dmax, __ldg(depth + (int64_t)iy * p.w_s + ix));
     for (int o = 1; o < 8; o <<= 1) dmax = fmaxf(dmax, __shfl_xor_sync(gm, dmax, o));
     return !(zmin - 1e-4f > dmax + p.bias);
 }
@@ -360,7 +372,9 @@ __device__ __forceinline__ bool lasso_hit(const LassoArg &p, const Edges &sh, co
     band = band < 0 ? 0 : (band >= kBands ? kBands - 1 : band);
     bool inside = false;
     for (int k = sh.band_off[band]; k < sh.band_off[band + 1]; ++k) {
+        if (!LCL_IN(k, kBandEdgesMax)) break;
         const int e = sh.band_edge[k];
+        if (!LCL_IN(e, LCL_MAX_LASSO_VERTICES)) continue;
         const float ax = sh.vx[e], ay = sh.vy[e], bx = sh.vx[e + 1], by = sh.vy[e + 1];
         if ((ay > ys) != (by > ys)) {
             const float2 r = edge_xrange(ax, bx);
@@ -371,6 +385,7 @@ __device__ __forceinline__ bool lasso_hit(const LassoArg &p, const Edges &sh, co
     const float zn = __fdiv_rn(clip_row(p.m + 8, fx, fy, fz), cw);
     if (!(zn >= 0.0f && zn <= 1.0f)) return false;
     const int32_t ix = __float2int_rz(xs), iy = __float2int_rz(ys);
+    if (!LCL_IN((int64_t)iy * p.w_s + ix, (int64_t)p.w_s * p.h_s)) return false;
     const float d = __ldg(depth + (int64_t)iy * p.w_s + ix);
     return zn <= __fadd_rn(d, p.bias);
 }
@@ -420,7 +435,9 @@ __device__ __forceinline__ uint32_t lasso_quad(const LassoArg &p, const LassoSha
     uint32_t inside = 0;
     if (same) {
         for (int j = sh.band_off[b0]; j < sh.band_off[b0 + 1]; ++j) {
+            if (!LCL_IN(j, kBandEdgesMax)) break;
             const int e = sh.band_edge[j];
+            if (!LCL_IN(e, LCL_MAX_LASSO_VERTICES)) continue;
             const float4 r = sh.rec[e];
 #pragma unroll
             for (int k = 0; k < 4; ++k)
@@ -432,7 +449,9 @@ __device__ __forceinline__ uint32_t lasso_quad(const LassoArg &p, const LassoSha
         for (int k = 0; k < 4; ++k) {
             if (band[k] < 0) continue;
             for (int j = sh.band_off[band[k]]; j < sh.band_off[band[k] + 1]; ++j) {
+                if (!LCL_IN(j, kBandEdgesMax)) break;
                 const int e = sh.band_edge[j];
+                if (!LCL_IN(e, LCL_MAX_LASSO_VERTICES)) continue;
                 const float4 r = sh.rec[e];
                 if ((r.x > ys[k]) != (r.y > ys[k]) && edge_left(sh.vx, e, xs[k], ys[k], r.x, r.y, r.z, r.w))
                     inside ^= 1u << k;
@@ -447,6 +466,7 @@ __device__ __forceinline__ uint32_t lasso_quad(const LassoArg &p, const LassoSha
         const float zn = __fdiv_rn(clip_row(p.m + 8, (float)xq[k], (float)yq[k], (float)zq[k]), cw[k]);
         if (!(zn >= 0.0f && zn <= 1.0f)) continue;
         const int32_t ix = __float2int_rz(xs[k]), iy = __float2int_rz(ys[k]);
+        if (!LCL_IN((int64_t)iy * p.w_s + ix, (int64_t)p.w_s * p.h_s)) continue;
         const float d = __ldg(depth + (int64_t)iy * p.w_s + ix);
         if (zn <= __fadd_rn(d, p.bias)) m |= 1u << k;
     }
@@ -486,7 +506,9 @@ __device__ __forceinline__ bool tool_hit(const LassoArg &p, const ToolArg &t, co
     if (MASK) {
         const float fu = __fmul_rn(__fsub_rn(xs, t.x0), t.su), fv = __fmul_rn(__fsub_rn(ys, t.y0), t.sv);
         if (!(fu >= 0.0f && fu < t.fw && fv >= 0.0f && fv < t.fh)) return false;
-        if (__ldg(t.shape + (int64_t)__float2int_rz(fv) * t.sw + __float2int_rz(fu)) == 0) return false;
+        const int64_t si = (int64_t)__float2int_rz(fv) * t.sw + __float2int_rz(fu);
+        if (!LCL_IN(si, (int64_t)t.sw * t.sh)) return false;
+        if (__ldg(t.shape + si) == 0) return false;
     } else {
         const float ex = __fmul_rn(__fsub_rn(xs, t.px), t.kx), ey = __fmul_rn(__fsub_rn(ys, t.py), t.ky);
         if (!(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)) <= 1.0f)) return false;
@@ -494,6 +516,7 @@ __device__ __forceinline__ bool tool_hit(const LassoArg &p, const ToolArg &t, co
     const float zn = __fdiv_rn(clip_row(p.m + 8, fx, fy, fz), cw);
     if (!(zn >= 0.0f && zn <= 1.0f)) return false;
     const int32_t ix = __float2int_rz(xs), iy = __float2int_rz(ys);
+    if (!LCL_IN((int64_t)iy * p.w_s + ix, (int64_t)p.w_s * p.h_s)) return false;
     const float d = __ldg(depth + (int64_t)iy * p.w_s + ix);
     return zn <= __fadd_rn(d, p.bias);
 }

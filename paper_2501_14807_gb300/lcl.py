@@ -15,6 +15,9 @@ import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblcl.so")
+# The same library built with bounds checks in every kernel (LCL_DEBUG_BOUNDS); loaded instead of
+# liblcl.so when the environment variable LCL_DEBUG_BOUNDS is 1.
+DEBUG_LIB_PATH = os.path.join(HERE, "liblcl_debug.so")
 
 LCL_OK = 0
 STATUS = {0: "LCL_OK", 1: "LCL_ERR_INVALID_ARG", 2: "LCL_ERR_OUT_OF_MEMORY", 3: "LCL_ERR_CUDA",
@@ -35,7 +38,9 @@ EXPORTS = ["lcl_atlas_bytes", "lcl_atlas_bind", "lcl_atlas_rows", "lcl_atlas_wor
            "lcl_overlay", "lcl_label_area", "lcl_numeric_sphere", "lcl_numeric_lasso", "lcl_numeric_tool",
            "lcl_numeric_arith", "lcl_numeric_select", "lcl_numeric_stats",
            "lcl_pool_create", "lcl_pool_acquire", "lcl_pool_release", "lcl_pool_stats_get", "lcl_pool_destroy",
-           "lcl_status_str", "lcl_last_error", "lcl_kernel_launches"]
+           "lcl_status_str", "lcl_last_error", "lcl_kernel_launches", "lcl_last_device_status", "lcl_build_flags",
+           "lcl_describe_site"]
+LCL_BUILD_BOUNDS_CHECKS = 1
 
 
 class lcl_mesh(C.Structure):
@@ -139,10 +144,11 @@ def library():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first (python -c 'import "
+    path = DEBUG_LIB_PATH if os.environ.get("LCL_DEBUG_BOUNDS") == "1" else LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first (python -c 'import "
                            "__graft_entry__ as g; g.build()'); there is no CPU fallback")
-    lib = C.CDLL(LIB_PATH)
+    lib = C.CDLL(path)
     P, I32, I64, U32, SZ, F, D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_size_t, C.c_float, C.c_double
     st = C.c_int
     sig = {
@@ -194,6 +200,9 @@ def library():
         "lcl_status_str": (C.c_char_p, [C.c_int]),
         "lcl_last_error": (C.c_char_p, []),
         "lcl_kernel_launches": (C.c_uint64, []),
+        "lcl_last_device_status": (st, [P]),
+        "lcl_build_flags": (U32, []),
+        "lcl_describe_site": (SZ, [U32, P, SZ]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -838,3 +847,23 @@ def lcl_last_error():
 
 def lcl_kernel_launches():
     return int(library().lcl_kernel_launches())
+
+
+def lcl_last_device_status(stream=None):
+    """Synchronises `stream` (default: the current torch stream) and returns the library's device
+    status (an lcl_status code; lcl_last_error() explains a non-zero one).  Raises nothing."""
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    elif isinstance(stream, torch.cuda.Stream):
+        stream = stream.cuda_stream
+    return int(library().lcl_last_device_status(C.c_void_p(stream)))
+
+
+def lcl_build_flags():
+    return int(library().lcl_build_flags())
+
+
+def lcl_describe_site(site):
+    buf = C.create_string_buffer(64)
+    library().lcl_describe_site(C.c_uint32(site), buf, 64)
+    return buf.value.decode()

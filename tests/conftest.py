@@ -20,3 +20,19 @@ def pytest_configure(config):
 def _oracle_built():
     from oracle.build import build_oracle
     build_oracle()
+
+
+@pytest.fixture(autouse=True)
+def _device_status_clean(request):
+    """Under the bounds-checking library (LCL_DEBUG_BOUNDS=1), every GPU test must leave no
+    out-of-range index behind: lcl_last_device_status is LCL_OK after the test."""
+    yield
+    if os.environ.get("LCL_DEBUG_BOUNDS") != "1" or request.node.get_closest_marker("gpu") is None:
+        return
+    import torch
+
+    from paper_2501_14807_gb300 import lcl
+    assert lcl.lcl_build_flags() & lcl.LCL_BUILD_BOUNDS_CHECKS, "the bounds-checking library is not the one loaded"
+    torch.cuda.synchronize()
+    st = lcl.lcl_last_device_status()
+    assert st == 0, f"device status after {request.node.nodeid}: {lcl.lcl_status_str(st)}: {lcl.lcl_last_error()}"

@@ -373,3 +373,48 @@ def test_pool_rejects_bad_arguments_on_host(lcl):
     st = lcl.lcl_pool_stats()
     assert lib.lcl_pool_stats_get(None, C.byref(st)) == 1
     assert lib.lcl_pool_destroy(None) == 0
+
+
+def _site(name, line):
+    """A bounds-check site as the kernels record it: 16-bit fold of the FNV-1a hash of the file
+    name (after the last '/') above the line number."""
+    h = 2166136261
+    for c in name.encode():
+        h = ((h ^ c) * 16777619) & 0xFFFFFFFF
+    return (((h ^ (h >> 16)) & 0xFFFF) << 16) | (line & 0xFFFF)
+
+
+def test_device_status_sites_decode_to_file_and_line(lcl):
+    names = ["atlas.cu", "batch.cu", "depth.cu", "layers.cu", "numeric.cu", "select.cu", "noalloc.cu",
+             "lcl_api.cu", "pool.cu", "select_common.cuh", "lcl_impl.cuh"]
+    assert len({_site(n, 0) for n in names}) == len(names)          # no two files share a hash
+    for i, n in enumerate(names):
+        assert lcl.lcl_describe_site(_site(n, 17 + i)) == f"{n}:{17 + i}"
+    unknown = _site("elsewhere.cu", 9)
+    assert lcl.lcl_describe_site(unknown) == f"file#{unknown >> 16:04x}:9"
+    lib = lcl.library()
+    assert lib.lcl_describe_site(_site("select.cu", 123), None, 0) == len("select.cu:123")
+    buf = C.create_string_buffer(5)
+    lib.lcl_describe_site(_site("select.cu", 123), buf, 5)
+    assert buf.value == b"sele"                                        # truncated, NUL-terminated
+
+
+def test_debug_build_reports_bounds_checks(lcl):
+    """liblcl.so has no bounds checks; liblcl_debug.so (built by the same build()) has them."""
+    from paper_2501_14807_gb300 import build
+    assert lcl.lcl_build_flags() & lcl.LCL_BUILD_BOUNDS_CHECKS == 0
+    if not os.path.exists(lcl.DEBUG_LIB_PATH):
+        build.build(debug=True)
+    dbg = C.CDLL(lcl.DEBUG_LIB_PATH)
+    dbg.lcl_build_flags.restype = C.c_uint32
+    assert dbg.lcl_build_flags() == lcl.LCL_BUILD_BOUNDS_CHECKS
+    missing = [n for n in declared_functions() if not hasattr(dbg, n)]
+    assert not missing
+
+
+def test_device_status_without_a_gpu_is_a_cuda_error(lcl):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("checks the no-device answer")
+    assert lcl.library().lcl_last_device_status(None) == 3           # LCL_ERR_CUDA: nothing to synchronise
+    assert "lcl_last_device_status" in lcl.lcl_last_error()
