@@ -84,7 +84,9 @@ typedef struct {
  *  super_box: the same record per super-tile of LCL_SUPER x LCL_SUPER tiles.
  *  area_w: uint64 per triangle, the surface area one of its texels stands for.
  *  bbox_min, scale: the quantisation, grid = floor((p - bbox_min) * scale + 0.5).
- *  row0: first texture row held by this atlas (0, or the start of a row view). */
+ *  row0: first texture row held by this atlas (0, or the start of a row view or band).
+ *  tex_height: rows of the whole texture this atlas is part of (height for a whole atlas; a band
+ *      or row view holds rows [row0, row0 + height) of it). */
 typedef struct {
     int32_t width, height, tile;
     int32_t tiles_x, tiles_y, supers_x, supers_y;
@@ -97,7 +99,7 @@ typedef struct {
     int32_t *super_box; /* NULL in a row view */
     uint64_t *area_w;
     float bbox_min[3];
-    int32_t _pad;
+    int32_t tex_height;
     double scale;
 } lcl_atlas;
 
@@ -131,6 +133,19 @@ lcl_status lcl_atlas_bind(void *base, size_t bytes, int32_t width, int32_t heigh
  * band of the texture (layer pointers passed with it must point at row y0).  Requires
  * y0 * width to be a multiple of 32.  Selections reject views. */
 lcl_status lcl_atlas_rows(const lcl_atlas *atlas, int32_t y0, int32_t y1, lcl_atlas *out);
+
+/* A band atlas: rows [y0, y1) of a width x tex_height texture, with its own planes, coverage bits,
+ * tile and super-tile boxes (tiles counted from row y0), in a buffer of
+ * lcl_atlas_bytes(width, y1 - y0, tile, n_tri) bytes.  Texels are independent of one another
+ * (Section 4.3.1 edits each texel by its own position and depth test), so one large texture can be
+ * split into row bands, one per GPU: lcl_atlas_build fills a band with exactly the rows of the
+ * whole atlas (texture coordinates are snapped against tex_height), every area weight included;
+ * sphere, lasso and tool edits, overlays and per-label areas on a band give the rows of the whole
+ * result (per-label counts and areas add up over the bands).  Texture padding reads texels up to 8
+ * rows beyond a band, so padded edits on a band (height != tex_height) return LCL_ERR_UNSUPPORTED.
+ * Writes only *out; nothing is enqueued. */
+lcl_status lcl_atlas_bind_band(void *base, size_t bytes, int32_t width, int32_t tex_height, int32_t y0, int32_t y1,
+                               int32_t tile, int64_t n_tri, lcl_atlas *out);
 
 /* ---- atlas build -------------------------------------------------------- */
 

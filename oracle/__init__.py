@@ -112,16 +112,17 @@ class Atlas:
         return bits
 
     def tile_aabb(self):
-        assert self.y0 == 0 and self.y1 == self.H, "tile boxes need the full texture"
-        ntx, nty = -(-self.W // self.T), -(-self.H // self.T)
+        """Tile boxes of the rows this atlas holds, tiles counted from its first row y0."""
+        rows = self.y1 - self.y0
+        ntx, nty = -(-self.W // self.T), -(-rows // self.T)
         box = np.empty((nty * ntx, 8), np.int32)
-        _chk(lib().orc_tile_aabb(C.c_int32(self.W), C.c_int32(self.H), C.c_int32(self.T), _p(self.px),
+        _chk(lib().orc_tile_aabb(C.c_int32(self.W), C.c_int32(rows), C.c_int32(self.T), _p(self.px),
                                  _p(self.py), _p(self.pz), _p(self.tri), _p(box)), "tile_aabb")
         return box
 
     def super_aabb(self, box=None):
         box = self.tile_aabb() if box is None else box
-        ntx, nty = -(-self.W // self.T), -(-self.H // self.T)
+        ntx, nty = -(-self.W // self.T), -(-(self.y1 - self.y0) // self.T)
         nsx, nsy = -(-ntx // SUPER), -(-nty // SUPER)
         sbox = np.empty((nsy * nsx, 8), np.int32)
         _chk(lib().orc_super_aabb(C.c_int32(ntx), C.c_int32(nty), C.c_int32(SUPER), _p(box), _p(sbox)),

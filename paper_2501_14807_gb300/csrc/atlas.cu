@@ -147,7 +147,8 @@ struct RasterArgs {
     int64_t n_tri, n_pos, n_uv;
     const int4 *q;
     const int2 *uvs;
-    int32_t w, h;
+    int32_t w, h;        // texture size (h: rows of the whole texture)
+    int32_t row0, rows;  // the rows this atlas holds: [row0, row0 + rows)
     TriSetup *setup;
     uint64_t *area_w;
     uint32_t *tri_plane;
@@ -156,17 +157,19 @@ struct RasterArgs {
     int64_t big_cap;
 };
 
-// Texel-centre range [i0, i1] of sub-pixel interval [lo, hi] clamped to [0, n-1].
-__device__ __forceinline__ void texel_range(int64_t lo, int64_t hi, int32_t n, int64_t &i0, int64_t &i1) {
+// Texel-centre range [i0, i1] of sub-pixel interval [lo, hi] clamped to [first, last].
+__device__ __forceinline__ void texel_range(int64_t lo, int64_t hi, int64_t first, int64_t last, int64_t &i0,
+                                            int64_t &i1) {
     i0 = -floordiv(-(lo - 128), 256);
     i1 = floordiv(hi - 128, 256);
-    i0 = i0 < 0 ? 0 : i0;
-    i1 = i1 > n - 1 ? n - 1 : i1;
+    i0 = i0 < first ? first : i0;
+    i1 = i1 > last ? last : i1;
 }
 
-// Rasterises texels [i0, i1] x [j0, j1] of a set-up triangle: atomicMin of its id.
+// Rasterises texels [i0, i1] x [j0, j1] (texture rows j) of a set-up triangle into a plane that
+// holds rows [row0, row0 + rows): atomicMin of its id.
 __device__ void raster_rect(const TriSetup &s, uint32_t t, int64_t i0, int64_t i1, int64_t j0, int64_t j1, int32_t w,
-                            int32_t h, uint32_t *__restrict__ tri_plane) {
+                            int32_t row0, int32_t rows, uint32_t *__restrict__ tri_plane) {
     int64_t X0 = s.x[0], X1 = s.x[1], X2 = s.x[2], Y0 = s.y[0], Y1 = s.y[1], Y2 = s.y[2];
     int64_t px = 256 * i0 + 128, py = 256 * j0 + 128;
     // w_k + bias_k > 0 <=> covered (integer edge values, owned edges get bias 1)
@@ -180,10 +183,11 @@ __device__ void raster_rect(const TriSetup &s, uint32_t t, int64_t i0, int64_t i
 #pragma unroll 1
     for (int64_t j = j0; j <= j1; ++j) {
         int64_t r0 = e0, r1 = e1, r2 = e2;
-        uint32_t *row = tri_plane + j * (int64_t)w;
+        uint32_t *row = tri_plane + (j - row0) * (int64_t)w;
 #pragma unroll 1
         for (int64_t i = i0; i <= i1; ++i) {
-            if (r0 > 0 && r1 > 0 && r2 > 0 && LCL_IN(j * (int64_t)w + i, (int64_t)w * h)) atomicMin(row + i, t);
+            if (r0 > 0 && r1 > 0 && r2 > 0 && LCL_IN((j - row0) * (int64_t)w + i, (int64_t)w * rows))
+                atomicMin(row + i, t);
             r0 += dx0;
             r1 += dx1;
             r2 += dx2;
@@ -259,12 +263,12 @@ __global__ void k_raster(RasterArgs a) {
     int64_t xmin = min(s.x[0], min(s.x[1], s.x[2])), xmax = max(s.x[0], max(s.x[1], s.x[2]));
     int64_t ymin = min(s.y[0], min(s.y[1], s.y[2])), ymax = max(s.y[0], max(s.y[1], s.y[2]));
     int64_t i0, i1, j0, j1;
-    texel_range(xmin, xmax, a.w, i0, i1);
-    texel_range(ymin, ymax, a.h, j0, j1);
+    texel_range(xmin, xmax, 0, a.w - 1, i0, i1);
+    texel_range(ymin, ymax, a.row0, (int64_t)a.row0 + a.rows - 1, j0, j1);  // this atlas's rows only
     if (i0 > i1 || j0 > j1) return;
     int64_t nx = i1 - i0 + 1, ny = j1 - j0 + 1;
     if (nx * ny <= kSmallRaster) {
-        raster_rect(s, (uint32_t)t, i0, i1, j0, j1, a.w, a.h, a.tri_plane);
+        raster_rect(s, (uint32_t)t, i0, i1, j0, j1, a.w, a.row0, a.rows, a.tri_plane);
         return;
     }
     int64_t nbx = (nx + kBlockSide - 1) / kBlockSide, nby = (ny + kBlockSide - 1) / kBlockSide;
@@ -274,13 +278,13 @@ __global__ void k_raster(RasterArgs a) {
         for (int64_t b = 0; b < nb; ++b)
             if (LCL_IN((int64_t)base + b, a.big_cap)) a.big[base + b] = make_uint2((uint32_t)t, (uint32_t)b);
     } else {
-        raster_rect(s, (uint32_t)t, i0, i1, j0, j1, a.w, a.h, a.tri_plane);  // list full: do it here
+        raster_rect(s, (uint32_t)t, i0, i1, j0, j1, a.w, a.row0, a.rows, a.tri_plane);  // list full: do it here
     }
 }
 
 __global__ void k_raster_big(const uint2 *__restrict__ big, const AtlasHdr *__restrict__ hdr, int64_t cap,
-                             const TriSetup *__restrict__ setup, int64_t n_tri, int32_t w, int32_t h,
-                             uint32_t *__restrict__ tri_plane) {
+                             const TriSetup *__restrict__ setup, int64_t n_tri, int32_t w, int32_t row0,
+                             int32_t rows, uint32_t *__restrict__ tri_plane) {
     int64_t n = min((int64_t)hdr->n_big, cap);
     for (int64_t e = blockIdx.x; e < n; e += gridDim.x) {
         if (!LCL_IN(e, cap)) break;
@@ -290,8 +294,8 @@ __global__ void k_raster_big(const uint2 *__restrict__ big, const AtlasHdr *__re
         int64_t xmin = min(s.x[0], min(s.x[1], s.x[2])), xmax = max(s.x[0], max(s.x[1], s.x[2]));
         int64_t ymin = min(s.y[0], min(s.y[1], s.y[2])), ymax = max(s.y[0], max(s.y[1], s.y[2]));
         int64_t i0, i1, j0, j1;
-        texel_range(xmin, xmax, w, i0, i1);
-        texel_range(ymin, ymax, h, j0, j1);
+        texel_range(xmin, xmax, 0, w - 1, i0, i1);
+        texel_range(ymin, ymax, row0, (int64_t)row0 + rows - 1, j0, j1);  // as k_raster cut the blocks
         int64_t nbx = (i1 - i0 + 1 + kBlockSide - 1) / kBlockSide;
         int64_t bx = ent.y % nbx, by = ent.y / nbx;
         int64_t i = i0 + bx * kBlockSide + (threadIdx.x % kBlockSide);
@@ -302,8 +306,8 @@ __global__ void k_raster_big(const uint2 *__restrict__ big, const AtlasHdr *__re
         int64_t e0 = edge_fn(X1, Y1, X2, Y2, px, py) + edge_bias(X2 - X1, Y2 - Y1);
         int64_t e1 = edge_fn(X2, Y2, X0, Y0, px, py) + edge_bias(X0 - X2, Y0 - Y2);
         int64_t e2 = edge_fn(X0, Y0, X1, Y1, px, py) + edge_bias(X1 - X0, Y1 - Y0);
-        if (e0 > 0 && e1 > 0 && e2 > 0 && LCL_IN(j * (int64_t)w + i, (int64_t)w * h))
-            atomicMin(tri_plane + j * (int64_t)w + i, ent.x);
+        if (e0 > 0 && e1 > 0 && e2 > 0 && LCL_IN((j - row0) * (int64_t)w + i, (int64_t)w * rows))
+            atomicMin(tri_plane + (j - row0) * (int64_t)w + i, ent.x);
     }
 }
 
@@ -339,7 +343,8 @@ __device__ __forceinline__ int32_t interp_axis(int64_t w1, int64_t w2, int64_t A
 }
 
 __global__ void __launch_bounds__(kThreads) k_resolve(const TriSetup *__restrict__ setup, int64_t n_tri, int32_t w,
-                                                      int32_t h, int32_t T, const uint32_t *__restrict__ tri_plane,
+                                                      int32_t h, int32_t row0, int32_t T,
+                                                      const uint32_t *__restrict__ tri_plane,
                                                       int32_t *__restrict__ px, int32_t *__restrict__ py,
                                                       int32_t *__restrict__ pz, uint32_t *__restrict__ cover,
                                                       int32_t *__restrict__ tile_box) {
@@ -376,7 +381,7 @@ __global__ void __launch_bounds__(kThreads) k_resolve(const TriSetup *__restrict
                 if (tt[k] != cur) {
                     cur = tt[k];
                     s = setup[cur];
-                    const int64_t cx = 256 * (int64_t)(x + k) + 128, cy = 256 * (int64_t)y + 128;
+                    const int64_t cx = 256 * (int64_t)(x + k) + 128, cy = 256 * ((int64_t)y + row0) + 128;
                     A = edge_fn(s.x[0], s.y[0], s.x[1], s.y[1], s.x[2], s.y[2]);
                     w1 = edge_fn(s.x[2], s.y[2], s.x[0], s.y[0], cx, cy);
                     w2 = edge_fn(s.x[0], s.y[0], s.x[1], s.y[1], cx, cy);
@@ -525,8 +530,9 @@ lcl_status atlas_build_impl(const lcl_mesh *mesh, lcl_atlas *at, void *ws, size_
         mesh->pos, mesh->n_pos, hdr);
     k_scale<<<1, 1, 0, st>>>(hdr);
     k_quant<<<(unsigned)((mesh->n_pos + kThreads - 1) / kThreads), kThreads, 0, st>>>(mesh->pos, mesh->n_pos, hdr, q);
+    const int32_t tex_h = at->tex_height > 0 ? at->tex_height : at->height;  // snapped against the whole texture
     k_snap<<<(unsigned)((mesh->n_uv + kThreads - 1) / kThreads), kThreads, 0, st>>>(mesh->uv, mesh->n_uv, at->width,
-                                                                                   at->height, hdr, uvs);
+                                                                                   tex_h, hdr, uvs);
     count_launches(5);
     if (mesh->n_tri > 0) {
         RasterArgs ra;
@@ -538,21 +544,23 @@ lcl_status atlas_build_impl(const lcl_mesh *mesh, lcl_atlas *at, void *ws, size_
         ra.q = q;
         ra.uvs = uvs;
         ra.w = at->width;
-        ra.h = at->height;
+        ra.h = tex_h;
+        ra.row0 = at->row0;
+        ra.rows = at->height;
         ra.setup = setup;
         ra.area_w = at->area_w;
         ra.tri_plane = at->tri;
         ra.hdr = hdr;
         ra.big = big;
-        ra.big_cap = (int64_t)big_capacity(mesh->n_tri, at->width, at->height);
+        ra.big_cap = (int64_t)big_capacity(mesh->n_tri, at->width, at->height);  // blocks of this atlas's rows
         k_raster<<<(unsigned)((mesh->n_tri + 127) / 128), 128, 0, st>>>(ra);
-        k_raster_big<<<sms * 8, kThreads, 0, st>>>(big, hdr, ra.big_cap, setup, mesh->n_tri, at->width, at->height,
-                                                   at->tri);
+        k_raster_big<<<sms * 8, kThreads, 0, st>>>(big, hdr, ra.big_cap, setup, mesh->n_tri, at->width, at->row0,
+                                                   at->height, at->tri);
         count_launches(2);
     }
     dim3 tg(at->tiles_x, at->tiles_y);
-    k_resolve<<<tg, kThreads, 0, st>>>(setup, mesh->n_tri, at->width, at->height, at->tile, at->tri, at->pos_x,
-                                       at->pos_y, at->pos_z, at->cover, at->tile_box);
+    k_resolve<<<tg, kThreads, 0, st>>>(setup, mesh->n_tri, at->width, at->height, at->row0, at->tile, at->tri,
+                                       at->pos_x, at->pos_y, at->pos_z, at->cover, at->tile_box);
     dim3 sg(at->supers_x, at->supers_y);
     k_super<<<sg, kThreads, 0, st>>>(at->tile_box, at->tiles_x, at->tiles_y, at->super_box);
     count_launches(2);

@@ -456,6 +456,8 @@ lcl_status check_batch(const lcl_batch_model *models, int32_t n_models, const lc
         if (m.first_stroke < 0 || (int64_t)m.first_stroke + m.n_strokes > n_strokes)
             return fail(LCL_ERR_INVALID_ARG, "batch model stroke range out of bounds");
         const uint32_t lab_max = m.dtype == LCL_U8 ? 0xFFu : 0xFFFFu;
+        // a band of a texture's rows cannot pad (padding reads up to 8 rows beyond the band)
+        const bool band = a->tex_height > 0 && a->height != a->tex_height;
         for (int32_t k = 0; k < m.n_strokes; ++k) {
             const lcl_batch_stroke &s = strokes[m.first_stroke + k];
             if (s.kind == LCL_STROKE_SPHERE) {
@@ -465,9 +467,13 @@ lcl_status check_batch(const lcl_batch_model *models, int32_t n_models, const lc
                     sp.cz < lo || sp.cz > hi || (sp.flags & ~0xFFu) || (sp.flags & 15u) > 8 ||
                     ((sp.flags >> 4) & 15u) > 8)
                     return fail(LCL_ERR_INVALID_ARG, "batch sphere stroke out of range");
+                if (band && (sp.flags & 15u))
+                    return fail(LCL_ERR_UNSUPPORTED, "texture padding needs the whole texture, not a band of its rows");
             } else if (s.kind == LCL_STROKE_LASSO) {
                 if (s.lasso < 0 || s.lasso >= n_lassos) return fail(LCL_ERR_INVALID_ARG, "batch lasso index");
                 if (lassos[s.lasso].label > lab_max) return fail(LCL_ERR_INVALID_ARG, "batch lasso label too wide");
+                if (band && (lassos[s.lasso].flags & 15u))
+                    return fail(LCL_ERR_UNSUPPORTED, "texture padding needs the whole texture, not a band of its rows");
             } else {
                 return fail(LCL_ERR_INVALID_ARG, "unknown batch stroke kind");
             }

@@ -101,9 +101,22 @@ Layout layout(int32_t w, int32_t h, int32_t tile, int64_t n_tri) {
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// A band (or a view) holds only some rows of its texture: texture padding, which reads texels up
+// to 8 rows away, is not available on it.
+bool partial_rows(const lcl_atlas *a) { return a->tex_height > 0 && a->height != a->tex_height; }
+
+lcl_status check_padding_rows(const lcl_atlas *a, uint32_t pad_flags) {
+    if ((pad_flags & 15u) && partial_rows(a))
+        return fail(LCL_ERR_UNSUPPORTED, "texture padding needs the whole texture, not a band of its rows");
+    return LCL_OK;
+}
+
 lcl_status check_atlas(const lcl_atlas *a, bool need_boxes) {
     if (!a) return fail(LCL_ERR_INVALID_ARG, "atlas is NULL");
     if (!dims_ok(a->width, a->height, a->tile)) return fail(LCL_ERR_INVALID_ARG, "atlas sizes out of range");
+    const int32_t th = a->tex_height > 0 ? a->tex_height : a->height;
+    if (a->row0 < 0 || th > 16384 || (int64_t)a->row0 + a->height > th)
+        return fail(LCL_ERR_INVALID_ARG, "atlas rows lie outside its texture");
     if (!a->pos_x || !a->pos_y || !a->pos_z || !a->tri || !a->cover || !a->area_w)
         return fail(LCL_ERR_INVALID_ARG, "atlas is not bound");
     if (need_boxes && (!a->tile_box || !a->super_box))
@@ -194,6 +207,7 @@ lcl_status lcl_atlas_bind(void *base, size_t bytes, int32_t width, int32_t heigh
     out->supers_x = L.supers_x;
     out->supers_y = L.supers_y;
     out->row0 = 0;
+    out->tex_height = height;
     out->n_tri = n_tri;
     out->pos_x = reinterpret_cast<int32_t *>(b + L.px);
     out->pos_y = reinterpret_cast<int32_t *>(b + L.py);
@@ -204,6 +218,17 @@ lcl_status lcl_atlas_bind(void *base, size_t bytes, int32_t width, int32_t heigh
     out->super_box = reinterpret_cast<int32_t *>(b + L.super_box);
     out->area_w = reinterpret_cast<uint64_t *>(b + L.area_w);
     out->scale = 0.0;
+    return LCL_OK;
+}
+
+lcl_status lcl_atlas_bind_band(void *base, size_t bytes, int32_t width, int32_t tex_height, int32_t y0, int32_t y1,
+                               int32_t tile, int64_t n_tri, lcl_atlas *out) {
+    if (tex_height < 1 || tex_height > 16384 || y0 < 0 || y1 > tex_height || y0 >= y1)
+        return fail(LCL_ERR_INVALID_ARG, "band rows out of range");
+    const lcl_status s = lcl_atlas_bind(base, bytes, width, y1 - y0, tile, n_tri, out);
+    if (s != LCL_OK) return s;
+    out->row0 = y0;
+    out->tex_height = tex_height;
     return LCL_OK;
 }
 
@@ -241,7 +266,6 @@ lcl_status lcl_atlas_build(const lcl_mesh *mesh, lcl_atlas *atlas, void *workspa
     if (s != LCL_OK) return s;
     s = check_atlas(atlas, true);
     if (s != LCL_OK) return s;
-    if (atlas->row0 != 0) return fail(LCL_ERR_INVALID_ARG, "cannot build into a row view");
     if (mesh->n_tri != atlas->n_tri) return fail(LCL_ERR_INVALID_ARG, "atlas was bound for another triangle count");
     if (!workspace || !aligned(workspace, 256)) return fail(LCL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     return atlas_build_impl(mesh, atlas, workspace, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
@@ -345,6 +369,7 @@ lcl_status check_sphere_call(const lcl_atlas *atlas, const void *layer, lcl_dtyp
         const int32_t lo = -(1 << 22), hi = (1 << 22) + (1 << 21);
         if (st.cx < lo || st.cx > hi || st.cy < lo || st.cy > hi || st.cz < lo || st.cz > hi)
             return fail(LCL_ERR_INVALID_ARG, "stroke centre outside [-2^22, 2^22 + 2^21]");
+        if ((s = check_padding_rows(atlas, st.flags)) != LCL_OK) return s;
     }
     *proceed = true;
     return LCL_OK;
@@ -402,6 +427,7 @@ lcl_status lcl_select_lasso(const lcl_atlas *atlas, void *layer, lcl_dtype dtype
     if (label > (db == 1 ? 0xFFu : 0xFFFFu)) return fail(LCL_ERR_INVALID_ARG, "label does not fit the layer dtype");
     if ((flags & ~0xFFu) || (flags & 15u) > 8 || ((flags >> 4) & 15u) > 8)
         return fail(LCL_ERR_INVALID_ARG, "lasso flags: padding radius and thickness at most 8, other bits 0");
+    if ((s = check_padding_rows(atlas, flags)) != LCL_OK) return s;
     if (!std::isfinite(bias)) return fail(LCL_ERR_INVALID_ARG, "bias is not finite");
     if (hits_out && !aligned(hits_out, 8)) return fail(LCL_ERR_INVALID_ARG, "hits_out must be 8-byte aligned");
     if (!workspace || !aligned(workspace, 256)) return fail(LCL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
@@ -423,6 +449,7 @@ lcl_status lcl_select_tool(const lcl_atlas *atlas, void *layer, lcl_dtype dtype,
     if (!depth || !aligned(depth, 4)) return fail(LCL_ERR_INVALID_ARG, "depth must be a 4-byte aligned device pointer");
     s = check_tool(tool);
     if (s != LCL_OK) return s;
+    if ((s = check_padding_rows(atlas, tool->flags)) != LCL_OK) return s;
     if (label > (db == 1 ? 0xFFu : 0xFFFFu)) return fail(LCL_ERR_INVALID_ARG, "label does not fit the layer dtype");
     if (!std::isfinite(bias)) return fail(LCL_ERR_INVALID_ARG, "bias is not finite");
     if (hits_out && !aligned(hits_out, 8)) return fail(LCL_ERR_INVALID_ARG, "hits_out must be 8-byte aligned");
@@ -520,6 +547,7 @@ lcl_status lcl_numeric_sphere(const lcl_atlas *atlas, const lcl_numeric_layer *l
         if (st.label & ~vmax) return fail(LCL_ERR_INVALID_ARG, "stroke value is wider than the layer type");
         if ((st.flags & ~0x1FFu) || (st.flags & 15u) > 8 || ((st.flags >> 4) & 15u) > 8)
             return fail(LCL_ERR_INVALID_ARG, "stroke flags: padding radius and thickness at most 8, LCL_ERASE, other bits 0");
+        if ((s = check_padding_rows(atlas, st.flags)) != LCL_OK) return s;
         const int32_t lo = -(1 << 22), hi = (1 << 22) + (1 << 21);
         if (st.cx < lo || st.cx > hi || st.cy < lo || st.cy > hi || st.cz < lo || st.cz > hi)
             return fail(LCL_ERR_INVALID_ARG, "stroke centre outside [-2^22, 2^22 + 2^21]");
@@ -547,6 +575,7 @@ lcl_status lcl_numeric_lasso(const lcl_atlas *atlas, const lcl_numeric_layer *la
     if (value & ~value_mask(layer->type)) return fail(LCL_ERR_INVALID_ARG, "value is wider than the layer type");
     if ((flags & ~(0xFFu | LCL_ERASE)) || (flags & 15u) > 8 || ((flags >> 4) & 15u) > 8)
         return fail(LCL_ERR_INVALID_ARG, "flags: padding radius and thickness at most 8, LCL_ERASE, other bits 0");
+    if ((s = check_padding_rows(atlas, flags)) != LCL_OK) return s;
     if (!std::isfinite(bias)) return fail(LCL_ERR_INVALID_ARG, "bias is not finite");
     if (hits_out && !aligned(hits_out, 8)) return fail(LCL_ERR_INVALID_ARG, "hits_out must be 8-byte aligned");
     if (!workspace || !aligned(workspace, 256)) return fail(LCL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
@@ -567,6 +596,7 @@ lcl_status lcl_numeric_tool(const lcl_atlas *atlas, const lcl_numeric_layer *lay
     if (!depth || !aligned(depth, 4)) return fail(LCL_ERR_INVALID_ARG, "depth must be a 4-byte aligned device pointer");
     s = check_tool(tool);
     if (s != LCL_OK) return s;
+    if ((s = check_padding_rows(atlas, tool->flags)) != LCL_OK) return s;
     if (value & ~value_mask(layer->type)) return fail(LCL_ERR_INVALID_ARG, "value is wider than the layer type");
     if (flags & ~LCL_ERASE) return fail(LCL_ERR_INVALID_ARG, "flags must be 0 or LCL_ERASE");
     if (!std::isfinite(bias)) return fail(LCL_ERR_INVALID_ARG, "bias is not finite");

@@ -30,7 +30,7 @@ NO_TRIANGLE = 0xFFFFFFFF
 SUPER = 16
 DEFAULT_BIAS = 2.0 ** -10
 
-EXPORTS = ["lcl_atlas_bytes", "lcl_atlas_bind", "lcl_atlas_rows", "lcl_atlas_workspace_bytes", "lcl_atlas_build",
+EXPORTS = ["lcl_atlas_bytes", "lcl_atlas_bind", "lcl_atlas_bind_band", "lcl_atlas_rows", "lcl_atlas_workspace_bytes", "lcl_atlas_build",
            "lcl_quantize_sphere", "lcl_quantize_spheres", "lcl_camera_from_vp", "lcl_select_workspace_bytes", "lcl_select_sphere",
            "lcl_select_sphere_static", "lcl_depth_workspace_bytes", "lcl_depth_render", "lcl_select_lasso", "lcl_select_tool",
            "lcl_batch_limits_of", "lcl_batch_workspace_bytes", "lcl_batch_staging_bytes", "lcl_batch_upload",
@@ -54,7 +54,7 @@ class lcl_atlas(C.Structure):
                 ("row0", C.c_int32), ("n_tri", C.c_int64),
                 ("pos_x", C.c_void_p), ("pos_y", C.c_void_p), ("pos_z", C.c_void_p), ("tri", C.c_void_p),
                 ("cover", C.c_void_p), ("tile_box", C.c_void_p), ("super_box", C.c_void_p), ("area_w", C.c_void_p),
-                ("bbox_min", C.c_float * 3), ("_pad", C.c_int32), ("scale", C.c_double)]
+                ("bbox_min", C.c_float * 3), ("tex_height", C.c_int32), ("scale", C.c_double)]
 
 
 class lcl_sphere(C.Structure):
@@ -155,6 +155,7 @@ def library():
         "lcl_atlas_bytes": (SZ, [I32, I32, I32, I64]),
         "lcl_atlas_bind": (st, [P, SZ, I32, I32, I32, I64, C.POINTER(lcl_atlas)]),
         "lcl_atlas_rows": (st, [C.POINTER(lcl_atlas), I32, I32, C.POINTER(lcl_atlas)]),
+        "lcl_atlas_bind_band": (st, [P, SZ, I32, I32, I32, I32, I32, I64, C.POINTER(lcl_atlas)]),
         "lcl_atlas_workspace_bytes": (SZ, [C.POINTER(lcl_mesh), I32, I32]),
         "lcl_atlas_build": (st, [C.POINTER(lcl_mesh), C.POINTER(lcl_atlas), P, SZ, P]),
         "lcl_quantize_sphere": (st, [C.POINTER(lcl_atlas), C.POINTER(D), D, U32, C.POINTER(lcl_sphere)]),
@@ -273,21 +274,29 @@ class Mesh:
 
 
 class Atlas:
-    """One atlas buffer (device) bound with lcl_atlas_bind."""
+    """One atlas buffer (device) bound with lcl_atlas_bind, or with band=(y0, y1) a band atlas of
+    rows [y0, y1) of a width x height texture (lcl_atlas_bind_band)."""
 
-    def __init__(self, width, height, tile, n_tri, device="cuda", buffer=None):
+    def __init__(self, width, height, tile, n_tri, device="cuda", buffer=None, band=None):
         lib = library()
-        nbytes = lib.lcl_atlas_bytes(width, height, tile, n_tri)
+        y0, y1 = (0, height) if band is None else (int(band[0]), int(band[1]))
+        nbytes = lib.lcl_atlas_bytes(width, y1 - y0, tile, n_tri) if y1 > y0 else 0
         if nbytes == 0:
             raise LclError("lcl_atlas_bytes", 1, "invalid atlas sizes")
         self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device) if buffer is None else buffer
         self.c = lcl_atlas()
-        _check("lcl_atlas_bind", lib.lcl_atlas_bind(C.c_void_p(self.buf.data_ptr()), nbytes, width, height, tile,
-                                                   n_tri, C.byref(self.c)))
+        if band is None:
+            _check("lcl_atlas_bind", lib.lcl_atlas_bind(C.c_void_p(self.buf.data_ptr()), nbytes, width, height, tile,
+                                                       n_tri, C.byref(self.c)))
+        else:
+            _check("lcl_atlas_bind_band", lib.lcl_atlas_bind_band(C.c_void_p(self.buf.data_ptr()), nbytes, width,
+                                                                 height, y0, y1, tile, n_tri, C.byref(self.c)))
 
     width = property(lambda s: int(s.c.width))
-    height = property(lambda s: int(s.c.height))
+    height = property(lambda s: int(s.c.height))       # rows this atlas holds
     tile = property(lambda s: int(s.c.tile))
+    row0 = property(lambda s: int(s.c.row0))           # first texture row it holds
+    tex_height = property(lambda s: int(s.c.tex_height))
 
     def _view(self, ptr, count, dtype, shape):
         off = ptr - self.buf.data_ptr()

@@ -77,6 +77,41 @@ def test_atlas_layout(lcl):
     assert lib.lcl_atlas_rows(C.byref(a), 0, 71, C.byref(v)) == 1
 
 
+def test_band_atlas_binding(lcl):
+    """lcl_atlas_bind_band: rows [y0, y1) of a texture, laid out as an atlas of y1 - y0 rows with its
+    own boxes; texture padding is refused on it (host-side checks only)."""
+    lib = lcl.library()
+    W, TH, T, n = 128, 300, 32, 50
+    a = lcl.lcl_atlas()
+    nb = lib.lcl_atlas_bytes(W, 300 - 192, T, n)
+    assert lib.lcl_atlas_bind_band(C.c_void_p(1 << 40), nb, W, TH, 192, 300, T, n, C.byref(a)) == 0
+    assert (a.height, a.row0, a.tex_height, a.tiles_y, a.tiles_x) == (108, 192, 300, 4, 4)
+    assert a.tile_box is not None and a.super_box is not None
+    w = lcl.lcl_atlas()
+    assert lib.lcl_atlas_bind(C.c_void_p(1 << 40), lib.lcl_atlas_bytes(W, TH, T, n), W, TH, T, n, C.byref(w)) == 0
+    assert (w.row0, w.tex_height) == (0, TH)
+    for y0, y1 in ((-1, 10), (10, 10), (200, 301)):
+        assert lib.lcl_atlas_bind_band(C.c_void_p(1 << 40), nb, W, TH, y0, y1, T, n, C.byref(a)) == 1
+    assert lib.lcl_atlas_bind_band(C.c_void_p(1 << 40), nb - 1, W, TH, 192, 300, T, n, C.byref(a)) == 2
+    assert lib.lcl_atlas_bind_band(C.c_void_p(1 << 40), nb, W, TH, 192, 300, T, n, C.byref(a)) == 0
+    recs = np.zeros(2, lcl.SPHERE_DTYPE)
+    recs[1]["flags"] = 1                                     # padding radius 1
+    wsb = lib.lcl_select_workspace_bytes(C.byref(a), 2)
+    P = lambda r: r.ctypes.data_as(C.c_void_p)  # noqa: E731
+    st = lib.lcl_select_sphere(C.byref(a), C.c_void_p(1 << 41), 1, P(recs), 2, None, C.c_void_p(1 << 42), wsb, None)
+    assert st == 4 and "band" in lcl.lcl_last_error()
+    cam = lcl.lcl_camera()
+    cam.width, cam.height = 64, 48
+    poly = np.zeros((3, 2), np.float32)
+    st = lib.lcl_select_lasso(C.byref(a), C.c_void_p(1 << 41), 1, C.byref(cam), C.c_void_p(1 << 43), P(poly), 3, 5,
+                              0x22, C.c_float(0.001), None, C.c_void_p(1 << 42), wsb, None)
+    assert st == 4
+    bad = lcl.lcl_atlas.from_buffer_copy(a)
+    bad.row0 = 250                                           # rows past the texture
+    st = lib.lcl_overlay(C.byref(bad), C.c_void_p(1 << 41), C.c_void_p(1 << 41), C.c_void_p(1 << 41), 1, 0, 0, None)
+    assert st == 1
+
+
 def _bound(lcl, W=64, H=64, T=16, n=10):
     lib = lcl.library()
     a = lcl.lcl_atlas()
