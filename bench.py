@@ -15,6 +15,11 @@ texel of each overlay and each area query -- over the whole step.  The roofline 
 for the sphere edits (the dominant kernels): algorithmic bytes = hit texels x (12 B of
 position + 1 B of label), over their CUDA-event time, against the measured HBM copy peak.
 
+With N GPUs (torchrun, one rank each) the texture is split into N row bands (tile rows dealt
+out evenly): each rank builds its band atlas, applies every stroke and lasso to its rows, runs the
+overlays and area queries on them and sums the area tables with one all-reduce per step; texels
+add up over ranks and the slowest rank sets the time (strong scaling: the total work is fixed).
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 from __future__ import annotations
@@ -245,7 +250,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2501_14807_gb300 import lcl
+    from paper_2501_14807_gb300 import lcl, shard
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -260,13 +265,17 @@ def run_ours(args):
     cpu = cpu_baseline(w, args.cpu_rows) if (rank == 0 and world == 1 and args.cpu_rows > 0) else None
     cpu_all = cpu_baseline_all_cores(w, args.cpu_rows) if cpu is not None else None
 
+    # N ranks split the texture into row bands (one band atlas and the same rows of every layer per
+    # rank; every stroke, lasso and depth map on every rank; the area tables summed over ranks)
+    y0, y1 = shard.band_rows(H, w.tile, world, rank) if world > 1 else (0, H)
+    rows = y1 - y0
     mesh = lcl.Mesh.from_host(w.mesh, dev)
-    atlas = lcl.Atlas(W, H, w.tile, w.mesh.n_tri, dev)
-    ws_atlas = torch.empty(lcl.lcl_atlas_workspace_bytes(mesh, W, H), dtype=torch.uint8, device=dev)
+    atlas = lcl.Atlas(W, H, w.tile, w.mesh.n_tri, dev, band=(y0, y1) if world > 1 else None)
+    ws_atlas = torch.empty(lcl.lcl_atlas_workspace_bytes(mesh, W, rows), dtype=torch.uint8, device=dev)
     lcl.lcl_atlas_build(mesh, atlas, ws_atlas)
     lt = torch.uint8 if w.dtype_bytes == 1 else torch.int16
-    layers = [torch.zeros((H, W), dtype=lt, device=dev) for _ in range(w.n_layers)]
-    outs = [torch.empty((H, W), dtype=lt, device=dev) for _ in w.overlays]
+    layers = [torch.zeros((rows, W), dtype=lt, device=dev) for _ in range(w.n_layers)]
+    outs = [torch.empty((rows, W), dtype=lt, device=dev) for _ in w.overlays]
     per_layer = []
     for li in range(w.n_layers):
         sel = np.nonzero(w.strokes.layer == li)[0]
@@ -283,8 +292,9 @@ def run_ours(args):
     ws_depth = torch.empty(max([lcl.lcl_depth_workspace_bytes(mesh, c.width, c.height) for c in w.cams] + [256]),
                            dtype=torch.uint8, device=dev)
     lasso_hits = torch.zeros(max(len(w.lassos), 1), dtype=torch.int64, device=dev)
-    counts = [torch.empty(w.n_labels, dtype=torch.int64, device=dev) for _ in range(w.n_layers)]
-    areas = [torch.empty(w.n_labels, dtype=torch.int64, device=dev) for _ in range(w.n_layers)]
+    table_buf = torch.empty(2 * w.n_layers * w.n_labels, dtype=torch.int64, device=dev)   # counts | areas
+    counts = [table_buf[li * w.n_labels:(li + 1) * w.n_labels] for li in range(w.n_layers)]
+    areas = [table_buf[(w.n_layers + li) * w.n_labels:(w.n_layers + li + 1) * w.n_labels] for li in range(w.n_layers)]
     stream = torch.cuda.current_stream(dev)
 
     # one event at each boundary between the rows of a step (recorded on the launching stream)
@@ -310,6 +320,8 @@ def run_ours(args):
         mark(5)
         for li, layer in enumerate(layers):
             lcl.lcl_label_area(atlas, layer, w.n_labels, counts[li], areas[li], stream)
+        if world > 1:   # the whole texture's tables: one all-reduce of the integer sums
+            shard.reduce_tables([table_buf])
         mark(6)
 
     def barrier():
@@ -324,7 +336,7 @@ def run_ours(args):
     # texels per step (identical every step: the same strokes on the same atlas)
     sph_hits = sum(int(h[:len(r)].sum().item()) for h, r in zip(sphere_hits, per_layer))
     las_hits = int(lasso_hits[:len(w.lassos)].sum().item())
-    texels = sph_hits + las_hits + (len(w.overlays) + w.n_layers) * W * H
+    texels = sph_hits + las_hits + (len(w.overlays) + w.n_layers) * W * rows
 
     clocks = Clocks(local)
     clocks.start()
@@ -389,6 +401,8 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     serving = serving_summary(args.serving_models, 20000.0, 1.0) if (world == 1 and args.serving_models > 0) else None
+    # the batching workload (256 models, 64 queued strokes each), outside the timed region
+    batch = batch_summary(args.batch_models, 5, 2, torch_device=local) if (world == 1 and args.batch_models > 0) else None
     peak, peak_kind = peaks()
     sph_bytes = sph_hits * (12 + w.dtype_bytes)
     achieved = sph_bytes / (sph_ms / args.steps / 1e3) / 1e9
@@ -397,8 +411,11 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded vessels; scans unavailable)",
-        "config": workload_desc(w, args),
+        "scaling": "strong", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded vessels; scans unavailable)",
+        "config": dict(workload_desc(w, args),
+                       parallelism=(f"{world} row bands of the one texture, one per GPU (tile rows dealt out evenly; "
+                                    "strokes, lassos and depth maps on every GPU; the area tables summed by one "
+                                    "all-reduce per step)") if world > 1 else "1 GPU, the whole texture"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic,
                      "kernel": "sphere edit (k_sphere_step, one launch per stroke)",
@@ -411,6 +428,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "serving": serving,
+        "batch": batch,
         "breakdown": {"sphere_ms_per_step": sph_ms / args.steps, "sphere_hit_texels": sph_hits,
                       "lasso_hit_texels": las_hits, "texels_per_step": texels},
         "rows": row_rooflines(w, row_ms, args.steps, sph_hits, las_hits, peak),
@@ -503,7 +521,7 @@ def sphere_radius_breakdown(w, atlas, layers, per_layer, ws_sel, stream, dev):
 
 def combine_ranks(times_ms, texels, world, device):
     """Whole-job figures over ranks: the maximum of each time and the sum of the texels (each rank
-    edits its own model, so the texels add up; the slowest rank sets the time)."""
+    edits its own rows of the texture, so the texels add up; the slowest rank sets the time)."""
     import torch
     import torch.distributed as dist
     tt = torch.tensor(list(times_ms), dtype=torch.float64, device=device)
@@ -515,17 +533,29 @@ def combine_ranks(times_ms, texels, world, device):
 
 
 def run_batch(args):
+    """Batching workload as its own JSON line (see batch_summary)."""
+    r = batch_summary(args.models or 256, args.steps, args.warmup, torch_device=0)
+    line = {"metric": METRIC, "value": r["batched"]["gtexels_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["batched"]["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": r.pop("config"), "gpu_launches": 3}
+    line.update(r)
+    print(json.dumps(line), flush=True)
+
+
+def batch_summary(n_models, steps, warmup, torch_device=0):
     """Batching workload: many models of uneven size, 64 queued sphere/lasso strokes each, edited by
     one batched launch (descriptor upload + cull + persistent apply), against the same strokes as
-    per-model, per-stroke calls.  Both arms do identical work (bit-identical results, checked)."""
+    per-model, per-stroke calls.  Both arms do identical work (bit-identical results, checked).
+    Bytes: hit texels x (12 B position + 1 B label), the per-stroke algorithmic bytes summed over
+    strokes, over the batched time, against the measured copy peak."""
     import torch
 
     import synth
     from paper_2501_14807_gb300 import lcl
 
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch_device)
     torch.cuda.set_device(dev)
-    bms = synth.config_batch(args.models or 256, depth_side=1024)
+    bms = synth.config_batch(n_models, depth_side=1024)
     models, queues, layers, inits = [], [], [], []
     for bm in bms:
         mesh = lcl.Mesh.from_host(bm.mesh, dev)
@@ -579,22 +609,22 @@ def run_batch(args):
         torch.cuda.synchronize(dev)
         return e0.elapsed_time(e1) / steps
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         sequential()
     torch.cuda.synchronize(dev)
     ref = [l.clone() for l in layers]
     hits = int(sum(int(h.sum().item()) for h in hit_bufs))
     l0 = lcl.lcl_kernel_launches()
-    seq_ms = timed(sequential, args.steps)
-    seq_launches = (lcl.lcl_kernel_launches() - l0) // args.steps
+    seq_ms = timed(sequential, steps)
+    seq_launches = (lcl.lcl_kernel_launches() - l0) // steps
     for l in layers:
         l.zero_()
     # default launch shape, then the autotuner on the uploaded batch, then one CUDA graph of the
     # tuned launch; every timed step uploads the descriptors and replays the graph
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batched_default()
         torch.cuda.synchronize(dev)
-    def_ms = timed(batched_default, args.steps)
+    def_ms = timed(batched_default, steps)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     lcl.lcl_batch_upload(batch, stream)
@@ -606,20 +636,19 @@ def run_batch(args):
         lcl.lcl_batch_upload(batch, stream)
         graph.replay()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batched()
         torch.cuda.synchronize(dev)
-    clocks = Clocks(0)
+    clocks = Clocks(torch_device)
     clocks.start()
     time.sleep(0.3)
-    bat_ms = timed(batched, args.steps)
+    bat_ms = timed(batched, steps)
     clk = clocks.stop()
     same = all(torch.equal(r, l) for r, l in zip(ref, layers))
     n_strokes = sum(len(q) for q in queues)
-    line = {"metric": METRIC, "value": hits / (bat_ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": bat_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": f"batching: {len(models)} models ({sum(b.mesh.n_tri for b in bms)} triangles, "
+    peak, peak_kind = peaks()
+    gbs = hits * 13 / (bat_ms / 1e3) / 1e9
+    return {"config": {"workload": f"batching: {len(models)} models ({sum(b.mesh.n_tri for b in bms)} triangles, "
                                    f"atlases 512^2-4096^2 u8), {n_strokes} queued strokes (48 sphere + 16 lasso "
                                    f"per model)", "mode": "batched launch (descriptor upload + CUDA graph replay "
                                                           "of the tuned shape) vs per-model per-stroke calls"},
@@ -629,9 +658,11 @@ def run_batch(args):
             "upload_host_ms": upload_host_ms,
             "autotune": {"best_ms": tune_ms, "candidates": "threads 64/128/256 x split 1/2/4/8 x CTAs/SM all/half"},
             "per_stroke_calls": {"ms": seq_ms, "gtexels_s": hits / (seq_ms / 1e3) / 1e9, "launches": int(seq_launches)},
-            "speedup": seq_ms / bat_ms, "identical_results": bool(same), "hit_texels": hits, "gpu_launches": 3,
-            "clocks": clk}
-    print(json.dumps(line), flush=True)
+            "speedup": seq_ms / bat_ms, "identical_results": bool(same), "hit_texels": hits,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": gbs / peak, "bytes": "hit texels x 13 B, summed over strokes (per-stroke "
+                                                      "algorithmic bytes; positions are read once per tile)"},
+            "steps": steps, "warmup": warmup, "clocks": clk}
 
 
 def serving_setup(n_models, seed=5):
@@ -1013,6 +1044,8 @@ def main():
     ap.add_argument("--duration", type=float, default=5.0, help="serving: trace length (s)")
     ap.add_argument("--models", type=int, default=None,
                     help="models in the batching (default 256) / serving (default 128: 64 resident + 64 spilled) workload")
+    ap.add_argument("--batch-models", type=int, default=256,
+                    help="models of the batching workload reported in the headline line (0: skip)")
     ap.add_argument("--serving-models", type=int, default=32,
                     help="models of the short serving run reported in the headline line (0: skip)")
     ap.add_argument("--atlas-side", type=int, default=None,
