@@ -587,6 +587,16 @@ uint64_t lcl_kernel_launches(void);
  * no call returns LCL_ERR_TIMEOUT (reserved). */
 lcl_status lcl_last_device_status(lcl_stream stream);
 
+/* Self-check of the library's division (device diagnostic).  The edits project texels with IEEE
+ * binary32 division (Section 4.3.1's projective texturing, written out in lcl_select_lasso); the
+ * library computes it on a faster route for operands in [2^-30, 2^31) and must give exactly the
+ * correctly rounded quotient everywhere.  This call compares the two on n operand pairs drawn
+ * from `seed` (random operands across and beyond that window, quotients next to rounding
+ * midpoints, the window's edges, zeros, subnormals, infinities, NaN) and adds to counts[0] the
+ * pairs compared and to counts[1] those whose results differ (NaN equals NaN).  counts: device,
+ * two uint64 (not cleared by the call). */
+lcl_status lcl_check_division(uint64_t n, uint32_t seed, uint64_t *counts, lcl_stream stream);
+
 #define LCL_BUILD_BOUNDS_CHECKS 1u  /* lcl_build_flags bit: kernels check their indices */
 /* How this library was built (LCL_BUILD_* bits). */
 uint32_t lcl_build_flags(void);

@@ -674,6 +674,11 @@ const char *lcl_status_str(lcl_status status) {
 
 const char *lcl_last_error(void) { return g_last_error.c_str(); }
 
+lcl_status lcl_check_division(uint64_t n, uint32_t seed, uint64_t *counts, lcl_stream stream) {
+    if (!counts || !aligned(counts, 8)) return fail(LCL_ERR_INVALID_ARG, "counts must be an 8-byte aligned device pointer");
+    return division_check_impl(n, seed, counts, reinterpret_cast<cudaStream_t>(stream));
+}
+
 uint32_t lcl_build_flags(void) {
 #ifdef LCL_DEBUG_BOUNDS
     return LCL_BUILD_BOUNDS_CHECKS;

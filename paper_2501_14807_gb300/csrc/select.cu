@@ -230,7 +230,9 @@ __global__ void __launch_bounds__(kThreads) k_sphere_step(AtlasDev a, L *__restr
 // (blockIdx.z selects its share when a super-tile is split over several CTAs), 8 lanes per tile
 // (box_may_touch8); the super-tile's own box is tested first, uniformly over the CTA.  FLAGS:
 // write a 0/1 flag per tile instead of appending candidates (first pass of a padded edit).
-template <bool FLAGS>
+// CLASSIFY (lassos): tiles that lasso_tile_class8 finds outside the polygon are dropped, and those
+// it finds inside are listed with kInsideTile set (their texels skip the edge tests).
+template <bool FLAGS, bool CLASSIFY>
 __global__ void __launch_bounds__(kThreads) k_lasso_cull(AtlasDev a, const __grid_constant__ LassoArg p,
                                                          const float *__restrict__ depth, uint32_t *counter,
                                                          uint32_t *list) {
@@ -246,17 +248,26 @@ __global__ void __launch_bounds__(kThreads) k_lasso_cull(AtlasDev a, const __gri
         const int32_t tx = sx * LCL_SUPER + local % LCL_SUPER, ty = sy * LCL_SUPER + local / LCL_SUPER;
         const bool in_grid = tx < a.tiles_x && ty < a.tiles_y;  // uniform over each group of 8 lanes
         bool cand = false;
+        int cls = kTileTest;
         // the group's 8 lanes take the same branch (in_grid and the index check are per tile)
         if (super_in && in_grid && LCL_IN((int64_t)ty * a.tiles_x + tx, n_tiles)) {
             const int4 *tb = reinterpret_cast<const int4 *>(a.tile_box + 8 * ((int64_t)ty * a.tiles_x + tx));
             const int4 lo = tb[0], hi = tb[1];
-            cand = lo.w > 0 && box_may_touch8(p, lo, hi, depth);
+            if (lo.w > 0) {  // uniform over the group (one tile)
+                float4 sb;
+                cand = box_may_touch8(p, lo, hi, depth, CLASSIFY ? &sb : nullptr);
+                if (CLASSIFY && cand) {
+                    cls = lasso_tile_class8(p, sb);
+                    cand = cls != kTileOut;
+                }
+            }
         }
         const uint32_t tile = (uint32_t)(ty * a.tiles_x + tx);
         if (FLAGS) {
             if (in_grid && (threadIdx.x & 7u) == 0 && LCL_IN(tile, n_tiles)) list[tile] = cand ? 1u : 0u;
         } else {
-            append_candidate(cand && (threadIdx.x & 7u) == 0, tile, counter, list, n_tiles);
+            append_candidate(cand && (threadIdx.x & 7u) == 0, tile | (cls == kTileIn ? kInsideTile : 0u), counter,
+                             list, n_tiles);
         }
     }
 }
@@ -312,6 +323,8 @@ __device__ uint32_t lasso_pad_mask(const AtlasDev &a, int64_t l, int4 X, const L
     return m;
 }
 
+// A lasso's candidate-list entry: tile index, kInsideTile set when every texel of the tile that
+// projects lies inside the polygon (lasso_tile_class8).  Padded edits list plain tile indices.
 template <typename L, bool NUM, bool PAD>
 __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restrict__ layer,
                                                           const __grid_constant__ LassoArg p,
@@ -329,7 +342,9 @@ __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restr
     const int64_t n_tex = (int64_t)a.w * a.h;
     for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
         if (!LCL_IN(i, (int64_t)a.tiles_x * a.tiles_y)) break;
-        const uint32_t tile = list[i];
+        const uint32_t entry = list[i];
+        const bool inside = (entry & kInsideTile) != 0u;  // uniform over the CTA
+        const uint32_t tile = entry & ~kInsideTile;
         const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
         for (int32_t qd = threadIdx.x; qd < nq; qd += kThreads) {
             const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
@@ -339,7 +354,7 @@ __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restr
             const int4 X = __ldg(reinterpret_cast<const int4 *>(a.px + l));
             const int4 Y = __ldg(reinterpret_cast<const int4 *>(a.py + l));
             const int4 Z = __ldg(reinterpret_cast<const int4 *>(a.pz + l));
-            const uint32_t m = lasso_quad(p, sh, depth, X, Y, Z);
+            const uint32_t m = inside ? lasso_quad<true>(p, sh, depth, X, Y, Z) : lasso_quad<false>(p, sh, depth, X, Y, Z);
             const uint32_t pm = PAD ? lasso_pad_mask(a, l, X, p, sh, depth, pad_r, pad_t) : 0u;
             if (m | pm) {
                 store_hits<L>(layer, l, m | pm, p.label);
@@ -401,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_tool_apply(AtlasDev a, L *__res
     const int64_t n_tex = (int64_t)a.w * a.h;
     for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
         if (!LCL_IN(i, (int64_t)a.tiles_x * a.tiles_y)) break;
-        const uint32_t tile = list[i];
+        const uint32_t tile = list[i] & ~kInsideTile;  // the tool's cull lists plain tiles
         const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
         for (int32_t qd = threadIdx.x; qd < nq; qd += kThreads) {
             const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
@@ -446,22 +461,105 @@ SelWs sel_ws(const lcl_atlas *a, int32_t n, void *ws) {
 // go to w.list2 first.  Small atlases split each super-tile over up to 8 CTAs so that the grid
 // still covers the GPU.  Returns the number of launches.
 int launch_lasso_cull(const AtlasDev &a, const lcl_atlas *atlas, const LassoArg &p, const float *depth,
-                      const SelWs &w, bool pad, cudaStream_t st) {
+                      const SelWs &w, bool pad, bool classify, cudaStream_t st) {
     const int n_super = atlas->supers_x * atlas->supers_y;
     const int split = std::max(1, std::min(8, (4 * sm_count() + n_super - 1) / n_super));
     const dim3 cg(atlas->supers_x, atlas->supers_y, split);
     if (!pad) {
-        k_lasso_cull<false><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list);
+        if (classify) k_lasso_cull<false, true><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list);
+        else k_lasso_cull<false, false><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list);
         return 1;
     }
-    k_lasso_cull<true><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list2);
+    // padded edits: flags for every tile that may hold a selected texel (polygon-outside tiles of a
+    // lasso hold none), dilated to the tiles padding can reach
+    if (classify) k_lasso_cull<true, true><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list2);
+    else k_lasso_cull<true, false><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list2);
     const int64_t tiles = (int64_t)atlas->tiles_x * atlas->tiles_y;
     k_dilate_candidates<<<(unsigned)((tiles + kThreads - 1) / kThreads), kThreads, 0, st>>>(a, w.list2, w.counters,
                                                                                         w.list);
     return 2;
 }
 
+// ---- division check ----------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// Compares div_rn with __fdiv_rn on operand i of four families (i % 4): random signs and mantissas
+// with exponents across and beyond div_rn's window; quotients next to a rounding midpoint (a = q b
+// rounded, +-1 ulp); operands at the window's edges and just outside; special values (zeros,
+// subnormals, infinities, NaN, the largest and smallest normals, tiny positive and negative w).
+// counts[0] += compared, counts[1] += mismatches (NaN results compare equal to NaN).
+__global__ void k_check_division(uint64_t n, uint32_t seed, unsigned long long *counts) {
+    unsigned long long cmp = 0, bad = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t h1 = mix32((uint32_t)i * 2u + seed), h2 = mix32((uint32_t)(i >> 32) ^ ((uint32_t)i * 2u + 1u) ^ (seed * 0x9e3779b9u));
+        float a, b;
+        switch (i & 3u) {
+        case 0: {  // exponents 67..187 (the window is 97..157)
+            const uint32_t ea = 67u + (h1 >> 25) % 121u, eb = 67u + (h2 >> 25) % 121u;
+            a = __uint_as_float((h1 & 0x80000000u) | (ea << 23) | (h2 & 0x7FFFFFu));
+            b = __uint_as_float((h2 & 0x80000000u) | (eb << 23) | (h1 & 0x7FFFFFu));
+            break;
+        }
+        case 1: {  // near-midpoint quotients: a = RN(q b) and its neighbours
+            const uint32_t eq = 97u + (h1 >> 26) % 30u, eb = 110u + (h2 >> 27) % 30u;
+            const float q = __uint_as_float((eq << 23) | (h1 & 0x7FFFFFu));
+            b = __uint_as_float((h2 & 0x80000000u) | (eb << 23) | (h2 & 0x7FFFFFu));
+            a = __fmul_rn(q, b);
+            a = __uint_as_float(__float_as_uint(a) + (h1 >> 30) - 1u);
+            break;
+        }
+        case 2: {  // window edges: exponents 95..99 and 155..159, mantissas at their ends
+            const uint32_t edges[10] = {95u, 96u, 97u, 98u, 99u, 155u, 156u, 157u, 158u, 159u};
+            const uint32_t ma = (h1 & 1u) ? 0x7FFFFFu : (h1 & 2u) ? 0u : (h2 & 0x7FFFFFu);
+            const uint32_t mb = (h2 & 1u) ? 0x7FFFFFu : (h2 & 2u) ? 0u : (h1 & 0x7FFFFFu);
+            a = __uint_as_float((h1 & 0x80000000u) | (edges[(h1 >> 8) % 10u] << 23) | ma);
+            b = __uint_as_float((h2 & 0x80000000u) | (edges[(h2 >> 8) % 10u] << 23) | mb);
+            break;
+        }
+        default: {  // special values against random ones
+            const float sp[12] = {0.0f, -0.0f, __uint_as_float(1u), __uint_as_float(0x807FFFFFu), INFINITY, -INFINITY,
+                                  __uint_as_float(0x7FC00000u), 3.4028235e38f, 1.17549435e-38f, 1e-30f, -1e-30f,
+                                  7.0f};
+            const float rnd = __uint_as_float((h1 & 0x80000000u) | ((97u + (h2 >> 26) % 61u) << 23) | (h2 & 0x7FFFFFu));
+            const float s = sp[(h1 >> 4) % 12u];
+            a = (h2 & 1u) ? s : rnd;
+            b = (h2 & 1u) ? rnd : s;
+            if ((h2 & 6u) == 6u) b = sp[(h2 >> 9) % 12u];
+            break;
+        }
+        }
+        const float q = __fdiv_rn(a, b), m = div_rn(a, b);
+        const bool same = __float_as_uint(q) == __float_as_uint(m) || (isnan(q) && isnan(m));
+        ++cmp;
+        bad += same ? 0 : 1;
+    }
+    for (int o = 16; o; o >>= 1) {
+        cmp += __shfl_xor_sync(0xffffffffu, cmp, o);
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(counts, cmp);
+        if (bad) atomicAdd(counts + 1, bad);
+    }
+}
+
 }  // namespace
+
+lcl_status division_check_impl(uint64_t n, uint32_t seed, uint64_t *counts, cudaStream_t st) {
+    k_check_division<<<sm_count() * 8, kThreads, 0, st>>>(n, seed, reinterpret_cast<unsigned long long *>(counts));
+    count_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "lcl_check_division launch");
+    return LCL_OK;
+}
 
 size_t select_ws_bytes(const lcl_atlas *a, int32_t n) {
     return align256((size_t)(n + 1) * 4) + 3 * align256((size_t)a->tiles_x * a->tiles_y * 4);
@@ -563,7 +661,7 @@ lcl_status lasso_run(const lcl_atlas *atlas, void *layer, int bytes, uint32_t *m
     const int32_t pad_r = (int32_t)(pad_flags & 15u), pad_t = (int32_t)((pad_flags >> 4) & 15u);
     const bool pad = pad_r > 0;
     k_sel_init<<<1, kThreads, 0, st>>>(w.counters, 1, h);
-    const int n_cull = launch_lasso_cull(a, atlas, p, depth, w, pad, st);
+    const int n_cull = launch_lasso_cull(a, atlas, p, depth, w, pad, true, st);
     ValMask vm;
     vm.bits = mask;
     vm.set = set;
@@ -636,7 +734,7 @@ lcl_status tool_run(const lcl_atlas *atlas, void *layer, int bytes, uint32_t *ma
     fill_tool_arg(t, p, cam, tool, label, bias);
     k_sel_init<<<1, kThreads, 0, st>>>(w.counters, 1, h);
     const bool pad = t.pad_r > 0;
-    const int n_cull = launch_lasso_cull(a, atlas, p, depth, w, pad, st);
+    const int n_cull = launch_lasso_cull(a, atlas, p, depth, w, pad, false, st);
     const int sel = (tool->shape != nullptr ? 1 : 0) + (pad ? 2 : 0);
     ValMask vm;
     vm.bits = mask;

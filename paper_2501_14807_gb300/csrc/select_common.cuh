@@ -247,7 +247,7 @@ __device__ __forceinline__ bool edge_left(const float *__restrict__ vx, int e, f
     if (xs < lo) return true;
     if (xs > hi) return false;
     const float ax = vx[e], bx = vx[e + 1];
-    const float xi = __fadd_rn(__fdiv_rn(__fmul_rn(__fsub_rn(bx, ax), __fsub_rn(ys, ay)), __fsub_rn(by, ay)), ax);
+    const float xi = __fadd_rn(div_rn(__fmul_rn(__fsub_rn(bx, ax), __fsub_rn(ys, ay)), __fsub_rn(by, ay)), ax);
     return xs < xi;
 }
 
@@ -280,9 +280,9 @@ __device__ inline bool box_may_touch(const LassoArg &p, int4 lo, int4 hi, const 
         float x = (float)((c & 1) ? hi.x : lo.x), y = (float)((c & 2) ? hi.y : lo.y), z = (float)((c & 4) ? hi.z : lo.z);
         float cw = clip_row(p.m + 12, x, y, z);
         if (!(cw > 0.0f)) return true;
-        float xs = screen_of(__fdiv_rn(clip_row(p.m, x, y, z), cw), p.ws);
-        float ys = screen_of(__fdiv_rn(clip_row(p.m + 4, x, y, z), cw), p.hs);
-        float zn = __fdiv_rn(clip_row(p.m + 8, x, y, z), cw);
+        float xs = screen_of(div_rn(clip_row(p.m, x, y, z), cw), p.ws);
+        float ys = screen_of(div_rn(clip_row(p.m + 4, x, y, z), cw), p.hs);
+        float zn = div_rn(clip_row(p.m + 8, x, y, z), cw);
         xmin = fminf(xmin, xs); xmax = fmaxf(xmax, xs);
         ymin = fminf(ymin, ys); ymax = fmaxf(ymax, ys);
         zmin = fminf(zmin, zn);
@@ -307,19 +307,24 @@ __device__ inline bool box_may_touch(const LassoArg &p, int4 lo, int4 hi, const 
 // box): lane c projects corner c, the group reduces the screen box and the nearest depth, and the
 // depth-footprint scan is split by rows over the group.  The tests of box_may_touch, with
 // footprints of up to 2048 px scanned (1024 there) before the test gives up and keeps the box.
-__device__ __forceinline__ bool box_may_touch8(const LassoArg &p, int4 lo, int4 hi, const float *__restrict__ depth) {
+// sbox (optional): the screen box {xmin, xmax, ymin, ymax} of the projected corners when every
+// corner lies in front of the camera and projects to finite coordinates, else NaNs.
+__device__ __forceinline__ bool box_may_touch8(const LassoArg &p, int4 lo, int4 hi, const float *__restrict__ depth,
+                                               float4 *sbox = nullptr) {
     const unsigned lane = threadIdx.x & 31u, sub = lane & 7u;
     const unsigned gm = 0xFFu << (lane & 24u);
     const float x = (float)((sub & 1u) ? hi.x : lo.x), y = (float)((sub & 2u) ? hi.y : lo.y);
     const float z = (float)((sub & 4u) ? hi.z : lo.z);
     const float cw = clip_row(p.m + 12, x, y, z);
+    if (sbox) *sbox = make_float4(NAN, NAN, NAN, NAN);
     if (__any_sync(gm, !(cw > 0.0f))) return true;
     // each lane folds its corner into empty bounds exactly as the serial loop does (NaN ignored)
-    const float xs = screen_of(__fdiv_rn(clip_row(p.m, x, y, z), cw), p.ws);
-    const float ys = screen_of(__fdiv_rn(clip_row(p.m + 4, x, y, z), cw), p.hs);
+    const float xs = screen_of(div_rn(clip_row(p.m, x, y, z), cw), p.ws);
+    const float ys = screen_of(div_rn(clip_row(p.m + 4, x, y, z), cw), p.hs);
+    const bool finite = __all_sync(gm, isfinite(xs) && isfinite(ys));
     float xmin = fminf(INFINITY, xs), xmax = fmaxf(-INFINITY, xs);
     float ymin = fminf(INFINITY, ys), ymax = fmaxf(-INFINITY, ys);
-    float zmin = fminf(INFINITY, __fdiv_rn(clip_row(p.m + 8, x, y, z), cw));
+    float zmin = fminf(INFINITY, div_rn(clip_row(p.m + 8, x, y, z), cw));
     for (int o = 1; o < 8; o <<= 1) {
         xmin = fminf(xmin, __shfl_xor_sync(gm, xmin, o));
         xmax = fmaxf(xmax, __shfl_xor_sync(gm, xmax, o));
@@ -328,6 +333,7 @@ __device__ __forceinline__ bool box_may_touch8(const LassoArg &p, int4 lo, int4 
         zmin = fminf(zmin, __shfl_xor_sync(gm, zmin, o));
     }
     if (xmax < p.bx0 || xmin > p.bx1 || ymax < p.by0 || ymin > p.by1) return false;
+    if (sbox && finite) *sbox = make_float4(xmin, xmax, ymin, ymax);
     if (!depth) return true;
     const float margin = 2.0f;
     const int ix0 = max(0, __float2int_rd(xmin - margin)), ix1 = min(p.w_s - 1, __float2int_rd(xmax + margin));
@@ -341,6 +347,64 @@ __device__ __forceinline__ bool box_may_touch8(const LassoArg &p, int4 lo, int4 
                 dmax = fmaxf(dmax, __ldg(depth + (int64_t)iy * p.w_s + ix));
     for (int o = 1; o < 8; o <<= 1) dmax = fmaxf(dmax, __shfl_xor_sync(gm, dmax, o));
     return !(zmin - 1e-4f > dmax + p.bias);
+}
+
+// Tile classes for a lasso (the texels of a box projected to screen box `sb`, by box_may_touch8).
+enum : int { kTileOut = 0, kTileTest = 1, kTileIn = 2 };
+
+// Classifies a box whose projection lies in the screen box sb, by the aligned group of 8 lanes of
+// box_may_touch8 (all 8 call it; lane c takes edges c, c + 8, ...):
+//   kTileOut   no edge of the polygon comes near the box and its centre is outside: no texel of the
+//              box is inside (the tile is dropped);
+//   kTileIn    no edge comes near the box, its centre is inside and the box lies on screen: every
+//              texel of the box that projects is inside, so the texels skip the edge tests;
+//   kTileTest  otherwise (every texel is tested).
+// Why this is exact for the per-texel test in FP32: each texel's FP32 screen point lies in sb up to
+// far less than the margin m = 1 px (a few ulps of coordinates below 2^15), and no edge segment meets
+// sb widened by m, so along any straddled edge the crossing lies more than m - 0.05 px from the point,
+// beyond the error bound of the FP32 crossing (edge_xrange's 4.01 u (|ax| + |bx|) < 0.01 px); every
+// per-texel edge decision is then the exact one at that point, and the exact even-odd parity is the
+// same at every point of a region no edge meets -- the parity at the centre.  The segment-box test is
+// conservative: an FP32 side value whose magnitude is within its error bound counts as meeting.
+__device__ __forceinline__ int lasso_tile_class8(const LassoArg &p, float4 sb) {
+    const unsigned lane = threadIdx.x & 31u, sub = lane & 7u;
+    const unsigned gm = 0xFFu << (lane & 24u);
+    if (!(isfinite(sb.x) && isfinite(sb.y) && isfinite(sb.z) && isfinite(sb.w))) return kTileTest;  // uniform
+    const float m = 1.0f;
+    const float x0 = sb.x - m, x1 = sb.y + m, y0 = sb.z - m, y1 = sb.w + m;
+    const float cx = __fmul_rn(0.5f, __fadd_rn(sb.x, sb.y)), cy = __fmul_rn(0.5f, __fadd_rn(sb.z, sb.w));
+    const float u5 = 5.0f * 5.9604645e-8f;  // 5 u, u = 2^-24
+    bool meets = false, parity = false;
+    for (int e = (int)sub; e < p.nv; e += 8) {
+        const float ax = p.vx[e], ay = p.vy[e], bx = p.vx[e + 1], by = p.vy[e + 1];
+        if (!(fmaxf(ax, bx) < x0 || fminf(ax, bx) > x1 || fmaxf(ay, by) < y0 || fminf(ay, by) > y1)) {
+            const float dx = __fsub_rn(bx, ax), dy = __fsub_rn(by, ay);
+            bool pos = false, neg = false;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float X = (c & 1) ? x1 : x0, Y = (c & 2) ? y1 : y0;
+                const float a1 = __fmul_rn(dx, __fsub_rn(Y, ay)), a2 = __fmul_rn(dy, __fsub_rn(X, ax));
+                const float side = __fsub_rn(a1, a2), err = __fmul_rn(u5, __fadd_rn(fabsf(a1), fabsf(a2)));
+                if (side > err) pos = true;
+                else if (side < -err) neg = true;
+                else pos = neg = true;
+            }
+            meets = meets || (pos && neg);
+        }
+        if ((ay > cy) != (by > cy)) {  // the definition's crossing test at the centre
+            const float xi = __fadd_rn(div_rn(__fmul_rn(__fsub_rn(bx, ax), __fsub_rn(cy, ay)), __fsub_rn(by, ay)), ax);
+            if (cx < xi) parity = !parity;
+        }
+    }
+    uint32_t bits = (meets ? 1u : 0u) | (parity ? 2u : 0u);
+    for (int o = 1; o < 8; o <<= 1) {
+        const uint32_t t = __shfl_xor_sync(gm, bits, o);
+        bits = (bits | (t & 1u)) ^ (t & 2u);
+    }
+    if (bits & 1u) return kTileTest;
+    if (!(bits & 2u)) return kTileOut;
+    const bool on_screen = x0 >= 0.0f && x1 < p.ws && y0 >= 0.0f && y1 < p.hs;
+    return on_screen ? kTileIn : kTileTest;
 }
 
 // The lasso test of one texel.  The conditions of the definition are all required, so they are
@@ -364,8 +428,8 @@ __device__ __forceinline__ bool lasso_hit(const LassoArg &p, const Edges &sh, co
     if (cx < __fmul_rn(p.nx0, cw) || cx > __fmul_rn(p.nx1, cw)) return false;
     const float cy = clip_row(p.m + 4, fx, fy, fz);
     if (cy < __fmul_rn(p.ny0, cw) || cy > __fmul_rn(p.ny1, cw)) return false;
-    const float xs = screen_of(__fdiv_rn(cx, cw), p.ws);
-    const float ys = screen_of(__fdiv_rn(cy, cw), p.hs);
+    const float xs = screen_of(div_rn(cx, cw), p.ws);
+    const float ys = screen_of(div_rn(cy, cw), p.hs);
     if (!(xs >= 0.0f && xs < p.ws && ys >= 0.0f && ys < p.hs)) return false;
     if (!(ys >= p.ymin && ys < p.ymax)) return false;  // no edge straddles y
     int band = __float2int_rz(__fmul_rn(__fsub_rn(ys, p.band_y0), p.band_inv_h));
@@ -382,7 +446,7 @@ __device__ __forceinline__ bool lasso_hit(const LassoArg &p, const Edges &sh, co
         }
     }
     if (!inside) return false;
-    const float zn = __fdiv_rn(clip_row(p.m + 8, fx, fy, fz), cw);
+    const float zn = div_rn(clip_row(p.m + 8, fx, fy, fz), cw);
     if (!(zn >= 0.0f && zn <= 1.0f)) return false;
     const int32_t ix = __float2int_rz(xs), iy = __float2int_rz(ys);
     if (!LCL_IN((int64_t)iy * p.w_s + ix, (int64_t)p.w_s * p.h_s)) return false;
@@ -391,10 +455,36 @@ __device__ __forceinline__ bool lasso_hit(const LassoArg &p, const Edges &sh, co
 }
 
 
+// The depth test (Fig. 3a) of the texels `live` of a quad that passed the other steps: NDC depth in
+// [0, 1] and z <= depth[floor(ys)][floor(xs)] + bias.
+__device__ __forceinline__ uint32_t lasso_depth_quad(const LassoArg &p, const float *__restrict__ depth,
+                                                     const int32_t (&xq)[4], const int32_t (&yq)[4],
+                                                     const int32_t (&zq)[4], const float (&xs)[4],
+                                                     const float (&ys)[4], const float (&cw)[4], uint32_t live) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (!(live & (1u << k))) continue;
+        const float zn = div_rn(clip_row(p.m + 8, (float)xq[k], (float)yq[k], (float)zq[k]), cw[k]);
+        if (!(zn >= 0.0f && zn <= 1.0f)) continue;
+        const int32_t ix = __float2int_rz(xs[k]), iy = __float2int_rz(ys[k]);
+        if (!LCL_IN((int64_t)iy * p.w_s + ix, (int64_t)p.w_s * p.h_s)) continue;
+        const float d = __ldg(depth + (int64_t)iy * p.w_s + ix);
+        if (zn <= __fadd_rn(d, p.bias)) m |= 1u << k;
+    }
+    return m;
+}
+
+// Candidate-list entry bit of a tile whose projecting texels all lie inside the lasso polygon.
+constexpr uint32_t kInsideTile = 0x80000000u;
+
 // lasso_hit for the four texels of a quad (bit k: texel k).  Each texel takes the steps of
 // lasso_hit up to its band; when the quad's live texels share a band (nearly always: they are
 // neighbours on the surface) one pass over that band's edge records tests all of them.  Texels
-// that failed a step carry ys = NaN, which straddles no edge.
+// that failed a step carry ys = NaN, which straddles no edge.  INSIDE: the quad's tile is known to
+// lie inside the polygon (lasso_tile_class8), so the edge tests are skipped: their outcome for
+// every texel that reaches them is "inside".
+template <bool INSIDE>
 __device__ __forceinline__ uint32_t lasso_quad(const LassoArg &p, const LassoShared &sh,
                                                const float *__restrict__ depth, int4 X, int4 Y, int4 Z) {
     const int32_t xq[4] = {X.x, X.y, X.z, X.w}, yq[4] = {Y.x, Y.y, Y.z, Y.w}, zq[4] = {Z.x, Z.y, Z.z, Z.w};
@@ -415,8 +505,8 @@ __device__ __forceinline__ uint32_t lasso_quad(const LassoArg &p, const LassoSha
         if (cx < __fmul_rn(p.nx0, w) || cx > __fmul_rn(p.nx1, w)) continue;
         const float cy = clip_row(p.m + 4, fx, fy, fz);
         if (cy < __fmul_rn(p.ny0, w) || cy > __fmul_rn(p.ny1, w)) continue;
-        const float x = screen_of(__fdiv_rn(cx, w), p.ws);
-        const float y = screen_of(__fdiv_rn(cy, w), p.hs);
+        const float x = screen_of(div_rn(cx, w), p.ws);
+        const float y = screen_of(div_rn(cy, w), p.hs);
         if (!(x >= 0.0f && x < p.ws && y >= 0.0f && y < p.hs)) continue;
         if (!(y >= p.ymin && y < p.ymax)) continue;
         int b = __float2int_rz(__fmul_rn(__fsub_rn(y, p.band_y0), p.band_inv_h));
@@ -428,6 +518,7 @@ __device__ __forceinline__ uint32_t lasso_quad(const LassoArg &p, const LassoSha
         live |= 1u << k;
     }
     if (!live) return 0;
+    if (INSIDE) return lasso_depth_quad(p, depth, xq, yq, zq, xs, ys, cw, live);
     const int b0 = (live & 1u) ? band[0] : (live & 2u) ? band[1] : (live & 4u) ? band[2] : band[3];
     bool same = true;
 #pragma unroll
@@ -458,19 +549,7 @@ __device__ __forceinline__ uint32_t lasso_quad(const LassoArg &p, const LassoSha
             }
         }
     }
-    live &= inside;
-    uint32_t m = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (!(live & (1u << k))) continue;
-        const float zn = __fdiv_rn(clip_row(p.m + 8, (float)xq[k], (float)yq[k], (float)zq[k]), cw[k]);
-        if (!(zn >= 0.0f && zn <= 1.0f)) continue;
-        const int32_t ix = __float2int_rz(xs[k]), iy = __float2int_rz(ys[k]);
-        if (!LCL_IN((int64_t)iy * p.w_s + ix, (int64_t)p.w_s * p.h_s)) continue;
-        const float d = __ldg(depth + (int64_t)iy * p.w_s + ix);
-        if (zn <= __fadd_rn(d, p.bias)) m |= 1u << k;
-    }
-    return m;
+    return lasso_depth_quad(p, depth, xq, yq, zq, xs, ys, cw, live & inside);
 }
 
 
@@ -500,8 +579,8 @@ __device__ __forceinline__ bool tool_hit(const LassoArg &p, const ToolArg &t, co
     if (cx < __fmul_rn(p.nx0, cw) || cx > __fmul_rn(p.nx1, cw)) return false;
     const float cy = clip_row(p.m + 4, fx, fy, fz);
     if (cy < __fmul_rn(p.ny0, cw) || cy > __fmul_rn(p.ny1, cw)) return false;
-    const float xs = screen_of(__fdiv_rn(cx, cw), p.ws);
-    const float ys = screen_of(__fdiv_rn(cy, cw), p.hs);
+    const float xs = screen_of(div_rn(cx, cw), p.ws);
+    const float ys = screen_of(div_rn(cy, cw), p.hs);
     if (!(xs >= 0.0f && xs < p.ws && ys >= 0.0f && ys < p.hs)) return false;
     if (MASK) {
         const float fu = __fmul_rn(__fsub_rn(xs, t.x0), t.su), fv = __fmul_rn(__fsub_rn(ys, t.y0), t.sv);
@@ -513,7 +592,7 @@ __device__ __forceinline__ bool tool_hit(const LassoArg &p, const ToolArg &t, co
         const float ex = __fmul_rn(__fsub_rn(xs, t.px), t.kx), ey = __fmul_rn(__fsub_rn(ys, t.py), t.ky);
         if (!(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)) <= 1.0f)) return false;
     }
-    const float zn = __fdiv_rn(clip_row(p.m + 8, fx, fy, fz), cw);
+    const float zn = div_rn(clip_row(p.m + 8, fx, fy, fz), cw);
     if (!(zn >= 0.0f && zn <= 1.0f)) return false;
     const int32_t ix = __float2int_rz(xs), iy = __float2int_rz(ys);
     if (!LCL_IN((int64_t)iy * p.w_s + ix, (int64_t)p.w_s * p.h_s)) return false;

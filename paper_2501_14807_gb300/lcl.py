@@ -39,7 +39,7 @@ EXPORTS = ["lcl_atlas_bytes", "lcl_atlas_bind", "lcl_atlas_bind_band", "lcl_atla
            "lcl_numeric_arith", "lcl_numeric_select", "lcl_numeric_stats",
            "lcl_pool_create", "lcl_pool_acquire", "lcl_pool_release", "lcl_pool_stats_get", "lcl_pool_destroy",
            "lcl_status_str", "lcl_last_error", "lcl_kernel_launches", "lcl_last_device_status", "lcl_build_flags",
-           "lcl_describe_site"]
+           "lcl_describe_site", "lcl_check_division"]
 LCL_BUILD_BOUNDS_CHECKS = 1
 
 
@@ -204,6 +204,7 @@ def library():
         "lcl_last_device_status": (st, [P]),
         "lcl_build_flags": (U32, []),
         "lcl_describe_site": (SZ, [U32, P, SZ]),
+        "lcl_check_division": (st, [C.c_uint64, U32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -876,3 +877,12 @@ def lcl_describe_site(site):
     buf = C.create_string_buffer(64)
     library().lcl_describe_site(C.c_uint32(site), buf, 64)
     return buf.value.decode()
+
+
+def lcl_check_division(n, seed=1, stream=None, device="cuda"):
+    """Runs the library's division self-check on n operand pairs; returns (compared, mismatches)."""
+    counts = torch.zeros(2, dtype=torch.int64, device=device)
+    _check("lcl_check_division", library().lcl_check_division(C.c_uint64(int(n)), C.c_uint32(int(seed)),
+                                                              _ptr(counts), _stream(stream)))
+    c = counts.cpu().numpy().view(np.uint64)
+    return int(c[0]), int(c[1])

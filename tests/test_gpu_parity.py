@@ -494,3 +494,14 @@ def test_sphere_with_texture_padding_bit_exact(T, dt):
     lcl.lcl_select_sphere(a, layer, recs, hits_out=hits)
     assert np.array_equal(to_np(layer, dt), exp)
     assert np.array_equal(to_np(hits, np.uint64), exp_hits)
+
+
+def test_library_division_equals_ieee_division():
+    """The projections divide with the library's own correctly rounded binary32 division (a fast
+    route for operands in [2^-30, 2^31), IEEE division elsewhere); it must equal __fdiv_rn bit for
+    bit: random operands across and beyond the window, quotients next to rounding midpoints, the
+    window's edges, zeros, subnormals, infinities and NaN."""
+    for seed in (1, 2, 3):
+        compared, mismatches = lcl.lcl_check_division(1 << 28, seed=seed)
+        assert compared == 1 << 28
+        assert mismatches == 0
