@@ -412,16 +412,20 @@ def test_overlay_bit_exact(dt):
     assert np.array_equal(to_np(dA2, dt), oracle.overlay(o, A, B, "xor"))
 
 
-@pytest.mark.parametrize("dt,n_labels", [(np.uint8, 256), (np.uint8, 37), (np.uint16, 1000), (np.uint16, 5000),
-                                         (np.uint16, 65536)])
-def test_label_area_bit_exact(dt, n_labels):
+@pytest.mark.parametrize("dt,n_labels,W,H", [(np.uint8, 256, 512, 508), (np.uint8, 37, 512, 508),
+                                             (np.uint16, 1000, 512, 508), (np.uint16, 5000, 512, 508),
+                                             (np.uint16, 65536, 512, 508),
+                                             (np.uint8, 256, 1040, 300),    # strips of 512, 512 and 16 columns
+                                             (np.uint16, 300, 1040, 77),
+                                             (np.uint8, 256, 300, 201),     # width not a multiple of 16: linear order
+                                             (np.uint16, 3000, 484, 97)])
+def test_label_area_bit_exact(dt, n_labels, W, H):
     mesh = synth.vessel_charts(200, 100, 25, 10, 512, seed=5)
-    W, H = 512, 508
     o = oracle.Atlas(mesh, W, H, tile=32)
     _, a = gpu_atlas(mesh, W, H, 32)
     rng = np.random.default_rng(n_labels)
     L = rng.integers(0, min(np.iinfo(dt).max, n_labels + 30) + 1, size=(H, W)).astype(dt)
-    L[100:300, 50:400] = 7                               # long runs of one label
+    L[min(100, H // 3):min(300, H), 50:400] = 7          # long runs of one label
     ec, ea = oracle.label_area(o, L, n_labels)
     c, ar = lcl.lcl_label_area(a, to_dev(L), n_labels)
     assert np.array_equal(to_np(c, np.uint64), ec)
