@@ -399,6 +399,128 @@ lcl_status lcl_batch_edit(const lcl_batch_limits *limits, const lcl_batch_config
 lcl_status lcl_batch_tune(const lcl_batch_limits *limits, void *workspace, size_t ws_bytes, int32_t reps,
                           lcl_stream stream, lcl_batch_config *best, float *best_ms);
 
+/* ---- served edits (native request loop) ------------------------------------ */
+
+/* A request server: many models' atlases, layers and depth maps kept in device memory while a budget
+ * allows, edit and query requests arriving continuously, batched into launches.  The paper keeps all
+ * layers on the GPU and lets the CPU only manage (Section 4, Fig. 2), its texture manager commits
+ * texture memory on demand (Section 4.2), and every request performs the edit of Section 4.3.1; the
+ * server is that manager for many models at once:
+ *  - resident models: a model's device image (atlas buffer | layers | depth maps) lives in a caller
+ *    arena (the HBM budget) while it fits; a model that has work and is not resident is admitted by a
+ *    host-to-device copy of its image on a copy stream, evicting idle resident models with the lowest
+ *    recent request rate (requests decayed with a 1 s time constant), whose layers are first copied
+ *    back to their host images; a model's requests join the first epoch after its copy completed;
+ *  - per-model FIFO order; continuous batching: each epoch takes, for every ready model with queued
+ *    work, the leading run of edits (at most max_edits per layer) or one query, uploads the edits as
+ *    one batch (lcl_batch_upload) and replays a captured graph of lcl_batch_launch, then the queries
+ *    (lcl_overlay into scratch + lcl_label_area, the tables copied to the request's host buffer);
+ *    epochs overlap (max_in_flight), each with its own workspace, staging and graph;
+ *  - open-loop arrivals: requests are submitted with their arrival times on the server clock and
+ *    taken only once that time has come; a request is done when the host sees its epoch's completion
+ *    event (t_done, same clock).
+ * The loop runs in a host thread of the server (lcl_serve_start .. lcl_serve_destroy); the calls
+ * below may come from any one other thread.  Device memory is the caller's (arena and work buffer);
+ * the server object holds host memory (queues, copies of the requests), two streams and events. */
+typedef struct lcl_server lcl_server;
+
+enum { LCL_REQ_SPHERE = 0, LCL_REQ_LASSO = 1, LCL_REQ_QUERY = 2 };
+
+typedef struct {
+    size_t arena_bytes;     /* device arena for model images: the HBM budget */
+    int32_t max_in_flight;  /* epochs in flight, 1..8 (0: 2) */
+    int32_t max_edits;      /* edits per layer per epoch, 1..LCL_BATCH_MAX_STROKES (0: 64) */
+    int32_t max_queries;    /* queries per epoch, 1..1024 (0: 16) */
+    int32_t max_labels;     /* largest n_labels of a query, 1..65536 (0: 256) */
+    int32_t max_admitting;  /* admissions in flight, 1..1024 (0: 16) */
+    int32_t _pad;
+} lcl_serve_config;
+
+/* A model, registered from its host image: pinned host memory of image_bytes bytes holding exactly
+ * the device image [atlas buffer of lcl_atlas_bytes(side, side, tile, n_tri) bytes (built) |
+ * n_layers uint8 layers of side x side at layer_offset + k layer_stride | depth map c (float32,
+ * cams[c].height x cams[c].width) at depth_offsets[c]], offsets 256-byte aligned.  The server copies
+ * it in on admission and writes the layers back on eviction; the caller keeps it alive and untouched
+ * until lcl_serve_destroy.  cams and depth_offsets are copied. */
+typedef struct {
+    int32_t side, tile;
+    int64_t n_tri;
+    float bbox_min[3];   /* the built atlas's quantisation */
+    int32_t n_layers;
+    double scale;
+    const lcl_camera *cams;
+    const size_t *depth_offsets;
+    int32_t n_cams, _pad;
+    void *host_image;
+    size_t image_bytes, layer_offset, layer_stride;
+} lcl_serve_model;
+
+/* One request.  Sphere: centre and radius in world units (quantised with lcl_quantize_sphere),
+ * `label` into `layer`.  Lasso: polygon of n_vertices (3..64) screen pixels on camera `cam`, `label`
+ * into `layer`, bias 2^-10.  Query: the overlay op(layer, layer_b) (an lcl_op, no flags) and its
+ * per-label counts and areas over n_labels labels, written to result (host, 2 n_labels uint64:
+ * counts then areas) before the request is reported done. */
+typedef struct {
+    double t_arrive;    /* seconds on the server clock (lcl_serve_clock) */
+    uint64_t tag;       /* returned by lcl_serve_poll */
+    int32_t model, kind, layer, label;
+    double centre[3], radius;
+    int32_t cam, n_vertices;
+    int32_t op, layer_b, n_labels, _pad;
+    uint64_t *result;
+    float poly[2 * LCL_MAX_LASSO_VERTICES];
+} lcl_serve_request;
+
+typedef struct {
+    uint64_t tag;
+    double t_done;      /* server clock */
+} lcl_serve_done;
+
+typedef struct {
+    uint64_t submitted, done, epochs, admissions, spills;
+    uint64_t resident_bytes, resident_models;
+    double host_busy_s;  /* loop time spent building epochs, admitting and spilling */
+} lcl_serve_stats;
+
+/* Seconds on the server clock (a monotonic host clock). */
+double lcl_serve_clock(void);
+
+/* Creates a server on the current device.  Errors: LCL_ERR_INVALID_ARG. */
+lcl_status lcl_serve_create(const lcl_serve_config *config, lcl_server **out);
+
+/* Registers a model (before lcl_serve_start); *id = its index.  Errors: LCL_ERR_INVALID_ARG (sizes,
+ * layout, an image larger than the arena), LCL_ERR_UNSUPPORTED (after start). */
+lcl_status lcl_serve_add_model(lcl_server *server, const lcl_serve_model *model, int32_t *id);
+
+/* Device and pinned host work memory the server needs for its registered models (batch workspaces,
+ * staging, query scratch), for lcl_serve_start. */
+size_t lcl_serve_work_bytes(const lcl_server *server);
+size_t lcl_serve_host_work_bytes(const lcl_server *server);
+
+/* Starts the loop thread.  arena: device, config.arena_bytes, 256-byte aligned; work: device,
+ * lcl_serve_work_bytes; host_work: pinned host, lcl_serve_host_work_bytes.  Models are admitted in
+ * registration order while they fit.  Errors: LCL_ERR_INVALID_ARG, LCL_ERR_CUDA. */
+lcl_status lcl_serve_start(lcl_server *server, void *arena, void *work, size_t work_bytes, void *host_work,
+                           size_t host_work_bytes);
+
+/* Queues n requests (copied), in order of arrival time (non-decreasing t_arrive over all submits).
+ * Errors: LCL_ERR_INVALID_ARG (a bad model, layer, camera, label, polygon or query), nothing queued. */
+lcl_status lcl_serve_submit(lcl_server *server, const lcl_serve_request *requests, int32_t n);
+
+/* Takes up to max completions (in completion order); *n_out = how many.  Non-blocking.  A failure of
+ * the loop (a CUDA error) is returned here as LCL_ERR_CUDA. */
+lcl_status lcl_serve_poll(lcl_server *server, lcl_serve_done *out, int32_t max, int32_t *n_out);
+
+lcl_status lcl_serve_stats_get(lcl_server *server, lcl_serve_stats *out);
+
+/* Copies layer `layer` of model `model` (side x side bytes) to host memory `dst`, once every
+ * submitted request is done (waits for that).  Errors: LCL_ERR_INVALID_ARG, LCL_ERR_CUDA. */
+lcl_status lcl_serve_read_layer(lcl_server *server, int32_t model, int32_t layer, void *dst);
+
+/* Stops the loop (queued requests that have not run are dropped), waits for the device, destroys
+ * the streams and the server. */
+lcl_status lcl_serve_destroy(lcl_server *server);
+
 /* ---- layer operations --------------------------------------------------- */
 
 /* Boolean overlay of two layers (layer systems combine layers with logic operations,

@@ -105,18 +105,10 @@ __device__ __forceinline__ void flush(const Run &r, unsigned long long *hc, unsi
     (void)n_labels;
 }
 
-// Texel order of the area kernel.  kLinear: the texture as one array, warp iteration `it` takes
-// 16-texel chunks 32 it .. 32 it + 31 (any width).  kStrips (width a multiple of 16): the texture
-// cut into strips of 512 columns, a warp iteration takes one row of one strip (lane l: columns
-// 16 l .. 16 l + 15 of it) and a warp walks its strip-rows down the rows, so the triangles of one
-// row recur in the next and their area weights are found in L1 instead of being fetched again.
-enum : int { kLinear = 0, kStrips = 1 };
-constexpr int kStripW = 512;
-
-template <typename L, bool SMEM, int ORDER>
+template <typename L, bool SMEM>
 __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ layer, const uint32_t *__restrict__ tri,
                                                       const uint64_t *__restrict__ area_w, int64_t n_tri,
-                                                      int64_t n_texels, int32_t width, uint32_t n_labels,
+                                                      int64_t n_texels, uint32_t n_labels,
                                                       unsigned long long *__restrict__ count,
                                                       unsigned long long *__restrict__ area) {
     (void)n_tri;
@@ -156,28 +148,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ laye
     const int64_t n_chunks = n_texels / 16;
     const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t rows = ORDER == kStrips ? n_texels / width : 0;
-    const int64_t n_iter = ORDER == kStrips ? ((width + kStripW - 1) / kStripW) * rows : (n_chunks + 31) / 32;
+    const int64_t n_iter = (n_chunks + 31) / 32;
     const int64_t per = (n_iter + n_warps - 1) / n_warps;
     const int64_t it0 = warp * per, it1 = min(n_iter, it0 + per);
-    // first texel of this lane's chunk in iteration it, or -1 if the lane has none there
-    auto chunk_at = [&](int64_t it) -> int64_t {
-        if (ORDER == kStrips) {
-            const int64_t strip = it / rows, y = it - strip * rows;
-            const int64_t x = strip * kStripW + 16 * lane;
-            return x < width ? y * width + x : -1;
-        }
-        const int64_t c = it * 32 + lane;
-        return c < n_chunks ? 16 * c : -1;
-    };
     uint4 T4[4], V[LW];
-    auto load = [&](int64_t t0) {
-        if (!LCL_IN(t0 + 15, n_texels)) return;
-        const uint4 *tp = reinterpret_cast<const uint4 *>(tri + t0);
+    auto load = [&](int64_t c) {
+        if (!LCL_IN(16 * c + 15, n_texels)) return;
+        const uint4 *tp = reinterpret_cast<const uint4 *>(tri + 16 * c);
 #pragma unroll
         for (int k = 0; k < 4; ++k) T4[k] = __ldcs(tp + k);
 #pragma unroll
-        for (int k = 0; k < LW; ++k) V[k] = __ldcs(reinterpret_cast<const uint4 *>(layer + t0) + k);
+        for (int k = 0; k < LW; ++k) V[k] = __ldcs(reinterpret_cast<const uint4 *>(layer + 16 * c) + k);
     };
     // warp run: while every lane's run of an iteration has the warp's label, each lane adds its run
     // to its own share of the warp run (registers only); when an iteration brings another label, the
@@ -185,11 +166,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ laye
     // reduced label by label (match_any groups)
     uint32_t wlabel = kNone;
     unsigned long long wcnt = 0, warea = 0;
-    int64_t t_cur = it0 < it1 ? chunk_at(it0) : -1;
-    if (t_cur >= 0) load(t_cur);
+    if (it0 < it1 && it0 * 32 + lane < n_chunks) load(it0 * 32 + lane);
     for (int64_t it = it0; it < it1; ++it) {
-        const int64_t t_next = it + 1 < it1 ? chunk_at(it + 1) : -1;
-        if (t_cur >= 0) {
+        const int64_t c = it * 32 + lane;
+        if (c < n_chunks) {
             const uint32_t ts[16] = {T4[0].x, T4[0].y, T4[0].z, T4[0].w, T4[1].x, T4[1].y, T4[1].z, T4[1].w,
                                      T4[2].x, T4[2].y, T4[2].z, T4[2].w, T4[3].x, T4[3].y, T4[3].z, T4[3].w};
             uint32_t w[4 * LW];
@@ -200,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ laye
                 w[4 * k + 2] = V[k].z;
                 w[4 * k + 3] = V[k].w;
             }
-            if (t_next >= 0) load(t_next);
+            if (it + 1 < it1 && c + 32 < n_chunks) load(c + 32);
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 const uint32_t lab =
@@ -237,7 +217,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ laye
         }
         run.cnt = 0;
         run.area = 0;
-        t_cur = t_next;
     }
     {
         unsigned long long tc = wcnt, ta = warea;
@@ -251,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ laye
             atomicAdd(ha + wlabel, ta);
         }
     }
-    // tail texels (n_texels % 16; none in strip order, whose width is a multiple of 16), one per thread
+    // tail texels (n_texels % 16), one per thread
     for (int64_t t = n_chunks * 16 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_texels;
          t += (int64_t)gridDim.x * blockDim.x)
         if (LCL_IN(t, n_texels)) visit((uint32_t)layer[t], tri[t]);
@@ -303,29 +282,19 @@ lcl_status label_area_impl(const lcl_atlas *atlas, const void *layer, int dtype_
                                                            (n_tex / 16 + kThreads - 1) / kThreads));
     };
     const uint32_t *tri = atlas->tri;
-    const int32_t W = atlas->width;
-    const bool strips = W % 16 == 0 && W >= kStripW;  // else the linear order (any width)
-    auto run = [&](auto kernel, size_t smem_bytes, auto *l) {
-        kernel<<<fit(kernel), kThreads, smem_bytes, st>>>(l, tri, atlas->area_w, atlas->n_tri, n_tex, W, n_labels, c, ar);
-    };
     if (dtype_bytes == 1) {
         const uint8_t *l = static_cast<const uint8_t *>(layer);
-        if (strips) {
-            if (smem) run(k_area<uint8_t, true, kStrips>, shb, l);
-            else run(k_area<uint8_t, false, kStrips>, 0, l);
-        } else {
-            if (smem) run(k_area<uint8_t, true, kLinear>, shb, l);
-            else run(k_area<uint8_t, false, kLinear>, 0, l);
-        }
+        if (smem) k_area<uint8_t, true><<<fit(k_area<uint8_t, true>), kThreads, shb, st>>>(l, tri, atlas->area_w, atlas->n_tri,
+                                                                                          n_tex, n_labels, c, ar);
+        else k_area<uint8_t, false><<<fit(k_area<uint8_t, false>), kThreads, 0, st>>>(l, tri, atlas->area_w, atlas->n_tri,
+                                                                                      n_tex, n_labels, c, ar);
     } else {
         const uint16_t *l = static_cast<const uint16_t *>(layer);
-        if (strips) {
-            if (smem) run(k_area<uint16_t, true, kStrips>, shb, l);
-            else run(k_area<uint16_t, false, kStrips>, 0, l);
-        } else {
-            if (smem) run(k_area<uint16_t, true, kLinear>, shb, l);
-            else run(k_area<uint16_t, false, kLinear>, 0, l);
-        }
+        if (smem) k_area<uint16_t, true><<<fit(k_area<uint16_t, true>), kThreads, shb, st>>>(l, tri, atlas->area_w,
+                                                                                            atlas->n_tri, n_tex,
+                                                                                            n_labels, c, ar);
+        else k_area<uint16_t, false><<<fit(k_area<uint16_t, false>), kThreads, 0, st>>>(l, tri, atlas->area_w, atlas->n_tri,
+                                                                                        n_tex, n_labels, c, ar);
     }
     count_launches(2);
     cudaError_t e = cudaGetLastError();

@@ -39,7 +39,10 @@ EXPORTS = ["lcl_atlas_bytes", "lcl_atlas_bind", "lcl_atlas_bind_band", "lcl_atla
            "lcl_numeric_arith", "lcl_numeric_select", "lcl_numeric_stats",
            "lcl_pool_create", "lcl_pool_acquire", "lcl_pool_release", "lcl_pool_stats_get", "lcl_pool_destroy",
            "lcl_status_str", "lcl_last_error", "lcl_kernel_launches", "lcl_last_device_status", "lcl_build_flags",
-           "lcl_describe_site", "lcl_check_division"]
+           "lcl_describe_site", "lcl_check_division",
+           "lcl_serve_clock", "lcl_serve_create", "lcl_serve_add_model", "lcl_serve_work_bytes",
+           "lcl_serve_host_work_bytes", "lcl_serve_start", "lcl_serve_submit", "lcl_serve_poll", "lcl_serve_stats_get",
+           "lcl_serve_read_layer", "lcl_serve_destroy"]
 LCL_BUILD_BOUNDS_CHECKS = 1
 
 
@@ -105,6 +108,37 @@ class lcl_batch_lasso(C.Structure):
                 ("label", C.c_uint32), ("bias", C.c_float), ("flags", C.c_uint32)]
 
 
+class lcl_serve_config(C.Structure):
+    _fields_ = [("arena_bytes", C.c_size_t), ("max_in_flight", C.c_int32), ("max_edits", C.c_int32),
+                ("max_queries", C.c_int32), ("max_labels", C.c_int32), ("max_admitting", C.c_int32),
+                ("_pad", C.c_int32)]
+
+
+class lcl_serve_model(C.Structure):
+    _fields_ = [("side", C.c_int32), ("tile", C.c_int32), ("n_tri", C.c_int64), ("bbox_min", C.c_float * 3),
+                ("n_layers", C.c_int32), ("scale", C.c_double), ("cams", C.c_void_p), ("depth_offsets", C.c_void_p),
+                ("n_cams", C.c_int32), ("_pad", C.c_int32), ("host_image", C.c_void_p), ("image_bytes", C.c_size_t),
+                ("layer_offset", C.c_size_t), ("layer_stride", C.c_size_t)]
+
+
+class lcl_serve_done(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("t_done", C.c_double)]
+
+
+class lcl_serve_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("done", C.c_uint64), ("epochs", C.c_uint64), ("admissions", C.c_uint64),
+                ("spills", C.c_uint64), ("resident_bytes", C.c_uint64), ("resident_models", C.c_uint64),
+                ("host_busy_s", C.c_double)]
+
+
+# lcl_serve_request as a numpy record (608 bytes), so a whole trace is one array
+SERVE_REQUEST_DTYPE = np.dtype([("t_arrive", "<f8"), ("tag", "<u8"), ("model", "<i4"), ("kind", "<i4"),
+                                ("layer", "<i4"), ("label", "<i4"), ("centre", "<f8", (3,)), ("radius", "<f8"),
+                                ("cam", "<i4"), ("n_vertices", "<i4"), ("op", "<i4"), ("layer_b", "<i4"),
+                                ("n_labels", "<i4"), ("_pad", "<i4"), ("result", "<u8"), ("poly", "<f4", (128,))])
+LCL_REQ_SPHERE, LCL_REQ_LASSO, LCL_REQ_QUERY = 0, 1, 2
+
+
 class lcl_batch_limits(C.Structure):
     _fields_ = [("models", C.c_int32), ("strokes", C.c_int32), ("lassos", C.c_int32), ("_pad", C.c_int32),
                 ("supers", C.c_int64), ("tiles", C.c_int64)]
@@ -125,6 +159,8 @@ assert C.sizeof(lcl_batch_model) == 32 and C.sizeof(lcl_batch_stroke) == 40 and 
 assert C.sizeof(lcl_batch_limits) == 32 and C.sizeof(lcl_batch_config) == 16 and C.sizeof(lcl_tool) == 40
 assert C.sizeof(lcl_numeric_layer) == 24 and C.sizeof(lcl_zone_stats) == 48
 assert C.sizeof(lcl_pool_layer) == 40 and C.sizeof(lcl_pool_stats) == 40
+assert C.sizeof(lcl_serve_config) == 32 and C.sizeof(lcl_serve_model) == 96 and C.sizeof(lcl_serve_done) == 16
+assert C.sizeof(lcl_serve_stats) == 64 and SERVE_REQUEST_DTYPE.itemsize == 608
 
 SPHERE_DTYPE = np.dtype([("cx", "<i4"), ("cy", "<i4"), ("cz", "<i4"), ("pad", "<i4"),
                          ("r2", "<i8"), ("label", "<u4"), ("flags", "<u4")])
@@ -205,6 +241,17 @@ def library():
         "lcl_build_flags": (U32, []),
         "lcl_describe_site": (SZ, [U32, P, SZ]),
         "lcl_check_division": (st, [C.c_uint64, U32, P, P]),
+        "lcl_serve_clock": (D, []),
+        "lcl_serve_create": (st, [C.POINTER(lcl_serve_config), C.POINTER(P)]),
+        "lcl_serve_add_model": (st, [P, C.POINTER(lcl_serve_model), C.POINTER(I32)]),
+        "lcl_serve_work_bytes": (SZ, [P]),
+        "lcl_serve_host_work_bytes": (SZ, [P]),
+        "lcl_serve_start": (st, [P, P, P, SZ, P, SZ]),
+        "lcl_serve_submit": (st, [P, P, I32]),
+        "lcl_serve_poll": (st, [P, P, I32, C.POINTER(I32)]),
+        "lcl_serve_stats_get": (st, [P, C.POINTER(lcl_serve_stats)]),
+        "lcl_serve_read_layer": (st, [P, I32, I32, P]),
+        "lcl_serve_destroy": (st, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

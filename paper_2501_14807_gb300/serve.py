@@ -542,6 +542,177 @@ class _Rebind:
         return a
 
 
+def model_image_layout(spec):
+    """Device image of a served model: atlas buffer | layers | depth maps, sections 256-byte aligned.
+    Returns (layer offset, layer stride, depth-map offsets, total bytes)."""
+    a256 = lambda x: (x + 255) // 256 * 256  # noqa: E731
+    ab = int(lcl.library().lcl_atlas_bytes(spec.side, spec.side, spec.tile, spec.mesh.n_tri))
+    lb = a256(spec.side * spec.side)
+    off_l = a256(ab)
+    off = off_l + spec.n_layers * lb
+    offs_d = []
+    for c in spec.cams:
+        offs_d.append(off)
+        off += a256(4 * c.width * c.height)
+    return off_l, lb, offs_d, off
+
+
+class NativeServer:
+    """The same serving policy run by the library's native loop (lcl_serve_*): admission and eviction
+    by recent request rate, per-model FIFO queues, continuous batching with epochs in flight, queries,
+    latency per request -- all in a host thread of liblcl.so; Python only prepares the models and
+    submits the whole trace (arrival times on the server clock) before collecting completions.
+
+    models: ServedModel list; hbm_budget_bytes: the device arena for model images."""
+
+    def __init__(self, models, hbm_budget_bytes, device="cuda", max_edits_per_layer=lcl.BATCH_MAX_STROKES,
+                 max_in_flight=2, max_labels=256, max_queries=16):
+        self.dev = torch.device(device)
+        self.lib = lcl.library()
+        self.specs = list(models)
+        self.max_labels = max_labels
+        cfg = lcl.lcl_serve_config()
+        cfg.arena_bytes = int(hbm_budget_bytes) // 256 * 256
+        cfg.max_in_flight, cfg.max_edits, cfg.max_queries, cfg.max_labels = (max_in_flight, max_edits_per_layer,
+                                                                              max_queries, max_labels)
+        self.ptr = lcl.C.c_void_p()
+        lcl._check("lcl_serve_create", self.lib.lcl_serve_create(lcl.C.byref(cfg), lcl.C.byref(self.ptr)))
+        self.images, self._keep = [], []
+        self.bytes = []
+        for spec in self.specs:
+            self._register(spec)
+        self.arena = torch.empty(cfg.arena_bytes, dtype=torch.uint8, device=self.dev)
+        wb = int(self.lib.lcl_serve_work_bytes(self.ptr))
+        hb = int(self.lib.lcl_serve_host_work_bytes(self.ptr))
+        self.work = torch.empty(max(wb, 256), dtype=torch.uint8, device=self.dev)
+        self.host_work = torch.empty(max(hb, 256), dtype=torch.uint8).pin_memory()
+        torch.cuda.synchronize(self.dev)
+        lcl._check("lcl_serve_start", self.lib.lcl_serve_start(self.ptr, lcl._ptr(self.arena), lcl._ptr(self.work),
+                                                               self.work.numel(), lcl._ptr(self.host_work),
+                                                               self.host_work.numel()))
+
+    def _register(self, spec):
+        """Builds the model's device image (atlas | layers | depth maps) once, keeps it in pinned host
+        memory and registers it; the device copy is dropped (the server admits it when needed)."""
+        off_l, lb, offs_d, off = model_image_layout(spec)
+        buf = torch.zeros(off, dtype=torch.uint8, device=self.dev)
+        mesh = lcl.Mesh.from_host(spec.mesh, self.dev)
+        atlas = lcl.Atlas(spec.side, spec.side, spec.tile, spec.mesh.n_tri, self.dev, buffer=buf)
+        lcl.lcl_atlas_build(mesh, atlas)
+        cams = [lcl.lcl_camera_from_vp(atlas, c.vp, c.width, c.height) for c in spec.cams]
+        for c, o in zip(cams, offs_d):
+            d = buf[o: o + 4 * c.width * c.height].view(torch.float32).view(c.height, c.width)
+            lcl.lcl_depth_render(mesh, atlas, c, d)
+        image = torch.empty(off, dtype=torch.uint8).pin_memory()
+        image.copy_(buf)
+        cam_arr = (lcl.lcl_camera * max(len(cams), 1))(*cams)
+        offs_arr = (lcl.C.c_size_t * max(len(offs_d), 1))(*offs_d)
+        d = lcl.lcl_serve_model()
+        d.side, d.tile, d.n_tri, d.n_layers = spec.side, spec.tile, spec.mesh.n_tri, spec.n_layers
+        d.bbox_min[:] = list(atlas.c.bbox_min)
+        d.scale = atlas.c.scale
+        d.cams = lcl.C.cast(cam_arr, lcl.C.c_void_p)
+        d.depth_offsets = lcl.C.cast(offs_arr, lcl.C.c_void_p)
+        d.n_cams = len(cams)
+        d.host_image = image.data_ptr()
+        d.image_bytes, d.layer_offset, d.layer_stride = off, off_l, lb
+        mid = lcl.C.c_int32()
+        lcl._check("lcl_serve_add_model", self.lib.lcl_serve_add_model(self.ptr, lcl.C.byref(d), lcl.C.byref(mid)))
+        self.images.append(image)
+        self._keep.append((cam_arr, offs_arr))
+        self.bytes.append(off)
+        del buf, mesh, atlas
+
+    def stats(self):
+        st = lcl.lcl_serve_stats()
+        lcl._check("lcl_serve_stats_get", self.lib.lcl_serve_stats_get(self.ptr, lcl.C.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    spills = property(lambda self: int(self.stats()["spills"]))
+    admissions = property(lambda self: int(self.stats()["admissions"]))
+    epochs = property(lambda self: int(self.stats()["epochs"]))
+
+    def run(self, requests, start_delay_s=0.05, stall_limit_s=60.0):
+        """Serves `requests` (sorted by t_arrive, seconds from the start) open-loop: the whole trace is
+        submitted at once with arrival times on the server clock, then completions are collected;
+        fills t_done (seconds from the start) and, for queries, result = (counts, areas)."""
+        n = len(requests)
+        rec = np.zeros(n, lcl.SERVE_REQUEST_DTYPE)
+        n_q = sum(1 for r in requests if r.kind == QUERY)
+        results = np.zeros((max(n_q, 1), 2, self.max_labels), np.uint64)
+        t0 = float(self.lib.lcl_serve_clock()) + start_delay_s
+        qi = 0
+        base = results.ctypes.data
+        for i, r in enumerate(requests):
+            x = rec[i]
+            x["t_arrive"] = t0 + r.t_arrive
+            x["tag"] = i
+            x["model"] = r.model
+            x["kind"] = r.kind
+            x["layer"] = r.layer
+            if r.kind == SPHERE:
+                c, rad, label = r.sphere
+                x["centre"] = c
+                x["radius"] = rad
+                x["label"] = label
+            elif r.kind == LASSO:
+                ci, poly, label = r.lasso
+                poly = np.asarray(poly, np.float32)
+                x["cam"] = ci
+                x["n_vertices"] = poly.shape[0]
+                x["poly"][:2 * poly.shape[0]] = poly.reshape(-1)
+                x["label"] = label
+            else:
+                op, la, lb, n_labels = r.query
+                x["op"] = lcl.OPS[op]
+                x["layer"], x["layer_b"], x["n_labels"] = la, lb, n_labels
+                x["result"] = base + qi * results.strides[0]
+                r._qi = qi
+                qi += 1
+        lcl._check("lcl_serve_submit", self.lib.lcl_serve_submit(self.ptr, rec.ctypes.data, n))
+        out = (lcl.lcl_serve_done * 4096)()
+        got = lcl.C.c_int32()
+        left = n
+        last = time.perf_counter()
+        while left:
+            lcl._check("lcl_serve_poll", self.lib.lcl_serve_poll(self.ptr, out, 4096, lcl.C.byref(got)))
+            for k in range(got.value):
+                r = requests[out[k].tag]
+                r.t_done = out[k].t_done - t0
+            left -= got.value
+            if got.value:
+                last = time.perf_counter()
+            elif time.perf_counter() - last > stall_limit_s:
+                raise RuntimeError(f"serving loop made no progress for {stall_limit_s} s ({left} requests outstanding)")
+            else:
+                time.sleep(200e-6)
+        for r in requests:
+            if r.kind == QUERY:
+                nl = r.query[3]
+                r.result = (results[r._qi, 0, :nl].copy(), results[r._qi, 1, :nl].copy())
+        return requests
+
+    def layers_of(self, mi):
+        spec = self.specs[mi]
+        out = []
+        for li in range(spec.n_layers):
+            h = np.empty((spec.side, spec.side), np.uint8)
+            lcl._check("lcl_serve_read_layer", self.lib.lcl_serve_read_layer(self.ptr, mi, li, h.ctypes.data))
+            out.append(torch.from_numpy(h).to(self.dev))
+        return out
+
+    def close(self):
+        if self.ptr:
+            self.lib.lcl_serve_destroy(self.ptr)
+            self.ptr = lcl.C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def poisson_requests(n_models, rate_hz, duration_s, seed, mix=(0.7, 0.2, 0.1), zipf_s=1.1, n_layers=2,
                      sphere_of=None, lasso_of=None, n_labels=256):
     """Open-loop arrivals: exponential gaps at `rate_hz`, kinds by `mix` (sphere, lasso, query),

@@ -415,9 +415,9 @@ def test_overlay_bit_exact(dt):
 @pytest.mark.parametrize("dt,n_labels,W,H", [(np.uint8, 256, 512, 508), (np.uint8, 37, 512, 508),
                                              (np.uint16, 1000, 512, 508), (np.uint16, 5000, 512, 508),
                                              (np.uint16, 65536, 512, 508),
-                                             (np.uint8, 256, 1040, 300),    # strips of 512, 512 and 16 columns
+                                             (np.uint8, 256, 1040, 300),
                                              (np.uint16, 300, 1040, 77),
-                                             (np.uint8, 256, 300, 201),     # width not a multiple of 16: linear order
+                                             (np.uint8, 256, 300, 201),     # width not a multiple of 16
                                              (np.uint16, 3000, 484, 97)])
 def test_label_area_bit_exact(dt, n_labels, W, H):
     mesh = synth.vessel_charts(200, 100, 25, 10, 512, seed=5)
