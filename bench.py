@@ -400,7 +400,8 @@ def run_ours(args):
         if world > 1:
             dist.destroy_process_group()
         return
-    serving = serving_summary(args.serving_models, 20000.0, 1.0) if (world == 1 and args.serving_models > 0) else None
+    serving = serving_summary(args.serving_models, 20000.0, args.serving_seconds) \
+        if (world == 1 and args.serving_models > 0) else None
     # the batching workload (256 models, 64 queued strokes each), outside the timed region
     batch = batch_summary(args.batch_models, 5, 2, torch_device=local) if (world == 1 and args.batch_models > 0) else None
     peak, peak_kind = peaks()
@@ -673,8 +674,7 @@ def serving_setup(n_models, seed=5):
     models = [serve.ServedModel(b.mesh, b.side, b.cams, n_layers=2) for b in bms]
     # the HBM budget holds the first half of the models (the resident set: model i is the i-th most
     # popular under the Zipf law of the trace); the other half are spillover models admitted on demand
-    probe_bytes = [b.side * b.side * 18 + 8 * 1024 * 1024 for b in bms]
-    budget = int(sum(probe_bytes[: len(bms) // 2]))
+    budget = int(sum(serve.model_image_layout(m)[3] for m in models[: len(models) // 2]))
 
     def sphere_of(m, rng):
         st = bms[m].strokes
@@ -688,30 +688,49 @@ def serving_setup(n_models, seed=5):
     return models, budget, sphere_of, lasso_of
 
 
+def native_serving_run(models, budget, sphere_of, lasso_of, rate, duration, seed=5):
+    """One open-loop run of the native server (lcl_serve_*) after a 0.2 s warm-up trace: latency
+    statistics (overall, per second of arrival, hot half vs spillover models) and the server's
+    counters over the timed trace."""
+    from paper_2501_14807_gb300 import serve
+    srv = serve.NativeServer(models, hbm_budget_bytes=budget)
+    try:
+        srv.run(serve.poisson_requests(len(models), rate, 0.2, seed + 1, sphere_of=sphere_of, lasso_of=lasso_of))
+        reqs = serve.poisson_requests(len(models), rate, duration, seed, sphere_of=sphere_of, lasso_of=lasso_of)
+        s0 = srv.stats()
+        srv.run(reqs)
+        s1 = srv.stats()
+    finally:
+        srv.close()
+    st = serve.latency_stats(reqs)
+    lat = np.array([r.t_done - r.t_arrive for r in reqs])
+    t = np.array([r.t_arrive for r in reqs])
+    cold = np.array([r.model >= len(models) // 2 for r in reqs])
+    st.update({k: int(s1[k] - s0[k]) for k in ("epochs", "admissions", "spills", "deferred")})
+    st["admitted_gb"] = (s1["admitted_bytes"] - s0["admitted_bytes"]) / 1e9
+    st["host_busy_s"] = round(s1["host_busy_s"] - s0["host_busy_s"], 3)
+    st["p99_ms_by_second"] = [round(1e3 * float(np.percentile(lat[(t >= i) & (t < i + 1)], 99)), 2)
+                              for i in range(int(duration)) if ((t >= i) & (t < i + 1)).any()]
+    if cold.any() and (~cold).any():
+        st["p99_ms_resident_half"] = 1e3 * float(np.percentile(lat[~cold], 99))
+        st["p99_ms_spillover_half"] = 1e3 * float(np.percentile(lat[cold], 99))
+        st["spillover_request_frac"] = float(cold.mean())
+    return st
+
+
 def serving_summary(n_models, rate, duration):
-    """A short live serving run (continuous batching only) for the headline line's latency figures."""
+    """The serving workload for the headline line: n_models models, an HBM budget that holds the
+    first half (the resident set) and spillover models admitted on demand, Poisson arrivals, served by
+    the native loop (continuous batching, admission by footprint and request rate)."""
     import torch
 
-    from paper_2501_14807_gb300 import serve
     models, budget, sphere_of, lasso_of = serving_setup(n_models)
-    out = None
-    for b in (budget, 1 << 50):   # the half-resident budget, then every model resident
-        srv = serve.Server(models, hbm_budget_bytes=b)
-        srv.run(serve.poisson_requests(len(models), rate, 0.2, 6, sphere_of=sphere_of, lasso_of=lasso_of))
-        reqs = serve.poisson_requests(len(models), rate, duration, 5, sphere_of=sphere_of, lasso_of=lasso_of)
-        spills0 = srv.spills
-        srv.run(reqs)
-        st = serve.latency_stats(reqs)
-        st.update({"spills": srv.spills - spills0, "host_s": {k: round(v, 3) for k, v in srv.host_s.items()}})
-        if out is None:
-            out = dict(st)
-            out.update({"models": len(models), "offered_rps": rate, "seconds": duration,
-                        "budget_gib": budget / 2**30,
-                        "mix": "70% sphere / 20% lasso / 10% overlay+area, Zipf(1.1) models, the hot half resident"})
-        else:
-            out["all_resident"] = st
-        del srv
-        torch.cuda.empty_cache()
+    out = native_serving_run(models, budget, sphere_of, lasso_of, rate, duration)
+    out.update({"models": len(models), "offered_rps": rate, "seconds": duration, "budget_gib": budget / 2**30,
+                "scheduler": "native loop in liblcl.so (lcl_serve_*)",
+                "mix": "70% sphere / 20% lasso / 10% overlay+area, Zipf(1.1) models, the first half resident "
+                       "under the budget, the rest spillover"})
+    torch.cuda.empty_cache()
     return out
 
 
@@ -979,39 +998,42 @@ def run_pool(args):
 def run_serve(args):
     """Serving workload: resident + spillover models (as in the batching workload), 2 layers each,
     an HBM budget that holds about half of them, open-loop Poisson arrivals (70% sphere strokes, 20%
-    lassos, 10% overlay + area queries, models by a Zipf(1.1) law), served with continuous batching;
-    the same trace served one request per call is the baseline."""
+    lassos, 10% overlay + area queries, models by a Zipf(1.1) law).  Served by the native loop
+    (lcl_serve_*), by the Python scheduler (serve.Server, the same policy with its bookkeeping in
+    Python) and one request per call (the baseline); the same trace for all three."""
     import torch
 
     from paper_2501_14807_gb300 import serve
 
     torch.cuda.set_device(0)
     models, budget, sphere_of, lasso_of = serving_setup(args.models or 128)
-    out = {}
-    for mode in ("batched", "per_request"):
+    clocks = Clocks(0)
+    clocks.start()
+    out = {"native": native_serving_run(models, budget, sphere_of, lasso_of, args.rate, args.duration)}
+    out["native"]["clocks"] = clocks.stop()
+    torch.cuda.empty_cache()
+    for mode in ("python_batched", "per_request"):
         srv = serve.Server(models, hbm_budget_bytes=budget)
         reqs = serve.poisson_requests(len(models), args.rate, args.duration, 5, sphere_of=sphere_of,
                                       lasso_of=lasso_of)
         warm = serve.poisson_requests(len(models), args.rate, 0.2, 6, sphere_of=sphere_of, lasso_of=lasso_of)
-        (srv.run if mode == "batched" else srv.run_per_request)(warm)
-        clocks = Clocks(0)
-        clocks.start()
-        (srv.run if mode == "batched" else srv.run_per_request)(reqs)
-        clk = clocks.stop()
+        (srv.run if mode == "python_batched" else srv.run_per_request)(warm)
+        (srv.run if mode == "python_batched" else srv.run_per_request)(reqs)
         st = serve.latency_stats(reqs)
-        st.update({"epochs": srv.epochs, "spills": srv.spills, "admissions": srv.admissions, "clocks": clk,
+        st.update({"epochs": srv.epochs, "spills": srv.spills, "admissions": srv.admissions,
                    "host_s": {k: round(v, 3) for k, v in srv.host_s.items()}})
         out[mode] = st
+        srv.close()
         del srv
         torch.cuda.empty_cache()
-    b = out["batched"]
+    b = out["native"]
     line = {"metric": METRIC, "value": b["throughput_rps"], "unit": "requests/s", "n_gpus": 1, "steps": 1,
             "warmup": 1, "ms_per_step": 1e3 * args.duration, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": f"serving: {len(models)} models (half resident under a {budget / 2**30:.2f} GiB "
                                    f"budget), Poisson {args.rate:.0f} req/s for {args.duration:.1f} s, mix 70% sphere / "
                                    f"20% lasso / 10% overlay+area, Zipf(1.1) model choice"},
-            "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"], "served": out}
+            "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"], "served": out, "gpu_launches": None}
     print(json.dumps(line), flush=True)
 
 
@@ -1046,8 +1068,10 @@ def main():
                     help="models in the batching (default 256) / serving (default 128: 64 resident + 64 spilled) workload")
     ap.add_argument("--batch-models", type=int, default=256,
                     help="models of the batching workload reported in the headline line (0: skip)")
-    ap.add_argument("--serving-models", type=int, default=32,
-                    help="models of the short serving run reported in the headline line (0: skip)")
+    ap.add_argument("--serving-models", type=int, default=128,
+                    help="models of the serving run reported in the headline line (0: skip)")
+    ap.add_argument("--serving-seconds", type=float, default=10.0,
+                    help="length of the headline serving trace (Poisson 20k requests/s)")
     ap.add_argument("--atlas-side", type=int, default=None,
                     help="mid config: atlas side (default 4096; the mesh is scaled with it)")
     ap.add_argument("--strokes", type=int, default=None)

@@ -473,13 +473,17 @@ typedef struct {
 
 typedef struct {
     uint64_t tag;
-    double t_done;      /* server clock */
+    double t_done;      /* server clock: the host saw the request's epoch complete */
+    double t_launch;    /* server clock: its epoch was launched */
+    double _pad;
 } lcl_serve_done;
 
 typedef struct {
     uint64_t submitted, done, epochs, admissions, spills;
     uint64_t resident_bytes, resident_models;
-    double host_busy_s;  /* loop time spent building epochs, admitting and spilling */
+    double host_busy_s;        /* loop time spent building epochs, admitting and spilling */
+    uint64_t admitted_bytes;   /* bytes copied in by admissions */
+    uint64_t deferred;         /* admissions put off: no room could be made at that moment */
 } lcl_serve_stats;
 
 /* Seconds on the server clock (a monotonic host clock). */

@@ -15,8 +15,8 @@
 //                 small triangles (atomicMin of the triangle id: smallest id wins); big
 //                 triangles are split into 16x16-texel blocks appended to a work list
 //   k_raster_big  one CTA per (triangle, block) entry
-//   k_resolve     one CTA per tile: exact barycentric position of every covered texel,
-//                 coverage bits, tile box
+//   k_resolve     one CTA per tile, one texel per thread and step: exact barycentric position of
+//                 every covered texel, coverage bits, tile box
 //   k_super       one CTA per super-tile: union of its tile boxes
 #include <algorithm>
 #include <cstring>
@@ -342,75 +342,54 @@ __device__ __forceinline__ int32_t interp_axis(int64_t w1, int64_t w2, int64_t A
     return q0 + (int32_t)est;
 }
 
-__global__ void __launch_bounds__(kThreads) k_resolve(const TriSetup *__restrict__ setup, int64_t n_tri, int32_t w,
+__global__ void __launch_bounds__(kThreads, 4) k_resolve(const TriSetup *__restrict__ setup, int64_t n_tri, int32_t w,
                                                       int32_t h, int32_t row0, int32_t T,
                                                       const uint32_t *__restrict__ tri_plane,
                                                       int32_t *__restrict__ px, int32_t *__restrict__ py,
                                                       int32_t *__restrict__ pz, uint32_t *__restrict__ cover,
                                                       int32_t *__restrict__ tile_box) {
     const int32_t tx = blockIdx.x, ty = blockIdx.y;
-    const int32_t qpr = T / 4, nq = T * qpr;
     int32_t mn[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, mx[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
     int32_t cnt = 0;
-    const int iters = (nq + kThreads - 1) / kThreads;
+    // one texel per thread and step, a tile row after the other: warps read the triangle plane and
+    // write the position planes in whole 128-byte rows, and the texels of one triangle, which lie
+    // together, find its set-up record in L1
+    const int32_t n_tex_tile = T * T;
+    const int iters = (n_tex_tile + kThreads - 1) / kThreads;
     for (int it = 0; it < iters; ++it) {
-        int32_t qd = it * kThreads + threadIdx.x;
-        int32_t x = tx * T + 4 * (qd % qpr), y = ty * T + qd / qpr;
-        bool valid = qd < nq && x < w && y < h && LCL_IN((int64_t)y * w + x + 3, (int64_t)w * h);
-        uint32_t nib = 0;
-        int64_t l = valid ? (int64_t)y * w + x : 0;
+        const int32_t i = it * kThreads + threadIdx.x;
+        const int32_t x = tx * T + (i % T), y = ty * T + i / T;
+        const bool valid = i < n_tex_tile && x < w && y < h && LCL_IN((int64_t)y * w + x, (int64_t)w * h);
+        const int64_t l = valid ? (int64_t)y * w + x : 0;
+        bool covered = false;
         if (valid) {
-            uint4 t4 = *reinterpret_cast<const uint4 *>(tri_plane + l);
-            uint32_t tt[4] = {t4.x, t4.y, t4.z, t4.w};
-            int32_t ox[4], oy[4], oz[4];
-            // texels of one triangle in a row share its set-up record, its area and reciprocal, and
-            // their edge functions differ by exact integer steps along x (d/dpx of edge_fn(a, b, p)
-            // is -(b.y - a.y), 256 sub-pixels per texel)
-            uint32_t cur = kNone;
-            int32_t last_k = 0;
-            TriSetup s;
-            int64_t A = 0, w1 = 0, w2 = 0, dw1 = 0, dw2 = 0;
-            float rden = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                ox[k] = INT32_MIN;
-                oy[k] = 0;
-                oz[k] = 0;
-                if (tt[k] == kNone) continue;
-                if (!LCL_IN(tt[k], n_tri)) continue;
-                if (tt[k] != cur) {
-                    cur = tt[k];
-                    s = setup[cur];
-                    const int64_t cx = 256 * (int64_t)(x + k) + 128, cy = 256 * ((int64_t)y + row0) + 128;
-                    A = edge_fn(s.x[0], s.y[0], s.x[1], s.y[1], s.x[2], s.y[2]);
-                    w1 = edge_fn(s.x[2], s.y[2], s.x[0], s.y[0], cx, cy);
-                    w2 = edge_fn(s.x[0], s.y[0], s.x[1], s.y[1], cx, cy);
-                    dw1 = -256 * ((int64_t)s.y[0] - s.y[2]);
-                    dw2 = -256 * ((int64_t)s.y[1] - s.y[0]);
-                    rden = __frcp_rn((float)(2 * A));
-                } else {
-                    w1 += dw1 * (k - last_k);
-                    w2 += dw2 * (k - last_k);
-                }
-                last_k = k;
-                ox[k] = interp_axis(w1, w2, A, rden, s.qx[0], s.qx[1], s.qx[2]);
-                oy[k] = interp_axis(w1, w2, A, rden, s.qy[0], s.qy[1], s.qy[2]);
-                oz[k] = interp_axis(w1, w2, A, rden, s.qz[0], s.qz[1], s.qz[2]);
-                nib |= 1u << k;
-                mn[0] = min(mn[0], ox[k]); mx[0] = max(mx[0], ox[k]);
-                mn[1] = min(mn[1], oy[k]); mx[1] = max(mx[1], oy[k]);
-                mn[2] = min(mn[2], oz[k]); mx[2] = max(mx[2], oz[k]);
+            const uint32_t t = __ldcs(tri_plane + l);
+            int32_t ox = INT32_MIN, oy = 0, oz = 0;
+            if (t != kNone && LCL_IN(t, n_tri)) {
+                const TriSetup s = setup[t];
+                const int64_t cx = 256 * (int64_t)x + 128, cy = 256 * ((int64_t)y + row0) + 128;
+                const int64_t A = edge_fn(s.x[0], s.y[0], s.x[1], s.y[1], s.x[2], s.y[2]);
+                const int64_t w1 = edge_fn(s.x[2], s.y[2], s.x[0], s.y[0], cx, cy);
+                const int64_t w2 = edge_fn(s.x[0], s.y[0], s.x[1], s.y[1], cx, cy);
+                const float rden = __frcp_rn((float)(2 * A));
+                ox = interp_axis(w1, w2, A, rden, s.qx[0], s.qx[1], s.qx[2]);
+                oy = interp_axis(w1, w2, A, rden, s.qy[0], s.qy[1], s.qy[2]);
+                oz = interp_axis(w1, w2, A, rden, s.qz[0], s.qz[1], s.qz[2]);
+                mn[0] = min(mn[0], ox); mx[0] = max(mx[0], ox);
+                mn[1] = min(mn[1], oy); mx[1] = max(mx[1], oy);
+                mn[2] = min(mn[2], oz); mx[2] = max(mx[2], oz);
                 ++cnt;
+                covered = true;
             }
-            *reinterpret_cast<int4 *>(px + l) = make_int4(ox[0], ox[1], ox[2], ox[3]);
-            *reinterpret_cast<int4 *>(py + l) = make_int4(oy[0], oy[1], oy[2], oy[3]);
-            *reinterpret_cast<int4 *>(pz + l) = make_int4(oz[0], oz[1], oz[2], oz[3]);
+            __stcs(px + l, ox);
+            __stcs(py + l, oy);
+            __stcs(pz + l, oz);
         }
         // coverage bits: lanes writing the same 32-bit word combine, one atomicOr per word
-        uint32_t word = (uint32_t)(l >> 5);
-        uint32_t val = nib << (uint32_t)(l & 31);
-        uint32_t peers = __match_any_sync(0xffffffffu, valid ? word : 0xFFFFFFFFu);
-        uint32_t orv = __reduce_or_sync(peers, val);
+        const uint32_t word = (uint32_t)(l >> 5);
+        const uint32_t val = covered ? 1u << (uint32_t)(l & 31) : 0u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? word : 0xFFFFFFFFu);
+        const uint32_t orv = __reduce_or_sync(peers, val);
         if (valid && orv != 0 && (threadIdx.x & 31) == (__ffs(peers) - 1) && LCL_IN(word, ((int64_t)w * h + 31) / 32))
             atomicOr(cover + word, orv);
     }

@@ -66,7 +66,9 @@ struct BLassoIn {  // what the host uploads per lasso
 
 struct BItem {
     uint32_t model, tile;
-    unsigned long long mask;
+    unsigned long long mask;  // strokes that can write a texel of the tile
+    unsigned long long sure;  // of those: spheres containing the tile's box (every covered texel
+                              // selected) and unpadded lassos inside whose polygon the tile lies
 };
 
 // Capacities of a workspace's arrays (its limits), for the kernels' index checks.
@@ -210,13 +212,33 @@ __global__ void __launch_bounds__(kThreads) k_batch_cull(const BHdr *__restrict_
         if (smask == 0ull) continue;  // uniform over the CTA
         const int32_t tx = sx * LCL_SUPER + (threadIdx.x % LCL_SUPER);
         const int32_t ty = sy * LCL_SUPER + (threadIdx.x / LCL_SUPER);
-        unsigned long long mask = 0ull;
+        unsigned long long mask = 0ull, sure = 0ull;
         if (tx < a.tiles_x && ty < a.tiles_y) {
             for (unsigned long long m = smask; m; m &= m - 1) {
                 const int k = __ffsll((long long)m) - 1;
-                if (stroke_in_bounds(strokes, (int64_t)M.s0 + k, caps) &&
-                    stroke_may_reach(strokes[M.s0 + k], lassos, a.tile_box, a.tiles_x, a.tiles_y, tx, ty))
+                if (!stroke_in_bounds(strokes, (int64_t)M.s0 + k, caps)) continue;
+                const BStroke &st = strokes[M.s0 + k];
+                if (!stroke_pads(st, lassos) && LCL_IN((int64_t)ty * a.tiles_x + tx, (int64_t)a.tiles_x * a.tiles_y)) {
+                    // unpadded: the tile's own box decides, with its exact class
+                    const int4 *b = reinterpret_cast<const int4 *>(a.tile_box + 8 * ((int64_t)ty * a.tiles_x + tx));
+                    const int4 lo = b[0], hi = b[1];
+                    if (lo.w == 0) continue;
+                    if (st.kind == LCL_STROKE_SPHERE) {
+                        if (box_dist2(lo, hi, st.sphere) > st.sphere.r2) continue;
+                        mask |= 1ull << k;
+                        if (box_far2(lo, hi, st.sphere) <= st.sphere.r2) sure |= 1ull << k;
+                    } else {
+                        const BLasso &L = lassos[st.lasso];
+                        float4 sb;
+                        if (!box_may_touch(L.arg, lo, hi, L.depth, &sb)) continue;
+                        const int cls = lasso_tile_class8<1>(L.arg, L.arg.vx, L.arg.vy, sb);
+                        if (cls == kTileOut) continue;
+                        mask |= 1ull << k;
+                        if (cls == kTileIn) sure |= 1ull << k;
+                    }
+                } else if (stroke_may_reach(st, lassos, a.tile_box, a.tiles_x, a.tiles_y, tx, ty)) {
                     mask |= 1ull << k;
+                }
             }
         }
         const bool cand = mask != 0ull;
@@ -232,6 +254,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_cull(const BHdr *__restrict_
                 it.model = mi;
                 it.tile = (uint32_t)(ty * a.tiles_x + tx);
                 it.mask = mask;
+                it.sure = sure;
                 items[slot] = it;
             }
         }
@@ -357,14 +380,19 @@ __device__ __forceinline__ void apply_part(const BModel &M, const BItem &it, int
             if (!stroke_in_bounds(strokes, (int64_t)M.s0 + si, caps)) continue;
             const BStroke &st = strokes[M.s0 + si];
             uint32_t sel = 0u;
+            const bool sure = (it.sure >> si) & 1ull;
             if (st.kind == LCL_STROKE_SPHERE) {
+                if (sure) {
+                    sel = open;  // the sphere contains the tile's box: every covered texel is selected
+                } else {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int64_t dx = (int64_t)xs[k] - st.sphere.cx, dy = (int64_t)ys[k] - st.sphere.cy;
-                    const int64_t dz = (int64_t)zs[k] - st.sphere.cz;
-                    sel |= (dx * dx + dy * dy + dz * dz <= st.sphere.r2 ? 1u : 0u) << k;
+                    for (int k = 0; k < 4; ++k) {
+                        const int64_t dx = (int64_t)xs[k] - st.sphere.cx, dy = (int64_t)ys[k] - st.sphere.cy;
+                        const int64_t dz = (int64_t)zs[k] - st.sphere.cz;
+                        sel |= (dx * dx + dy * dy + dz * dz <= st.sphere.r2 ? 1u : 0u) << k;
+                    }
+                    sel &= open;
                 }
-                sel &= open;
                 if (sel) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
@@ -378,7 +406,9 @@ __device__ __forceinline__ void apply_part(const BModel &M, const BItem &it, int
                     const int32_t qx = k == 0 ? X.x : k == 1 ? X.y : k == 2 ? X.z : X.w;
                     const int32_t qy = k == 0 ? Y.x : k == 1 ? Y.y : k == 2 ? Y.z : Y.w;
                     const int32_t qz = k == 0 ? Z.x : k == 1 ? Z.y : k == 2 ? Z.z : Z.w;
-                    if (lasso_hit(ls.arg, ls.arg, ls.depth, qx, qy, qz)) sel |= 1u << k;
+                    if (sure ? lasso_hit<true>(ls.arg, ls.arg, ls.depth, qx, qy, qz)
+                             : lasso_hit<false>(ls.arg, ls.arg, ls.depth, qx, qy, qz))
+                        sel |= 1u << k;
                 }
                 const uint32_t label = ls.arg.label;
 #pragma unroll

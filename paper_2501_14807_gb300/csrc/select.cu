@@ -238,6 +238,14 @@ __global__ void __launch_bounds__(kThreads) k_lasso_cull(AtlasDev a, const __gri
                                                          uint32_t *list) {
     const int32_t sx = blockIdx.x, sy = blockIdx.y;
     if (!LCL_IN((int64_t)sy * a.supers_x + sx, (int64_t)a.supers_x * a.supers_y)) return;  // uniform
+    __shared__ float svx[LCL_MAX_LASSO_VERTICES + 1], svy[LCL_MAX_LASSO_VERTICES + 1];
+    if (CLASSIFY) {
+        for (int e = threadIdx.x; e <= p.nv; e += blockDim.x) {
+            svx[e] = p.vx[e];
+            svy[e] = p.vy[e];
+        }
+        __syncthreads();
+    }
     const int4 *sb = reinterpret_cast<const int4 *>(a.super_box + 8 * ((int64_t)sy * a.supers_x + sx));
     const int4 slo = sb[0], shi = sb[1];
     const bool super_in = slo.w > 0 && box_may_touch8(p, slo, shi, nullptr);  // uniform over the CTA
@@ -257,7 +265,7 @@ __global__ void __launch_bounds__(kThreads) k_lasso_cull(AtlasDev a, const __gri
                 float4 sb;
                 cand = box_may_touch8(p, lo, hi, depth, CLASSIFY ? &sb : nullptr);
                 if (CLASSIFY && cand) {
-                    cls = lasso_tile_class8(p, sb);
+                    cls = lasso_tile_class8<8>(p, svx, svy, sb);
                     cand = cls != kTileOut;
                 }
             }

@@ -48,6 +48,15 @@ __device__ __forceinline__ int64_t box_dist2(int4 lo, int4 hi, const SphereArg &
     return ex * ex + ey * ey + ez * ez;
 }
 
+// Squared distance from the sphere's centre to the box's farthest point: at most r2 means the sphere
+// contains the whole box.
+__device__ __forceinline__ int64_t box_far2(int4 lo, int4 hi, const SphereArg &s) {
+    const int64_t fx = max(s.cx - (int64_t)lo.x, (int64_t)hi.x - s.cx);
+    const int64_t fy = max(s.cy - (int64_t)lo.y, (int64_t)hi.y - s.cy);
+    const int64_t fz = max(s.cz - (int64_t)lo.z, (int64_t)hi.z - s.cz);
+    return fx * fx + fy * fy + fz * fz;
+}
+
 // Any box of the 3 x 3 neighbourhood of (bx, by) in a grid of nx x ny boxes within the sphere's
 // reach (used when padding may write texels next to the selected ones).
 __device__ __forceinline__ bool near_box_3x3(const int32_t *boxes, int32_t nx, int32_t ny, int32_t bx, int32_t by,
@@ -273,8 +282,12 @@ __device__ __forceinline__ void stage_lasso(LassoShared &sh, const LassoArg &p) 
 //    minimum over the box is at a corner; if that minimum (less 1e-4 for FP32 rounding) exceeds
 //    the largest depth-map value over the box's widened pixel footprint plus the bias, every texel
 //    of the box fails the depth test.  Footprints above 1024 pixels are not scanned (kept).
-__device__ inline bool box_may_touch(const LassoArg &p, int4 lo, int4 hi, const float *__restrict__ depth = nullptr) {
+// sbox (optional): as for box_may_touch8.
+__device__ inline bool box_may_touch(const LassoArg &p, int4 lo, int4 hi, const float *__restrict__ depth = nullptr,
+                                     float4 *sbox = nullptr) {
     float xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY, zmin = INFINITY;
+    bool finite = true;
+    if (sbox) *sbox = make_float4(NAN, NAN, NAN, NAN);
 #pragma unroll 1
     for (int c = 0; c < 8; ++c) {
         float x = (float)((c & 1) ? hi.x : lo.x), y = (float)((c & 2) ? hi.y : lo.y), z = (float)((c & 4) ? hi.z : lo.z);
@@ -282,12 +295,14 @@ __device__ inline bool box_may_touch(const LassoArg &p, int4 lo, int4 hi, const 
         if (!(cw > 0.0f)) return true;
         float xs = screen_of(div_rn(clip_row(p.m, x, y, z), cw), p.ws);
         float ys = screen_of(div_rn(clip_row(p.m + 4, x, y, z), cw), p.hs);
+        finite = finite && isfinite(xs) && isfinite(ys);
         float zn = div_rn(clip_row(p.m + 8, x, y, z), cw);
         xmin = fminf(xmin, xs); xmax = fmaxf(xmax, xs);
         ymin = fminf(ymin, ys); ymax = fmaxf(ymax, ys);
         zmin = fminf(zmin, zn);
     }
     if (xmax < p.bx0 || xmin > p.bx1 || ymax < p.by0 || ymin > p.by1) return false;
+    if (sbox && finite) *sbox = make_float4(xmin, xmax, ymin, ymax);
     if (!depth) return true;
     const float margin = 2.0f;
     const int ix0 = max(0, __float2int_rd(xmin - margin)), ix1 = min(p.w_s - 1, __float2int_rd(xmax + margin));
@@ -366,8 +381,12 @@ enum : int { kTileOut = 0, kTileTest = 1, kTileIn = 2 };
 // per-texel edge decision is then the exact one at that point, and the exact even-odd parity is the
 // same at every point of a region no edge meets -- the parity at the centre.  The segment-box test is
 // conservative: an FP32 side value whose magnitude is within its error bound counts as meeting.
-__device__ __forceinline__ int lasso_tile_class8(const LassoArg &p, float4 sb) {
-    const unsigned lane = threadIdx.x & 31u, sub = lane & 7u;
+// vx, vy: the polygon's vertices (vertex nv = vertex 0), staged in shared memory by the caller so
+// that the lanes' different edges are not serialised on the parameter bank.  LANES: 8 (an aligned
+// group of 8 lanes shares the work, as after box_may_touch8) or 1 (one thread does it alone).
+template <int LANES = 8>
+__device__ __forceinline__ int lasso_tile_class8(const LassoArg &p, const float *vx, const float *vy, float4 sb) {
+    const unsigned lane = threadIdx.x & 31u, sub = LANES == 8 ? (lane & 7u) : 0u;
     const unsigned gm = 0xFFu << (lane & 24u);
     if (!(isfinite(sb.x) && isfinite(sb.y) && isfinite(sb.z) && isfinite(sb.w))) return kTileTest;  // uniform
     const float m = 1.0f;
@@ -375,8 +394,8 @@ __device__ __forceinline__ int lasso_tile_class8(const LassoArg &p, float4 sb) {
     const float cx = __fmul_rn(0.5f, __fadd_rn(sb.x, sb.y)), cy = __fmul_rn(0.5f, __fadd_rn(sb.z, sb.w));
     const float u5 = 5.0f * 5.9604645e-8f;  // 5 u, u = 2^-24
     bool meets = false, parity = false;
-    for (int e = (int)sub; e < p.nv; e += 8) {
-        const float ax = p.vx[e], ay = p.vy[e], bx = p.vx[e + 1], by = p.vy[e + 1];
+    for (int e = (int)sub; e < p.nv; e += LANES) {
+        const float ax = vx[e], ay = vy[e], bx = vx[e + 1], by = vy[e + 1];
         if (!(fmaxf(ax, bx) < x0 || fminf(ax, bx) > x1 || fmaxf(ay, by) < y0 || fminf(ay, by) > y1)) {
             const float dx = __fsub_rn(bx, ax), dy = __fsub_rn(by, ay);
             bool pos = false, neg = false;
@@ -397,10 +416,11 @@ __device__ __forceinline__ int lasso_tile_class8(const LassoArg &p, float4 sb) {
         }
     }
     uint32_t bits = (meets ? 1u : 0u) | (parity ? 2u : 0u);
-    for (int o = 1; o < 8; o <<= 1) {
+    for (int o = 1; o < LANES; o <<= 1) {
         const uint32_t t = __shfl_xor_sync(gm, bits, o);
         bits = (bits | (t & 1u)) ^ (t & 2u);
     }
+    (void)gm;
     if (bits & 1u) return kTileTest;
     if (!(bits & 2u)) return kTileOut;
     const bool on_screen = x0 >= 0.0f && x1 < p.ws && y0 >= 0.0f && y1 < p.hs;
@@ -417,7 +437,9 @@ __device__ __forceinline__ int lasso_tile_class8(const LassoArg &p, float4 sb) {
 //    rounding is far below the 2-pixel margin;
 //  - only edges listed for the point's y-band are tested: an edge can count only if its y-range
 //    contains y, and each band lists every edge whose y-range comes within a margin of the band.
-template <typename Edges>
+// INSIDE: the texel's tile is known to lie inside the polygon (lasso_tile_class8): the edge tests,
+// whose outcome would be "inside", are skipped.
+template <bool INSIDE = false, typename Edges>
 __device__ __forceinline__ bool lasso_hit(const LassoArg &p, const Edges &sh, const float *__restrict__ depth,
                                           int32_t X, int32_t Y, int32_t Z) {
     if (X == INT32_MIN) return false;  // uncovered
@@ -434,8 +456,8 @@ __device__ __forceinline__ bool lasso_hit(const LassoArg &p, const Edges &sh, co
     if (!(ys >= p.ymin && ys < p.ymax)) return false;  // no edge straddles y
     int band = __float2int_rz(__fmul_rn(__fsub_rn(ys, p.band_y0), p.band_inv_h));
     band = band < 0 ? 0 : (band >= kBands ? kBands - 1 : band);
-    bool inside = false;
-    for (int k = sh.band_off[band]; k < sh.band_off[band + 1]; ++k) {
+    bool inside = INSIDE;
+    for (int k = sh.band_off[band]; !INSIDE && k < sh.band_off[band + 1]; ++k) {
         if (!LCL_IN(k, kBandEdgesMax)) break;
         const int e = sh.band_edge[k];
         if (!LCL_IN(e, LCL_MAX_LASSO_VERTICES)) continue;

@@ -30,7 +30,7 @@
 
 static_assert(sizeof(lcl_serve_request) == 608, "lcl_serve_request layout");
 static_assert(sizeof(lcl_serve_model) == 96, "lcl_serve_model layout");
-static_assert(sizeof(lcl_serve_config) == 32 && sizeof(lcl_serve_done) == 16 && sizeof(lcl_serve_stats) == 64,
+static_assert(sizeof(lcl_serve_config) == 32 && sizeof(lcl_serve_done) == 32 && sizeof(lcl_serve_stats) == 80,
               "serve struct layouts");
 
 namespace {
@@ -83,6 +83,7 @@ struct Slot {
 struct Epoch {
     int64_t seq;
     int slot;
+    double t_launch;
     cudaEvent_t done;
     std::vector<const lcl_serve_request *> reqs;
     std::vector<Query> queries;
@@ -123,6 +124,7 @@ struct lcl_server {
     std::vector<int32_t> active;  // models with queued requests
     // stats
     uint64_t epochs = 0, admissions = 0, spills = 0, resident_bytes = 0, resident_models = 0;
+    uint64_t admitted_bytes = 0, deferred = 0;
     double host_busy = 0.0;
 };
 
@@ -241,6 +243,7 @@ bool place(lcl_server *s, Model &m, size_t off, bool fresh, lcl_status *st) {
     s->resident_bytes += need;
     s->resident_models += 1;
     s->admissions += 1;
+    s->admitted_bytes += m.desc.image_bytes;
     return true;
 }
 
@@ -263,7 +266,10 @@ bool admit(lcl_server *s, Model &m, double now, lcl_status *st) {
                 victim = &v;
             }
         }
-        if (!victim) return false;
+        if (!victim) {
+            s->deferred += 1;
+            return false;
+        }
         if ((*st = spill(s, *victim)) != LCL_OK) return false;
     }
     return place(s, m, off, true, st);
@@ -403,6 +409,7 @@ bool run_epoch(lcl_server *s, double now, lcl_status *st) {
         return false;
     }
     for (int32_t mi : used) s->models[mi].last_seq = ep.seq;
+    ep.t_launch = now_s();
     sl.busy = true;
     s->next_seq += 1;
     s->epochs += 1;
@@ -444,7 +451,7 @@ void serve_loop(lcl_server *s) {
                     std::memcpy(qq.req->result, sl.host_tables + qq.host_off, 16 * (size_t)qq.req->n_labels);
                 {
                     std::lock_guard<std::mutex> lock(s->mu);
-                    for (const lcl_serve_request *r : ep.reqs) s->done.push_back({r->tag, t});
+                    for (const lcl_serve_request *r : ep.reqs) s->done.push_back({r->tag, t, ep.t_launch, 0.0});
                     s->n_done += ep.reqs.size();
                 }
                 s->completed_seq = ep.seq;
@@ -708,6 +715,8 @@ lcl_status lcl_serve_stats_get(lcl_server *s, lcl_serve_stats *out) {
     out->resident_bytes = s->resident_bytes;
     out->resident_models = s->resident_models;
     out->host_busy_s = s->host_busy;
+    out->admitted_bytes = s->admitted_bytes;
+    out->deferred = s->deferred;
     return LCL_OK;
 }
 

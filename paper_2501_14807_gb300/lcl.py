@@ -122,13 +122,13 @@ class lcl_serve_model(C.Structure):
 
 
 class lcl_serve_done(C.Structure):
-    _fields_ = [("tag", C.c_uint64), ("t_done", C.c_double)]
+    _fields_ = [("tag", C.c_uint64), ("t_done", C.c_double), ("t_launch", C.c_double), ("_pad", C.c_double)]
 
 
 class lcl_serve_stats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("done", C.c_uint64), ("epochs", C.c_uint64), ("admissions", C.c_uint64),
                 ("spills", C.c_uint64), ("resident_bytes", C.c_uint64), ("resident_models", C.c_uint64),
-                ("host_busy_s", C.c_double)]
+                ("host_busy_s", C.c_double), ("admitted_bytes", C.c_uint64), ("deferred", C.c_uint64)]
 
 
 # lcl_serve_request as a numpy record (608 bytes), so a whole trace is one array
@@ -159,8 +159,8 @@ assert C.sizeof(lcl_batch_model) == 32 and C.sizeof(lcl_batch_stroke) == 40 and 
 assert C.sizeof(lcl_batch_limits) == 32 and C.sizeof(lcl_batch_config) == 16 and C.sizeof(lcl_tool) == 40
 assert C.sizeof(lcl_numeric_layer) == 24 and C.sizeof(lcl_zone_stats) == 48
 assert C.sizeof(lcl_pool_layer) == 40 and C.sizeof(lcl_pool_stats) == 40
-assert C.sizeof(lcl_serve_config) == 32 and C.sizeof(lcl_serve_model) == 96 and C.sizeof(lcl_serve_done) == 16
-assert C.sizeof(lcl_serve_stats) == 64 and SERVE_REQUEST_DTYPE.itemsize == 608
+assert C.sizeof(lcl_serve_config) == 32 and C.sizeof(lcl_serve_model) == 96 and C.sizeof(lcl_serve_done) == 32
+assert C.sizeof(lcl_serve_stats) == 80 and SERVE_REQUEST_DTYPE.itemsize == 608
 
 SPHERE_DTYPE = np.dtype([("cx", "<i4"), ("cy", "<i4"), ("cz", "<i4"), ("pad", "<i4"),
                          ("r2", "<i8"), ("label", "<u4"), ("flags", "<u4")])

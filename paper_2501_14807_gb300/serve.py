@@ -60,6 +60,7 @@ class Request:
     query: object = None     # (op name, layer a, layer b, n_labels)
     t_done: float = -1.0
     result: object = None    # QUERY: (counts, areas) as numpy uint64 arrays
+    t_launch: float = -1.0   # native server: when the request's epoch was launched
 
 
 @dataclass
@@ -640,12 +641,11 @@ class NativeServer:
         rec = np.zeros(n, lcl.SERVE_REQUEST_DTYPE)
         n_q = sum(1 for r in requests if r.kind == QUERY)
         results = np.zeros((max(n_q, 1), 2, self.max_labels), np.uint64)
-        t0 = float(self.lib.lcl_serve_clock()) + start_delay_s
         qi = 0
         base = results.ctypes.data
         for i, r in enumerate(requests):
             x = rec[i]
-            x["t_arrive"] = t0 + r.t_arrive
+            x["t_arrive"] = r.t_arrive
             x["tag"] = i
             x["model"] = r.model
             x["kind"] = r.kind
@@ -669,6 +669,10 @@ class NativeServer:
                 x["result"] = base + qi * results.strides[0]
                 r._qi = qi
                 qi += 1
+        # the arrival times go on the server clock only now, once the records are ready, so that no
+        # request is late before the loop sees it
+        t0 = float(self.lib.lcl_serve_clock()) + start_delay_s
+        rec["t_arrive"] += t0
         lcl._check("lcl_serve_submit", self.lib.lcl_serve_submit(self.ptr, rec.ctypes.data, n))
         out = (lcl.lcl_serve_done * 4096)()
         got = lcl.C.c_int32()
@@ -679,6 +683,7 @@ class NativeServer:
             for k in range(got.value):
                 r = requests[out[k].tag]
                 r.t_done = out[k].t_done - t0
+                r.t_launch = out[k].t_launch - t0
             left -= got.value
             if got.value:
                 last = time.perf_counter()

@@ -498,6 +498,11 @@ def test_sphere_with_texture_padding_bit_exact(T, dt):
     lcl.lcl_select_sphere(a, layer, recs, hits_out=hits)
     assert np.array_equal(to_np(layer, dt), exp)
     assert np.array_equal(to_np(hits, np.uint64), exp_hits)
+    # short calls (one launch per stroke) and long calls (one launch for all) give the same layer
+    layer2 = to_dev(init)
+    for k in range(0, len(recs), 3):
+        lcl.lcl_select_sphere(a, layer2, recs[k:k + 3])
+    assert np.array_equal(to_np(layer2, dt), exp)
 
 
 def test_library_division_equals_ieee_division():
