@@ -287,6 +287,7 @@ def run_ours(args):
     ws_sel = torch.empty(lcl.lcl_select_workspace_bytes(atlas, max(len(r) for r in per_layer)), dtype=torch.uint8,
                          device=dev)
     sphere_hits = [torch.zeros(max(len(r), 1), dtype=torch.int64, device=dev) for r in per_layer]
+    inside_per_layer = [sphere_inside_texels(atlas, r, dev) for r in per_layer]
     cams = [lcl.lcl_camera_from_vp(atlas, c.vp, c.width, c.height) for c in w.cams]
     depths = [torch.empty((c.height, c.width), dtype=torch.float32, device=dev) for c in w.cams]
     ws_depth = torch.empty(max([lcl.lcl_depth_workspace_bytes(mesh, c.width, c.height) for c in w.cams] + [256]),
@@ -393,7 +394,8 @@ def run_ours(args):
     barrier()
     e2e_ms = f0.elapsed_time(f1)
 
-    by_radius = sphere_radius_breakdown(w, atlas, layers, per_layer, ws_sel, stream, dev) if rank == 0 else None
+    by_radius = sphere_radius_breakdown(w, atlas, layers, per_layer, inside_per_layer, ws_sel, stream, dev) \
+        if rank == 0 else None
 
     (total_ms, e2e_ms, sph_ms), all_texels = combine_ranks([total_ms, e2e_ms, sph_ms], texels, world, dev)
     if rank != 0:
@@ -405,7 +407,9 @@ def run_ours(args):
     # the batching workload (256 models, 64 queued strokes each), outside the timed region
     batch = batch_summary(args.batch_models, 5, 2, torch_device=local) if (world == 1 and args.batch_models > 0) else None
     peak, peak_kind = peaks()
-    sph_bytes = sph_hits * (12 + w.dtype_bytes)
+    sph_inside = int(sum(int(x.sum()) for x in inside_per_layer))
+    sph_bytes = sph_hits * (12 + w.dtype_bytes)          # the per-unit bytes of the hot-path scope: 12 B + label
+    sph_needed = float(sphere_bytes(sph_hits, sph_inside, w.dtype_bytes))
     achieved = sph_bytes / (sph_ms / args.steps / 1e3) / 1e9
     value = all_texels * args.steps / (total_ms / 1e3) / 1e9
     traffic = profile_traffic(w)
@@ -421,6 +425,12 @@ def run_ours(args):
                      "peak_kind": peak_kind, "traffic": traffic,
                      "kernel": "sphere edit (k_sphere_step, one launch per stroke)",
                      "algorithmic_bytes_per_launch": sph_bytes / max(n_strokes, 1),
+                     "bytes_model": "12 B position + label per selected texel (the scope's per-unit bytes); the "
+                                    "kernel reads positions only for tiles the sphere's surface crosses and the "
+                                    "coverage bits (1/8 B per texel) for tiles inside the sphere",
+                     "hit_texels": sph_hits, "hit_texels_inside_tiles": sph_inside,
+                     "bytes_needed_per_launch": sph_needed / max(n_strokes, 1),
+                     "frac_of_bytes_needed": sph_needed / (sph_ms / args.steps / 1e3) / 1e9 / peak,
                      "ms_per_launch": sph_ms / args.steps / max(n_strokes, 1)},
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,
@@ -432,7 +442,9 @@ def run_ours(args):
         "batch": batch,
         "breakdown": {"sphere_ms_per_step": sph_ms / args.steps, "sphere_hit_texels": sph_hits,
                       "lasso_hit_texels": las_hits, "texels_per_step": texels},
-        "rows": row_rooflines(w, row_ms, args.steps, sph_hits, las_hits, peak),
+        "rows": row_rooflines(w, row_ms, args.steps, sph_bytes, sph_hits, las_hits, peak),
+        "sphere_bytes_needed": {"inside_tile_texels": sph_inside, "bytes": sph_needed,
+                                "gb_s": sph_needed / (sph_ms / args.steps / 1e3) / 1e9},
         "sphere_by_radius": by_radius,
     }
     print(json.dumps(line), flush=True)
@@ -443,10 +455,38 @@ def run_ours(args):
 ROWS = ("atlas", "sphere", "depth", "lasso", "overlay", "area")
 
 
-def row_rooflines(w, row_ms, steps, sph_hits, las_hits, peak):
+def sphere_inside_texels(atlas, records, dev, chunk=16):
+    """Per stroke, the covered texels of the tiles whose box lies inside the stroke's sphere (the
+    library selects them from the coverage bits without reading their positions): tile boxes against
+    each stroke on the device, chunk strokes at a time.  Strokes with texture padding count 0 (the
+    library reads positions for them).  Returns a numpy int64 array."""
+    import torch
+    tb = atlas.tile_box().to(torch.int64)
+    lo, cnt, hi = tb[:, 0:3], tb[:, 3], tb[:, 4:7]
+    out = np.zeros(len(records), np.int64)
+    for k0 in range(0, len(records), chunk):
+        r = records[k0:k0 + chunk]
+        c = torch.tensor(np.stack([r["cx"], r["cy"], r["cz"]], 1).astype(np.int64), device=dev)[:, None, :]
+        far = torch.maximum(c - lo[None], hi[None] - c)
+        inside = ((far * far).sum(-1) <= torch.tensor(r["r2"].astype(np.int64), device=dev)[:, None]) & (cnt > 0)[None]
+        n = (inside.to(torch.int64) * cnt[None]).sum(1).cpu().numpy()
+        n[(r["flags"] & 15) != 0] = 0
+        out[k0:k0 + len(r)] = n
+    return out
+
+
+def sphere_bytes(hits, inside, label_bytes):
+    """Algorithmic bytes of sphere edits: a selected texel that must be tested costs its 12-byte position
+    and its label; a texel of a tile inside the sphere costs its coverage bit and its label."""
+    hits, inside = np.asarray(hits, np.float64), np.asarray(inside, np.float64)
+    return (hits - inside) * (12 + label_bytes) + inside * (label_bytes + 1 / 8)
+
+
+def row_rooflines(w, row_ms, steps, sph_bytes, sph_hits, las_hits, peak):
     """Per-row CUDA-event time of one step and, for the streaming rows, algorithmic bytes over
     that time against the HBM peak.  Bytes per unit (s = label bytes):
-      sphere / lasso   hit texels x (12 + s), plus the depth map read once per lasso
+      sphere           hit texels x (12 + s) (sph_bytes, computed by the caller)
+      lasso            hit texels x (12 + s), plus the depth map read once per lasso
       overlay          every texel x (3 s + 1/8)
       area             every texel x (s + 4), plus 8 B per triangle
       atlas            every texel x (16 + 1/8) written plus the mesh read (a rasteriser:
@@ -460,7 +500,7 @@ def row_rooflines(w, row_ms, steps, sph_hits, las_hits, peak):
     lasso_depth = sum(w.cams[L.cam].width * w.cams[L.cam].height * 4 for L in w.lassos)
     spec = {
         "atlas": (n * (16 + 1 / 8) + mesh_bytes, "raster", "atlas build (quantise, UV raster, resolve, boxes)"),
-        "sphere": (sph_hits * (12 + s), "hbm", f"{len(w.strokes.radius)} sphere strokes, {sph_hits} hit texels"),
+        "sphere": (sph_bytes, "hbm", f"{len(w.strokes.radius)} sphere strokes, {sph_hits} hit texels"),
         "depth": (cam_px * 4 + m.pos.nbytes + m.tri_pos.nbytes, "raster", f"{len(w.cams)} depth maps"),
         "lasso": (las_hits * (12 + s) + lasso_depth, "hbm", f"{len(w.lassos)} lassos, {las_hits} hit texels"),
         "overlay": (len(w.overlays) * n * (3 * s + 1 / 8), "hbm", f"{len(w.overlays)} full-layer overlays"),
@@ -478,11 +518,11 @@ def row_rooflines(w, row_ms, steps, sph_hits, las_hits, peak):
     return out
 
 
-def sphere_radius_breakdown(w, atlas, layers, per_layer, ws_sel, stream, dev):
+def sphere_radius_breakdown(w, atlas, layers, per_layer, inside_per_layer, ws_sel, stream, dev):
     """Per-radius breakdown of the sphere strokes, outside the timed region: every stroke again as
     its own call (zeroing, cull and apply launches), timed with CUDA events, binned by radius in
-    half-decades of the bounding-box diagonal.  Bytes are the algorithmic (12 + label bytes) per
-    hit texel, against the measured copy peak.  Small strokes are bound by launch and cull
+    half-decades of the bounding-box diagonal.  Bytes are 12 + label bytes per hit texel (and, beside
+    them, the bytes the kernel needs, sphere_bytes), against the measured copy peak.  Small strokes are bound by launch and cull
     latency; the chained call of the timed region hides part of that."""
     import torch
     from paper_2501_14807_gb300 import lcl
@@ -504,7 +544,8 @@ def sphere_radius_breakdown(w, atlas, layers, per_layer, ws_sel, stream, dev):
         torch.cuda.synchronize(dev)
         hh = hs.cpu().numpy()
         for k in range(len(recs)):
-            rows.append((float(w.strokes.radius[sel[k]]) / diag, int(hh[k]), ev[k].elapsed_time(ev[k + 1])))
+            rows.append((float(w.strokes.radius[sel[k]]) / diag, int(hh[k]), ev[k].elapsed_time(ev[k + 1]),
+                         int(inside_per_layer[li][k])))
     edges = [0.0, 0.001, 0.00316, 0.01, 0.0316, 0.1, 0.316, 10.0]
     out = []
     for lo, hi in zip(edges[:-1], edges[1:]):
@@ -514,8 +555,11 @@ def sphere_radius_breakdown(w, atlas, layers, per_layer, ws_sel, stream, dev):
         hit = sum(r[1] for r in b)
         ms = sum(r[2] for r in b)
         gbs = hit * (12 + w.dtype_bytes) / (ms / 1e3) / 1e9
+        inside = sum(r[3] for r in b)
         out.append({"radius_of_diagonal": [lo, hi], "strokes": len(b), "hit_texels": hit, "ms": ms,
-                    "us_per_stroke": 1e3 * ms / len(b), "gb_s": gbs, "frac": gbs / peak})
+                    "us_per_stroke": 1e3 * ms / len(b), "gb_s": gbs, "frac": gbs / peak,
+                    "hit_texels_inside_tiles": inside,
+                    "frac_of_bytes_needed": float(sphere_bytes(hit, inside, w.dtype_bytes)) / (ms / 1e3) / 1e9 / peak})
     return {"timing": "one call per stroke (zeroing, cull, apply), CUDA events; not the chained timed call",
             "bins": out}
 

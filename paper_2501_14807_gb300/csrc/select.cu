@@ -35,11 +35,12 @@
 namespace lcl {
 namespace {
 
-__global__ void k_sel_init(uint32_t *counters, int32_t n, unsigned long long *hits) {
+// Zeroes n counters and the first n_hits of `hits` (nullable).
+__global__ void k_sel_init(uint32_t *counters, int32_t n, unsigned long long *hits, int32_t n_hits) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (!LCL_IN(i, n)) break;
         counters[i] = 0;
-        if (hits) hits[i] = 0;
+        if (hits && i < n_hits) hits[i] = 0;
     }
 }
 
@@ -64,7 +65,7 @@ __device__ __forceinline__ void cull_super_sphere(const AtlasDev &a, const Spher
     if (!in_reach) return;  // uniform over the CTA
     const int32_t tx = sx * LCL_SUPER + (threadIdx.x % LCL_SUPER);
     const int32_t ty = sy * LCL_SUPER + (threadIdx.x / LCL_SUPER);
-    bool cand = false;
+    bool cand = false, inside = false;
     const int64_t n_tiles = (int64_t)a.tiles_x * a.tiles_y;
     if (tx < a.tiles_x && ty < a.tiles_y) {
         if (PAD) {
@@ -73,9 +74,11 @@ __device__ __forceinline__ void cull_super_sphere(const AtlasDev &a, const Spher
             const int4 *tb = reinterpret_cast<const int4 *>(a.tile_box + 8 * ((int64_t)ty * a.tiles_x + tx));
             const int4 lo = tb[0], hi = tb[1];
             cand = lo.w > 0 && box_dist2(lo, hi, s) <= s.r2;
+            // the sphere contains the tile's box: every covered texel of the tile is selected
+            inside = cand && box_far2(lo, hi, s) <= s.r2;
         }
     }
-    append_candidate(cand, (uint32_t)(ty * a.tiles_x + tx), counter, list, n_tiles);
+    append_candidate(cand, (uint32_t)(ty * a.tiles_x + tx) | (inside ? kInsideTile : 0u), counter, list, n_tiles);
 }
 
 // Culls the first stroke of a call.
@@ -94,24 +97,34 @@ __global__ void __launch_bounds__(kThreads) k_sphere_cull(AtlasDev a, SphereArg 
 
 // One work item = one tile, or a 256-quad chunk of a larger tile; this thread's quad of it.
 struct Item {
-    int64_t l;  // linear index of the quad's first texel, -1 if the thread has no quad here
-    int4 X, Y, Z;
+    int64_t l;     // linear index of the quad's first texel, -1 if the thread has no quad here
+    int32_t sure;  // the quad's tile lies inside the sphere: its covered texels (bit k: texel k), else -1
+    int4 X, Y, Z;  // positions (loaded only when sure is -1)
 };
 
 __device__ __forceinline__ Item load_item(const AtlasDev &a, const uint32_t *__restrict__ list, uint32_t item,
                                           int cpt_log2, int32_t qpr, int32_t nq) {
     Item it;
     it.l = -1;
+    it.sure = -1;
     if (!LCL_IN(item >> cpt_log2, (int64_t)a.tiles_x * a.tiles_y)) return it;
-    const uint32_t tile = __ldg(list + (item >> cpt_log2));
+    const uint32_t entry = __ldg(list + (item >> cpt_log2));
+    const uint32_t tile = entry & ~kInsideTile;
     const int32_t qd = (int32_t)((item & ((1u << cpt_log2) - 1)) * kThreads + threadIdx.x);
     const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
     if (qd < nq && x < a.w && y < a.h && LCL_IN((int64_t)y * a.w + x + 3, (int64_t)a.w * a.h)) {
         it.l = (int64_t)y * a.w + x;
-        it.X = __ldg(reinterpret_cast<const int4 *>(a.px + it.l));
-        it.Y = __ldg(reinterpret_cast<const int4 *>(a.py + it.l));
-        it.Z = __ldg(reinterpret_cast<const int4 *>(a.pz + it.l));
+        if (entry & kInsideTile) {  // inside the sphere: the coverage bits decide, no positions needed
+            if (LCL_IN(it.l >> 5, ((int64_t)a.w * a.h + 31) >> 5))
+                it.sure = (int32_t)((__ldg(a.cover + (it.l >> 5)) >> (it.l & 31)) & 0xFu);
+            else
+                it.sure = 0;
+        } else {
+            it.X = __ldg(reinterpret_cast<const int4 *>(a.px + it.l));
+            it.Y = __ldg(reinterpret_cast<const int4 *>(a.py + it.l));
+            it.Z = __ldg(reinterpret_cast<const int4 *>(a.pz + it.l));
+        }
     }
     return it;
 }
@@ -119,6 +132,7 @@ __device__ __forceinline__ Item load_item(const AtlasDev &a, const uint32_t *__r
 // Hit mask of a quad.  Uncovered texels hold x = INT32_MIN, y = z = 0: their squared distance
 // exceeds 2^61, above every accepted r2 (<= 2^50), so they never test as hit.
 __device__ __forceinline__ uint32_t sphere_mask(const Item &it, const SphereArg &s) {
+    if (it.sure >= 0) return (uint32_t)it.sure;
     const int32_t xs[4] = {it.X.x, it.X.y, it.X.z, it.X.w}, ys[4] = {it.Y.x, it.Y.y, it.Y.z, it.Y.w};
     const int32_t zs[4] = {it.Z.x, it.Z.y, it.Z.z, it.Z.w};
     uint32_t m = 0;
@@ -169,7 +183,7 @@ __device__ uint32_t pad_mask(const AtlasDev &a, const Item &it, const SphereArg 
 // PAD: `s` pads the texture; NEXT_PAD: `nxt` does.  NUM: a numeric layer, whose mask bits (vm) are
 // set (or cleared) for every texel written.
 template <typename L, bool PAD, bool NEXT_PAD, bool NUM>
-__global__ void __launch_bounds__(kThreads) k_sphere_step(AtlasDev a, L *__restrict__ layer, SphereArg s,
+__global__ void __launch_bounds__(kThreads, 6) k_sphere_step(AtlasDev a, L *__restrict__ layer, SphereArg s,
                                                           const uint32_t *__restrict__ counter,
                                                           const uint32_t *__restrict__ list,
                                                           unsigned long long *hits, int has_next, SphereArg nxt,
@@ -226,18 +240,36 @@ __global__ void __launch_bounds__(kThreads) k_sphere_step(AtlasDev a, L *__restr
 
 // ---- lasso ---------------------------------------------------------------------------
 
-// Candidate tiles of a lasso (or tool window).  A CTA takes 32 tiles of one super-tile per pass
-// (blockIdx.z selects its share when a super-tile is split over several CTAs), 8 lanes per tile
-// (box_may_touch8); the super-tile's own box is tested first, uniformly over the CTA.  FLAGS:
-// write a 0/1 flag per tile instead of appending candidates (first pass of a padded edit).
-// CLASSIFY (lassos): tiles that lasso_tile_class8 finds outside the polygon are dropped, and those
-// it finds inside are listed with kInsideTile set (their texels skip the edge tests).
+// Super-tiles a lasso (or tool window) can touch: 8 lanes per super-tile (box_may_touch8 without
+// the depth map), appended to `list` (counter `counter`).
+__global__ void __launch_bounds__(kThreads) k_lasso_supers(AtlasDev a, const __grid_constant__ LassoArg p,
+                                                           uint32_t *counter, uint32_t *list) {
+    const int64_t n_super = (int64_t)a.supers_x * a.supers_y;
+    const int64_t sidx = (int64_t)blockIdx.x * (kThreads / 8) + threadIdx.x / 8;
+    bool cand = false;
+    if (sidx < n_super) {  // uniform over each group of 8 lanes
+        const int4 *sb = reinterpret_cast<const int4 *>(a.super_box + 8 * sidx);
+        const int4 slo = sb[0], shi = sb[1];
+        cand = slo.w > 0 && box_may_touch8(p, slo, shi, nullptr);
+    }
+    append_candidate(cand && (threadIdx.x & 7u) == 0, (uint32_t)sidx, counter, list, n_super);
+}
+
+constexpr int kCullParts = LCL_SUPER * LCL_SUPER / (kThreads / 8);  // 8 parts of 32 tiles per super-tile
+
+// Candidate tiles of a lasso (or tool window) in the super-tiles k_lasso_supers listed: the CTAs take
+// (super-tile, part) units, a part being 32 tiles tested by 8 lanes each (box_may_touch8 with the
+// depth map), so the work spreads over the GPU however few super-tiles the lasso reaches.  FLAGS:
+// write a 0/1 flag per tile instead of appending candidates (first pass of a padded edit; the flags
+// of tiles in other super-tiles were cleared before).  CLASSIFY (lassos): tiles that
+// lasso_tile_class8 finds outside the polygon are dropped, and those it finds inside are listed with
+// kInsideTile set (their texels skip the edge tests).
 template <bool FLAGS, bool CLASSIFY>
 __global__ void __launch_bounds__(kThreads) k_lasso_cull(AtlasDev a, const __grid_constant__ LassoArg p,
-                                                         const float *__restrict__ depth, uint32_t *counter,
+                                                         const float *__restrict__ depth,
+                                                         const uint32_t *__restrict__ super_count,
+                                                         const uint32_t *__restrict__ supers, uint32_t *counter,
                                                          uint32_t *list) {
-    const int32_t sx = blockIdx.x, sy = blockIdx.y;
-    if (!LCL_IN((int64_t)sy * a.supers_x + sx, (int64_t)a.supers_x * a.supers_y)) return;  // uniform
     __shared__ float svx[LCL_MAX_LASSO_VERTICES + 1], svy[LCL_MAX_LASSO_VERTICES + 1];
     if (CLASSIFY) {
         for (int e = threadIdx.x; e <= p.nv; e += blockDim.x) {
@@ -246,28 +278,24 @@ __global__ void __launch_bounds__(kThreads) k_lasso_cull(AtlasDev a, const __gri
         }
         __syncthreads();
     }
-    const int4 *sb = reinterpret_cast<const int4 *>(a.super_box + 8 * ((int64_t)sy * a.supers_x + sx));
-    const int4 slo = sb[0], shi = sb[1];
-    const bool super_in = slo.w > 0 && box_may_touch8(p, slo, shi, nullptr);  // uniform over the CTA
-    const int64_t n_tiles = (int64_t)a.tiles_x * a.tiles_y;
-    constexpr int kPerPass = kThreads / 8;
-    for (int32_t local = blockIdx.z * kPerPass + (int32_t)(threadIdx.x / 8); local < LCL_SUPER * LCL_SUPER;
-         local += gridDim.z * kPerPass) {
+    const int64_t n_tiles = (int64_t)a.tiles_x * a.tiles_y, n_super = (int64_t)a.supers_x * a.supers_y;
+    const uint32_t n_units = *super_count * kCullParts;
+    for (uint32_t u = blockIdx.x; u < n_units; u += gridDim.x) {  // uniform over the CTA
+        if (!LCL_IN(u / kCullParts, n_super)) break;
+        const uint32_t sidx = supers[u / kCullParts];
+        const int32_t sx = (int32_t)(sidx % a.supers_x), sy = (int32_t)(sidx / a.supers_x);
+        const int32_t local = (int32_t)(u % kCullParts) * (kThreads / 8) + (int32_t)(threadIdx.x / 8);
         const int32_t tx = sx * LCL_SUPER + local % LCL_SUPER, ty = sy * LCL_SUPER + local / LCL_SUPER;
         const bool in_grid = tx < a.tiles_x && ty < a.tiles_y;  // uniform over each group of 8 lanes
         bool cand = false;
         int cls = kTileTest;
         // the group's 8 lanes take the same branch (in_grid and the index check are per tile)
-        if (super_in && in_grid && LCL_IN((int64_t)ty * a.tiles_x + tx, n_tiles)) {
+        if (in_grid && LCL_IN((int64_t)ty * a.tiles_x + tx, n_tiles)) {
             const int4 *tb = reinterpret_cast<const int4 *>(a.tile_box + 8 * ((int64_t)ty * a.tiles_x + tx));
             const int4 lo = tb[0], hi = tb[1];
             if (lo.w > 0) {  // uniform over the group (one tile)
-                float4 sb;
-                cand = box_may_touch8(p, lo, hi, depth, CLASSIFY ? &sb : nullptr);
-                if (CLASSIFY && cand) {
-                    cls = lasso_tile_class8<8>(p, svx, svy, sb);
-                    cand = cls != kTileOut;
-                }
+                if (CLASSIFY) cand = box_may_touch8<true>(p, lo, hi, depth, nullptr, svx, svy, &cls);
+                else cand = box_may_touch8(p, lo, hi, depth);
             }
         }
         const uint32_t tile = (uint32_t)(ty * a.tiles_x + tx);
@@ -470,22 +498,32 @@ SelWs sel_ws(const lcl_atlas *a, int32_t n, void *ws) {
 // still covers the GPU.  Returns the number of launches.
 int launch_lasso_cull(const AtlasDev &a, const lcl_atlas *atlas, const LassoArg &p, const float *depth,
                       const SelWs &w, bool pad, bool classify, cudaStream_t st) {
+    // counters[1] and list3 hold the candidate super-tiles (lassos and the tool use list and list2 only)
     const int n_super = atlas->supers_x * atlas->supers_y;
-    const int split = std::max(1, std::min(8, (4 * sm_count() + n_super - 1) / n_super));
-    const dim3 cg(atlas->supers_x, atlas->supers_y, split);
+    k_lasso_supers<<<(n_super + kThreads / 8 - 1) / (kThreads / 8), kThreads, 0, st>>>(a, p, w.counters + 1, w.list3);
+    const int grid = std::max(1, std::min(n_super * kCullParts, 8 * sm_count()));
     if (!pad) {
-        if (classify) k_lasso_cull<false, true><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list);
-        else k_lasso_cull<false, false><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list);
-        return 1;
+        if (classify)
+            k_lasso_cull<false, true><<<grid, kThreads, 0, st>>>(a, p, depth, w.counters + 1, w.list3, w.counters,
+                                                                 w.list);
+        else
+            k_lasso_cull<false, false><<<grid, kThreads, 0, st>>>(a, p, depth, w.counters + 1, w.list3, w.counters,
+                                                                  w.list);
+        return 2;
     }
     // padded edits: flags for every tile that may hold a selected texel (polygon-outside tiles of a
-    // lasso hold none), dilated to the tiles padding can reach
-    if (classify) k_lasso_cull<true, true><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list2);
-    else k_lasso_cull<true, false><<<cg, kThreads, 0, st>>>(a, p, depth, w.counters, w.list2);
+    // lasso hold none; tiles of super-tiles the lasso cannot reach keep the cleared 0), dilated to the
+    // tiles padding can reach
     const int64_t tiles = (int64_t)atlas->tiles_x * atlas->tiles_y;
+    cudaMemsetAsync(w.list2, 0, (size_t)tiles * 4, st);
+    if (classify)
+        k_lasso_cull<true, true><<<grid, kThreads, 0, st>>>(a, p, depth, w.counters + 1, w.list3, w.counters, w.list2);
+    else
+        k_lasso_cull<true, false><<<grid, kThreads, 0, st>>>(a, p, depth, w.counters + 1, w.list3, w.counters,
+                                                             w.list2);
     k_dilate_candidates<<<(unsigned)((tiles + kThreads - 1) / kThreads), kThreads, 0, st>>>(a, w.list2, w.counters,
                                                                                         w.list);
-    return 2;
+    return 3;
 }
 
 // ---- division check ----------------------------------------------------------------------
@@ -608,7 +646,7 @@ lcl_status select_sphere_run(const lcl_atlas *atlas, L *layer, uint32_t *mask, c
     int grid[2][2];
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) grid[i][j] = resident_grid(step[i][j]);
-    k_sel_init<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(w.counters, n, h);
+    k_sel_init<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(w.counters, n, h, n);
     const int n_super = atlas->supers_x * atlas->supers_y;
     cudaError_t e = launch_pdl(k_sphere_cull, dim3(std::min(n_super, grid[0][0])), st, a, arg(0), w.counters, w.list);
     for (int32_t k = 0; k < n && e == cudaSuccess; ++k) {
@@ -668,7 +706,7 @@ lcl_status lasso_run(const lcl_atlas *atlas, void *layer, int bytes, uint32_t *m
     fill_lasso_arg(p, cam, poly, nv, label, bias);
     const int32_t pad_r = (int32_t)(pad_flags & 15u), pad_t = (int32_t)((pad_flags >> 4) & 15u);
     const bool pad = pad_r > 0;
-    k_sel_init<<<1, kThreads, 0, st>>>(w.counters, 1, h);
+    k_sel_init<<<1, kThreads, 0, st>>>(w.counters, 2, h, 1);
     const int n_cull = launch_lasso_cull(a, atlas, p, depth, w, pad, true, st);
     ValMask vm;
     vm.bits = mask;
@@ -740,7 +778,7 @@ lcl_status tool_run(const lcl_atlas *atlas, void *layer, int bytes, uint32_t *ma
     static thread_local LassoArg p;  // ~2.8 KB: kept off the stack
     ToolArg t;
     fill_tool_arg(t, p, cam, tool, label, bias);
-    k_sel_init<<<1, kThreads, 0, st>>>(w.counters, 1, h);
+    k_sel_init<<<1, kThreads, 0, st>>>(w.counters, 2, h, 1);
     const bool pad = t.pad_r > 0;
     const int n_cull = launch_lasso_cull(a, atlas, p, depth, w, pad, false, st);
     const int sel = (tool->shape != nullptr ? 1 : 0) + (pad ? 2 : 0);

@@ -12,6 +12,7 @@ namespace lcl {
 
 struct AtlasDev {
     const int32_t *px, *py, *pz;
+    const uint32_t *cover;
     const int32_t *tile_box, *super_box;
     int32_t w, h, T, tiles_x, tiles_y, supers_x, supers_y;
 };
@@ -21,6 +22,7 @@ inline AtlasDev dev_view(const lcl_atlas *a) {
     d.px = a->pos_x;
     d.py = a->pos_y;
     d.pz = a->pos_z;
+    d.cover = a->cover;
     d.tile_box = a->tile_box;
     d.super_box = a->super_box;
     d.w = a->width;
@@ -324,8 +326,19 @@ __device__ inline bool box_may_touch(const LassoArg &p, int4 lo, int4 hi, const 
 // footprints of up to 2048 px scanned (1024 there) before the test gives up and keeps the box.
 // sbox (optional): the screen box {xmin, xmax, ymin, ymax} of the projected corners when every
 // corner lies in front of the camera and projects to finite coordinates, else NaNs.
+// Tile classes for a lasso (the texels of a box projected to screen box `sb`, by box_may_touch8).
+enum : int { kTileOut = 0, kTileTest = 1, kTileIn = 2 };
+
+template <int LANES>
+__device__ __forceinline__ int lasso_tile_class8(const LassoArg &p, const float *vx, const float *vy, float4 sb);
+
+// CLASSIFY (with vx, vy, *cls): between the screen-box test and the depth-footprint scan, the tile is
+// classified by lasso_tile_class8 (its class in *cls, kTileTest where it cannot be); a tile outside the
+// polygon returns false at once, without the scan.
+template <bool CLASSIFY = false>
 __device__ __forceinline__ bool box_may_touch8(const LassoArg &p, int4 lo, int4 hi, const float *__restrict__ depth,
-                                               float4 *sbox = nullptr) {
+                                               float4 *sbox = nullptr, const float *vx = nullptr,
+                                               const float *vy = nullptr, int *cls = nullptr) {
     const unsigned lane = threadIdx.x & 31u, sub = lane & 7u;
     const unsigned gm = 0xFFu << (lane & 24u);
     const float x = (float)((sub & 1u) ? hi.x : lo.x), y = (float)((sub & 2u) ? hi.y : lo.y);
@@ -349,6 +362,10 @@ __device__ __forceinline__ bool box_may_touch8(const LassoArg &p, int4 lo, int4 
     }
     if (xmax < p.bx0 || xmin > p.bx1 || ymax < p.by0 || ymin > p.by1) return false;
     if (sbox && finite) *sbox = make_float4(xmin, xmax, ymin, ymax);
+    if (CLASSIFY) {
+        *cls = finite ? lasso_tile_class8<8>(p, vx, vy, make_float4(xmin, xmax, ymin, ymax)) : kTileTest;
+        if (*cls == kTileOut) return false;  // outside the polygon: no texel can be selected
+    }
     if (!depth) return true;
     const float margin = 2.0f;
     const int ix0 = max(0, __float2int_rd(xmin - margin)), ix1 = min(p.w_s - 1, __float2int_rd(xmax + margin));
@@ -364,8 +381,6 @@ __device__ __forceinline__ bool box_may_touch8(const LassoArg &p, int4 lo, int4 
     return !(zmin - 1e-4f > dmax + p.bias);
 }
 
-// Tile classes for a lasso (the texels of a box projected to screen box `sb`, by box_may_touch8).
-enum : int { kTileOut = 0, kTileTest = 1, kTileIn = 2 };
 
 // Classifies a box whose projection lies in the screen box sb, by the aligned group of 8 lanes of
 // box_may_touch8 (all 8 call it; lane c takes edges c, c + 8, ...):
@@ -384,7 +399,7 @@ enum : int { kTileOut = 0, kTileTest = 1, kTileIn = 2 };
 // vx, vy: the polygon's vertices (vertex nv = vertex 0), staged in shared memory by the caller so
 // that the lanes' different edges are not serialised on the parameter bank.  LANES: 8 (an aligned
 // group of 8 lanes shares the work, as after box_may_touch8) or 1 (one thread does it alone).
-template <int LANES = 8>
+template <int LANES>
 __device__ __forceinline__ int lasso_tile_class8(const LassoArg &p, const float *vx, const float *vy, float4 sb) {
     const unsigned lane = threadIdx.x & 31u, sub = LANES == 8 ? (lane & 7u) : 0u;
     const unsigned gm = 0xFFu << (lane & 24u);

@@ -62,7 +62,7 @@ def test_row_rooflines_units(s):
     w = _stub_workload(s)
     n = 128 * 64
     row_ms = [2.0, 4.0, 1.0, 3.0, 0.5, 1.5]          # per row, summed over 2 steps
-    out = bench.row_rooflines(w, row_ms, 2, 1000, 300, 5000.0)
+    out = bench.row_rooflines(w, row_ms, 2, 1000 * (12 + s), 1000, 300, 5000.0)
     assert list(out) == list(bench.ROWS)
     expect = {
         "sphere": 1000 * (12 + s),
@@ -91,3 +91,38 @@ def test_all_cores_oracle_sample_equals_its_bands_run_one_by_one():
     assert bands == 3 and secs > 0
     assert texels == sum(bench.oracle_sample(w, 24, y0=24 * k)[0] for k in range(3))
     assert texels > 3 * 24 * 512 * (len(w.overlays) + w.n_layers)    # full-row passes plus some hits
+
+
+def test_sphere_inside_texels_counts_covered_texels_of_contained_tiles():
+    """bench.sphere_inside_texels: per stroke, the covered texels of the tiles whose box the sphere
+    contains (farthest corner within r), checked against a plain loop; padded strokes count 0."""
+    import numpy as np
+    import torch
+
+    import bench
+    rng = np.random.default_rng(5)
+    n_tiles = 300
+    lo = rng.integers(0, 1000, size=(n_tiles, 3))
+    hi = lo + rng.integers(0, 60, size=(n_tiles, 3))
+    cnt = rng.integers(0, 1025, size=n_tiles)
+    cnt[::7] = 0
+    tb = np.zeros((n_tiles, 8), np.int32)
+    tb[:, 0:3], tb[:, 3], tb[:, 4:7] = lo, cnt, hi
+
+    class FakeAtlas:
+        def tile_box(self):
+            return torch.from_numpy(tb)
+
+    from paper_2501_14807_gb300 import lcl
+    recs = np.zeros(40, lcl.SPHERE_DTYPE)
+    recs["cx"], recs["cy"], recs["cz"] = rng.integers(0, 1100, size=(3, 40))
+    recs["r2"] = rng.integers(0, 400 ** 2, size=40)
+    recs["flags"][5] = 0x21
+    got = bench.sphere_inside_texels(FakeAtlas(), recs, "cpu", chunk=7)
+    for k, r in enumerate(recs):
+        c = np.array([r["cx"], r["cy"], r["cz"]])
+        far = np.maximum(c - lo, hi - c)
+        exp = int(cnt[((far ** 2).sum(1) <= r["r2"]) & (cnt > 0)].sum()) if not (r["flags"] & 15) else 0
+        assert got[k] == exp
+    assert got.sum() > 0
+    assert bench.sphere_bytes(10, 4, 1) == 6 * 13 + 4 * 1.125
