@@ -523,7 +523,8 @@ def sphere_radius_breakdown(w, atlas, layers, per_layer, inside_per_layer, ws_se
     its own call (zeroing, cull and apply launches), timed with CUDA events, binned by radius in
     half-decades of the bounding-box diagonal.  Bytes are 12 + label bytes per hit texel (and, beside
     them, the bytes the kernel needs, sphere_bytes), against the measured copy peak.  Small strokes are bound by launch and cull
-    latency; the chained call of the timed region hides part of that."""
+    latency; the chained call of the timed region hides part of that.  The host queues all calls of a
+    layer behind a short device-side sleep, so the intervals are GPU time, not Python launch time."""
     import torch
     from paper_2501_14807_gb300 import lcl
 
@@ -537,6 +538,10 @@ def sphere_radius_breakdown(w, atlas, layers, per_layer, inside_per_layer, ws_se
         sel = np.nonzero(w.strokes.layer == li)[0]
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(recs) + 1)]
         hs = torch.zeros(len(recs), dtype=torch.int64, device=dev)
+        # a bounded device-side sleep (about 60 us of SM cycles per call) lets the host queue every
+        # call first, so that each interval is the GPU's time for its call, not the host's launch time
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(int(120_000 * len(recs)))
         ev[0].record(stream)
         for k in range(len(recs)):
             lcl.lcl_select_sphere(atlas, layers[li], recs[k:k + 1], hs[k:k + 1], ws_sel, stream)
@@ -560,7 +565,8 @@ def sphere_radius_breakdown(w, atlas, layers, per_layer, inside_per_layer, ws_se
                     "us_per_stroke": 1e3 * ms / len(b), "gb_s": gbs, "frac": gbs / peak,
                     "hit_texels_inside_tiles": inside,
                     "frac_of_bytes_needed": float(sphere_bytes(hit, inside, w.dtype_bytes)) / (ms / 1e3) / 1e9 / peak})
-    return {"timing": "one call per stroke (zeroing, cull, apply), CUDA events; not the chained timed call",
+    return {"timing": "one call per stroke (zeroing, cull, apply), CUDA events between calls queued ahead of the "
+                      "GPU (GPU time per call, not host launch time); not the chained timed call",
             "bins": out}
 
 

@@ -48,9 +48,13 @@ __global__ void k_sel_init(uint32_t *counters, int32_t n, unsigned long long *hi
 // With texture padding (PAD) a texel may be written because a neighbour within 8 texels was
 // selected, so a tile (super-tile) is then a candidate if any box of its 3 x 3 neighbourhood is
 // in reach.  PAD is a template parameter so that the common case carries no registers for it.
+// Tiles inside the sphere go to the back of the list (counter `inside_counter`) when whole-row
+// handling applies (`rows`: tile side >= 32 and width a multiple of 32), else to the front with
+// kInsideTile set.
 template <bool PAD>
 __device__ __forceinline__ void cull_super_sphere(const AtlasDev &a, const SphereArg &s, int32_t sidx,
-                                                  uint32_t *counter, uint32_t *list) {
+                                                  uint32_t *counter, uint32_t *list, uint32_t *inside_counter,
+                                                  bool rows) {
     const int32_t sx = sidx % a.supers_x, sy = sidx / a.supers_x;
     bool in_reach;
     if (PAD) {
@@ -78,19 +82,22 @@ __device__ __forceinline__ void cull_super_sphere(const AtlasDev &a, const Spher
             inside = cand && box_far2(lo, hi, s) <= s.r2;
         }
     }
-    append_candidate(cand, (uint32_t)(ty * a.tiles_x + tx) | (inside ? kInsideTile : 0u), counter, list, n_tiles);
+    const uint32_t tile = (uint32_t)(ty * a.tiles_x + tx);
+    append_candidate(cand && !(inside && rows), tile | (inside ? kInsideTile : 0u), counter, list, n_tiles);
+    if (!PAD) append_candidate_back(inside && rows, tile, inside_counter, list, n_tiles);
 }
 
 // Culls the first stroke of a call.
 __global__ void __launch_bounds__(kThreads) k_sphere_cull(AtlasDev a, SphereArg s, uint32_t *counter,
-                                                          uint32_t *list) {
+                                                          uint32_t *list, uint32_t *inside_counter) {
     pdl_wait();
     const int32_t n_super = a.supers_x * a.supers_y;
+    const bool rows = a.T >= 32 && (a.w & 31) == 0;
     for (int32_t sidx = blockIdx.x; sidx < n_super; sidx += gridDim.x) {
         if (s.pad_r > 0)
-            cull_super_sphere<true>(a, s, sidx, counter, list);
+            cull_super_sphere<true>(a, s, sidx, counter, list, inside_counter, rows);
         else
-            cull_super_sphere<false>(a, s, sidx, counter, list);
+            cull_super_sphere<false>(a, s, sidx, counter, list, inside_counter, rows);
     }
     pdl_allow_next();
 }
@@ -182,17 +189,23 @@ __device__ uint32_t pad_mask(const AtlasDev &a, const Item &it, const SphereArg 
 // Applies stroke `s` from its candidate list and culls stroke `nxt` (if has_next) into the other list.
 // PAD: `s` pads the texture; NEXT_PAD: `nxt` does.  NUM: a numeric layer, whose mask bits (vm) are
 // set (or cleared) for every texel written.
+// Lists: candidate tiles the sphere's surface may cross at the front (`counter` entries), tiles
+// inside the sphere at the back (`inside_counter` entries, whole-row layouts only): a warp takes one
+// such tile, each lane one 32-texel row segment, whose coverage word says which texels get the label.
 template <typename L, bool PAD, bool NEXT_PAD, bool NUM>
 __global__ void __launch_bounds__(kThreads, 6) k_sphere_step(AtlasDev a, L *__restrict__ layer, SphereArg s,
                                                           const uint32_t *__restrict__ counter,
+                                                          const uint32_t *__restrict__ inside_counter,
                                                           const uint32_t *__restrict__ list,
                                                           unsigned long long *hits, int has_next, SphereArg nxt,
-                                                          uint32_t *next_counter, uint32_t *next_list, ValMask vm) {
+                                                          uint32_t *next_counter, uint32_t *next_inside_counter,
+                                                          uint32_t *next_list, ValMask vm) {
+    const bool rows = a.T >= 32 && (a.w & 31) == 0;  // uniform
     // Cull of the next stroke: reads only the atlas boxes; its list is free (see the top of the file).
     if (has_next) {
         const int32_t n_super = a.supers_x * a.supers_y;
         for (int32_t sidx = blockIdx.x; sidx < n_super; sidx += gridDim.x)
-            cull_super_sphere<NEXT_PAD>(a, nxt, sidx, next_counter, next_list);
+            cull_super_sphere<NEXT_PAD>(a, nxt, sidx, next_counter, next_list, next_inside_counter, rows);
     }
     pdl_wait();
     pdl_allow_next();  // after the wait: grid k + 1 starts once every CTA of this grid got here
@@ -234,6 +247,34 @@ __global__ void __launch_bounds__(kThreads, 6) k_sphere_step(AtlasDev a, L *__re
             }
         }
         cur = next;
+    }
+    // tiles inside the sphere: one warp per tile, one lane per 32-texel row segment
+    const uint32_t n_in = *inside_counter;
+    if (n_in) {  // uniform
+        const int64_t cap = (int64_t)a.tiles_x * a.tiles_y;
+        const int32_t wpr = a.T >> 5, words = a.T * wpr;  // row segments per tile row and per tile
+        const uint32_t warps = gridDim.x * (kThreads / 32);
+        // from the last CTA down: when the grid has CTAs to spare, the tiles above go to the first
+        // CTAs and these to others, so that neither waits for the other
+        for (uint32_t b = (gridDim.x - 1 - blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); b < n_in; b += warps) {
+            if (!LCL_IN(cap - 1 - (int64_t)b, cap)) break;
+            const uint32_t tile = __ldg(list + (cap - 1 - (int64_t)b));
+            const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+            for (int32_t wi = threadIdx.x & 31; wi < words; wi += 32) {
+                const int32_t x = tx * a.T + 32 * (wi % wpr), y = ty * a.T + wi / wpr;
+                if (x >= a.w || y >= a.h) continue;   // x < w implies x + 31 < w (w a multiple of 32)
+                const int64_t l = (int64_t)y * a.w + x;
+                if (!LCL_IN(l + 31, n_tex)) continue;
+                const uint32_t cov = __ldg(a.cover + (l >> 5));
+                if (!cov) continue;
+                store_word32<L>(layer, l, cov, s.label);
+                if (NUM) {  // the row segment's mask word belongs to this lane alone
+                    uint32_t *mp = vm.bits + (l >> 5);
+                    *mp = vm.set ? (*mp | cov) : (*mp & ~cov);
+                }
+                cnt += __popc(cov);
+            }
+        }
     }
     add_hits(hits, cnt);
 }
@@ -486,8 +527,8 @@ SelWs sel_ws(const lcl_atlas *a, int32_t n, void *ws) {
     SelWs w;
     char *base = static_cast<char *>(ws);
     const size_t lb = align256((size_t)a->tiles_x * a->tiles_y * 4);
-    w.counters = reinterpret_cast<uint32_t *>(base);
-    w.list = reinterpret_cast<uint32_t *>(base + align256((size_t)(n + 1) * 4));
+    w.counters = reinterpret_cast<uint32_t *>(base);  // n + 1 front counters, then n + 1 inside counters
+    w.list = reinterpret_cast<uint32_t *>(base + align256((size_t)2 * (n + 1) * 4));
     w.list2 = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(w.list) + lb);
     w.list3 = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(w.list2) + lb);
     return w;
@@ -608,12 +649,12 @@ lcl_status division_check_impl(uint64_t n, uint32_t seed, uint64_t *counts, cuda
 }
 
 size_t select_ws_bytes(const lcl_atlas *a, int32_t n) {
-    return align256((size_t)(n + 1) * 4) + 3 * align256((size_t)a->tiles_x * a->tiles_y * 4);
+    return align256((size_t)2 * (n + 1) * 4) + 3 * align256((size_t)a->tiles_x * a->tiles_y * 4);
 }
 
 template <typename L>
-using StepKernel = void (*)(AtlasDev, L *, SphereArg, const uint32_t *, const uint32_t *, unsigned long long *, int,
-                            SphereArg, uint32_t *, uint32_t *, ValMask);
+using StepKernel = void (*)(AtlasDev, L *, SphereArg, const uint32_t *, const uint32_t *, const uint32_t *,
+                            unsigned long long *, int, SphereArg, uint32_t *, uint32_t *, uint32_t *, ValMask);
 
 // Sphere strokes on a label layer (NUM false) or on the data texture of a numeric layer whose mask
 // bits are `mask` (NUM true; an erase stroke writes 0 and clears the bits).
@@ -646,9 +687,11 @@ lcl_status select_sphere_run(const lcl_atlas *atlas, L *layer, uint32_t *mask, c
     int grid[2][2];
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) grid[i][j] = resident_grid(step[i][j]);
-    k_sel_init<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(w.counters, n, h, n);
+    uint32_t *const inside = w.counters + (n + 1);
+    k_sel_init<<<(2 * (n + 1) + kThreads - 1) / kThreads, kThreads, 0, st>>>(w.counters, 2 * (n + 1), h, n);
     const int n_super = atlas->supers_x * atlas->supers_y;
-    cudaError_t e = launch_pdl(k_sphere_cull, dim3(std::min(n_super, grid[0][0])), st, a, arg(0), w.counters, w.list);
+    cudaError_t e = launch_pdl(k_sphere_cull, dim3(std::min(n_super, grid[0][0])), st, a, arg(0), w.counters, w.list,
+                               inside);
     for (int32_t k = 0; k < n && e == cudaSuccess; ++k) {
         uint32_t *const lists[3] = {w.list, w.list2, w.list3};
         uint32_t *cur_list = lists[k % 3], *next_list = lists[(k + 1) % 3];
@@ -656,8 +699,8 @@ lcl_status select_sphere_run(const lcl_atlas *atlas, L *layer, uint32_t *mask, c
         const SphereArg cur = arg(k), nxt = arg(has_next ? k + 1 : k);
         const int pi = cur.pad_r > 0, pj = has_next && nxt.pad_r > 0;
         e = launch_pdl(step[pi][pj], dim3(grid[pi][pj]), st, a, layer, cur, (const uint32_t *)(w.counters + k),
-                       (const uint32_t *)cur_list, h ? h + k : nullptr, has_next, nxt, w.counters + k + 1, next_list,
-                       vmask(k));
+                       (const uint32_t *)(inside + k), (const uint32_t *)cur_list, h ? h + k : nullptr, has_next, nxt,
+                       w.counters + k + 1, inside + k + 1, next_list, vmask(k));
     }
     count_launches(2 + n);
     if (e == cudaSuccess) e = cudaGetLastError();

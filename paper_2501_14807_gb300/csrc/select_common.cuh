@@ -90,6 +90,49 @@ __device__ __forceinline__ void append_candidate(bool cand, uint32_t tile, uint3
 }
 
 
+// Appends this lane's tile to the back of the list (slots cap - 1, cap - 2, ... counted by `counter`)
+// if `cand`; one atomic per warp.  A list filled from both ends holds at most cap entries in all.
+__device__ __forceinline__ void append_candidate_back(bool cand, uint32_t tile, uint32_t *counter, uint32_t *list,
+                                                      int64_t cap) {
+    uint32_t m = __ballot_sync(0xffffffffu, cand);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(counter, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    const int64_t slot = cap - 1 - (int64_t)(base + __popc(m & ((1u << lane) - 1)));
+    if (cand && LCL_IN(slot, cap)) list[slot] = tile;
+}
+
+// Writes `label` into the covered texels (bits of `cov`) of the 32 texels starting at l (l a
+// multiple of 32, the layer 16-byte aligned): 16-byte stores, read first only where some texel of
+// the 16 bytes is not written.
+template <typename L>
+__device__ __forceinline__ void store_word32(L *layer, int64_t l, uint32_t cov, uint32_t label) {
+    constexpr int kPer = 16 / (int)sizeof(L);  // texels per 16-byte store
+    const uint32_t rep = sizeof(L) == 1 ? label * 0x01010101u : sizeof(L) == 2 ? label * 0x00010001u : label;
+    uint4 *p = reinterpret_cast<uint4 *>(layer + l);
+#pragma unroll
+    for (int g = 0; g < 32 / kPer; ++g) {
+        const uint32_t bits = (cov >> (g * kPer)) & (kPer == 32 ? 0xFFFFFFFFu : ((1u << kPer) - 1u));
+        if (!bits) continue;
+        if (bits == ((1u << kPer) - 1u)) {
+            p[g] = make_uint4(rep, rep, rep, rep);
+            continue;
+        }
+        uint32_t wm[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (sizeof(L) == 1) wm[j] = (((bits >> (4 * j)) & 0xFu) * 0x00204081u & 0x01010101u) * 0xFFu;
+            else if (sizeof(L) == 2) wm[j] = (((bits >> (2 * j)) & 1u) ? 0x0000FFFFu : 0u) | (((bits >> (2 * j)) & 2u) ? 0xFFFF0000u : 0u);
+            else wm[j] = ((bits >> j) & 1u) ? 0xFFFFFFFFu : 0u;
+        }
+        const uint4 o = p[g];
+        p[g] = make_uint4((o.x & ~wm[0]) | (rep & wm[0]), (o.y & ~wm[1]) | (rep & wm[1]), (o.z & ~wm[2]) | (rep & wm[2]),
+                          (o.w & ~wm[3]) | (rep & wm[3]));
+    }
+}
+
 // Programmatic dependent launch: wait for the previous grid on the stream to complete (its
 // memory is then visible); let the next grid be scheduled.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }

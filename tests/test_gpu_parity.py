@@ -74,6 +74,10 @@ SPHERE_CASES = [
     ("charts-u8-t64", lambda: synth.vessel_charts(200, 100, 25, 10, 512, seed=5), 512, 512, 64, np.uint8, 80,
      0.001, 0.3),
     ("t128-u16", lambda: synth.vessel_cylindrical(50, 30, seed=2), 384, 256, 128, np.uint16, 40, 0.05, 0.6),
+    # tiles inside big spheres: whole-row handling (W a multiple of 32) and per-quad handling (not)
+    ("t32-big-u16", lambda: synth.vessel_charts(160, 80, 20, 10, 1024, seed=6), 1024, 512, 32, np.uint16, 40,
+     0.1, 0.6),
+    ("t32-odd-width-u8", lambda: synth.vessel_cylindrical(60, 30, seed=6), 1000, 600, 32, np.uint8, 40, 0.05, 0.5),
 ]
 
 
