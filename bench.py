@@ -288,6 +288,10 @@ def run_ours(args):
                          device=dev)
     sphere_hits = [torch.zeros(max(len(r), 1), dtype=torch.int64, device=dev) for r in per_layer]
     inside_per_layer = [sphere_inside_texels(atlas, r, dev) for r in per_layer]
+    # every layer's strokes are one call of >= 2 unpadded strokes: the grouped path
+    grouped = [sphere_group_bytes(atlas, r, dev, w.dtype_bytes) for r in per_layer]
+    assert all(len(r) >= 2 and not (r["flags"] & 15).any() for r in per_layer)
+    torch.cuda.empty_cache()
     cams = [lcl.lcl_camera_from_vp(atlas, c.vp, c.width, c.height) for c in w.cams]
     depths = [torch.empty((c.height, c.width), dtype=torch.float32, device=dev) for c in w.cams]
     ws_depth = torch.empty(max([lcl.lcl_depth_workspace_bytes(mesh, c.width, c.height) for c in w.cams] + [256]),
@@ -409,7 +413,8 @@ def run_ours(args):
     peak, peak_kind = peaks()
     sph_inside = int(sum(int(x.sum()) for x in inside_per_layer))
     sph_bytes = sph_hits * (12 + w.dtype_bytes)          # the per-unit bytes of the hot-path scope: 12 B + label
-    sph_needed = float(sphere_bytes(sph_hits, sph_inside, w.dtype_bytes))
+    n_groups = sum(g for _, g in grouped)
+    grp_bytes = sum(b for b, _ in grouped)
     achieved = sph_bytes / (sph_ms / args.steps / 1e3) / 1e9
     value = all_texels * args.steps / (total_ms / 1e3) / 1e9
     traffic = profile_traffic(w)
@@ -423,15 +428,22 @@ def run_ours(args):
                                     "all-reduce per step)") if world > 1 else "1 GPU, the whole texture"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic,
-                     "kernel": "sphere edit (k_sphere_step, one launch per stroke)",
-                     "algorithmic_bytes_per_launch": sph_bytes / max(n_strokes, 1),
-                     "bytes_model": "12 B position + label per selected texel (the scope's per-unit bytes); the "
-                                    "kernel reads positions only for tiles the sphere's surface crosses and the "
-                                    "coverage bits (1/8 B per texel) for tiles inside the sphere",
+                     "kernel": f"sphere edit, grouped: k_group_cull + k_group_apply per {SPHERE_GROUP} consecutive "
+                               "strokes of a call (a launch = one group), timed over the whole sphere row",
+                     "algorithmic_bytes_per_launch": sph_bytes / max(n_groups, 1),
+                     "bytes_model": "12 B position + label per selected texel, summed over the strokes (the scope's "
+                                    "per-unit bytes).  The grouped apply reads a tile's positions once per group "
+                                    "(and none for tiles every stroke of the group contains: coverage bits only) "
+                                    "and writes each texel once per group, so this sum exceeds the bytes moved "
+                                    "and the fraction can exceed 1",
                      "hit_texels": sph_hits, "hit_texels_inside_tiles": sph_inside,
-                     "bytes_needed_per_launch": sph_needed / max(n_strokes, 1),
-                     "frac_of_bytes_needed": sph_needed / (sph_ms / args.steps / 1e3) / 1e9 / peak,
-                     "ms_per_launch": sph_ms / args.steps / max(n_strokes, 1)},
+                     "strokes": n_strokes, "launches": n_groups,
+                     "group_bytes_per_launch": grp_bytes / max(n_groups, 1),
+                     "group_bytes_model": "per group: label bytes x covered texels of every tile a stroke reaches, "
+                                          "+ 12 B x covered texels of tiles a sphere surface crosses, + 1/8 B x "
+                                          "covered texels of tiles only contained (sphere_group_bytes)",
+                     "frac_of_group_bytes": grp_bytes / (sph_ms / args.steps / 1e3) / 1e9 / peak,
+                     "ms_per_launch": sph_ms / args.steps / max(n_groups, 1)},
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,
         "e2e": {"value": all_texels * args.steps / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
@@ -443,8 +455,8 @@ def run_ours(args):
         "breakdown": {"sphere_ms_per_step": sph_ms / args.steps, "sphere_hit_texels": sph_hits,
                       "lasso_hit_texels": las_hits, "texels_per_step": texels},
         "rows": row_rooflines(w, row_ms, args.steps, sph_bytes, sph_hits, las_hits, peak),
-        "sphere_bytes_needed": {"inside_tile_texels": sph_inside, "bytes": sph_needed,
-                                "gb_s": sph_needed / (sph_ms / args.steps / 1e3) / 1e9},
+        "sphere_group_bytes": {"groups": n_groups, "bytes": grp_bytes,
+                               "gb_s": grp_bytes / (sph_ms / args.steps / 1e3) / 1e9},
         "sphere_by_radius": by_radius,
     }
     print(json.dumps(line), flush=True)
@@ -473,6 +485,36 @@ def sphere_inside_texels(atlas, records, dev, chunk=16):
         n[(r["flags"] & 15) != 0] = 0
         out[k0:k0 + len(r)] = n
     return out
+
+
+SPHERE_GROUP = 32  # strokes per grouped launch pair of the library (k_group_cull + k_group_apply)
+
+
+def sphere_group_bytes(atlas, records, dev, label_bytes, group=SPHERE_GROUP):
+    """Bytes the grouped sphere apply moves at tile granularity for one call applying `records` (the
+    library applies a call of two or more unpadded strokes on a label layer `group` strokes per
+    launch): per group, every tile that some stroke of the group reaches costs its covered texels'
+    labels; a tile that some stroke's surface crosses also costs their 12-byte positions, a tile that
+    every stroke reaching it contains only their coverage bits.  Tile boxes against the strokes on
+    the device, one group at a time.  Returns (bytes, groups)."""
+    import torch
+    tb = atlas.tile_box().to(torch.int64)
+    lo, cnt, hi = tb[:, 0:3], tb[:, 3], tb[:, 4:7]
+    cov = cnt > 0
+    total, groups = 0.0, 0
+    for g0 in range(0, len(records), group):
+        r = records[g0:g0 + group]
+        c = torch.tensor(np.stack([r["cx"], r["cy"], r["cz"]], 1).astype(np.int64), device=dev)[:, None, :]
+        r2 = torch.tensor(np.minimum(r["r2"].astype(np.int64), 1 << 50), device=dev)[:, None]
+        near = torch.clamp(torch.maximum(lo[None] - c, c - hi[None]), min=0)
+        reach = ((near * near).sum(-1) <= r2) & cov[None]
+        far = torch.maximum(c - lo[None], hi[None] - c)
+        sure = ((far * far).sum(-1) <= r2) & reach
+        any_r, cross = reach.any(0), (reach & ~sure).any(0)
+        total += float((cnt * any_r).sum()) * label_bytes + float((cnt * cross).sum()) * 12 + \
+            float((cnt * (any_r & ~cross)).sum()) / 8
+        groups += 1
+    return total, groups
 
 
 def sphere_bytes(hits, inside, label_bytes):
@@ -1088,10 +1130,10 @@ def run_serve(args):
 
 
 def profile_traffic(w):
-    """DRAM bytes per sphere-edit launch from the committed ncu summary, if it was taken on the
-    current kernel source (null otherwise)."""
+    """DRAM bytes per grouped sphere-edit launch (one group's cull and apply) from the committed ncu
+    summary, if it was taken on the current kernel source (null otherwise)."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "sphere_edit_traffic.json")
+    p = os.path.join(ROOT, "profiles", "sphere_group_traffic.json")
     src = os.path.join(ROOT, "paper_2501_14807_gb300", "csrc", "select.cu")
     if not os.path.exists(p):
         return None

@@ -37,9 +37,9 @@ namespace {
 
 // Zeroes n counters and the first n_hits of `hits` (nullable).
 __global__ void k_sel_init(uint32_t *counters, int32_t n, unsigned long long *hits, int32_t n_hits) {
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        if (!LCL_IN(i, n)) break;
-        counters[i] = 0;
+    const int32_t end = max(n, hits ? n_hits : 0);
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < end; i += gridDim.x * blockDim.x) {
+        if (i < n && LCL_IN(i, n)) counters[i] = 0;
         if (hits && i < n_hits) hits[i] = 0;
     }
 }
@@ -279,6 +279,233 @@ __global__ void __launch_bounds__(kThreads, 6) k_sphere_step(AtlasDev a, L *__re
     add_hits(hits, cnt);
 }
 
+// ---- grouped sphere strokes ----------------------------------------------------------------
+//
+// A run of up to kGroup consecutive unpadded strokes on a label layer is applied by one cull and one
+// apply launch instead of one launch per stroke.  Applying strokes one by one leaves each texel with
+// the label of the newest stroke that selects it (older labels are overwritten), so the apply walks a
+// texel's strokes from the newest down and writes it once; every stroke is still evaluated for its
+// hit count, which does not depend on the order.  Items are (tile, mask, sure): `mask` holds the
+// group's strokes whose sphere reaches the tile's box (bit k = stroke k of the group), `sure` those
+// of them whose sphere contains the box, so that every covered texel of the tile is selected.  Tiles
+// whose strokes are all sure need no positions: with whole-row layouts they go to the back of the
+// lists and a warp writes them from the coverage bits, one lane per 32-texel row segment.
+
+constexpr int kGroup = 32;
+
+struct GroupArg {
+    int32_t n;     // strokes in the group (<= kGroup)
+    int32_t rows;  // whole-row handling of all-sure tiles (tile side >= 32, width a multiple of 32)
+    SphereArg s[kGroup];
+};
+
+// The three lists hold an item's tile, mask and sure at the same index; front items from index 0
+// (count counters[0]), all-sure items from the last index down (count counters[1]).
+__device__ __forceinline__ void append_item(bool front, bool back, uint32_t tile, uint32_t mask, uint32_t sure,
+                                            uint32_t *counters, uint32_t *tiles, uint32_t *masks, uint32_t *sures,
+                                            int64_t cap) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t fm = __ballot_sync(0xffffffffu, front), bm = __ballot_sync(0xffffffffu, back);
+    uint32_t fb = 0, bb = 0;
+    if (fm && lane == __ffs(fm) - 1) fb = atomicAdd(counters, (uint32_t)__popc(fm));
+    if (bm && lane == __ffs(bm) - 1) bb = atomicAdd(counters + 1, (uint32_t)__popc(bm));
+    if (fm) fb = __shfl_sync(0xffffffffu, fb, __ffs(fm) - 1);
+    if (bm) bb = __shfl_sync(0xffffffffu, bb, __ffs(bm) - 1);
+    int64_t slot = -1;
+    if (front) slot = fb + __popc(fm & ((1u << lane) - 1));
+    if (back) slot = cap - 1 - (int64_t)(bb + __popc(bm & ((1u << lane) - 1)));
+    if ((front || back) && LCL_IN(slot, cap)) {
+        tiles[slot] = tile;
+        masks[slot] = mask;
+        sures[slot] = sure;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_group_cull(AtlasDev a, const __grid_constant__ GroupArg g,
+                                                         uint32_t *counters, uint32_t *tiles, uint32_t *masks,
+                                                         uint32_t *sures) {
+    pdl_wait();  // the previous group's apply has read the lists
+    __shared__ uint32_t s_mask;
+    const int32_t n_super = a.supers_x * a.supers_y;
+    const int64_t n_tiles = (int64_t)a.tiles_x * a.tiles_y;
+    for (int32_t sidx = blockIdx.x; sidx < n_super; sidx += gridDim.x) {
+        if (threadIdx.x == 0) s_mask = 0u;
+        __syncthreads();
+        if ((int)threadIdx.x < g.n && LCL_IN(sidx, (int64_t)n_super)) {  // one thread per stroke
+            const int4 *sb = reinterpret_cast<const int4 *>(a.super_box + 8 * (int64_t)sidx);
+            const int4 slo = sb[0], shi = sb[1];
+            const SphereArg &sp = g.s[threadIdx.x];
+            if (slo.w > 0 && box_dist2(slo, shi, sp) <= sp.r2) atomicOr(&s_mask, 1u << threadIdx.x);
+        }
+        __syncthreads();
+        const uint32_t smask = s_mask;
+        __syncthreads();
+        if (!smask) continue;  // uniform over the CTA
+        const int32_t sx = sidx % a.supers_x, sy = sidx / a.supers_x;
+        const int32_t tx = sx * LCL_SUPER + (threadIdx.x % LCL_SUPER);
+        const int32_t ty = sy * LCL_SUPER + (threadIdx.x / LCL_SUPER);
+        const int64_t tile = (int64_t)ty * a.tiles_x + tx;
+        uint32_t mask = 0u, sure = 0u;
+        if (tx < a.tiles_x && ty < a.tiles_y && LCL_IN(tile, n_tiles)) {
+            const int4 *tb = reinterpret_cast<const int4 *>(a.tile_box + 8 * tile);
+            const int4 lo = tb[0], hi = tb[1];
+            if (lo.w > 0) {
+                for (uint32_t m = smask; m; m &= m - 1) {
+                    const int k = __ffs(m) - 1;
+                    const SphereArg &sp = g.s[k];
+                    if (box_dist2(lo, hi, sp) > sp.r2) continue;
+                    mask |= 1u << k;
+                    if (box_far2(lo, hi, sp) <= sp.r2) sure |= 1u << k;
+                }
+            }
+        }
+        const bool back = g.rows && mask != 0u && mask == sure;
+        append_item(mask != 0u && !back, back, (uint32_t)tile, mask, sure, counters, tiles, masks, sures, n_tiles);
+    }
+    pdl_allow_next();
+}
+
+// A front item's quad for this thread: the item's masks, the quad's coverage and, when some stroke
+// of the item is not sure, its positions.
+struct GItem {
+    int64_t l;  // -1: no quad for this thread (the masks are still the item's)
+    uint32_t mask, sure, cov;
+    int4 X, Y, Z;
+};
+
+__device__ __forceinline__ GItem load_gitem(const AtlasDev &a, const uint32_t *__restrict__ tiles,
+                                            const uint32_t *__restrict__ masks, const uint32_t *__restrict__ sures,
+                                            uint32_t item, int cpt_log2, int32_t qpr, int32_t nq) {
+    GItem it;
+    it.l = -1;
+    it.mask = it.sure = it.cov = 0u;
+    const int64_t n_tiles = (int64_t)a.tiles_x * a.tiles_y;
+    (void)n_tiles;
+    const uint32_t idx = item >> cpt_log2;
+    if (!LCL_IN(idx, n_tiles)) return it;
+    const uint32_t tile = __ldg(tiles + idx);
+    it.mask = __ldg(masks + idx);
+    it.sure = __ldg(sures + idx);
+    const int32_t qd = (int32_t)((item & ((1u << cpt_log2) - 1)) * kThreads + threadIdx.x);
+    const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
+    const int64_t n_tex = (int64_t)a.w * a.h;
+    (void)n_tex;
+    if (qd < nq && x < a.w && y < a.h && LCL_IN((int64_t)y * a.w + x + 3, n_tex)) {
+        it.l = (int64_t)y * a.w + x;
+        if (it.mask & ~it.sure) {  // uniform over the item
+            it.X = __ldg(reinterpret_cast<const int4 *>(a.px + it.l));
+            it.Y = __ldg(reinterpret_cast<const int4 *>(a.py + it.l));
+            it.Z = __ldg(reinterpret_cast<const int4 *>(a.pz + it.l));
+            it.cov = (it.X.x != INT32_MIN ? 1u : 0u) | (it.X.y != INT32_MIN ? 2u : 0u) |
+                     (it.X.z != INT32_MIN ? 4u : 0u) | (it.X.w != INT32_MIN ? 8u : 0u);
+        } else if (LCL_IN(it.l >> 5, (n_tex + 31) >> 5)) {
+            it.cov = (__ldg(a.cover + (it.l >> 5)) >> (it.l & 31)) & 0xFu;
+        }
+    }
+    return it;
+}
+
+template <typename L>
+__global__ void __launch_bounds__(kThreads, 4) k_group_apply(AtlasDev a, L *__restrict__ layer,
+                                                             const __grid_constant__ GroupArg g,
+                                                             const uint32_t *__restrict__ counters,
+                                                             const uint32_t *__restrict__ tiles,
+                                                             const uint32_t *__restrict__ masks,
+                                                             const uint32_t *__restrict__ sures,
+                                                             unsigned long long *hits) {
+    __shared__ unsigned long long s_hits[kGroup];
+    if (threadIdx.x < kGroup) s_hits[threadIdx.x] = 0ull;
+    __syncthreads();
+    pdl_wait();
+    pdl_allow_next();
+    const int lane = threadIdx.x & 31;
+    const int64_t n_tex = (int64_t)a.w * a.h;
+    (void)n_tex;
+    // front items: a CTA per tile (or 256-quad chunk of one), a thread per quad
+    const int32_t qpr = a.T / 4, nq = a.T * qpr;
+    const int cpt_log2 = nq > kThreads ? 31 - __clz(nq / kThreads) : 0;
+    const uint32_t n_items = counters[0] << cpt_log2;
+    uint32_t item = blockIdx.x;
+    GItem cur;
+    cur.l = -1;
+    if (item < n_items) cur = load_gitem(a, tiles, masks, sures, item, cpt_log2, qpr, nq);
+    for (; item < n_items; item += gridDim.x) {
+        const uint32_t after = item + gridDim.x;
+        GItem next;
+        next.l = -1;
+        if (after < n_items) next = load_gitem(a, tiles, masks, sures, after, cpt_log2, qpr, nq);
+        const int32_t xs[4] = {cur.X.x, cur.X.y, cur.X.z, cur.X.w}, ys[4] = {cur.Y.x, cur.Y.y, cur.Y.z, cur.Y.w},
+                      zs[4] = {cur.Z.x, cur.Z.y, cur.Z.z, cur.Z.w};
+        uint32_t open = cur.l >= 0 ? cur.cov : 0u;
+        uint32_t lab[4] = {0u, 0u, 0u, 0u};
+        for (uint32_t m = cur.mask; m;) {  // uniform over the CTA: newest stroke first
+            const int k = 31 - __clz(m);
+            m &= ~(1u << k);
+            const SphereArg &sp = g.s[k];
+            uint32_t sel = 0u;
+            if ((cur.sure >> k) & 1u) {
+                sel = cur.l >= 0 ? cur.cov : 0u;
+            } else if (cur.l >= 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {  // uncovered texels (x = INT32_MIN) are never within r2
+                    const int64_t dx = (int64_t)xs[q] - sp.cx, dy = (int64_t)ys[q] - sp.cy, dz = (int64_t)zs[q] - sp.cz;
+                    sel |= (dx * dx + dy * dy + dz * dz <= sp.r2 ? 1u : 0u) << q;
+                }
+            }
+            if (hits) {
+                const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(sel));
+                if (lane == 0 && c) atomicAdd(&s_hits[k], (unsigned long long)c);
+            }
+            const uint32_t nw = sel & open;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (nw & (1u << q)) lab[q] = sp.label;
+            open &= ~sel;
+            if (!hits && !open) break;  // no counts wanted: the quad's labels are final
+        }
+        const uint32_t written = cur.l >= 0 ? (cur.cov & ~open) : 0u;
+        if (written && LCL_IN(cur.l + 3, n_tex)) store_labels<L>(layer, cur.l, written, lab);
+        cur = next;
+    }
+    // all-sure items (whole-row layouts): a warp per tile from the far end of the grid, one lane per
+    // 32-texel row segment; the newest stroke's label goes to every covered texel
+    const uint32_t n_back = counters[1];
+    if (n_back) {  // uniform
+        const int64_t cap = (int64_t)a.tiles_x * a.tiles_y;
+        const int32_t wpr = a.T >> 5, words = a.T * wpr;
+        const uint32_t warps = gridDim.x * (kThreads / 32);
+        for (uint32_t b = (gridDim.x - 1 - blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); b < n_back; b += warps) {
+            const int64_t idx = cap - 1 - (int64_t)b;
+            if (!LCL_IN(idx, cap)) break;
+            const uint32_t tile = __ldg(tiles + idx), mask = __ldg(masks + idx);
+            if (!mask) continue;  // uniform over the warp
+            const uint32_t label = g.s[31 - __clz(mask)].label;
+            const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+            uint32_t c = 0u;
+            for (int32_t wi = lane; wi < words; wi += 32) {
+                const int32_t x = tx * a.T + 32 * (wi % wpr), y = ty * a.T + wi / wpr;
+                if (x >= a.w || y >= a.h) continue;  // x < w implies x + 31 < w (w a multiple of 32)
+                const int64_t l = (int64_t)y * a.w + x;
+                if (!LCL_IN(l + 31, n_tex)) continue;
+                const uint32_t cov = __ldg(a.cover + (l >> 5));
+                if (!cov) continue;
+                store_word32<L>(layer, l, cov, label);
+                c += __popc(cov);
+            }
+            if (hits) {
+                c = __reduce_add_sync(0xffffffffu, c);
+                if (lane == 0 && c)
+                    for (uint32_t m = mask; m; m &= m - 1) atomicAdd(&s_hits[__ffs(m) - 1], (unsigned long long)c);
+            }
+        }
+    }
+    if (hits) {
+        __syncthreads();
+        if ((int)threadIdx.x < g.n && s_hits[threadIdx.x]) atomicAdd(hits + threadIdx.x, s_hits[threadIdx.x]);
+    }
+}
+
 // ---- lasso ---------------------------------------------------------------------------
 
 // Super-tiles a lasso (or tool window) can touch: 8 lanes per super-tile (box_may_touch8 without
@@ -320,6 +547,7 @@ __global__ void __launch_bounds__(kThreads) k_lasso_cull(AtlasDev a, const __gri
         __syncthreads();
     }
     const int64_t n_tiles = (int64_t)a.tiles_x * a.tiles_y, n_super = (int64_t)a.supers_x * a.supers_y;
+    (void)n_super;
     const uint32_t n_units = *super_count * kCullParts;
     for (uint32_t u = blockIdx.x; u < n_units; u += gridDim.x) {  // uniform over the CTA
         if (!LCL_IN(u / kCullParts, n_super)) break;
@@ -652,6 +880,37 @@ size_t select_ws_bytes(const lcl_atlas *a, int32_t n) {
     return align256((size_t)2 * (n + 1) * 4) + 3 * align256((size_t)a->tiles_x * a->tiles_y * 4);
 }
 
+// Unpadded strokes on a label layer, kGroup at a time (see k_group_apply): zeroing, then a cull and
+// an apply launch per group, chained with programmatic dependent launch.
+template <typename L, typename ArgOf>
+lcl_status select_sphere_grouped(const lcl_atlas *atlas, const AtlasDev &a, L *layer, const SelWs &w, int32_t n,
+                                 unsigned long long *h, const ArgOf &arg, cudaStream_t st) {
+    const int32_t n_groups = (n + kGroup - 1) / kGroup;
+    k_sel_init<<<(std::max(2 * n_groups, n) + kThreads - 1) / kThreads, kThreads, 0, st>>>(w.counters, 2 * n_groups,
+                                                                                          h, n);
+    static thread_local GroupArg g;  // ~1.5 KB: kept off the stack
+    g.rows = (a.T >= 32 && (a.w & 31) == 0) ? 1 : 0;
+    const int n_super = atlas->supers_x * atlas->supers_y;
+    const int cull_grid = std::min(n_super, resident_grid(k_group_cull));
+    const int apply_grid = resident_grid(k_group_apply<L>);
+    cudaError_t e = cudaSuccess;
+    for (int32_t gi = 0; gi < n_groups && e == cudaSuccess; ++gi) {
+        const int32_t k0 = gi * kGroup;
+        g.n = std::min(kGroup, n - k0);
+        for (int32_t k = 0; k < g.n; ++k) g.s[k] = arg(k0 + k);
+        uint32_t *const c = w.counters + 2 * gi;
+        e = launch_pdl(k_group_cull, dim3(cull_grid), st, a, g, c, w.list, w.list2, w.list3);
+        if (e == cudaSuccess)
+            e = launch_pdl(k_group_apply<L>, dim3(apply_grid), st, a, layer, g, (const uint32_t *)c,
+                           (const uint32_t *)w.list, (const uint32_t *)w.list2, (const uint32_t *)w.list3,
+                           h ? h + k0 : nullptr);
+    }
+    count_launches(1 + 2 * n_groups);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "lcl_select_sphere launch");
+    return LCL_OK;
+}
+
 template <typename L>
 using StepKernel = void (*)(AtlasDev, L *, SphereArg, const uint32_t *, const uint32_t *, const uint32_t *,
                             unsigned long long *, int, SphereArg, uint32_t *, uint32_t *, uint32_t *, ValMask);
@@ -681,6 +940,11 @@ lcl_status select_sphere_run(const lcl_atlas *atlas, L *layer, uint32_t *mask, c
         vm.set = (strokes[k].flags & LCL_ERASE) ? 0u : 1u;
         return vm;
     };
+    if constexpr (!NUM) {
+        bool padded = false;
+        for (int32_t k = 0; k < n; ++k) padded = padded || (strokes[k].flags & 15u) != 0;
+        if (n >= 2 && !padded) return select_sphere_grouped(atlas, a, layer, w, n, h, arg, st);
+    }
     // [pad][next_pad] variants and their resident grids
     const StepKernel<L> step[2][2] = {{k_sphere_step<L, false, false, NUM>, k_sphere_step<L, false, true, NUM>},
                                       {k_sphere_step<L, true, false, NUM>, k_sphere_step<L, true, true, NUM>}};

@@ -90,6 +90,36 @@ __device__ __forceinline__ void append_candidate(bool cand, uint32_t tile, uint3
 }
 
 
+// Writes per-texel labels lab[k] into the texels of a quad whose bit is set in m (m != 0).
+template <typename L>
+__device__ __forceinline__ void store_labels(L *layer, int64_t l, uint32_t m, const uint32_t lab[4]);
+
+template <>
+__device__ __forceinline__ void store_labels<uint8_t>(uint8_t *layer, int64_t l, uint32_t m, const uint32_t lab[4]) {
+    uint32_t *p = reinterpret_cast<uint32_t *>(layer + l);
+    const uint32_t v = (lab[0] & 0xFFu) | ((lab[1] & 0xFFu) << 8) | ((lab[2] & 0xFFu) << 16) | ((lab[3] & 0xFFu) << 24);
+    if (m == 0xFu) {
+        *p = v;
+        return;
+    }
+    const uint32_t bm = ((m * 0x00204081u) & 0x01010101u) * 0xFFu;
+    *p = (*p & ~bm) | (v & bm);
+}
+
+template <>
+__device__ __forceinline__ void store_labels<uint16_t>(uint16_t *layer, int64_t l, uint32_t m, const uint32_t lab[4]) {
+    uint2 *p = reinterpret_cast<uint2 *>(layer + l);
+    const uint32_t v0 = (lab[0] & 0xFFFFu) | (lab[1] << 16), v1 = (lab[2] & 0xFFFFu) | (lab[3] << 16);
+    if (m == 0xFu) {
+        *p = make_uint2(v0, v1);
+        return;
+    }
+    const uint2 o = *p;
+    const uint32_t lo = ((m & 1u) ? 0x0000FFFFu : 0u) | ((m & 2u) ? 0xFFFF0000u : 0u);
+    const uint32_t hi = ((m & 4u) ? 0x0000FFFFu : 0u) | ((m & 8u) ? 0xFFFF0000u : 0u);
+    *p = make_uint2((o.x & ~lo) | (v0 & lo), (o.y & ~hi) | (v1 & hi));
+}
+
 // Appends this lane's tile to the back of the list (slots cap - 1, cap - 2, ... counted by `counter`)
 // if `cand`; one atomic per warp.  A list filled from both ends holds at most cap entries in all.
 __device__ __forceinline__ void append_candidate_back(bool cand, uint32_t tile, uint32_t *counter, uint32_t *list,

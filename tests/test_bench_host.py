@@ -126,3 +126,49 @@ def test_sphere_inside_texels_counts_covered_texels_of_contained_tiles():
         assert got[k] == exp
     assert got.sum() > 0
     assert bench.sphere_bytes(10, 4, 1) == 6 * 13 + 4 * 1.125
+
+
+def test_sphere_group_bytes_against_a_plain_loop():
+    """bench.sphere_group_bytes: per group of strokes, tiles reached by some stroke cost label bytes per
+    covered texel, tiles some stroke's surface crosses 12 B more, tiles only contained 1/8 B more;
+    checked against a plain per-tile loop."""
+    import numpy as np
+    import torch
+
+    import bench
+    rng = np.random.default_rng(8)
+    n_tiles = 200
+    lo = rng.integers(0, 1000, size=(n_tiles, 3))
+    hi = lo + rng.integers(0, 80, size=(n_tiles, 3))
+    cnt = rng.integers(0, 1025, size=n_tiles)
+    cnt[::9] = 0
+    tb = np.zeros((n_tiles, 8), np.int32)
+    tb[:, 0:3], tb[:, 3], tb[:, 4:7] = lo, cnt, hi
+
+    class FakeAtlas:
+        def tile_box(self):
+            return torch.from_numpy(tb)
+
+    from paper_2501_14807_gb300 import lcl
+    recs = np.zeros(23, lcl.SPHERE_DTYPE)
+    recs["cx"], recs["cy"], recs["cz"] = rng.integers(0, 1100, size=(3, 23))
+    recs["r2"] = rng.integers(0, 500 ** 2, size=23)
+    got, groups = bench.sphere_group_bytes(FakeAtlas(), recs, "cpu", 2, group=8)
+    assert groups == 3
+    exp = 0.0
+    for g0 in range(0, 23, 8):
+        for t in range(n_tiles):
+            if cnt[t] == 0:
+                continue
+            reach = cross = False
+            for r in recs[g0:g0 + 8]:
+                c = np.array([r["cx"], r["cy"], r["cz"]])
+                near = np.maximum(np.maximum(lo[t] - c, c - hi[t]), 0)
+                far = np.maximum(c - lo[t], hi[t] - c)
+                if (near ** 2).sum() <= r["r2"]:
+                    reach = True
+                    if (far ** 2).sum() > r["r2"]:
+                        cross = True  # the sphere's surface crosses the tile
+            if reach:
+                exp += cnt[t] * 2 + (cnt[t] * 12 if cross else cnt[t] / 8)
+    assert abs(got - exp) < 1e-6 * exp and exp > 0

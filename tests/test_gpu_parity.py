@@ -108,6 +108,16 @@ def test_sphere_bit_exact(name, make, W, H, T, dt, n, rlo, rhi):
     for k in range(len(recs)):
         lcl.lcl_select_sphere(a, layer2, recs[k:k + 1])
     assert torch.equal(layer, layer2)
+    # in one call without hit counts (the apply may stop at a texel's newest selecting stroke), and
+    # in calls of 2 and of 33 strokes (group boundaries)
+    layer3 = to_dev(init)
+    lcl.lcl_select_sphere(a, layer3, recs)
+    assert torch.equal(layer, layer3)
+    layer4 = to_dev(init)
+    for k0 in range(0, len(recs), 35):
+        lcl.lcl_select_sphere(a, layer4, recs[k0:k0 + 2])
+        lcl.lcl_select_sphere(a, layer4, recs[k0 + 2:k0 + 35])
+    assert torch.equal(layer, layer4)
 
 
 def test_sphere_host_helper_matches_oracle():
