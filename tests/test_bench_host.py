@@ -17,7 +17,7 @@ def _root_with(tmp_path, select_src=b"// kernel source\n", traffic=None, peaks=N
     (csrc / "select.cu").write_bytes(select_src)
     (tmp_path / "profiles").mkdir()
     if traffic is not None:
-        (tmp_path / "profiles" / "sphere_edit_traffic.json").write_text(json.dumps(traffic))
+        (tmp_path / "profiles" / "sphere_group_traffic.json").write_text(json.dumps(traffic))
     if peaks is not None:
         (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps(peaks))
     return str(tmp_path)
