@@ -407,7 +407,7 @@ __device__ __forceinline__ GItem load_gitem(const AtlasDev &a, const uint32_t *_
 }
 
 template <typename L>
-__global__ void __launch_bounds__(kThreads, 4) k_group_apply(AtlasDev a, L *__restrict__ layer,
+__global__ void __launch_bounds__(kThreads, 5) k_group_apply(AtlasDev a, L *__restrict__ layer,
                                                              const __grid_constant__ GroupArg g,
                                                              const uint32_t *__restrict__ counters,
                                                              const uint32_t *__restrict__ tiles,
@@ -437,32 +437,56 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(AtlasDev a, L *__re
         if (after < n_items) next = load_gitem(a, tiles, masks, sures, after, cpt_log2, qpr, nq);
         const int32_t xs[4] = {cur.X.x, cur.X.y, cur.X.z, cur.X.w}, ys[4] = {cur.Y.x, cur.Y.y, cur.Y.z, cur.Y.w},
                       zs[4] = {cur.Z.x, cur.Z.y, cur.Z.z, cur.Z.w};
-        uint32_t open = cur.l >= 0 ? cur.cov : 0u;
+        const uint32_t cov = cur.l >= 0 ? cur.cov : 0u;
+        const int ks = cur.sure ? 31 - __clz(cur.sure) : -1;  // the newest stroke containing the tile
+        uint32_t open = cov;
         uint32_t lab[4] = {0u, 0u, 0u, 0u};
-        for (uint32_t m = cur.mask; m;) {  // uniform over the CTA: newest stroke first
+        // strokes whose surface crosses the tile, newest first (uniform over the CTA): each is tested
+        // per texel for its hit count; only those newer than stroke ks can give a texel its label
+        for (uint32_t m = cur.mask & ~cur.sure; m;) {
             const int k = 31 - __clz(m);
             m &= ~(1u << k);
+            if (!hits && k < ks) break;  // no counts wanted: stroke ks labels every open texel
             const SphereArg &sp = g.s[k];
             uint32_t sel = 0u;
-            if ((cur.sure >> k) & 1u) {
-                sel = cur.l >= 0 ? cur.cov : 0u;
-            } else if (cur.l >= 0) {
+            if (cur.l >= 0) {
+                // The stroke reaches the tile's box (r <= 2^25 and the box inside [0, 2^21)^3), so for a
+                // covered texel every coordinate difference lies within +-(2^25 + 2^21) and its square
+                // is one 32 x 32 -> 64-bit product.  Uncovered texels (x = INT32_MIN) wrap around in
+                // the unsigned difference; the coverage bits drop them.
+                const uint32_t cx = (uint32_t)sp.cx, cy = (uint32_t)sp.cy, cz = (uint32_t)sp.cz;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {  // uncovered texels (x = INT32_MIN) are never within r2
-                    const int64_t dx = (int64_t)xs[q] - sp.cx, dy = (int64_t)ys[q] - sp.cy, dz = (int64_t)zs[q] - sp.cz;
-                    sel |= (dx * dx + dy * dy + dz * dz <= sp.r2 ? 1u : 0u) << q;
+                for (int q = 0; q < 4; ++q) {
+                    const int32_t dx = (int32_t)((uint32_t)xs[q] - cx), dy = (int32_t)((uint32_t)ys[q] - cy),
+                                  dz = (int32_t)((uint32_t)zs[q] - cz);
+                    const int64_t d2 = (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz;
+                    sel |= (d2 <= sp.r2 ? 1u : 0u) << q;
                 }
+                sel &= cov;
             }
             if (hits) {
                 const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(sel));
                 if (lane == 0 && c) atomicAdd(&s_hits[k], (unsigned long long)c);
             }
-            const uint32_t nw = sel & open;
+            if (k > ks) {
+                const uint32_t nw = sel & open;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (nw & (1u << q)) lab[q] = sp.label;
+                open &= ~sel;
+            }
+        }
+        if (ks >= 0) {  // strokes containing the tile select every covered texel
+            const uint32_t label = g.s[ks].label;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (nw & (1u << q)) lab[q] = sp.label;
-            open &= ~sel;
-            if (!hits && !open) break;  // no counts wanted: the quad's labels are final
+                if (open & (1u << q)) lab[q] = label;
+            open = 0u;
+            if (hits) {
+                const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(cov));
+                if (lane == 0 && c)
+                    for (uint32_t m = cur.sure; m; m &= m - 1) atomicAdd(&s_hits[__ffs(m) - 1], (unsigned long long)c);
+            }
         }
         const uint32_t written = cur.l >= 0 ? (cur.cov & ~open) : 0u;
         if (written && LCL_IN(cur.l + 3, n_tex)) store_labels<L>(layer, cur.l, written, lab);
