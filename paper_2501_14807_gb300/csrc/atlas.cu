@@ -126,20 +126,18 @@ __global__ void k_snap(const float *__restrict__ uv, int64_t n_uv, int32_t w, in
     out[v] = make_int2((int32_t)X, (int32_t)Y);
 }
 
-// Integer square root floor(sqrt(n)) of a 128-bit value, bit by bit (restoring method).
-__device__ uint64_t isqrt128(unsigned __int128 n) {
-    unsigned __int128 rem = 0, root = 0;
+// floor(sqrt(n)) for n < 2^88 (the squared length of a cross product of 21-bit differences,
+// at most 3 * 2^86): a binary64 estimate, then exact integer corrections.  Converting n to binary64
+// and the correctly rounded square root each err by at most half an ulp, so the estimate is within
+// 2^-8 of sqrt(n) < 2^44, and its floor within one of the result.
+__device__ uint64_t isqrt_u88(unsigned __int128 n) {
+    const double d = (double)(uint64_t)(n >> 64) * 18446744073709551616.0 + (double)(uint64_t)n;
+    uint64_t r = (uint64_t)__dsqrt_rn(d);
 #pragma unroll 1
-    for (int i = 63; i >= 0; --i) {
-        root <<= 1;
-        rem = (rem << 2) | ((n >> (2 * i)) & 3);
-        unsigned __int128 trial = (root << 1) | 1;
-        if (rem >= trial) {
-            rem -= trial;
-            root |= 1;
-        }
-    }
-    return (uint64_t)root;
+    for (int k = 0; k < 3 && (unsigned __int128)r * r > n; ++k) --r;
+#pragma unroll 1
+    for (int k = 0; k < 3 && (unsigned __int128)(r + 1) * (r + 1) <= n; ++k) ++r;
+    return r;
 }
 
 struct RasterArgs {
@@ -164,6 +162,40 @@ __device__ __forceinline__ void texel_range(int64_t lo, int64_t hi, int64_t firs
     i1 = floordiv(hi - 128, 256);
     i0 = i0 < first ? first : i0;
     i1 = i1 > last ? last : i1;
+}
+
+// raster_rect for a triangle whose corners span at most 2^14 sub-pixels (64 texels) on each axis.
+// The scanned texel centres lie within the corners' bounding box (the texel range is cut from it),
+// and the values computed one texel past the last column or row within one texel of it, so with
+// ex, ey <= 2^14 the extents: |edge value| <= ex (ey + 256) + ey (ex + 256) + 1 < 2^30, and the
+// steps are at most 256 * 2^14.  The scan therefore runs in 32-bit integers after an exact start.
+__device__ void raster_rect_small(const TriSetup &s, uint32_t t, int64_t i0, int64_t i1, int64_t j0, int64_t j1,
+                                  int32_t w, int32_t row0, int32_t rows, uint32_t *__restrict__ tri_plane) {
+    const int32_t X0 = s.x[0], X1 = s.x[1], X2 = s.x[2], Y0 = s.y[0], Y1 = s.y[1], Y2 = s.y[2];
+    const int32_t px = 256 * (int32_t)i0 + 128, py = 256 * (int32_t)j0 + 128;
+    int32_t e0 = (int32_t)(edge_fn32(X1, Y1, X2, Y2, px, py) + edge_bias(X2 - X1, Y2 - Y1));
+    int32_t e1 = (int32_t)(edge_fn32(X2, Y2, X0, Y0, px, py) + edge_bias(X0 - X2, Y0 - Y2));
+    int32_t e2 = (int32_t)(edge_fn32(X0, Y0, X1, Y1, px, py) + edge_bias(X1 - X0, Y1 - Y0));
+    const int32_t dx0 = -(Y2 - Y1) * 256, dy0 = (X2 - X1) * 256;
+    const int32_t dx1 = -(Y0 - Y2) * 256, dy1 = (X0 - X2) * 256;
+    const int32_t dx2 = -(Y1 - Y0) * 256, dy2 = (X1 - X0) * 256;
+    const int32_t n_i = (int32_t)(i1 - i0);
+#pragma unroll 1
+    for (int64_t j = j0; j <= j1; ++j) {
+        int32_t r0 = e0, r1 = e1, r2 = e2;
+        uint32_t *row = tri_plane + (j - row0) * (int64_t)w + i0;
+#pragma unroll 1
+        for (int32_t i = 0; i <= n_i; ++i) {
+            if (min(r0, min(r1, r2)) > 0 && LCL_IN((j - row0) * (int64_t)w + i0 + i, (int64_t)w * rows))
+                atomicMin(row + i, t);
+            r0 += dx0;
+            r1 += dx1;
+            r2 += dx2;
+        }
+        e0 += dy0;
+        e1 += dy1;
+        e2 += dy2;
+    }
 }
 
 // Rasterises texels [i0, i1] x [j0, j1] (texture rows j) of a set-up triangle into a plane that
@@ -202,7 +234,7 @@ __global__ void k_raster(RasterArgs a) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= a.n_tri) return;
     TriSetup s;
-    s.pad = 0;
+    s.rden = 0.0f;
     uint32_t ip[3], iu[3];
     bool ok = true;
 #pragma unroll
@@ -238,7 +270,7 @@ __global__ void k_raster(RasterArgs a) {
                                (unsigned __int128)((__int128)nz * nz);
         uint64_t wgt = 0;
         if (A != 0) {
-            uint64_t a3 = isqrt128(nn);
+            uint64_t a3 = isqrt_u88(nn);
             unsigned __int128 num = (unsigned __int128)a3 << (16 + LCL_AREA_FRAC_BITS);
             uint64_t den = (uint64_t)(A < 0 ? -A : A);
             unsigned __int128 wq = num / den;
@@ -251,6 +283,7 @@ __global__ void k_raster(RasterArgs a) {
         a.setup[t] = s;
         return;
     }
+    s.rden = __frcp_rn((float)(2 * (A < 0 ? -A : A)));
     if (A < 0) {  // counter-clockwise: swap corners 1 and 2
         int32_t tmp;
         tmp = s.x[1]; s.x[1] = s.x[2]; s.x[2] = tmp;
@@ -268,7 +301,10 @@ __global__ void k_raster(RasterArgs a) {
     if (i0 > i1 || j0 > j1) return;
     int64_t nx = i1 - i0 + 1, ny = j1 - j0 + 1;
     if (nx * ny <= kSmallRaster) {
-        raster_rect(s, (uint32_t)t, i0, i1, j0, j1, a.w, a.row0, a.rows, a.tri_plane);
+        if (xmax - xmin <= (1 << 14) && ymax - ymin <= (1 << 14))
+            raster_rect_small(s, (uint32_t)t, i0, i1, j0, j1, a.w, a.row0, a.rows, a.tri_plane);
+        else
+            raster_rect(s, (uint32_t)t, i0, i1, j0, j1, a.w, a.row0, a.rows, a.tri_plane);
         return;
     }
     int64_t nbx = (nx + kBlockSide - 1) / kBlockSide, nby = (ny + kBlockSide - 1) / kBlockSide;
@@ -278,7 +314,11 @@ __global__ void k_raster(RasterArgs a) {
         for (int64_t b = 0; b < nb; ++b)
             if (LCL_IN((int64_t)base + b, a.big_cap)) a.big[base + b] = make_uint2((uint32_t)t, (uint32_t)b);
     } else {
-        raster_rect(s, (uint32_t)t, i0, i1, j0, j1, a.w, a.row0, a.rows, a.tri_plane);  // list full: do it here
+        // list full: the reserved slots that lie below the capacity are read by k_raster_big, so they
+        // get empty entries, and this thread rasterises the triangle itself
+        for (int64_t b = 0; b < nb && (int64_t)base + b < a.big_cap; ++b)
+            if (LCL_IN((int64_t)base + b, a.big_cap)) a.big[base + b] = make_uint2(kNone, 0u);
+        raster_rect(s, (uint32_t)t, i0, i1, j0, j1, a.w, a.row0, a.rows, a.tri_plane);
     }
 }
 
@@ -289,6 +329,7 @@ __global__ void k_raster_big(const uint2 *__restrict__ big, const AtlasHdr *__re
     for (int64_t e = blockIdx.x; e < n; e += gridDim.x) {
         if (!LCL_IN(e, cap)) break;
         uint2 ent = big[e];
+        if (ent.x == kNone) continue;  // a slot of a reservation that did not fit
         if (!LCL_IN(ent.x, n_tri)) continue;
         TriSetup s = setup[ent.x];
         int64_t xmin = min(s.x[0], min(s.x[1], s.x[2])), xmax = max(s.x[0], max(s.x[1], s.x[2]));
@@ -318,12 +359,13 @@ __global__ void k_raster_big(const uint2 *__restrict__ big, const AtlasHdr *__re
 // remainder corrections.
 __device__ __forceinline__ int32_t interp_axis(int64_t w1, int64_t w2, int64_t A, float rden, int32_t q0, int32_t q1,
                                                int32_t q2) {
-    const int64_t d1 = (int64_t)q1 - q0, d2 = (int64_t)q2 - q0;
+    const int32_t d1 = q1 - q0, d2 = q2 - q0;  // |d| < 2^21
     if (A < (int64_t(1) << 40)) {
         const int64_t num = 2 * (w1 * d1 + w2 * d2) + A;  // |num| < 2^63 since w <= A < 2^40, |d| < 2^21
         const int64_t den = 2 * A;
-        int64_t est = (int64_t)floorf(__fmul_rn((float)num, rden));
-        int64_t r = num - est * den;
+        // the quotient lies within the corners' range (|est| < 2^22): an int32 floor of the estimate
+        int32_t est = __float2int_rd(__fmul_rn((float)num, rden));
+        int64_t r = num - (int64_t)est * den;
 #pragma unroll 1
         for (int k = 0; k < 4 && r < 0; ++k) { est -= 1; r += den; }
 #pragma unroll 1
@@ -356,6 +398,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_resolve(const TriSetup *__restr
     // together, find its set-up record in L1
     const int32_t n_tex_tile = T * T;
     const int iters = (n_tex_tile + kThreads - 1) / kThreads;
+    // tiles of 32 texels or more on a width that is a multiple of 32: each warp's 32 texels are one
+    // aligned coverage word (uniform over the grid)
+    const bool aligned = T >= 32 && (w & 31) == 0;
     for (int it = 0; it < iters; ++it) {
         const int32_t i = it * kThreads + threadIdx.x;
         const int32_t x = tx * T + (i % T), y = ty * T + i / T;
@@ -367,11 +412,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_resolve(const TriSetup *__restr
             int32_t ox = INT32_MIN, oy = 0, oz = 0;
             if (t != kNone && LCL_IN(t, n_tri)) {
                 const TriSetup s = setup[t];
-                const int64_t cx = 256 * (int64_t)x + 128, cy = 256 * ((int64_t)y + row0) + 128;
-                const int64_t A = edge_fn(s.x[0], s.y[0], s.x[1], s.y[1], s.x[2], s.y[2]);
-                const int64_t w1 = edge_fn(s.x[2], s.y[2], s.x[0], s.y[0], cx, cy);
-                const int64_t w2 = edge_fn(s.x[0], s.y[0], s.x[1], s.y[1], cx, cy);
-                const float rden = __frcp_rn((float)(2 * A));
+                // sub-pixel coordinates and texel centres lie within [-2^22, 2^23] (sides <= 2^14,
+                // UVs in [-1, 2]): differences fit in 32 bits, products in 64
+                const int32_t cx = 256 * x + 128, cy = 256 * (y + row0) + 128;
+                const int64_t A = edge_fn32(s.x[0], s.y[0], s.x[1], s.y[1], s.x[2], s.y[2]);
+                const int64_t w1 = edge_fn32(s.x[2], s.y[2], s.x[0], s.y[0], cx, cy);
+                const int64_t w2 = edge_fn32(s.x[0], s.y[0], s.x[1], s.y[1], cx, cy);
+                const float rden = s.rden;
                 ox = interp_axis(w1, w2, A, rden, s.qx[0], s.qx[1], s.qx[2]);
                 oy = interp_axis(w1, w2, A, rden, s.qy[0], s.qy[1], s.qy[2]);
                 oz = interp_axis(w1, w2, A, rden, s.qz[0], s.qz[1], s.qz[2]);
@@ -385,13 +432,22 @@ __global__ void __launch_bounds__(kThreads, 4) k_resolve(const TriSetup *__restr
             __stcs(py + l, oy);
             __stcs(pz + l, oz);
         }
-        // coverage bits: lanes writing the same 32-bit word combine, one atomicOr per word
+        // coverage bits
         const uint32_t word = (uint32_t)(l >> 5);
-        const uint32_t val = covered ? 1u << (uint32_t)(l & 31) : 0u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? word : 0xFFFFFFFFu);
-        const uint32_t orv = __reduce_or_sync(peers, val);
-        if (valid && orv != 0 && (threadIdx.x & 31) == (__ffs(peers) - 1) && LCL_IN(word, ((int64_t)w * h + 31) / 32))
-            atomicOr(cover + word, orv);
+        if (aligned) {
+            // the warp holds one whole 32-texel word of one tile row (lane k = texel k): a ballot is
+            // the word, written by lane 0 (the tile's CTA is its only writer)
+            const uint32_t bits = __ballot_sync(0xffffffffu, covered);
+            if (valid && (threadIdx.x & 31) == 0 && LCL_IN(word, ((int64_t)w * h + 31) / 32)) cover[word] = bits;
+        } else {
+            // lanes writing the same 32-bit word combine, one atomicOr per word
+            const uint32_t val = covered ? 1u << (uint32_t)(l & 31) : 0u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, valid ? word : 0xFFFFFFFFu);
+            const uint32_t orv = __reduce_or_sync(peers, val);
+            if (valid && orv != 0 && (threadIdx.x & 31) == (__ffs(peers) - 1) &&
+                LCL_IN(word, ((int64_t)w * h + 31) / 32))
+                atomicOr(cover + word, orv);
+        }
     }
     // tile box: block reduction
     __shared__ int32_t red[7][kThreads / 32];

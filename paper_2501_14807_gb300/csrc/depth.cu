@@ -170,6 +170,10 @@ __global__ void k_raster(const __grid_constant__ DepthArgs a) {
                 if (LCL_IN((int64_t)base + b, a.big_cap)) a.big[base + b] = make_uint2((uint32_t)t, (uint32_t)b);
             return;
         }
+        // list full: the reserved slots below the capacity are read by k_raster_big, so they get
+        // empty entries, and this thread rasterises the triangle itself (below)
+        for (int64_t b = 0; b < nb && (int64_t)base + b < a.big_cap; ++b)
+            if (LCL_IN((int64_t)base + b, a.big_cap)) a.big[base + b] = make_uint2(kNone, 0u);
     }
 #pragma unroll 1
     for (int64_t j = j0; j <= j1; ++j)
@@ -184,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_raster_big(const __grid_constant__
     for (int64_t e = blockIdx.x; e < n; e += gridDim.x) {
         if (!LCL_IN(e, a.big_cap)) break;  // uniform over the CTA
         const uint2 ent = a.big[e];
-        if (threadIdx.x == 0) ok = depth_setup(a, ent.x, sd) ? 1 : 0;
+        if (threadIdx.x == 0) ok = ent.x != kNone && depth_setup(a, ent.x, sd) ? 1 : 0;
         __syncthreads();
         if (ok) {
             const DTri d = sd;

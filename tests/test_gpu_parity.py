@@ -36,6 +36,9 @@ ATLAS_CASES = [
     ("lattice-ties", lambda: lattice_soup(8, 48, 40), 48, 40, 16),
     ("square-big-tris", lambda: synth.uv_square_patch(512, 384, 3), 512, 384, 128),
     ("grid-jitter", lambda: synth.grid_patch(37, 23, 256, 200, seed=9, jitter=0.4), 256, 200, 32),
+    # big overlapping UV triangles: ~15,800 16x16 blocks against a list of 4096, so most triangles
+    # find the list full and are rasterised by their own thread
+    ("soup-list-full", lambda: synth.random_soup(400, 11), 512, 384, 32),
 ]
 
 
@@ -148,6 +151,8 @@ DEPTH_CASES = [
     ("vessel-orbit", lambda: synth.config_small().mesh, 512, 384, 0),
     ("vessel-orbit-2", lambda: synth.vessel_cylindrical(120, 40, noise_amp=0.05, seed=3), 333, 211, 1),
     ("charts-orbit", lambda: synth.vessel_charts(200, 100, 25, 10, 512, seed=5), 256, 256, 2),
+    # triangles spanning most of the screen: far more 16x16 blocks than the list holds
+    ("soup-list-full", lambda: synth.random_soup(400, 11), 512, 512, 3),
 ]
 
 
