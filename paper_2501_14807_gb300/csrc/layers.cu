@@ -4,15 +4,16 @@
 // Both are pure HBM streams over the texture:
 //   k_overlay  16 bytes of each operand and of the output per thread step, coverage bits
 //              expanded to byte / half-word masks in registers (SWAR), no shared memory
-//   k_area     a contiguous range of 16-texel chunks per warp (one chunk per lane and step);
-//              runs of equal labels stay in registers while the whole warp sees one label,
-//              then are reduced across the warp (shuffles, match_any groups) and flushed
-//              into a shared-memory histogram (64-bit shared atomics); the histogram goes
-//              into the outputs with one global atomic per non-zero bin per CTA.  All sums
-//              are integers, so the result does not depend on the order.  A flush per lane
-//              and chunk (one shared atomic pair each) cost 0.39-0.57 ms per 16384^2 query
-//              on GB300; the same loads and gathers without any flush take 0.25 ms.
+//   k_area4    four consecutive texels per lane and step, a contiguous range of steps per warp
+//              (128 consecutive texels per warp and step, coalesced loads of triangle ids and
+//              labels, the next step's issued ahead); the four weight gathers of a lane are
+//              independent loads; texels carrying the warp's current label add to per-lane
+//              sums in registers, reduced across the warp only when another label appears;
+//              the histogram lives in shared memory (64-bit shared atomics) and goes into the
+//              outputs with one global atomic per non-zero bin per CTA.  All sums are
+//              integers, so the result does not depend on the order.
 #include <algorithm>
+#include <type_traits>
 
 #include "lcl_impl.cuh"
 
@@ -90,28 +91,19 @@ __global__ void k_zero2(unsigned long long *x, unsigned long long *y, uint32_t n
     }
 }
 
-struct Run {
-    uint32_t label;
-    uint32_t cnt;
-    unsigned long long area;
-};
-
-template <bool SMEM>
-__device__ __forceinline__ void flush(const Run &r, unsigned long long *hc, unsigned long long *ha, uint32_t n_labels) {
-    if (r.cnt == 0) return;
-    if (!LCL_IN(r.label, n_labels)) return;
-    atomicAdd(hc + r.label, (unsigned long long)r.cnt);
-    atomicAdd(ha + r.label, r.area);
-    (void)n_labels;
-}
-
+// Per-label area, four consecutive texels (a quad) per lane and step: a warp reads 128 consecutive
+// texels per step, one 16-byte load of triangle ids and one 4- or 8-byte load of labels per lane.
+// The four weight gathers of a lane are independent loads (a texel whose triangle is its left
+// neighbour's reuses that weight), so they are in flight together.
+// Texels carrying the warp's current label add to per-lane sums in registers; when a step holds
+// other labels, the warp's sums are reduced into the histogram, the warp takes the label of the
+// step's last such texel, and texels of any third label go to the histogram one by one.
 template <typename L, bool SMEM>
-__global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ layer, const uint32_t *__restrict__ tri,
-                                                      const uint64_t *__restrict__ area_w, int64_t n_tri,
-                                                      int64_t n_texels, uint32_t n_labels,
-                                                      unsigned long long *__restrict__ count,
-                                                      unsigned long long *__restrict__ area) {
-    (void)n_tri;
+__global__ void __launch_bounds__(kThreads, 5) k_area4(const L *__restrict__ layer, const uint32_t *__restrict__ tri,
+                                                    const uint64_t *__restrict__ area_w, int64_t n_tri,
+                                                    int64_t n_texels, uint32_t n_labels,
+                                                    unsigned long long *__restrict__ count,
+                                                    unsigned long long *__restrict__ area) {
     extern __shared__ unsigned long long sh[];
     unsigned long long *hc = SMEM ? sh : count;
     unsigned long long *ha = SMEM ? sh + n_labels : area;
@@ -120,121 +112,108 @@ __global__ void __launch_bounds__(kThreads, 4) k_area(const L *__restrict__ laye
         __syncthreads();
     }
     const unsigned long long *aw = reinterpret_cast<const unsigned long long *>(area_w);
-    Run run{0u, 0u, 0ull};
-    uint32_t last_t = kNone;
-    unsigned long long last_w = 0;
-    // a lane's run is flushed by itself only when the label changes inside its chunk
-    auto visit = [&](uint32_t lab, uint32_t t) {
-        if (t == kNone || lab >= n_labels) return;
-        if (!LCL_IN(t, n_tri)) return;
-        if (t != last_t) {
-            last_t = t;
-            last_w = __ldg(aw + t);
-        }
-        if (lab != run.label && run.cnt != 0) {
-            flush<SMEM>(run, hc, ha, n_labels);
-            run.cnt = 0;
-            run.area = 0;
-        }
-        run.label = lab;
-        run.cnt += 1;
-        run.area += last_w;
-    };
-    // Each warp takes a contiguous range of iterations; in one iteration lane l takes the 16-texel
-    // chunk 32 it + l (four 16-byte loads of triangle ids, one or two of labels), the next
-    // iteration's loads issued before the current chunk is visited.
-    constexpr int LW = sizeof(L) == 1 ? 1 : 2;
     const int lane = threadIdx.x & 31;
-    const int64_t n_chunks = n_texels / 16;
+    const int64_t n_quads = n_texels / 4;  // the width is a multiple of 4
+    const int64_t n_steps = (n_quads + 31) / 32;
     const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t n_iter = (n_chunks + 31) / 32;
-    const int64_t per = (n_iter + n_warps - 1) / n_warps;
-    const int64_t it0 = warp * per, it1 = min(n_iter, it0 + per);
-    uint4 T4[4], V[LW];
-    auto load = [&](int64_t c) {
-        if (!LCL_IN(16 * c + 15, n_texels)) return;
-        const uint4 *tp = reinterpret_cast<const uint4 *>(tri + 16 * c);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) T4[k] = __ldcs(tp + k);
-#pragma unroll
-        for (int k = 0; k < LW; ++k) V[k] = __ldcs(reinterpret_cast<const uint4 *>(layer + 16 * c) + k);
+    const int64_t per = (n_steps + n_warps - 1) / n_warps;
+    const int64_t s0 = warp * per, s1 = min(n_steps, s0 + per);
+    using LV = typename std::conditional<sizeof(L) == 1, uint32_t, uint2>::type;  // a lane's four labels
+    // step s: quad 32 s + lane; the next step's loads are issued before this step is summed
+    uint4 T = make_uint4(kNone, kNone, kNone, kNone);
+    LV V{};
+    auto load = [&](int64_t st) {
+        const int64_t q = st * 32 + lane;
+        T = make_uint4(kNone, kNone, kNone, kNone);
+        if (q < n_quads && LCL_IN(4 * q + 3, n_texels)) {
+            T = __ldcs(reinterpret_cast<const uint4 *>(tri) + q);
+            V = __ldcs(reinterpret_cast<const LV *>(layer) + q);
+        }
     };
-    // warp run: while every lane's run of an iteration has the warp's label, each lane adds its run
-    // to its own share of the warp run (registers only); when an iteration brings another label, the
-    // shares are reduced across the warp and written by one lane, and this iteration's runs are
-    // reduced label by label (match_any groups)
-    uint32_t wlabel = kNone;
-    unsigned long long wcnt = 0, warea = 0;
-    if (it0 < it1 && it0 * 32 + lane < n_chunks) load(it0 * 32 + lane);
-    for (int64_t it = it0; it < it1; ++it) {
-        const int64_t c = it * 32 + lane;
-        if (c < n_chunks) {
-            const uint32_t ts[16] = {T4[0].x, T4[0].y, T4[0].z, T4[0].w, T4[1].x, T4[1].y, T4[1].z, T4[1].w,
-                                     T4[2].x, T4[2].y, T4[2].z, T4[2].w, T4[3].x, T4[3].y, T4[3].z, T4[3].w};
-            uint32_t w[4 * LW];
+    uint32_t wlabel = kNone, wcnt = 0;  // the warp's label; this lane's share of its count and area
+    unsigned long long warea = 0;
+    if (s0 < s1) load(s0);
+    for (int64_t st = s0; st < s1; ++st) {
+        const uint32_t ts[4] = {T.x, T.y, T.z, T.w};
+        uint32_t lab[4];
+        if constexpr (sizeof(L) == 1) {
 #pragma unroll
-            for (int k = 0; k < LW; ++k) {
-                w[4 * k] = V[k].x;
-                w[4 * k + 1] = V[k].y;
-                w[4 * k + 2] = V[k].z;
-                w[4 * k + 3] = V[k].w;
-            }
-            if (it + 1 < it1 && c + 32 < n_chunks) load(c + 32);
+            for (int k = 0; k < 4; ++k) lab[k] = (V >> (8 * k)) & 0xFFu;
+        } else {
+            lab[0] = V.x & 0xFFFFu;
+            lab[1] = V.x >> 16;
+            lab[2] = V.y & 0xFFFFu;
+            lab[3] = V.y >> 16;
+        }
+        if (st + 1 < s1) load(st + 1);
+        unsigned long long w[4];
+        bool vt[4];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const uint32_t lab =
-                    sizeof(L) == 1 ? (w[k / 4] >> (8 * (k % 4))) & 0xFFu : (w[k / 2] >> (16 * (k % 2))) & 0xFFFFu;
-                visit(lab, ts[k]);
+        for (int k = 0; k < 4; ++k) {
+            vt[k] = ts[k] != kNone && ts[k] < (uint64_t)n_tri;
+            w[k] = (vt[k] && (k == 0 || ts[k] != ts[k - 1])) ? __ldg(aw + ts[k]) : 0ull;
+        }
+#pragma unroll
+        for (int k = 1; k < 4; ++k)
+            if (vt[k] && ts[k] == ts[k - 1]) w[k] = w[k - 1];
+        uint32_t odd = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!vt[k] || lab[k] >= n_labels) continue;
+            if (lab[k] == wlabel) {
+                wcnt += 1;
+                warea += w[k];
+            } else {
+                odd |= 1u << k;
             }
         }
-        const uint32_t key = run.cnt ? run.label : kNone;
-        if (__all_sync(0xffffffffu, key == wlabel || key == kNone)) {
-            wcnt += run.cnt;
-            warea += run.area;
-        } else {
-            unsigned long long tc = wcnt, ta = warea;
+        const uint32_t bal = __ballot_sync(0xffffffffu, odd != 0);
+        if (bal) {  // uniform over the warp
+            uint32_t c = wcnt;
+            unsigned long long a = warea;
 #pragma unroll
             for (int o = 16; o; o >>= 1) {
-                tc += __shfl_xor_sync(0xffffffffu, tc, o);
-                ta += __shfl_xor_sync(0xffffffffu, ta, o);
+                c += __shfl_xor_sync(0xffffffffu, c, o);
+                a += __shfl_xor_sync(0xffffffffu, a, o);
             }
-            if (lane == 0 && tc && LCL_IN(wlabel, n_labels)) {
-                atomicAdd(hc + wlabel, tc);
-                atomicAdd(ha + wlabel, ta);
+            if (lane == 0 && c && LCL_IN(wlabel, n_labels)) {
+                atomicAdd(hc + wlabel, (unsigned long long)c);
+                atomicAdd(ha + wlabel, a);
             }
+            uint32_t last = kNone;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (odd & (1u << k)) last = lab[k];
+            wlabel = __shfl_sync(0xffffffffu, last, 31 - __clz(bal));
             wcnt = 0;
             warea = 0;
-            const unsigned peers = __match_any_sync(0xffffffffu, key);
-            const uint32_t cnt = __reduce_add_sync(peers, run.cnt);
-            const uint32_t lo = __reduce_add_sync(peers, (uint32_t)(run.area & 0xFFFFFu));
-            const uint32_t hi = __reduce_add_sync(peers, (uint32_t)(run.area >> 20));
-            if (key != kNone && lane == __ffs(peers) - 1 && LCL_IN(key, n_labels)) {
-                atomicAdd(hc + key, (unsigned long long)cnt);
-                atomicAdd(ha + key, (unsigned long long)lo + ((unsigned long long)hi << 20));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (!(odd & (1u << k))) continue;
+                if (lab[k] == wlabel) {
+                    wcnt += 1;
+                    warea += w[k];
+                } else if (LCL_IN(lab[k], n_labels)) {
+                    atomicAdd(hc + lab[k], 1ull);
+                    atomicAdd(ha + lab[k], w[k]);
+                }
             }
-            wlabel = __shfl_sync(0xffffffffu, key, 31);
         }
-        run.cnt = 0;
-        run.area = 0;
     }
     {
-        unsigned long long tc = wcnt, ta = warea;
+        uint32_t c = wcnt;
+        unsigned long long a = warea;
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
-            tc += __shfl_xor_sync(0xffffffffu, tc, o);
-            ta += __shfl_xor_sync(0xffffffffu, ta, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            a += __shfl_xor_sync(0xffffffffu, a, o);
         }
-        if (lane == 0 && tc && LCL_IN(wlabel, n_labels)) {
-            atomicAdd(hc + wlabel, tc);
-            atomicAdd(ha + wlabel, ta);
+        if (lane == 0 && c && LCL_IN(wlabel, n_labels)) {
+            atomicAdd(hc + wlabel, (unsigned long long)c);
+            atomicAdd(ha + wlabel, a);
         }
     }
-    // tail texels (n_texels % 16), one per thread
-    for (int64_t t = n_chunks * 16 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_texels;
-         t += (int64_t)gridDim.x * blockDim.x)
-        if (LCL_IN(t, n_texels)) visit((uint32_t)layer[t], tri[t]);
-    flush<SMEM>(run, hc, ha, n_labels);
     if (SMEM) {
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < n_labels; i += blockDim.x) {
@@ -284,16 +263,16 @@ lcl_status label_area_impl(const lcl_atlas *atlas, const void *layer, int dtype_
     const uint32_t *tri = atlas->tri;
     if (dtype_bytes == 1) {
         const uint8_t *l = static_cast<const uint8_t *>(layer);
-        if (smem) k_area<uint8_t, true><<<fit(k_area<uint8_t, true>), kThreads, shb, st>>>(l, tri, atlas->area_w, atlas->n_tri,
+        if (smem) k_area4<uint8_t, true><<<fit(k_area4<uint8_t, true>), kThreads, shb, st>>>(l, tri, atlas->area_w, atlas->n_tri,
                                                                                           n_tex, n_labels, c, ar);
-        else k_area<uint8_t, false><<<fit(k_area<uint8_t, false>), kThreads, 0, st>>>(l, tri, atlas->area_w, atlas->n_tri,
+        else k_area4<uint8_t, false><<<fit(k_area4<uint8_t, false>), kThreads, 0, st>>>(l, tri, atlas->area_w, atlas->n_tri,
                                                                                       n_tex, n_labels, c, ar);
     } else {
         const uint16_t *l = static_cast<const uint16_t *>(layer);
-        if (smem) k_area<uint16_t, true><<<fit(k_area<uint16_t, true>), kThreads, shb, st>>>(l, tri, atlas->area_w,
+        if (smem) k_area4<uint16_t, true><<<fit(k_area4<uint16_t, true>), kThreads, shb, st>>>(l, tri, atlas->area_w,
                                                                                             atlas->n_tri, n_tex,
                                                                                             n_labels, c, ar);
-        else k_area<uint16_t, false><<<fit(k_area<uint16_t, false>), kThreads, 0, st>>>(l, tri, atlas->area_w, atlas->n_tri,
+        else k_area4<uint16_t, false><<<fit(k_area4<uint16_t, false>), kThreads, 0, st>>>(l, tri, atlas->area_w, atlas->n_tri,
                                                                                         n_tex, n_labels, c, ar);
     }
     count_launches(2);
