@@ -37,6 +37,8 @@ namespace {
 
 // Zeroes n counters and the first n_hits of `hits` (nullable).
 __global__ void k_sel_init(uint32_t *counters, int32_t n, unsigned long long *hits, int32_t n_hits) {
+    pdl_wait();  // launched as a dependent: the previous grid no longer reads the counters
+    pdl_allow_next();
     const int32_t end = max(n, hits ? n_hits : 0);
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < end; i += gridDim.x * blockDim.x) {
         if (i < n && LCL_IN(i, n)) counters[i] = 0;
@@ -544,6 +546,8 @@ __global__ void __launch_bounds__(kThreads) k_lasso_supers(AtlasDev a, const __g
         const int4 slo = sb[0], shi = sb[1];
         cand = slo.w > 0 && box_may_touch8(p, slo, shi, nullptr);
     }
+    pdl_wait();  // the counter was reset by the previous grid
+    pdl_allow_next();
     append_candidate(cand && (threadIdx.x & 7u) == 0, (uint32_t)sidx, counter, list, n_super);
 }
 
@@ -570,6 +574,8 @@ __global__ void __launch_bounds__(kThreads) k_lasso_cull(AtlasDev a, const __gri
         }
         __syncthreads();
     }
+    pdl_wait();  // the candidate super-tiles are complete
+    pdl_allow_next();
     const int64_t n_tiles = (int64_t)a.tiles_x * a.tiles_y, n_super = (int64_t)a.supers_x * a.supers_y;
     (void)n_super;
     const uint32_t n_units = *super_count * kCullParts;
@@ -665,6 +671,8 @@ __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restr
     __shared__ LassoShared sh;
     stage_lasso(sh, p);
     __syncthreads();
+    pdl_wait();  // the candidate tiles are complete
+    pdl_allow_next();
     const uint32_t n = *counter;
     const int32_t qpr = a.T / 4, nq = a.T * qpr;
     uint32_t cnt = 0;
@@ -793,8 +801,15 @@ int launch_lasso_cull(const AtlasDev &a, const lcl_atlas *atlas, const LassoArg 
                       const SelWs &w, bool pad, bool classify, cudaStream_t st) {
     // counters[1] and list3 hold the candidate super-tiles (lassos and the tool use list and list2 only)
     const int n_super = atlas->supers_x * atlas->supers_y;
-    k_lasso_supers<<<(n_super + kThreads / 8 - 1) / (kThreads / 8), kThreads, 0, st>>>(a, p, w.counters + 1, w.list3);
     const int grid = std::max(1, std::min(n_super * kCullParts, 8 * sm_count()));
+    if (!pad && classify) {  // the lasso's chain: each launch a programmatic dependent of the one before
+        launch_pdl(k_lasso_supers, dim3((n_super + kThreads / 8 - 1) / (kThreads / 8)), st, a, p, w.counters + 1,
+                   w.list3);
+        launch_pdl(k_lasso_cull<false, true>, dim3(grid), st, a, p, depth, (const uint32_t *)(w.counters + 1),
+                   (const uint32_t *)w.list3, w.counters, w.list);
+        return 2;
+    }
+    k_lasso_supers<<<(n_super + kThreads / 8 - 1) / (kThreads / 8), kThreads, 0, st>>>(a, p, w.counters + 1, w.list3);
     if (!pad) {
         if (classify)
             k_lasso_cull<false, true><<<grid, kThreads, 0, st>>>(a, p, depth, w.counters + 1, w.list3, w.counters,
@@ -1021,8 +1036,8 @@ void launch_lasso_apply(bool pad, const AtlasDev &a, L *layer, const LassoArg &p
         k_lasso_apply<L, NUM, true><<<resident_grid(k_lasso_apply<L, NUM, true>), kThreads, 0, st>>>(
             a, layer, p, depth, w.counters, w.list, h, vm, pad_r, pad_t);
     else
-        k_lasso_apply<L, NUM, false><<<resident_grid(k_lasso_apply<L, NUM, false>), kThreads, 0, st>>>(
-            a, layer, p, depth, w.counters, w.list, h, vm, 0, 0);
+        launch_pdl(k_lasso_apply<L, NUM, false>, dim3(resident_grid(k_lasso_apply<L, NUM, false>)), st, a, layer, p,
+                   depth, (const uint32_t *)w.counters, (const uint32_t *)w.list, h, vm, 0, 0);
 }
 
 // Lasso on a label layer (mask NULL) or on a numeric layer (data bytes 1, 2 or 4 and its mask bits),
@@ -1037,7 +1052,10 @@ lcl_status lasso_run(const lcl_atlas *atlas, void *layer, int bytes, uint32_t *m
     fill_lasso_arg(p, cam, poly, nv, label, bias);
     const int32_t pad_r = (int32_t)(pad_flags & 15u), pad_t = (int32_t)((pad_flags >> 4) & 15u);
     const bool pad = pad_r > 0;
-    k_sel_init<<<1, kThreads, 0, st>>>(w.counters, 2, h, 1);
+    if (pad)
+        k_sel_init<<<1, kThreads, 0, st>>>(w.counters, 2, h, 1);
+    else
+        launch_pdl(k_sel_init, dim3(1), st, w.counters, 2, h, 1);
     const int n_cull = launch_lasso_cull(a, atlas, p, depth, w, pad, true, st);
     ValMask vm;
     vm.bits = mask;

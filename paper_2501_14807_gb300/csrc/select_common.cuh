@@ -515,6 +515,26 @@ __device__ __forceinline__ int lasso_tile_class8(const LassoArg &p, const float 
     return on_screen ? kTileIn : kTileTest;
 }
 
+// Decisions on the correctly rounded quotient q = RN(a / b), b > 0, made exactly without dividing
+// when a product says enough (the correctly rounded division runs only in the narrow band left):
+//   q >= 0:  a >= 0 gives a / b >= 0; a < 0 takes the division (a quotient that underflows to -0
+//            passes);
+//   q <= t:  e = RN(a - t b) (one rounding, an FMA) has the sign of a - t b, so e < 0 means a / b < t
+//            and then q <= t (rounding is monotone and t is a float).  For t, b and t b normal, e above
+//            RN(t b) 2^-20 means a / b > t + t 2^-21 > t + ulp(t) / 2, beyond the rounding boundary
+//            above t, so q > t.  Otherwise (e near 0, or an operand too small or not finite) the
+//            quotient is computed.
+__device__ __forceinline__ bool quot_ge0(float a, float b) { return a >= 0.0f || div_rn(a, b) >= 0.0f; }
+
+__device__ __forceinline__ bool quot_le(float a, float b, float t) {
+    const float e = __fmaf_rn(-t, b, a);
+    if (e < 0.0f) return true;
+    const float tb = __fmul_rn(t, b);
+    if (t >= 0x1p-126f && b >= 0x1p-126f && tb >= 0x1p-100f && tb <= 0x1p100f && e > __fmul_rn(tb, 0x1p-20f))
+        return false;
+    return div_rn(a, b) <= t;
+}
+
 // The lasso test of one texel.  The conditions of the definition are all required, so they are
 // evaluated cheapest first; every value that decides the result is computed in the exact FP32
 // order of the definition.  Two shortcuts are exact as well:
@@ -556,12 +576,13 @@ __device__ __forceinline__ bool lasso_hit(const LassoArg &p, const Edges &sh, co
         }
     }
     if (!inside) return false;
-    const float zn = div_rn(clip_row(p.m + 8, fx, fy, fz), cw);
-    if (!(zn >= 0.0f && zn <= 1.0f)) return false;
+    // NDC depth zn = RN(cz / cw) in [0, 1] and zn <= depth + bias, decided as quot_* describes
+    const float cz = clip_row(p.m + 8, fx, fy, fz);
+    if (!(quot_ge0(cz, cw) && quot_le(cz, cw, 1.0f))) return false;
     const int32_t ix = __float2int_rz(xs), iy = __float2int_rz(ys);
     if (!LCL_IN((int64_t)iy * p.w_s + ix, (int64_t)p.w_s * p.h_s)) return false;
     const float d = __ldg(depth + (int64_t)iy * p.w_s + ix);
-    return zn <= __fadd_rn(d, p.bias);
+    return quot_le(cz, cw, __fadd_rn(d, p.bias));
 }
 
 
@@ -575,12 +596,12 @@ __device__ __forceinline__ uint32_t lasso_depth_quad(const LassoArg &p, const fl
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         if (!(live & (1u << k))) continue;
-        const float zn = div_rn(clip_row(p.m + 8, (float)xq[k], (float)yq[k], (float)zq[k]), cw[k]);
-        if (!(zn >= 0.0f && zn <= 1.0f)) continue;
+        const float cz = clip_row(p.m + 8, (float)xq[k], (float)yq[k], (float)zq[k]);
+        if (!(quot_ge0(cz, cw[k]) && quot_le(cz, cw[k], 1.0f))) continue;
         const int32_t ix = __float2int_rz(xs[k]), iy = __float2int_rz(ys[k]);
         if (!LCL_IN((int64_t)iy * p.w_s + ix, (int64_t)p.w_s * p.h_s)) continue;
         const float d = __ldg(depth + (int64_t)iy * p.w_s + ix);
-        if (zn <= __fadd_rn(d, p.bias)) m |= 1u << k;
+        if (quot_le(cz, cw[k], __fadd_rn(d, p.bias))) m |= 1u << k;
     }
     return m;
 }
@@ -702,12 +723,12 @@ __device__ __forceinline__ bool tool_hit(const LassoArg &p, const ToolArg &t, co
         const float ex = __fmul_rn(__fsub_rn(xs, t.px), t.kx), ey = __fmul_rn(__fsub_rn(ys, t.py), t.ky);
         if (!(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)) <= 1.0f)) return false;
     }
-    const float zn = div_rn(clip_row(p.m + 8, fx, fy, fz), cw);
-    if (!(zn >= 0.0f && zn <= 1.0f)) return false;
+    const float cz = clip_row(p.m + 8, fx, fy, fz);  // zn = RN(cz / cw), decided as quot_* describes
+    if (!(quot_ge0(cz, cw) && quot_le(cz, cw, 1.0f))) return false;
     const int32_t ix = __float2int_rz(xs), iy = __float2int_rz(ys);
     if (!LCL_IN((int64_t)iy * p.w_s + ix, (int64_t)p.w_s * p.h_s)) return false;
     const float d = __ldg(depth + (int64_t)iy * p.w_s + ix);
-    return zn <= __fadd_rn(d, p.bias);
+    return quot_le(cz, cw, __fadd_rn(d, p.bias));
 }
 
 // CTAs of `threads` threads that fit on one SM at once (at least 1).
