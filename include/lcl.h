@@ -718,9 +718,12 @@ lcl_status lcl_last_device_status(lcl_stream stream);
  * library computes it on a faster route for operands in [2^-30, 2^31) and must give exactly the
  * correctly rounded quotient everywhere.  This call compares the two on n operand pairs drawn
  * from `seed` (random operands across and beyond that window, quotients next to rounding
- * midpoints, the window's edges, zeros, subnormals, infinities, NaN) and adds to counts[0] the
- * pairs compared and to counts[1] those whose results differ (NaN equals NaN).  counts: device,
- * two uint64 (not cleared by the call). */
+ * midpoints, the window's edges, zeros, subnormals, infinities, NaN).  For each pair with a
+ * positive divisor it also checks the depth test's decisions on the quotient (q >= 0 and q <= t,
+ * taken without dividing where one FMA settles them) against the same tests on the correctly
+ * rounded quotient, for t on the quotient, one ulp either side, 1 and a random value.  It adds to
+ * counts[0] the checks made (at least n) and to counts[1] those that differ (NaN equals NaN).
+ * counts: device, two uint64 (not cleared by the call). */
 lcl_status lcl_check_division(uint64_t n, uint32_t seed, uint64_t *counts, lcl_stream stream);
 
 #define LCL_BUILD_BOUNDS_CHECKS 1u  /* lcl_build_flags bit: kernels check their indices */

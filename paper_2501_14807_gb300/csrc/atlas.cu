@@ -363,7 +363,9 @@ __device__ __forceinline__ int32_t interp_axis(int64_t w1, int64_t w2, int64_t A
     if (A < (int64_t(1) << 40)) {
         const int64_t num = 2 * (w1 * d1 + w2 * d2) + A;  // |num| < 2^63 since w <= A < 2^40, |d| < 2^21
         const int64_t den = 2 * A;
-        // the quotient lies within the corners' range (|est| < 2^22): an int32 floor of the estimate
+        // the quotient lies within the corners' range (|num / den| <= 2^21 + 1): an int32 floor of the
+        // estimate, which four roundings (num and 2A to FP32, the reciprocal, the product) leave within
+        // 1/2 of num / den, so the corrections below take at most one step and usually none
         int32_t est = __float2int_rd(__fmul_rn((float)num, rden));
         int64_t r = num - (int64_t)est * den;
 #pragma unroll 1

@@ -849,7 +849,8 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
 // with exponents across and beyond div_rn's window; quotients next to a rounding midpoint (a = q b
 // rounded, +-1 ulp); operands at the window's edges and just outside; special values (zeros,
 // subnormals, infinities, NaN, the largest and smallest normals, tiny positive and negative w).
-// counts[0] += compared, counts[1] += mismatches (NaN results compare equal to NaN).
+// counts[0] += compared, counts[1] += mismatches (NaN results compare equal to NaN).  For b > 0 the
+// exact decisions quot_ge0 and quot_le are compared with the same tests on __fdiv_rn's quotient.
 __global__ void k_check_division(uint64_t n, uint32_t seed, unsigned long long *counts) {
     unsigned long long cmp = 0, bad = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
@@ -894,6 +895,19 @@ __global__ void k_check_division(uint64_t n, uint32_t seed, unsigned long long *
         const bool same = __float_as_uint(q) == __float_as_uint(m) || (isnan(q) && isnan(m));
         ++cmp;
         bad += same ? 0 : 1;
+        // quot_ge0 and quot_le (b > 0) against the quotient, at thresholds on it, one ulp either
+        // side, 1 and a random value
+        if (b > 0.0f && !isnan(q)) {
+            ++cmp;
+            bad += quot_ge0(a, b) == (q >= 0.0f) ? 0 : 1;
+            const float ts[5] = {q, nextafterf(q, INFINITY), nextafterf(q, -INFINITY), 1.0f,
+                                 __uint_as_float((h2 & 0x80000000u) | ((100u + (h1 >> 27)) << 23) | (h1 & 0x7FFFFFu))};
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                ++cmp;
+                bad += quot_le(a, b, ts[j]) == (q <= ts[j]) ? 0 : 1;
+            }
+        }
     }
     for (int o = 16; o; o >>= 1) {
         cmp += __shfl_xor_sync(0xffffffffu, cmp, o);
