@@ -367,29 +367,46 @@ __global__ void __launch_bounds__(kThreads) k_group_cull(AtlasDev a, const __gri
     pdl_allow_next();
 }
 
-// A front item's quad for this thread: the item's masks, the quad's coverage and, when some stroke
-// of the item is not sure, its positions.
+// A front item's list entry, loaded two items ahead; tile = kNone: none.
+struct GEnt {
+    uint32_t tile, mask, sure;
+};
+
+__device__ __forceinline__ GEnt load_gent(const AtlasDev &a, const uint32_t *__restrict__ tiles,
+                                          const uint32_t *__restrict__ masks, const uint32_t *__restrict__ sures,
+                                          uint32_t item, uint32_t n_items, int cpt_log2) {
+    GEnt e;
+    e.tile = kNone;
+    e.mask = e.sure = 0u;
+    const uint32_t idx = item >> cpt_log2;
+    if (item < n_items && LCL_IN(idx, (int64_t)a.tiles_x * a.tiles_y)) {
+        e.tile = __ldg(tiles + idx);
+        e.mask = __ldg(masks + idx);
+        e.sure = __ldg(sures + idx);
+    }
+    return e;
+}
+
+// A front item's quad for this thread, loaded one item ahead: the entry's masks and the raw data --
+// positions when some stroke of the item is not sure, else the coverage word -- with nothing that
+// waits for them (the coverage bits are taken out when the item is processed).
 struct GItem {
     int64_t l;  // -1: no quad for this thread (the masks are still the item's)
-    uint32_t mask, sure, cov;
+    uint32_t mask, sure, cw;
     int4 X, Y, Z;
 };
 
-__device__ __forceinline__ GItem load_gitem(const AtlasDev &a, const uint32_t *__restrict__ tiles,
-                                            const uint32_t *__restrict__ masks, const uint32_t *__restrict__ sures,
-                                            uint32_t item, int cpt_log2, int32_t qpr, int32_t nq) {
+__device__ __forceinline__ GItem load_gquad(const AtlasDev &a, const GEnt &e, uint32_t item, int cpt_log2,
+                                            int32_t qpr, int32_t nq) {
     GItem it;
     it.l = -1;
-    it.mask = it.sure = it.cov = 0u;
-    const int64_t n_tiles = (int64_t)a.tiles_x * a.tiles_y;
-    (void)n_tiles;
-    const uint32_t idx = item >> cpt_log2;
-    if (!LCL_IN(idx, n_tiles)) return it;
-    const uint32_t tile = __ldg(tiles + idx);
-    it.mask = __ldg(masks + idx);
-    it.sure = __ldg(sures + idx);
+    it.mask = e.mask;
+    it.sure = e.sure;
+    it.cw = 0u;
+    it.X = it.Y = it.Z = make_int4(INT32_MIN, 0, 0, 0);
+    if (e.tile == kNone) return it;
     const int32_t qd = (int32_t)((item & ((1u << cpt_log2) - 1)) * kThreads + threadIdx.x);
-    const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int32_t tx = e.tile % a.tiles_x, ty = e.tile / a.tiles_x;
     const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
     const int64_t n_tex = (int64_t)a.w * a.h;
     (void)n_tex;
@@ -399,13 +416,20 @@ __device__ __forceinline__ GItem load_gitem(const AtlasDev &a, const uint32_t *_
             it.X = __ldg(reinterpret_cast<const int4 *>(a.px + it.l));
             it.Y = __ldg(reinterpret_cast<const int4 *>(a.py + it.l));
             it.Z = __ldg(reinterpret_cast<const int4 *>(a.pz + it.l));
-            it.cov = (it.X.x != INT32_MIN ? 1u : 0u) | (it.X.y != INT32_MIN ? 2u : 0u) |
-                     (it.X.z != INT32_MIN ? 4u : 0u) | (it.X.w != INT32_MIN ? 8u : 0u);
         } else if (LCL_IN(it.l >> 5, (n_tex + 31) >> 5)) {
-            it.cov = (__ldg(a.cover + (it.l >> 5)) >> (it.l & 31)) & 0xFu;
+            it.cw = __ldg(a.cover + (it.l >> 5));
         }
     }
     return it;
+}
+
+// The quad's coverage bits (bit k: texel k) from its raw data.
+__device__ __forceinline__ uint32_t gquad_cov(const GItem &it) {
+    if (it.l < 0) return 0u;
+    if (it.mask & ~it.sure)
+        return (it.X.x != INT32_MIN ? 1u : 0u) | (it.X.y != INT32_MIN ? 2u : 0u) | (it.X.z != INT32_MIN ? 4u : 0u) |
+               (it.X.w != INT32_MIN ? 8u : 0u);
+    return (it.cw >> (it.l & 31)) & 0xFu;
 }
 
 template <typename L>
@@ -428,18 +452,19 @@ __global__ void __launch_bounds__(kThreads, 5) k_group_apply(AtlasDev a, L *__re
     const int32_t qpr = a.T / 4, nq = a.T * qpr;
     const int cpt_log2 = nq > kThreads ? 31 - __clz(nq / kThreads) : 0;
     const uint32_t n_items = counters[0] << cpt_log2;
+    // entries two items ahead, quads one item ahead: the position loads of the next item are issued
+    // as soon as this item starts, from an entry that arrived during the previous one
     uint32_t item = blockIdx.x;
-    GItem cur;
-    cur.l = -1;
-    if (item < n_items) cur = load_gitem(a, tiles, masks, sures, item, cpt_log2, qpr, nq);
+    GItem cur = load_gquad(a, load_gent(a, tiles, masks, sures, item, n_items, cpt_log2), item, cpt_log2, qpr, nq);
+    GEnt e1 = load_gent(a, tiles, masks, sures, item + gridDim.x, n_items, cpt_log2);
     for (; item < n_items; item += gridDim.x) {
         const uint32_t after = item + gridDim.x;
-        GItem next;
-        next.l = -1;
-        if (after < n_items) next = load_gitem(a, tiles, masks, sures, after, cpt_log2, qpr, nq);
+        const GEnt e2 = load_gent(a, tiles, masks, sures, after + gridDim.x, n_items, cpt_log2);
+        const GItem next = load_gquad(a, e1, after, cpt_log2, qpr, nq);
+        e1 = e2;
         const int32_t xs[4] = {cur.X.x, cur.X.y, cur.X.z, cur.X.w}, ys[4] = {cur.Y.x, cur.Y.y, cur.Y.z, cur.Y.w},
                       zs[4] = {cur.Z.x, cur.Z.y, cur.Z.z, cur.Z.w};
-        const uint32_t cov = cur.l >= 0 ? cur.cov : 0u;
+        const uint32_t cov = gquad_cov(cur);
         const int ks = cur.sure ? 31 - __clz(cur.sure) : -1;  // the newest stroke containing the tile
         uint32_t open = cov;
         uint32_t lab[4] = {0u, 0u, 0u, 0u};
@@ -490,7 +515,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_group_apply(AtlasDev a, L *__re
                     for (uint32_t m = cur.sure; m; m &= m - 1) atomicAdd(&s_hits[__ffs(m) - 1], (unsigned long long)c);
             }
         }
-        const uint32_t written = cur.l >= 0 ? (cur.cov & ~open) : 0u;
+        const uint32_t written = cov & ~open;
         if (written && LCL_IN(cur.l + 3, n_tex)) store_labels<L>(layer, cur.l, written, lab);
         cur = next;
     }
@@ -501,11 +526,22 @@ __global__ void __launch_bounds__(kThreads, 5) k_group_apply(AtlasDev a, L *__re
         const int64_t cap = (int64_t)a.tiles_x * a.tiles_y;
         const int32_t wpr = a.T >> 5, words = a.T * wpr;
         const uint32_t warps = gridDim.x * (kThreads / 32);
-        for (uint32_t b = (gridDim.x - 1 - blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); b < n_back; b += warps) {
-            const int64_t idx = cap - 1 - (int64_t)b;
-            if (!LCL_IN(idx, cap)) break;
-            const uint32_t tile = __ldg(tiles + idx), mask = __ldg(masks + idx);
-            if (!mask) continue;  // uniform over the warp
+        // the next tile's entry is loaded one tile ahead
+        auto entry = [&](uint32_t bb, uint32_t &t, uint32_t &m) {
+            t = kNone;
+            m = 0u;
+            if (bb < n_back && LCL_IN(cap - 1 - (int64_t)bb, cap)) {
+                t = __ldg(tiles + (cap - 1 - (int64_t)bb));
+                m = __ldg(masks + (cap - 1 - (int64_t)bb));
+            }
+        };
+        uint32_t b = (gridDim.x - 1 - blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
+        uint32_t next_tile, next_mask;
+        entry(b, next_tile, next_mask);
+        for (; b < n_back; b += warps) {
+            const uint32_t tile = next_tile, mask = next_mask;
+            entry(b + warps, next_tile, next_mask);
+            if (!mask || tile == kNone) continue;  // uniform over the warp
             const uint32_t label = g.s[31 - __clz(mask)].label;
             const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
             uint32_t c = 0u;
