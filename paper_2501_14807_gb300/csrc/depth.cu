@@ -48,8 +48,11 @@ struct DepthArgs {
     int64_t big_cap;
 };
 
+// A set-up triangle.  Snapped corners lie within the guard band (|X|, |Y| <= 2^28 sub-pixels) and
+// pixel centres within [0, 2^22), so coordinate differences fit in 32 bits and the edge functions
+// are 32 x 32 -> 64-bit products.
 struct DTri {
-    int64_t X[3], Y[3];
+    int32_t X[3], Y[3];
     float Z[3];
     int64_t A;
 };
@@ -100,10 +103,10 @@ __device__ bool depth_setup(const DepthArgs &a, int64_t t, DTri &d) {
         d.Y[k] = p.Y;
         d.Z[k] = p.z;
     }
-    d.A = edge_fn(d.X[0], d.Y[0], d.X[1], d.Y[1], d.X[2], d.Y[2]);
+    d.A = edge_fn32(d.X[0], d.Y[0], d.X[1], d.Y[1], d.X[2], d.Y[2]);
     if (d.A == 0) return false;
     if (d.A < 0) {
-        int64_t tx = d.X[1], ty = d.Y[1];
+        int32_t tx = d.X[1], ty = d.Y[1];
         float tz = d.Z[1];
         d.X[1] = d.X[2]; d.Y[1] = d.Y[2]; d.Z[1] = d.Z[2];
         d.X[2] = tx; d.Y[2] = ty; d.Z[2] = tz;
@@ -128,10 +131,10 @@ __device__ __forceinline__ void pixel_range(const DTri &d, int32_t w, int32_t h,
 
 // Depth of the pixel centre (px, py) if covered; writes it with atomicMin.
 __device__ __forceinline__ void depth_pixel(const DTri &d, int64_t i, int64_t j, int32_t w, int32_t h, uint32_t *depth) {
-    const int64_t px = 256 * i + 128, py = 256 * j + 128;
-    const int64_t w0 = edge_fn(d.X[1], d.Y[1], d.X[2], d.Y[2], px, py);
-    const int64_t w1 = edge_fn(d.X[2], d.Y[2], d.X[0], d.Y[0], px, py);
-    const int64_t w2 = edge_fn(d.X[0], d.Y[0], d.X[1], d.Y[1], px, py);
+    const int32_t px = 256 * (int32_t)i + 128, py = 256 * (int32_t)j + 128;
+    const int64_t w0 = edge_fn32(d.X[1], d.Y[1], d.X[2], d.Y[2], px, py);
+    const int64_t w1 = edge_fn32(d.X[2], d.Y[2], d.X[0], d.Y[0], px, py);
+    const int64_t w2 = edge_fn32(d.X[0], d.Y[0], d.X[1], d.Y[1], px, py);
     if (w0 + edge_bias(d.X[2] - d.X[1], d.Y[2] - d.Y[1]) <= 0) return;
     if (w1 + edge_bias(d.X[0] - d.X[2], d.Y[0] - d.Y[2]) <= 0) return;
     if (w2 + edge_bias(d.X[1] - d.X[0], d.Y[1] - d.Y[0]) <= 0) return;
