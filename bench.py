@@ -341,6 +341,7 @@ def run_ours(args):
     # texels per step (identical every step: the same strokes on the same atlas)
     sph_hits = sum(int(h[:len(r)].sum().item()) for h, r in zip(sphere_hits, per_layer))
     las_hits = int(lasso_hits[:len(w.lassos)].sum().item())
+    las_each = [int(x) for x in lasso_hits[:len(w.lassos)].tolist()]  # per lasso, in launch order
     texels = sph_hits + las_hits + (len(w.overlays) + w.n_layers) * W * rows
 
     clocks = Clocks(local)
@@ -453,7 +454,7 @@ def run_ours(args):
         "serving": serving,
         "batch": batch,
         "breakdown": {"sphere_ms_per_step": sph_ms / args.steps, "sphere_hit_texels": sph_hits,
-                      "lasso_hit_texels": las_hits, "texels_per_step": texels},
+                      "lasso_hit_texels": las_hits, "lasso_hit_texels_each": las_each, "texels_per_step": texels},
         "rows": row_rooflines(w, row_ms, args.steps, sph_bytes, sph_hits, las_hits, peak),
         "sphere_group_bytes": {"groups": n_groups, "bytes": grp_bytes,
                                "gb_s": grp_bytes / (sph_ms / args.steps / 1e3) / 1e9},
@@ -630,7 +631,7 @@ def run_batch(args):
     r = batch_summary(args.models or 256, args.steps, args.warmup, torch_device=0)
     line = {"metric": METRIC, "value": r["batched"]["gtexels_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["batched"]["ms"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": r.pop("config"), "gpu_launches": 3}
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": r.pop("config"), "gpu_launches": 4}
     line.update(r)
     print(json.dumps(line), flush=True)
 
@@ -746,7 +747,7 @@ def batch_summary(n_models, steps, warmup, torch_device=0):
                                    f"per model)", "mode": "batched launch (descriptor upload + CUDA graph replay "
                                                           "of the tuned shape) vs per-model per-stroke calls"},
             "batched": {"ms": bat_ms, "gtexels_s": hits / (bat_ms / 1e3) / 1e9, "config": tuned.as_dict(),
-                        "graph": True, "launches": 3},
+                        "graph": True, "launches": 4},
             "batched_default_shape": {"ms": def_ms, "config": lcl.batch_config().as_dict(), "graph": False},
             "upload_host_ms": upload_host_ms,
             "autotune": {"best_ms": tune_ms, "candidates": "threads 64/128/256 x split 1/2/4/8 x CTAs/SM all/half"},

@@ -373,8 +373,9 @@ lcl_status lcl_batch_upload(const lcl_batch_limits *limits, const lcl_batch_mode
 /* Edits the models of the batch last uploaded to `workspace`: every model's queued strokes are
  * applied to its layer in queue order, with results identical to calling lcl_select_sphere /
  * lcl_select_lasso once per stroke in that order (Section 4.3.1 applied per stroke; batching is a
- * serving-side schedule the paper does not discuss).  One cull launch gives every touched tile of
- * every model a mask of the strokes that can reach it; one persistent apply launch takes
+ * serving-side schedule the paper does not discuss).  Two cull launches give every touched tile of
+ * every model a mask of the strokes that can reach it (tested per (super-tile, stroke) pair, then
+ * compacted into work items); one persistent apply launch takes
  * (model, tile part) units from a work queue, loads each texel's position once and evaluates its
  * masked strokes from the newest down, stopping at the first that selects it (the label the
  * sequence leaves).  No host-to-device copy and a launch shape fixed by (limits, config): the call

@@ -1,13 +1,15 @@
 // batch.cu -- batched edits: many models, each with a queue of sphere and lasso strokes, edited
-// by one cull launch and one persistent apply launch (capturable in a CUDA graph).
+// by two cull launches and one persistent apply launch (capturable in a CUDA graph).
 //
 // The paper edits one layer of one model per operation (Section 4.3.1).  A server holding many
 // models batches their queued strokes instead: the result must equal applying each model's
 // strokes one by one, in queue order, so
-//   k_batch_cull   gives every tile of every model a 64-bit mask of the model's queued strokes
-//                  (queue order = bit order) whose conservative box test can reach the tile; the
-//                  super-tile's mask is computed first and only its strokes are tested per tile;
-//                  tiles with a non-empty mask become work items (model, tile, mask);
+//   k_batch_pairs  gives every tile of every model a 64-bit mask of the model's queued strokes
+//                  (queue order = bit order) whose conservative box test can reach the tile, and
+//                  of those a `sure` mask (spheres containing the tile, lassos inside whose polygon
+//                  it lies): a CTA per (super-tile, stroke) unit, a thread per tile, the bits ORed
+//                  into per-tile masks, so one super-tile's strokes are tested in parallel;
+//   k_batch_compact turns every tile with a non-empty mask into a work item (model, tile, masks);
 //   k_batch_apply  takes (item, part) units from a work queue (one atomic per unit and CTA); a
 //                  thread loads its four texels' positions once and evaluates the masked strokes
 //                  from the newest down: the first stroke that selects a texel is the last one
@@ -22,8 +24,8 @@
 // sequential single-stroke calls.
 //
 // The host uploads compact descriptors (models, strokes, each lasso's camera and polygon);
-// k_batch_prep builds the lassos' culling boxes and y-band edge lists on the device, one warp per
-// lasso.  Workspace layout and launch shape depend only on the limits (capacities) and the config,
+// k_batch_prep clears the tile masks and builds the lassos' culling boxes and y-band edge lists on
+// the device, one warp per lasso.  Workspace layout and launch shape depend only on the limits (capacities) and the config,
 // and the kernels read the batch's counts from the workspace header, so the launch is independent
 // of the batch's contents: it can be captured once in a CUDA graph and replayed after each upload.
 #include <cstring>
@@ -39,6 +41,7 @@ struct BModel {
     int32_t dtype_bytes;
     int32_t s0, ns;   // this model's strokes: [s0, s0 + ns) of the batch's stroke array, ns <= 64
     int32_t super0;   // first flattened super-tile of this model
+    int64_t tile0;    // first flattened tile of this model (index into the tile masks)
 };
 
 struct BStroke {
@@ -88,15 +91,15 @@ __device__ __forceinline__ bool stroke_in_bounds(const BStroke *strokes, int64_t
 // k_batch_prep at every launch.
 struct BHdr {
     int32_t n_models, n_strokes, n_lassos, n_supers;
-    unsigned int n_items;          // written by k_batch_cull
-    unsigned int pad;
+    unsigned int n_items;          // written by k_batch_compact
+    unsigned int n_tiles;          // tiles of the batch's models (the tile masks in use)
     unsigned long long next_unit;  // work queue of k_batch_apply
 };
 
 // Workspace: [hdr | models | strokes | lasso inputs | super-tile -> model] is uploaded (the
-// staging holds its image); [lassos | items] is written by the kernels.
+// staging holds its image); [lassos | items | tile masks] is written by the kernels.
 struct BLayout {
-    size_t hdr, models, strokes, lasso_in, super_model, upload, lassos, items, total;
+    size_t hdr, models, strokes, lasso_in, super_model, upload, lassos, items, tmask, total;
 };
 
 BLayout b_layout(const lcl_batch_limits &lim) {
@@ -109,7 +112,8 @@ BLayout b_layout(const lcl_batch_limits &lim) {
     L.upload = L.super_model + align256((size_t)std::max<int64_t>(lim.supers, 1) * 4);
     L.lassos = L.upload;
     L.items = L.lassos + align256((size_t)std::max(lim.lassos, 1) * sizeof(BLasso));
-    L.total = L.items + align256((size_t)std::max<int64_t>(lim.tiles, 1) * sizeof(BItem));
+    L.tmask = L.items + align256((size_t)std::max<int64_t>(lim.tiles, 1) * sizeof(BItem));
+    L.total = L.tmask + align256((size_t)std::max<int64_t>(lim.tiles, 1) * sizeof(ulonglong2));
     return L;
 }
 
@@ -142,16 +146,21 @@ __device__ __forceinline__ bool stroke_may_reach(const BStroke &st, const BLasso
 constexpr int kPrepWarps = kThreads / 32;  // lassos per CTA of k_batch_prep
 static_assert(kBands == 32, "k_batch_prep gives each y-band one lane");
 
-// Resets the work counters and builds every lasso's argument, one warp per lasso: lane 0 the
+// Resets the work counters and the tile masks and builds every lasso's argument, one warp per
+// lasso: lane 0 the
 // head (bounding boxes, band mapping), then lane b counts and lists the edges of band b (the
 // same predicate, in the same edge order, as the host builder).
 __global__ void __launch_bounds__(kThreads) k_batch_prep(BHdr *hdr, const BLassoIn *__restrict__ in,
-                                                         BLasso *__restrict__ out, BCaps caps) {
+                                                         BLasso *__restrict__ out, ulonglong2 *__restrict__ tmask,
+                                                         BCaps caps) {
     pdl_allow_next();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         hdr->n_items = 0;
         hdr->next_unit = 0;
     }
+    const int64_t n_tiles = hdr->n_tiles;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tiles; t += (int64_t)gridDim.x * blockDim.x)
+        if (LCL_IN(t, caps.tiles)) tmask[t] = make_ulonglong2(0ull, 0ull);
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * kPrepWarps + (int)(threadIdx.x / 32);
     if (j >= hdr->n_lassos) return;  // uniform over the warp
@@ -182,14 +191,79 @@ __global__ void __launch_bounds__(kThreads) k_batch_prep(BHdr *hdr, const BLasso
         if (lasso_band_has(p, lane, e, bh)) p.band_edge[k++] = (uint8_t)e;
 }
 
-__global__ void __launch_bounds__(kThreads) k_batch_cull(const BHdr *__restrict__ hdr, const BModel *__restrict__ models,
-                                                         const BStroke *__restrict__ strokes,
-                                                         const BLasso *__restrict__ lassos,
-                                                         const uint32_t *__restrict__ super_model, BItem *items,
-                                                         unsigned int *n_items, BCaps caps) {
-    pdl_wait();
+// Masks of one (super-tile, stroke) unit: unit u is super-tile u / 64 of the batch and stroke u % 64
+// of its model, so the tile tests of one super-tile and all its strokes run in parallel (a thread
+// per tile, a CTA per unit) rather than one after another in one thread.  A stroke whose test can
+// reach the super-tile tests each of its 256 tiles and ORs its bit into the tile's mask (and, for an
+// exact class, into `sure`).
+__global__ void __launch_bounds__(kThreads) k_batch_pairs(const BHdr *__restrict__ hdr,
+                                                          const BModel *__restrict__ models,
+                                                          const BStroke *__restrict__ strokes,
+                                                          const BLasso *__restrict__ lassos,
+                                                          const uint32_t *__restrict__ super_model,
+                                                          ulonglong2 *__restrict__ tmask, BCaps caps) {
+    pdl_wait();  // the tile masks are cleared and the lassos built
     pdl_allow_next();
-    __shared__ unsigned long long s_mask;
+    __shared__ int s_reach;
+    const int64_t n_units = (int64_t)hdr->n_supers * 64;
+    for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {  // uniform over the CTA
+        const int32_t g = (int32_t)(u >> 6), k = (int32_t)(u & 63);
+        if (!LCL_IN(g, caps.supers)) break;
+        const uint32_t mi = super_model[g];
+        if (!LCL_IN(mi, caps.models)) continue;
+        const BModel &M = models[mi];
+        if (k >= M.ns) continue;
+        if (!stroke_in_bounds(strokes, (int64_t)M.s0 + k, caps)) continue;
+        const AtlasDev &a = M.a;
+        const int32_t sidx = g - M.super0;
+        if (!LCL_IN(sidx, (int64_t)a.supers_x * a.supers_y)) continue;
+        const int32_t sx = sidx % a.supers_x, sy = sidx / a.supers_x;
+        const BStroke &st = strokes[M.s0 + k];
+        __syncthreads();  // s_reach of the previous unit has been read
+        if (threadIdx.x == 0) s_reach = stroke_may_reach(st, lassos, a.super_box, a.supers_x, a.supers_y, sx, sy);
+        __syncthreads();
+        if (!s_reach) continue;
+        const int32_t tx = sx * LCL_SUPER + (threadIdx.x % LCL_SUPER);
+        const int32_t ty = sy * LCL_SUPER + (threadIdx.x / LCL_SUPER);
+        if (tx >= a.tiles_x || ty >= a.tiles_y) continue;
+        const int64_t tile = (int64_t)ty * a.tiles_x + tx;
+        bool hit = false, sure = false;
+        if (!stroke_pads(st, lassos) && LCL_IN(tile, (int64_t)a.tiles_x * a.tiles_y)) {
+            // unpadded: the tile's own box decides, with its exact class
+            const int4 *b = reinterpret_cast<const int4 *>(a.tile_box + 8 * tile);
+            const int4 lo = b[0], hi = b[1];
+            if (lo.w == 0) continue;
+            if (st.kind == LCL_STROKE_SPHERE) {
+                hit = box_dist2(lo, hi, st.sphere) <= st.sphere.r2;
+                sure = hit && box_far2(lo, hi, st.sphere) <= st.sphere.r2;
+            } else {
+                const BLasso &L = lassos[st.lasso];
+                float4 sb;
+                if (box_may_touch(L.arg, lo, hi, L.depth, &sb)) {
+                    const int cls = lasso_tile_class8<1>(L.arg, L.arg.vx, L.arg.vy, sb);
+                    hit = cls != kTileOut;
+                    sure = cls == kTileIn;
+                }
+            }
+        } else {
+            hit = stroke_may_reach(st, lassos, a.tile_box, a.tiles_x, a.tiles_y, tx, ty);
+        }
+        if (hit && LCL_IN(M.tile0 + tile, caps.tiles)) {
+            atomicOr(&tmask[M.tile0 + tile].x, 1ull << k);
+            if (sure) atomicOr(&tmask[M.tile0 + tile].y, 1ull << k);
+        }
+    }
+}
+
+// Work items: every tile whose mask is not empty becomes (model, tile, mask, sure); a CTA per
+// super-tile, a thread per tile.
+__global__ void __launch_bounds__(kThreads) k_batch_compact(const BHdr *__restrict__ hdr,
+                                                            const BModel *__restrict__ models,
+                                                            const uint32_t *__restrict__ super_model,
+                                                            const ulonglong2 *__restrict__ tmask, BItem *items,
+                                                            unsigned int *n_items, BCaps caps) {
+    pdl_wait();  // the masks are complete
+    pdl_allow_next();
     const int32_t n_supers = hdr->n_supers;
     for (int32_t g = blockIdx.x; g < n_supers; g += gridDim.x) {
         if (!LCL_IN(g, caps.supers)) break;  // uniform over the CTA
@@ -199,49 +273,13 @@ __global__ void __launch_bounds__(kThreads) k_batch_cull(const BHdr *__restrict_
         const AtlasDev &a = M.a;
         const int32_t sidx = g - M.super0;
         if (!LCL_IN(sidx, (int64_t)a.supers_x * a.supers_y)) continue;
-        if (threadIdx.x == 0) s_mask = 0ull;
-        __syncthreads();
         const int32_t sx = sidx % a.supers_x, sy = sidx / a.supers_x;
-        // strokes that can reach the super-tile, one thread per stroke (ns <= 64)
-        if (threadIdx.x < (unsigned)M.ns && stroke_in_bounds(strokes, (int64_t)M.s0 + threadIdx.x, caps) &&
-            stroke_may_reach(strokes[M.s0 + threadIdx.x], lassos, a.super_box, a.supers_x, a.supers_y, sx, sy))
-            atomicOr(&s_mask, 1ull << threadIdx.x);
-        __syncthreads();
-        const unsigned long long smask = s_mask;
-        __syncthreads();
-        if (smask == 0ull) continue;  // uniform over the CTA
         const int32_t tx = sx * LCL_SUPER + (threadIdx.x % LCL_SUPER);
         const int32_t ty = sy * LCL_SUPER + (threadIdx.x / LCL_SUPER);
-        unsigned long long mask = 0ull, sure = 0ull;
-        if (tx < a.tiles_x && ty < a.tiles_y) {
-            for (unsigned long long m = smask; m; m &= m - 1) {
-                const int k = __ffsll((long long)m) - 1;
-                if (!stroke_in_bounds(strokes, (int64_t)M.s0 + k, caps)) continue;
-                const BStroke &st = strokes[M.s0 + k];
-                if (!stroke_pads(st, lassos) && LCL_IN((int64_t)ty * a.tiles_x + tx, (int64_t)a.tiles_x * a.tiles_y)) {
-                    // unpadded: the tile's own box decides, with its exact class
-                    const int4 *b = reinterpret_cast<const int4 *>(a.tile_box + 8 * ((int64_t)ty * a.tiles_x + tx));
-                    const int4 lo = b[0], hi = b[1];
-                    if (lo.w == 0) continue;
-                    if (st.kind == LCL_STROKE_SPHERE) {
-                        if (box_dist2(lo, hi, st.sphere) > st.sphere.r2) continue;
-                        mask |= 1ull << k;
-                        if (box_far2(lo, hi, st.sphere) <= st.sphere.r2) sure |= 1ull << k;
-                    } else {
-                        const BLasso &L = lassos[st.lasso];
-                        float4 sb;
-                        if (!box_may_touch(L.arg, lo, hi, L.depth, &sb)) continue;
-                        const int cls = lasso_tile_class8<1>(L.arg, L.arg.vx, L.arg.vy, sb);
-                        if (cls == kTileOut) continue;
-                        mask |= 1ull << k;
-                        if (cls == kTileIn) sure |= 1ull << k;
-                    }
-                } else if (stroke_may_reach(st, lassos, a.tile_box, a.tiles_x, a.tiles_y, tx, ty)) {
-                    mask |= 1ull << k;
-                }
-            }
-        }
-        const bool cand = mask != 0ull;
+        ulonglong2 m = make_ulonglong2(0ull, 0ull);
+        const int64_t tile = (int64_t)ty * a.tiles_x + tx;
+        if (tx < a.tiles_x && ty < a.tiles_y && LCL_IN(M.tile0 + tile, caps.tiles)) m = tmask[M.tile0 + tile];
+        const bool cand = m.x != 0ull;
         const uint32_t bal = __ballot_sync(0xffffffffu, cand);
         if (bal) {
             const int lane = threadIdx.x & 31;
@@ -252,9 +290,9 @@ __global__ void __launch_bounds__(kThreads) k_batch_cull(const BHdr *__restrict_
             if (cand && LCL_IN(slot, caps.tiles)) {
                 BItem it;
                 it.model = mi;
-                it.tile = (uint32_t)(ty * a.tiles_x + tx);
-                it.mask = mask;
-                it.sure = sure;
+                it.tile = (uint32_t)tile;
+                it.mask = m.x;
+                it.sure = m.y;
                 items[slot] = it;
             }
         }
@@ -529,6 +567,7 @@ struct BPtrs {
     BLasso *lassos;
     const uint32_t *super_model;
     BItem *items;
+    ulonglong2 *tmask;
 };
 
 BPtrs b_ptrs(const BLayout &L, void *ws) {
@@ -541,6 +580,7 @@ BPtrs b_ptrs(const BLayout &L, void *ws) {
     p.lassos = reinterpret_cast<BLasso *>(base + L.lassos);
     p.super_model = reinterpret_cast<const uint32_t *>(base + L.super_model);
     p.items = reinterpret_cast<BItem *>(base + L.items);
+    p.tmask = reinterpret_cast<ulonglong2 *>(base + L.tmask);
     return p;
 }
 
@@ -552,13 +592,19 @@ cudaError_t launch_kernels(const BPtrs &p, const lcl_batch_limits &lim, const lc
     caps.pad = 0;
     caps.supers = lim.supers;
     caps.tiles = lim.tiles;
-    const int pg = (std::max(lim.lassos, 1) + kPrepWarps - 1) / kPrepWarps;
-    k_batch_prep<<<pg, kThreads, 0, st>>>(p.hdr, p.lasso_in, p.lassos, caps);
+    // enough CTAs for the lassos (a warp each) and for clearing the tile masks
+    const int pg = (int)std::max<int64_t>((std::max(lim.lassos, 1) + kPrepWarps - 1) / kPrepWarps,
+                                          std::min<int64_t>((lim.tiles + kThreads - 1) / kThreads, 4 * sm_count()));
+    k_batch_prep<<<pg, kThreads, 0, st>>>(p.hdr, p.lasso_in, p.lassos, p.tmask, caps);
     cudaError_t e = cudaSuccess;
     if (lim.supers > 0) {
-        const int cg = (int)std::min<int64_t>(lim.supers, resident_grid(k_batch_cull));
-        e = launch_pdl(k_batch_cull, dim3(cg), st, (const BHdr *)p.hdr, p.models, p.strokes, p.lassos, p.super_model,
-                       p.items, &p.hdr->n_items, caps);
+        const int ug = (int)std::min<int64_t>(lim.supers * 64, resident_grid(k_batch_pairs));
+        e = launch_pdl(k_batch_pairs, dim3(ug), st, (const BHdr *)p.hdr, p.models, p.strokes, p.lassos, p.super_model,
+                       p.tmask, caps);
+        const int cg = (int)std::min<int64_t>(lim.supers, resident_grid(k_batch_compact));
+        if (e == cudaSuccess)
+            e = launch_pdl(k_batch_compact, dim3(cg), st, (const BHdr *)p.hdr, p.models, p.super_model,
+                           (const ulonglong2 *)p.tmask, p.items, &p.hdr->n_items, caps);
         if (e == cudaSuccess) {
             const int fit = resident_per_sm(k_batch_apply, c.threads);
             const int per_sm = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, fit) : fit;
@@ -567,7 +613,7 @@ cudaError_t launch_kernels(const BPtrs &p, const lcl_batch_limits &lim, const lc
                                  (int32_t)c.split, caps);
         }
     }
-    count_launches(lim.supers > 0 ? 3 : 1);
+    count_launches(lim.supers > 0 ? 4 : 1);
     if (e == cudaSuccess) e = cudaGetLastError();
     return e;
 }
@@ -623,10 +669,12 @@ lcl_status batch_upload_impl(const lcl_batch_limits *lim, const lcl_batch_model 
     hdr.n_strokes = n_strokes;
     hdr.n_lassos = n_lassos;
     hdr.n_supers = (int32_t)n_supers;
+    hdr.n_tiles = (uint32_t)n_tiles;
     std::memcpy(img + L.hdr, &hdr, sizeof(hdr));
     BModel *bm = reinterpret_cast<BModel *>(img + L.models);
     uint32_t *super_model = reinterpret_cast<uint32_t *>(img + L.super_model);
     int32_t super0 = 0;
+    int64_t tile0 = 0;
     for (int32_t i = 0; i < n_models; ++i) {
         const lcl_batch_model &m = models[i];
         BModel d;
@@ -637,7 +685,9 @@ lcl_status batch_upload_impl(const lcl_batch_limits *lim, const lcl_batch_model 
         d.s0 = m.first_stroke;
         d.ns = m.n_strokes;
         d.super0 = super0;
+        d.tile0 = tile0;
         bm[i] = d;
+        tile0 += (int64_t)m.atlas->tiles_x * m.atlas->tiles_y;
         const int32_t nsup = m.atlas->supers_x * m.atlas->supers_y;
         for (int32_t k = 0; k < nsup; ++k) super_model[super0 + k] = (uint32_t)i;
         super0 += nsup;
