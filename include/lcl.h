@@ -216,11 +216,11 @@ lcl_status lcl_select_sphere(const lcl_atlas *atlas, void *layer, lcl_dtype dtyp
  * risk an allocation failure in the middle of a stroke.  (The paper has no counterpart: it edits
  * through the graphics pipeline, which keeps its own buffers.)
  * Same arguments, results and errors as lcl_select_sphere, whose work it does (its argument checks
- * run first), except that the scratch space (candidate counters and three tile lists, about 3 MiB)
+ * run first), except that the scratch space (candidate counters and six tile lists, about 6 MiB)
  * is a fixed array compiled into the library, and the limits below.
  * Memory: the array belongs to the module of the library that holds it.  CUDA loads that module
  * into a context on first use, so the first call in each context (each device, or each context a
- * host application creates) loads it and allocates the ~3 MiB there; that first call can fail
+ * host application creates) loads it and allocates the ~6 MiB there; that first call can fail
  * with LCL_ERR_CUDA (out of memory).  Make it once, before the stroke loop and before any stream
  * capture; from then on the array stays until the context ends, and no call allocates or frees
  * anything.  Every call looks up the array's address in the current context (cudaGetSymbolAddress,

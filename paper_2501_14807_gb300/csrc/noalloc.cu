@@ -18,10 +18,11 @@ namespace {
 
 constexpr int32_t kStaticMaxStrokes = LCL_STATIC_MAX_STROKES;
 constexpr int64_t kStaticMaxTiles = LCL_STATIC_MAX_TILES;
-// Candidate counters (two per stroke) and three candidate-tile lists, laid out as the workspace
-// of lcl_select_sphere for kStaticMaxStrokes strokes on an atlas of kStaticMaxTiles tiles.
+// Candidate counters (two per stroke) and six tile lists (three for per-stroke candidates, three
+// more for the second item set of grouped calls), laid out as the workspace of lcl_select_sphere for
+// kStaticMaxStrokes strokes on an atlas of kStaticMaxTiles tiles.
 constexpr size_t kStaticScratchBytes =
-    ((size_t(2) * (kStaticMaxStrokes + 1) * 4 + 255) & ~size_t(255)) + 3 * size_t(kStaticMaxTiles) * 4;
+    ((size_t(2) * (kStaticMaxStrokes + 1) * 4 + 255) & ~size_t(255)) + 6 * size_t(kStaticMaxTiles) * 4;
 
 static __device__ __align__(256) unsigned char g_sphere_scratch[kStaticScratchBytes];
 

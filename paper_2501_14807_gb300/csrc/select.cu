@@ -323,10 +323,15 @@ __device__ __forceinline__ void append_item(bool front, bool back, uint32_t tile
     }
 }
 
+// ahead = 1 (every group but a call's first): the lists this cull writes were last read by the apply
+// two groups back, which had completed before the previous apply started, so the cull runs while the
+// previous group's apply is still writing the layer, and waits for it only at its end (the next
+// apply starts after this grid completes, hence after the previous apply).  The first group's cull
+// waits at once: its counters are being cleared by the grid before it.
 __global__ void __launch_bounds__(kThreads) k_group_cull(AtlasDev a, const __grid_constant__ GroupArg g,
                                                          uint32_t *counters, uint32_t *tiles, uint32_t *masks,
-                                                         uint32_t *sures) {
-    pdl_wait();  // the previous group's apply has read the lists
+                                                         uint32_t *sures, int ahead) {
+    if (!ahead) pdl_wait();
     __shared__ uint32_t s_mask;
     const int32_t n_super = a.supers_x * a.supers_y;
     const int64_t n_tiles = (int64_t)a.tiles_x * a.tiles_y;
@@ -364,6 +369,7 @@ __global__ void __launch_bounds__(kThreads) k_group_cull(AtlasDev a, const __gri
         const bool back = g.rows && mask != 0u && mask == sure;
         append_item(mask != 0u && !back, back, (uint32_t)tile, mask, sure, counters, tiles, masks, sures, n_tiles);
     }
+    if (ahead) pdl_wait();
     pdl_allow_next();
 }
 
@@ -817,6 +823,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_tool_apply(AtlasDev a, L *__res
 
 struct SelWs {
     uint32_t *counters, *list, *list2, *list3;  // three candidate lists: sphere stroke k uses list k mod 3
+    uint32_t *list4, *list5, *list6;            // calls of two or more strokes: a second item set for groups
 };
 
 SelWs sel_ws(const lcl_atlas *a, int32_t n, void *ws) {
@@ -827,6 +834,12 @@ SelWs sel_ws(const lcl_atlas *a, int32_t n, void *ws) {
     w.list = reinterpret_cast<uint32_t *>(base + align256((size_t)2 * (n + 1) * 4));
     w.list2 = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(w.list) + lb);
     w.list3 = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(w.list2) + lb);
+    w.list4 = w.list5 = w.list6 = nullptr;
+    if (n >= 2) {
+        w.list4 = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(w.list3) + lb);
+        w.list5 = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(w.list4) + lb);
+        w.list6 = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(w.list5) + lb);
+    }
     return w;
 }
 
@@ -966,7 +979,7 @@ lcl_status division_check_impl(uint64_t n, uint32_t seed, uint64_t *counts, cuda
 }
 
 size_t select_ws_bytes(const lcl_atlas *a, int32_t n) {
-    return align256((size_t)2 * (n + 1) * 4) + 3 * align256((size_t)a->tiles_x * a->tiles_y * 4);
+    return align256((size_t)2 * (n + 1) * 4) + (n >= 2 ? 6 : 3) * align256((size_t)a->tiles_x * a->tiles_y * 4);
 }
 
 // Unpadded strokes on a label layer, kGroup at a time (see k_group_apply): zeroing, then a cull and
@@ -988,11 +1001,13 @@ lcl_status select_sphere_grouped(const lcl_atlas *atlas, const AtlasDev &a, L *l
         g.n = std::min(kGroup, n - k0);
         for (int32_t k = 0; k < g.n; ++k) g.s[k] = arg(k0 + k);
         uint32_t *const c = w.counters + 2 * gi;
-        e = launch_pdl(k_group_cull, dim3(cull_grid), st, a, g, c, w.list, w.list2, w.list3);
+        // item sets alternate between groups, so a group's cull can run while the previous apply does
+        uint32_t *const t = (gi & 1) ? w.list4 : w.list, *const m = (gi & 1) ? w.list5 : w.list2,
+                        *const su = (gi & 1) ? w.list6 : w.list3;
+        e = launch_pdl(k_group_cull, dim3(cull_grid), st, a, g, c, t, m, su, gi > 0 ? 1 : 0);
         if (e == cudaSuccess)
             e = launch_pdl(k_group_apply<L>, dim3(apply_grid), st, a, layer, g, (const uint32_t *)c,
-                           (const uint32_t *)w.list, (const uint32_t *)w.list2, (const uint32_t *)w.list3,
-                           h ? h + k0 : nullptr);
+                           (const uint32_t *)t, (const uint32_t *)m, (const uint32_t *)su, h ? h + k0 : nullptr);
     }
     count_launches(1 + 2 * n_groups);
     if (e == cudaSuccess) e = cudaGetLastError();
