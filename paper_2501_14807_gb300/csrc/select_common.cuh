@@ -633,15 +633,20 @@ __device__ __forceinline__ uint32_t lasso_quad(const LassoArg &p, const LassoSha
         const float w = clip_row(p.m + 12, fx, fy, fz);
         if (!(w > 0.0f)) continue;
         const float cx = clip_row(p.m, fx, fy, fz);
-        if (cx < __fmul_rn(p.nx0, w) || cx > __fmul_rn(p.nx1, w)) continue;
+        if (!INSIDE && (cx < __fmul_rn(p.nx0, w) || cx > __fmul_rn(p.nx1, w))) continue;
         const float cy = clip_row(p.m + 4, fx, fy, fz);
-        if (cy < __fmul_rn(p.ny0, w) || cy > __fmul_rn(p.ny1, w)) continue;
+        if (!INSIDE && (cy < __fmul_rn(p.ny0, w) || cy > __fmul_rn(p.ny1, w))) continue;
         const float x = screen_of(div_rn(cx, w), p.ws);
         const float y = screen_of(div_rn(cy, w), p.hs);
-        if (!(x >= 0.0f && x < p.ws && y >= 0.0f && y < p.hs)) continue;
-        if (!(y >= p.ymin && y < p.ymax)) continue;
-        int b = __float2int_rz(__fmul_rn(__fsub_rn(y, p.band_y0), p.band_inv_h));
-        b = b < 0 ? 0 : (b >= kBands ? kBands - 1 : b);
+        // INSIDE: the tile's class already settles the viewport, the polygon's box and its y-range
+        // (the projected box widened by the margin lies on screen and inside the polygon)
+        if (!INSIDE && !(x >= 0.0f && x < p.ws && y >= 0.0f && y < p.hs)) continue;
+        if (!INSIDE && !(y >= p.ymin && y < p.ymax)) continue;
+        int b = 0;
+        if (!INSIDE) {
+            b = __float2int_rz(__fmul_rn(__fsub_rn(y, p.band_y0), p.band_inv_h));
+            b = b < 0 ? 0 : (b >= kBands ? kBands - 1 : b);
+        }
         xs[k] = x;
         ys[k] = y;
         cw[k] = w;
