@@ -403,14 +403,29 @@ __global__ void __launch_bounds__(kThreads, 4) k_resolve(const TriSetup *__restr
     // tiles of 32 texels or more on a width that is a multiple of 32: each warp's 32 texels are one
     // aligned coverage word (uniform over the grid)
     const bool aligned = T >= 32 && (w & 31) == 0;
+    // the triangle id of the thread's texel in step it + 1 is loaded during step it
+    auto texel = [&](int step, int32_t &x, int32_t &y, int64_t &l) {
+        const int32_t i = step * kThreads + threadIdx.x;
+        x = tx * T + (i % T);
+        y = ty * T + i / T;
+        const bool v = i < n_tex_tile && x < w && y < h && LCL_IN((int64_t)y * w + x, (int64_t)w * h);
+        l = v ? (int64_t)y * w + x : -1;
+    };
+    int32_t nx, ny;
+    int64_t nl;
+    texel(0, nx, ny, nl);
+    uint32_t nt = nl >= 0 ? __ldcs(tri_plane + nl) : kNone;
     for (int it = 0; it < iters; ++it) {
-        const int32_t i = it * kThreads + threadIdx.x;
-        const int32_t x = tx * T + (i % T), y = ty * T + i / T;
-        const bool valid = i < n_tex_tile && x < w && y < h && LCL_IN((int64_t)y * w + x, (int64_t)w * h);
-        const int64_t l = valid ? (int64_t)y * w + x : 0;
+        const int32_t x = nx, y = ny;
+        const bool valid = nl >= 0;
+        const int64_t l = valid ? nl : 0;
+        const uint32_t t = nt;
+        if (it + 1 < iters) {
+            texel(it + 1, nx, ny, nl);
+            nt = nl >= 0 ? __ldcs(tri_plane + nl) : kNone;
+        }
         bool covered = false;
         if (valid) {
-            const uint32_t t = __ldcs(tri_plane + l);
             int32_t ox = INT32_MIN, oy = 0, oz = 0;
             if (t != kNone && LCL_IN(t, n_tri)) {
                 const TriSetup s = setup[t];
