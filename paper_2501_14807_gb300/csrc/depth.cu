@@ -77,9 +77,10 @@ __global__ void k_vertex(const float *__restrict__ pos, int64_t n_pos, const Mat
     const float qz = (float)quantize_coord(pos[3 * v + 2], mn2, scale);
     const float cw = clip_row(m + 12, qx, qy, qz);
     if (cw > 0.0f) {
-        const float zn = __fdiv_rn(clip_row(m + 8, qx, qy, qz), cw);
-        const float xs = __fmul_rn(screen_of(__fdiv_rn(clip_row(m, qx, qy, qz), cw), fw), 256.0f);
-        const float ys = __fmul_rn(screen_of(__fdiv_rn(clip_row(m + 4, qx, qy, qz), cw), fh), 256.0f);
+        // div_rn: the correctly rounded quotient, the value of __fdiv_rn (checked by lcl_check_division)
+        const float zn = div_rn(clip_row(m + 8, qx, qy, qz), cw);
+        const float xs = __fmul_rn(screen_of(div_rn(clip_row(m, qx, qy, qz), cw), fw), 256.0f);
+        const float ys = __fmul_rn(screen_of(div_rn(clip_row(m + 4, qx, qy, qz), cw), fh), 256.0f);
         if (zn >= 0.0f && zn <= 1.0f && fabsf(xs) <= (float)kGuardSub && fabsf(ys) <= (float)kGuardSub) {
             r.X = (int32_t)__float2ll_rn(xs);
             r.Y = (int32_t)__float2ll_rn(ys);
@@ -129,6 +130,66 @@ __device__ __forceinline__ void pixel_range(const DTri &d, int32_t w, int32_t h,
     j1 = min(j1, (int64_t)h - 1);
 }
 
+// The depth of a covered pixel as the definition computes it: v = ((w0 z0 + w1 z1) + w2 z2) / A in
+// binary64 (each operation rounded), then rounded to binary32.  The FP64 pipe is slow on this part,
+// so the result is first decided in FP32 pairs:
+//  - w_k >= 0 and z_k >= 0 (a covered pixel), so no sum cancels and the binary64 result is within
+//    6 * 2^-53 (relative) of the exact x = sum w_k z_k / A (one rounding per operation);
+//  - w0 + w1 + w2 = A exactly, so with A < 2^24 every w_k and A are exact floats; each product is
+//    an exact pair (RN(w z), its error by FMA), the pairs' high parts are added exactly (TwoSum) and
+//    the rest rounds, and the quotient is qh = RN(sh / A) plus ql from the exact remainder:
+//    |qh + ql - x| <= 2^-44 x;
+//  - if qh + ql lies, with that margin and the binary64 one, strictly between the rounding boundaries
+//    around qh (half an ulp above, half an ulp below -- a quarter below a power of two), every value
+//    within the margins rounds to qh, the binary64 result included, so the result is qh.
+// Otherwise (near a boundary, about 2^-19 of the pixels, or A >= 2^24: triangles above 256 px^2)
+// the binary64 sequence itself runs.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {  // s + e = a + b exactly
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __noinline__ float depth_z_binary64(int64_t w0, int64_t w1, int64_t w2, float z0, float z1, float z2,
+                                               int64_t A) {
+    const double num = __dadd_rn(__dadd_rn(__dmul_rn(__ll2double_rn(w0), (double)z0), __dmul_rn(__ll2double_rn(w1), (double)z1)),
+                                 __dmul_rn(__ll2double_rn(w2), (double)z2));
+    return __double2float_rn(__ddiv_rn(num, __ll2double_rn(A)));
+}
+
+__device__ __forceinline__ float depth_z(int64_t w0, int64_t w1, int64_t w2, const DTri &d) {
+    if (d.A < (int64_t(1) << 24)) {
+        const float wf[3] = {__int2float_rn((int32_t)w0), __int2float_rn((int32_t)w1), __int2float_rn((int32_t)w2)};
+        float ph[3], pl[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            ph[k] = __fmul_rn(wf[k], d.Z[k]);
+            pl[k] = __fmaf_rn(wf[k], d.Z[k], -ph[k]);  // the product's rounding error, exactly
+        }
+        float a, e1, sh, e2;
+        two_sum(ph[0], ph[1], a, e1);
+        two_sum(a, ph[2], sh, e2);
+        float sl = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(pl[0], pl[1]), pl[2]));
+        const float t = __fadd_rn(sh, sl);  // renormalise (|sl| is far below sh)
+        sl = __fsub_rn(sl, __fsub_rn(t, sh));
+        sh = t;
+        if (sh == 0.0f) return 0.0f;  // every term is 0: x = 0 exactly
+        const float af = __int2float_rn((int32_t)d.A);
+        const float qh = div_rn(sh, af);
+        // sh - qh A is exactly representable (the remainder of a correctly rounded quotient)
+        const float ql = __fdividef(__fadd_rn(__fmaf_rn(-qh, af, sh), sl), af);
+        const uint32_t bits = __float_as_uint(qh);
+        const uint32_t eb = (bits >> 23) & 0xFFu;
+        if (eb > 26u && eb < 255u) {
+            const float half = __uint_as_float((eb - 24u) << 23);                  // ulp(qh) / 2
+            const float below = (bits & 0x7FFFFFu) ? half : __fmul_rn(half, 0.5f);  // half the gap below
+            const float err = __fmul_rn(qh, 0x1p-40f);
+            if (ql < __fsub_rn(half, err) && -ql < __fsub_rn(below, err)) return qh;
+        }
+    }
+    return depth_z_binary64(w0, w1, w2, d.Z[0], d.Z[1], d.Z[2], d.A);
+}
+
 // Depth of the pixel centre (px, py) if covered; writes it with atomicMin.
 __device__ __forceinline__ void depth_pixel(const DTri &d, int64_t i, int64_t j, int32_t w, int32_t h, uint32_t *depth) {
     const int32_t px = 256 * (int32_t)i + 128, py = 256 * (int32_t)j + 128;
@@ -138,10 +199,7 @@ __device__ __forceinline__ void depth_pixel(const DTri &d, int64_t i, int64_t j,
     if (w0 + edge_bias(d.X[2] - d.X[1], d.Y[2] - d.Y[1]) <= 0) return;
     if (w1 + edge_bias(d.X[0] - d.X[2], d.Y[0] - d.Y[2]) <= 0) return;
     if (w2 + edge_bias(d.X[1] - d.X[0], d.Y[1] - d.Y[0]) <= 0) return;
-    const double num = __dadd_rn(__dadd_rn(__dmul_rn(__ll2double_rn(w0), (double)d.Z[0]),
-                                           __dmul_rn(__ll2double_rn(w1), (double)d.Z[1])),
-                                 __dmul_rn(__ll2double_rn(w2), (double)d.Z[2]));
-    float z = __double2float_rn(__ddiv_rn(num, __ll2double_rn(d.A)));
+    float z = depth_z(w0, w1, w2, d);
     z = __fadd_rn(z, 0.0f);  // no negative zero
     if (!LCL_IN(j * (int64_t)w + i, (int64_t)w * h)) return;
     atomicMin(depth + j * (int64_t)w + i, __float_as_uint(z));

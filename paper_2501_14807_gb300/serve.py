@@ -194,6 +194,10 @@ class Server:
         s.cams = [lcl.lcl_camera_from_vp(s.atlas, c.vp, c.width, c.height) for c in spec.cams]
         for c, d in zip(s.cams, s.depths):
             lcl.lcl_depth_render(s.mesh_dev, s.atlas, c, d)
+        # the renders (and the layers' clearing) run on the current stream: a spill, whose copy runs
+        # on the copy stream, waits for them like for an epoch
+        s.busy_until = torch.cuda.Event()
+        s.busy_until.record(torch.cuda.current_stream(self.dev))
         s.buf = buf
         layer_bytes = 0
         if self.pool is not None:   # committed in whole allocation-granularity units

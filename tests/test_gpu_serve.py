@@ -84,3 +84,32 @@ def test_served_results_equal_requests_applied_alone(layer_pool):
         resident_layers = sum(len(sl.layers) for sl in srv.slots if sl.resident)
         assert st["layers"] == resident_layers < sum(m.n_layers for m in models)
     srv.close()
+
+
+@pytest.mark.parametrize("layer_pool", [False, True])
+def test_models_spilled_as_they_are_built_keep_complete_depth_maps(layer_pool):
+    """A model over the budget is spilled right after it is built: the copy to its host image runs on
+    the copy stream and must wait for the depth maps rendered on the build's stream (an image taken
+    too early holds a partly rendered map, and every later lasso on the model reads it)."""
+    models, _ = served_models(6)
+    probe = serve.Server(models[:1], hbm_budget_bytes=1 << 40, layer_pool=layer_pool)
+    one = probe.slots[0].bytes
+    probe.close()
+    del probe
+    torch.cuda.empty_cache()
+    srv = serve.Server(models, hbm_budget_bytes=one, layer_pool=layer_pool)   # one model fits
+    assert srv.spills >= len(models) - 1
+    dev = torch.device("cuda")
+    for spec, sl in zip(models, srv.slots):
+        if sl.resident:
+            continue
+        mesh = lcl.Mesh.from_host(spec.mesh, dev)
+        a = lcl.Atlas(spec.side, spec.side, spec.tile, spec.mesh.n_tri, dev)
+        lcl.lcl_atlas_build(mesh, a)
+        _, _, _, offs_d, _ = sl.lay
+        for o, c in zip(offs_d, spec.cams):
+            d = torch.empty((c.height, c.width), dtype=torch.float32, device=dev)
+            lcl.lcl_depth_render(mesh, a, lcl.lcl_camera_from_vp(a, c.vp, c.width, c.height), d)
+            stored = sl.host["image"][o:o + 4 * c.width * c.height].view(torch.float32).view(c.height, c.width)
+            assert torch.equal(stored.view(torch.int32), d.cpu().view(torch.int32))
+    srv.close()
