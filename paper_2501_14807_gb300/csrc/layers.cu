@@ -91,6 +91,17 @@ __global__ void k_zero2(unsigned long long *x, unsigned long long *y, uint32_t n
     }
 }
 
+// Sums of the warp's lanes: counts below 2^28 in all; a lane's area below 2^63 (at most 2^28 texels
+// of weight below 2^35), cut into three 21-bit pieces whose sums over 32 lanes stay below 2^26, so
+// four 32-bit warp reductions give the exact 64-bit sum.
+__device__ __forceinline__ void warp_sums(uint32_t &c, unsigned long long &a) {
+    c = __reduce_add_sync(0xffffffffu, c);
+    const uint32_t a0 = __reduce_add_sync(0xffffffffu, (uint32_t)(a & 0x1FFFFFull));
+    const uint32_t a1 = __reduce_add_sync(0xffffffffu, (uint32_t)((a >> 21) & 0x1FFFFFull));
+    const uint32_t a2 = __reduce_add_sync(0xffffffffu, (uint32_t)(a >> 42));
+    a = (unsigned long long)a0 + ((unsigned long long)a1 << 21) + ((unsigned long long)a2 << 42);
+}
+
 // Per-label area, four consecutive texels (a quad) per lane and step: a warp reads 128 consecutive
 // texels per step, one 16-byte load of triangle ids and one 4- or 8-byte load of labels per lane.
 // The four weight gathers of a lane are independent loads (a texel whose triangle is its left
@@ -173,10 +184,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_area4(const L *__restrict__ lay
             uint32_t c = wcnt;
             unsigned long long a = warea;
 #pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                c += __shfl_xor_sync(0xffffffffu, c, o);
-                a += __shfl_xor_sync(0xffffffffu, a, o);
-            }
+            warp_sums(c, a);
             if (lane == 0 && c && LCL_IN(wlabel, n_labels)) {
                 atomicAdd(hc + wlabel, (unsigned long long)c);
                 atomicAdd(ha + wlabel, a);
@@ -205,10 +213,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_area4(const L *__restrict__ lay
         uint32_t c = wcnt;
         unsigned long long a = warea;
 #pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            c += __shfl_xor_sync(0xffffffffu, c, o);
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-        }
+        warp_sums(c, a);
         if (lane == 0 && c && LCL_IN(wlabel, n_labels)) {
             atomicAdd(hc + wlabel, (unsigned long long)c);
             atomicAdd(ha + wlabel, a);
