@@ -8,7 +8,8 @@
 //              (128 consecutive texels per warp and step, coalesced loads of triangle ids and
 //              labels, the next step's issued ahead); the four weight gathers of a lane are
 //              independent loads; texels carrying the warp's current label add to per-lane
-//              sums in registers, reduced across the warp only when another label appears;
+//              sums in registers (a quad whose four labels are that label is recognised by one
+//              compare of its label word), reduced across the warp only when another label appears;
 //              the histogram lives in shared memory (64-bit shared atomics) and goes into the
 //              outputs with one global atomic per non-zero bin per CTA.  All sums are
 //              integers, so the result does not depend on the order.
@@ -144,46 +145,61 @@ __global__ void __launch_bounds__(kThreads, 5) k_area4(const L *__restrict__ lay
     };
     uint32_t wlabel = kNone, wcnt = 0;  // the warp's label; this lane's share of its count and area
     unsigned long long warea = 0;
+    // a quad whose four labels are the warp's label matches wl4 (the label in every lane of a word);
+    // wvalid is false until the warp has a label
+    uint32_t wl4 = 0;
+    bool wvalid = false;
+    // tri ids are 32-bit and kNone = 0xFFFFFFFF is not below any 32-bit count, so one compare with
+    // the count decides whether a texel is covered by a valid triangle
+    const uint32_t ntri = n_tri < (int64_t)0xFFFFFFFFu ? (uint32_t)n_tri : 0xFFFFFFFFu;
     if (s0 < s1) load(s0);
     for (int64_t st = s0; st < s1; ++st) {
         const uint32_t ts[4] = {T.x, T.y, T.z, T.w};
-        uint32_t lab[4];
-        if constexpr (sizeof(L) == 1) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) lab[k] = (V >> (8 * k)) & 0xFFu;
-        } else {
-            lab[0] = V.x & 0xFFFFu;
-            lab[1] = V.x >> 16;
-            lab[2] = V.y & 0xFFFFu;
-            lab[3] = V.y >> 16;
-        }
+        const LV Vc = V;
         if (st + 1 < s1) load(st + 1);
         unsigned long long w[4];
         bool vt[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            vt[k] = ts[k] != kNone && ts[k] < (uint64_t)n_tri;
+            vt[k] = ts[k] < ntri;
             w[k] = (vt[k] && (k == 0 || ts[k] != ts[k - 1])) ? __ldg(aw + ts[k]) : 0ull;
         }
 #pragma unroll
         for (int k = 1; k < 4; ++k)
             if (vt[k] && ts[k] == ts[k - 1]) w[k] = w[k - 1];
+        bool same;
+        if constexpr (sizeof(L) == 1) same = wvalid && Vc == wl4;
+        else same = wvalid && Vc.x == wl4 && Vc.y == wl4;
         uint32_t odd = 0;
+        uint32_t lab[4] = {0u, 0u, 0u, 0u};
+        if (same) {  // every texel of the quad carries the warp's label (below n_labels): w is 0 off the mesh
+            wcnt += (uint32_t)vt[0] + (uint32_t)vt[1] + (uint32_t)vt[2] + (uint32_t)vt[3];
+            warea += (w[0] + w[1]) + (w[2] + w[3]);
+        } else {
+            if constexpr (sizeof(L) == 1) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (!vt[k] || lab[k] >= n_labels) continue;
-            if (lab[k] == wlabel) {
-                wcnt += 1;
-                warea += w[k];
+                for (int k = 0; k < 4; ++k) lab[k] = (Vc >> (8 * k)) & 0xFFu;
             } else {
-                odd |= 1u << k;
+                lab[0] = Vc.x & 0xFFFFu;
+                lab[1] = Vc.x >> 16;
+                lab[2] = Vc.y & 0xFFFFu;
+                lab[3] = Vc.y >> 16;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (!vt[k] || lab[k] >= n_labels) continue;
+                if (lab[k] == wlabel) {
+                    wcnt += 1;
+                    warea += w[k];
+                } else {
+                    odd |= 1u << k;
+                }
             }
         }
         const uint32_t bal = __ballot_sync(0xffffffffu, odd != 0);
         if (bal) {  // uniform over the warp
             uint32_t c = wcnt;
             unsigned long long a = warea;
-#pragma unroll
             warp_sums(c, a);
             if (lane == 0 && c && LCL_IN(wlabel, n_labels)) {
                 atomicAdd(hc + wlabel, (unsigned long long)c);
@@ -194,6 +210,8 @@ __global__ void __launch_bounds__(kThreads, 5) k_area4(const L *__restrict__ lay
             for (int k = 0; k < 4; ++k)
                 if (odd & (1u << k)) last = lab[k];
             wlabel = __shfl_sync(0xffffffffu, last, 31 - __clz(bal));
+            wvalid = true;
+            wl4 = sizeof(L) == 1 ? wlabel * 0x01010101u : wlabel * 0x00010001u;
             wcnt = 0;
             warea = 0;
 #pragma unroll
@@ -212,7 +230,6 @@ __global__ void __launch_bounds__(kThreads, 5) k_area4(const L *__restrict__ lay
     {
         uint32_t c = wcnt;
         unsigned long long a = warea;
-#pragma unroll
         warp_sums(c, a);
         if (lane == 0 && c && LCL_IN(wlabel, n_labels)) {
             atomicAdd(hc + wlabel, (unsigned long long)c);

@@ -445,6 +445,8 @@ def test_label_area_bit_exact(dt, n_labels, W, H):
     rng = np.random.default_rng(n_labels)
     L = rng.integers(0, min(np.iinfo(dt).max, n_labels + 30) + 1, size=(H, W)).astype(dt)
     L[min(100, H // 3):min(300, H), 50:400] = 7          # long runs of one label
+    if n_labels <= np.iinfo(dt).max:
+        L[min(30, H // 5):min(90, H), 100:460] = n_labels   # long runs of a label the query ignores
     ec, ea = oracle.label_area(o, L, n_labels)
     c, ar = lcl.lcl_label_area(a, to_dev(L), n_labels)
     assert np.array_equal(to_np(c, np.uint64), ec)
