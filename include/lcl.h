@@ -413,8 +413,9 @@ lcl_status lcl_batch_tune(const lcl_batch_limits *limits, void *workspace, size_
  *    recent request rate (requests decayed with a 1 s time constant), whose layers are first copied
  *    back to their host images; a model's requests join the first epoch after its copy completed;
  *  - per-model FIFO order; continuous batching: each epoch takes, for every ready model with queued
- *    work, the leading run of edits (at most max_edits per layer) or one query, uploads the edits as
- *    one batch (lcl_batch_upload) and replays a captured graph of lcl_batch_launch, then the queries
+ *    work, the leading run of edits (at most max_edits per layer) and the query that follows them, if
+ *    any, uploads the edits as one batch (lcl_batch_upload) and replays a captured graph of
+ *    lcl_batch_launch, then the queries
  *    (lcl_overlay into scratch + lcl_label_area, the tables copied to the request's host buffer);
  *    epochs overlap (max_in_flight), each with its own workspace, staging and graph;
  *  - open-loop arrivals: requests are submitted with their arrival times on the server clock and
@@ -429,7 +430,7 @@ enum { LCL_REQ_SPHERE = 0, LCL_REQ_LASSO = 1, LCL_REQ_QUERY = 2 };
 
 typedef struct {
     size_t arena_bytes;     /* device arena for model images: the HBM budget */
-    int32_t max_in_flight;  /* epochs in flight, 1..8 (0: 2) */
+    int32_t max_in_flight;  /* epochs in flight, 1..8 (0: 4) */
     int32_t max_edits;      /* edits per layer per epoch, 1..LCL_BATCH_MAX_STROKES (0: 64) */
     int32_t max_queries;    /* queries per epoch, 1..1024 (0: 16) */
     int32_t max_labels;     /* largest n_labels of a query, 1..65536 (0: 256) */

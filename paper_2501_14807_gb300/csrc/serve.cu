@@ -304,7 +304,7 @@ bool run_epoch(lcl_server *s, double now, lcl_status *st) {
             continue;  // its requests join an epoch after the copy
         }
         if (m.admitting) continue;
-        // leading edits (at most max_edits per layer), else one query
+        // leading edits (at most max_edits per layer)
         int32_t per_layer[256] = {0};
         std::vector<const lcl_serve_request *> edits;
         while (!m.queue.empty()) {
@@ -314,12 +314,16 @@ bool run_epoch(lcl_server *s, double now, lcl_status *st) {
             edits.push_back(r);
             m.queue.pop_front();
         }
-        if (edits.empty()) {
+        // then the query that follows them (it runs after the epoch's edits on the same stream, so it
+        // sees them; later edits wait for the next epoch)
+        if (!m.queue.empty() && m.queue.front()->kind == LCL_REQ_QUERY &&
+            (int32_t)ep.queries.size() < s->cfg.max_queries) {
             const lcl_serve_request *r = m.queue.front();
-            if (r->kind != LCL_REQ_QUERY || (int32_t)ep.queries.size() >= s->cfg.max_queries) continue;
             m.queue.pop_front();
             ep.queries.push_back({r, 0});
             ep.reqs.push_back(r);
+        } else if (edits.empty()) {
+            continue;
         }
         m.in_epoch = true;
         m.fresh = false;
@@ -505,7 +509,7 @@ double lcl_serve_clock(void) { return now_s(); }
 lcl_status lcl_serve_create(const lcl_serve_config *config, lcl_server **out) {
     if (!config || !out) return fail(LCL_ERR_INVALID_ARG, "NULL argument");
     lcl_serve_config c = *config;
-    if (c.max_in_flight == 0) c.max_in_flight = 2;
+    if (c.max_in_flight == 0) c.max_in_flight = 4;
     if (c.max_edits == 0) c.max_edits = LCL_BATCH_MAX_STROKES;
     if (c.max_queries == 0) c.max_queries = 16;
     if (c.max_labels == 0) c.max_labels = 256;

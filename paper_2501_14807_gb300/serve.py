@@ -571,7 +571,7 @@ class NativeServer:
     models: ServedModel list; hbm_budget_bytes: the device arena for model images."""
 
     def __init__(self, models, hbm_budget_bytes, device="cuda", max_edits_per_layer=lcl.BATCH_MAX_STROKES,
-                 max_in_flight=2, max_labels=256, max_queries=16):
+                 max_in_flight=4, max_labels=256, max_queries=16):
         self.dev = torch.device(device)
         self.lib = lcl.library()
         self.specs = list(models)
