@@ -804,6 +804,16 @@ def native_serving_run(models, budget, sphere_of, lasso_of, rate, duration, seed
     st["host_busy_s"] = round(s1["host_busy_s"] - s0["host_busy_s"], 3)
     st["p99_ms_by_second"] = [round(1e3 * float(np.percentile(lat[(t >= i) & (t < i + 1)], 99)), 2)
                               for i in range(int(duration)) if ((t >= i) & (t < i + 1)).any()]
+    # where a request's time goes: arrival -> its epoch's launch (queued on the host), launch -> the host
+    # seeing the epoch complete, and the GPU time of the epoch itself (events around its work)
+    t_l = np.array([r.t_launch for r in reqs])
+    t_g = np.array([r.t_gpu for r in reqs])
+    wait, after = t_l - t, np.array([r.t_done for r in reqs]) - t_l
+    st["latency_split_ms"] = {
+        "arrival_to_launch_p50_p99": [round(1e3 * float(np.percentile(wait, q)), 3) for q in (50, 99)],
+        "launch_to_done_p50_p99": [round(1e3 * float(np.percentile(after, q)), 3) for q in (50, 99)],
+        "epoch_gpu_p50_p99_max": [round(1e3 * float(np.percentile(t_g[t_g >= 0], q)), 3) for q in (50, 99)] +
+                                 [round(1e3 * float(t_g.max()), 3)] if (t_g >= 0).any() else None}
     if cold.any() and (~cold).any():
         st["p99_ms_resident_half"] = 1e3 * float(np.percentile(lat[~cold], 99))
         st["p99_ms_spillover_half"] = 1e3 * float(np.percentile(lat[cold], 99))

@@ -477,7 +477,8 @@ typedef struct {
     uint64_t tag;
     double t_done;      /* server clock: the host saw the request's epoch complete */
     double t_launch;    /* server clock: its epoch was launched */
-    double _pad;
+    double t_gpu;       /* seconds the GPU spent on its epoch (CUDA events before and after the epoch's
+                           work on the compute stream), -1 if unavailable */
 } lcl_serve_done;
 
 typedef struct {

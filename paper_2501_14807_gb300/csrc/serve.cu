@@ -84,7 +84,8 @@ struct Epoch {
     int64_t seq;
     int slot;
     double t_launch;
-    cudaEvent_t done;
+    cudaEvent_t start = nullptr;  // recorded on the compute stream before the epoch's work (GPU time: start..done)
+    cudaEvent_t done = nullptr;
     std::vector<const lcl_serve_request *> reqs;
     std::vector<Query> queries;
 };
@@ -157,8 +158,8 @@ cudaEvent_t take_event(lcl_server *s) {
         s->event_pool.pop_back();
         return e;
     }
-    cudaEvent_t e = nullptr;
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    cudaEvent_t e = nullptr;  // with timing: an epoch's GPU time is measured between two of them
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
     return e;
 }
 
@@ -368,20 +369,23 @@ bool run_epoch(lcl_server *s, double now, lcl_status *st) {
     }
     for (int32_t mi : used) s->models[mi].in_epoch = false;
     if (ep.reqs.empty()) return false;
-    cudaError_t e = cudaSuccess;
+    ep.start = take_event(s);
+    // a failure from here on ends the loop; the epoch's events go back to the pool (freed by destroy)
+    auto abandon = [&](lcl_status fs) {
+        if (ep.start) s->event_pool.push_back(ep.start);
+        if (ep.done) s->event_pool.push_back(ep.done);
+        *st = fs;
+        return false;
+    };
+    cudaError_t e = ep.start ? cudaEventRecord(ep.start, s->compute) : cudaErrorMemoryAllocation;
+    if (e != cudaSuccess) return abandon(loop_fail(s, e, "epoch start event"));
     if (!sl.bm.empty()) {
         const lcl_status us = batch_upload_impl(&s->limits, sl.bm.data(), (int32_t)sl.bm.size(), sl.bs.data(),
                                                 (int32_t)sl.bs.size(), sl.bl.data(), (int32_t)sl.bl.size(), sl.ws,
                                                 sl.ws_bytes, sl.staging, sl.staging_bytes, s->compute);
-        if (us != LCL_OK) {
-            *st = loop_fail_status(s, us, "batch upload");
-            return false;
-        }
+        if (us != LCL_OK) return abandon(loop_fail_status(s, us, "batch upload"));
         e = cudaGraphLaunch(sl.graph, s->compute);
-        if (e != cudaSuccess) {
-            *st = loop_fail(s, e, "batch graph launch");
-            return false;
-        }
+        if (e != cudaSuccess) return abandon(loop_fail(s, e, "batch graph launch"));
     }
     const size_t n_tab = 2 * (size_t)s->cfg.max_labels;
     for (size_t qi = 0; qi < ep.queries.size(); ++qi) {
@@ -394,24 +398,15 @@ bool run_epoch(lcl_server *s, double now, lcl_status *st) {
         uint64_t *tab = sl.tables + qi * n_tab;
         lcl_status qs = overlay_impl(&m.atlas, la, lb, out, 1, r->op, 0u, s->compute);
         if (qs == LCL_OK) qs = label_area_impl(&m.atlas, out, 1, (uint32_t)r->n_labels, tab, tab + r->n_labels, s->compute);
-        if (qs != LCL_OK) {
-            *st = loop_fail_status(s, qs, "query launch");
-            return false;
-        }
+        if (qs != LCL_OK) return abandon(loop_fail_status(s, qs, "query launch"));
         q.host_off = qi * n_tab;
         e = cudaMemcpyAsync(sl.host_tables + q.host_off, tab, 16 * (size_t)r->n_labels, cudaMemcpyDeviceToHost,
                             s->compute);
-        if (e != cudaSuccess) {
-            *st = loop_fail(s, e, "query result copy");
-            return false;
-        }
+        if (e != cudaSuccess) return abandon(loop_fail(s, e, "query result copy"));
     }
     ep.done = take_event(s);
     e = ep.done ? cudaEventRecord(ep.done, s->compute) : cudaErrorMemoryAllocation;
-    if (e != cudaSuccess) {
-        *st = loop_fail(s, e, "epoch event");
-        return false;
-    }
+    if (e != cudaSuccess) return abandon(loop_fail(s, e, "epoch event"));
     for (int32_t mi : used) s->models[mi].last_seq = ep.seq;
     ep.t_launch = now_s();
     sl.busy = true;
@@ -450,17 +445,21 @@ void serve_loop(lcl_server *s) {
                     break;
                 }
                 const double t = now_s();
+                float gpu_ms = 0.0f;
+                if (cudaEventElapsedTime(&gpu_ms, ep.start, ep.done) != cudaSuccess) gpu_ms = -1.0f;
                 Slot &sl = s->slots[ep.slot];
                 for (const Query &qq : ep.queries)
                     std::memcpy(qq.req->result, sl.host_tables + qq.host_off, 16 * (size_t)qq.req->n_labels);
                 {
                     std::lock_guard<std::mutex> lock(s->mu);
-                    for (const lcl_serve_request *r : ep.reqs) s->done.push_back({r->tag, t, ep.t_launch, 0.0});
+                    for (const lcl_serve_request *r : ep.reqs)
+                        s->done.push_back({r->tag, t, ep.t_launch, gpu_ms < 0.0f ? -1.0 : 1e-3 * gpu_ms});
                     s->n_done += ep.reqs.size();
                 }
                 s->completed_seq = ep.seq;
                 sl.busy = false;
                 s->event_pool.push_back(ep.done);
+                s->event_pool.push_back(ep.start);
                 s->in_flight.pop_front();
                 worked = true;
             }
@@ -758,8 +757,10 @@ lcl_status lcl_serve_destroy(lcl_server *s) {
     if (s->copy) cudaStreamSynchronize(s->copy);
     for (Slot &sl : s->slots)
         if (sl.graph) cudaGraphExecDestroy(sl.graph);
-    for (Epoch &ep : s->in_flight)
+    for (Epoch &ep : s->in_flight) {
         if (ep.done) cudaEventDestroy(ep.done);
+        if (ep.start) cudaEventDestroy(ep.start);
+    }
     for (Model &m : s->models)
         if (m.ready) cudaEventDestroy(m.ready);
     for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);

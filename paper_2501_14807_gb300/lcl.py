@@ -122,7 +122,7 @@ class lcl_serve_model(C.Structure):
 
 
 class lcl_serve_done(C.Structure):
-    _fields_ = [("tag", C.c_uint64), ("t_done", C.c_double), ("t_launch", C.c_double), ("_pad", C.c_double)]
+    _fields_ = [("tag", C.c_uint64), ("t_done", C.c_double), ("t_launch", C.c_double), ("t_gpu", C.c_double)]
 
 
 class lcl_serve_stats(C.Structure):

@@ -61,6 +61,7 @@ class Request:
     t_done: float = -1.0
     result: object = None    # QUERY: (counts, areas) as numpy uint64 arrays
     t_launch: float = -1.0   # native server: when the request's epoch was launched
+    t_gpu: float = -1.0      # native server: seconds the GPU spent on the request's epoch
 
 
 @dataclass
@@ -688,6 +689,7 @@ class NativeServer:
                 r = requests[out[k].tag]
                 r.t_done = out[k].t_done - t0
                 r.t_launch = out[k].t_launch - t0
+                r.t_gpu = out[k].t_gpu
             left -= got.value
             if got.value:
                 last = time.perf_counter()
