@@ -25,6 +25,9 @@ def test_native_server_results_equal_the_oracle_and_requests_alone():
     st = srv.stats()
     assert st["done"] == st["submitted"] == len(reqs)
     assert all(r.t_done >= r.t_arrive for r in reqs)
+    # each completion carries its epoch's GPU time: the epoch's work starts after the request arrived and
+    # ends before the host sees it complete
+    assert all(0.0 <= r.t_gpu <= r.t_done - r.t_arrive + 1e-4 for r in reqs)
     assert st["spills"] > 0 and st["admissions"] > len(models) // 2 and st["epochs"] > 1
     served = {mi: srv.layers_of(mi) for mi in range(len(models))}
     oracle_layers, oracle_results = replay_oracle(models, reqs)
