@@ -645,10 +645,28 @@ size_t batch_ws_bytes(const lcl_batch_limits *lim) { return limits_ok(lim) ? b_l
 
 size_t batch_host_bytes(const lcl_batch_limits *lim) { return limits_ok(lim) ? b_layout(*lim).upload : 0; }
 
+namespace {
+__global__ void k_copy16(uint4 *__restrict__ dst, const uint4 *__restrict__ src, int64_t n16) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+}  // namespace
+
+cudaError_t copy_by_kernel(void *dst, const void *src, size_t n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int64_t n16 = (int64_t)(n / 16);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n16 + kThreads - 1) / kThreads, 2 * sm_count()));
+    k_copy16<<<grid, kThreads, 0, st>>>(static_cast<uint4 *>(dst), static_cast<const uint4 *>(src), n16);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// staging_dev: the device address of host_staging (pinned, mapped) or NULL; with it the descriptors
+// go to the workspace by a copy kernel instead of the copy engines.
 lcl_status batch_upload_impl(const lcl_batch_limits *lim, const lcl_batch_model *models, int32_t n_models,
                              const lcl_batch_stroke *strokes, int32_t n_strokes, const lcl_batch_lasso *lassos,
                              int32_t n_lassos, void *ws, size_t ws_bytes, void *host_staging, size_t host_bytes,
-                             cudaStream_t st) {
+                             cudaStream_t st, const void *staging_dev) {
     if (!limits_ok(lim)) return fail(LCL_ERR_INVALID_ARG, "batch limits out of range");
     if (!ws || !host_staging) return fail(LCL_ERR_INVALID_ARG, "batch workspace or staging is NULL");
     int64_t n_supers = 0, n_tiles = 0;
@@ -728,7 +746,11 @@ lcl_status batch_upload_impl(const lcl_batch_limits *lim, const lcl_batch_model 
     char *dst = static_cast<char *>(ws);
     for (const auto &pc : part) {
         if (pc[1] == 0) continue;
-        const cudaError_t e = cudaMemcpyAsync(dst + pc[0], img + pc[0], pc[1], cudaMemcpyHostToDevice, st);
+        // by kernel: whole 16-byte words (regions are 256-byte aligned and sized, so rounding up stays
+        // inside the region in both images)
+        const cudaError_t e = staging_dev ? copy_by_kernel(dst + pc[0], static_cast<const char *>(staging_dev) + pc[0],
+                                                           (pc[1] + 15) & ~size_t(15), st)
+                                          : cudaMemcpyAsync(dst + pc[0], img + pc[0], pc[1], cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "batch descriptor upload");
     }
     return LCL_OK;

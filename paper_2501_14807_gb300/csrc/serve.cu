@@ -13,7 +13,12 @@
 //    copy is queued behind the spill's;
 //  - a model is spilled only when its last epoch has completed (the compute stream no longer uses it),
 //    and it joins an epoch only once its admission copy has completed;
-//  - a slot (workspace, staging, graph, query scratch) is reused only after its epoch has completed.
+//  - a slot (workspace, staging, graph, query scratch) is reused only after its epoch has completed;
+//  - the compute stream uses no copy engine: an epoch's descriptors are read from the slot's pinned
+//    staging, and its query tables written to the slot's pinned tables, by copy kernels through the
+//    memory's mapped device address, so epochs never wait behind admission or spill copies (a run with
+//    a host-to-device copy loop beside the server made an epoch's GPU time 0.2 ms -> 5.5 ms when the
+//    descriptors went through the copy engines).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -73,6 +78,11 @@ struct Slot {
     uint8_t *scratch = nullptr;       // max_queries overlay outputs
     uint64_t *tables = nullptr;       // max_queries x 2 max_labels (device)
     uint64_t *host_tables = nullptr;  // the same (pinned host)
+    // device addresses of the pinned staging and host tables (NULL if the memory is not mapped): through
+    // them the epoch's descriptors and query tables move by copy kernels on the compute stream, so an
+    // epoch never queues behind admission or spill copies on the copy engines
+    const void *staging_dev = nullptr;
+    uint64_t *host_tables_dev = nullptr;
     cudaGraphExec_t graph = nullptr;
     bool busy = false;
     std::vector<lcl_batch_model> bm;
@@ -382,7 +392,7 @@ bool run_epoch(lcl_server *s, double now, lcl_status *st) {
     if (!sl.bm.empty()) {
         const lcl_status us = batch_upload_impl(&s->limits, sl.bm.data(), (int32_t)sl.bm.size(), sl.bs.data(),
                                                 (int32_t)sl.bs.size(), sl.bl.data(), (int32_t)sl.bl.size(), sl.ws,
-                                                sl.ws_bytes, sl.staging, sl.staging_bytes, s->compute);
+                                                sl.ws_bytes, sl.staging, sl.staging_bytes, s->compute, sl.staging_dev);
         if (us != LCL_OK) return abandon(loop_fail_status(s, us, "batch upload"));
         e = cudaGraphLaunch(sl.graph, s->compute);
         if (e != cudaSuccess) return abandon(loop_fail(s, e, "batch graph launch"));
@@ -400,8 +410,9 @@ bool run_epoch(lcl_server *s, double now, lcl_status *st) {
         if (qs == LCL_OK) qs = label_area_impl(&m.atlas, out, 1, (uint32_t)r->n_labels, tab, tab + r->n_labels, s->compute);
         if (qs != LCL_OK) return abandon(loop_fail_status(s, qs, "query launch"));
         q.host_off = qi * n_tab;
-        e = cudaMemcpyAsync(sl.host_tables + q.host_off, tab, 16 * (size_t)r->n_labels, cudaMemcpyDeviceToHost,
-                            s->compute);
+        e = sl.host_tables_dev ? copy_by_kernel(sl.host_tables_dev + q.host_off, tab, 16 * (size_t)r->n_labels, s->compute)
+                               : cudaMemcpyAsync(sl.host_tables + q.host_off, tab, 16 * (size_t)r->n_labels,
+                                                 cudaMemcpyDeviceToHost, s->compute);
         if (e != cudaSuccess) return abandon(loop_fail(s, e, "query result copy"));
     }
     ep.done = take_event(s);
@@ -629,6 +640,14 @@ lcl_status lcl_serve_start(lcl_server *s, void *arena, void *work, size_t work_b
         sl.staging_bytes = lcl_batch_staging_bytes(&s->limits);
         sl.staging = h;
         sl.host_tables = reinterpret_cast<uint64_t *>(h + a256(sl.staging_bytes));
+        void *dp = nullptr;
+        if (cudaHostGetDevicePointer(&dp, sl.staging, 0) == cudaSuccess && dp) {
+            sl.staging_dev = dp;
+            dp = nullptr;
+            if (cudaHostGetDevicePointer(&dp, sl.host_tables, 0) == cudaSuccess && dp)
+                sl.host_tables_dev = static_cast<uint64_t *>(dp);
+        }
+        cudaGetLastError();  // a host buffer that is not mapped leaves the copy-engine path
         // one captured graph of the batched launch per slot: its shape depends only on the limits
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(s->compute, cudaStreamCaptureModeThreadLocal);
