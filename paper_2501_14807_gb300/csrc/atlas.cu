@@ -403,11 +403,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_resolve(const TriSetup *__restr
     // tiles of 32 texels or more on a width that is a multiple of 32: each warp's 32 texels are one
     // aligned coverage word (uniform over the grid)
     const bool aligned = T >= 32 && (w & 31) == 0;
-    // the triangle id of the thread's texel in step it + 1 is loaded during step it
+    // the triangle id of the thread's texel in step it + 1 is loaded during step it; T is a power of
+    // two, so the texel's row and column in the tile come from a shift and a mask
+    const int tshift = __ffs(T) - 1;
     auto texel = [&](int step, int32_t &x, int32_t &y, int64_t &l) {
         const int32_t i = step * kThreads + threadIdx.x;
-        x = tx * T + (i % T);
-        y = ty * T + i / T;
+        x = tx * T + (i & (T - 1));
+        y = ty * T + (i >> tshift);
         const bool v = i < n_tex_tile && x < w && y < h && LCL_IN((int64_t)y * w + x, (int64_t)w * h);
         l = v ? (int64_t)y * w + x : -1;
     };

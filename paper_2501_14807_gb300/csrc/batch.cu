@@ -366,10 +366,11 @@ __device__ __forceinline__ void apply_part(const BModel &M, const BItem &it, int
     const AtlasDev &a = M.a;
     L *layer = static_cast<L *>(M.layer);
     if (!LCL_IN(it.tile, (int64_t)a.tiles_x * a.tiles_y)) return;
-    const int32_t tx = it.tile % a.tiles_x, ty = it.tile / a.tiles_x;
+    int32_t tx, ty;
+    tile_xy(a, it.tile, tx, ty);
     const int32_t qpr = a.T / 4;
     for (int32_t qd = q0 + (int32_t)threadIdx.x; qd < q1; qd += (int32_t)blockDim.x) {
-        const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
+        const int32_t x = tx * a.T + 4 * (qd & (qpr - 1)), y = ty * a.T + (qd >> (__ffs(qpr) - 1));
         if (x >= a.w || y >= a.h) continue;
         const int64_t l = (int64_t)y * a.w + x;
         if (!LCL_IN(l + 3, (int64_t)a.w * a.h)) continue;

@@ -120,8 +120,9 @@ __device__ __forceinline__ Item load_item(const AtlasDev &a, const uint32_t *__r
     const uint32_t entry = __ldg(list + (item >> cpt_log2));
     const uint32_t tile = entry & ~kInsideTile;
     const int32_t qd = (int32_t)((item & ((1u << cpt_log2) - 1)) * kThreads + threadIdx.x);
-    const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
+    int32_t tx, ty;
+    tile_xy(a, tile, tx, ty);
+    const int32_t x = tx * a.T + 4 * (qd & (qpr - 1)), y = ty * a.T + (qd >> (__ffs(qpr) - 1));
     if (qd < nq && x < a.w && y < a.h && LCL_IN((int64_t)y * a.w + x + 3, (int64_t)a.w * a.h)) {
         it.l = (int64_t)y * a.w + x;
         if (entry & kInsideTile) {  // inside the sphere: the coverage bits decide, no positions needed
@@ -261,7 +262,8 @@ __global__ void __launch_bounds__(kThreads, 6) k_sphere_step(AtlasDev a, L *__re
         for (uint32_t b = (gridDim.x - 1 - blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); b < n_in; b += warps) {
             if (!LCL_IN(cap - 1 - (int64_t)b, cap)) break;
             const uint32_t tile = __ldg(list + (cap - 1 - (int64_t)b));
-            const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+            int32_t tx, ty;
+            tile_xy(a, tile, tx, ty);
             for (int32_t wi = threadIdx.x & 31; wi < words; wi += 32) {
                 const int32_t x = tx * a.T + 32 * (wi % wpr), y = ty * a.T + wi / wpr;
                 if (x >= a.w || y >= a.h) continue;   // x < w implies x + 31 < w (w a multiple of 32)
@@ -412,8 +414,9 @@ __device__ __forceinline__ GItem load_gquad(const AtlasDev &a, const GEnt &e, ui
     it.X = it.Y = it.Z = make_int4(INT32_MIN, 0, 0, 0);
     if (e.tile == kNone) return it;
     const int32_t qd = (int32_t)((item & ((1u << cpt_log2) - 1)) * kThreads + threadIdx.x);
-    const int32_t tx = e.tile % a.tiles_x, ty = e.tile / a.tiles_x;
-    const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
+    int32_t tx, ty;
+    tile_xy(a, e.tile, tx, ty);
+    const int32_t x = tx * a.T + 4 * (qd & (qpr - 1)), y = ty * a.T + (qd >> (__ffs(qpr) - 1));
     const int64_t n_tex = (int64_t)a.w * a.h;
     (void)n_tex;
     if (qd < nq && x < a.w && y < a.h && LCL_IN((int64_t)y * a.w + x + 3, n_tex)) {
@@ -549,7 +552,8 @@ __global__ void __launch_bounds__(kThreads, 5) k_group_apply(AtlasDev a, L *__re
             entry(b + warps, next_tile, next_mask);
             if (!mask || tile == kNone) continue;  // uniform over the warp
             const uint32_t label = g.s[31 - __clz(mask)].label;
-            const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+            int32_t tx, ty;
+            tile_xy(a, tile, tx, ty);
             uint32_t c = 0u;
             for (int32_t wi = lane; wi < words; wi += 32) {
                 const int32_t x = tx * a.T + 32 * (wi % wpr), y = ty * a.T + wi / wpr;
@@ -724,9 +728,10 @@ __global__ void __launch_bounds__(kThreads) k_lasso_apply(AtlasDev a, L *__restr
         const uint32_t entry = list[i];
         const bool inside = (entry & kInsideTile) != 0u;  // uniform over the CTA
         const uint32_t tile = entry & ~kInsideTile;
-        const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+        int32_t tx, ty;
+        tile_xy(a, tile, tx, ty);
         for (int32_t qd = threadIdx.x; qd < nq; qd += kThreads) {
-            const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
+            const int32_t x = tx * a.T + 4 * (qd & (qpr - 1)), y = ty * a.T + (qd >> (__ffs(qpr) - 1));
             if (x >= a.w || y >= a.h) continue;
             const int64_t l = (int64_t)y * a.w + x;
             if (!LCL_IN(l + 3, n_tex)) continue;
@@ -796,9 +801,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_tool_apply(AtlasDev a, L *__res
     for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
         if (!LCL_IN(i, (int64_t)a.tiles_x * a.tiles_y)) break;
         const uint32_t tile = list[i] & ~kInsideTile;  // the tool's cull lists plain tiles
-        const int32_t tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+        int32_t tx, ty;
+        tile_xy(a, tile, tx, ty);
         for (int32_t qd = threadIdx.x; qd < nq; qd += kThreads) {
-            const int32_t x = tx * a.T + 4 * (qd % qpr), y = ty * a.T + qd / qpr;
+            const int32_t x = tx * a.T + 4 * (qd & (qpr - 1)), y = ty * a.T + (qd >> (__ffs(qpr) - 1));
             if (x >= a.w || y >= a.h) continue;
             const int64_t l = (int64_t)y * a.w + x;
             if (!LCL_IN(l + 3, n_tex)) continue;

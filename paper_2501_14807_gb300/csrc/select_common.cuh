@@ -15,7 +15,20 @@ struct AtlasDev {
     const uint32_t *cover;
     const int32_t *tile_box, *super_box;
     int32_t w, h, T, tiles_x, tiles_y, supers_x, supers_y;
+    uint32_t tdiv_m, tdiv_s;  // tile index t -> tile row: (t tdiv_m) >> tdiv_s = t / tiles_x (tile_row)
 };
+
+// Multiplier and shift that divide every n < 2^24 exactly by d, 1 <= d <= 2^24, without a division
+// (Granlund and Montgomery, "Division by invariant integers using multiplication", 1994, Thm 4.2):
+// with l = ceil(log2 d) and m = ceil(2^(24+l) / d), m d = 2^(24+l) + e with 0 <= e < d <= 2^l, so
+// n m / 2^(24+l) = n / d + n e / (d 2^(24+l)) and the second term is below 1/d for n < 2^24, which
+// leaves the floor unchanged; m <= 2^25, so n m < 2^49.  Tile indices are below 2^22.
+inline void tile_divisor(int32_t d, uint32_t *m, uint32_t *s) {
+    int l = 0;
+    while ((int64_t(1) << l) < d) ++l;
+    *m = (uint32_t)(((uint64_t(1) << (24 + l)) + (uint64_t)d - 1) / (uint64_t)d);
+    *s = (uint32_t)(24 + l);
+}
 
 inline AtlasDev dev_view(const lcl_atlas *a) {
     AtlasDev d;
@@ -32,7 +45,14 @@ inline AtlasDev dev_view(const lcl_atlas *a) {
     d.tiles_y = a->tiles_y;
     d.supers_x = a->supers_x;
     d.supers_y = a->supers_y;
+    tile_divisor(d.tiles_x > 0 ? d.tiles_x : 1, &d.tdiv_m, &d.tdiv_s);
     return d;
+}
+
+// Column and row of tile t (t < 2^24) of the atlas's tile grid.
+__device__ __forceinline__ void tile_xy(const AtlasDev &a, uint32_t t, int32_t &tx, int32_t &ty) {
+    ty = (int32_t)(((uint64_t)t * a.tdiv_m) >> a.tdiv_s);
+    tx = (int32_t)t - ty * a.tiles_x;
 }
 
 struct SphereArg {
