@@ -411,6 +411,9 @@ def run_ours(args):
         if (world == 1 and args.serving_models > 0) else None
     # the batching workload (256 models, 64 queued strokes each), outside the timed region
     batch = batch_summary(args.batch_models, 5, 2, torch_device=local) if (world == 1 and args.batch_models > 0) else None
+    # the single large model on 16 u16 layers, as its own run in a child process
+    large = large_summary(args.large_steps) if (world == 1 and args.config == "roofline" and args.large_steps > 0) \
+        else None
     peak, peak_kind = peaks()
     sph_inside = int(sum(int(x.sum()) for x in inside_per_layer))
     sph_bytes = sph_hits * (12 + w.dtype_bytes)          # the per-unit bytes of the hot-path scope: 12 B + label
@@ -453,6 +456,7 @@ def run_ours(args):
         "clocks": clk,
         "serving": serving,
         "batch": batch,
+        "large": large,
         "breakdown": {"sphere_ms_per_step": sph_ms / args.steps, "sphere_hit_texels": sph_hits,
                       "lasso_hit_texels": las_hits, "lasso_hit_texels_each": las_each, "texels_per_step": texels},
         "rows": row_rooflines(w, row_ms, args.steps, sph_bytes, sph_hits, las_hits, peak),
@@ -821,6 +825,36 @@ def native_serving_run(models, budget, sphere_of, lasso_of, rate, duration, seed
     return st
 
 
+def large_summary(steps):
+    """The single large model (a 1M-triangle vessel in ~2k charts shelf-packed into a 4096^2 atlas,
+    16 u16 layers, 10k sphere strokes, 200 lassos on 2048^2 depth maps), run by this script in a
+    child process (`--config large`), outside the headline's timed region: its step throughput,
+    per-row times, end-to-end figure and clocks.  A failure is reported in the line instead of
+    ending the run."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--config", "large", "--steps", str(steps), "--warmup", "3",
+           "--cpu-rows", "0", "--serving-models", "0", "--batch-models", "0", "--large-steps", "0"]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=900, cwd=ROOT)
+    except subprocess.TimeoutExpired:
+        return {"error": "the large-model run timed out"}
+    return parse_large(r.returncode, r.stdout, r.stderr)
+
+
+def parse_large(rc, stdout, stderr):
+    """The large-model summary from the child run's output (its last JSON line)."""
+    lines = [ln for ln in stdout.splitlines() if ln.startswith("{")]
+    if rc != 0 or not lines:
+        tail = stderr.strip().splitlines()[-1:] if stderr else []
+        return {"error": f"the large-model run exited {rc}: {' '.join(tail)}"}
+    d = json.loads(lines[-1])
+    return {"command": "bench.py --config large (child process)", "workload": d["config"]["workload"],
+            "value": d["value"], "unit": d["unit"], "ms_per_step": d["ms_per_step"], "steps": d["steps"],
+            "warmup": d["warmup"], "dtype": d["dtype"],
+            "rows": {k: {kk: v[kk] for kk in ("ms_per_step", "frac") if kk in v} for k, v in d["rows"].items()},
+            "sphere_frac_of_group_bytes": d["roofline"].get("frac_of_group_bytes"),
+            "e2e": d["e2e"]["value"], "gpu_launches": d["gpu_launches"], "clocks": d["clocks"]}
+
+
 def serving_summary(n_models, rate, duration):
     """The serving workload for the headline line: n_models models, an HBM budget that holds the
     first half (the resident set) and spillover models admitted on demand, Poisson arrivals, served by
@@ -1175,6 +1209,8 @@ def main():
                     help="models of the serving run reported in the headline line (0: skip)")
     ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="length of the headline serving trace (Poisson 20k requests/s)")
+    ap.add_argument("--large-steps", type=int, default=5,
+                    help="timed steps of the large-model (16 u16 layers) run reported in the headline line (0: skip)")
     ap.add_argument("--atlas-side", type=int, default=None,
                     help="mid config: atlas side (default 4096; the mesh is scaled with it)")
     ap.add_argument("--strokes", type=int, default=None)

@@ -172,3 +172,20 @@ def test_sphere_group_bytes_against_a_plain_loop():
             if reach:
                 exp += cnt[t] * 2 + (cnt[t] * 12 if cross else cnt[t] / 8)
     assert abs(got - exp) < 1e-6 * exp and exp > 0
+
+
+def test_large_model_summary_from_the_child_run():
+    child = {"config": {"workload": "vessel-1M-charts-4096sq-u16: ..."}, "value": 123.0, "unit": "Gtexels/s",
+             "ms_per_step": 40.0, "steps": 5, "warmup": 3, "dtype": "int64",
+             "rows": {"sphere": {"ms_per_step": 20.0, "frac": 0.5, "what": "x"}, "atlas": {"ms_per_step": 3.0}},
+             "roofline": {"frac_of_group_bytes": 0.3}, "e2e": {"value": 100.0}, "gpu_launches": 77,
+             "clocks": {"sm_mhz": 2070.0}}
+    out = "warning line\n" + json.dumps({"value": 1}) + "\n" + json.dumps(child) + "\n"
+    s = bench.parse_large(0, out, "")
+    assert s["value"] == 123.0 and s["ms_per_step"] == 40.0 and s["dtype"] == "int64"
+    assert s["rows"] == {"sphere": {"ms_per_step": 20.0, "frac": 0.5}, "atlas": {"ms_per_step": 3.0}}
+    assert s["sphere_frac_of_group_bytes"] == 0.3 and s["e2e"] == 100.0 and s["gpu_launches"] == 77
+    # a failed child run is reported, not raised
+    bad = bench.parse_large(1, "", "Traceback ...\nRuntimeError: out of memory\n")
+    assert "error" in bad and "out of memory" in bad["error"]
+    assert "error" in bench.parse_large(0, "no json here\n", "")
