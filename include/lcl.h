@@ -505,8 +505,11 @@ size_t lcl_serve_work_bytes(const lcl_server *server);
 size_t lcl_serve_host_work_bytes(const lcl_server *server);
 
 /* Starts the loop thread.  arena: device, config.arena_bytes, 256-byte aligned; work: device,
- * lcl_serve_work_bytes; host_work: pinned host, lcl_serve_host_work_bytes.  Models are admitted in
- * registration order while they fit.  Errors: LCL_ERR_INVALID_ARG, LCL_ERR_CUDA. */
+ * lcl_serve_work_bytes; host_work: pinned host, lcl_serve_host_work_bytes.  When host_work is mapped
+ * into the device's address space (pinned memory under unified addressing is), each epoch reads its
+ * descriptors from it and writes its query tables to it with copy kernels, so epochs do not wait
+ * behind admission and spill copies on the copy engines; otherwise they use cudaMemcpyAsync.  Models
+ * are admitted in registration order while they fit.  Errors: LCL_ERR_INVALID_ARG, LCL_ERR_CUDA. */
 lcl_status lcl_serve_start(lcl_server *server, void *arena, void *work, size_t work_bytes, void *host_work,
                            size_t host_work_bytes);
 
