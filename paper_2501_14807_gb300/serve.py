@@ -21,7 +21,7 @@ textures).  This module is the server-side counterpart for many models at once:
   (``lcl_batch_upload``) and replays a CUDA graph of the batched launch, followed by the queries
   (``lcl_overlay`` + ``lcl_label_area``) on one compute stream, and records an event; requests that
   arrive meanwhile join the next epoch, which is prepared on the host while the previous one runs
-  (two epochs in flight, each with its own workspace, staging and graph);
+  (several epochs in flight, each with its own workspace, staging and graph);
 * one launch shape for every epoch: the workspaces are sized for the largest possible epoch (every
   layer of every model with a full queue), so the graph captured once per in-flight slot serves
   every epoch;
