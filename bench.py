@@ -785,6 +785,22 @@ def serving_setup(n_models, seed=5):
     return models, budget, sphere_of, lasso_of
 
 
+def latency_split(reqs):
+    """Where the served requests' time goes, in ms (p50 and p99): arrival -> their epoch's launch
+    (queued on the host: admissions, epochs in flight), launch -> the host seeing the epoch complete,
+    and the GPU time of the epoch itself (events around its work; -1 where unavailable)."""
+    t = np.array([r.t_arrive for r in reqs])
+    t_l = np.array([r.t_launch for r in reqs])
+    t_g = np.array([r.t_gpu for r in reqs])
+    wait, after = t_l - t, np.array([r.t_done for r in reqs]) - t_l
+    ok = t_g >= 0
+    return {
+        "arrival_to_launch_p50_p99": [round(1e3 * float(np.percentile(wait, q)), 3) for q in (50, 99)],
+        "launch_to_done_p50_p99": [round(1e3 * float(np.percentile(after, q)), 3) for q in (50, 99)],
+        "epoch_gpu_p50_p99_max": ([round(1e3 * float(np.percentile(t_g[ok], q)), 3) for q in (50, 99)] +
+                                  [round(1e3 * float(t_g[ok].max()), 3)]) if ok.any() else None}
+
+
 def native_serving_run(models, budget, sphere_of, lasso_of, rate, duration, seed=5):
     """One open-loop run of the native server (lcl_serve_*) after a 0.2 s warm-up trace: latency
     statistics (overall, per second of arrival, hot half vs spillover models) and the server's
@@ -808,16 +824,7 @@ def native_serving_run(models, budget, sphere_of, lasso_of, rate, duration, seed
     st["host_busy_s"] = round(s1["host_busy_s"] - s0["host_busy_s"], 3)
     st["p99_ms_by_second"] = [round(1e3 * float(np.percentile(lat[(t >= i) & (t < i + 1)], 99)), 2)
                               for i in range(int(duration)) if ((t >= i) & (t < i + 1)).any()]
-    # where a request's time goes: arrival -> its epoch's launch (queued on the host), launch -> the host
-    # seeing the epoch complete, and the GPU time of the epoch itself (events around its work)
-    t_l = np.array([r.t_launch for r in reqs])
-    t_g = np.array([r.t_gpu for r in reqs])
-    wait, after = t_l - t, np.array([r.t_done for r in reqs]) - t_l
-    st["latency_split_ms"] = {
-        "arrival_to_launch_p50_p99": [round(1e3 * float(np.percentile(wait, q)), 3) for q in (50, 99)],
-        "launch_to_done_p50_p99": [round(1e3 * float(np.percentile(after, q)), 3) for q in (50, 99)],
-        "epoch_gpu_p50_p99_max": [round(1e3 * float(np.percentile(t_g[t_g >= 0], q)), 3) for q in (50, 99)] +
-                                 [round(1e3 * float(t_g.max()), 3)] if (t_g >= 0).any() else None}
+    st["latency_split_ms"] = latency_split(reqs)
     if cold.any() and (~cold).any():
         st["p99_ms_resident_half"] = 1e3 * float(np.percentile(lat[~cold], 99))
         st["p99_ms_spillover_half"] = 1e3 * float(np.percentile(lat[cold], 99))

@@ -189,3 +189,14 @@ def test_large_model_summary_from_the_child_run():
     bad = bench.parse_large(1, "", "Traceback ...\nRuntimeError: out of memory\n")
     assert "error" in bad and "out of memory" in bad["error"]
     assert "error" in bench.parse_large(0, "no json here\n", "")
+
+
+def test_latency_split_of_served_requests():
+    R = lambda a, l, d, g: SimpleNamespace(t_arrive=a, t_launch=l, t_done=d, t_gpu=g)  # noqa: E731
+    reqs = [R(0.0, 0.001, 0.003, 0.0005) for _ in range(99)] + [R(0.0, 0.050, 0.052, 0.002)]
+    s = bench.latency_split(reqs)
+    assert s["arrival_to_launch_p50_p99"][0] == 1.0 and 1.0 < s["arrival_to_launch_p50_p99"][1] <= 50.0
+    assert s["launch_to_done_p50_p99"] == [2.0, 2.0]
+    assert s["epoch_gpu_p50_p99_max"][0] == 0.5 and s["epoch_gpu_p50_p99_max"][2] == 2.0
+    # no GPU times (a server that could not time its epochs): that part is null
+    assert bench.latency_split([R(0.0, 0.001, 0.002, -1.0)])["epoch_gpu_p50_p99_max"] is None
